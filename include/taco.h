@@ -1,0 +1,181 @@
+/*
+ * taco.h -- C ABI of the GB300 (sm_103a) TaCo query path.
+ *
+ * TaCo (arXiv 2603.24919) answers k-approximate-nearest-neighbour queries (Def. 3) over a
+ * dataset D of n points in R^d. The index (Alg. 3) holds an entropy-balanced orthonormal
+ * transform B (Alg. 1, Alg. 2), and for each of N_s subspaces of s transformed
+ * dimensions an inverted multi-index: two sets of sqrt(K) half-subspace centroids and the
+ * list of point ids in each of the K = sqrt(K)^2 cells. A query (Alg. 6) is transformed,
+ * probes each subspace's cells nearest-first until a collision budget is met (Alg. 4),
+ * counts per point the subspaces it collided in (SC-score, Def. 6), keeps the points of
+ * the highest SC levels (Alg. 5) and returns the k nearest of them by exact distance.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: TACO_OK (0) or a negative TACO_E* code; taco_last_error() then holds a
+ *     message for the calling thread. No entry point aborts the process.
+ *   - Pointers are host or device pointers as each argument states. "host or device"
+ *     arguments are classified with cudaPointerGetAttributes.
+ *   - Work is ordered on the caller's CUDA stream (`stream`, a cudaStream_t; NULL = the
+ *     legacy default stream). Calls return once the work is enqueued, except where an
+ *     argument is a host output, in which case the call synchronises the stream first.
+ *   - Matrices are row-major, float32 unless stated. Point ids are 0-based row numbers.
+ *   - One search at a time per index: searches on one index share its workspace and are
+ *     serialised on the host; two streams searching one index concurrently would race on
+ *     the device.
+ */
+#ifndef TACO_H_
+#define TACO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------------- */
+#define TACO_OK 0
+#define TACO_EINVAL (-1)    /* bad argument: null pointer, size or parameter out of range */
+#define TACO_ENOMEM (-2)    /* device or host allocation failed */
+#define TACO_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define TACO_ETIMEOUT (-4)  /* reserved: a bounded device wait gave up */
+#define TACO_ECAPACITY (-5) /* the request exceeds a compiled capacity (n, k, sqrt_k) */
+#define TACO_EIO (-6)       /* file could not be read or written, or has a bad format */
+
+/* ---- enums ------------------------------------------------------------------------- */
+#define TACO_PREC_FP32 0    /* re-rank candidates with FP32 distances */
+#define TACO_PREC_BF16 1    /* re-rank with a BF16 copy of D, then exact FP32 on a shortlist */
+
+#define TACO_SELECT_LITERAL 0 /* Alg. 5 as printed: stop at j when h[j] > R - sum_{j'>=j} h */
+#define TACO_SELECT_PROSE 1   /* Alg. 5 as described: stop when sum_{j'>=j} h[j'] > R */
+
+/* Compiled capacities. */
+#define TACO_MAX_SUBSPACES 15  /* SC-scores are held in 4-bit counters */
+#define TACO_MAX_SQRT_K 128
+#define TACO_MAX_K 512         /* k, and the BF16 shortlist, per query */
+
+typedef struct taco_index taco_index; /* opaque; owns all device memory of one index */
+
+/* Build parameters (Alg. 3 inputs; Table 1 notation). */
+typedef struct {
+    int32_t n_subspaces;   /* N_s, 1..TACO_MAX_SUBSPACES */
+    int32_t sub_dim;       /* s; N_s * s <= d. Half 1 = first floor(s/2) dims, half 2 = rest */
+    int32_t sqrt_k;        /* sqrt(K): centroids per half-subspace, 1..TACO_MAX_SQRT_K */
+    int32_t kmeans_iters;  /* t: Lloyd iterations of each half-subspace k-means */
+    uint64_t seed;         /* seeds the k-means initial centroids */
+    int32_t keep_bf16;     /* nonzero: also keep a BF16 copy of D for TACO_PREC_BF16 */
+    int32_t reserved;      /* must be 0 */
+} taco_build_params;
+
+/* Query parameters (Alg. 6 inputs). One struct per query, or one for the whole batch. */
+typedef struct {
+    int32_t k;             /* results wanted, 1..TACO_MAX_K and <= k_stride */
+    int32_t precision;     /* TACO_PREC_*; must be the same for every query of a batch */
+    int64_t budget;        /* collision budget per subspace: B = ceil(alpha * n) >= 1 (Alg. 4) */
+    int64_t rerank_target; /* R = floor(beta * n) >= 0 (Alg. 5) */
+    int32_t select_rule;   /* TACO_SELECT_*; must be the same for every query of a batch */
+    int32_t shortlist_mult;/* TACO_PREC_BF16: exact FP32 re-rank of min(mult*k, TACO_MAX_K) */
+} taco_query_params;
+
+/* An index given by its parts (e.g. built elsewhere); all pointers are host pointers. */
+typedef struct {
+    const double* o_bar;       /* [d]      data mean (Alg. 1) */
+    const double* B;           /* [d][N_s*s] transform; column c of subspace i is B[:, i*s + c] */
+    const double* centroids;   /* [N_s][sqrt_k][s]: row r holds half-1 centroid r in dims
+                                  [0, floor(s/2)) and half-2 centroid r in [floor(s/2), s) */
+    const uint16_t* codes;     /* [N_s][n] cell of each point: r * sqrt_k + c */
+    int32_t n_subspaces, sub_dim, sqrt_k;
+    int32_t reserved;          /* must be 0 */
+} taco_index_parts;
+
+typedef struct {
+    int64_t n;
+    int32_t d, n_subspaces, sub_dim, sqrt_k;
+    int32_t d_pad;             /* row pitch of the device copy of D, in elements */
+    int32_t has_bf16;
+    int32_t n_slabs;           /* id slabs of 32768 points (collision-counter granularity) */
+    int32_t cluster_size;      /* CTAs that share one query's counters */
+    int64_t device_bytes;      /* device memory owned by the index, workspace excluded */
+} taco_index_info;
+
+/* Optional device outputs of taco_search_debug (any may be NULL). */
+typedef struct {
+    float* query_t;            /* [nq][N_s*s] transformed queries B^T (q - o_bar) */
+    uint8_t* probed;           /* [nq][N_s][K] 1 where Alg. 4 retrieved the cell */
+    int64_t* retrieved_num;    /* [nq][N_s] sum of retrieved cell sizes (Alg. 4) */
+    uint8_t* sc;               /* [nq][n] SC-score of every point (Def. 6) */
+    int64_t* collision_num;    /* [nq][N_s+1] collision_num of Alg. 5 */
+    int32_t* last_collision;   /* [nq] last_collision of Alg. 5 (-1 .. N_s) */
+    int64_t* candidate_num;    /* [nq] candidate_num = |C| of Alg. 5 */
+} taco_debug_out;
+
+/*
+ * taco_build_index -- build the index of Alg. 3 (with Alg. 1 and Alg. 2) from D.
+ *   data    host or device, [n][d] float32 (finite values). Copied; the caller keeps it.
+ *   n >= 2, 1 <= d; params as documented above.
+ * Mean and covariance are accumulated in FP64 on the device, the eigendecomposition and the
+ * allocation of Alg. 2 run in FP64 on the host, k-means runs on the device. Synchronises
+ * `stream`. On success *out owns the index (free with taco_free_index).
+ */
+int taco_build_index(const float* data, int64_t n, int32_t d, const taco_build_params* params,
+                     void* stream, taco_index** out);
+
+/*
+ * taco_index_create -- make an index from given parts (Alg. 3 output) and the data D.
+ *   data host or device [n][d] float32; parts host pointers as in taco_index_parts.
+ * Cell lists are rebuilt from codes with ids ascending in every cell. Synchronises `stream`.
+ */
+int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts,
+                      int32_t keep_bf16, void* stream, taco_index** out);
+
+/*
+ * taco_search_batch -- Alg. 6 for nq queries.
+ *   queries    host or device, [nq][d] float32.
+ *   per_query  host pointer to nq structs, or NULL to use *defaults for every query.
+ *   defaults   host pointer; required when per_query is NULL.
+ *   k_stride   row length of the outputs (>= every query's k).
+ *   out_ids    host or device, [nq][k_stride] int64: ids ascending by (distance, id);
+ *              entries past min(k, |C|) are -1.
+ *   out_dists  host or device, [nq][k_stride] float32: Euclidean (not squared) distances;
+ *              +inf where out_ids is -1.
+ * Errors: TACO_EINVAL for bad arguments; TACO_ECAPACITY for k > TACO_MAX_K.
+ */
+int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
+                      const taco_query_params* per_query, const taco_query_params* defaults,
+                      int32_t k_stride, int64_t* out_ids, float* out_dists, void* stream);
+
+/* taco_search_debug -- taco_search_batch that also writes the intermediate results
+ * selected in *debug (device pointers). Test aid; same errors as taco_search_batch. */
+int taco_search_debug(const taco_index* index, const float* queries, int64_t nq,
+                      const taco_query_params* per_query, const taco_query_params* defaults,
+                      int32_t k_stride, int64_t* out_ids, float* out_dists,
+                      const taco_debug_out* debug, void* stream);
+
+/* taco_index_get_info -- sizes and layout of an index (host output). */
+int taco_index_get_info(const taco_index* index, taco_index_info* info);
+
+/*
+ * taco_index_export -- copy the index parts to host buffers (any may be NULL):
+ *   o_bar [d] f64, B [d][N_s*s] f64, eigvals [d] f64 (covariance eigenvalues, descending;
+ *   zeros for an index made by taco_index_create), alloc [N_s*s] i32 (rank, in descending
+ *   eigenvalue order, of the eigenvector in each column of B; -1 when unknown),
+ *   centroids [N_s][sqrt_k][s] f64, codes [N_s][n] u16.
+ */
+int taco_index_export(const taco_index* index, double* o_bar, double* B, double* eigvals,
+                      int32_t* alloc, double* centroids, uint16_t* codes);
+
+/* taco_save_index / taco_load_index -- binary file with the parts and D (little endian).
+ * Loading rebuilds the device index; taco_load_index synchronises `stream`. */
+int taco_save_index(const taco_index* index, const char* path);
+int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_index** out);
+
+/* taco_free_index -- release an index and all its device memory (NULL is a no-op). */
+void taco_free_index(taco_index* index);
+
+/* taco_last_error -- message of the last failed call on this thread ("" if none). */
+const char* taco_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TACO_H_ */

@@ -1,0 +1,589 @@
+// C ABI entry points (include/taco.h): index build and import (Alg. 1-3), search (Alg. 6),
+// export, persistence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "taco_internal.h"
+
+using namespace taco;
+
+namespace {
+
+template <typename T>
+int dev_alloc(T** p, size_t count, int64_t* acct) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    if (acct) *acct += int64_t(count * sizeof(T));
+    return TACO_OK;
+}
+
+#define TRY(x)                   \
+    do {                         \
+        int rc_ = (x);           \
+        if (rc_ != TACO_OK) return rc_; \
+    } while (0)
+
+void free_device(taco_index* ix) {
+    cudaFree(ix->d_data);
+    cudaFree(ix->d_data_bf16);
+    cudaFree(ix->d_obar);
+    cudaFree(ix->d_B);
+    cudaFree(ix->d_cent);
+    cudaFree(ix->d_sizes);
+    cudaFree(ix->d_ids);
+    cudaFree(ix->d_split);
+    cudaFree(ix->ws.base);
+    if (ix->ws.host_pinned) cudaFreeHost(ix->ws.host_pinned);
+}
+
+struct IndexDeleter {
+    void operator()(taco_index* ix) const {
+        if (ix) {
+            free_device(ix);
+            delete ix;
+        }
+    }
+};
+using IndexPtr = std::unique_ptr<taco_index, IndexDeleter>;
+
+int check_geometry(int64_t n, int d, int Ns, int s, int sk) {
+    if (n < 1 || n > int64_t(0x7fffffff)) return fail(TACO_EINVAL, "n = %lld out of range", (long long)n);
+    if (d < 1 || d > 65536) return fail(TACO_EINVAL, "d = %d out of range", d);
+    if (Ns < 1 || Ns > TACO_MAX_SUBSPACES)
+        return fail(TACO_EINVAL, "n_subspaces = %d must be in [1, %d]", Ns, TACO_MAX_SUBSPACES);
+    if (s < 2) return fail(TACO_EINVAL, "sub_dim = %d must be >= 2", s);
+    if (int64_t(Ns) * s > d) return fail(TACO_EINVAL, "n_subspaces * sub_dim > d");
+    if (sk < 1 || sk > TACO_MAX_SQRT_K)
+        return fail(TACO_EINVAL, "sqrt_k = %d must be in [1, %d]", sk, TACO_MAX_SQRT_K);
+    return TACO_OK;
+}
+
+// Copy D (host or device, [n][d]) into the padded device layout [n][d_pad].
+int upload_data(taco_index* ix, const float* data, cudaStream_t st) {
+    TRY(dev_alloc(&ix->d_data, size_t(ix->n) * ix->d_pad, &ix->device_bytes));
+    if (ix->d_pad != ix->d)
+        TACO_CUDA(cudaMemsetAsync(ix->d_data, 0, size_t(ix->n) * ix->d_pad * sizeof(float), st));
+    const cudaMemcpyKind kind = is_device_pointer(data) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    TACO_CUDA(cudaMemcpy2DAsync(ix->d_data, size_t(ix->d_pad) * sizeof(float), data,
+                                size_t(ix->d) * sizeof(float), size_t(ix->d) * sizeof(float),
+                                size_t(ix->n), kind, st));
+    return TACO_OK;
+}
+
+void set_geometry(taco_index* ix, int64_t n, int d, int Ns, int s, int sk) {
+    ix->n = n;
+    ix->d = d;
+    ix->d_pad = (d + 7) & ~7;
+    ix->Ns = Ns;
+    ix->s = s;
+    ix->sk = sk;
+    ix->K = sk * sk;
+    ix->Dp = Ns * s;
+    ix->h1 = s / 2;
+}
+
+// Everything downstream of the parts: cell lists (ids ascending per cell), slab split
+// table, device copies of transform and centroids, optional BF16 rows.
+int finish_index(taco_index* ix, int keep_bf16, cudaStream_t st) {
+    const int64_t n = ix->n;
+    const int Ns = ix->Ns, K = ix->K;
+    TRY(configure_search(ix));
+    const int ns1 = ix->n_slabs + 1;
+    std::vector<uint32_t> sizes(size_t(Ns) * K, 0), ids(size_t(Ns) * n), split(size_t(Ns) * K * ns1);
+    for (int i = 0; i < Ns; ++i) {
+        const uint16_t* code = ix->codes.data() + size_t(i) * n;
+        uint32_t* sz = sizes.data() + size_t(i) * K;
+        for (int64_t p = 0; p < n; ++p) {
+            if (code[p] >= K) return fail(TACO_EINVAL, "code %d of point %lld >= K", int(code[p]), (long long)p);
+            ++sz[code[p]];
+        }
+        std::vector<uint32_t> start(K + 1, 0);
+        for (int c = 0; c < K; ++c) start[c + 1] = start[c] + sz[c];
+        std::vector<uint32_t> cur(start.begin(), start.end() - 1);
+        uint32_t* idl = ids.data() + size_t(i) * n;
+        for (int64_t p = 0; p < n; ++p) idl[cur[code[p]]++] = uint32_t(p);  // ascending ids
+        uint32_t* sp = split.data() + size_t(i) * K * ns1;
+        for (int c = 0; c < K; ++c) {
+            const uint32_t* b = idl + start[c];
+            const uint32_t* e = idl + start[c + 1];
+            for (int sl = 0; sl < ns1; ++sl) {
+                const int64_t bound = std::min<int64_t>(int64_t(sl) << kSlabLog2, n);
+                sp[size_t(c) * ns1 + sl] =
+                    uint32_t(std::lower_bound(b, e, uint32_t(bound)) - idl);
+            }
+        }
+    }
+    TRY(dev_alloc(&ix->d_sizes, sizes.size(), &ix->device_bytes));
+    TRY(dev_alloc(&ix->d_ids, ids.size(), &ix->device_bytes));
+    TRY(dev_alloc(&ix->d_split, split.size(), &ix->device_bytes));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_sizes, sizes.data(), sizes.size() * 4, cudaMemcpyHostToDevice, st));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, st));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_split, split.data(), split.size() * 4, cudaMemcpyHostToDevice, st));
+    // FP32 copies of o_bar, B, centroids for the query path
+    std::vector<float> ob(ix->d), Bf(size_t(ix->d) * ix->Dp), cf(ix->centroids.size());
+    for (int j = 0; j < ix->d; ++j) ob[j] = float(ix->o_bar[j]);
+    for (size_t j = 0; j < Bf.size(); ++j) Bf[j] = float(ix->B[j]);
+    for (size_t j = 0; j < cf.size(); ++j) cf[j] = float(ix->centroids[j]);
+    if (!ix->d_obar) TRY(dev_alloc(&ix->d_obar, ob.size(), &ix->device_bytes));
+    if (!ix->d_B) TRY(dev_alloc(&ix->d_B, Bf.size(), &ix->device_bytes));
+    if (!ix->d_cent) TRY(dev_alloc(&ix->d_cent, cf.size(), &ix->device_bytes));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_obar, ob.data(), ob.size() * 4, cudaMemcpyHostToDevice, st));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_B, Bf.data(), Bf.size() * 4, cudaMemcpyHostToDevice, st));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_cent, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice, st));
+    if (keep_bf16) {
+        TRY(dev_alloc(&ix->d_data_bf16, size_t(n) * ix->d_pad, &ix->device_bytes));
+        TACO_CUDA(launch_to_bf16(ix->d_data, ix->d_data_bf16, size_t(n) * ix->d_pad, st));
+    }
+    TACO_CUDA(cudaStreamSynchronize(st));  // host vectors above die on return
+    return TACO_OK;
+}
+
+// splitmix64 (Steele, Lea, Flood: "Fast splittable pseudorandom number generators").
+uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// sqrt_k distinct rows by a partial Fisher-Yates shuffle (k-means initial centroids).
+void pick_rows(int64_t n, int k, uint64_t seed, int64_t* out) {
+    uint64_t st = seed;
+    if (n <= 4 * int64_t(k) + 16) {
+        std::vector<int64_t> perm(n);
+        std::iota(perm.begin(), perm.end(), 0);
+        for (int j = 0; j < k && j < n; ++j) {
+            const int64_t r = j + int64_t(splitmix64(st) % uint64_t(n - j));
+            std::swap(perm[j], perm[r]);
+            out[j] = perm[j];
+        }
+        for (int j = int(std::min<int64_t>(k, n)); j < k; ++j) out[j] = out[j % std::max<int64_t>(n, 1)];
+        return;
+    }
+    // sparse Fisher-Yates: swaps recorded in a small map
+    std::vector<std::pair<int64_t, int64_t>> swaps;
+    auto get = [&](int64_t p) {
+        for (auto& s : swaps)
+            if (s.first == p) return s.second;
+        return p;
+    };
+    auto set = [&](int64_t p, int64_t v) {
+        for (auto& s : swaps)
+            if (s.first == p) {
+                s.second = v;
+                return;
+            }
+        swaps.push_back({p, v});
+    };
+    for (int j = 0; j < k; ++j) {
+        const int64_t r = j + int64_t(splitmix64(st) % uint64_t(n - j));
+        const int64_t vj = get(j), vr = get(r);
+        set(j, vr);
+        set(r, vj);
+        out[j] = vr;
+    }
+}
+
+int build_impl(const float* data, int64_t n, int32_t d, const taco_build_params* p, cudaStream_t st,
+               taco_index** out) {
+    if (!data || !p || !out) return fail(TACO_EINVAL, "null argument");
+    *out = nullptr;
+    if (p->reserved != 0) return fail(TACO_EINVAL, "reserved field must be 0");
+    TRY(check_geometry(n, d, p->n_subspaces, p->sub_dim, p->sqrt_k));
+    if (n < 2) return fail(TACO_EINVAL, "the covariance needs n >= 2");
+    if (p->kmeans_iters < 0) return fail(TACO_EINVAL, "kmeans_iters < 0");
+    if (n < p->sqrt_k) return fail(TACO_EINVAL, "n < sqrt_k");
+    IndexPtr ix(new (std::nothrow) taco_index());
+    if (!ix) return fail(TACO_ENOMEM, "host allocation failed");
+    TACO_CUDA(cudaGetDevice(&ix->device));
+    set_geometry(ix.get(), n, d, p->n_subspaces, p->sub_dim, p->sqrt_k);
+    TRY(upload_data(ix.get(), data, st));
+    // Alg. 1 steps 2-3: mean and covariance, FP64 accumulation on the device
+    double* dsum = nullptr;
+    double* dcov = nullptr;
+    TRY(dev_alloc(&dsum, size_t(d), nullptr));
+    std::unique_ptr<double, void (*)(double*)> g1(dsum, [](double* q) { cudaFree(q); });
+    TRY(dev_alloc(&dcov, size_t(d) * d, nullptr));
+    std::unique_ptr<double, void (*)(double*)> g2(dcov, [](double* q) { cudaFree(q); });
+    TACO_CUDA(cudaMemsetAsync(dsum, 0, size_t(d) * 8, st));
+    TACO_CUDA(cudaMemsetAsync(dcov, 0, size_t(d) * d * 8, st));
+    TACO_CUDA(launch_col_mean(ix->d_data, n, d, ix->d_pad, dsum, st));
+    std::vector<double> mean(d);
+    TACO_CUDA(cudaMemcpyAsync(mean.data(), dsum, size_t(d) * 8, cudaMemcpyDeviceToHost, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    for (double& v : mean) v /= double(n);
+    TACO_CUDA(cudaMemcpyAsync(dsum, mean.data(), size_t(d) * 8, cudaMemcpyHostToDevice, st));
+    TACO_CUDA(launch_covariance(ix->d_data, n, d, ix->d_pad, dsum, dcov, st));
+    std::vector<double> cov(size_t(d) * d);
+    TACO_CUDA(cudaMemcpyAsync(cov.data(), dcov, cov.size() * 8, cudaMemcpyDeviceToHost, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    for (int a = 0; a < d; ++a)
+        for (int b = a; b < d; ++b) {
+            const double v = cov[size_t(a) * d + b] / double(n - 1);
+            cov[size_t(a) * d + b] = v;
+            cov[size_t(b) * d + a] = v;
+        }
+    // Alg. 1 step 4 and Alg. 2 (host, FP64)
+    std::vector<double> vecs, vals;
+    jacobi_eigen(d, cov, vecs, vals);
+    std::vector<std::vector<int>> buckets;
+    eigensystem_allocation(vals, p->n_subspaces, p->sub_dim, buckets);
+    std::vector<int> desc(d);
+    std::iota(desc.begin(), desc.end(), 0);
+    std::stable_sort(desc.begin(), desc.end(), [&](int x, int y) { return vals[x] > vals[y]; });
+    std::vector<int> rank_of(d);
+    for (int r = 0; r < d; ++r) rank_of[desc[r]] = r;
+    const int Dp = ix->Dp;
+    ix->o_bar = mean;
+    ix->B.assign(size_t(d) * Dp, 0.0);
+    ix->alloc.assign(Dp, -1);
+    int col = 0;
+    for (auto& b : buckets)
+        for (int e : b) {
+            for (int a = 0; a < d; ++a) ix->B[size_t(a) * Dp + col] = vecs[size_t(a) * d + e];
+            ix->alloc[col] = rank_of[e];
+            ++col;
+        }
+    ix->eigvals.resize(d);
+    for (int r = 0; r < d; ++r) ix->eigvals[r] = vals[desc[r]];
+    // Alg. 1 steps 6-11: T = (D - o_bar) B on the device
+    std::vector<float> ob(d), Bf(size_t(d) * Dp);
+    for (int j = 0; j < d; ++j) ob[j] = float(mean[j]);
+    for (size_t j = 0; j < Bf.size(); ++j) Bf[j] = float(ix->B[j]);
+    TRY(dev_alloc(&ix->d_obar, size_t(d), &ix->device_bytes));
+    TRY(dev_alloc(&ix->d_B, Bf.size(), &ix->device_bytes));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_obar, ob.data(), ob.size() * 4, cudaMemcpyHostToDevice, st));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_B, Bf.data(), Bf.size() * 4, cudaMemcpyHostToDevice, st));
+    float* dT = nullptr;
+    TRY(dev_alloc(&dT, size_t(n) * Dp, nullptr));
+    std::unique_ptr<float, void (*)(float*)> g3(dT, [](float* q) { cudaFree(q); });
+    TACO_CUDA(launch_project(ix->d_data, n, d, ix->d_pad, ix->d_obar, ix->d_B, Dp, dT, st));
+    // Alg. 3 steps 4-9: k-means on both halves of every subspace
+    const int P = 2 * p->n_subspaces;
+    std::vector<int64_t> init(size_t(P) * p->sqrt_k);
+    for (int pr = 0; pr < P; ++pr)
+        pick_rows(n, p->sqrt_k, p->seed * 0x100000001b3ull + uint64_t(pr) + 1, init.data() + size_t(pr) * p->sqrt_k);
+    float* dcent = nullptr;
+    uint16_t* dcodes = nullptr;
+    TRY(dev_alloc(&dcent, size_t(p->n_subspaces) * p->sqrt_k * p->sub_dim, nullptr));
+    std::unique_ptr<float, void (*)(float*)> g4(dcent, [](float* q) { cudaFree(q); });
+    TRY(dev_alloc(&dcodes, size_t(p->n_subspaces) * n, nullptr));
+    std::unique_ptr<uint16_t, void (*)(uint16_t*)> g5(dcodes, [](uint16_t* q) { cudaFree(q); });
+    TACO_CUDA(launch_kmeans(dT, n, Dp, p->n_subspaces, p->sub_dim, ix->h1, p->sqrt_k, p->kmeans_iters,
+                            init.data(), dcent, dcodes, st));
+    std::vector<float> cent(size_t(p->n_subspaces) * p->sqrt_k * p->sub_dim);
+    ix->codes.resize(size_t(p->n_subspaces) * n);
+    TACO_CUDA(cudaMemcpyAsync(cent.data(), dcent, cent.size() * 4, cudaMemcpyDeviceToHost, st));
+    TACO_CUDA(cudaMemcpyAsync(ix->codes.data(), dcodes, ix->codes.size() * 2, cudaMemcpyDeviceToHost, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    ix->centroids.assign(cent.begin(), cent.end());
+    TRY(finish_index(ix.get(), p->keep_bf16, st));
+    *out = ix.release();
+    return TACO_OK;
+}
+
+int create_impl(const float* data, int64_t n, int32_t d, const taco_index_parts* parts, int keep_bf16,
+                cudaStream_t st, taco_index** out) {
+    if (!data || !parts || !out || !parts->o_bar || !parts->B || !parts->centroids || !parts->codes)
+        return fail(TACO_EINVAL, "null argument");
+    *out = nullptr;
+    if (parts->reserved != 0) return fail(TACO_EINVAL, "reserved field must be 0");
+    TRY(check_geometry(n, d, parts->n_subspaces, parts->sub_dim, parts->sqrt_k));
+    IndexPtr ix(new (std::nothrow) taco_index());
+    if (!ix) return fail(TACO_ENOMEM, "host allocation failed");
+    TACO_CUDA(cudaGetDevice(&ix->device));
+    set_geometry(ix.get(), n, d, parts->n_subspaces, parts->sub_dim, parts->sqrt_k);
+    ix->o_bar.assign(parts->o_bar, parts->o_bar + d);
+    ix->B.assign(parts->B, parts->B + size_t(d) * ix->Dp);
+    ix->centroids.assign(parts->centroids, parts->centroids + size_t(ix->Ns) * ix->sk * ix->s);
+    ix->codes.assign(parts->codes, parts->codes + size_t(ix->Ns) * n);
+    ix->eigvals.assign(d, 0.0);
+    ix->alloc.assign(ix->Dp, -1);
+    TRY(upload_data(ix.get(), data, st));
+    TRY(finish_index(ix.get(), keep_bf16, st));
+    *out = ix.release();
+    return TACO_OK;
+}
+
+int ensure_workspace(taco_index* ix, size_t bytes, size_t host_bytes) {
+    if (bytes > ix->ws.bytes) {
+        cudaFree(ix->ws.base);
+        ix->ws.base = nullptr;
+        ix->ws.bytes = 0;
+        TACO_CUDA(cudaMalloc(&ix->ws.base, bytes));
+        ix->ws.bytes = bytes;
+    }
+    if (host_bytes > ix->ws.host_bytes) {
+        if (ix->ws.host_pinned) cudaFreeHost(ix->ws.host_pinned);
+        ix->ws.host_pinned = nullptr;
+        ix->ws.host_bytes = 0;
+        TACO_CUDA(cudaMallocHost(&ix->ws.host_pinned, host_bytes));
+        ix->ws.host_bytes = host_bytes;
+    }
+    return TACO_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int check_params(const taco_query_params& q, int k_stride) {
+    if (q.k < 1 || q.k > k_stride) return fail(TACO_EINVAL, "k = %d must be in [1, k_stride = %d]", q.k, k_stride);
+    if (q.k > TACO_MAX_K) return fail(TACO_ECAPACITY, "k = %d exceeds %d", q.k, TACO_MAX_K);
+    if (q.budget < 1) return fail(TACO_EINVAL, "budget must be >= 1");
+    if (q.rerank_target < 0) return fail(TACO_EINVAL, "rerank_target must be >= 0");
+    if (q.select_rule != TACO_SELECT_LITERAL && q.select_rule != TACO_SELECT_PROSE)
+        return fail(TACO_EINVAL, "unknown select_rule %d", q.select_rule);
+    if (q.precision != TACO_PREC_FP32 && q.precision != TACO_PREC_BF16)
+        return fail(TACO_EINVAL, "unknown precision %d", q.precision);
+    if (q.precision == TACO_PREC_BF16 && q.shortlist_mult < 1)
+        return fail(TACO_EINVAL, "shortlist_mult must be >= 1 for BF16");
+    return TACO_OK;
+}
+
+int list_len(const taco_query_params& q) {
+    if (q.precision == TACO_PREC_BF16) {
+        const int64_t m = int64_t(q.k) * q.shortlist_mult;
+        return int(std::min<int64_t>(std::max<int64_t>(m, q.k), TACO_MAX_K));
+    }
+    return q.k;
+}
+
+QueryParamsDev to_dev(const taco_query_params& q) {
+    QueryParamsDev r;
+    r.k = q.k;
+    r.select_rule = q.select_rule;
+    r.budget = q.budget;
+    r.rerank_target = q.rerank_target;
+    r.kk = list_len(q);
+    r.pad = 0;
+    return r;
+}
+
+int search_impl(const taco_index* cix, const float* queries, int64_t nq, const taco_query_params* per_query,
+                const taco_query_params* defaults, int32_t k_stride, int64_t* out_ids, float* out_dists,
+                const taco_debug_out* dbg, cudaStream_t st) {
+    if (!cix) return fail(TACO_EINVAL, "null index");
+    taco_index* ix = const_cast<taco_index*>(cix);
+    if (nq < 0) return fail(TACO_EINVAL, "nq < 0");
+    if (nq == 0) return TACO_OK;
+    if (!queries || !out_ids || !out_dists) return fail(TACO_EINVAL, "null queries or outputs");
+    if (!per_query && !defaults) return fail(TACO_EINVAL, "per_query and defaults are both NULL");
+    if (k_stride < 1) return fail(TACO_EINVAL, "k_stride < 1");
+    const taco_query_params& head = per_query ? per_query[0] : *defaults;
+    const int precision = head.precision;
+    int kk_max = 0;
+    if (per_query) {
+        for (int64_t j = 0; j < nq; ++j) {
+            TRY(check_params(per_query[j], k_stride));
+            if (per_query[j].precision != precision || per_query[j].select_rule != head.select_rule)
+                return fail(TACO_EINVAL, "precision and select_rule must be uniform in a batch");
+            kk_max = std::max(kk_max, list_len(per_query[j]));
+        }
+    } else {
+        TRY(check_params(*defaults, k_stride));
+        kk_max = list_len(*defaults);
+    }
+    if (precision == TACO_PREC_BF16 && !ix->d_data_bf16)
+        return fail(TACO_EINVAL, "BF16 search needs an index built with keep_bf16");
+    int cur_dev = 0;
+    TACO_CUDA(cudaGetDevice(&cur_dev));
+    if (cur_dev != ix->device) return fail(TACO_EINVAL, "current device %d is not the index's device %d", cur_dev, ix->device);
+
+    const bool q_dev = is_device_pointer(queries);
+    const bool id_dev = is_device_pointer(out_ids);
+    const bool dist_dev = is_device_pointer(out_dists);
+    std::lock_guard<std::mutex> lock(ix->ws_mu);
+    const int64_t chunk = std::min<int64_t>(nq, kQueryChunk);
+    const int Ns = ix->Ns, K = ix->K;
+    // device workspace layout
+    size_t off = 0;
+    const size_t o_qt = off; off = align_up(off + size_t(chunk) * ix->Dp * 4);
+    const size_t o_cells = off; off = align_up(off + size_t(chunk) * Ns * K * 2);
+    const size_t o_nc = off; off = align_up(off + size_t(chunk) * Ns * 4);
+    const size_t o_ret = off; off = align_up(off + size_t(chunk) * Ns * 8);
+    const size_t o_par = off; off = align_up(off + (per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0));
+    const size_t o_q = off; off = align_up(off + (q_dev ? 0 : size_t(chunk) * ix->d * 4));
+    const size_t o_oi = off; off = align_up(off + (id_dev ? 0 : size_t(chunk) * k_stride * 8));
+    const size_t o_od = off; off = align_up(off + (dist_dev ? 0 : size_t(chunk) * k_stride * 4));
+    const size_t host_need = per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0;
+    TRY(ensure_workspace(ix, off, host_need));
+    char* wb = static_cast<char*>(ix->ws.base);
+    QueryParamsDev* dparams = nullptr;
+    if (per_query) {
+        QueryParamsDev* hp = static_cast<QueryParamsDev*>(ix->ws.host_pinned);
+        for (int64_t j = 0; j < nq; ++j) hp[j] = to_dev(per_query[j]);
+        dparams = reinterpret_cast<QueryParamsDev*>(wb + o_par);
+        TACO_CUDA(cudaMemcpyAsync(dparams, hp, size_t(nq) * sizeof(QueryParamsDev), cudaMemcpyHostToDevice, st));
+    }
+    for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
+        const int64_t cn = std::min(chunk, nq - c0);
+        SearchLaunch L = {};
+        L.ix = ix;
+        L.nq = cn;
+        if (q_dev) {
+            L.queries = queries + c0 * ix->d;
+        } else {
+            float* dq = reinterpret_cast<float*>(wb + o_q);
+            TACO_CUDA(cudaMemcpyAsync(dq, queries + c0 * ix->d, size_t(cn) * ix->d * 4, cudaMemcpyHostToDevice, st));
+            L.queries = dq;
+        }
+        L.defaults = to_dev(head);
+        L.params = dparams ? dparams + c0 : nullptr;
+        L.precision = precision;
+        L.kk_max = kk_max;
+        L.qt = reinterpret_cast<float*>(wb + o_qt);
+        L.cells = reinterpret_cast<uint16_t*>(wb + o_cells);
+        L.ncells = reinterpret_cast<int32_t*>(wb + o_nc);
+        L.retrieved = reinterpret_cast<int64_t*>(wb + o_ret);
+        L.out_ids = id_dev ? out_ids + c0 * k_stride : reinterpret_cast<int64_t*>(wb + o_oi);
+        L.out_dists = dist_dev ? out_dists + c0 * k_stride : reinterpret_cast<float*>(wb + o_od);
+        L.k_stride = k_stride;
+        if (dbg) {
+            L.dbg.query_t = dbg->query_t ? dbg->query_t + c0 * ix->Dp : nullptr;
+            L.dbg.probed = dbg->probed ? dbg->probed + size_t(c0) * Ns * K : nullptr;
+            L.dbg.retrieved_num = dbg->retrieved_num ? dbg->retrieved_num + c0 * Ns : nullptr;
+            L.dbg.sc = dbg->sc ? dbg->sc + size_t(c0) * ix->n : nullptr;
+            L.dbg.collision_num = dbg->collision_num ? dbg->collision_num + c0 * (Ns + 1) : nullptr;
+            L.dbg.last_collision = dbg->last_collision ? dbg->last_collision + c0 : nullptr;
+            L.dbg.candidate_num = dbg->candidate_num ? dbg->candidate_num + c0 : nullptr;
+        }
+        TRY(run_search_chunk(L, st));
+        if (!id_dev)
+            TACO_CUDA(cudaMemcpyAsync(out_ids + c0 * k_stride, L.out_ids, size_t(cn) * k_stride * 8,
+                                      cudaMemcpyDeviceToHost, st));
+        if (!dist_dev)
+            TACO_CUDA(cudaMemcpyAsync(out_dists + c0 * k_stride, L.out_dists, size_t(cn) * k_stride * 4,
+                                      cudaMemcpyDeviceToHost, st));
+    }
+    if (!id_dev || !dist_dev || per_query) TACO_CUDA(cudaStreamSynchronize(st));
+    return TACO_OK;
+}
+
+const char kMagic[8] = {'T', 'A', 'C', 'O', 'I', 'D', 'X', '1'};
+
+}  // namespace
+
+extern "C" {
+
+int taco_build_index(const float* data, int64_t n, int32_t d, const taco_build_params* params, void* stream,
+                     taco_index** out) {
+    return build_impl(data, n, d, params, static_cast<cudaStream_t>(stream), out);
+}
+
+int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts, int32_t keep_bf16,
+                      void* stream, taco_index** out) {
+    return create_impl(data, n, d, parts, keep_bf16, static_cast<cudaStream_t>(stream), out);
+}
+
+int taco_search_batch(const taco_index* index, const float* queries, int64_t nq, const taco_query_params* per_query,
+                      const taco_query_params* defaults, int32_t k_stride, int64_t* out_ids, float* out_dists,
+                      void* stream) {
+    return search_impl(index, queries, nq, per_query, defaults, k_stride, out_ids, out_dists, nullptr,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int taco_search_debug(const taco_index* index, const float* queries, int64_t nq, const taco_query_params* per_query,
+                      const taco_query_params* defaults, int32_t k_stride, int64_t* out_ids, float* out_dists,
+                      const taco_debug_out* debug, void* stream) {
+    if (!debug) return fail(TACO_EINVAL, "null debug struct");
+    return search_impl(index, queries, nq, per_query, defaults, k_stride, out_ids, out_dists, debug,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int taco_index_get_info(const taco_index* ix, taco_index_info* info) {
+    if (!ix || !info) return fail(TACO_EINVAL, "null argument");
+    info->n = ix->n;
+    info->d = ix->d;
+    info->n_subspaces = ix->Ns;
+    info->sub_dim = ix->s;
+    info->sqrt_k = ix->sk;
+    info->d_pad = ix->d_pad;
+    info->has_bf16 = ix->d_data_bf16 != nullptr;
+    info->n_slabs = ix->n_slabs;
+    info->cluster_size = ix->cluster;
+    info->device_bytes = ix->device_bytes;
+    return TACO_OK;
+}
+
+int taco_index_export(const taco_index* ix, double* o_bar, double* B, double* eigvals, int32_t* alloc,
+                      double* centroids, uint16_t* codes) {
+    if (!ix) return fail(TACO_EINVAL, "null index");
+    if (o_bar) std::copy(ix->o_bar.begin(), ix->o_bar.end(), o_bar);
+    if (B) std::copy(ix->B.begin(), ix->B.end(), B);
+    if (eigvals) std::copy(ix->eigvals.begin(), ix->eigvals.end(), eigvals);
+    if (alloc) std::copy(ix->alloc.begin(), ix->alloc.end(), alloc);
+    if (centroids) std::copy(ix->centroids.begin(), ix->centroids.end(), centroids);
+    if (codes) std::copy(ix->codes.begin(), ix->codes.end(), codes);
+    return TACO_OK;
+}
+
+int taco_save_index(const taco_index* ix, const char* path) {
+    if (!ix || !path) return fail(TACO_EINVAL, "null argument");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(TACO_EIO, "cannot open %s for writing", path);
+    std::unique_ptr<FILE, int (*)(FILE*)> guard(f, std::fclose);
+    const int64_t hdr[6] = {ix->n, ix->d, ix->Ns, ix->s, ix->sk, 0};
+    std::vector<float> data(size_t(ix->n) * ix->d);
+    if (cudaMemcpy2D(data.data(), size_t(ix->d) * 4, ix->d_data, size_t(ix->d_pad) * 4, size_t(ix->d) * 4,
+                     size_t(ix->n), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(TACO_ECUDA, "reading the data back failed");
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 8, 6, f) == 6 &&
+              std::fwrite(ix->o_bar.data(), 8, ix->o_bar.size(), f) == ix->o_bar.size() &&
+              std::fwrite(ix->B.data(), 8, ix->B.size(), f) == ix->B.size() &&
+              std::fwrite(ix->eigvals.data(), 8, ix->eigvals.size(), f) == ix->eigvals.size() &&
+              std::fwrite(ix->alloc.data(), 4, ix->alloc.size(), f) == ix->alloc.size() &&
+              std::fwrite(ix->centroids.data(), 8, ix->centroids.size(), f) == ix->centroids.size() &&
+              std::fwrite(ix->codes.data(), 2, ix->codes.size(), f) == ix->codes.size() &&
+              std::fwrite(data.data(), 4, data.size(), f) == data.size();
+    if (!ok) return fail(TACO_EIO, "short write to %s", path);
+    return TACO_OK;
+}
+
+int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_index** out) {
+    if (!path || !out) return fail(TACO_EINVAL, "null argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(TACO_EIO, "cannot open %s", path);
+    std::unique_ptr<FILE, int (*)(FILE*)> guard(f, std::fclose);
+    char magic[8];
+    int64_t hdr[6];
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0 || std::fread(hdr, 8, 6, f) != 6)
+        return fail(TACO_EIO, "%s is not a TaCo index file", path);
+    const int64_t n = hdr[0];
+    const int d = int(hdr[1]), Ns = int(hdr[2]), s = int(hdr[3]), sk = int(hdr[4]);
+    TRY(check_geometry(n, d, Ns, s, sk));
+    const size_t Dp = size_t(Ns) * s;
+    std::vector<double> ob(d), B(size_t(d) * Dp), ev(d), cent(size_t(Ns) * sk * s);
+    std::vector<int32_t> alloc(Dp);
+    std::vector<uint16_t> codes(size_t(Ns) * n);
+    std::vector<float> data(size_t(n) * d);
+    bool ok = std::fread(ob.data(), 8, ob.size(), f) == ob.size() && std::fread(B.data(), 8, B.size(), f) == B.size() &&
+              std::fread(ev.data(), 8, ev.size(), f) == ev.size() &&
+              std::fread(alloc.data(), 4, alloc.size(), f) == alloc.size() &&
+              std::fread(cent.data(), 8, cent.size(), f) == cent.size() &&
+              std::fread(codes.data(), 2, codes.size(), f) == codes.size() &&
+              std::fread(data.data(), 4, data.size(), f) == data.size();
+    if (!ok) return fail(TACO_EIO, "%s is truncated", path);
+    taco_index_parts parts = {ob.data(), B.data(), cent.data(), codes.data(), Ns, s, sk, 0};
+    taco_index* ix = nullptr;
+    TRY(create_impl(data.data(), n, d, &parts, keep_bf16, static_cast<cudaStream_t>(stream), &ix));
+    ix->eigvals = ev;
+    ix->alloc = alloc;
+    *out = ix;
+    return TACO_OK;
+}
+
+void taco_free_index(taco_index* ix) {
+    if (!ix) return;
+    free_device(ix);
+    delete ix;
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// Device kernels of the index build (Alg. 1 steps 2-3 and 6-11, Alg. 3 steps 6-9) and the
+// query projection of Alg. 6 step 1, which uses the same transform kernel.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "taco_internal.h"
+
+namespace taco {
+
+// ---------------------------------------------------------------------------------------
+// Y[rows][Dp] = (X[rows][d] - o_bar) * B[d][Dp]   (Alg. 1: r = B^T (o - o_bar))
+// 64x64 output tile per 256-thread CTA, 4x4 outputs per thread, k-steps of 16.
+// ---------------------------------------------------------------------------------------
+constexpr int kPT = 64, kPK = 16;
+
+__global__ void __launch_bounds__(256)
+project_kernel(const float* __restrict__ X, int64_t rows, int d, int64_t ldx,
+               const float* __restrict__ obar, const float* __restrict__ B, int Dp,
+               float* __restrict__ Y) {
+    __shared__ float As[kPK][kPT + 4];
+    __shared__ float Bs[kPK][kPT];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t row0 = int64_t(blockIdx.x) * kPT;
+    const int col0 = blockIdx.y * kPT;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = 0; k0 < d; k0 += kPK) {
+        for (int e = threadIdx.x; e < kPT * kPK; e += 256) {
+            const int r = e / kPK, kk = e % kPK;
+            const int64_t gr = row0 + r;
+            const int gk = k0 + kk;
+            float v = 0.f;
+            if (gr < rows && gk < d) v = X[gr * ldx + gk] - obar[gk];
+            As[kk][r] = v;
+        }
+        for (int e = threadIdx.x; e < kPT * kPK; e += 256) {
+            const int kk = e / kPT, c = e % kPT;
+            const int gk = k0 + kk, gc = col0 + c;
+            Bs[kk][c] = (gk < d && gc < Dp) ? B[int64_t(gk) * Dp + gc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kPK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                a[t] = As[kk][ty * 4 + t];
+                b[t] = Bs[kk][tx * 4 + t];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gr = row0 + ty * 4 + i;
+        if (gr >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gc = col0 + tx * 4 + j;
+            if (gc < Dp) Y[gr * Dp + gc] = acc[i][j];
+        }
+    }
+}
+
+cudaError_t launch_project(const float* X, int64_t rows, int d, int64_t ldx, const float* obar,
+                           const float* B, int Dp, float* Y, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    dim3 grid(unsigned((rows + kPT - 1) / kPT), unsigned((Dp + kPT - 1) / kPT));
+    project_kernel<<<grid, 256, 0, st>>>(X, rows, d, ldx, obar, B, Dp, Y);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Column sums in FP64 (Alg. 1 step 2). Each CTA sums a block of rows.
+// ---------------------------------------------------------------------------------------
+constexpr int kMeanRows = 4096;
+
+__global__ void col_sum_kernel(const float* __restrict__ X, int64_t n, int d, int ldx,
+                               double* __restrict__ sums) {
+    const int64_t r0 = int64_t(blockIdx.x) * kMeanRows;
+    const int64_t r1 = min(n, r0 + kMeanRows);
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t r = r0; r < r1; ++r) acc += double(X[r * ldx + c]);
+        atomicAdd(&sums[c], acc);
+    }
+}
+
+cudaError_t launch_col_mean(const float* X, int64_t n, int d, int ldx, double* sums,
+                            cudaStream_t st) {
+    const unsigned blocks = unsigned((n + kMeanRows - 1) / kMeanRows);
+    col_sum_kernel<<<blocks, 256, 0, st>>>(X, n, d, ldx, sums);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Sum of (x - mean)(x - mean)^T in FP64 (Alg. 1 step 3, before the 1/(n-1) factor).
+// One CTA per (32x32 tile with ta <= tb, block of rows); 256 threads, 2x2 entries each.
+// ---------------------------------------------------------------------------------------
+constexpr int kCovTile = 32, kCovRows = 8192, kCovStep = 32;
+
+__global__ void __launch_bounds__(256)
+covariance_kernel(const float* __restrict__ X, int64_t n, int d, int ldx,
+                  const double* __restrict__ mean, double* __restrict__ cov, int ntiles) {
+    // decode the upper-triangular tile pair
+    int t = blockIdx.x, ta = 0;
+    while (t >= ntiles - ta) {
+        t -= ntiles - ta;
+        ++ta;
+    }
+    const int tb = ta + t;
+    const int a0 = ta * kCovTile, b0 = tb * kCovTile;
+    const int64_t r0 = int64_t(blockIdx.y) * kCovRows;
+    const int64_t r1 = min(n, r0 + kCovRows);
+    __shared__ double xa[kCovStep][kCovTile + 1];
+    __shared__ double xb[kCovStep][kCovTile + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int64_t r = r0; r < r1; r += kCovStep) {
+        for (int e = threadIdx.x; e < kCovStep * kCovTile; e += 256) {
+            const int rr = e / kCovTile, cc = e % kCovTile;
+            const int64_t gr = r + rr;
+            double va = 0.0, vb = 0.0;
+            if (gr < r1) {
+                if (a0 + cc < d) va = double(X[gr * ldx + a0 + cc]) - mean[a0 + cc];
+                if (b0 + cc < d) vb = double(X[gr * ldx + b0 + cc]) - mean[b0 + cc];
+            }
+            xa[rr][cc] = va;
+            xb[rr][cc] = vb;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kCovStep; ++rr) {
+            const double u0 = xa[rr][ty * 2], u1 = xa[rr][ty * 2 + 1];
+            const double v0 = xb[rr][tx * 2], v1 = xb[rr][tx * 2 + 1];
+            acc[0][0] = fma(u0, v0, acc[0][0]);
+            acc[0][1] = fma(u0, v1, acc[0][1]);
+            acc[1][0] = fma(u1, v0, acc[1][0]);
+            acc[1][1] = fma(u1, v1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int a = a0 + ty * 2 + i, b = b0 + tx * 2 + j;
+            if (a < d && b < d) atomicAdd(&cov[int64_t(a) * d + b], acc[i][j]);
+        }
+}
+
+cudaError_t launch_covariance(const float* X, int64_t n, int d, int ldx, const double* mean,
+                              double* cov, cudaStream_t st) {
+    const int ntiles = (d + kCovTile - 1) / kCovTile;
+    const int npairs = ntiles * (ntiles + 1) / 2;
+    dim3 grid(unsigned(npairs), unsigned((n + kCovRows - 1) / kCovRows));
+    covariance_kernel<<<grid, 256, 0, st>>>(X, n, d, ldx, mean, cov, ntiles);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Lloyd k-means on all 2*N_s half-subspaces at once (Alg. 3 steps 6-8).
+// Problem p = 2*i + h works on columns [i*s + off_h, i*s + off_h + len_h) of T.
+// ---------------------------------------------------------------------------------------
+constexpr int kKmThreads = 256;
+constexpr int kKmPoints = 4096;   // points per CTA in the assignment pass
+
+struct KmGeom {
+    int Ns, s, h1, sk, Dp, hmax;
+};
+
+__device__ __forceinline__ void km_problem(const KmGeom& g, int p, int& col, int& len) {
+    const int i = p >> 1, h = p & 1;
+    col = i * g.s + (h ? g.h1 : 0);
+    len = h ? g.s - g.h1 : g.h1;
+}
+
+// Assign every point to its nearest centroid (ties to the lowest id) and accumulate the
+// per-centroid sums and counts of this CTA's points.
+__global__ void __launch_bounds__(kKmThreads)
+kmeans_assign_kernel(const float* __restrict__ T, int64_t n, KmGeom g,
+                     const float* __restrict__ cent,   // [2Ns][sk][hmax]
+                     uint16_t* __restrict__ assign,    // [2Ns][n]
+                     double* __restrict__ sums,        // [2Ns][sk][hmax]
+                     unsigned long long* __restrict__ counts,  // [2Ns][sk]
+                     int accumulate) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int p = blockIdx.y;
+    int col, len;
+    km_problem(g, p, col, len);
+    float* c_s = reinterpret_cast<float*>(sm);              // sk*hmax
+    float* sum_s = c_s + g.sk * g.hmax;                     // sk*hmax (per-CTA partial sums)
+    unsigned int* cnt_s = reinterpret_cast<unsigned int*>(sum_s + g.sk * g.hmax);  // sk
+    const float* cp = cent + size_t(p) * g.sk * g.hmax;
+    for (int e = threadIdx.x; e < g.sk * g.hmax; e += kKmThreads) {
+        c_s[e] = cp[e];
+        sum_s[e] = 0.f;
+    }
+    for (int e = threadIdx.x; e < g.sk; e += kKmThreads) cnt_s[e] = 0;
+    __syncthreads();
+    const int64_t p0 = int64_t(blockIdx.x) * kKmPoints;
+    const int64_t p1 = min(n, p0 + kKmPoints);
+    for (int64_t pt = p0 + threadIdx.x; pt < p1; pt += kKmThreads) {
+        const float* x = T + pt * g.Dp + col;
+        float xv[64];
+        const int L = len < 64 ? len : 64;
+        for (int j = 0; j < L; ++j) xv[j] = x[j];
+        float best = 3.4e38f;
+        int bi = 0;
+        for (int c = 0; c < g.sk; ++c) {
+            const float* cc = c_s + c * g.hmax;
+            float acc = 0.f;
+            for (int j = 0; j < L; ++j) {
+                const float df = xv[j] - cc[j];
+                acc = fmaf(df, df, acc);
+            }
+            for (int j = L; j < len; ++j) {
+                const float df = x[j] - cc[j];
+                acc = fmaf(df, df, acc);
+            }
+            if (acc < best) {
+                best = acc;
+                bi = c;
+            }
+        }
+        assign[size_t(p) * n + pt] = uint16_t(bi);
+        if (accumulate) {
+            for (int j = 0; j < len; ++j) atomicAdd(&sum_s[bi * g.hmax + j], x[j]);
+            atomicAdd(&cnt_s[bi], 1u);
+        }
+    }
+    if (!accumulate) return;
+    __syncthreads();
+    double* sp = sums + size_t(p) * g.sk * g.hmax;
+    for (int e = threadIdx.x; e < g.sk * g.hmax; e += kKmThreads) {
+        if (sum_s[e] != 0.f) atomicAdd(&sp[e], double(sum_s[e]));
+    }
+    for (int e = threadIdx.x; e < g.sk; e += kKmThreads) {
+        if (cnt_s[e]) atomicAdd(&counts[size_t(p) * g.sk + e], (unsigned long long)cnt_s[e]);
+    }
+}
+
+// New centroid = mean of its points; an empty cluster keeps its centroid. Clears sums.
+__global__ void kmeans_update_kernel(KmGeom g, float* __restrict__ cent,
+                                     double* __restrict__ sums,
+                                     unsigned long long* __restrict__ counts) {
+    const int p = blockIdx.x;
+    for (int e = threadIdx.x; e < g.sk * g.hmax; e += blockDim.x) {
+        const int c = e / g.hmax;
+        const unsigned long long m = counts[size_t(p) * g.sk + c];
+        const size_t at = size_t(p) * g.sk * g.hmax + e;
+        if (m > 0) cent[at] = float(sums[at] / double(m));
+        sums[at] = 0.0;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < g.sk; c += blockDim.x) counts[size_t(p) * g.sk + c] = 0;
+}
+
+__global__ void kmeans_init_kernel(const float* __restrict__ T, KmGeom g,
+                                   const int64_t* __restrict__ rows,  // [2Ns][sk]
+                                   float* __restrict__ cent) {
+    const int p = blockIdx.x;
+    int col, len;
+    km_problem(g, p, col, len);
+    for (int e = threadIdx.x; e < g.sk * g.hmax; e += blockDim.x) {
+        const int c = e / g.hmax, j = e % g.hmax;
+        const int64_t r = rows[size_t(p) * g.sk + c];
+        cent[size_t(p) * g.sk * g.hmax + e] = j < len ? T[r * g.Dp + col + j] : 0.f;
+    }
+}
+
+__global__ void kmeans_codes_kernel(const uint16_t* __restrict__ assign, int64_t n, int Ns,
+                                    int sk, uint16_t* __restrict__ codes) {
+    const int i = blockIdx.y;
+    for (int64_t pt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pt < n;
+         pt += int64_t(gridDim.x) * blockDim.x) {
+        const int r = assign[size_t(2 * i) * n + pt];
+        const int c = assign[size_t(2 * i + 1) * n + pt];
+        codes[size_t(i) * n + pt] = uint16_t(r * sk + c);
+    }
+}
+
+// Centroids gathered into the index layout [Ns][sk][s].
+__global__ void kmeans_export_kernel(const float* __restrict__ cent, KmGeom g,
+                                     float* __restrict__ out) {
+    const int i = blockIdx.x;
+    for (int e = threadIdx.x; e < g.sk * g.s; e += blockDim.x) {
+        const int c = e / g.s, j = e % g.s;
+        const int h = j >= g.h1;
+        const int jj = h ? j - g.h1 : j;
+        out[size_t(i) * g.sk * g.s + e] = cent[(size_t(2 * i + h) * g.sk + c) * g.hmax + jj];
+    }
+}
+
+cudaError_t launch_kmeans(const float* T, int64_t n, int Dp, int Ns, int s, int h1, int sk,
+                          int iters, const int64_t* init_rows_host, float* cent_out,
+                          uint16_t* codes_out, cudaStream_t st) {
+    KmGeom g{Ns, s, h1, sk, Dp, s - h1};
+    const int P = 2 * Ns;
+    float* cent = nullptr;
+    double* sums = nullptr;
+    unsigned long long* counts = nullptr;
+    uint16_t* assign = nullptr;
+    int64_t* rows = nullptr;
+    cudaError_t e = cudaSuccess;
+    const size_t ncent = size_t(P) * sk * g.hmax;
+    auto cleanup = [&]() {
+        cudaFree(cent);
+        cudaFree(sums);
+        cudaFree(counts);
+        cudaFree(assign);
+        cudaFree(rows);
+    };
+#define KM_TRY(x)          \
+    do {                   \
+        e = (x);           \
+        if (e != cudaSuccess) { \
+            cleanup();     \
+            return e;      \
+        }                  \
+    } while (0)
+    KM_TRY(cudaMalloc(&cent, ncent * sizeof(float)));
+    KM_TRY(cudaMalloc(&sums, ncent * sizeof(double)));
+    KM_TRY(cudaMalloc(&counts, size_t(P) * sk * sizeof(unsigned long long)));
+    KM_TRY(cudaMalloc(&assign, size_t(P) * n * sizeof(uint16_t)));
+    KM_TRY(cudaMalloc(&rows, size_t(P) * sk * sizeof(int64_t)));
+    KM_TRY(cudaMemcpyAsync(rows, init_rows_host, size_t(P) * sk * sizeof(int64_t),
+                           cudaMemcpyHostToDevice, st));
+    KM_TRY(cudaMemsetAsync(sums, 0, ncent * sizeof(double), st));
+    KM_TRY(cudaMemsetAsync(counts, 0, size_t(P) * sk * sizeof(unsigned long long), st));
+    kmeans_init_kernel<<<P, 256, 0, st>>>(T, g, rows, cent);
+    KM_TRY(cudaGetLastError());
+    const size_t smem = 2 * size_t(sk) * g.hmax * sizeof(float) + size_t(sk) * sizeof(unsigned);
+    if (smem > 48 * 1024)
+        KM_TRY(cudaFuncSetAttribute(kmeans_assign_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    dim3 grid(unsigned((n + kKmPoints - 1) / kKmPoints), unsigned(P));
+    for (int it = 0; it < iters; ++it) {
+        kmeans_assign_kernel<<<grid, kKmThreads, smem, st>>>(T, n, g, cent, assign, sums,
+                                                              counts, 1);
+        KM_TRY(cudaGetLastError());
+        kmeans_update_kernel<<<P, 256, 0, st>>>(g, cent, sums, counts);
+        KM_TRY(cudaGetLastError());
+    }
+    kmeans_assign_kernel<<<grid, kKmThreads, smem, st>>>(T, n, g, cent, assign, sums, counts, 0);
+    KM_TRY(cudaGetLastError());
+    dim3 cg(unsigned(std::min<int64_t>((n + 255) / 256, 4096)), unsigned(Ns));
+    kmeans_codes_kernel<<<cg, 256, 0, st>>>(assign, n, Ns, sk, codes_out);
+    KM_TRY(cudaGetLastError());
+    kmeans_export_kernel<<<Ns, 256, 0, st>>>(cent, g, cent_out);
+    KM_TRY(cudaGetLastError());
+    KM_TRY(cudaStreamSynchronize(st));
+    cleanup();
+    return cudaSuccess;
+#undef KM_TRY
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                               size_t count) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += size_t(gridDim.x) * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, size_t count, cudaStream_t st) {
+    const size_t blocks = std::min<size_t>((count + 255) / 256, 152 * 64);
+    to_bf16_kernel<<<unsigned(blocks), 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+}  // namespace taco

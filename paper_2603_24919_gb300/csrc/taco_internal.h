@@ -1,0 +1,121 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "taco.h"
+
+namespace taco {
+
+// Collision counters are 4-bit nibbles, 8 per 32-bit word. Point ids are grouped into
+// slabs of 2^15; one CTA of a query's cluster owns a contiguous range of slabs and keeps
+// their counters in shared memory.
+constexpr int kSlabLog2 = 15;
+constexpr int64_t kSlabIds = int64_t(1) << kSlabLog2;
+constexpr int kSlabWords = int(kSlabIds / 8);
+constexpr int kSlabBytes = kSlabWords * 4;
+
+// Queries handled per internal launch group (bounds the workspace and grid.y).
+constexpr int64_t kQueryChunk = 16384;
+
+struct QueryParamsDev {
+    int32_t k;
+    int32_t select_rule;
+    int64_t budget;
+    int64_t rerank_target;
+    int32_t kk;       // list length kept per warp (k, or the BF16 shortlist)
+    int32_t pad;
+};
+
+// Error reporting (thread-local message).
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+#define TACO_CUDA(call)                                                        \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::taco::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+bool is_device_pointer(const void* p);
+
+// Host FP64 linear algebra (build side).
+void jacobi_eigen(int d, std::vector<double>& a, std::vector<double>& vecs,
+                  std::vector<double>& vals);
+void eigensystem_allocation(const std::vector<double>& lam, int n_subspaces, int sub_dim,
+                            std::vector<std::vector<int>>& buckets);
+
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+    void* host_pinned = nullptr;
+    size_t host_bytes = 0;
+};
+
+}  // namespace taco
+
+struct taco_index {
+    int64_t n = 0;
+    int d = 0, d_pad = 0, Ns = 0, s = 0, sk = 0, K = 0, Dp = 0, h1 = 0;
+    int n_slabs = 0;
+    int cluster = 1, slabs_per_cta = 1;
+    int device = 0;
+    // host copies of the parts
+    std::vector<double> o_bar, B, eigvals, centroids;
+    std::vector<int32_t> alloc;
+    std::vector<uint16_t> codes;
+    // device arrays
+    float* d_data = nullptr;            // [n][d_pad]
+    __nv_bfloat16* d_data_bf16 = nullptr;  // [n][d_pad] or null
+    float* d_obar = nullptr;            // [d]
+    float* d_B = nullptr;               // [d][Dp]
+    float* d_cent = nullptr;            // [Ns][sk][s]
+    uint32_t* d_sizes = nullptr;        // [Ns][K]
+    uint32_t* d_ids = nullptr;          // [Ns][n]
+    uint32_t* d_split = nullptr;        // [Ns][K][n_slabs + 1]
+    int64_t device_bytes = 0;
+    std::mutex ws_mu;
+    taco::Workspace ws;
+};
+
+namespace taco {
+
+// Kernel launchers (return cudaGetLastError of the launch).
+cudaError_t launch_project(const float* X, int64_t rows, int d, int64_t ldx, const float* obar,
+                           const float* B, int Dp, float* Y, cudaStream_t st);
+cudaError_t launch_col_mean(const float* X, int64_t n, int d, int ldx, double* sums,
+                            cudaStream_t st);
+cudaError_t launch_covariance(const float* X, int64_t n, int d, int ldx, const double* mean,
+                              double* cov, cudaStream_t st);
+cudaError_t launch_kmeans(const float* T, int64_t n, int Dp, int Ns, int s, int h1, int sk,
+                          int iters, const int64_t* init_rows_host, float* cent_out,
+                          uint16_t* codes_out, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, size_t count,
+                           cudaStream_t st);
+
+struct SearchLaunch {
+    const taco_index* ix;
+    const float* queries;      // device [nq][d]
+    int64_t nq;
+    QueryParamsDev defaults;
+    const QueryParamsDev* params;  // device [nq] or null
+    int precision;
+    int kk_max;
+    float* qt;                 // device [nq][Dp]
+    uint16_t* cells;           // device [nq][Ns][K]
+    int32_t* ncells;           // device [nq][Ns]
+    int64_t* retrieved;        // device [nq][Ns]
+    int64_t* out_ids;
+    float* out_dists;
+    int k_stride;
+    taco_debug_out dbg;        // device pointers, already offset to this chunk
+};
+int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
+int configure_search(taco_index* ix);
+
+}  // namespace taco

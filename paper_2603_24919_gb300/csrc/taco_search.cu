@@ -1,0 +1,333 @@
+// Query path orchestration and the cell-probe kernel (Alg. 6 steps 3-6 with Alg. 4).
+//
+// Alg. 4 pops IMI cells in ascending order of d1[r] + d2[c] and stops as soon as the
+// retrieved sizes reach the budget; the popped set is therefore the shortest prefix of
+// the key-sorted cells whose sizes sum to >= B (the paper notes that its heap and the
+// linear activation array of SuCo return the same cells). The GPU computes that prefix
+// directly: one CTA per (query, subspace) builds the K keys (FP32 sum bits << 32 | cell id,
+// a total order that breaks equal sums by r then c), finds the bucket of a size-weighted
+// histogram over the key range where the running size crosses B, sorts only that bucket,
+// and walks it to the exact threshold key T. Cells with key <= T are the probed set.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "taco_internal.h"
+#include "taco_rerank.cuh"
+
+namespace taco {
+
+constexpr int kSelThreads = 256;
+constexpr int kSelBins = 2048;
+constexpr int kSelBinsPerThread = kSelBins / kSelThreads;
+
+__device__ __forceinline__ unsigned long long cell_key(const float* d1, const float* d2, int sk,
+                                                       int cell) {
+    const int r = cell / sk, c = cell - r * sk;
+    const float sum = d1[r] + d2[c];
+    return (static_cast<unsigned long long>(__float_as_uint(sum)) << 32) | unsigned(cell);
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict__ cent,
+                   int Ns, int s, int h1, int sk, const uint32_t* __restrict__ sizes, int64_t n,
+                   QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
+                   int list_cap, uint16_t* __restrict__ cells_out,
+                   int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out,
+                   uint8_t* __restrict__ dbg_probed) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int i = blockIdx.x;
+    const int64_t q = blockIdx.y;
+    const int K = sk * sk;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long* list = reinterpret_cast<unsigned long long*>(sm);  // list_cap
+    uint32_t* hist = reinterpret_cast<uint32_t*>(list + list_cap);         // kSelBins
+    float* d1 = reinterpret_cast<float*>(hist + kSelBins);                  // sk
+    float* d2 = d1 + sk;                                                    // sk
+    __shared__ uint32_t s_min, s_max;
+    __shared__ int s_bucket, s_m, s_cnt;
+    __shared__ unsigned long long s_pre, s_T, s_ret;
+    __shared__ uint32_t s_wsum[kSelThreads / 32];
+
+    const QueryParamsDev qp = params ? params[q] : defaults;
+    const int64_t budget = qp.budget;
+
+    // Alg. 6 steps 4-5: squared distances of the two half-queries to their centroids
+    const float* qi = qt + q * Dp + size_t(i) * s;
+    for (int t = tid; t < 2 * sk; t += kSelThreads) {
+        const int h = t >= sk;
+        const int c = h ? t - sk : t;
+        const int off = h ? h1 : 0, len = h ? s - h1 : h1;
+        const float* cc = cent + (size_t(i) * sk + c) * s + off;
+        float acc = 0.f;
+        for (int j = 0; j < len; ++j) {
+            const float df = qi[off + j] - cc[j];
+            acc = fmaf(df, df, acc);
+        }
+        (h ? d2 : d1)[c] = acc;
+    }
+    for (int t = tid; t < kSelBins; t += kSelThreads) hist[t] = 0u;
+    if (tid == 0) {
+        s_min = 0xffffffffu;
+        s_max = 0u;
+        s_m = 0;
+        s_cnt = 0;
+        s_ret = 0ull;
+        s_T = ~0ull;
+        s_bucket = -1;
+        s_pre = 0ull;
+    }
+    __syncthreads();
+    const uint32_t* sz = sizes + size_t(i) * K;
+
+    if (budget <= n) {
+        // key range (the sums are >= +0, so their bit patterns order like the values)
+        uint32_t mn = 0xffffffffu, mx = 0u;
+        for (int cell = tid; cell < K; cell += kSelThreads) {
+            const uint32_t b = uint32_t(cell_key(d1, d2, sk, cell) >> 32);
+            mn = min(mn, b);
+            mx = max(mx, b);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        }
+        if (lane == 0) {
+            atomicMin(&s_min, mn);
+            atomicMax(&s_max, mx);
+        }
+        __syncthreads();
+        const uint32_t minb = s_min, range = s_max - s_min;
+        const int bits = range ? 32 - __clz(range) : 0;
+        const int shift = bits > 11 ? bits - 11 : 0;
+        // size-weighted histogram of the high key bits
+        for (int cell = tid; cell < K; cell += kSelThreads) {
+            const uint32_t w = sz[cell];
+            if (w) {
+                const uint32_t b = uint32_t(cell_key(d1, d2, sk, cell) >> 32);
+                atomicAdd(&hist[(b - minb) >> shift], w);
+            }
+        }
+        __syncthreads();
+        // block scan over the bins; find the bin where the running size first reaches B
+        unsigned long long loc = 0;
+#pragma unroll
+        for (int j = 0; j < kSelBinsPerThread; ++j) loc += hist[tid * kSelBinsPerThread + j];
+        unsigned long long incl = loc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) s_wsum[warp] = uint32_t(incl);
+        __syncthreads();
+        unsigned long long wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+        unsigned long long pre = wpre + incl - loc;
+        for (int j = 0; j < kSelBinsPerThread; ++j) {
+            const uint32_t hb = hist[tid * kSelBinsPerThread + j];
+            if (pre < (unsigned long long)budget && (unsigned long long)budget <= pre + hb) {
+                s_bucket = tid * kSelBinsPerThread + j;
+                s_pre = pre;
+            }
+            pre += hb;
+        }
+        __syncthreads();
+        // cells of that bin (with any size: empty cells keep their place in the order)
+        const int bucket = s_bucket;
+        for (int cell = tid; cell < K; cell += kSelThreads) {
+            const unsigned long long key = cell_key(d1, d2, sk, cell);
+            if (int((uint32_t(key >> 32) - minb) >> shift) == bucket) list[atomicAdd(&s_m, 1)] = key;
+        }
+        __syncthreads();
+        const int m = s_m;
+        int p2 = 1;
+        while (p2 < m) p2 <<= 1;
+        for (int t = m + tid; t < p2; t += kSelThreads) list[t] = ~0ull;
+        __syncthreads();
+        for (int k2 = 2; k2 <= p2; k2 <<= 1) {
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                for (int t = tid; t < p2; t += kSelThreads) {
+                    const int o = t ^ j;
+                    if (o > t) {
+                        const unsigned long long a = list[t], b = list[o];
+                        if ((a > b) == ((t & k2) == 0)) {
+                            list[t] = b;
+                            list[o] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // walk the sorted bin until the running size reaches B
+        if (warp == 0) {
+            unsigned long long cum = s_pre;
+            for (int b0 = 0; b0 < m; b0 += 32) {
+                const int idx = b0 + lane;
+                const unsigned long long key = idx < m ? list[idx] : ~0ull;
+                unsigned long long w = idx < m ? sz[uint32_t(key)] : 0ull;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned long long v = __shfl_up_sync(0xffffffffu, w, off);
+                    if (lane >= off) w += v;
+                }
+                const bool hit = idx < m && cum + w >= (unsigned long long)budget;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (bal) {
+                    if (lane == __ffs(bal) - 1) s_T = key;
+                    break;
+                }
+                cum += __shfl_sync(0xffffffffu, w, 31);
+            }
+        }
+        __syncthreads();
+    }
+    // the probed set: every cell whose key is <= T
+    const unsigned long long T = s_T;
+    const size_t qi_off = (size_t(q) * Ns + i);
+    unsigned long long ret = 0;
+    for (int base = 0; base < K; base += kSelThreads) {
+        const int cell = base + tid;
+        bool take = false;
+        if (cell < K) take = cell_key(d1, d2, sk, cell) <= T;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        int wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&s_cnt, __popc(bal));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (take) {
+            cells_out[qi_off * K + wbase + __popc(bal & ((1u << lane) - 1u))] = uint16_t(cell);
+            ret += sz[cell];
+        }
+        if (dbg_probed && cell < K) dbg_probed[qi_off * K + cell] = take ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) ret += __shfl_xor_sync(0xffffffffu, ret, off);
+    if (lane == 0 && ret) atomicAdd(&s_ret, ret);
+    __syncthreads();
+    if (tid == 0) {
+        ncells_out[qi_off] = s_cnt;
+        retrieved_out[qi_off] = (long long)s_ret;
+    }
+}
+
+static int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Cluster size and slabs per CTA for an index (called once at index creation).
+int configure_search(taco_index* ix) {
+    ix->n_slabs = int((ix->n + kSlabIds - 1) / kSlabIds);
+    // Aim for 4 slabs (64 KB of counters) per CTA so two clusters' CTAs share an SM.
+    int spc = 4;
+    int cluster = (ix->n_slabs + spc - 1) / spc;
+    if (cluster > 8) {
+        // grow the per-CTA range before going past the portable cluster size
+        spc = (ix->n_slabs + 7) / 8;
+        cluster = (ix->n_slabs + spc - 1) / spc;
+    }
+    if (spc > 12) {
+        spc = (ix->n_slabs + 15) / 16;
+        cluster = (ix->n_slabs + spc - 1) / spc;
+    }
+    if (spc > 12 || cluster > 16)
+        return fail(TACO_ECAPACITY, "n = %lld needs more than 16 x 12 counter slabs",
+                    (long long)ix->n);
+    if (cluster < 1) cluster = 1;
+    if (spc > ix->n_slabs) spc = ix->n_slabs;
+    ix->cluster = cluster;
+    ix->slabs_per_cta = spc;
+    return TACO_OK;
+}
+
+static int pick_g(int nchunks) {
+    // lanes per row so that each lane issues about 4 sixteen-byte loads per row
+    int g = 4;
+    while (g < 32 && g * 4 < nchunks) g <<= 1;
+    return g;
+}
+
+int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
+    const taco_index* ix = L.ix;
+    const int K = ix->K;
+    // 1. transform (Alg. 6 step 1)
+    TACO_CUDA(launch_project(L.queries, L.nq, ix->d, ix->d, ix->d_obar, ix->d_B, ix->Dp, L.qt, st));
+    if (L.dbg.query_t)
+        TACO_CUDA(cudaMemcpyAsync(L.dbg.query_t, L.qt, size_t(L.nq) * ix->Dp * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, st));
+    // 2. per (query, subspace) probed cells (Alg. 6 steps 3-6, Alg. 4)
+    {
+        const int cap = next_pow2(K);
+        const size_t smem = size_t(cap) * 8 + kSelBins * 4 + size_t(2) * ix->sk * 4;
+        static thread_local bool attr_set = false;
+        if (smem > 48 * 1024 && !attr_set) {
+            TACO_CUDA(cudaFuncSetAttribute(probe_cells_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+            attr_set = true;
+        }
+        dim3 grid(unsigned(ix->Ns), unsigned(L.nq));
+        probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
+            L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
+            L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed);
+        TACO_CUDA(cudaGetLastError());
+        if (L.dbg.retrieved_num)
+            TACO_CUDA(cudaMemcpyAsync(L.dbg.retrieved_num, L.retrieved,
+                                      size_t(L.nq) * ix->Ns * sizeof(int64_t),
+                                      cudaMemcpyDeviceToDevice, st));
+    }
+    // 3. count, select, re-rank (Alg. 6 steps 7-9, Alg. 5)
+    {
+        const bool bf16 = L.precision == TACO_PREC_BF16;
+        RerankParams P = {};
+        P.queries = L.queries;
+        P.data = ix->d_data;
+        P.data_bf16 = ix->d_data_bf16;
+        P.ids = ix->d_ids;
+        P.split = ix->d_split;
+        P.cells = L.cells;
+        P.ncells = L.ncells;
+        P.params = L.params;
+        P.defaults = L.defaults;
+        P.n = ix->n;
+        P.d = ix->d;
+        P.d_pad = ix->d_pad;
+        P.Ns = ix->Ns;
+        P.K = K;
+        P.n_slabs = ix->n_slabs;
+        P.slabs_per_cta = ix->slabs_per_cta;
+        P.counter_words = ix->slabs_per_cta * kSlabWords;
+        P.kk = L.kk_max;
+        P.kkc = next_pow2(L.kk_max);
+        const size_t merge_bytes = (size_t(2) * kRrWarps * P.kkc + 4 * size_t(P.kkc)) * 4;
+        P.region_a = std::max(size_t(P.counter_words) * 4, merge_bytes);
+        P.region_a = (P.region_a + 15) & ~size_t(15);
+        P.out_ids = L.out_ids;
+        P.out_dists = L.out_dists;
+        P.k_stride = L.k_stride;
+        P.dbg_sc = L.dbg.sc;
+        P.dbg_hist = L.dbg.collision_num;
+        P.dbg_last = L.dbg.last_collision;
+        P.dbg_cand = L.dbg.candidate_num;
+        const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(kRrWarps) * kQueueCap * 4 + 64;
+        const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
+        const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
+        cudaError_t e;
+        if (!bf16) {
+            e = R == 1 ? launch_rerank_b0_r1(G, P, ix->cluster, L.nq, smem, st)
+                : R == 4 ? launch_rerank_b0_r4(G, P, ix->cluster, L.nq, smem, st)
+                         : launch_rerank_b0_r16(G, P, ix->cluster, L.nq, smem, st);
+        } else {
+            e = R == 1 ? launch_rerank_b1_r1(G, P, ix->cluster, L.nq, smem, st)
+                : R == 4 ? launch_rerank_b1_r4(G, P, ix->cluster, L.nq, smem, st)
+                         : launch_rerank_b1_r16(G, P, ix->cluster, L.nq, smem, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "count_select_rerank launch", __FILE__, __LINE__);
+    }
+    return TACO_OK;
+}
+
+}  // namespace taco

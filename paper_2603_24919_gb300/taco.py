@@ -1,0 +1,307 @@
+"""Python binding of the TaCo C ABI (include/taco.h): argument marshalling only.
+
+Every step of index build and search runs inside libtaco.so. Device buffers are PyTorch
+CUDA tensors (PyTorch provides device memory and streams); host buffers are NumPy arrays.
+If libtaco.so is missing the first call raises: there is no other implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtaco.so")
+
+OK = 0
+EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO = -1, -2, -3, -4, -5, -6
+PREC_FP32, PREC_BF16 = 0, 1
+SELECT_LITERAL, SELECT_PROSE = 0, 1
+MAX_SUBSPACES, MAX_SQRT_K, MAX_K = 15, 128, 512
+
+_PREC = {"fp32": PREC_FP32, "bf16": PREC_BF16}
+_RULE = {"literal": SELECT_LITERAL, "prose": SELECT_PROSE}
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("n_subspaces", C.c_int32), ("sub_dim", C.c_int32), ("sqrt_k", C.c_int32),
+                ("kmeans_iters", C.c_int32), ("seed", C.c_uint64), ("keep_bf16", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class QueryParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("precision", C.c_int32), ("budget", C.c_int64),
+                ("rerank_target", C.c_int64), ("select_rule", C.c_int32),
+                ("shortlist_mult", C.c_int32)]
+
+
+class IndexParts(C.Structure):
+    _fields_ = [("o_bar", C.c_void_p), ("B", C.c_void_p), ("centroids", C.c_void_p),
+                ("codes", C.c_void_p), ("n_subspaces", C.c_int32), ("sub_dim", C.c_int32),
+                ("sqrt_k", C.c_int32), ("reserved", C.c_int32)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("n_subspaces", C.c_int32),
+                ("sub_dim", C.c_int32), ("sqrt_k", C.c_int32), ("d_pad", C.c_int32),
+                ("has_bf16", C.c_int32), ("n_slabs", C.c_int32), ("cluster_size", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+class DebugOut(C.Structure):
+    _fields_ = [("query_t", C.c_void_p), ("probed", C.c_void_p), ("retrieved_num", C.c_void_p),
+                ("sc", C.c_void_p), ("collision_num", C.c_void_p),
+                ("last_collision", C.c_void_p), ("candidate_num", C.c_void_p)]
+
+
+# name -> (restype, argtypes); the exported symbols of include/taco.h
+SIGNATURES = {
+    "taco_build_index": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(BuildParams),
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
+    "taco_index_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(IndexParts),
+                                    C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "taco_search_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                    C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "taco_search_debug": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                    C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.POINTER(DebugOut), C.c_void_p]),
+    "taco_index_get_info": (C.c_int, [C.c_void_p, C.POINTER(IndexInfo)]),
+    "taco_index_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "taco_save_index": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "taco_load_index": (C.c_int, [C.c_char_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "taco_free_index": (None, [C.c_void_p]),
+    "taco_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtaco.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2603_24919_gb300.build_lib.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TacoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"taco error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != OK:
+        msg = load_library().taco_last_error().decode(errors="replace")
+        raise TacoError(rc, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda_tensor(x):
+    try:
+        torch = _torch()
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _as_f32(x):
+    if _is_cuda_tensor(x):
+        torch = _torch()
+        return x.to(torch.float32).contiguous()
+    if not isinstance(x, np.ndarray):
+        try:
+            x = x.detach().cpu().numpy()
+        except AttributeError:
+            x = np.asarray(x)
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def query_params(k, budget, rerank_target, precision="fp32", select_rule="literal",
+                 shortlist_mult=4):
+    return QueryParams(int(k), _PREC.get(precision, precision), int(budget), int(rerank_target),
+                       _RULE.get(select_rule, select_rule), int(shortlist_mult))
+
+
+class TacoIndex:
+    """An index owned by libtaco (device memory on the current CUDA device)."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+
+    # ---- construction --------------------------------------------------------------
+    @classmethod
+    def build(cls, data, n_subspaces, sub_dim, sqrt_k, kmeans_iters=20, seed=0, keep_bf16=True,
+              stream=None):
+        lib = load_library()
+        x = _as_f32(data)
+        n, d = x.shape
+        p = BuildParams(n_subspaces, sub_dim, sqrt_k, kmeans_iters, seed, int(bool(keep_bf16)), 0)
+        out = C.c_void_p()
+        _check(lib.taco_build_index(_ptr(x), n, d, C.byref(p), _stream_handle(stream), C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def from_parts(cls, data, o_bar, B, centroids, codes, n_subspaces, sub_dim, sqrt_k,
+                   keep_bf16=True, stream=None):
+        lib = load_library()
+        x = _as_f32(data)
+        n, d = x.shape
+        ob = np.ascontiguousarray(o_bar, dtype=np.float64)
+        Bm = np.ascontiguousarray(B, dtype=np.float64)
+        ce = np.ascontiguousarray(centroids, dtype=np.float64)
+        co = np.ascontiguousarray(codes, dtype=np.uint16)
+        assert ob.shape == (d,) and Bm.shape == (d, n_subspaces * sub_dim)
+        assert ce.shape == (n_subspaces, sqrt_k, sub_dim) and co.shape == (n_subspaces, n)
+        parts = IndexParts(ob.ctypes.data, Bm.ctypes.data, ce.ctypes.data, co.ctypes.data,
+                           n_subspaces, sub_dim, sqrt_k, 0)
+        out = C.c_void_p()
+        _check(lib.taco_index_create(_ptr(x), n, d, C.byref(parts), int(bool(keep_bf16)),
+                                     _stream_handle(stream), C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def load(cls, path, keep_bf16=True, stream=None):
+        out = C.c_void_p()
+        _check(load_library().taco_load_index(os.fsencode(path), int(bool(keep_bf16)),
+                                              _stream_handle(stream), C.byref(out)))
+        return cls(out.value)
+
+    def save(self, path):
+        _check(load_library().taco_save_index(self._h, os.fsencode(path)))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load_library().taco_free_index(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- introspection -------------------------------------------------------------
+    def info(self):
+        inf = IndexInfo()
+        _check(load_library().taco_index_get_info(self._h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in IndexInfo._fields_}
+
+    def export(self):
+        inf = self.info()
+        n, d = inf["n"], inf["d"]
+        ns, s, sk = inf["n_subspaces"], inf["sub_dim"], inf["sqrt_k"]
+        out = {
+            "o_bar": np.zeros(d), "B": np.zeros((d, ns * s)), "eigvals": np.zeros(d),
+            "alloc": np.zeros(ns * s, dtype=np.int32), "centroids": np.zeros((ns, sk, s)),
+            "codes": np.zeros((ns, n), dtype=np.uint16),
+        }
+        _check(load_library().taco_index_export(
+            self._h, *[out[k].ctypes.data for k in ("o_bar", "B", "eigvals", "alloc",
+                                                     "centroids", "codes")]))
+        return out
+
+    # ---- search --------------------------------------------------------------------
+    def _prepare(self, queries, k, budget, rerank_target, precision, select_rule,
+                 shortlist_mult, per_query, k_stride):
+        q = _as_f32(queries)
+        nq = q.shape[0]
+        defaults = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult)
+        pq = None
+        if per_query is not None:
+            arr = (QueryParams * nq)()
+            for j, item in enumerate(per_query):
+                arr[j] = item if isinstance(item, QueryParams) else query_params(**item)
+            pq = arr
+            kmax = max(arr[j].k for j in range(nq)) if nq else k
+        else:
+            kmax = k
+        k_stride = int(k_stride or kmax)
+        return q, nq, defaults, pq, k_stride
+
+    def _outputs(self, q, nq, k_stride, out_ids, out_dists):
+        if out_ids is None or out_dists is None:
+            if _is_cuda_tensor(q):
+                torch = _torch()
+                out_ids = torch.empty((nq, k_stride), dtype=torch.int64, device=q.device)
+                out_dists = torch.empty((nq, k_stride), dtype=torch.float32, device=q.device)
+            else:
+                out_ids = np.empty((nq, k_stride), dtype=np.int64)
+                out_dists = np.empty((nq, k_stride), dtype=np.float32)
+        return out_ids, out_dists
+
+    def search(self, queries, k, budget, rerank_target, precision="fp32", select_rule="literal",
+               shortlist_mult=4, per_query=None, k_stride=None, out_ids=None, out_dists=None,
+               stream=None):
+        """Alg. 6 for a batch; returns (ids int64 [nq,k_stride], dists float32 [nq,k_stride])."""
+        q, nq, defaults, pq, k_stride = self._prepare(queries, k, budget, rerank_target, precision,
+                                                      select_rule, shortlist_mult, per_query, k_stride)
+        out_ids, out_dists = self._outputs(q, nq, k_stride, out_ids, out_dists)
+        _check(load_library().taco_search_batch(
+            self._h, _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
+            C.byref(defaults), k_stride, _ptr(out_ids), _ptr(out_dists), _stream_handle(stream)))
+        return out_ids, out_dists
+
+    def search_debug(self, queries, k, budget, rerank_target, precision="fp32",
+                     select_rule="literal", shortlist_mult=4, per_query=None, k_stride=None,
+                     want_sc=True, stream=None):
+        """search() plus every intermediate result (device tensors); queries on CUDA."""
+        torch = _torch()
+        q, nq, defaults, pq, k_stride = self._prepare(queries, k, budget, rerank_target, precision,
+                                                      select_rule, shortlist_mult, per_query, k_stride)
+        assert _is_cuda_tensor(q), "search_debug needs CUDA queries"
+        inf = self.info()
+        ns, K, n = inf["n_subspaces"], inf["sqrt_k"] ** 2, inf["n"]
+        dev = q.device
+        dbg = {
+            "query_t": torch.empty((nq, ns * inf["sub_dim"]), dtype=torch.float32, device=dev),
+            "probed": torch.empty((nq, ns, K), dtype=torch.uint8, device=dev),
+            "retrieved_num": torch.empty((nq, ns), dtype=torch.int64, device=dev),
+            "sc": torch.empty((nq, n), dtype=torch.uint8, device=dev) if want_sc else None,
+            "collision_num": torch.empty((nq, ns + 1), dtype=torch.int64, device=dev),
+            "last_collision": torch.empty((nq,), dtype=torch.int32, device=dev),
+            "candidate_num": torch.empty((nq,), dtype=torch.int64, device=dev),
+        }
+        d = DebugOut(*[_ptr(dbg[f]) for f, _ in DebugOut._fields_])
+        out_ids, out_dists = self._outputs(q, nq, k_stride, None, None)
+        _check(load_library().taco_search_debug(
+            self._h, _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
+            C.byref(defaults), k_stride, _ptr(out_ids), _ptr(out_dists), C.byref(d),
+            _stream_handle(stream)))
+        dbg["ids"], dbg["dists"] = out_ids, out_dists
+        return dbg

@@ -1,0 +1,89 @@
+"""Element-by-element comparison of the GPU path with the FP64 oracle.
+
+Acceptance rule (the method's FP32 path against the FP64 oracle):
+  * probed cell sets, retrieved_num, SC-scores, collision_num, last_collision, candidate_num
+    and result ids are identical, except where the oracle's FP64 boundary margin is below
+    TOL_MARGIN relative (a cell-key gap next to the last probed cell of a subspace, or the
+    gap between the k-th and (k+1)-th candidate distance): such cases are counted and
+    reported, not compared;
+  * returned distances agree within TOL_DIST relative.
+"""
+import numpy as np
+
+TOL_MARGIN = 1e-5
+TOL_DIST = 1e-5
+
+
+class ParityReport:
+    def __init__(self):
+        self.queries = 0
+        self.subspaces = 0
+        self.excluded_subspaces = 0
+        self.excluded_queries = 0
+        self.excluded_topk = 0
+
+    def __repr__(self):
+        return (f"queries={self.queries} subspaces={self.subspaces} "
+                f"excluded_subspaces={self.excluded_subspaces} "
+                f"excluded_queries={self.excluded_queries} excluded_topk={self.excluded_topk}")
+
+
+def probed_sets(gpu_probed_row):
+    """[N_s][K] uint8 -> list of sorted cell arrays."""
+    return [np.nonzero(r)[0] for r in gpu_probed_row]
+
+
+def compare_query(rep, trace, gpu, j, k, n, check_sc=True):
+    """Compare GPU debug outputs of query j (numpy dict) with one oracle trace."""
+    rep.queries += 1
+    ns = len(trace.probed)
+    all_sets_equal = True
+    for i in range(ns):
+        rep.subspaces += 1
+        want = np.sort(trace.probed[i])
+        got = np.nonzero(gpu["probed"][j, i])[0]
+        if trace.probe_margin[i] < TOL_MARGIN:
+            rep.excluded_subspaces += 1
+            if not np.array_equal(want, got):
+                all_sets_equal = False
+            continue
+        assert np.array_equal(want, got), (j, i, trace.probe_margin[i], len(want), len(got))
+        assert gpu["retrieved_num"][j, i] == trace.retrieved_num[i], (j, i)
+    if not all_sets_equal:
+        rep.excluded_queries += 1
+        return
+    if check_sc and gpu.get("sc") is not None:
+        assert np.array_equal(gpu["sc"][j].astype(np.int64), trace.sc), j
+    assert np.array_equal(gpu["collision_num"][j], trace.collision_num), (j, gpu["collision_num"][j], trace.collision_num)
+    assert int(gpu["last_collision"][j]) == trace.last_collision, j
+    assert int(gpu["candidate_num"][j]) == trace.candidate_num, j
+    compare_topk(rep, trace.ids, trace.dists, trace.kth_margin, gpu["ids"][j], gpu["dists"][j], k)
+
+
+def compare_topk(rep, o_ids, o_dists, kth_margin, g_ids, g_dists, k):
+    g_ids = np.asarray(g_ids[:k])
+    g_dists = np.asarray(g_dists[:k], dtype=np.float64)
+    valid = o_ids[:k] >= 0
+    assert np.array_equal(g_ids < 0, ~valid), (g_ids, o_ids)
+    # distances of the returned ranks agree (ranks are distance-ordered on both sides)
+    od = o_dists[:k][valid]
+    gd = g_dists[valid]
+    assert np.all(np.abs(gd - od) <= TOL_DIST * np.maximum(od, 1e-30) + 1e-30), (gd, od)
+    if kth_margin < TOL_MARGIN:
+        rep.excluded_topk += 1
+        return
+    assert set(g_ids[valid].tolist()) == set(o_ids[:k][valid].tolist()), (g_ids, o_ids)
+    # order: where neighbouring oracle distances are well separated the ids match by rank
+    sq = o_dists[:k][valid] ** 2
+    for r in range(len(sq)):
+        lo_ok = r == 0 or (sq[r] - sq[r - 1]) > TOL_MARGIN * sq[r]
+        hi_ok = r == len(sq) - 1 or (sq[r + 1] - sq[r]) > TOL_MARGIN * sq[r + 1]
+        if lo_ok and hi_ok:
+            assert g_ids[r] == o_ids[r], (r, g_ids, o_ids)
+
+
+def to_numpy(dbg):
+    out = {}
+    for key, v in dbg.items():
+        out[key] = None if v is None else v.cpu().numpy()
+    return out

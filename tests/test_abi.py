@@ -1,0 +1,94 @@
+"""The C-ABI library loads without a GPU, exports every symbol include/taco.h declares,
+and the binding's structs match the header's layout. No compute calls."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2603_24919_gb300 import build_lib
+from paper_2603_24919_gb300 import taco as T
+
+HEADER = os.path.join(build_lib.INCLUDE, "taco.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return T.load_library()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(taco_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ["taco_build_index", "taco_index_create", "taco_search_batch", "taco_search_debug",
+                 "taco_index_get_info", "taco_index_export", "taco_save_index",
+                 "taco_load_index", "taco_free_index", "taco_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", build_lib.LIB], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\sT\s+(taco_\w+)", out))
+    assert set(_declared_functions()) <= exported
+    assert set(T.SIGNATURES) == set(_declared_functions())
+
+
+def test_last_error_empty_and_null_args(lib):
+    assert lib.taco_last_error() is not None
+    # argument checks run before any CUDA call
+    assert lib.taco_search_batch(None, None, 0, None, None, 1, None, None, None) == T.EINVAL
+    assert b"null index" in lib.taco_last_error()
+    assert lib.taco_index_get_info(None, None) == T.EINVAL
+    assert lib.taco_save_index(None, b"/nonexistent") == T.EINVAL
+    out = ctypes.c_void_p()
+    assert lib.taco_load_index(b"/nonexistent/file", 0, None, ctypes.byref(out)) == T.EIO
+    lib.taco_free_index(None)
+
+
+_LAYOUT_C = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "taco.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+#define S(T) printf(#T " %zu\n", sizeof(T))
+int main(void) {
+  S(taco_build_params); P(taco_build_params, seed); P(taco_build_params, keep_bf16);
+  S(taco_query_params); P(taco_query_params, budget); P(taco_query_params, rerank_target);
+  P(taco_query_params, select_rule); P(taco_query_params, shortlist_mult);
+  S(taco_index_parts); P(taco_index_parts, codes); P(taco_index_parts, sqrt_k);
+  S(taco_index_info); P(taco_index_info, d_pad); P(taco_index_info, cluster_size);
+  P(taco_index_info, device_bytes);
+  S(taco_debug_out); P(taco_debug_out, candidate_num);
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_header():
+    with tempfile.TemporaryDirectory() as td:
+        src = os.path.join(td, "layout.c")
+        exe = os.path.join(td, "layout")
+        open(src, "w").write(_LAYOUT_C)
+        subprocess.run(["gcc", "-I", build_lib.INCLUDE, src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    want = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    cmap = {"taco_build_params": T.BuildParams, "taco_query_params": T.QueryParams,
+            "taco_index_parts": T.IndexParts, "taco_index_info": T.IndexInfo,
+            "taco_debug_out": T.DebugOut}
+    for key, val in want.items():
+        if "." in key:
+            s, f = key.split(".")
+            assert getattr(cmap[s], f).offset == int(val), key
+        else:
+            assert ctypes.sizeof(cmap[key]) == int(val), key

@@ -1,0 +1,85 @@
+"""The library's own index build (taco_build_index) checked against the FP64 oracle's
+build by invariants: Alg. 1 (mean, covariance eigenvectors), Alg. 2 (allocation),
+Alg. 3 (k-means fixed point, IMI cells), and search quality on the built index."""
+import numpy as np
+import pytest
+
+from oracle import taco_oracle as O
+from synth import make_workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2603_24919_gb300 import TacoIndex, build_lib  # noqa: E402
+
+build_lib.build()
+
+
+@pytest.fixture(scope="module")
+def built():
+    w, data, queries = make_workload("tiny20k")
+    ix = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=20, seed=4)
+    ex = ix.export()
+    yield w, data, queries, ix, ex
+    ix.close()
+
+
+def test_transform_matches_oracle_eigensystem(built):
+    w, data, queries, ix, ex = built
+    mu, sigma = O.mean_and_covariance(data)
+    assert np.allclose(ex["o_bar"], mu, rtol=1e-10, atol=1e-9)
+    B = ex["B"]
+    assert np.abs(B.T @ B - np.eye(B.shape[1])).max() < 1e-10
+    lam, xi = O.spectral_decomposition(sigma)
+    lam_desc = np.sort(lam)[::-1]
+    assert np.allclose(ex["eigvals"], lam_desc, rtol=1e-9, atol=1e-9 * lam_desc[0])
+    # every column of B is an eigenvector of the oracle's covariance with the eigenvalue of
+    # its allocation rank
+    for c in range(B.shape[1]):
+        v = B[:, c]
+        lv = lam_desc[ex["alloc"][c]]
+        assert np.linalg.norm(sigma @ v - lv * v) <= 1e-7 * lam_desc[0]
+
+
+def test_allocation_matches_oracle(built):
+    w, data, queries, ix, ex = built
+    mu, sigma = O.mean_and_covariance(data)
+    lam, _ = O.spectral_decomposition(sigma)
+    buckets, order = O.eigensystem_allocation(lam, w.n_subspaces, w.sub_dim)
+    rank = {int(e): r for r, e in enumerate(order)}
+    lam_sorted = np.sort(lam)[::-1]
+    gaps = np.diff(lam_sorted) / lam_sorted[0]
+    if np.min(np.abs(gaps[:w.n_subspaces * w.sub_dim])) > 1e-9:
+        want = [[rank[e] for e in b] for b in buckets]
+        got = ex["alloc"].reshape(w.n_subspaces, w.sub_dim).tolist()
+        assert got == want
+
+
+def test_kmeans_codes_are_nearest_centroids(built):
+    w, data, queries, ix, ex = built
+    T = O.transform(data, ex["o_bar"], ex["B"])
+    h1 = w.sub_dim // 2
+    mismatch = 0
+    for i in range(w.n_subspaces):
+        Ti = T[:, i * w.sub_dim:(i + 1) * w.sub_dim]
+        C = ex["centroids"][i]
+        d1 = ((Ti[:, None, :h1] - C[None, :, :h1]) ** 2).sum(-1)
+        d2 = ((Ti[:, None, h1:] - C[None, :, h1:]) ** 2).sum(-1)
+        r = ex["codes"][i].astype(np.int64) // w.sqrt_k
+        c = ex["codes"][i].astype(np.int64) % w.sqrt_k
+        # the assigned centroid is nearest up to FP32 rounding of the GPU distances
+        best1, best2 = d1.min(1), d2.min(1)
+        got1, got2 = d1[np.arange(len(r)), r], d2[np.arange(len(c)), c]
+        mismatch += np.sum(got1 > best1 * (1 + 1e-4) + 1e-6) + np.sum(got2 > best2 * (1 + 1e-4) + 1e-6)
+    assert mismatch == 0
+
+
+def test_built_index_recall(built):
+    w, data, queries, ix, ex = built
+    t_ids, _ = O.brute_force_knn(data, queries, 10)
+    ids, _ = ix.search(torch.from_numpy(queries).cuda(), 10, w.budget, w.rerank_target)
+    rec = O.recall(ids.cpu().numpy(), t_ids, 10)
+    assert rec > 0.9, rec
