@@ -1,0 +1,510 @@
+#!/usr/bin/env python
+"""Benchmark of the TaCo query path on one GB300: QPS at recall@10 >= 0.95.
+
+Workload: 1,000,000 x 128 float32 points with integer values 0..255 (a 1024-component
+Gaussian mixture rounded and clipped, a SIFT-like stand-in), 10,000 queries from the same
+mixture, k = 10, N_s = 8 subspaces of s = 16 dims, sqrt(K) = 64. One step = the whole
+query path (transform, cell probe, collision counting, Alg. 5 selection, re-rank) over the
+batch of 10,000 queries.
+
+The operating point (alpha, beta) of each form (plain FP32, batched BF16) is the one with
+the highest QPS whose mean recall@10 against exact k-NN is >= 0.95, over a grid inside the
+paper's ranges. The headline `value` is the BF16 form; the FP32 form is reported beside it.
+
+Arms:
+  default            the CUDA library (libtaco.so) through its C ABI
+  --impl reference   the FP64 CPU oracle on the host cores, a bounded query sample per step
+
+Multi-GPU (torchrun): every rank holds a replica of the index and answers its own batch;
+no collective is on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10≥0.95, 1 GB300: batched BF16 vs plain FP32; p50/p99 latency"
+WORKLOAD = "sift1m"
+ALPHAS = [0.01, 0.02, 0.03, 0.05, 0.08, 0.1]
+BETAS = [0.001, 0.002, 0.005, 0.01]
+RECALL_TARGET = 0.95
+SHORTLIST_MULTS = [1, 2, 4]   # BF16 form: exact FP32 re-rank of mult * k
+K = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="taco", choices=["taco", "reference"])
+    ap.add_argument("--nq", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--alpha", type=float, default=None, help="skip calibration (both forms)")
+    ap.add_argument("--beta", type=float, default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------------------ helpers
+def exact_knn_gpu(torch, data_t, queries_t, data_np, queries_np, k, extra=32, chunk=1000):
+    """Exact k-NN for recall: FP32 brute force on the GPU for a candidate pool of k+extra,
+    then FP64 re-check of the pool on the host (ordered by distance, then id)."""
+    xn = (data_t * data_t).sum(1)
+    out = np.empty((queries_t.shape[0], k), dtype=np.int64)
+    for a in range(0, queries_t.shape[0], chunk):
+        q = queries_t[a:a + chunk]
+        d2 = (q * q).sum(1, keepdim=True) - 2.0 * (q @ data_t.T) + xn[None, :]
+        pool = torch.topk(d2, k + extra, dim=1, largest=False).indices.cpu().numpy()
+        qq = queries_np[a:a + chunk].astype(np.float64)
+        for j in range(pool.shape[0]):
+            cand = pool[j]
+            dd = ((data_np[cand].astype(np.float64) - qq[j]) ** 2).sum(1)
+            o = np.lexsort((cand, dd))[:k]
+            out[a + j] = cand[o]
+    return out
+
+
+def recall_at(ids, truth, k):
+    ids = np.asarray(ids)[:, :k]
+    hits = [len(set(r.tolist()) & set(t.tolist())) for r, t in zip(ids, truth[:, :k])]
+    return float(np.mean(hits)) / k
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_24919_gb300", "csrc")
+    for name in ("taco_rerank.cuh", "taco_search.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "count_select_rerank_sift1m.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    entry = j.get(precision)
+    if not entry or entry.get("source_hash") != kernel_source_hash():
+        return None
+    return entry.get("dram_bytes_per_launch_full_batch")
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_taco(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    from paper_2603_24919_gb300 import TacoIndex, build_lib
+    from synth import budget_from_alpha, make_workload, target_from_beta
+
+    if rank == 0:
+        build_lib.build()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.time()
+    w, data, queries = make_workload(WORKLOAD, nq=args.nq)
+    nq = queries.shape[0]
+    log(f"[rank {rank}] workload {w.name}: n={w.n} d={w.d} nq={nq} ({time.time() - t0:.1f}s)")
+    t0 = time.time()
+    ix = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=20, seed=1,
+                         keep_bf16=True)
+    torch.cuda.synchronize()
+    info = ix.info()
+    log(f"[rank {rank}] index built in {time.time() - t0:.1f}s: {info}")
+    q_dev = torch.from_numpy(queries).cuda()
+    data_dev = torch.from_numpy(data).cuda()
+    truth = exact_knn_gpu(torch, data_dev, q_dev, data, queries, K)
+    del data_dev
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    def timed(prec, a, b, reps, mult=4):
+        bud, tgt = budget_from_alpha(a, w.n), target_from_beta(b, w.n)
+        ids, _ = ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ids, _ = ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return recall_at(ids.cpu().numpy(), truth, K), nq / (ms * 1e-3), ms
+
+    # ---- calibration: per form, the fastest grid point meeting the recall target ------
+    calib = {}
+    for prec in ("fp32", "bf16"):
+        best = None
+        grid = [(args.alpha, args.beta)] if args.alpha else [(a, b) for a in ALPHAS for b in BETAS]
+        mults = SHORTLIST_MULTS if prec == "bf16" else [4]
+        for a, b in grid:
+            for mult in mults:
+                rec, qps, ms = timed(prec, a, b, 2, mult)
+                ok = rec >= RECALL_TARGET
+                if ok and (best is None or qps > best["qps"]):
+                    best = {"alpha": a, "beta": b, "shortlist_mult": mult, "recall": rec, "qps": qps}
+        if best is None:  # nothing met the target: take the highest recall point
+            a, b = ALPHAS[-1], BETAS[-1]
+            rec, qps, ms = timed(prec, a, b, 2)
+            best = {"alpha": a, "beta": b, "shortlist_mult": 4, "recall": rec, "qps": qps}
+        calib[prec] = best
+        log(f"[rank {rank}] {prec} operating point: {best}")
+
+    def run_steps(prec, steps, warmup, profile=False):
+        a, b = calib[prec]["alpha"], calib[prec]["beta"]
+        mult = calib[prec]["shortlist_mult"]
+        bud, tgt = budget_from_alpha(a, w.n), target_from_beta(b, w.n)
+        out_ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
+        out_d = torch.empty((nq, K), dtype=torch.float32, device="cuda")
+        for _ in range(warmup):
+            ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult, out_ids=out_ids,
+                      out_dists=out_d)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ix.profile_read(reset=True)
+            ix.profile(True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for s in range(steps):
+            ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult, out_ids=out_ids,
+                      out_dists=out_d)
+            evs[s + 1].record(stream)
+        torch.cuda.synchronize()
+        if profile:
+            ix.profile(False)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
+        total = evs[0].elapsed_time(evs[-1])
+        kt = ix.profile_read(reset=True) if profile else None
+        rec = recall_at(out_ids.cpu().numpy(), truth, K)
+        return total, per, kt, rec
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    tot_b, per_b, kt_b, rec_b = run_steps("bf16", args.steps, args.warmup, profile=True)
+    tot_f, per_f, kt_f, rec_f = run_steps("fp32", args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+
+    # max over ranks of the timed region
+    if ws > 1:
+        t = torch.tensor([tot_b, tot_f], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_b, tot_f = float(t[0]), float(t[1])
+    value = ws * nq * args.steps / (tot_b * 1e-3)
+    value_fp32 = ws * nq * args.steps / (tot_f * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers --------------------------------
+    a, b = calib["bf16"]["alpha"], calib["bf16"]["beta"]
+    mult = calib["bf16"]["shortlist_mult"]
+    bud, tgt = budget_from_alpha(a, w.n), target_from_beta(b, w.n)
+    q_host = torch.from_numpy(queries).pin_memory()
+    o_ids = torch.empty((nq, K), dtype=torch.int64).pin_memory()
+    o_d = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+    qh, oi, od = q_host.numpy(), o_ids.numpy(), o_d.numpy()
+    for _ in range(max(1, args.warmup)):
+        ix.search(qh, K, bud, tgt, precision="bf16", shortlist_mult=mult, out_ids=oi, out_dists=od)
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ix.search(qh, K, bud, tgt, precision="bf16", shortlist_mult=mult, out_ids=oi, out_dists=od)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e_recall = recall_at(oi, truth, K)
+
+    # ---- roofline of the dominant kernel ----------------------------------------------
+    dbg = ix.search_debug(q_dev, K, bud, tgt, precision="bf16", shortlist_mult=mult,
+                          want_sc=False)
+    torch.cuda.synchronize()
+    retrieved = int(dbg["retrieved_num"].sum().item())
+    ncells = int(dbg["probed"].sum(dtype=torch.int64).item())
+    cand = int(dbg["candidate_num"].sum().item())
+    shortlist = min(mult * K, 512)
+    d_pad = info["d_pad"]
+    alg_bytes = (4 * retrieved + 8 * ncells + cand * d_pad * 2 + nq * shortlist * d_pad * 4
+                 + nq * (w.d * 4 + K * 12))
+    kk = kt_b["count_select_rerank"]
+    launch_ms = kk["ms"] / max(kk["launches"], 1)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    shares = {name: round(v["ms"] / max(sum(x["ms"] for x in kt_b.values()), 1e-9), 4)
+              for name, v in kt_b.items() if v["launches"]}
+
+    # small-batch latency (serving-sized batches of 64 queries, not part of `value`)
+    lat_small = []
+    for s in range(0, min(nq, 64 * 100), 64):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.search(q_dev[s:s + 64], K, bud, tgt, precision="bf16", shortlist_mult=mult)
+        e1.record(stream)
+        e1.synchronize()
+        lat_small.append(e0.elapsed_time(e1))
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(tot_b / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "sift1m-like: n=1,000,000 d=128 integer GMM, nq=10,000 per step, "
+                               "k=10, N_s=8, s=16, sqrtK=64",
+                   "global_batch": ws * nq, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (512 MB FP32 / 256 MB BF16 rows gathered)",
+                   "operating_point": calib},
+        "recall_at_10": {"bf16": round(rec_b, 4), "fp32": round(rec_f, 4)},
+        "fp32_qps": round(value_fp32, 1),
+        "bf16_over_fp32": round(value / value_fp32, 3),
+        "latency_ms": {"batch": nq,
+                       "p50": round(float(np.percentile(per_b, 50)), 4),
+                       "p99": round(float(np.percentile(per_b, 99)), 4),
+                       "fp32_p50": round(float(np.percentile(per_f, 50)), 4),
+                       "fp32_p99": round(float(np.percentile(per_f, 99)), 4),
+                       "batch64_p50": round(float(np.percentile(lat_small, 50)), 4),
+                       "batch64_p99": round(float(np.percentile(lat_small, 99)), 4)},
+        "e2e": {"value": round(ws * nq * args.steps / e2e_s, 1), "unit": "queries/s",
+                "h2d_bytes_per_step": int(queries.nbytes),
+                "d2h_bytes_per_step": int(nq * K * (8 + 4)),
+                "recall_at_10": round(e2e_recall, 4)},
+        "gpu_launches": int(sum(v["launches"] for v in kt_b.values())),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": ncu_traffic("bf16"), "peak_kind": peak_kind,
+                     "kernel": "count_select_rerank (bf16)",
+                     "algorithmic_bytes_per_launch": int(alg_bytes),
+                     "launch_ms": round(launch_ms, 4),
+                     "kernel_share": shares},
+        "clocks": clk,
+    }
+    fk = kt_f["count_select_rerank"]
+    f_launch_ms = fk["ms"] / max(fk["launches"], 1)
+    line["roofline_fp32"] = {"launch_ms": round(f_launch_ms, 4)}
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(ix, data, queries, w, calib["fp32"], args.cpu_seconds)
+    ix.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(ix, data, queries, w, op, seconds):
+    """The FP64 oracle's query routine (Alg. 6) on the host, over the same index (exported
+    from the library), data and queries, for a bounded sample of queries."""
+    from oracle import taco_oracle as O
+    from synth import budget_from_alpha, target_from_beta
+
+    ex = ix.export()
+    oix = O.index_from_parts(ex["o_bar"], ex["B"], ex["centroids"], ex["codes"],
+                             w.n_subspaces, w.sub_dim, w.sqrt_k)
+    bud, tgt = budget_from_alpha(op["alpha"], w.n), target_from_beta(op["beta"], w.n)
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(queries) and time.perf_counter() - t0 < seconds:
+        O.search_one(oix, data, queries[done], K, bud, tgt)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of {len(queries)} queries, fp32 operating point "
+                      f"alpha={op['alpha']} beta={op['beta']}, single-threaded NumPy FP64"}
+
+
+# ------------------------------------------------------------------------ reference arm
+def _kmeans_job(args):
+    from oracle import taco_oracle as O
+    cols, sk, iters, seed = args
+    return O.kmeans(cols, sk, iters, seed)
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+
+    from oracle import taco_oracle as O
+    from synth import budget_from_alpha, make_workload, target_from_beta
+
+    t0 = time.time()
+    w, data, queries = make_workload(WORKLOAD, nq=args.nq)
+    # the oracle's own index (Alg. 1-3 in FP64); k-means halves run in a spawn pool
+    mu, sigma = O.mean_and_covariance(data)
+    lam, xi = O.spectral_decomposition(sigma)
+    buckets, _ = O.eigensystem_allocation(lam, w.n_subspaces, w.sub_dim)
+    B = O.transform_matrix(xi, buckets)
+    T = O.transform(data, mu, B)
+    h1, _ = O.half_dims(w.sub_dim)
+    jobs = []
+    for i in range(w.n_subspaces):
+        Ti = T[:, i * w.sub_dim:(i + 1) * w.sub_dim]
+        jobs.append((np.ascontiguousarray(Ti[:, :h1]), w.sqrt_k, 20, 1 * 7919 + 2 * i))
+        jobs.append((np.ascontiguousarray(Ti[:, h1:]), w.sqrt_k, 20, 1 * 7919 + 2 * i + 1))
+    del T
+    cores = os.cpu_count() or 1
+    with ProcessPoolExecutor(max_workers=min(cores, len(jobs)),
+                             mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_kmeans_job, jobs))
+    cent = np.zeros((w.n_subspaces, w.sqrt_k, w.sub_dim))
+    codes = np.zeros((w.n_subspaces, w.n), dtype=np.int64)
+    for i in range(w.n_subspaces):
+        (c1, a1), (c2, a2) = res[2 * i], res[2 * i + 1]
+        cent[i, :, :h1], cent[i, :, h1:] = c1, c2
+        codes[i] = a1 * w.sqrt_k + a2
+    oix = O.index_from_parts(mu, B, cent, codes, w.n_subspaces, w.sub_dim, w.sqrt_k)
+    log(f"[reference] oracle index built in {time.time() - t0:.1f}s")
+    # the FP32 form's usual operating point on this workload (GPU calibration: alpha .02,
+    # beta .001); the oracle is not calibrated itself
+    alpha, beta = (args.alpha or 0.02), (args.beta or 0.001)
+    bud, tgt = budget_from_alpha(alpha, w.n), target_from_beta(beta, w.n)
+    per_step = max(1, int(os.environ.get("TACO_REF_QUERIES_PER_STEP", "4")))
+    qi = 0
+    for _ in range(args.warmup):
+        O.search_one(oix, data, queries[qi % len(queries)], K, bud, tgt)
+        qi += 1
+    times = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        for _ in range(per_step):
+            O.search_one(oix, data, queries[qi % len(queries)], K, bud, tgt)
+            qi += 1
+        times.append(time.perf_counter() - t1)
+    total = sum(times)
+    value = args.steps * per_step / total
+    sample = (f"{per_step} queries per step of the {len(queries)}-query batch, alpha={alpha} "
+              f"beta={beta}, single-threaded NumPy FP64 oracle")
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sift1m-like: n=1,000,000 d=128 integer GMM, nq=10,000, k=10, "
+                               "N_s=8, s=16, sqrtK=64", "parallelism": "host cores"},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_taco(args)
+
+
+if __name__ == "__main__":
+    main()

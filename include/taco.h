@@ -169,6 +169,24 @@ int taco_index_export(const taco_index* index, double* o_bar, double* B, double*
 int taco_save_index(const taco_index* index, const char* path);
 int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_index** out);
 
+/* Per-kernel device time of the search path, accumulated while profiling is enabled.
+ * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 fused count/select/
+ * re-rank (Def. 6, Alg. 5, Alg. 6 step 9), 3 reserved. */
+#define TACO_NUM_KERNELS 4
+typedef struct {
+    int64_t launches[TACO_NUM_KERNELS];
+    double ms[TACO_NUM_KERNELS];
+} taco_kernel_times;
+
+/* taco_profile_enable -- start (enable != 0) or stop recording a CUDA event pair on the
+ * search stream around every kernel launch of this index. Recording adds no
+ * synchronisation; events are read by taco_profile_read. */
+int taco_profile_enable(taco_index* index, int32_t enable);
+
+/* taco_profile_read -- wait for the recorded events, add their elapsed times to *out
+ * (host struct, overwritten) and, if reset != 0, clear the accumulated totals. */
+int taco_profile_read(taco_index* index, taco_kernel_times* out, int32_t reset);
+
 /* taco_free_index -- release an index and all its device memory (NULL is a no-op). */
 void taco_free_index(taco_index* index);
 

@@ -177,7 +177,11 @@ class OracleIndex:
         return self.sqrt_k * self.sqrt_k
 
     def cell_sizes(self, i):
-        return np.array([len(c) for c in self.cells[i]], dtype=np.int64)
+        """|IMI_i[cell]| for every cell of subspace i (computed once, then reused)."""
+        cache = self.__dict__.setdefault("_sizes", {})
+        if i not in cache:
+            cache[i] = np.array([len(c) for c in self.cells[i]], dtype=np.int64)
+        return cache[i]
 
 
 def imi_cells(codes_i, n_cells):

@@ -47,6 +47,7 @@ void free_device(taco_index* ix) {
 struct IndexDeleter {
     void operator()(taco_index* ix) const {
         if (ix) {
+            for (cudaEvent_t e : ix->prof.pool) cudaEventDestroy(e);
             free_device(ix);
             delete ix;
         }
@@ -580,8 +581,40 @@ int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_inde
     return TACO_OK;
 }
 
+int taco_profile_enable(taco_index* ix, int32_t enable) {
+    if (!ix) return fail(TACO_EINVAL, "null index");
+    std::lock_guard<std::mutex> lock(ix->ws_mu);
+    ix->prof.enabled = enable != 0;
+    return TACO_OK;
+}
+
+int taco_profile_read(taco_index* ix, taco_kernel_times* out, int32_t reset) {
+    if (!ix || !out) return fail(TACO_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lock(ix->ws_mu);
+    Profiler& pr = ix->prof;
+    for (auto& p : pr.pending) {
+        TACO_CUDA(cudaEventSynchronize(p.second.second));
+        float ms = 0.f;
+        TACO_CUDA(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+        pr.ms[p.first] += ms;
+        pr.launches[p.first] += 1;
+    }
+    pr.pending.clear();
+    pr.used = 0;
+    for (int k = 0; k < TACO_NUM_KERNELS; ++k) {
+        out->launches[k] = pr.launches[k];
+        out->ms[k] = pr.ms[k];
+        if (reset) {
+            pr.launches[k] = 0;
+            pr.ms[k] = 0.0;
+        }
+    }
+    return TACO_OK;
+}
+
 void taco_free_index(taco_index* ix) {
     if (!ix) return;
+    for (cudaEvent_t e : ix->prof.pool) cudaEventDestroy(e);
     free_device(ix);
     delete ix;
 }

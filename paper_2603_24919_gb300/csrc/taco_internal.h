@@ -50,6 +50,15 @@ void jacobi_eigen(int d, std::vector<double>& a, std::vector<double>& vecs,
 void eigensystem_allocation(const std::vector<double>& lam, int n_subspaces, int sub_dim,
                             std::vector<std::vector<int>>& buckets);
 
+struct Profiler {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;                 // reusable events
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    size_t used = 0;
+    int64_t launches[TACO_NUM_KERNELS] = {0, 0, 0, 0};
+    double ms[TACO_NUM_KERNELS] = {0, 0, 0, 0};
+};
+
 struct Workspace {
     void* base = nullptr;
     size_t bytes = 0;
@@ -81,6 +90,7 @@ struct taco_index {
     int64_t device_bytes = 0;
     std::mutex ws_mu;
     taco::Workspace ws;
+    taco::Profiler prof;
 };
 
 namespace taco {
@@ -116,6 +126,9 @@ struct SearchLaunch {
     taco_debug_out dbg;        // device pointers, already offset to this chunk
 };
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
+// Event pair around one kernel launch when profiling is enabled (no-op otherwise).
+int prof_begin(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t* b, cudaEvent_t* e);
+int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent_t e);
 int configure_search(taco_index* ix);
 
 }  // namespace taco

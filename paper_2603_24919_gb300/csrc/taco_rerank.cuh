@@ -1,21 +1,26 @@
 // Fused collision counting (Alg. 6 step 7, Def. 6), query-aware candidate selection
-// (Alg. 5) and exact re-rank (Alg. 6 step 9) for one query per thread-block cluster.
+// (Alg. 5) and exact re-rank (Alg. 6 step 9). One thread-block cluster answers a query;
+// the clusters of a persistent grid loop over the batch.
 //
-// Layout: the n point ids are split into slabs of 2^15. CTA r of a query's cluster owns a
+// Layout: the n point ids are split into slabs of 2^15. CTA r of a cluster owns a
 // contiguous range of slabs and holds one 4-bit SC counter per owned id in shared memory
-// (N_s <= 15). Cell id lists are ascending, so the ids of a probed cell that fall in the
-// CTA's range form one contiguous run; a per-cell table of slab boundaries gives the run.
-//   1. count:  every warp takes probed cells; lanes read the run's ids (coalesced) and add
-//              1 to the id's nibble with a shared-memory atomic.
-//   2. levels: each CTA counts its ids with SC >= j for every j (SWAR over nibbles); the
-//              cluster sums these through distributed shared memory, giving collision_num
-//              over all n points, and every CTA evaluates Alg. 5 to the same threshold.
-//   3. re-rank: warps scan their counter words, queue the ids whose SC reaches the
-//              threshold, gather the rows (G lanes per row, 16-byte loads) and keep a
-//              warp-wide sorted top list in registers (insertion by ballot + shuffle).
-//   4. merge:  warp lists -> CTA list (warp 0, k-way merge) -> cluster list in CTA 0 via
-//              distributed shared memory. With BF16 rows the merged list is a shortlist
-//              that CTA 0 re-ranks with FP32 rows before writing the top k.
+// (N_s <= 15), plus one bit per counter word marking the words the query touched. Cell id
+// lists are ascending, so the ids of a probed cell that fall in the CTA's range form one
+// contiguous run; a per-cell table of slab boundaries gives the run.
+//   1. count:   the runs of all probed cells are staged (start, prefix of lengths) and
+//               walked by all warps; each id adds 1 to its nibble with a shared-memory
+//               atomic whose old value also tells which SC level the id just reached, so
+//               the per-level counts (ids with SC >= j) come for free.
+//   2. select:  the cluster sums the per-level counts through distributed shared memory,
+//               giving collision_num over all n points; every CTA evaluates Alg. 5 to the
+//               same threshold.
+//   3. re-rank: the touched words are scanned (and cleared, so the counters are zero for
+//               the next query); ids whose SC reaches the threshold are buffered, their rows
+//               gathered (G lanes per row, 16-byte loads) and each warp keeps a sorted top
+//               list in registers (insertion by ballot + shuffle).
+//   4. merge:   warp lists -> CTA list -> cluster list in CTA 0 through distributed shared
+//               memory, each by a parallel rank merge. With BF16 rows the merged list is a
+//               shortlist that CTA 0 re-ranks with FP32 rows before writing the top k.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -31,7 +36,6 @@ namespace cg = cooperative_groups;
 
 constexpr int kRrThreads = 512;
 constexpr int kRrWarps = kRrThreads / 32;
-constexpr int kQueueCap = 256;   // one scan step: 32 words x 8 ids
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kNoId = 0xffffffffu;
 
@@ -50,7 +54,9 @@ struct RerankParams {
     int counter_words;      // slabs_per_cta * kSlabWords
     int kk;                 // list length (<= 32*R)
     int kkc;                // power of two >= kk
-    size_t region_a;        // bytes of the counter / merge region
+    size_t region_a;        // bytes of the counter region (multiple of 16)
+    int64_t nq;             // queries of this launch
+    int buf_cap;            // candidate buffer entries: max(kBufCap, 16 * kkc)
     int64_t* out_ids;
     float* out_dists;
     int k_stride;
@@ -124,77 +130,64 @@ struct WarpTop {
     }
 };
 
-// k-way merge of `nl` sorted lists (list j at (ld + j*stride, li + j*stride), each of
-// length kk) into the first kk entries of (od, oi). Called by one full warp; nl <= 32.
-__device__ __forceinline__ void warp_merge(const float* ld, const uint32_t* li, int stride,
-                                           int nl, int kk, float* od, uint32_t* oi, int lane) {
-    int p = 0;
-    for (int o = 0; o < kk; ++o) {
-        float v = __int_as_float(0x7f800000);
-        uint32_t vi = kNoId;
-        if (lane < nl && p < kk) {
-            v = ld[lane * stride + p];
-            vi = li[lane * stride + p];
+// Merge of `nl` sorted lists (list L at ld/li + L*stride, each of length kk) into the kk
+// smallest entries, sorted, at (od, oi). Every entry finds its output position directly:
+// its rank is its index in its own list plus, for every other list, the number of that
+// list's entries ordered before it (binary search; equal (dist, id) pairs, which only
+// padding entries can form, are ordered by list index). The (entry, other list) searches
+// are spread over all threads and summed with shared-memory atomics into `rk` (nl*kk
+// ints); ranks are distinct, so the first kk positions are each written once.
+__device__ __forceinline__ void rank_merge(const float* ld, const uint32_t* li, int stride, int nl,
+                                           int kk, float* od, uint32_t* oi, int* rk, int tid,
+                                           int nthreads) {
+    const int total = nl * kk;
+    for (int e = tid; e < total; e += nthreads) rk[e] = e % kk;
+    __syncthreads();
+    for (int pr = tid; pr < total * nl; pr += nthreads) {
+        const int e = pr / nl, L2 = pr - e * nl;
+        const int L = e / kk, p = e - L * kk;
+        if (L2 == L) continue;
+        const float d = ld[L * stride + p];
+        const uint32_t id = li[L * stride + p];
+        const float* a = ld + L2 * stride;
+        const uint32_t* ai = li + L2 * stride;
+        int lo_i = 0, hi_i = kk;
+        while (lo_i < hi_i) {
+            const int mid = (lo_i + hi_i) >> 1;
+            const float am = a[mid];
+            const uint32_t aim = ai[mid];
+            const bool before = lt_pair(am, aim, d, id) || (am == d && aim == id && L2 < L);
+            if (before) lo_i = mid + 1;
+            else hi_i = mid;
         }
-        float bv = v;
-        uint32_t bi = vi;
-        int bl = lane;
-#pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            const float ov = __shfl_xor_sync(kFull, bv, off);
-            const uint32_t oi2 = __shfl_xor_sync(kFull, bi, off);
-            const int ol = __shfl_xor_sync(kFull, bl, off);
-            if (lt_pair(ov, oi2, bv, bi) || (ov == bv && oi2 == bi && ol < bl)) {
-                bv = ov;
-                bi = oi2;
-                bl = ol;
-            }
-        }
-        if (lane == bl) ++p;
-        if (lane == 0) {
-            od[o] = bv;
-            oi[o] = bi;
+        if (lo_i) atomicAdd(&rk[e], lo_i);
+    }
+    __syncthreads();
+    for (int e = tid; e < total; e += nthreads) {
+        const int r = rk[e];
+        if (r < kk) {
+            const int L = e / kk, p = e - L * kk;
+            od[r] = ld[L * stride + p];
+            oi[r] = li[L * stride + p];
         }
     }
 }
 
-// Same merge, reading list j from CTA j of the cluster (distributed shared memory).
-__device__ __forceinline__ void cluster_merge(cg::cluster_group& cluster, float* ld,
-                                              uint32_t* li, int nl, int kk, float* od,
-                                              uint32_t* oi, int lane) {
-    const float* rd = ld;
-    const uint32_t* ri = li;
-    if (lane < nl) {
-        rd = cluster.map_shared_rank(ld, lane);
-        ri = cluster.map_shared_rank(li, lane);
-    }
-    int p = 0;
-    for (int o = 0; o < kk; ++o) {
-        float v = __int_as_float(0x7f800000);
-        uint32_t vi = kNoId;
-        if (lane < nl && p < kk) {
-            v = rd[p];
-            vi = ri[p];
+// Sort n (dist, id) pairs by rank counting (n small); ties between equal pairs, which only
+// padding entries can form, go by index. Writes the sorted pairs to (od, oi).
+__device__ __forceinline__ void rank_sort(const float* d, const uint32_t* ix, int n, float* od,
+                                          uint32_t* oi, int tid, int nthreads) {
+    for (int e = tid; e < n; e += nthreads) {
+        const float x = d[e];
+        const uint32_t xi = ix[e];
+        int rank = 0;
+        for (int f = 0; f < n; ++f) {
+            const float y = d[f];
+            const uint32_t yi = ix[f];
+            rank += lt_pair(y, yi, x, xi) || (y == x && yi == xi && f < e);
         }
-        float bv = v;
-        uint32_t bi = vi;
-        int bl = lane;
-#pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            const float ov = __shfl_xor_sync(kFull, bv, off);
-            const uint32_t oi2 = __shfl_xor_sync(kFull, bi, off);
-            const int ol = __shfl_xor_sync(kFull, bl, off);
-            if (lt_pair(ov, oi2, bv, bi) || (ov == bv && oi2 == bi && ol < bl)) {
-                bv = ov;
-                bi = oi2;
-                bl = ol;
-            }
-        }
-        if (lane == bl) ++p;
-        if (lane == 0) {
-            od[o] = bv;
-            oi[o] = bi;
-        }
+        od[rank] = x;
+        oi[rank] = xi;
     }
 }
 
@@ -243,288 +236,532 @@ __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, f
     }
 }
 
+// Squared distances of up to CPW*U queued candidates to the query, G lanes per row.
+// Lane-group leaders (gl == 0) end with the full sums; val/cid tell which are real.
+template <int G, bool BF16>
+__device__ __forceinline__ void gather_distances(const unsigned char* base, size_t row_bytes,
+                                                 int nch, const float* qv, const uint32_t* buf,
+                                                 int b0, int m, float (&acc)[2], uint32_t (&cid)[2],
+                                                 bool (&val)[2], int gid, int gl) {
+    constexpr int CPW = 32 / G;
+    constexpr int U = 2;
+    constexpr int CH = 2;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * CPW + gid;
+        val[u] = idx < m;
+        cid[u] = val[u] ? buf[idx] : 0u;
+        acc[u] = 0.f;
+    }
+    for (int f0 = 0; f0 < nch; f0 += G * CH) {
+        uint4 raw[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int ch = 0; ch < CH; ++ch) {
+                const int f = f0 + ch * G + gl;
+                raw[u][ch] = (val[u] && f < nch)
+                                 ? ldg_nc_u4(base + size_t(cid[u]) * row_bytes + size_t(f) * 16)
+                                 : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int ch = 0; ch < CH; ++ch) {
+                const int f = f0 + ch * G + gl;
+                if (f < nch) acc[u] = chunk_dist<BF16>(raw[u][ch], qv, f, acc[u]);
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int off = G / 2; off; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
+    }
+}
+
+// Exclusive scan of v over the block (kRrThreads threads); returns the thread's prefix and
+// the block total. Uses `tmp` (kRrWarps entries of shared memory).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, uint32_t& total,
+                                                    int lane, int warp) {
+    uint32_t incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) tmp[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kRrWarps; ++w) {
+        const uint32_t x = tmp[w];
+        wpre += w < warp ? x : 0u;
+        tot += x;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + incl - v;
+}
+
+constexpr int kCellBatch = 512;    // probed cells staged per walk
+constexpr int kBufCap = 2048;      // candidate ids buffered per re-rank round
+constexpr int kBufFlush = 1024;    // re-rank once this many are buffered (fallback scan)
+constexpr int kListCap = 4096;     // ids that reached a level >= 2 during counting
+constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
+
+// Stage the id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
+// [slab_lo, slab_hi): cbeg[t] = absolute start in the id array, cpre = exclusive prefix
+// of the run lengths (cpre[nb] = total). Block-wide; ends with a barrier.
+__device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
+                                                int cb0, int nb, int slab_lo, int slab_hi,
+                                                unsigned long long* cbeg, uint32_t* cpre,
+                                                uint32_t* s_tmp, int tid, int lane, int warp) {
+    const int Ns = P.Ns, K = P.K;
+    const int sstride = P.n_slabs + 1;
+    uint32_t len = 0;
+    if (tid < nb) {
+        const int g = cb0 + tid;
+        int i = 0;
+        while (g >= s_pre[i + 1]) ++i;
+        const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
+        const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
+        const uint32_t b = __ldg(sp + slab_lo), e = __ldg(sp + slab_hi);
+        cbeg[tid] = (unsigned long long)i * (unsigned long long)P.n + b;
+        len = e - b;
+    }
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(len, s_tmp, total, lane, warp);
+    if (tid < nb) cpre[tid] = ex;
+    if (tid == 0) cpre[nb] = total;
+    __syncthreads();
+    return total;
+}
+
+// k-way merge of `nl` sorted lists (list j at ld/li + j*stride, each of length kk) into the
+// first kk entries of (od, oi), by one full warp: lane j holds the head of list j, and each
+// round moves the smallest (dist, id) head (ties by lane) to the output. nl <= 32.
+__device__ __forceinline__ void warp_merge(const float* ld, const uint32_t* li, int stride,
+                                           int nl, int kk, float* od, uint32_t* oi, int lane) {
+    int p = 0;
+    for (int o = 0; o < kk; ++o) {
+        float v = __int_as_float(0x7f800000);
+        uint32_t vi = kNoId;
+        if (lane < nl && p < kk) {
+            v = ld[lane * stride + p];
+            vi = li[lane * stride + p];
+        }
+        float bv = v;
+        uint32_t bi = vi;
+        int bl = lane;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const float ov = __shfl_xor_sync(kFull, bv, off);
+            const uint32_t oi2 = __shfl_xor_sync(kFull, bi, off);
+            const int ol = __shfl_xor_sync(kFull, bl, off);
+            if (lt_pair(ov, oi2, bv, bi) || (ov == bv && oi2 == bi && ol < bl)) {
+                bv = ov;
+                bi = oi2;
+                bl = ol;
+            }
+        }
+        if (lane == bl) ++p;
+        if (lane == 0) {
+            od[o] = bv;
+            oi[o] = bi;
+        }
+    }
+}
+
 // G lanes per candidate, R registers per lane of top list, BF16 rows or FP32 rows.
+// Persistent: the clusters of the grid take queries blockIdx.y, blockIdx.y + gridDim.y, ...
 template <int G, int R, bool BF16>
 __global__ void __launch_bounds__(kRrThreads, (R <= 4 ? 2 : 1))
 count_select_rerank_kernel(const RerankParams P) {
     constexpr int CPW = 32 / G;   // candidates per warp pass
     constexpr int U = 2;          // passes in flight
-    constexpr int CH = 4;         // 16-byte chunks per lane per row pass
     cg::cluster_group cluster = cg::this_cluster();
     const int cta = int(cluster.block_rank());
     const int ncta = int(cluster.num_blocks());
-    const int64_t q = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
-    float* qv = reinterpret_cast<float*>(smem + P.region_a);
-    uint32_t* queue = reinterpret_cast<uint32_t*>(qv + P.d_pad);
-    uint32_t* ge = queue + kRrWarps * kQueueCap;   // [16]
-    __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
-    __shared__ int s_last;
-
-    const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
-    const int Ns = P.Ns, K = P.K;
-    const int slab_lo = cta * P.slabs_per_cta;
-    const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
-    const int64_t lo = int64_t(slab_lo) << kSlabLog2;
-    const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
-    const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
-
-    // ---- 0. clear counters, stage the query --------------------------------------------
-    for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
-    for (int j = tid; j < P.d_pad; j += kRrThreads)
-        qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
-    if (tid < 16) ge[tid] = 0u;
-    if (tid == 0) {
-        int acc = 0;
-        s_pre[0] = 0;
-        for (int i = 0; i < Ns; ++i) {
-            acc += P.ncells[q * Ns + i];
-            s_pre[i + 1] = acc;
-        }
-    }
-    __syncthreads();
-
-    // ---- 1. count collisions of the probed cells' ids in this CTA's range ---------------
-    const int total_cells = s_pre[Ns];
-    const int sstride = P.n_slabs + 1;
-    for (int t = warp; t < total_cells; t += kRrWarps) {
-        int i = 0;
-        while (t >= s_pre[i + 1]) ++i;
-        const int cell = P.cells[(q * Ns + i) * K + (t - s_pre[i])];
-        const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
-        const uint32_t beg = __ldg(sp + slab_lo), end = __ldg(sp + slab_hi);
-        const uint32_t* idp = P.ids + size_t(i) * P.n;
-        for (uint32_t p = beg + lane; p < end; p += 32) {
-            const uint32_t id = __ldg(idp + p) - uint32_t(lo);
-            atomicAdd(&cnt[id >> 3], 1u << ((id & 7u) << 2));
-        }
-    }
-    __syncthreads();
-
-    // ---- 2. SC levels: ge[j] = #ids of this CTA with SC >= j ---------------------------
-    {
-        uint32_t gel[TACO_MAX_SUBSPACES];
-#pragma unroll
-        for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
-        for (int w = tid; w < words; w += kRrThreads) {
-            const uint32_t x = cnt[w];
-            if (x == 0u) continue;
-            const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
-#pragma unroll
-            for (int j = 1; j <= TACO_MAX_SUBSPACES; ++j) {
-                if (j <= Ns) {
-                    const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
-                    gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) {
-            if (j < Ns) {
-                uint32_t v = gel[j];
-#pragma unroll
-                for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-                if (lane == 0 && v) atomicAdd(&ge[j + 1], v);
-            }
-        }
-    }
-    cluster.sync();
-
-    // ---- 3. Alg. 5 on the cluster-wide collision_num (same result in every CTA) --------
-    if (tid == 0) {
-        long long gs[TACO_MAX_SUBSPACES + 2];
-        for (int j = 0; j <= Ns + 1; ++j) gs[j] = 0;
-        for (int r = 0; r < ncta; ++r) {
-            const uint32_t* rg = cluster.map_shared_rank(ge, r);
-            for (int j = 1; j <= Ns; ++j) gs[j] += rg[j];
-        }
-        gs[0] = P.n;
-        int last = Ns;
-        long long cand = 0;
-        for (int j = Ns; j >= 0; --j) {
-            const long long h = gs[j] - gs[j + 1];
-            cand += h;
-            const bool go = qp.select_rule == TACO_SELECT_LITERAL ? (h <= qp.rerank_target - cand)
-                                                                 : (cand <= qp.rerank_target);
-            if (go) --last;
-            else break;
-        }
-        s_last = last;
-        if (cta == 0) {
-            if (P.dbg_hist)
-                for (int j = 0; j <= Ns; ++j) P.dbg_hist[q * (Ns + 1) + j] = gs[j] - gs[j + 1];
-            if (P.dbg_last) P.dbg_last[q] = last;
-            if (P.dbg_cand) P.dbg_cand[q] = cand;
-        }
-    }
-    __syncthreads();
-    const int last = s_last;
-
-    // ---- 4. gather the candidates of this CTA and keep the warp's best kk ---------------
-    WarpTop<R> top;
-    top.init();
-    const int kk = P.kk;
-    float kth_d = __int_as_float(0x7f800000);
-    uint32_t kth_i = kNoId;
-    uint32_t* wq = queue + warp * kQueueCap;
-    const int gid = lane / G, gl = lane % G;
-    const int nch = P.d_pad / RowChunk<BF16>::kElems;
-    const size_t row_bytes = size_t(P.d_pad) * (BF16 ? 2 : 4);
-    const unsigned char* base = BF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
-                                     : reinterpret_cast<const unsigned char*>(P.data);
-    for (int wb = warp * 32; wb < words; wb += kRrWarps * 32) {
-        const int w = wb + lane;
-        uint32_t m8 = 0;
-        const int64_t id0 = lo + (int64_t(w) << 3);
-        if (w < words) {
-            const uint32_t x = cnt[w];
-            if (last <= 0) {
-                m8 = 0xffu;
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (int((x >> (4 * j)) & 15u) >= last) m8 |= 1u << j;
-            }
-            const int64_t rem = hi - id0;
-            if (rem < 8) m8 &= (1u << rem) - 1u;
-            if (P.dbg_sc) {
-                for (int j = 0; j < 8 && j < rem; ++j)
-                    P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (4 * j)) & 15u);
-            }
-        }
-        const int c = __popc(m8);
-        int incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl += v;
-        }
-        const int tot = __shfl_sync(kFull, incl, 31);
-        int at = incl - c;
-        while (m8) {
-            const int b = __ffs(m8) - 1;
-            m8 &= m8 - 1;
-            wq[at++] = uint32_t(id0 + b);
-        }
-        __syncwarp();
-        for (int b0 = 0; b0 < tot; b0 += CPW * U) {
-            float acc[U];
-            uint32_t cid[U];
-            bool val[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int idx = b0 + u * CPW + gid;
-                val[u] = idx < tot;
-                cid[u] = val[u] ? wq[idx] : 0u;
-                acc[u] = 0.f;
-            }
-            for (int f0 = 0; f0 < nch; f0 += G * CH) {
-                uint4 raw[U][CH];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int ch = 0; ch < CH; ++ch) {
-                        const int f = f0 + ch * G + gl;
-                        raw[u][ch] = (val[u] && f < nch)
-                                         ? ldg_nc_u4(base + size_t(cid[u]) * row_bytes + size_t(f) * 16)
-                                         : make_uint4(0, 0, 0, 0);
-                    }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int ch = 0; ch < CH; ++ch) {
-                        const int f = f0 + ch * G + gl;
-                        if (f < nch) acc[u] = chunk_dist<BF16>(raw[u][ch], qv, f, acc[u]);
-                    }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-#pragma unroll
-                for (int off = G / 2; off; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool better = val[u] && gl == 0 && lt_pair(acc[u], cid[u], kth_d, kth_i);
-                unsigned bal = __ballot_sync(kFull, better);
-                while (bal) {
-                    const int src = __ffs(bal) - 1;
-                    bal &= bal - 1;
-                    const float x = __shfl_sync(kFull, acc[u], src);
-                    const uint32_t xi = __shfl_sync(kFull, cid[u], src);
-                    if (lt_pair(x, xi, kth_d, kth_i)) {
-                        top.insert(x, xi, kk, lane);
-                        top.kth(kk, kth_d, kth_i);
-                    }
-                }
-            }
-        }
-        __syncwarp();
-    }
-    __syncthreads();   // counters are dead from here on: region A becomes the merge area
-
-    // ---- 5. merge: warps -> CTA -> cluster --------------------------------------------
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);                          // counters
+    unsigned char* mp = smem + P.region_a;                                       // merge area
     const int kkc = P.kkc;
-    float* Ld = reinterpret_cast<float*>(smem);
+    float* Ld = reinterpret_cast<float*>(mp);
     uint32_t* Li = reinterpret_cast<uint32_t*>(Ld + kRrWarps * kkc);
     float* CLd = reinterpret_cast<float*>(Li + kRrWarps * kkc);
     uint32_t* CLi = reinterpret_cast<uint32_t*>(CLd + kkc);
     float* GLd = reinterpret_cast<float*>(CLi + kkc);
     uint32_t* GLi = reinterpret_cast<uint32_t*>(GLd + kkc);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = r * 32 + lane;
-        if (e < kk) {
-            Ld[warp * kkc + e] = top.d[r];
-            Li[warp * kkc + e] = top.i[r];
+    float* qv = reinterpret_cast<float*>(GLi + kkc);                             // d_pad
+    uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);                   // buf_cap
+    uint32_t* lst = buf + P.buf_cap;                                             // kListCap
+    unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);  // kCellBatch
+    uint32_t* cpre = reinterpret_cast<uint32_t*>(cbeg + kCellBatch);            // kCellBatch+1
+    uint32_t* ge2 = cpre + kCellBatch + 4;                                       // [2][16]
+    __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
+    __shared__ int s_last;
+    __shared__ uint32_t s_tmp[kRrWarps];
+    __shared__ uint32_t s_wcnt[2][kRrWarps];
+    __shared__ uint32_t s_allge[16 * 16];
+    __shared__ uint32_t s_bufn, s_app;
+
+    const int Ns = P.Ns;
+    const int slab_lo = cta * P.slabs_per_cta;
+    const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
+    const int64_t lo = int64_t(slab_lo) << kSlabLog2;
+    const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
+    const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
+    const int gid = lane / G, gl = lane % G;
+    const int nch = P.d_pad / RowChunk<BF16>::kElems;
+    const size_t row_bytes = size_t(P.d_pad) * (BF16 ? 2 : 4);
+    const unsigned char* rows = BF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
+                                     : reinterpret_cast<const unsigned char*>(P.data);
+    const int kk = P.kk;
+
+    // counters start at zero; every query leaves them at zero again
+    for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
+    if (tid < 32) ge2[tid] = 0u;
+
+    int par = 0;
+    for (int64_t q = blockIdx.y; q < P.nq; q += gridDim.y, par ^= 1) {
+        const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
+        uint32_t* ge = ge2 + 16 * par;
+        __syncthreads();   // the previous query's readers of qv / s_pre / lists are done
+        for (int j = tid; j < P.d_pad; j += kRrThreads)
+            qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
+        if (tid < 16) ge[tid] = 0u;
+        if (tid == 0) {
+            int acc = 0;
+            s_pre[0] = 0;
+            for (int i = 0; i < Ns; ++i) {
+                acc += P.ncells[q * Ns + i];
+                s_pre[i + 1] = acc;
+            }
+            s_app = 0u;
+            s_bufn = 0u;
         }
-    }
-    __syncthreads();
-    if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, CLd, CLi, lane);
-    cluster.sync();
-    if (cta == 0) {
-        if (warp == 0) cluster_merge(cluster, CLd, CLi, ncta, kk, GLd, GLi, lane);
+        __syncthreads();
+        const int total_cells = s_pre[Ns];
+        const int nbatch = (total_cells + kCellBatch - 1) / kCellBatch;
+
+        // ---- 1. count: SC[id] += 1 for every id of every probed cell in this CTA's range.
+        // The nibble's old value v says the id just reached level v + 1. Ids reaching a
+        // level >= 2 are appended to `lst` with that level: every id with SC >= j >= 2 is
+        // there exactly once tagged j, which gives both the level counts and, once Alg. 5
+        // has chosen j, the candidates. First touches (level 1) are counted per lane.
+        {
+            uint32_t c1 = 0;
+            for (int bt = 0; bt < nbatch; ++bt) {
+                const int cb0 = bt * kCellBatch;
+                const int nb = min(kCellBatch, total_cells - cb0);
+                stage_cells(P, q, s_pre, cb0, nb, slab_lo, slab_hi, cbeg, cpre, s_tmp, tid, lane, warp);
+                // warp w takes cells w, w + 16, w + 32, ... eight at a time; lane l reads
+                // element l (+32, ...) of each run
+                for (int c0 = warp; c0 < nb; c0 += kRrWarps * 8) {
+                    unsigned long long rb[8];
+                    uint32_t rl[8];
+                    uint32_t maxl = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = c0 + u * kRrWarps;
+                        rb[u] = c < nb ? cbeg[c] : 0ull;
+                        rl[u] = c < nb ? cpre[c + 1] - cpre[c] : 0u;
+                        maxl = max(maxl, rl[u]);
+                    }
+                    for (uint32_t off = 0; off < maxl; off += 32) {
+                        uint32_t idv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            idv[u] = off + lane < rl[u] ? __ldg(P.ids + rb[u] + off + lane) : 0xffffffffu;
+                        // all counter atomics first (independent), then one list
+                        // reservation per warp for the ids that reached level >= 2
+                        uint32_t ent[8];
+                        uint32_t nmine = 0;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            ent[u] = 0u;
+                            if (idv[u] != 0xffffffffu) {
+                                const uint32_t id = idv[u] - uint32_t(lo);
+                                const uint32_t sh = (id & 7u) << 2;
+                                const uint32_t v = (atomicAdd(&cnt[id >> 3], 1u << sh) >> sh) & 15u;
+                                c1 += v == 0u;
+                                if (v != 0u) {
+                                    ent[u] = id | ((v + 1u) << kLevelShift);
+                                    ++nmine;
+                                }
+                            }
+                        }
+                        uint32_t incl = nmine;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                            if (lane >= o) incl += t;
+                        }
+                        const uint32_t wtot = __shfl_sync(kFull, incl, 31);
+                        if (wtot) {
+                            uint32_t base = 0;
+                            if (lane == 31) base = atomicAdd(&s_app, wtot);
+                            base = __shfl_sync(kFull, base, 31);
+                            uint32_t at = base + incl - nmine;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                if (ent[u]) {
+                                    if (at < uint32_t(kListCap)) lst[at] = ent[u];
+                                    ++at;
+                                }
+                            }
+                        }
+                    }
+                }
+                if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
+            }
+            const uint32_t t1 = __reduce_add_sync(kFull, c1);
+            if (lane == 0 && t1) atomicAdd(&ge[1], t1);
+        }
+        __syncthreads();
+        const bool overflow = s_app > uint32_t(kListCap);
+        if (!overflow) {
+            for (int e = tid; e < int(s_app); e += kRrThreads) atomicAdd(&ge[lst[e] >> kLevelShift], 1u);
+        } else {
+            // the list overflowed: count the levels from the counters themselves
+            uint32_t gel[TACO_MAX_SUBSPACES];
+#pragma unroll
+            for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
+            for (int w = tid; w < words; w += kRrThreads) {
+                const uint32_t x = cnt[w];
+                if (x == 0u) continue;
+                const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
+#pragma unroll
+                for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+                    if (j <= Ns) {
+                        const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
+                        gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+                if (j <= Ns) {
+                    const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
+                    if (lane == 0 && v) atomicAdd(&ge[j], v);
+                }
+            }
+        }
+        cluster.sync();
+
+        // ---- 2. Alg. 5 on the cluster-wide collision_num (same result in every CTA) ----
+        if (tid < ncta * Ns) {
+            const int r = tid / Ns, j = tid - r * Ns + 1;
+            s_allge[r * 16 + j] = cluster.map_shared_rank(ge, r)[j];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long gs[TACO_MAX_SUBSPACES + 2];
+            for (int j = 0; j <= Ns + 1; ++j) gs[j] = 0;
+            for (int r = 0; r < ncta; ++r)
+                for (int j = 1; j <= Ns; ++j) gs[j] += s_allge[r * 16 + j];
+            gs[0] = P.n;
+            int last = Ns;
+            long long cand = 0;
+            for (int j = Ns; j >= 0; --j) {
+                const long long h = gs[j] - gs[j + 1];
+                cand += h;
+                const bool go = qp.select_rule == TACO_SELECT_LITERAL ? (h <= qp.rerank_target - cand)
+                                                                     : (cand <= qp.rerank_target);
+                if (go) --last;
+                else break;
+            }
+            s_last = last;
+            if (cta == 0) {
+                if (P.dbg_hist)
+                    for (int j = 0; j <= Ns; ++j) P.dbg_hist[q * (Ns + 1) + j] = gs[j] - gs[j + 1];
+                if (P.dbg_last) P.dbg_last[q] = last;
+                if (P.dbg_cand) P.dbg_cand[q] = cand;
+            }
+        }
+        __syncthreads();
+        const int last = s_last;
+
+        // ---- 3. candidates of this CTA -> warp top lists --------------------------------
+        WarpTop<R> top;
+        top.init();
+        float kth_d = __int_as_float(0x7f800000);
+        uint32_t kth_i = kNoId;
+        auto rerank_buffer = [&](int m) {
+            for (int b0 = warp * CPW * U; b0 < m; b0 += kRrWarps * CPW * U) {
+                float acc[U];
+                uint32_t cid[U];
+                bool val[U];
+                gather_distances<G, BF16>(rows, row_bytes, nch, qv, buf, b0, m, acc, cid, val, gid, gl);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool better = val[u] && gl == 0 && lt_pair(acc[u], cid[u], kth_d, kth_i);
+                    unsigned bal = __ballot_sync(kFull, better);
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const float x = __shfl_sync(kFull, acc[u], src);
+                        const uint32_t xi = __shfl_sync(kFull, cid[u], src);
+                        if (lt_pair(x, xi, kth_d, kth_i)) {
+                            top.insert(x, xi, kk, lane);
+                            top.kth(kk, kth_d, kth_i);
+                        }
+                    }
+                }
+            }
+        };
+        const uint32_t mine = last >= 1 ? s_allge[cta * 16 + last] : 0u;   // ids with SC >= last
+        if (P.dbg_sc && last >= 1) {
+            for (int w = tid; w < words; w += kRrThreads) {
+                const uint32_t x = cnt[w];
+                if (!x) continue;
+                const int64_t id0 = lo + (int64_t(w) << 3);
+                for (int j = 0; j < 8 && id0 + j < hi; ++j)
+                    if ((x >> (4 * j)) & 15u) P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (4 * j)) & 15u);
+            }
+        }
+        if (last >= 2 && !overflow && mine <= uint32_t(P.buf_cap)) {
+            // the candidates are the list entries tagged `last`
+            for (int e = tid; e < int(s_app); e += kRrThreads) {
+                const uint32_t x = lst[e];
+                if (int(x >> kLevelShift) == last)
+                    buf[atomicAdd(&s_bufn, 1u)] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
+            }
+            // clear the counters for the next query
+            uint4* c4 = reinterpret_cast<uint4*>(cnt);
+            for (int w = tid; w < (words + 3) / 4; w += kRrThreads) c4[w] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            rerank_buffer(int(s_bufn));
+        } else if (last >= 1) {
+            // SC >= 1 (or an overflowing list): scan every counter word in tiles, clearing
+            // it, re-ranking whenever kBufFlush ids are buffered
+            uint32_t bufn = 0;
+            int wpar = 0;
+            const uint32_t add = (0x80u - uint32_t(last)) * 0x01010101u;
+            for (int t0 = 0; t0 < words; t0 += kRrThreads) {
+                const int w = t0 + tid;
+                uint32_t m8 = 0;
+                const int64_t id0 = lo + (int64_t(w) << 3);
+                if (w < words) {
+                    const uint32_t x = cnt[w];
+                    if (x) {
+                        cnt[w] = 0u;
+                        const uint32_t he = ((x & 0x0f0f0f0fu) + add) & 0x80808080u;
+                        const uint32_t ho = (((x >> 4) & 0x0f0f0f0fu) + add) & 0x80808080u;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            m8 |= ((he >> (8 * b + 7)) & 1u) << (2 * b);
+                            m8 |= ((ho >> (8 * b + 7)) & 1u) << (2 * b + 1);
+                        }
+                    }
+                }
+                const uint32_t cnum = __popc(m8);
+                uint32_t incl = cnum;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t v = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                if (lane == 31) s_wcnt[wpar][warp] = incl;
+                __syncthreads();
+                uint32_t wbase = 0, step_total = 0;
+#pragma unroll
+                for (int ww = 0; ww < kRrWarps; ++ww) {
+                    const uint32_t x = s_wcnt[wpar][ww];
+                    wbase += ww < warp ? x : 0u;
+                    step_total += x;
+                }
+                uint32_t at = bufn + wbase + incl - cnum;
+                while (m8) {
+                    const int j = __ffs(m8) - 1;
+                    m8 &= m8 - 1;
+                    buf[at++] = uint32_t(id0 + j);
+                }
+                bufn += step_total;
+                wpar ^= 1;
+                if (bufn >= uint32_t(kBufFlush) || t0 + kRrThreads >= words) {
+                    __syncthreads();
+                    rerank_buffer(int(bufn));
+                    __syncthreads();
+                    bufn = 0;
+                }
+            }
+        } else {
+            // Alg. 5 kept every level: all ids of this CTA's range are candidates.
+            if (P.dbg_sc) {
+                for (int w = tid; w < words; w += kRrThreads) {
+                    const uint32_t x = cnt[w];
+                    for (int j = 0; j < 8 && lo + 8 * w + j < hi; ++j)
+                        P.dbg_sc[q * P.n + lo + 8 * w + j] = uint8_t((x >> (4 * j)) & 15u);
+                }
+            }
+            for (int64_t b = lo; b < hi; b += P.buf_cap) {
+                const int m = int(hi - b < int64_t(P.buf_cap) ? hi - b : int64_t(P.buf_cap));
+                __syncthreads();
+                for (int t = tid; t < m; t += kRrThreads) buf[t] = uint32_t(b + t);
+                __syncthreads();
+                rerank_buffer(m);
+            }
+            __syncthreads();
+            for (int w = tid; w < words; w += kRrThreads) cnt[w] = 0u;
+        }
+
+        // ---- 4. merge: warps -> CTA -> cluster ------------------------------------------
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane;
+            if (e < kk) {
+                Ld[warp * kkc + e] = top.d[r];
+                Li[warp * kkc + e] = top.i[r];
+            }
+        }
+        __syncthreads();
+        if (kk <= 64) {
+            if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, CLd, CLi, lane);
+        } else {
+            rank_merge(Ld, Li, kkc, kRrWarps, kk, CLd, CLi, reinterpret_cast<int*>(buf), tid, kRrThreads);
+        }
+        cluster.sync();
+        if (cta != 0) continue;   // CTA 0 reads the lists before any CTA passes the next
+                                  // query's first cluster barrier, so they stay intact
+        for (int t = tid; t < ncta * kk; t += kRrThreads) {
+            const int r = t / kk, e = t - r * kk;
+            Ld[r * kkc + e] = cluster.map_shared_rank(CLd, r)[e];
+            Li[r * kkc + e] = cluster.map_shared_rank(CLi, r)[e];
+        }
+        __syncthreads();
+        if (kk <= 64) {
+            if (warp == 0) warp_merge(Ld, Li, kkc, ncta, kk, GLd, GLi, lane);
+        } else {
+            rank_merge(Ld, Li, kkc, ncta, kk, GLd, GLi, reinterpret_cast<int*>(buf), tid, kRrThreads);
+        }
         __syncthreads();
         if constexpr (BF16) {
-            // exact FP32 re-rank of the shortlist, then sort it by (dist, id)
+            // exact FP32 re-rank of the shortlist (8 lanes per row, all warps), then sort
+            constexpr int G8 = 8;
             const int nf4 = P.d_pad / 4;
-            for (int e = warp; e < kkc; e += kRrWarps) {
+            const int gid8 = tid / G8, gl8 = tid % G8;
+            for (int eb = 0; eb < kkc; eb += kRrThreads / G8) {   // warp-uniform trip count
+                const int e = eb + gid8;
                 const uint32_t id = e < kk ? GLi[e] : kNoId;
                 float acc = 0.f;
                 if (id != kNoId) {
                     const float4* row = reinterpret_cast<const float4*>(P.data + size_t(id) * P.d_pad);
                     const float4* q4 = reinterpret_cast<const float4*>(qv);
-                    for (int f = lane; f < nf4; f += 32) acc = sq4(__ldg(row + f), q4[f], acc);
+                    for (int f = gl8; f < nf4; f += G8) acc = sq4(__ldg(row + f), q4[f], acc);
                 }
 #pragma unroll
-                for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-                if (lane == 0) {
-                    GLd[e] = id != kNoId ? acc : __int_as_float(0x7f800000);
-                    GLi[e] = id;
+                for (int off = G8 / 2; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+                if (gl8 == 0 && e < kkc) {
+                    Ld[e] = id != kNoId ? acc : __int_as_float(0x7f800000);
+                    Li[e] = id;
                 }
             }
             __syncthreads();
-            for (int k2 = 2; k2 <= kkc; k2 <<= 1) {
-                for (int j = k2 >> 1; j > 0; j >>= 1) {
-                    for (int t = tid; t < kkc; t += kRrThreads) {
-                        const int o = t ^ j;
-                        if (o > t) {
-                            const float a = GLd[t], b = GLd[o];
-                            const uint32_t ia = GLi[t], ib = GLi[o];
-                            const bool asc = (t & k2) == 0;
-                            if (lt_pair(b, ib, a, ia) == asc) {
-                                GLd[t] = b;
-                                GLd[o] = a;
-                                GLi[t] = ib;
-                                GLi[o] = ia;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
+            rank_sort(Ld, Li, kk, GLd, GLi, tid, kRrThreads);
+            __syncthreads();
         }
         for (int t = tid; t < P.k_stride; t += kRrThreads) {
             const bool ok = t < qp.k && t < kk && GLi[t] != kNoId;
@@ -532,22 +769,46 @@ count_select_rerank_kernel(const RerankParams P) {
             P.out_dists[q * P.k_stride + t] = ok ? sqrtf(GLd[t]) : __int_as_float(0x7f800000);
         }
     }
-    cluster.sync();   // keep every CTA's shared memory alive until CTA 0 has read it
+    cluster.sync();   // no CTA leaves while CTA 0 may still read its list
 }
 
 template <int G, int R, bool BF16>
 cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size_t smem,
                             cudaStream_t st) {
     auto kern = count_select_rerank_kernel<G, R, BF16>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) return e;
-    if (cluster > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    // persistent grid: as many clusters as can be resident at once (cached per shape)
+    static thread_local size_t cached_smem = 0;
+    static thread_local int cached_cluster = 0, cached_active = 0;
+    cudaError_t e;
+    if (cached_smem != smem || cached_cluster != cluster) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
+        if (cluster > 8) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        cudaLaunchConfig_t occ = {};
+        occ.gridDim = dim3(unsigned(cluster), 1, 1);
+        occ.blockDim = dim3(kRrThreads, 1, 1);
+        occ.dynamicSmemBytes = smem;
+        cudaLaunchAttribute oa[1];
+        oa[0].id = cudaLaunchAttributeClusterDimension;
+        oa[0].val.clusterDim.x = unsigned(cluster);
+        oa[0].val.clusterDim.y = 1;
+        oa[0].val.clusterDim.z = 1;
+        occ.attrs = oa;
+        occ.numAttrs = 1;
+        int active = 0;
+        e = cudaOccupancyMaxActiveClusters(&active, kern, &occ);
+        if (e != cudaSuccess) return e;
+        if (active < 1) return cudaErrorInvalidConfiguration;
+        cached_smem = smem;
+        cached_cluster = cluster;
+        cached_active = active;
     }
+    const int64_t gy = nq < cached_active ? nq : cached_active;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(cluster), unsigned(nq), 1);
+    cfg.gridDim = dim3(unsigned(cluster), unsigned(gy), 1);
     cfg.blockDim = dim3(kRrThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;

@@ -245,17 +245,47 @@ int configure_search(taco_index* ix) {
 }
 
 static int pick_g(int nchunks) {
-    // lanes per row so that each lane issues about 4 sixteen-byte loads per row
+    // lanes per row so that each lane issues about 2 sixteen-byte loads per row
     int g = 4;
-    while (g < 32 && g * 4 < nchunks) g <<= 1;
+    while (g < 32 && g * 2 < nchunks) g <<= 1;
     return g;
 }
 
+static cudaEvent_t prof_event(Profiler& pr) {
+    if (pr.used == pr.pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pr.pool.push_back(e);
+    }
+    return pr.pool[pr.used++];
+}
+
+int prof_begin(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t* b, cudaEvent_t* e) {
+    (void)slot;
+    *b = *e = nullptr;
+    if (!ix->prof.enabled) return TACO_OK;
+    *b = prof_event(ix->prof);
+    *e = prof_event(ix->prof);
+    if (!*b || !*e) return fail(TACO_ECUDA, "cudaEventCreate failed");
+    TACO_CUDA(cudaEventRecord(*b, st));
+    return TACO_OK;
+}
+
+int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent_t e) {
+    if (!b) return TACO_OK;
+    TACO_CUDA(cudaEventRecord(e, st));
+    ix->prof.pending.push_back({slot, {b, e}});
+    return TACO_OK;
+}
+
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
-    const taco_index* ix = L.ix;
+    taco_index* ix = const_cast<taco_index*>(L.ix);
+    cudaEvent_t pb, pe;
     const int K = ix->K;
     // 1. transform (Alg. 6 step 1)
+    if (int rc = prof_begin(ix, 0, st, &pb, &pe)) return rc;
     TACO_CUDA(launch_project(L.queries, L.nq, ix->d, ix->d, ix->d_obar, ix->d_B, ix->Dp, L.qt, st));
+    if (int rc = prof_end(ix, 0, st, pb, pe)) return rc;
     if (L.dbg.query_t)
         TACO_CUDA(cudaMemcpyAsync(L.dbg.query_t, L.qt, size_t(L.nq) * ix->Dp * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
@@ -270,10 +300,12 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             attr_set = true;
         }
         dim3 grid(unsigned(ix->Ns), unsigned(L.nq));
+        if (int rc = prof_begin(ix, 1, st, &pb, &pe)) return rc;
         probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
             L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
             L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed);
         TACO_CUDA(cudaGetLastError());
+        if (int rc = prof_end(ix, 1, st, pb, pe)) return rc;
         if (L.dbg.retrieved_num)
             TACO_CUDA(cudaMemcpyAsync(L.dbg.retrieved_num, L.retrieved,
                                       size_t(L.nq) * ix->Ns * sizeof(int64_t),
@@ -302,9 +334,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.counter_words = ix->slabs_per_cta * kSlabWords;
         P.kk = L.kk_max;
         P.kkc = next_pow2(L.kk_max);
-        const size_t merge_bytes = (size_t(2) * kRrWarps * P.kkc + 4 * size_t(P.kkc)) * 4;
-        P.region_a = std::max(size_t(P.counter_words) * 4, merge_bytes);
-        P.region_a = (P.region_a + 15) & ~size_t(15);
+        P.nq = L.nq;
+        P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
         P.out_ids = L.out_ids;
         P.out_dists = L.out_dists;
         P.k_stride = L.k_stride;
@@ -312,10 +343,16 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.dbg_hist = L.dbg.collision_num;
         P.dbg_last = L.dbg.last_collision;
         P.dbg_cand = L.dbg.candidate_num;
-        const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(kRrWarps) * kQueueCap * 4 + 64;
+        if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
+        // counters | merge lists | query | candidate buffer | staged runs | level counts
+        const size_t merge_bytes = (size_t(2) * kRrWarps * P.kkc + 4 * size_t(P.kkc)) * 4;
+        P.buf_cap = std::max(kBufCap, kRrWarps * P.kkc);
+        const size_t smem = P.region_a + merge_bytes + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
+                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
         cudaError_t e;
+        if (int rc = prof_begin(ix, 2, st, &pb, &pe)) return rc;
         if (!bf16) {
             e = R == 1 ? launch_rerank_b0_r1(G, P, ix->cluster, L.nq, smem, st)
                 : R == 4 ? launch_rerank_b0_r4(G, P, ix->cluster, L.nq, smem, st)
@@ -326,6 +363,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                          : launch_rerank_b1_r16(G, P, ix->cluster, L.nq, smem, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "count_select_rerank launch", __FILE__, __LINE__);
+        if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
     }
     return TACO_OK;
 }

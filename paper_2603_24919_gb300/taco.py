@@ -55,6 +55,14 @@ class DebugOut(C.Structure):
                 ("last_collision", C.c_void_p), ("candidate_num", C.c_void_p)]
 
 
+NUM_KERNELS = 4
+KERNEL_NAMES = ("project", "probe_cells", "count_select_rerank", "reserved")
+
+
+class KernelTimes(C.Structure):
+    _fields_ = [("launches", C.c_int64 * NUM_KERNELS), ("ms", C.c_double * NUM_KERNELS)]
+
+
 # name -> (restype, argtypes); the exported symbols of include/taco.h
 SIGNATURES = {
     "taco_build_index": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(BuildParams),
@@ -72,6 +80,8 @@ SIGNATURES = {
                                     C.c_void_p, C.c_void_p]),
     "taco_save_index": (C.c_int, [C.c_void_p, C.c_char_p]),
     "taco_load_index": (C.c_int, [C.c_char_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "taco_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "taco_profile_read": (C.c_int, [C.c_void_p, C.POINTER(KernelTimes), C.c_int32]),
     "taco_free_index": (None, [C.c_void_p]),
     "taco_last_error": (C.c_char_p, []),
 }
@@ -235,6 +245,16 @@ class TacoIndex:
             self._h, *[out[k].ctypes.data for k in ("o_bar", "B", "eigvals", "alloc",
                                                      "centroids", "codes")]))
         return out
+
+    # ---- per-kernel timing -----------------------------------------------------------
+    def profile(self, enable=True):
+        _check(load_library().taco_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self, reset=True):
+        kt = KernelTimes()
+        _check(load_library().taco_profile_read(self._h, C.byref(kt), int(bool(reset))))
+        return {name: {"launches": int(kt.launches[j]), "ms": float(kt.ms[j])}
+                for j, name in enumerate(KERNEL_NAMES)}
 
     # ---- search --------------------------------------------------------------------
     def _prepare(self, queries, k, budget, rerank_target, precision, select_rule,

@@ -67,16 +67,20 @@ def test_tiny_parity_all_intermediates(tiny):
 
 
 @pytest.mark.parametrize("rule", ["literal", "prose"])
-@pytest.mark.parametrize("alpha,beta", [(0.01, 0.002), (0.05, 0.01), (0.1, 0.05)])
+@pytest.mark.parametrize("alpha,beta", [(0.01, 0.002), (0.05, 0.01), (0.1, 0.05), (0.5, 0.4)])
 def test_tiny_parity_budget_grid(tiny, rule, alpha, beta):
     w, data, queries, oix, ix = tiny
     b, t = budget_from_alpha(alpha, oix.n), target_from_beta(beta, oix.n)
-    gpu = _run(ix, oix, data, queries[:40], 10, b, t, rule=rule, want_sc=False)
+    gpu = _run(ix, oix, data, queries[:40], 10, b, t, rule=rule)
     rep = ParityReport()
+    big = 0
     for j, q in enumerate(queries[:40]):
-        compare_query(rep, O.search_one(oix, data, q, 10, b, t, rule), gpu, j, 10, oix.n,
-                      check_sc=False)
+        tr = O.search_one(oix, data, q, 10, b, t, rule)
+        big += tr.n_candidates > 4096
+        compare_query(rep, tr, gpu, j, 10, oix.n)
     assert rep.excluded_queries <= 10, rep
+    if alpha == 0.5:
+        assert big > 0   # exercises the path for more candidates than one buffer holds
 
 
 @pytest.mark.parametrize("k", [1, 33, 100, 300])
