@@ -144,6 +144,27 @@ int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
                       const taco_query_params* per_query, const taco_query_params* defaults,
                       int32_t k_stride, int64_t* out_ids, float* out_dists, void* stream);
 
+/*
+ * taco_search_batch_noalloc -- taco_search_batch for callers that may not allocate device
+ * memory (a process whose device memory is owned by its own pool or framework, or a
+ * request path where a cudaMalloc, which can synchronise the device, is not allowed).
+ * The paper has no counterpart: this is a deployment variant of the same Alg. 6 kernels.
+ *   queries    device, [nq][d] float32.     out_ids / out_dists  device, [nq][k_stride].
+ *   params     host pointer, one struct for the whole batch (no per-query parameters).
+ * Scratch lives in a fixed 64 MiB array in device memory that every GPU which loads the
+ * library holds until the process exits; the call itself calls no allocating routine.
+ * Every scratch byte read by a call is written earlier in the same call, so nothing needs
+ * clearing between calls. Limits: nq <= 16384 and the batch's scratch (about
+ * 4*N_s*s + 2*N_s*K + 12*N_s bytes per query) must fit the array, else TACO_ECAPACITY.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the array, so calls
+ * that overlap on the GPU (other streams, other threads) race: serialise them.
+ * Returns TACO_EINVAL while profiling (taco_profile_enable) is on for the index.
+ */
+int taco_search_batch_noalloc(const taco_index* index, const float* queries, int64_t nq,
+                              const taco_query_params* params, int32_t k_stride,
+                              int64_t* out_ids, float* out_dists, void* stream);
+
 /* taco_search_debug -- taco_search_batch that also writes the intermediate results
  * selected in *debug (device pointers). Test aid; same errors as taco_search_batch. */
 int taco_search_debug(const taco_index* index, const float* queries, int64_t nq,

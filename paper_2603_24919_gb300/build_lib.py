@@ -38,6 +38,7 @@ def _units():
         ("taco_build_kernels.o", "taco_build_kernels.cu", []),
         ("taco_search.o", "taco_search.cu", []),
         ("taco_api.o", "taco_api.cu", []),
+        ("taco_noalloc.o", "taco_noalloc.cu", []),
     ]
     for bf16 in (0, 1):
         for r in (1, 4, 16):

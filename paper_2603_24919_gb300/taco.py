@@ -72,6 +72,9 @@ SIGNATURES = {
     "taco_search_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                     C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "taco_search_batch_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
+                                            C.POINTER(QueryParams), C.c_int32, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]),
     "taco_search_debug": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                     C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
                                     C.POINTER(DebugOut), C.c_void_p]),
@@ -295,6 +298,16 @@ class TacoIndex:
         _check(load_library().taco_search_batch(
             self._h, _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
             C.byref(defaults), k_stride, _ptr(out_ids), _ptr(out_dists), _stream_handle(stream)))
+        return out_ids, out_dists
+
+    def search_noalloc(self, queries, out_ids, out_dists, k, budget, rerank_target,
+                       precision="fp32", select_rule="literal", shortlist_mult=4, stream=None):
+        """taco_search_batch_noalloc: CUDA queries and caller-owned CUDA outputs; the
+        library allocates nothing (its scratch is a fixed device array)."""
+        p = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult)
+        _check(load_library().taco_search_batch_noalloc(
+            self._h, _ptr(queries), int(queries.shape[0]), C.byref(p), int(out_ids.shape[1]),
+            _ptr(out_ids), _ptr(out_dists), _stream_handle(stream)))
         return out_ids, out_dists
 
     def search_debug(self, queries, k, budget, rerank_target, precision="fp32",
