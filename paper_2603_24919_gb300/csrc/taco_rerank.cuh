@@ -208,11 +208,29 @@ struct RowChunk {
     static constexpr int kElems = BF16 ? 8 : 4;
 };
 
-__device__ __forceinline__ uint4 ldg_nc_u4(const void* p) {
+// L2 eviction policies: candidate rows are read once per query and streamed (evict
+// first); the cell id lists and slab tables are re-read by every query and kept (evict
+// last), so the row stream does not push them out of L2.
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ldg_stream_u4(const void* p, uint64_t pol) {
     uint4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ldg_keep_u32(const uint32_t* p, uint64_t pol) {
+    uint32_t r;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
     return r;
 }
 
@@ -242,7 +260,7 @@ template <int G, bool BF16>
 __device__ __forceinline__ void gather_distances(const unsigned char* base, size_t row_bytes,
                                                  int nch, const float* qv, const uint32_t* buf,
                                                  int b0, int m, float (&acc)[2], uint32_t (&cid)[2],
-                                                 bool (&val)[2], int gid, int gl) {
+                                                 bool (&val)[2], int gid, int gl, uint64_t pol) {
     constexpr int CPW = 32 / G;
     constexpr int U = 2;
     constexpr int CH = 2;
@@ -261,7 +279,7 @@ __device__ __forceinline__ void gather_distances(const unsigned char* base, size
             for (int ch = 0; ch < CH; ++ch) {
                 const int f = f0 + ch * G + gl;
                 raw[u][ch] = (val[u] && f < nch)
-                                 ? ldg_nc_u4(base + size_t(cid[u]) * row_bytes + size_t(f) * 16)
+                                 ? ldg_stream_u4(base + size_t(cid[u]) * row_bytes + size_t(f) * 16, pol)
                                  : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
@@ -304,8 +322,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, u
 }
 
 constexpr int kCellBatch = 512;    // probed cells staged per walk
-constexpr int kBufCap = 2048;      // candidate ids buffered per re-rank round
-constexpr int kBufFlush = 1024;    // re-rank once this many are buffered (fallback scan)
+constexpr int kBufCap = 4096;      // candidate ids buffered per re-rank round (>= 8 * kRrThreads)
 constexpr int kListCap = 4096;     // ids that reached a level >= 2 during counting
 constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
 
@@ -315,7 +332,8 @@ constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range |
 __device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
                                                 int cb0, int nb, int slab_lo, int slab_hi,
                                                 unsigned long long* cbeg, uint32_t* cpre,
-                                                uint32_t* s_tmp, int tid, int lane, int warp) {
+                                                uint32_t* s_tmp, int tid, int lane, int warp,
+                                                uint64_t keep) {
     const int Ns = P.Ns, K = P.K;
     const int sstride = P.n_slabs + 1;
     uint32_t len = 0;
@@ -325,7 +343,7 @@ __device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q
         while (g >= s_pre[i + 1]) ++i;
         const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
         const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
-        const uint32_t b = __ldg(sp + slab_lo), e = __ldg(sp + slab_hi);
+        const uint32_t b = ldg_keep_u32(sp + slab_lo, keep), e = ldg_keep_u32(sp + slab_hi, keep);
         cbeg[tid] = (unsigned long long)i * (unsigned long long)P.n + b;
         len = e - b;
     }
@@ -400,6 +418,8 @@ count_select_rerank_kernel(const RerankParams P) {
     unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);  // kCellBatch
     uint32_t* cpre = reinterpret_cast<uint32_t*>(cbeg + kCellBatch);            // kCellBatch+1
     uint32_t* ge2 = cpre + kCellBatch + 4;                                       // [2][16]
+    float* RLd = reinterpret_cast<float*>(ge2 + 32);                             // [16][kkc]
+    uint32_t* RLi = reinterpret_cast<uint32_t*>(RLd + 16 * kkc);                 // [16][kkc]
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ int s_last;
     __shared__ uint32_t s_tmp[kRrWarps];
@@ -419,6 +439,7 @@ count_select_rerank_kernel(const RerankParams P) {
     const unsigned char* rows = BF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
                                      : reinterpret_cast<const unsigned char*>(P.data);
     const int kk = P.kk;
+    const uint64_t pol_keep = l2_policy_keep(), pol_stream = l2_policy_stream();
 
     // counters start at zero; every query leaves them at zero again
     for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
@@ -456,7 +477,8 @@ count_select_rerank_kernel(const RerankParams P) {
             for (int bt = 0; bt < nbatch; ++bt) {
                 const int cb0 = bt * kCellBatch;
                 const int nb = min(kCellBatch, total_cells - cb0);
-                stage_cells(P, q, s_pre, cb0, nb, slab_lo, slab_hi, cbeg, cpre, s_tmp, tid, lane, warp);
+                stage_cells(P, q, s_pre, cb0, nb, slab_lo, slab_hi, cbeg, cpre, s_tmp, tid, lane, warp,
+                            pol_keep);
                 // warp w takes cells w, w + 16, w + 32, ... eight at a time; lane l reads
                 // element l (+32, ...) of each run
                 for (int c0 = warp; c0 < nb; c0 += kRrWarps * 8) {
@@ -474,7 +496,8 @@ count_select_rerank_kernel(const RerankParams P) {
                         uint32_t idv[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u)
-                            idv[u] = off + lane < rl[u] ? __ldg(P.ids + rb[u] + off + lane) : 0xffffffffu;
+                            idv[u] = off + lane < rl[u] ? ldg_keep_u32(P.ids + rb[u] + off + lane, pol_keep)
+                                                        : 0xffffffffu;
                         // all counter atomics first (independent), then one list
                         // reservation per warp for the ids that reached level >= 2
                         uint32_t ent[8];
@@ -549,14 +572,15 @@ count_select_rerank_kernel(const RerankParams P) {
                 }
             }
         }
+        // push this CTA's level counts into row `cta` of every CTA's table
+        __syncthreads();
+        if (tid < ncta * Ns) {
+            const int r = tid / Ns, j = tid - r * Ns + 1;
+            cluster.map_shared_rank(s_allge, r)[cta * 16 + j] = ge[j];
+        }
         cluster.sync();
 
         // ---- 2. Alg. 5 on the cluster-wide collision_num (same result in every CTA) ----
-        if (tid < ncta * Ns) {
-            const int r = tid / Ns, j = tid - r * Ns + 1;
-            s_allge[r * 16 + j] = cluster.map_shared_rank(ge, r)[j];
-        }
-        __syncthreads();
         if (tid == 0) {
             long long gs[TACO_MAX_SUBSPACES + 2];
             for (int j = 0; j <= Ns + 1; ++j) gs[j] = 0;
@@ -594,7 +618,8 @@ count_select_rerank_kernel(const RerankParams P) {
                 float acc[U];
                 uint32_t cid[U];
                 bool val[U];
-                gather_distances<G, BF16>(rows, row_bytes, nch, qv, buf, b0, m, acc, cid, val, gid, gl);
+                gather_distances<G, BF16>(rows, row_bytes, nch, qv, buf, b0, m, acc, cid, val, gid, gl,
+                                          pol_stream);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const bool better = val[u] && gl == 0 && lt_pair(acc[u], cid[u], kth_d, kth_i);
@@ -621,6 +646,7 @@ count_select_rerank_kernel(const RerankParams P) {
                 for (int j = 0; j < 8 && id0 + j < hi; ++j)
                     if ((x >> (4 * j)) & 15u) P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (4 * j)) & 15u);
             }
+            __syncthreads();   // every counter is read before any is cleared below
         }
         if (last >= 2 && !overflow && mine <= uint32_t(P.buf_cap)) {
             // the candidates are the list entries tagged `last`
@@ -635,8 +661,9 @@ count_select_rerank_kernel(const RerankParams P) {
             __syncthreads();
             rerank_buffer(int(s_bufn));
         } else if (last >= 1) {
-            // SC >= 1 (or an overflowing list): scan every counter word in tiles, clearing
-            // it, re-ranking whenever kBufFlush ids are buffered
+            // SC >= 1 (or an overflowing list): scan every counter word in tiles of
+            // kRrThreads words (at most 8 * kRrThreads ids each), clearing it; the buffer is
+            // re-ranked and emptied before a tile that would not fit
             uint32_t bufn = 0;
             int wpar = 0;
             const uint32_t add = (0x80u - uint32_t(last)) * 0x01010101u;
@@ -673,6 +700,11 @@ count_select_rerank_kernel(const RerankParams P) {
                     wbase += ww < warp ? x : 0u;
                     step_total += x;
                 }
+                if (bufn + step_total > uint32_t(P.buf_cap)) {
+                    rerank_buffer(int(bufn));   // entries were written before the barrier above
+                    __syncthreads();
+                    bufn = 0;
+                }
                 uint32_t at = bufn + wbase + incl - cnum;
                 while (m8) {
                     const int j = __ffs(m8) - 1;
@@ -681,13 +713,9 @@ count_select_rerank_kernel(const RerankParams P) {
                 }
                 bufn += step_total;
                 wpar ^= 1;
-                if (bufn >= uint32_t(kBufFlush) || t0 + kRrThreads >= words) {
-                    __syncthreads();
-                    rerank_buffer(int(bufn));
-                    __syncthreads();
-                    bufn = 0;
-                }
             }
+            __syncthreads();
+            rerank_buffer(int(bufn));
         } else {
             // Alg. 5 kept every level: all ids of this CTA's range are candidates.
             if (P.dbg_sc) {
@@ -718,24 +746,23 @@ count_select_rerank_kernel(const RerankParams P) {
             }
         }
         __syncthreads();
-        if (kk <= 64) {
-            if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, CLd, CLi, lane);
-        } else {
-            rank_merge(Ld, Li, kkc, kRrWarps, kk, CLd, CLi, reinterpret_cast<int*>(buf), tid, kRrThreads);
+        // the CTA's merged list goes straight into row `cta` of CTA 0's receive area
+        {
+            float* rd = cluster.map_shared_rank(RLd, 0) + cta * kkc;
+            uint32_t* ri = cluster.map_shared_rank(RLi, 0) + cta * kkc;
+            if (kk <= 64) {
+                if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, rd, ri, lane);
+            } else {
+                rank_merge(Ld, Li, kkc, kRrWarps, kk, rd, ri, reinterpret_cast<int*>(buf), tid, kRrThreads);
+            }
         }
         cluster.sync();
-        if (cta != 0) continue;   // CTA 0 reads the lists before any CTA passes the next
-                                  // query's first cluster barrier, so they stay intact
-        for (int t = tid; t < ncta * kk; t += kRrThreads) {
-            const int r = t / kk, e = t - r * kk;
-            Ld[r * kkc + e] = cluster.map_shared_rank(CLd, r)[e];
-            Li[r * kkc + e] = cluster.map_shared_rank(CLi, r)[e];
-        }
-        __syncthreads();
+        if (cta != 0) continue;   // CTA 0's receive area is rewritten only after every CTA
+                                  // passes the next query's first cluster barrier
         if (kk <= 64) {
-            if (warp == 0) warp_merge(Ld, Li, kkc, ncta, kk, GLd, GLi, lane);
+            if (warp == 0) warp_merge(RLd, RLi, kkc, ncta, kk, GLd, GLi, lane);
         } else {
-            rank_merge(Ld, Li, kkc, ncta, kk, GLd, GLi, reinterpret_cast<int*>(buf), tid, kRrThreads);
+            rank_merge(RLd, RLi, kkc, ncta, kk, GLd, GLi, reinterpret_cast<int*>(buf), tid, kRrThreads);
         }
         __syncthreads();
         if constexpr (BF16) {
@@ -750,7 +777,12 @@ count_select_rerank_kernel(const RerankParams P) {
                 if (id != kNoId) {
                     const float4* row = reinterpret_cast<const float4*>(P.data + size_t(id) * P.d_pad);
                     const float4* q4 = reinterpret_cast<const float4*>(qv);
-                    for (int f = gl8; f < nf4; f += G8) acc = sq4(__ldg(row + f), q4[f], acc);
+                    for (int f = gl8; f < nf4; f += G8) {
+                        const uint4 r4 = ldg_stream_u4(row + f, pol_stream);
+                        acc = sq4(make_float4(__uint_as_float(r4.x), __uint_as_float(r4.y),
+                                              __uint_as_float(r4.z), __uint_as_float(r4.w)),
+                                  q4[f], acc);
+                    }
                 }
 #pragma unroll
                 for (int off = G8 / 2; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);

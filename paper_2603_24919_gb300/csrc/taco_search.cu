@@ -348,7 +348,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         const size_t merge_bytes = (size_t(2) * kRrWarps * P.kkc + 4 * size_t(P.kkc)) * 4;
         P.buf_cap = std::max(kBufCap, kRrWarps * P.kkc);
         const size_t smem = P.region_a + merge_bytes + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
-                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
+                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4 +
+                            size_t(16) * P.kkc * 8;
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
         cudaError_t e;
