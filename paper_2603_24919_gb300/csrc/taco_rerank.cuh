@@ -324,6 +324,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, u
 constexpr int kCellBatch = 512;    // probed cells staged per walk
 constexpr int kBufCap = 4096;      // candidate ids buffered per re-rank round (>= 8 * kRrThreads)
 constexpr int kListCap = 4096;     // ids that reached a level >= 2 during counting
+constexpr int kSegCap = kListCap / kRrWarps;   // per-warp segment of the list
+constexpr int kWalkUnroll = 16;    // id loads in flight per lane while counting
 constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
 
 // Stage the id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
@@ -353,6 +355,17 @@ __device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q
     if (tid == 0) cpre[nb] = total;
     __syncthreads();
     return total;
+}
+
+// Cell whose run holds element `key` of the concatenation (largest c with cpre[c] <= key).
+__device__ __forceinline__ int find_cell(const uint32_t* cpre, int nb, uint32_t key) {
+    int lo_c = 0, hi_c = nb - 1;
+    while (lo_c < hi_c) {
+        const int mid = (lo_c + hi_c + 1) >> 1;
+        if (cpre[mid] <= key) lo_c = mid;
+        else hi_c = mid - 1;
+    }
+    return lo_c;
 }
 
 // k-way merge of `nl` sorted lists (list j at ld/li + j*stride, each of length kk) into the
@@ -426,6 +439,7 @@ count_select_rerank_kernel(const RerankParams P) {
     __shared__ uint32_t s_wcnt[2][kRrWarps];
     __shared__ uint32_t s_allge[16 * 16];
     __shared__ uint32_t s_bufn, s_app;
+    __shared__ uint32_t s_seg[kRrWarps];
 
     const int Ns = P.Ns;
     const int slab_lo = cta * P.slabs_per_cta;
@@ -474,79 +488,68 @@ count_select_rerank_kernel(const RerankParams P) {
         // has chosen j, the candidates. First touches (level 1) are counted per lane.
         {
             uint32_t c1 = 0;
+            uint32_t wapp = 0;                       // entries this warp appended
+            uint32_t* wseg = lst + warp * kSegCap;   // this warp's list segment
             for (int bt = 0; bt < nbatch; ++bt) {
                 const int cb0 = bt * kCellBatch;
                 const int nb = min(kCellBatch, total_cells - cb0);
-                stage_cells(P, q, s_pre, cb0, nb, slab_lo, slab_hi, cbeg, cpre, s_tmp, tid, lane, warp,
-                            pol_keep);
-                // warp w takes cells w, w + 16, w + 32, ... eight at a time; lane l reads
-                // element l (+32, ...) of each run
-                for (int c0 = warp; c0 < nb; c0 += kRrWarps * 8) {
-                    unsigned long long rb[8];
-                    uint32_t rl[8];
-                    uint32_t maxl = 0;
+                const uint32_t total = stage_cells(P, q, s_pre, cb0, nb, slab_lo, slab_hi, cbeg, cpre,
+                                                   s_tmp, tid, lane, warp, pol_keep);
+                // warp w walks a contiguous share [e0, e1) of the concatenated runs; lane l
+                // takes elements e0 + l + 32 u, 16 per round, so all loads of a round are
+                // in flight together; the lane's cell pointer only moves forward
+                const uint32_t chunk = ((total + kRrWarps - 1) / kRrWarps + 31) & ~31u;
+                const uint32_t e0 = uint32_t(warp) * chunk;
+                const uint32_t e1 = min(total, e0 + chunk);
+                int c = e0 < e1 ? find_cell(cpre, nb, e0 + lane < e1 ? e0 + lane : e1 - 1) : 0;
+                for (uint32_t e = e0; e < e1; e += 32u * kWalkUnroll) {   // warp-uniform
+                    uint32_t idv[kWalkUnroll];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int c = c0 + u * kRrWarps;
-                        rb[u] = c < nb ? cbeg[c] : 0ull;
-                        rl[u] = c < nb ? cpre[c + 1] - cpre[c] : 0u;
-                        maxl = max(maxl, rl[u]);
+                    for (int u = 0; u < kWalkUnroll; ++u) {
+                        const uint32_t eu = e + lane + 32u * u;
+                        idv[u] = 0xffffffffu;
+                        if (eu < e1) {
+                            while (cpre[c + 1] <= eu) ++c;
+                            idv[u] = ldg_keep_u32(P.ids + cbeg[c] + (eu - cpre[c]), pol_keep);
+                        }
                     }
-                    for (uint32_t off = 0; off < maxl; off += 32) {
-                        uint32_t idv[8];
+                    // all counter atomics first (independent), then the ids that reached
+                    // level >= 2 go to this warp's list segment (offsets by ballot)
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            idv[u] = off + lane < rl[u] ? ldg_keep_u32(P.ids + rb[u] + off + lane, pol_keep)
-                                                        : 0xffffffffu;
-                        // all counter atomics first (independent), then one list
-                        // reservation per warp for the ids that reached level >= 2
-                        uint32_t ent[8];
-                        uint32_t nmine = 0;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            ent[u] = 0u;
-                            if (idv[u] != 0xffffffffu) {
-                                const uint32_t id = idv[u] - uint32_t(lo);
-                                const uint32_t sh = (id & 7u) << 2;
-                                const uint32_t v = (atomicAdd(&cnt[id >> 3], 1u << sh) >> sh) & 15u;
-                                c1 += v == 0u;
-                                if (v != 0u) {
-                                    ent[u] = id | ((v + 1u) << kLevelShift);
-                                    ++nmine;
-                                }
-                            }
+                    for (int u = 0; u < kWalkUnroll; ++u) {
+                        if (idv[u] != 0xffffffffu) {
+                            const uint32_t id = idv[u] - uint32_t(lo);
+                            const uint32_t sh = (id & 7u) << 2;
+                            const uint32_t v = (atomicAdd(&cnt[id >> 3], 1u << sh) >> sh) & 15u;
+                            c1 += v == 0u;
+                            idv[u] = v != 0u ? (id | ((v + 1u) << kLevelShift)) : 0u;
+                        } else {
+                            idv[u] = 0u;
                         }
-                        uint32_t incl = nmine;
+                    }
 #pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                            if (lane >= o) incl += t;
-                        }
-                        const uint32_t wtot = __shfl_sync(kFull, incl, 31);
-                        if (wtot) {
-                            uint32_t base = 0;
-                            if (lane == 31) base = atomicAdd(&s_app, wtot);
-                            base = __shfl_sync(kFull, base, 31);
-                            uint32_t at = base + incl - nmine;
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                if (ent[u]) {
-                                    if (at < uint32_t(kListCap)) lst[at] = ent[u];
-                                    ++at;
-                                }
-                            }
-                        }
+                    for (int u = 0; u < kWalkUnroll; ++u) {
+                        const unsigned bal = __ballot_sync(kFull, idv[u] != 0u);
+                        const uint32_t at = wapp + __popc(bal & ((1u << lane) - 1u));
+                        if (idv[u] && at < uint32_t(kSegCap)) wseg[at] = idv[u];
+                        wapp += __popc(bal);
                     }
                 }
                 if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
             }
             const uint32_t t1 = __reduce_add_sync(kFull, c1);
-            if (lane == 0 && t1) atomicAdd(&ge[1], t1);
+            if (lane == 0) {
+                if (t1) atomicAdd(&ge[1], t1);
+                s_seg[warp] = wapp;
+                if (wapp > uint32_t(kSegCap)) s_app = 1u;   // a segment overflowed
+            }
         }
         __syncthreads();
-        const bool overflow = s_app > uint32_t(kListCap);
+        const bool overflow = s_app != 0u;
         if (!overflow) {
-            for (int e = tid; e < int(s_app); e += kRrThreads) atomicAdd(&ge[lst[e] >> kLevelShift], 1u);
+            for (int e = tid; e < kListCap; e += kRrThreads) {
+                if (uint32_t(e % kSegCap) < s_seg[e / kSegCap]) atomicAdd(&ge[lst[e] >> kLevelShift], 1u);
+            }
         } else {
             // the list overflowed: count the levels from the counters themselves
             uint32_t gel[TACO_MAX_SUBSPACES];
@@ -650,7 +653,8 @@ count_select_rerank_kernel(const RerankParams P) {
         }
         if (last >= 2 && !overflow && mine <= uint32_t(P.buf_cap)) {
             // the candidates are the list entries tagged `last`
-            for (int e = tid; e < int(s_app); e += kRrThreads) {
+            for (int e = tid; e < kListCap; e += kRrThreads) {
+                if (uint32_t(e % kSegCap) >= s_seg[e / kSegCap]) continue;
                 const uint32_t x = lst[e];
                 if (int(x >> kLevelShift) == last)
                     buf[atomicAdd(&s_bufn, 1u)] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
