@@ -409,6 +409,8 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     const size_t o_cells = off; off = align_up(off + size_t(chunk) * Ns * K * 2);
     const size_t o_nc = off; off = align_up(off + size_t(chunk) * Ns * 4);
     const size_t o_ret = off; off = align_up(off + size_t(chunk) * Ns * 8);
+    const size_t o_ld = off; off = align_up(off + size_t(chunk) * ix->cluster * kk_max * 4);
+    const size_t o_li = off; off = align_up(off + size_t(chunk) * ix->cluster * kk_max * 4);
     const size_t o_par = off; off = align_up(off + (per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0));
     const size_t o_q = off; off = align_up(off + (q_dev ? 0 : size_t(chunk) * ix->d * 4));
     const size_t o_oi = off; off = align_up(off + (id_dev ? 0 : size_t(chunk) * k_stride * 8));
@@ -443,6 +445,8 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         L.cells = reinterpret_cast<uint16_t*>(wb + o_cells);
         L.ncells = reinterpret_cast<int32_t*>(wb + o_nc);
         L.retrieved = reinterpret_cast<int64_t*>(wb + o_ret);
+        L.lists_d = reinterpret_cast<float*>(wb + o_ld);
+        L.lists_i = reinterpret_cast<uint32_t*>(wb + o_li);
         L.out_ids = id_dev ? out_ids + c0 * k_stride : reinterpret_cast<int64_t*>(wb + o_oi);
         L.out_dists = dist_dev ? out_dists + c0 * k_stride : reinterpret_cast<float*>(wb + o_od);
         L.k_stride = k_stride;

@@ -120,6 +120,8 @@ struct SearchLaunch {
     uint16_t* cells;           // device [nq][Ns][K]
     int32_t* ncells;           // device [nq][Ns]
     int64_t* retrieved;        // device [nq][Ns]
+    float* lists_d;            // device [nq][cluster][kk_max]
+    uint32_t* lists_i;         // device [nq][cluster][kk_max]
     int64_t* out_ids;
     float* out_dists;
     int k_stride;

@@ -78,9 +78,14 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     const size_t per_cells = up256(size_t(nq) * ix->Ns * ix->K * 2);
     const size_t per_nc = up256(size_t(nq) * ix->Ns * 4);
     const size_t per_ret = up256(size_t(nq) * ix->Ns * 8);
-    const size_t need = per_qt + per_cells + per_nc + per_ret;
+    const int kk = q.precision == TACO_PREC_BF16
+                       ? int(std::min<int64_t>(std::max<int64_t>(int64_t(q.k) * q.shortlist_mult, q.k), TACO_MAX_K))
+                       : q.k;
+    const size_t per_list = up256(size_t(nq) * ix->cluster * kk * 4);
+    const size_t need = per_qt + per_cells + per_nc + per_ret + 2 * per_list;
     if (need > kNoAllocScratchBytes) {
-        const size_t one = size_t(ix->Dp) * 4 + size_t(ix->Ns) * ix->K * 2 + size_t(ix->Ns) * 12;
+        const size_t one = size_t(ix->Dp) * 4 + size_t(ix->Ns) * ix->K * 2 + size_t(ix->Ns) * 12 +
+                           size_t(ix->cluster) * kk * 8;
         return fail(TACO_ECAPACITY,
                     "nq = %lld needs %zu bytes of scratch; the fixed scratch holds %zu bytes "
                     "(about %zu queries of this index per call)",
@@ -99,9 +104,7 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     d.select_rule = q.select_rule;
     d.budget = q.budget;
     d.rerank_target = q.rerank_target;
-    d.kk = q.precision == TACO_PREC_BF16
-               ? int(std::min<int64_t>(std::max<int64_t>(int64_t(q.k) * q.shortlist_mult, q.k), TACO_MAX_K))
-               : q.k;
+    d.kk = kk;
     d.pad = 0;
     L.defaults = d;
     L.params = nullptr;
@@ -111,6 +114,8 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     L.cells = reinterpret_cast<uint16_t*>(b + per_qt);
     L.ncells = reinterpret_cast<int32_t*>(b + per_qt + per_cells);
     L.retrieved = reinterpret_cast<int64_t*>(b + per_qt + per_cells + per_nc);
+    L.lists_d = reinterpret_cast<float*>(b + per_qt + per_cells + per_nc + per_ret);
+    L.lists_i = reinterpret_cast<uint32_t*>(b + per_qt + per_cells + per_nc + per_ret + per_list);
     L.out_ids = out_ids;
     L.out_dists = out_dists;
     L.k_stride = k_stride;

@@ -18,9 +18,9 @@
 //               the next query); ids whose SC reaches the threshold are buffered, their rows
 //               gathered (G lanes per row, 16-byte loads) and each warp keeps a sorted top
 //               list in registers (insertion by ballot + shuffle).
-//   4. merge:   warp lists -> CTA list -> cluster list in CTA 0 through distributed shared
-//               memory, each by a parallel rank merge. With BF16 rows the merged list is a
-//               shortlist that CTA 0 re-ranks with FP32 rows before writing the top k.
+//   4. merge:   warp lists -> CTA list, written to global memory. A second kernel merges
+//               the cluster's lists per query (one warp each); with BF16 rows the merged
+//               list is a shortlist that it re-ranks with FP32 rows before writing the top k.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -57,9 +57,8 @@ struct RerankParams {
     size_t region_a;        // bytes of the counter region (multiple of 16)
     int64_t nq;             // queries of this launch
     int buf_cap;            // candidate buffer entries: max(kBufCap, 16 * kkc)
-    int64_t* out_ids;
-    float* out_dists;
-    int k_stride;
+    float* lists_d;         // [nq][cluster][kk] each CTA's best kk (dist^2), sorted
+    uint32_t* lists_i;      // [nq][cluster][kk] their ids
     uint8_t* dbg_sc;
     int64_t* dbg_hist;
     int32_t* dbg_last;
@@ -421,25 +420,20 @@ count_select_rerank_kernel(const RerankParams P) {
     const int kkc = P.kkc;
     float* Ld = reinterpret_cast<float*>(mp);
     uint32_t* Li = reinterpret_cast<uint32_t*>(Ld + kRrWarps * kkc);
-    float* CLd = reinterpret_cast<float*>(Li + kRrWarps * kkc);
-    uint32_t* CLi = reinterpret_cast<uint32_t*>(CLd + kkc);
-    float* GLd = reinterpret_cast<float*>(CLi + kkc);
-    uint32_t* GLi = reinterpret_cast<uint32_t*>(GLd + kkc);
-    float* qv = reinterpret_cast<float*>(GLi + kkc);                             // d_pad
+    float* qv = reinterpret_cast<float*>(Li + kRrWarps * kkc);                   // d_pad
     uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);                   // buf_cap
     uint32_t* lst = buf + P.buf_cap;                                             // kListCap
     unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);  // kCellBatch
     uint32_t* cpre = reinterpret_cast<uint32_t*>(cbeg + kCellBatch);            // kCellBatch+1
     uint32_t* ge2 = cpre + kCellBatch + 4;                                       // [2][16]
-    float* RLd = reinterpret_cast<float*>(ge2 + 32);                             // [16][kkc]
-    uint32_t* RLi = reinterpret_cast<uint32_t*>(RLd + 16 * kkc);                 // [16][kkc]
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ int s_last;
     __shared__ uint32_t s_tmp[kRrWarps];
     __shared__ uint32_t s_wcnt[2][kRrWarps];
-    __shared__ uint32_t s_allge[16 * 16];
+    __shared__ uint32_t s_allge2[2][16 * 16];   // [parity][cta][level], filled by every CTA
     __shared__ uint32_t s_bufn, s_app;
     __shared__ uint32_t s_seg[kRrWarps];
+    __shared__ uint32_t s_segpre[kRrWarps + 1];
 
     const int Ns = P.Ns;
     const int slab_lo = cta * P.slabs_per_cta;
@@ -463,6 +457,7 @@ count_select_rerank_kernel(const RerankParams P) {
     for (int64_t q = blockIdx.y; q < P.nq; q += gridDim.y, par ^= 1) {
         const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
         uint32_t* ge = ge2 + 16 * par;
+        uint32_t* s_allge = s_allge2[par];
         __syncthreads();   // the previous query's readers of qv / s_pre / lists are done
         for (int j = tid; j < P.d_pad; j += kRrThreads)
             qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
@@ -546,10 +541,24 @@ count_select_rerank_kernel(const RerankParams P) {
         }
         __syncthreads();
         const bool overflow = s_app != 0u;
-        if (!overflow) {
-            for (int e = tid; e < kListCap; e += kRrThreads) {
-                if (uint32_t(e % kSegCap) < s_seg[e / kSegCap]) atomicAdd(&ge[lst[e] >> kLevelShift], 1u);
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (int w = 0; w < kRrWarps; ++w) {
+                s_segpre[w] = acc;
+                acc += min(s_seg[w], uint32_t(kSegCap));
             }
+            s_segpre[kRrWarps] = acc;
+        }
+        __syncthreads();
+        const int napp = int(s_segpre[kRrWarps]);
+        // entry e of the concatenated segments
+        auto seg_entry = [&](int e) {
+            int w = 0;
+            while (uint32_t(e) >= s_segpre[w + 1]) ++w;
+            return lst[w * kSegCap + (e - int(s_segpre[w]))];
+        };
+        if (!overflow) {
+            for (int e = tid; e < napp; e += kRrThreads) atomicAdd(&ge[seg_entry(e) >> kLevelShift], 1u);
         } else {
             // the list overflowed: count the levels from the counters themselves
             uint32_t gel[TACO_MAX_SUBSPACES];
@@ -653,9 +662,8 @@ count_select_rerank_kernel(const RerankParams P) {
         }
         if (last >= 2 && !overflow && mine <= uint32_t(P.buf_cap)) {
             // the candidates are the list entries tagged `last`
-            for (int e = tid; e < kListCap; e += kRrThreads) {
-                if (uint32_t(e % kSegCap) >= s_seg[e / kSegCap]) continue;
-                const uint32_t x = lst[e];
+            for (int e = tid; e < napp; e += kRrThreads) {
+                const uint32_t x = seg_entry(e);
                 if (int(x >> kLevelShift) == last)
                     buf[atomicAdd(&s_bufn, 1u)] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
             }
@@ -750,62 +758,18 @@ count_select_rerank_kernel(const RerankParams P) {
             }
         }
         __syncthreads();
-        // the CTA's merged list goes straight into row `cta` of CTA 0's receive area
+        // the CTA's best kk go to global memory; a per-query kernel merges the cluster's lists
         {
-            float* rd = cluster.map_shared_rank(RLd, 0) + cta * kkc;
-            uint32_t* ri = cluster.map_shared_rank(RLi, 0) + cta * kkc;
+            float* od = P.lists_d + (size_t(q) * ncta + cta) * kk;
+            uint32_t* oi = P.lists_i + (size_t(q) * ncta + cta) * kk;
             if (kk <= 64) {
-                if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, rd, ri, lane);
+                if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, od, oi, lane);
             } else {
-                rank_merge(Ld, Li, kkc, kRrWarps, kk, rd, ri, reinterpret_cast<int*>(buf), tid, kRrThreads);
+                rank_merge(Ld, Li, kkc, kRrWarps, kk, od, oi, reinterpret_cast<int*>(buf), tid, kRrThreads);
             }
-        }
-        cluster.sync();
-        if (cta != 0) continue;   // CTA 0's receive area is rewritten only after every CTA
-                                  // passes the next query's first cluster barrier
-        if (kk <= 64) {
-            if (warp == 0) warp_merge(RLd, RLi, kkc, ncta, kk, GLd, GLi, lane);
-        } else {
-            rank_merge(RLd, RLi, kkc, ncta, kk, GLd, GLi, reinterpret_cast<int*>(buf), tid, kRrThreads);
-        }
-        __syncthreads();
-        if constexpr (BF16) {
-            // exact FP32 re-rank of the shortlist (8 lanes per row, all warps), then sort
-            constexpr int G8 = 8;
-            const int nf4 = P.d_pad / 4;
-            const int gid8 = tid / G8, gl8 = tid % G8;
-            for (int eb = 0; eb < kkc; eb += kRrThreads / G8) {   // warp-uniform trip count
-                const int e = eb + gid8;
-                const uint32_t id = e < kk ? GLi[e] : kNoId;
-                float acc = 0.f;
-                if (id != kNoId) {
-                    const float4* row = reinterpret_cast<const float4*>(P.data + size_t(id) * P.d_pad);
-                    const float4* q4 = reinterpret_cast<const float4*>(qv);
-                    for (int f = gl8; f < nf4; f += G8) {
-                        const uint4 r4 = ldg_stream_u4(row + f, pol_stream);
-                        acc = sq4(make_float4(__uint_as_float(r4.x), __uint_as_float(r4.y),
-                                              __uint_as_float(r4.z), __uint_as_float(r4.w)),
-                                  q4[f], acc);
-                    }
-                }
-#pragma unroll
-                for (int off = G8 / 2; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-                if (gl8 == 0 && e < kkc) {
-                    Ld[e] = id != kNoId ? acc : __int_as_float(0x7f800000);
-                    Li[e] = id;
-                }
-            }
-            __syncthreads();
-            rank_sort(Ld, Li, kk, GLd, GLi, tid, kRrThreads);
-            __syncthreads();
-        }
-        for (int t = tid; t < P.k_stride; t += kRrThreads) {
-            const bool ok = t < qp.k && t < kk && GLi[t] != kNoId;
-            P.out_ids[q * P.k_stride + t] = ok ? int64_t(GLi[t]) : int64_t(-1);
-            P.out_dists[q * P.k_stride + t] = ok ? sqrtf(GLd[t]) : __int_as_float(0x7f800000);
         }
     }
-    cluster.sync();   // no CTA leaves while CTA 0 may still read its list
+    cluster.sync();   // no CTA leaves while another may still write its level table
 }
 
 template <int G, int R, bool BF16>

@@ -213,6 +213,281 @@ probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict
     }
 }
 
+// Same selection as probe_cells_kernel for K <= 256 * CPT cells, keeping each thread's CPT
+// keys and sizes in registers: the key range comes from the extremes of d1 and d2 (FP32
+// addition is monotone, so min1 + min2 and max1 + max2 bound every key), and the histogram,
+// bucket collection and output passes reuse the registers instead of recomputing keys.
+template <int CPT>
+__global__ void __launch_bounds__(kSelThreads)
+probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __restrict__ cent,
+                       int Ns, int s, int h1, int sk, const uint32_t* __restrict__ sizes,
+                       int64_t n, QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
+                       int list_cap, uint16_t* __restrict__ cells_out,
+                       int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out,
+                       uint8_t* __restrict__ dbg_probed) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int i = blockIdx.x;
+    const int64_t q = blockIdx.y;
+    const int K = sk * sk;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long* list = reinterpret_cast<unsigned long long*>(sm);  // list_cap
+    uint32_t* hist = reinterpret_cast<uint32_t*>(list + list_cap);         // kSelBins
+    float* d1 = reinterpret_cast<float*>(hist + kSelBins);                  // sk
+    float* d2 = d1 + sk;                                                    // sk
+    __shared__ uint32_t s_min, s_max;
+    __shared__ int s_bucket, s_m, s_cnt;
+    __shared__ unsigned long long s_pre, s_T, s_ret;
+    __shared__ uint32_t s_wsum[kSelThreads / 32];
+
+    const QueryParamsDev qp = params ? params[q] : defaults;
+    const int64_t budget = qp.budget;
+    const uint32_t* sz = sizes + size_t(i) * K;
+    uint32_t kw[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {   // sizes first: their loads overlap the distance math
+        const int cell = tid + kSelThreads * u;
+        kw[u] = cell < K ? __ldg(sz + cell) : 0u;
+    }
+    // Alg. 6 steps 4-5: squared distances of the two half-queries to their centroids
+    const float* qi = qt + q * Dp + size_t(i) * s;
+    for (int t = tid; t < 2 * sk; t += kSelThreads) {
+        const int h = t >= sk;
+        const int c = h ? t - sk : t;
+        const int off = h ? h1 : 0, len = h ? s - h1 : h1;
+        const float* cc = cent + (size_t(i) * sk + c) * s + off;
+        float acc = 0.f;
+        for (int j = 0; j < len; ++j) {
+            const float df = qi[off + j] - cc[j];
+            acc = fmaf(df, df, acc);
+        }
+        (h ? d2 : d1)[c] = acc;
+    }
+    for (int t = tid; t < kSelBins; t += kSelThreads) hist[t] = 0u;
+    if (tid == 0) {
+        s_m = 0;
+        s_cnt = 0;
+        s_ret = 0ull;
+        s_T = ~0ull;
+        s_bucket = -1;
+        s_pre = 0ull;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float mn1 = 3.4e38f, mx1 = 0.f, mn2 = 3.4e38f, mx2 = 0.f;
+        for (int t = lane; t < sk; t += 32) {
+            mn1 = fminf(mn1, d1[t]);
+            mx1 = fmaxf(mx1, d1[t]);
+            mn2 = fminf(mn2, d2[t]);
+            mx2 = fmaxf(mx2, d2[t]);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            mn1 = fminf(mn1, __shfl_xor_sync(0xffffffffu, mn1, off));
+            mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, off));
+            mn2 = fminf(mn2, __shfl_xor_sync(0xffffffffu, mn2, off));
+            mx2 = fmaxf(mx2, __shfl_xor_sync(0xffffffffu, mx2, off));
+        }
+        if (lane == 0) {
+            s_min = __float_as_uint(mn1 + mn2);
+            s_max = __float_as_uint(mx1 + mx2);
+        }
+    }
+    uint32_t kb[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        const int cell = tid + kSelThreads * u;
+        kb[u] = 0xffffffffu;
+        if (cell < K) {
+            const int r = cell / sk, c = cell - r * sk;
+            kb[u] = __float_as_uint(d1[r] + d2[c]);
+        }
+    }
+    __syncthreads();
+    if (budget <= n) {
+        const uint32_t minb = s_min, range = s_max - s_min;
+        const int bits = range ? 32 - __clz(range) : 0;
+        const int shift = bits > 11 ? bits - 11 : 0;
+#pragma unroll
+        for (int u = 0; u < CPT; ++u)
+            if (kw[u]) atomicAdd(&hist[(kb[u] - minb) >> shift], kw[u]);
+        __syncthreads();
+        unsigned long long loc = 0;
+#pragma unroll
+        for (int j = 0; j < kSelBinsPerThread; ++j) loc += hist[tid * kSelBinsPerThread + j];
+        unsigned long long incl = loc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) s_wsum[warp] = uint32_t(incl);
+        __syncthreads();
+        unsigned long long wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+        unsigned long long pre = wpre + incl - loc;
+        for (int j = 0; j < kSelBinsPerThread; ++j) {
+            const uint32_t hb = hist[tid * kSelBinsPerThread + j];
+            if (pre < (unsigned long long)budget && (unsigned long long)budget <= pre + hb) {
+                s_bucket = tid * kSelBinsPerThread + j;
+                s_pre = pre;
+            }
+            pre += hb;
+        }
+        __syncthreads();
+        const int bucket = s_bucket;
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            const int cell = tid + kSelThreads * u;
+            if (cell < K && int((kb[u] - minb) >> shift) == bucket)
+                list[atomicAdd(&s_m, 1)] = (static_cast<unsigned long long>(kb[u]) << 32) | unsigned(cell);
+        }
+        __syncthreads();
+        const int m = s_m;
+        int p2 = 1;
+        while (p2 < m) p2 <<= 1;
+        for (int t = m + tid; t < p2; t += kSelThreads) list[t] = ~0ull;
+        __syncthreads();
+        for (int k2 = 2; k2 <= p2; k2 <<= 1) {
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                for (int t = tid; t < p2; t += kSelThreads) {
+                    const int o = t ^ j;
+                    if (o > t) {
+                        const unsigned long long a = list[t], b = list[o];
+                        if ((a > b) == ((t & k2) == 0)) {
+                            list[t] = b;
+                            list[o] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (warp == 0) {
+            unsigned long long cum = s_pre;
+            for (int b0 = 0; b0 < m; b0 += 32) {
+                const int idx = b0 + lane;
+                const unsigned long long key = idx < m ? list[idx] : ~0ull;
+                unsigned long long w = idx < m ? sz[uint32_t(key)] : 0ull;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned long long v = __shfl_up_sync(0xffffffffu, w, off);
+                    if (lane >= off) w += v;
+                }
+                const bool hit = idx < m && cum + w >= (unsigned long long)budget;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (bal) {
+                    if (lane == __ffs(bal) - 1) s_T = key;
+                    break;
+                }
+                cum += __shfl_sync(0xffffffffu, w, 31);
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long T = s_T;
+    const size_t qi_off = (size_t(q) * Ns + i);
+    unsigned long long ret = 0;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        const int cell = tid + kSelThreads * u;
+        const bool take = cell < K &&
+                          ((static_cast<unsigned long long>(kb[u]) << 32) | unsigned(cell)) <= T;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        int wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&s_cnt, __popc(bal));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (take) {
+            cells_out[qi_off * K + wbase + __popc(bal & ((1u << lane) - 1u))] = uint16_t(cell);
+            ret += kw[u];
+        }
+        if (dbg_probed && cell < K) dbg_probed[qi_off * K + cell] = take ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) ret += __shfl_xor_sync(0xffffffffu, ret, off);
+    if (lane == 0 && ret) atomicAdd(&s_ret, ret);
+    __syncthreads();
+    if (tid == 0) {
+        ncells_out[qi_off] = s_cnt;
+        retrieved_out[qi_off] = (long long)s_ret;
+    }
+}
+
+// Per query, one warp merges the cluster's CTA lists (Alg. 6 step 9: the k nearest
+// candidates) and writes the result. For BF16 rows the merged list is a shortlist: the warp
+// recomputes its distances from the FP32 rows and sorts them by (distance, id) first.
+constexpr int kFmWarps = 8;
+
+template <bool BF16>
+__global__ void __launch_bounds__(kFmWarps * 32)
+final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict__ lists_i,
+                   int ncta, int kk, int kkc, const float* __restrict__ queries, int d, int d_pad,
+                   const float* __restrict__ data, QueryParamsDev defaults,
+                   const QueryParamsDev* __restrict__ params, int64_t nq,
+                   int64_t* __restrict__ out_ids, float* __restrict__ out_dists, int k_stride) {
+    extern __shared__ __align__(16) unsigned char fm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = int64_t(blockIdx.x) * kFmWarps + warp;
+    if (q >= nq) return;
+    const size_t per_warp = size_t(4) * kkc * 4 + size_t(d_pad) * 4;
+    float* od = reinterpret_cast<float*>(fm + warp * per_warp);
+    uint32_t* oi = reinterpret_cast<uint32_t*>(od + kkc);
+    float* xd = reinterpret_cast<float*>(oi + kkc);
+    uint32_t* xi = reinterpret_cast<uint32_t*>(xd + kkc);
+    float* qv = reinterpret_cast<float*>(xi + kkc);
+    const QueryParamsDev qp = params ? params[q] : defaults;
+    warp_merge(lists_d + size_t(q) * ncta * kk, lists_i + size_t(q) * ncta * kk, kk, ncta, kk, od, oi,
+               lane);
+    __syncwarp();
+    if constexpr (BF16) {
+        for (int j = lane; j < d_pad; j += 32) qv[j] = j < d ? queries[q * d + j] : 0.f;
+        __syncwarp();
+        const int nf4 = d_pad / 4;
+        const float4* q4 = reinterpret_cast<const float4*>(qv);
+        for (int e0 = 0; e0 < kk; e0 += 4) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int f = lane; f < nf4; f += 32) {
+                float4 r[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u;
+                    const uint32_t id = e < kk ? oi[e] : kNoId;
+                    r[u] = id != kNoId ? __ldg(reinterpret_cast<const float4*>(data + size_t(id) * d_pad) + f)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = sq4(r[u], q4[f], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                for (int off = 16; off; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
+                const int e = e0 + u;
+                if (lane == 0 && e < kk) {
+                    xd[e] = oi[e] != kNoId ? acc[u] : __int_as_float(0x7f800000);
+                    xi[e] = oi[e];
+                }
+            }
+        }
+        __syncwarp();
+        // rank sort (ties between padding entries by position)
+        for (int e = lane; e < kk; e += 32) {
+            const float x = xd[e];
+            const uint32_t xid = xi[e];
+            int rank = 0;
+            for (int f = 0; f < kk; ++f)
+                rank += lt_pair(xd[f], xi[f], x, xid) || (xd[f] == x && xi[f] == xid && f < e);
+            od[rank] = x;
+            oi[rank] = xid;
+        }
+        __syncwarp();
+    }
+    for (int t = lane; t < k_stride; t += 32) {
+        const bool ok = t < qp.k && t < kk && oi[t] != kNoId;
+        out_ids[q * k_stride + t] = ok ? int64_t(oi[t]) : int64_t(-1);
+        out_dists[q * k_stride + t] = ok ? sqrtf(od[t]) : __int_as_float(0x7f800000);
+    }
+}
+
 static int next_pow2(int x) {
     int p = 1;
     while (p < x) p <<= 1;
@@ -299,11 +574,25 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
             attr_set = true;
         }
+        // the register variant handles K <= 4096, whose list needs at most 48 KB
+
         dim3 grid(unsigned(ix->Ns), unsigned(L.nq));
         if (int rc = prof_begin(ix, 1, st, &pb, &pe)) return rc;
-        probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
-            L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
-            L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed);
+        const int cpt = (K + kSelThreads - 1) / kSelThreads;
+#define TACO_PROBE_REG(N)                                                                         \
+    probe_cells_reg_kernel<N><<<grid, kSelThreads, smem, st>>>(                                   \
+        L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
+        L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed)
+        if (cpt <= 1) TACO_PROBE_REG(1);
+        else if (cpt <= 2) TACO_PROBE_REG(2);
+        else if (cpt <= 4) TACO_PROBE_REG(4);
+        else if (cpt <= 8) TACO_PROBE_REG(8);
+        else if (cpt <= 16) TACO_PROBE_REG(16);
+        else
+            probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
+                L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
+                L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed);
+#undef TACO_PROBE_REG
         TACO_CUDA(cudaGetLastError());
         if (int rc = prof_end(ix, 1, st, pb, pe)) return rc;
         if (L.dbg.retrieved_num)
@@ -336,20 +625,18 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.kkc = next_pow2(L.kk_max);
         P.nq = L.nq;
         P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
-        P.out_ids = L.out_ids;
-        P.out_dists = L.out_dists;
-        P.k_stride = L.k_stride;
+        P.lists_d = L.lists_d;
+        P.lists_i = L.lists_i;
         P.dbg_sc = L.dbg.sc;
         P.dbg_hist = L.dbg.collision_num;
         P.dbg_last = L.dbg.last_collision;
         P.dbg_cand = L.dbg.candidate_num;
         if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
         // counters | merge lists | query | candidate buffer | staged runs | level counts
-        const size_t merge_bytes = (size_t(2) * kRrWarps * P.kkc + 4 * size_t(P.kkc)) * 4;
+        const size_t merge_bytes = size_t(2) * kRrWarps * P.kkc * 4;
         P.buf_cap = std::max(kBufCap, kRrWarps * P.kkc);
         const size_t smem = P.region_a + merge_bytes + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
-                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4 +
-                            size_t(16) * P.kkc * 8;
+                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
         cudaError_t e;
@@ -365,6 +652,17 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         }
         if (e != cudaSuccess) return cuda_fail(e, "count_select_rerank launch", __FILE__, __LINE__);
         if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
+        // 4. per-query merge of the cluster's lists (and BF16 shortlist re-rank)
+        const size_t fsm = size_t(kFmWarps) * (size_t(4) * P.kkc * 4 + size_t(ix->d_pad) * 4);
+        auto fk = bf16 ? final_merge_kernel<true> : final_merge_kernel<false>;
+        if (fsm > 48 * 1024)
+            TACO_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
+        if (int rc = prof_begin(ix, 3, st, &pb, &pe)) return rc;
+        fk<<<unsigned((L.nq + kFmWarps - 1) / kFmWarps), kFmWarps * 32, fsm, st>>>(
+            L.lists_d, L.lists_i, ix->cluster, P.kk, P.kkc, L.queries, ix->d, ix->d_pad, ix->d_data,
+            L.defaults, L.params, L.nq, L.out_ids, L.out_dists, L.k_stride);
+        TACO_CUDA(cudaGetLastError());
+        if (int rc = prof_end(ix, 3, st, pb, pe)) return rc;
     }
     return TACO_OK;
 }

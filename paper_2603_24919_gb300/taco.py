@@ -56,7 +56,7 @@ class DebugOut(C.Structure):
 
 
 NUM_KERNELS = 4
-KERNEL_NAMES = ("project", "probe_cells", "count_select_rerank", "reserved")
+KERNEL_NAMES = ("project", "probe_cells", "count_select_rerank", "final_merge")
 
 
 class KernelTimes(C.Structure):
