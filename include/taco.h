@@ -155,8 +155,8 @@ int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
  * library holds until the process exits; the call itself calls no allocating routine.
  * Every scratch byte read by a call is written earlier in the same call, so nothing needs
  * clearing between calls. Limits: nq <= 16384 and the batch's scratch (about
- * 4*N_s*s + 2*N_s*K + 12*N_s + 8*C*kk bytes per query, C the index's cluster size and kk
- * the k of the query or its BF16 shortlist) must fit the array, else TACO_ECAPACITY.
+ * 4*N_s*s + 2*N_s*K + 12*N_s + 128*C*kk bytes per query, C the index's cluster size and
+ * kk the k of the query or its BF16 shortlist) must fit the array, else TACO_ECAPACITY.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture. All calls share the array, so calls
  * that overlap on the GPU (other streams, other threads) race: serialise them.

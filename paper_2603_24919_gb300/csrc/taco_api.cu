@@ -409,8 +409,9 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     const size_t o_cells = off; off = align_up(off + size_t(chunk) * Ns * K * 2);
     const size_t o_nc = off; off = align_up(off + size_t(chunk) * Ns * 4);
     const size_t o_ret = off; off = align_up(off + size_t(chunk) * Ns * 8);
-    const size_t o_ld = off; off = align_up(off + size_t(chunk) * ix->cluster * kk_max * 4);
-    const size_t o_li = off; off = align_up(off + size_t(chunk) * ix->cluster * kk_max * 4);
+    const size_t lists = size_t(chunk) * ix->cluster * kListsPerCta * kk_max * 4;
+    const size_t o_ld = off; off = align_up(off + lists);
+    const size_t o_li = off; off = align_up(off + lists);
     const size_t o_par = off; off = align_up(off + (per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0));
     const size_t o_q = off; off = align_up(off + (q_dev ? 0 : size_t(chunk) * ix->d * 4));
     const size_t o_oi = off; off = align_up(off + (id_dev ? 0 : size_t(chunk) * k_stride * 8));

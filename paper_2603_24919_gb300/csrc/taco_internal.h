@@ -23,6 +23,8 @@ constexpr int kSlabBytes = kSlabWords * 4;
 
 // Queries handled per internal launch group (bounds the workspace and grid.y).
 constexpr int64_t kQueryChunk = 16384;
+// Top lists each CTA of a query's cluster writes (one per warp of the fused kernel).
+constexpr int kListsPerCta = 16;
 
 struct QueryParamsDev {
     int32_t k;
@@ -120,8 +122,8 @@ struct SearchLaunch {
     uint16_t* cells;           // device [nq][Ns][K]
     int32_t* ncells;           // device [nq][Ns]
     int64_t* retrieved;        // device [nq][Ns]
-    float* lists_d;            // device [nq][cluster][kk_max]
-    uint32_t* lists_i;         // device [nq][cluster][kk_max]
+    float* lists_d;            // device [nq][cluster][kListsPerCta][kk_max]
+    uint32_t* lists_i;         // device [nq][cluster][kListsPerCta][kk_max]
     int64_t* out_ids;
     float* out_dists;
     int k_stride;

@@ -81,11 +81,11 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     const int kk = q.precision == TACO_PREC_BF16
                        ? int(std::min<int64_t>(std::max<int64_t>(int64_t(q.k) * q.shortlist_mult, q.k), TACO_MAX_K))
                        : q.k;
-    const size_t per_list = up256(size_t(nq) * ix->cluster * kk * 4);
+    const size_t per_list = up256(size_t(nq) * ix->cluster * kListsPerCta * kk * 4);
     const size_t need = per_qt + per_cells + per_nc + per_ret + 2 * per_list;
     if (need > kNoAllocScratchBytes) {
         const size_t one = size_t(ix->Dp) * 4 + size_t(ix->Ns) * ix->K * 2 + size_t(ix->Ns) * 12 +
-                           size_t(ix->cluster) * kk * 8;
+                           size_t(ix->cluster) * kListsPerCta * kk * 8;
         return fail(TACO_ECAPACITY,
                     "nq = %lld needs %zu bytes of scratch; the fixed scratch holds %zu bytes "
                     "(about %zu queries of this index per call)",

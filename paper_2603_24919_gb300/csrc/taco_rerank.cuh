@@ -18,9 +18,10 @@
 //               the next query); ids whose SC reaches the threshold are buffered, their rows
 //               gathered (G lanes per row, 16-byte loads) and each warp keeps a sorted top
 //               list in registers (insertion by ballot + shuffle).
-//   4. merge:   warp lists -> CTA list, written to global memory. A second kernel merges
-//               the cluster's lists per query (one warp each); with BF16 rows the merged
-//               list is a shortlist that it re-ranks with FP32 rows before writing the top k.
+//   4. lists:   every warp writes its sorted top list to global memory. A second kernel
+//               merges a query's lists (one warp per query: per CTA, then across the
+//               cluster); with BF16 rows the merged list is a shortlist that it re-ranks with
+//               FP32 rows before writing the top k.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -36,6 +37,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kRrThreads = 512;
 constexpr int kRrWarps = kRrThreads / 32;
+static_assert(kRrWarps == kListsPerCta, "one top list per warp of the fused kernel");
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kNoId = 0xffffffffu;
 
@@ -57,8 +59,8 @@ struct RerankParams {
     size_t region_a;        // bytes of the counter region (multiple of 16)
     int64_t nq;             // queries of this launch
     int buf_cap;            // candidate buffer entries: max(kBufCap, 16 * kkc)
-    float* lists_d;         // [nq][cluster][kk] each CTA's best kk (dist^2), sorted
-    uint32_t* lists_i;      // [nq][cluster][kk] their ids
+    float* lists_d;         // [nq][cluster][kRrWarps][kk] each warp's best kk (dist^2), sorted
+    uint32_t* lists_i;      // [nq][cluster][kRrWarps][kk] their ids
     uint8_t* dbg_sc;
     int64_t* dbg_hist;
     int32_t* dbg_last;
@@ -128,67 +130,6 @@ struct WarpTop {
         }
     }
 };
-
-// Merge of `nl` sorted lists (list L at ld/li + L*stride, each of length kk) into the kk
-// smallest entries, sorted, at (od, oi). Every entry finds its output position directly:
-// its rank is its index in its own list plus, for every other list, the number of that
-// list's entries ordered before it (binary search; equal (dist, id) pairs, which only
-// padding entries can form, are ordered by list index). The (entry, other list) searches
-// are spread over all threads and summed with shared-memory atomics into `rk` (nl*kk
-// ints); ranks are distinct, so the first kk positions are each written once.
-__device__ __forceinline__ void rank_merge(const float* ld, const uint32_t* li, int stride, int nl,
-                                           int kk, float* od, uint32_t* oi, int* rk, int tid,
-                                           int nthreads) {
-    const int total = nl * kk;
-    for (int e = tid; e < total; e += nthreads) rk[e] = e % kk;
-    __syncthreads();
-    for (int pr = tid; pr < total * nl; pr += nthreads) {
-        const int e = pr / nl, L2 = pr - e * nl;
-        const int L = e / kk, p = e - L * kk;
-        if (L2 == L) continue;
-        const float d = ld[L * stride + p];
-        const uint32_t id = li[L * stride + p];
-        const float* a = ld + L2 * stride;
-        const uint32_t* ai = li + L2 * stride;
-        int lo_i = 0, hi_i = kk;
-        while (lo_i < hi_i) {
-            const int mid = (lo_i + hi_i) >> 1;
-            const float am = a[mid];
-            const uint32_t aim = ai[mid];
-            const bool before = lt_pair(am, aim, d, id) || (am == d && aim == id && L2 < L);
-            if (before) lo_i = mid + 1;
-            else hi_i = mid;
-        }
-        if (lo_i) atomicAdd(&rk[e], lo_i);
-    }
-    __syncthreads();
-    for (int e = tid; e < total; e += nthreads) {
-        const int r = rk[e];
-        if (r < kk) {
-            const int L = e / kk, p = e - L * kk;
-            od[r] = ld[L * stride + p];
-            oi[r] = li[L * stride + p];
-        }
-    }
-}
-
-// Sort n (dist, id) pairs by rank counting (n small); ties between equal pairs, which only
-// padding entries can form, go by index. Writes the sorted pairs to (od, oi).
-__device__ __forceinline__ void rank_sort(const float* d, const uint32_t* ix, int n, float* od,
-                                          uint32_t* oi, int tid, int nthreads) {
-    for (int e = tid; e < n; e += nthreads) {
-        const float x = d[e];
-        const uint32_t xi = ix[e];
-        int rank = 0;
-        for (int f = 0; f < n; ++f) {
-            const float y = d[f];
-            const uint32_t yi = ix[f];
-            rank += lt_pair(y, yi, x, xi) || (y == x && yi == xi && f < e);
-        }
-        od[rank] = x;
-        oi[rank] = xi;
-    }
-}
 
 __device__ __forceinline__ float sq4(float4 o, float4 q, float acc) {
     float dx = o.x - q.x;
@@ -416,11 +357,7 @@ count_select_rerank_kernel(const RerankParams P) {
 
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);                          // counters
-    unsigned char* mp = smem + P.region_a;                                       // merge area
-    const int kkc = P.kkc;
-    float* Ld = reinterpret_cast<float*>(mp);
-    uint32_t* Li = reinterpret_cast<uint32_t*>(Ld + kRrWarps * kkc);
-    float* qv = reinterpret_cast<float*>(Li + kRrWarps * kkc);                   // d_pad
+    float* qv = reinterpret_cast<float*>(smem + P.region_a);                     // d_pad
     uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);                   // buf_cap
     uint32_t* lst = buf + P.buf_cap;                                             // kListCap
     unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);  // kCellBatch
@@ -434,6 +371,7 @@ count_select_rerank_kernel(const RerankParams P) {
     __shared__ uint32_t s_bufn, s_app;
     __shared__ uint32_t s_seg[kRrWarps];
     __shared__ uint32_t s_segpre[kRrWarps + 1];
+    __shared__ uint32_t s_gs[TACO_MAX_SUBSPACES + 1];
 
     const int Ns = P.Ns;
     const int slab_lo = cta * P.slabs_per_cta;
@@ -593,12 +531,17 @@ count_select_rerank_kernel(const RerankParams P) {
         cluster.sync();
 
         // ---- 2. Alg. 5 on the cluster-wide collision_num (same result in every CTA) ----
+        if (tid < Ns) {
+            uint32_t v = 0;
+            for (int r = 0; r < ncta; ++r) v += s_allge[r * 16 + tid + 1];
+            s_gs[tid + 1] = v;
+        }
+        __syncthreads();
         if (tid == 0) {
             long long gs[TACO_MAX_SUBSPACES + 2];
-            for (int j = 0; j <= Ns + 1; ++j) gs[j] = 0;
-            for (int r = 0; r < ncta; ++r)
-                for (int j = 1; j <= Ns; ++j) gs[j] += s_allge[r * 16 + j];
             gs[0] = P.n;
+            for (int j = 1; j <= Ns; ++j) gs[j] = s_gs[j];
+            gs[Ns + 1] = 0;
             int last = Ns;
             long long cand = 0;
             for (int j = Ns; j >= 0; --j) {
@@ -748,24 +691,16 @@ count_select_rerank_kernel(const RerankParams P) {
             for (int w = tid; w < words; w += kRrThreads) cnt[w] = 0u;
         }
 
-        // ---- 4. merge: warps -> CTA -> cluster ------------------------------------------
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int e = r * 32 + lane;
-            if (e < kk) {
-                Ld[warp * kkc + e] = top.d[r];
-                Li[warp * kkc + e] = top.i[r];
-            }
-        }
-        __syncthreads();
-        // the CTA's best kk go to global memory; a per-query kernel merges the cluster's lists
+        // ---- 4. every warp's best kk go to global memory; a per-query kernel merges them
         {
-            float* od = P.lists_d + (size_t(q) * ncta + cta) * kk;
-            uint32_t* oi = P.lists_i + (size_t(q) * ncta + cta) * kk;
-            if (kk <= 64) {
-                if (warp == 0) warp_merge(Ld, Li, kkc, kRrWarps, kk, od, oi, lane);
-            } else {
-                rank_merge(Ld, Li, kkc, kRrWarps, kk, od, oi, reinterpret_cast<int*>(buf), tid, kRrThreads);
+            const size_t row = ((size_t(q) * ncta + cta) * kRrWarps + warp) * kk;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int e = r * 32 + lane;
+                if (e < kk) {
+                    P.lists_d[row + e] = top.d[r];
+                    P.lists_i[row + e] = top.i[r];
+                }
             }
         }
     }

@@ -412,31 +412,37 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
     }
 }
 
-// Per query, one warp merges the cluster's CTA lists (Alg. 6 step 9: the k nearest
-// candidates) and writes the result. For BF16 rows the merged list is a shortlist: the warp
+// Per query, one warp merges the top lists of every warp of the cluster (Alg. 6 step 9:
+// the k nearest candidates) and writes the result: first the kRrWarps lists of each CTA,
+// then the cluster's CTA lists. For BF16 rows the merged list is a shortlist: the warp
 // recomputes its distances from the FP32 rows and sorts them by (distance, id) first.
-constexpr int kFmWarps = 8;
-
 template <bool BF16>
-__global__ void __launch_bounds__(kFmWarps * 32)
+__global__ void __launch_bounds__(256)
 final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict__ lists_i,
                    int ncta, int kk, int kkc, const float* __restrict__ queries, int d, int d_pad,
                    const float* __restrict__ data, QueryParamsDev defaults,
                    const QueryParamsDev* __restrict__ params, int64_t nq,
                    int64_t* __restrict__ out_ids, float* __restrict__ out_dists, int k_stride) {
     extern __shared__ __align__(16) unsigned char fm[];
+    const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t q = int64_t(blockIdx.x) * kFmWarps + warp;
+    const int64_t q = int64_t(blockIdx.x) * nw + warp;
     if (q >= nq) return;
-    const size_t per_warp = size_t(4) * kkc * 4 + size_t(d_pad) * 4;
-    float* od = reinterpret_cast<float*>(fm + warp * per_warp);
+    const size_t per_warp = size_t(ncta) * kkc * 8 + size_t(4) * kkc * 4 + size_t(d_pad) * 4;
+    float* cd = reinterpret_cast<float*>(fm + warp * per_warp);   // [ncta][kkc]
+    uint32_t* ci = reinterpret_cast<uint32_t*>(cd + ncta * kkc);  // [ncta][kkc]
+    float* od = reinterpret_cast<float*>(ci + ncta * kkc);
     uint32_t* oi = reinterpret_cast<uint32_t*>(od + kkc);
     float* xd = reinterpret_cast<float*>(oi + kkc);
     uint32_t* xi = reinterpret_cast<uint32_t*>(xd + kkc);
     float* qv = reinterpret_cast<float*>(xi + kkc);
     const QueryParamsDev qp = params ? params[q] : defaults;
-    warp_merge(lists_d + size_t(q) * ncta * kk, lists_i + size_t(q) * ncta * kk, kk, ncta, kk, od, oi,
-               lane);
+    for (int r = 0; r < ncta; ++r) {
+        const size_t row = (size_t(q) * ncta + r) * kRrWarps * kk;
+        warp_merge(lists_d + row, lists_i + row, kk, kRrWarps, kk, cd + r * kkc, ci + r * kkc, lane);
+    }
+    __syncwarp();
+    warp_merge(cd, ci, kkc, ncta, kk, od, oi, lane);
     __syncwarp();
     if constexpr (BF16) {
         for (int j = lane; j < d_pad; j += 32) qv[j] = j < d ? queries[q * d + j] : 0.f;
@@ -633,9 +639,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.dbg_cand = L.dbg.candidate_num;
         if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
         // counters | merge lists | query | candidate buffer | staged runs | level counts
-        const size_t merge_bytes = size_t(2) * kRrWarps * P.kkc * 4;
-        P.buf_cap = std::max(kBufCap, kRrWarps * P.kkc);
-        const size_t smem = P.region_a + merge_bytes + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
+        P.buf_cap = kBufCap;
+        const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
                             size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
@@ -653,12 +658,15 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         if (e != cudaSuccess) return cuda_fail(e, "count_select_rerank launch", __FILE__, __LINE__);
         if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
         // 4. per-query merge of the cluster's lists (and BF16 shortlist re-rank)
-        const size_t fsm = size_t(kFmWarps) * (size_t(4) * P.kkc * 4 + size_t(ix->d_pad) * 4);
+        const size_t per_warp = size_t(ix->cluster) * P.kkc * 8 + size_t(4) * P.kkc * 4 + size_t(ix->d_pad) * 4;
+        int fw = 8;
+        while (fw > 1 && size_t(fw) * per_warp > 160 * 1024) fw >>= 1;
+        const size_t fsm = size_t(fw) * per_warp;
         auto fk = bf16 ? final_merge_kernel<true> : final_merge_kernel<false>;
         if (fsm > 48 * 1024)
             TACO_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
         if (int rc = prof_begin(ix, 3, st, &pb, &pe)) return rc;
-        fk<<<unsigned((L.nq + kFmWarps - 1) / kFmWarps), kFmWarps * 32, fsm, st>>>(
+        fk<<<unsigned((L.nq + fw - 1) / fw), fw * 32, fsm, st>>>(
             L.lists_d, L.lists_i, ix->cluster, P.kk, P.kkc, L.queries, ix->d, ix->d_pad, ix->d_data,
             L.defaults, L.params, L.nq, L.out_ids, L.out_dists, L.k_stride);
         TACO_CUDA(cudaGetLastError());
