@@ -164,10 +164,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "count_select_rerank_sift1m.json")
+def ncu_traffic(kernel, precision):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_sift1m.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -321,13 +321,23 @@ def run_taco(args):
     retrieved = int(dbg["retrieved_num"].sum().item())
     ncells = int(dbg["probed"].sum(dtype=torch.int64).item())
     cand = int(dbg["candidate_num"].sum().item())
+    entries = int(dbg["collision_num"][:, 2:].sum().item())   # ids with SC >= 2 (level lists)
     shortlist = min(mult * K, 512)
     d_pad = info["d_pad"]
-    alg_bytes = (4 * retrieved + 8 * ncells + cand * d_pad * 2 + nq * shortlist * d_pad * 4
-                 + nq * (w.d * 4 + K * 12))
-    kk = kt_b["count_select_rerank"]
+    nr = info["cluster_size"]
+    io = nq * (w.d * 4 + K * 12)
+    alg = {   # algorithmic bytes per launch (one launch = the whole batch)
+        "count_lists": 4 * retrieved + 8 * ncells + 4 * entries + nq * nr * 72,
+        "select_rerank": cand * d_pad * 2 + nq * shortlist * d_pad * 4 + 4 * entries
+                         + nq * nr * 72 + io,
+        "cluster_count_select": 4 * retrieved + 8 * ncells + cand * d_pad * 2 + io,
+        "probe_cells": nq * w.n_subspaces * (w.sqrt_k ** 2) * 4 + 2 * ncells,
+    }
+    dominant = max((k for k in kt_b if kt_b[k]["launches"]), key=lambda k: kt_b[k]["ms"])
+    kk = kt_b[dominant]
     launch_ms = kk["ms"] / max(kk["launches"], 1)
     peak, peak_kind = measured_peaks()
+    alg_bytes = alg.get(dominant, 0)
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     shares = {name: round(v["ms"] / max(sum(x["ms"] for x in kt_b.values()), 1e-9), 4)
               for name, v in kt_b.items() if v["launches"]}
@@ -377,16 +387,17 @@ def run_taco(args):
         "gpu_launches": int(sum(v["launches"] for v in kt_b.values())),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": ncu_traffic("bf16"), "peak_kind": peak_kind,
-                     "kernel": "count_select_rerank (bf16)",
+                     "traffic": ncu_traffic(dominant, "bf16"), "peak_kind": peak_kind,
+                     "kernel": f"{dominant} (bf16 form)",
                      "algorithmic_bytes_per_launch": int(alg_bytes),
                      "launch_ms": round(launch_ms, 4),
                      "kernel_share": shares},
         "clocks": clk,
     }
-    fk = kt_f["count_select_rerank"]
-    f_launch_ms = fk["ms"] / max(fk["launches"], 1)
-    line["roofline_fp32"] = {"launch_ms": round(f_launch_ms, 4)}
+    line["kernel_ms_per_step_fp32"] = {k: round(v["ms"] / max(args.steps, 1), 4)
+                                       for k, v in kt_f.items() if v["launches"]}
+    line["kernel_ms_per_step_bf16"] = {k: round(v["ms"] / max(args.steps, 1), 4)
+                                       for k, v in kt_b.items() if v["launches"]}
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(ix, data, queries, w, calib["fp32"], args.cpu_seconds)

@@ -192,9 +192,11 @@ int taco_save_index(const taco_index* index, const char* path);
 int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_index** out);
 
 /* Per-kernel device time of the search path, accumulated while profiling is enabled.
- * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 fused count/select/
- * re-rank (Def. 6, Alg. 5, Alg. 6 step 9), 3 final per-query merge of the top lists. */
-#define TACO_NUM_KERNELS 4
+ * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 collision counting
+ * into per-range level lists (Def. 6), 3 selection and re-rank (Alg. 5, Alg. 6 step 9),
+ * 4 cluster kernel (counting, selection and re-rank for queries whose threshold is below 2,
+ * or for every query in taco_search_batch_noalloc), 5 merge of the cluster kernel's lists. */
+#define TACO_NUM_KERNELS 6
 typedef struct {
     int64_t launches[TACO_NUM_KERNELS];
     double ms[TACO_NUM_KERNELS];

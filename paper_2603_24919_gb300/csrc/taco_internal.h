@@ -25,6 +25,8 @@ constexpr int kSlabBytes = kSlabWords * 4;
 constexpr int64_t kQueryChunk = 16384;
 // Top lists each CTA of a query's cluster writes (one per warp of the fused kernel).
 constexpr int kListsPerCta = 16;
+// Average list entries (ids with SC >= 2) reserved per (query, id range) unit.
+constexpr size_t kArenaPerUnit = 2048;
 
 struct QueryParamsDev {
     int32_t k;
@@ -57,8 +59,8 @@ struct Profiler {
     std::vector<cudaEvent_t> pool;                 // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     size_t used = 0;
-    int64_t launches[TACO_NUM_KERNELS] = {0, 0, 0, 0};
-    double ms[TACO_NUM_KERNELS] = {0, 0, 0, 0};
+    int64_t launches[TACO_NUM_KERNELS] = {};
+    double ms[TACO_NUM_KERNELS] = {};
 };
 
 struct Workspace {
@@ -124,6 +126,14 @@ struct SearchLaunch {
     int64_t* retrieved;        // device [nq][Ns]
     float* lists_d;            // device [nq][cluster][kListsPerCta][kk_max]
     uint32_t* lists_i;         // device [nq][cluster][kListsPerCta][kk_max]
+    // two-pass form (null unit_ge: cluster kernel for every query)
+    uint32_t* unit_ge;         // device [nq][cluster][16]
+    uint32_t* unit_off;        // device [nq][cluster]
+    uint32_t* unit_len;        // device [nq][cluster]
+    uint32_t* arena;           // device [arena_cap]
+    uint32_t arena_cap;
+    uint32_t* arena_used;      // device [1]
+    uint32_t* qflag;           // device [nq]
     int64_t* out_ids;
     float* out_dists;
     int k_stride;

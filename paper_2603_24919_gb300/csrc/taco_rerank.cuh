@@ -61,6 +61,19 @@ struct RerankParams {
     int buf_cap;            // candidate buffer entries: max(kBufCap, 16 * kkc)
     float* lists_d;         // [nq][cluster][kRrWarps][kk] each warp's best kk (dist^2), sorted
     uint32_t* lists_i;      // [nq][cluster][kRrWarps][kk] their ids
+    const uint32_t* qmask;  // [nq] or null: only queries with qmask[q] != 0 are processed
+    int64_t* out_ids;       // [nq][k_stride] (two-pass form writes results directly)
+    float* out_dists;
+    int k_stride;
+    // two-pass form: per (query, id range) unit
+    int n_ranges;           // id ranges per query (= cluster size)
+    uint32_t* unit_ge;      // [nq][n_ranges][16] ids with SC >= j, j = 1..N_s
+    uint32_t* unit_off;     // [nq][n_ranges] start of the unit's entries in the arena
+    uint32_t* unit_len;     // [nq][n_ranges] entries (ids with SC >= 2)
+    uint32_t* arena;        // entries: id relative to the range | SC << 27
+    uint32_t* arena_used;   // [1] entries reserved so far
+    uint32_t arena_cap;
+    uint32_t* qflag;        // [nq] set when a query needs the cluster kernel
     uint8_t* dbg_sc;
     int64_t* dbg_hist;
     int32_t* dbg_last;
@@ -343,6 +356,157 @@ __device__ __forceinline__ void warp_merge(const float* ld, const uint32_t* li, 
     }
 }
 
+// Shared-memory state of the counting phase of one (query, id range) unit.
+struct CountSmem {
+    uint32_t* cnt;                 // 4-bit SC counters of the range
+    uint32_t* lst;                 // kRrWarps segments of kSegCap level entries
+    unsigned long long* cbeg;      // staged run starts
+    uint32_t* cpre;                // staged run prefix
+    uint32_t* ge;                  // [16] ids with SC >= j
+    int* s_pre;                    // prefix of probed cells per subspace
+    uint32_t* s_tmp;               // block-scan scratch
+    uint32_t* s_seg;               // entries per segment
+    uint32_t* s_segpre;            // prefix of segment sizes
+    uint32_t* s_app;               // segment overflow flag
+};
+
+// Count the collisions of query q in ids [lo, hi) (slabs [slab_lo, slab_hi)) into sm.cnt,
+// fill ge[1..N_s] and the level list. SC[id] += 1 for every id of every probed cell; the
+// nibble's old value v says the id just reached level v + 1. Ids reaching a level >= 2 are
+// appended to a per-warp list segment with that level, so every id with SC >= j >= 2 is
+// there exactly once tagged j; first touches (level 1) are counted per lane. Returns true
+// if a segment overflowed (then ge[2..] were counted from the counters). Block-wide; all
+// threads return after a barrier with s_pre set by the caller.
+__device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, int slab_lo, int slab_hi,
+                                            int64_t lo, int words, const CountSmem& sm, uint64_t pol_keep,
+                                            int tid, int lane, int warp) {
+    const int Ns = P.Ns;
+    const int total_cells = sm.s_pre[Ns];
+    const int nbatch = (total_cells + kCellBatch - 1) / kCellBatch;
+    {
+        uint32_t c1 = 0;
+        uint32_t wapp = 0;                          // entries this warp appended
+        uint32_t* wseg = sm.lst + warp * kSegCap;   // this warp's list segment
+        for (int bt = 0; bt < nbatch; ++bt) {
+            const int cb0 = bt * kCellBatch;
+            const int nb = min(kCellBatch, total_cells - cb0);
+            const uint32_t total = stage_cells(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.cbeg,
+                                               sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
+            // warp w walks a contiguous share [e0, e1) of the concatenated runs; lane l takes
+            // elements e0 + l + 32 u, 16 per round, so all loads of a round are in flight
+            // together; the lane's cell pointer only moves forward
+            const uint32_t chunk = ((total + kRrWarps - 1) / kRrWarps + 31) & ~31u;
+            const uint32_t e0 = uint32_t(warp) * chunk;
+            const uint32_t e1 = min(total, e0 + chunk);
+            int c = e0 < e1 ? find_cell(sm.cpre, nb, e0 + lane < e1 ? e0 + lane : e1 - 1) : 0;
+            for (uint32_t e = e0; e < e1; e += 32u * kWalkUnroll) {   // warp-uniform
+                uint32_t idv[kWalkUnroll];
+#pragma unroll
+                for (int u = 0; u < kWalkUnroll; ++u) {
+                    const uint32_t eu = e + lane + 32u * u;
+                    idv[u] = 0xffffffffu;
+                    if (eu < e1) {
+                        while (sm.cpre[c + 1] <= eu) ++c;
+                        idv[u] = ldg_keep_u32(P.ids + sm.cbeg[c] + (eu - sm.cpre[c]), pol_keep);
+                    }
+                }
+                // all counter atomics first (independent), then the ids that reached level
+                // >= 2 go to this warp's list segment (offsets by ballot)
+#pragma unroll
+                for (int u = 0; u < kWalkUnroll; ++u) {
+                    if (idv[u] != 0xffffffffu) {
+                        const uint32_t id = idv[u] - uint32_t(lo);
+                        const uint32_t sh = (id & 7u) << 2;
+                        const uint32_t v = (atomicAdd(&sm.cnt[id >> 3], 1u << sh) >> sh) & 15u;
+                        c1 += v == 0u;
+                        idv[u] = v != 0u ? (id | ((v + 1u) << kLevelShift)) : 0u;
+                    } else {
+                        idv[u] = 0u;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kWalkUnroll; ++u) {
+                    const unsigned bal = __ballot_sync(kFull, idv[u] != 0u);
+                    const uint32_t at = wapp + __popc(bal & ((1u << lane) - 1u));
+                    if (idv[u] && at < uint32_t(kSegCap)) wseg[at] = idv[u];
+                    wapp += __popc(bal);
+                }
+            }
+            if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
+        }
+        const uint32_t t1 = __reduce_add_sync(kFull, c1);
+        if (lane == 0) {
+            if (t1) atomicAdd(&sm.ge[1], t1);
+            sm.s_seg[warp] = wapp;
+            if (wapp > uint32_t(kSegCap)) *sm.s_app = 1u;   // a segment overflowed
+        }
+    }
+    __syncthreads();
+    const bool overflow = *sm.s_app != 0u;
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int w = 0; w < kRrWarps; ++w) {
+            sm.s_segpre[w] = acc;
+            acc += min(sm.s_seg[w], uint32_t(kSegCap));
+        }
+        sm.s_segpre[kRrWarps] = acc;
+    }
+    __syncthreads();
+    const int napp = int(sm.s_segpre[kRrWarps]);
+    if (!overflow) {
+        for (int e = tid; e < napp; e += kRrThreads) {
+            int w = 0;
+            while (uint32_t(e) >= sm.s_segpre[w + 1]) ++w;
+            atomicAdd(&sm.ge[sm.lst[w * kSegCap + (e - int(sm.s_segpre[w]))] >> kLevelShift], 1u);
+        }
+    } else {
+        // a segment overflowed: count the levels from the counters themselves
+        uint32_t gel[TACO_MAX_SUBSPACES];
+#pragma unroll
+        for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
+        for (int w = tid; w < words; w += kRrThreads) {
+            const uint32_t x = sm.cnt[w];
+            if (x == 0u) continue;
+            const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
+#pragma unroll
+            for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+                if (j <= Ns) {
+                    const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
+                    gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+            if (j <= Ns) {
+                const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
+                if (lane == 0 && v) atomicAdd(&sm.ge[j], v);
+            }
+        }
+    }
+    __syncthreads();
+    return overflow;
+}
+
+// Entry e of the concatenated list segments.
+__device__ __forceinline__ uint32_t seg_entry(const CountSmem& sm, int e) {
+    int w = 0;
+    while (uint32_t(e) >= sm.s_segpre[w + 1]) ++w;
+    return sm.lst[w * kSegCap + (e - int(sm.s_segpre[w]))];
+}
+
+// Debug: the SC of every touched id of the range (untouched ids stay at the caller's zero).
+__device__ __forceinline__ void debug_sc(const RerankParams& P, int64_t q, int64_t lo, int64_t hi,
+                                        int words, const uint32_t* cnt, int tid) {
+    for (int w = tid; w < words; w += kRrThreads) {
+        const uint32_t x = cnt[w];
+        if (!x) continue;
+        const int64_t id0 = lo + (int64_t(w) << 3);
+        for (int j = 0; j < 8 && id0 + j < hi; ++j)
+            if ((x >> (4 * j)) & 15u) P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (4 * j)) & 15u);
+    }
+}
+
 // G lanes per candidate, R registers per lane of top list, BF16 rows or FP32 rows.
 // Persistent: the clusters of the grid take queries blockIdx.y, blockIdx.y + gridDim.y, ...
 template <int G, int R, bool BF16>
@@ -386,6 +550,16 @@ count_select_rerank_kernel(const RerankParams P) {
                                      : reinterpret_cast<const unsigned char*>(P.data);
     const int kk = P.kk;
     const uint64_t pol_keep = l2_policy_keep(), pol_stream = l2_policy_stream();
+    CountSmem csm;
+    csm.cnt = cnt;
+    csm.lst = lst;
+    csm.cbeg = cbeg;
+    csm.cpre = cpre;
+    csm.s_pre = s_pre;
+    csm.s_tmp = s_tmp;
+    csm.s_seg = s_seg;
+    csm.s_segpre = s_segpre;
+    csm.s_app = &s_app;
 
     // counters start at zero; every query leaves them at zero again
     for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
@@ -393,9 +567,11 @@ count_select_rerank_kernel(const RerankParams P) {
 
     int par = 0;
     for (int64_t q = blockIdx.y; q < P.nq; q += gridDim.y, par ^= 1) {
+        if (P.qmask && !P.qmask[q]) continue;   // same decision in every CTA of the cluster
         const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
         uint32_t* ge = ge2 + 16 * par;
         uint32_t* s_allge = s_allge2[par];
+        csm.ge = ge;
         __syncthreads();   // the previous query's readers of qv / s_pre / lists are done
         for (int j = tid; j < P.d_pad; j += kRrThreads)
             qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
@@ -411,119 +587,11 @@ count_select_rerank_kernel(const RerankParams P) {
             s_bufn = 0u;
         }
         __syncthreads();
-        const int total_cells = s_pre[Ns];
-        const int nbatch = (total_cells + kCellBatch - 1) / kCellBatch;
 
-        // ---- 1. count: SC[id] += 1 for every id of every probed cell in this CTA's range.
-        // The nibble's old value v says the id just reached level v + 1. Ids reaching a
-        // level >= 2 are appended to `lst` with that level: every id with SC >= j >= 2 is
-        // there exactly once tagged j, which gives both the level counts and, once Alg. 5
-        // has chosen j, the candidates. First touches (level 1) are counted per lane.
-        {
-            uint32_t c1 = 0;
-            uint32_t wapp = 0;                       // entries this warp appended
-            uint32_t* wseg = lst + warp * kSegCap;   // this warp's list segment
-            for (int bt = 0; bt < nbatch; ++bt) {
-                const int cb0 = bt * kCellBatch;
-                const int nb = min(kCellBatch, total_cells - cb0);
-                const uint32_t total = stage_cells(P, q, s_pre, cb0, nb, slab_lo, slab_hi, cbeg, cpre,
-                                                   s_tmp, tid, lane, warp, pol_keep);
-                // warp w walks a contiguous share [e0, e1) of the concatenated runs; lane l
-                // takes elements e0 + l + 32 u, 16 per round, so all loads of a round are
-                // in flight together; the lane's cell pointer only moves forward
-                const uint32_t chunk = ((total + kRrWarps - 1) / kRrWarps + 31) & ~31u;
-                const uint32_t e0 = uint32_t(warp) * chunk;
-                const uint32_t e1 = min(total, e0 + chunk);
-                int c = e0 < e1 ? find_cell(cpre, nb, e0 + lane < e1 ? e0 + lane : e1 - 1) : 0;
-                for (uint32_t e = e0; e < e1; e += 32u * kWalkUnroll) {   // warp-uniform
-                    uint32_t idv[kWalkUnroll];
-#pragma unroll
-                    for (int u = 0; u < kWalkUnroll; ++u) {
-                        const uint32_t eu = e + lane + 32u * u;
-                        idv[u] = 0xffffffffu;
-                        if (eu < e1) {
-                            while (cpre[c + 1] <= eu) ++c;
-                            idv[u] = ldg_keep_u32(P.ids + cbeg[c] + (eu - cpre[c]), pol_keep);
-                        }
-                    }
-                    // all counter atomics first (independent), then the ids that reached
-                    // level >= 2 go to this warp's list segment (offsets by ballot)
-#pragma unroll
-                    for (int u = 0; u < kWalkUnroll; ++u) {
-                        if (idv[u] != 0xffffffffu) {
-                            const uint32_t id = idv[u] - uint32_t(lo);
-                            const uint32_t sh = (id & 7u) << 2;
-                            const uint32_t v = (atomicAdd(&cnt[id >> 3], 1u << sh) >> sh) & 15u;
-                            c1 += v == 0u;
-                            idv[u] = v != 0u ? (id | ((v + 1u) << kLevelShift)) : 0u;
-                        } else {
-                            idv[u] = 0u;
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < kWalkUnroll; ++u) {
-                        const unsigned bal = __ballot_sync(kFull, idv[u] != 0u);
-                        const uint32_t at = wapp + __popc(bal & ((1u << lane) - 1u));
-                        if (idv[u] && at < uint32_t(kSegCap)) wseg[at] = idv[u];
-                        wapp += __popc(bal);
-                    }
-                }
-                if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
-            }
-            const uint32_t t1 = __reduce_add_sync(kFull, c1);
-            if (lane == 0) {
-                if (t1) atomicAdd(&ge[1], t1);
-                s_seg[warp] = wapp;
-                if (wapp > uint32_t(kSegCap)) s_app = 1u;   // a segment overflowed
-            }
-        }
-        __syncthreads();
-        const bool overflow = s_app != 0u;
-        if (tid == 0) {
-            uint32_t acc = 0;
-            for (int w = 0; w < kRrWarps; ++w) {
-                s_segpre[w] = acc;
-                acc += min(s_seg[w], uint32_t(kSegCap));
-            }
-            s_segpre[kRrWarps] = acc;
-        }
-        __syncthreads();
+        // ---- 1. count the collisions of the probed cells' ids in this CTA's range
+        const bool overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
         const int napp = int(s_segpre[kRrWarps]);
-        // entry e of the concatenated segments
-        auto seg_entry = [&](int e) {
-            int w = 0;
-            while (uint32_t(e) >= s_segpre[w + 1]) ++w;
-            return lst[w * kSegCap + (e - int(s_segpre[w]))];
-        };
-        if (!overflow) {
-            for (int e = tid; e < napp; e += kRrThreads) atomicAdd(&ge[seg_entry(e) >> kLevelShift], 1u);
-        } else {
-            // the list overflowed: count the levels from the counters themselves
-            uint32_t gel[TACO_MAX_SUBSPACES];
-#pragma unroll
-            for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
-            for (int w = tid; w < words; w += kRrThreads) {
-                const uint32_t x = cnt[w];
-                if (x == 0u) continue;
-                const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
-#pragma unroll
-                for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
-                    if (j <= Ns) {
-                        const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
-                        gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
-                if (j <= Ns) {
-                    const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
-                    if (lane == 0 && v) atomicAdd(&ge[j], v);
-                }
-            }
-        }
         // push this CTA's level counts into row `cta` of every CTA's table
-        __syncthreads();
         if (tid < ncta * Ns) {
             const int r = tid / Ns, j = tid - r * Ns + 1;
             cluster.map_shared_rank(s_allge, r)[cta * 16 + j] = ge[j];
@@ -594,19 +662,13 @@ count_select_rerank_kernel(const RerankParams P) {
         };
         const uint32_t mine = last >= 1 ? s_allge[cta * 16 + last] : 0u;   // ids with SC >= last
         if (P.dbg_sc && last >= 1) {
-            for (int w = tid; w < words; w += kRrThreads) {
-                const uint32_t x = cnt[w];
-                if (!x) continue;
-                const int64_t id0 = lo + (int64_t(w) << 3);
-                for (int j = 0; j < 8 && id0 + j < hi; ++j)
-                    if ((x >> (4 * j)) & 15u) P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (4 * j)) & 15u);
-            }
+            debug_sc(P, q, lo, hi, words, cnt, tid);
             __syncthreads();   // every counter is read before any is cleared below
         }
         if (last >= 2 && !overflow && mine <= uint32_t(P.buf_cap)) {
             // the candidates are the list entries tagged `last`
             for (int e = tid; e < napp; e += kRrThreads) {
-                const uint32_t x = seg_entry(e);
+                const uint32_t x = seg_entry(csm, e);
                 if (int(x >> kLevelShift) == last)
                     buf[atomicAdd(&s_bufn, 1u)] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
             }
@@ -707,6 +769,294 @@ count_select_rerank_kernel(const RerankParams P) {
     cluster.sync();   // no CTA leaves while another may still write its level table
 }
 
+// ---------------------------------------------------------------------------------------
+// Two-pass form. Pass 1 (count_lists_kernel): persistent CTAs take (query, id range) units;
+// each counts the unit's collisions in shared memory and writes the unit's level counts and
+// the compact list of its ids with SC >= 2 (id relative to the range | SC << 27) to global
+// memory. Pass 2 (select_rerank_kernel): one CTA per query sums the level counts of its
+// ranges, applies Alg. 5, keeps the list entries with SC >= last_collision and re-ranks
+// them. Queries whose threshold falls below 2, or whose lists did not fit, are flagged for
+// the cluster kernel above.
+// ---------------------------------------------------------------------------------------
+#ifdef TACO_DEFINE_COUNT_LISTS   // defined by the one translation unit that launches it
+__global__ void __launch_bounds__(kRrThreads, 2)
+count_lists_kernel(const RerankParams P) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* lst = reinterpret_cast<uint32_t*>(smem + P.region_a);          // kListCap
+    unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);
+    uint32_t* cpre = reinterpret_cast<uint32_t*>(cbeg + kCellBatch);        // kCellBatch + 1
+    uint32_t* ge = cpre + kCellBatch + 4;                                    // [16]
+    __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
+    __shared__ uint32_t s_tmp[kRrWarps];
+    __shared__ uint32_t s_seg[kRrWarps];
+    __shared__ uint32_t s_segpre[kRrWarps + 1];
+    __shared__ uint32_t s_app, s_outn, s_base;
+    CountSmem csm{cnt, lst, cbeg, cpre, ge, s_pre, s_tmp, s_seg, s_segpre, &s_app};
+    const int Ns = P.Ns;
+    const uint64_t pol_keep = l2_policy_keep();
+    for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
+    const int64_t units = P.nq * P.n_ranges;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int64_t q = u / P.n_ranges;
+        const int r = int(u - q * P.n_ranges);
+        const int slab_lo = r * P.slabs_per_cta;
+        const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
+        const int64_t lo = int64_t(slab_lo) << kSlabLog2;
+        const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
+        const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
+        __syncthreads();   // the previous unit is finished with the shared state
+        if (tid < 16) ge[tid] = 0u;
+        if (tid == 0) {
+            int acc = 0;
+            s_pre[0] = 0;
+            for (int i = 0; i < Ns; ++i) {
+                acc += P.ncells[q * Ns + i];
+                s_pre[i + 1] = acc;
+            }
+            s_app = 0u;
+            s_outn = 0u;
+        }
+        __syncthreads();
+        const bool overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
+        const int napp = int(s_segpre[kRrWarps]);
+        if (P.dbg_sc) debug_sc(P, q, lo, hi, words, cnt, tid);
+        // reserve the unit's entries: ids with SC >= 2 number ge[2]
+        if (tid == 0) {
+            const uint32_t need = overflow ? 0u : ge[2];
+            uint32_t base = 0xffffffffu;
+            if (!overflow) {
+                base = atomicAdd(P.arena_used, need);
+                if (base > P.arena_cap || need > P.arena_cap - base) base = 0xffffffffu;
+            }
+            s_base = base;
+            P.unit_off[u] = base;
+            P.unit_len[u] = base == 0xffffffffu ? 0u : need;
+            if (base == 0xffffffffu) P.qflag[q] = 1u;   // list lost: the query takes the cluster path
+        }
+        if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
+        __syncthreads();
+        const uint32_t base = s_base;
+        if (base != 0xffffffffu) {
+            // an id's final SC is its counter; its entry tagged with that level is unique
+            for (int e = tid; e < napp; e += kRrThreads) {
+                const uint32_t x = seg_entry(csm, e);
+                const uint32_t id = x & ((1u << kLevelShift) - 1u);
+                const uint32_t sc = (cnt[id >> 3] >> ((id & 7u) << 2)) & 15u;
+                if ((x >> kLevelShift) == sc) P.arena[base + atomicAdd(&s_outn, 1u)] = x;
+            }
+        }
+        __syncthreads();
+        uint4* c4 = reinterpret_cast<uint4*>(cnt);
+        for (int w = tid; w < (words + 3) / 4; w += kRrThreads) c4[w] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+#endif  // TACO_DEFINE_COUNT_LISTS
+
+constexpr int kSrThreads = 256;
+constexpr int kSrWarps = kSrThreads / 32;
+constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
+
+template <int G, int R, bool BF16>
+__global__ void __launch_bounds__(kSrThreads)
+select_rerank_kernel(const RerankParams P) {
+    constexpr int CPW = 32 / G;
+    constexpr int U = 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int kkc = P.kkc;
+    float* Ld = reinterpret_cast<float*>(smem);                        // [kSrWarps][kkc]
+    uint32_t* Li = reinterpret_cast<uint32_t*>(Ld + kSrWarps * kkc);    // [kSrWarps][kkc]
+    float* Md = reinterpret_cast<float*>(Li + kSrWarps * kkc);          // [kkc] merged
+    uint32_t* Mi = reinterpret_cast<uint32_t*>(Md + kkc);
+    float* Xd = reinterpret_cast<float*>(Mi + kkc);                     // [kkc] exact (BF16)
+    uint32_t* Xi = reinterpret_cast<uint32_t*>(Xd + kkc);
+    float* qv = reinterpret_cast<float*>(Xi + kkc);                     // d_pad
+    uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);          // kSrBuf
+    __shared__ uint32_t s_gs[TACO_MAX_SUBSPACES + 2];
+    __shared__ int s_last;
+    __shared__ uint32_t s_bufn;
+    __shared__ uint32_t s_flag;
+    const int Ns = P.Ns, nr = P.n_ranges, kk = P.kk;
+    const int gid = lane / G, gl = lane % G;
+    const int nch = P.d_pad / RowChunk<BF16>::kElems;
+    const size_t row_bytes = size_t(P.d_pad) * (BF16 ? 2 : 4);
+    const unsigned char* rows = BF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
+                                     : reinterpret_cast<const unsigned char*>(P.data);
+    const uint64_t pol_stream = l2_policy_stream();
+    for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+        const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
+        __syncthreads();
+        for (int j = tid; j < P.d_pad; j += kSrThreads) qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
+        if (tid <= TACO_MAX_SUBSPACES + 1) s_gs[tid] = 0u;
+        if (tid == 0) {
+            s_bufn = 0u;
+            s_flag = P.qflag[q];
+        }
+        __syncthreads();
+        // Alg. 5 over the summed level counts of the query's ranges
+        if (tid < Ns) {
+            uint32_t v = 0;
+            for (int r = 0; r < nr; ++r) v += P.unit_ge[(q * nr + r) * 16 + tid + 1];
+            s_gs[tid + 1] = v;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long gs[TACO_MAX_SUBSPACES + 2];
+            gs[0] = P.n;
+            for (int j = 1; j <= Ns; ++j) gs[j] = s_gs[j];
+            gs[Ns + 1] = 0;
+            int last = Ns;
+            long long cand = 0;
+            for (int j = Ns; j >= 0; --j) {
+                const long long h = gs[j] - gs[j + 1];
+                cand += h;
+                const bool go = qp.select_rule == TACO_SELECT_LITERAL ? (h <= qp.rerank_target - cand)
+                                                                     : (cand <= qp.rerank_target);
+                if (go) --last;
+                else break;
+            }
+            s_last = last;
+            if (P.dbg_hist)
+                for (int j = 0; j <= Ns; ++j) P.dbg_hist[q * (Ns + 1) + j] = gs[j] - gs[j + 1];
+            if (P.dbg_last) P.dbg_last[q] = last;
+            if (P.dbg_cand) P.dbg_cand[q] = cand;
+            if (last < 2) {
+                s_flag = 1u;
+                P.qflag[q] = 1u;   // candidates below level 2 are not in the lists
+            }
+        }
+        __syncthreads();
+        if (s_flag) continue;   // answered by the cluster kernel
+        const int last = s_last;
+        WarpTop<R> top;
+        top.init();
+        float kth_d = __int_as_float(0x7f800000);
+        uint32_t kth_i = kNoId;
+        auto rerank_buffer = [&](int m) {
+            for (int b0 = warp * CPW * U; b0 < m; b0 += kSrWarps * CPW * U) {
+                float acc[U];
+                uint32_t cid[U];
+                bool val[U];
+                gather_distances<G, BF16>(rows, row_bytes, nch, qv, buf, b0, m, acc, cid, val, gid, gl,
+                                          pol_stream);
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                    const bool better = val[uu] && gl == 0 && lt_pair(acc[uu], cid[uu], kth_d, kth_i);
+                    unsigned bal = __ballot_sync(kFull, better);
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const float x = __shfl_sync(kFull, acc[uu], src);
+                        const uint32_t xi = __shfl_sync(kFull, cid[uu], src);
+                        if (lt_pair(x, xi, kth_d, kth_i)) {
+                            top.insert(x, xi, kk, lane);
+                            top.kth(kk, kth_d, kth_i);
+                        }
+                    }
+                }
+            }
+        };
+        // candidates: list entries with SC >= last, range by range, in tiles of kSrThreads;
+        // the buffer is re-ranked and emptied before a tile that would not fit
+        for (int r = 0; r < nr; ++r) {
+            const uint32_t off = P.unit_off[q * nr + r], len = P.unit_len[q * nr + r];
+            const uint32_t rlo = uint32_t(int64_t(r * P.slabs_per_cta) << kSlabLog2);
+            for (uint32_t t0 = 0; t0 < len; t0 += kSrThreads) {
+                if (s_bufn + kSrThreads > uint32_t(kSrBuf)) {
+                    __syncthreads();
+                    rerank_buffer(int(s_bufn));
+                    __syncthreads();
+                    if (tid == 0) s_bufn = 0u;
+                    __syncthreads();
+                }
+                const uint32_t t = t0 + tid;
+                if (t < len) {
+                    const uint32_t x = P.arena[off + t];
+                    if (int(x >> kLevelShift) >= last)
+                        buf[atomicAdd(&s_bufn, 1u)] = rlo + (x & ((1u << kLevelShift) - 1u));
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        rerank_buffer(int(s_bufn));
+        // warp lists -> one sorted list
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            const int e = rr * 32 + lane;
+            if (e < kk) {
+                Ld[warp * kkc + e] = top.d[rr];
+                Li[warp * kkc + e] = top.i[rr];
+            }
+        }
+        __syncthreads();
+        if (warp == 0) warp_merge(Ld, Li, kkc, kSrWarps, kk, Md, Mi, lane);
+        __syncthreads();
+        if constexpr (BF16) {
+            // exact FP32 distances of the shortlist, then rank sort by (distance, id)
+            const int nf4 = P.d_pad / 4;
+            const float4* q4 = reinterpret_cast<const float4*>(qv);
+            for (int e = warp; e < kk; e += kSrWarps) {
+                const uint32_t id = Mi[e];
+                float acc = 0.f;
+                if (id != kNoId) {
+                    const float4* row = reinterpret_cast<const float4*>(P.data + size_t(id) * P.d_pad);
+                    for (int f = lane; f < nf4; f += 32) acc = sq4(__ldg(row + f), q4[f], acc);
+                }
+#pragma unroll
+                for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+                if (lane == 0) {
+                    Xd[e] = id != kNoId ? acc : __int_as_float(0x7f800000);
+                    Xi[e] = id;
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < kk; e += kSrThreads) {
+                const float x = Xd[e];
+                const uint32_t xid = Xi[e];
+                int rank = 0;
+                for (int f = 0; f < kk; ++f)
+                    rank += lt_pair(Xd[f], Xi[f], x, xid) || (Xd[f] == x && Xi[f] == xid && f < e);
+                Md[rank] = x;
+                Mi[rank] = xid;
+            }
+            __syncthreads();
+        }
+        for (int t = tid; t < P.k_stride; t += kSrThreads) {
+            const bool ok = t < qp.k && t < kk && Mi[t] != kNoId;
+            P.out_ids[q * P.k_stride + t] = ok ? int64_t(Mi[t]) : int64_t(-1);
+            P.out_dists[q * P.k_stride + t] = ok ? sqrtf(Md[t]) : __int_as_float(0x7f800000);
+        }
+    }
+}
+
+template <int G, int R, bool BF16>
+cudaError_t launch_select_rerank_t(const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
+    auto kern = select_rerank_kernel<G, R, BF16>;
+    static thread_local size_t cached_smem = 0;
+    static thread_local int cached_blocks = 0;
+    cudaError_t e;
+    if (cached_smem != smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSrThreads, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached_blocks = per_sm * sms;
+        cached_smem = smem;
+        if (cached_blocks < 1) return cudaErrorInvalidConfiguration;
+    }
+    const int64_t blocks = nq < cached_blocks ? nq : cached_blocks;
+    kern<<<unsigned(blocks), kSrThreads, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
 template <int G, int R, bool BF16>
 cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size_t smem,
                             cudaStream_t st) {
@@ -762,7 +1112,9 @@ cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size
 // One translation unit per (row type, R) instantiates the four G variants.
 #define TACO_DECLARE_RERANK(B, R)                                                            \
     cudaError_t launch_rerank_b##B##_r##R(int G, const RerankParams& P, int cluster, int64_t nq, \
-                                          size_t smem, cudaStream_t st);
+                                          size_t smem, cudaStream_t st);                         \
+    cudaError_t launch_select_b##B##_r##R(int G, const RerankParams& P, int64_t nq, size_t smem,  \
+                                          cudaStream_t st);
 TACO_DECLARE_RERANK(0, 1)
 TACO_DECLARE_RERANK(0, 4)
 TACO_DECLARE_RERANK(0, 16)

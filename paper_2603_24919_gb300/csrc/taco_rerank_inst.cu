@@ -12,6 +12,7 @@
 #define TACO_CAT_(a, b, c, d) a##b##c##d
 #define TACO_CAT(a, b, c, d) TACO_CAT_(a, b, c, d)
 #define TACO_FN TACO_CAT(launch_rerank_b, TACO_INST_BF16, _r, TACO_INST_R)
+#define TACO_FN2 TACO_CAT(launch_select_b, TACO_INST_BF16, _r, TACO_INST_R)
 
 namespace taco {
 
@@ -23,6 +24,17 @@ cudaError_t TACO_FN(int G, const RerankParams& P, int cluster, int64_t nq, size_
         case 8: return launch_rerank_t<8, TACO_INST_R, kBf16>(P, cluster, nq, smem, st);
         case 16: return launch_rerank_t<16, TACO_INST_R, kBf16>(P, cluster, nq, smem, st);
         case 32: return launch_rerank_t<32, TACO_INST_R, kBf16>(P, cluster, nq, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t TACO_FN2(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
+    constexpr bool kBf16 = TACO_INST_BF16 != 0;
+    switch (G) {
+        case 4: return launch_select_rerank_t<4, TACO_INST_R, kBf16>(P, nq, smem, st);
+        case 8: return launch_select_rerank_t<8, TACO_INST_R, kBf16>(P, nq, smem, st);
+        case 16: return launch_select_rerank_t<16, TACO_INST_R, kBf16>(P, nq, smem, st);
+        case 32: return launch_select_rerank_t<32, TACO_INST_R, kBf16>(P, nq, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }

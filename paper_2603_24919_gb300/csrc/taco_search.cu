@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "taco_internal.h"
+#define TACO_DEFINE_COUNT_LISTS
 #include "taco_rerank.cuh"
 
 namespace taco {
@@ -422,12 +423,14 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
                    int ncta, int kk, int kkc, const float* __restrict__ queries, int d, int d_pad,
                    const float* __restrict__ data, QueryParamsDev defaults,
                    const QueryParamsDev* __restrict__ params, int64_t nq,
-                   int64_t* __restrict__ out_ids, float* __restrict__ out_dists, int k_stride) {
+                   int64_t* __restrict__ out_ids, float* __restrict__ out_dists, int k_stride,
+                   const uint32_t* __restrict__ qmask) {
     extern __shared__ __align__(16) unsigned char fm[];
     const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = int64_t(blockIdx.x) * nw + warp;
     if (q >= nq) return;
+    if (qmask && !qmask[q]) return;
     const size_t per_warp = size_t(ncta) * kkc * 8 + size_t(4) * kkc * 4 + size_t(d_pad) * 4;
     float* cd = reinterpret_cast<float*>(fm + warp * per_warp);   // [ncta][kkc]
     uint32_t* ci = reinterpret_cast<uint32_t*>(cd + ncta * kkc);  // [ncta][kkc]
@@ -633,19 +636,73 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
         P.lists_d = L.lists_d;
         P.lists_i = L.lists_i;
+        P.out_ids = L.out_ids;
+        P.out_dists = L.out_dists;
+        P.k_stride = L.k_stride;
         P.dbg_sc = L.dbg.sc;
         P.dbg_hist = L.dbg.collision_num;
         P.dbg_last = L.dbg.last_collision;
         P.dbg_cand = L.dbg.candidate_num;
-        if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
-        // counters | merge lists | query | candidate buffer | staged runs | level counts
         P.buf_cap = kBufCap;
-        const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
-                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
+        P.n_ranges = ix->cluster;
+        if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
+        const bool two_pass = L.unit_ge != nullptr;
+        if (two_pass) {
+            P.unit_ge = L.unit_ge;
+            P.unit_off = L.unit_off;
+            P.unit_len = L.unit_len;
+            P.arena = L.arena;
+            P.arena_cap = L.arena_cap;
+            P.arena_used = L.arena_used;
+            P.qflag = L.qflag;
+            TACO_CUDA(cudaMemsetAsync(L.arena_used, 0, sizeof(uint32_t), st));
+            TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
+            // pass 1: counting per (query, id range) unit
+            const size_t smem1 = P.region_a + size_t(kListCap) * 4 + size_t(kCellBatch) * 8 +
+                                 size_t(kCellBatch + 4) * 4 + 16 * 4;
+            static thread_local size_t c1_smem = 0;
+            static thread_local int c1_blocks = 0;
+            if (c1_smem != smem1) {
+                TACO_CUDA(cudaFuncSetAttribute(count_lists_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(smem1)));
+                int per_sm = 0, sms = 0;
+                TACO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, count_lists_kernel, kRrThreads,
+                                                                        smem1));
+                TACO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
+                if (per_sm < 1) return fail(TACO_ECAPACITY, "count_lists_kernel does not fit an SM");
+                c1_blocks = per_sm * sms;
+                c1_smem = smem1;
+            }
+            const int64_t units = L.nq * ix->cluster;
+            if (int rc = prof_begin(ix, 2, st, &pb, &pe)) return rc;
+            count_lists_kernel<<<unsigned(std::min<int64_t>(units, c1_blocks)), kRrThreads, smem1, st>>>(P);
+            TACO_CUDA(cudaGetLastError());
+            if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
+            // pass 2: Alg. 5, candidates, re-rank, results
+            const size_t smem2 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 +
+                                 size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4;
+            cudaError_t e;
+            if (int rc = prof_begin(ix, 3, st, &pb, &pe)) return rc;
+            if (!bf16) {
+                e = R == 1 ? launch_select_b0_r1(G, P, L.nq, smem2, st)
+                    : R == 4 ? launch_select_b0_r4(G, P, L.nq, smem2, st)
+                             : launch_select_b0_r16(G, P, L.nq, smem2, st);
+            } else {
+                e = R == 1 ? launch_select_b1_r1(G, P, L.nq, smem2, st)
+                    : R == 4 ? launch_select_b1_r4(G, P, L.nq, smem2, st)
+                             : launch_select_b1_r16(G, P, L.nq, smem2, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "select_rerank launch", __FILE__, __LINE__);
+            if (int rc = prof_end(ix, 3, st, pb, pe)) return rc;
+            P.qmask = L.qflag;   // the cluster kernel below only answers flagged queries
+        }
+        // cluster kernel: every query (single-pass form) or the flagged ones
+        const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
+                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
         cudaError_t e;
-        if (int rc = prof_begin(ix, 2, st, &pb, &pe)) return rc;
+        if (int rc = prof_begin(ix, 4, st, &pb, &pe)) return rc;
         if (!bf16) {
             e = R == 1 ? launch_rerank_b0_r1(G, P, ix->cluster, L.nq, smem, st)
                 : R == 4 ? launch_rerank_b0_r4(G, P, ix->cluster, L.nq, smem, st)
@@ -656,8 +713,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                          : launch_rerank_b1_r16(G, P, ix->cluster, L.nq, smem, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "count_select_rerank launch", __FILE__, __LINE__);
-        if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
-        // 4. per-query merge of the cluster's lists (and BF16 shortlist re-rank)
+        if (int rc = prof_end(ix, 4, st, pb, pe)) return rc;
+        // merge of the cluster kernel's lists (and BF16 shortlist re-rank)
         const size_t per_warp = size_t(ix->cluster) * P.kkc * 8 + size_t(4) * P.kkc * 4 + size_t(ix->d_pad) * 4;
         int fw = 8;
         while (fw > 1 && size_t(fw) * per_warp > 160 * 1024) fw >>= 1;
@@ -665,12 +722,12 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         auto fk = bf16 ? final_merge_kernel<true> : final_merge_kernel<false>;
         if (fsm > 48 * 1024)
             TACO_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
-        if (int rc = prof_begin(ix, 3, st, &pb, &pe)) return rc;
+        if (int rc = prof_begin(ix, 5, st, &pb, &pe)) return rc;
         fk<<<unsigned((L.nq + fw - 1) / fw), fw * 32, fsm, st>>>(
             L.lists_d, L.lists_i, ix->cluster, P.kk, P.kkc, L.queries, ix->d, ix->d_pad, ix->d_data,
-            L.defaults, L.params, L.nq, L.out_ids, L.out_dists, L.k_stride);
+            L.defaults, L.params, L.nq, L.out_ids, L.out_dists, L.k_stride, P.qmask);
         TACO_CUDA(cudaGetLastError());
-        if (int rc = prof_end(ix, 3, st, pb, pe)) return rc;
+        if (int rc = prof_end(ix, 5, st, pb, pe)) return rc;
     }
     return TACO_OK;
 }

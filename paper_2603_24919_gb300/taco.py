@@ -55,8 +55,9 @@ class DebugOut(C.Structure):
                 ("last_collision", C.c_void_p), ("candidate_num", C.c_void_p)]
 
 
-NUM_KERNELS = 4
-KERNEL_NAMES = ("project", "probe_cells", "count_select_rerank", "final_merge")
+NUM_KERNELS = 6
+KERNEL_NAMES = ("project", "probe_cells", "count_lists", "select_rerank", "cluster_count_select",
+                "final_merge")
 
 
 class KernelTimes(C.Structure):
