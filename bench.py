@@ -474,9 +474,9 @@ def run_reference(args):
         codes[i] = a1 * w.sqrt_k + a2
     oix = O.index_from_parts(mu, B, cent, codes, w.n_subspaces, w.sub_dim, w.sqrt_k)
     log(f"[reference] oracle index built in {time.time() - t0:.1f}s")
-    # the FP32 form's usual operating point on this workload (GPU calibration: alpha .02,
-    # beta .001); the oracle is not calibrated itself
-    alpha, beta = (args.alpha or 0.02), (args.beta or 0.001)
+    # the operating point the GPU calibration selects on this workload (alpha 0.01,
+    # beta 0.001); the oracle is not calibrated itself
+    alpha, beta = (args.alpha or 0.01), (args.beta or 0.001)
     bud, tgt = budget_from_alpha(alpha, w.n), target_from_beta(beta, w.n)
     per_step = max(1, int(os.environ.get("TACO_REF_QUERIES_PER_STEP", "4")))
     qi = 0

@@ -62,6 +62,8 @@ int check_geometry(int64_t n, int d, int Ns, int s, int sk) {
         return fail(TACO_EINVAL, "n_subspaces = %d must be in [1, %d]", Ns, TACO_MAX_SUBSPACES);
     if (s < 2) return fail(TACO_EINVAL, "sub_dim = %d must be >= 2", s);
     if (int64_t(Ns) * s > d) return fail(TACO_EINVAL, "n_subspaces * sub_dim > d");
+    if (int64_t(Ns) * n >= (int64_t(1) << 32))
+        return fail(TACO_ECAPACITY, "n_subspaces * n must be below 2^32 (32-bit id-list offsets)");
     if (sk < 1 || sk > TACO_MAX_SQRT_K)
         return fail(TACO_EINVAL, "sqrt_k = %d must be in [1, %d]", sk, TACO_MAX_SQRT_K);
     return TACO_OK;

@@ -282,11 +282,11 @@ constexpr int kWalkUnroll = 16;    // id loads in flight per lane while counting
 constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
 
 // Stage the id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
-// [slab_lo, slab_hi): cbeg[t] = absolute start in the id array, cpre = exclusive prefix
-// of the run lengths (cpre[nb] = total). Block-wide; ends with a barrier.
+// [slab_lo, slab_hi): cbeg[t] = absolute start in the id array (N_s * n < 2^32), cpre =
+// exclusive prefix of the run lengths (cpre[nb] = total). Block-wide; ends with a barrier.
 __device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
                                                 int cb0, int nb, int slab_lo, int slab_hi,
-                                                unsigned long long* cbeg, uint32_t* cpre,
+                                                uint32_t* cbeg, uint32_t* cpre,
                                                 uint32_t* s_tmp, int tid, int lane, int warp,
                                                 uint64_t keep) {
     const int Ns = P.Ns, K = P.K;
@@ -299,7 +299,7 @@ __device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q
         const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
         const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
         const uint32_t b = ldg_keep_u32(sp + slab_lo, keep), e = ldg_keep_u32(sp + slab_hi, keep);
-        cbeg[tid] = (unsigned long long)i * (unsigned long long)P.n + b;
+        cbeg[tid] = uint32_t(i) * uint32_t(P.n) + b;
         len = e - b;
     }
     uint32_t total;
@@ -360,7 +360,7 @@ __device__ __forceinline__ void warp_merge(const float* ld, const uint32_t* li, 
 struct CountSmem {
     uint32_t* cnt;                 // 4-bit SC counters of the range
     uint32_t* lst;                 // kRrWarps segments of kSegCap level entries
-    unsigned long long* cbeg;      // staged run starts
+    uint32_t* cbeg;                // staged run starts
     uint32_t* cpre;                // staged run prefix
     uint32_t* ge;                  // [16] ids with SC >= j
     int* s_pre;                    // prefix of probed cells per subspace
@@ -399,6 +399,9 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
             const uint32_t e0 = uint32_t(warp) * chunk;
             const uint32_t e1 = min(total, e0 + chunk);
             int c = e0 < e1 ? find_cell(sm.cpre, nb, e0 + lane < e1 ? e0 + lane : e1 - 1) : 0;
+            // the lane's current cell: where its run ends and the id-array index of element 0
+            uint32_t nxt = sm.cpre[c + 1];
+            uint32_t base = sm.cbeg[c] - sm.cpre[c];
             for (uint32_t e = e0; e < e1; e += 32u * kWalkUnroll) {   // warp-uniform
                 uint32_t idv[kWalkUnroll];
 #pragma unroll
@@ -406,8 +409,12 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
                     const uint32_t eu = e + lane + 32u * u;
                     idv[u] = 0xffffffffu;
                     if (eu < e1) {
-                        while (sm.cpre[c + 1] <= eu) ++c;
-                        idv[u] = ldg_keep_u32(P.ids + sm.cbeg[c] + (eu - sm.cpre[c]), pol_keep);
+                        while (nxt <= eu) {
+                            ++c;
+                            nxt = sm.cpre[c + 1];
+                            base = sm.cbeg[c] - sm.cpre[c];
+                        }
+                        idv[u] = ldg_keep_u32(P.ids + (base + eu), pol_keep);
                     }
                 }
                 // all counter atomics first (independent), then the ids that reached level
@@ -524,8 +531,8 @@ count_select_rerank_kernel(const RerankParams P) {
     float* qv = reinterpret_cast<float*>(smem + P.region_a);                     // d_pad
     uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);                   // buf_cap
     uint32_t* lst = buf + P.buf_cap;                                             // kListCap
-    unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);  // kCellBatch
-    uint32_t* cpre = reinterpret_cast<uint32_t*>(cbeg + kCellBatch);            // kCellBatch+1
+    uint32_t* cbeg = lst + kListCap;                                             // kCellBatch
+    uint32_t* cpre = cbeg + kCellBatch;                                          // kCellBatch+1
     uint32_t* ge2 = cpre + kCellBatch + 4;                                       // [2][16]
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ int s_last;
@@ -785,8 +792,8 @@ count_lists_kernel(const RerankParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
     uint32_t* lst = reinterpret_cast<uint32_t*>(smem + P.region_a);          // kListCap
-    unsigned long long* cbeg = reinterpret_cast<unsigned long long*>(lst + kListCap);
-    uint32_t* cpre = reinterpret_cast<uint32_t*>(cbeg + kCellBatch);        // kCellBatch + 1
+    uint32_t* cbeg = lst + kListCap;                                         // kCellBatch
+    uint32_t* cpre = cbeg + kCellBatch;                                      // kCellBatch + 1
     uint32_t* ge = cpre + kCellBatch + 4;                                    // [16]
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[kRrWarps];

@@ -660,7 +660,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             TACO_CUDA(cudaMemsetAsync(L.arena_used, 0, sizeof(uint32_t), st));
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit
-            const size_t smem1 = P.region_a + size_t(kListCap) * 4 + size_t(kCellBatch) * 8 +
+            const size_t smem1 = P.region_a + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
                                  size_t(kCellBatch + 4) * 4 + 16 * 4;
             static thread_local size_t c1_smem = 0;
             static thread_local int c1_blocks = 0;
@@ -700,7 +700,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         }
         // cluster kernel: every query (single-pass form) or the flagged ones
         const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
-                            size_t(kListCap) * 4 + size_t(kCellBatch) * 8 + size_t(kCellBatch + 4) * 4 + 32 * 4;
+                            size_t(kListCap) * 4 + size_t(kCellBatch) * 4 + size_t(kCellBatch + 4) * 4 + 32 * 4;
         cudaError_t e;
         if (int rc = prof_begin(ix, 4, st, &pb, &pe)) return rc;
         if (!bf16) {
