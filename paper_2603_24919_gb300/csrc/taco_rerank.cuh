@@ -250,48 +250,51 @@ __device__ __forceinline__ void gather_distances(const unsigned char* base, size
     }
 }
 
-// Exclusive scan of v over the block (kRrThreads threads); returns the thread's prefix and
-// the block total. Uses `tmp` (kRrWarps entries of shared memory).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, uint32_t& total,
-                                                    int lane, int warp) {
-    uint32_t incl = v;
+// Exclusive scan of two values over the block; tmp holds 2 * kRrWarps entries.
+__device__ __forceinline__ uint2 block_excl_scan2(uint32_t a, uint32_t b, uint32_t* tmp, uint2& total,
+                                                  int lane, int warp) {
+    uint32_t ia = a, ib = b;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += t;
+        const uint32_t ta = __shfl_up_sync(kFull, ia, off), tb = __shfl_up_sync(kFull, ib, off);
+        if (lane >= off) { ia += ta; ib += tb; }
     }
-    if (lane == 31) tmp[warp] = incl;
+    if (lane == 31) { tmp[warp] = ia; tmp[kRrWarps + warp] = ib; }
     __syncthreads();
-    uint32_t wpre = 0, tot = 0;
+    uint32_t pa = 0, pb = 0, sa = 0, sb = 0;
 #pragma unroll
     for (int w = 0; w < kRrWarps; ++w) {
-        const uint32_t x = tmp[w];
-        wpre += w < warp ? x : 0u;
-        tot += x;
+        const uint32_t xa = tmp[w], xb = tmp[kRrWarps + w];
+        pa += w < warp ? xa : 0u;
+        pb += w < warp ? xb : 0u;
+        sa += xa;
+        sb += xb;
     }
     __syncthreads();
-    total = tot;
-    return wpre + incl - v;
+    total = make_uint2(sa, sb);
+    return make_uint2(pa + ia - a, pb + ib - b);
 }
 
 constexpr int kCellBatch = 512;    // probed cells staged per walk
+constexpr int kRunPad = 36;        // boundary entries past the last staged run (>= 33)
 constexpr int kBufCap = 4096;      // candidate ids buffered per re-rank round (>= 8 * kRrThreads)
 constexpr int kListCap = 4096;     // ids that reached a level >= 2 during counting
-constexpr int kSegCap = kListCap / kRrWarps;   // per-warp segment of the list
-constexpr int kWalkUnroll = 16;    // id loads in flight per lane while counting
+constexpr int kWalkUnroll = 8;     // id loads in flight per lane while counting (<= 32)
 constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
 
-// Stage the id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
-// [slab_lo, slab_hi): cbeg[t] = absolute start in the id array (N_s * n < 2^32), cpre =
-// exclusive prefix of the run lengths (cpre[nb] = total). Block-wide; ends with a barrier.
-__device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
-                                                int cb0, int nb, int slab_lo, int slab_hi,
-                                                uint32_t* cbeg, uint32_t* cpre,
-                                                uint32_t* s_tmp, int tid, int lane, int warp,
-                                                uint64_t keep) {
+// Stage the non-empty id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
+// [slab_lo, slab_hi), in cell order. Element e of the concatenation lies in run r with
+// cpre[r] <= e < cpre[r + 1]; its id-array index is rbase[r] + e (uint32 arithmetic,
+// N_s * n < 2^32). cpre[nr] = total and cpre[nr + 1 .. nr + 32] = 0xffffffff. Returns
+// (total, nr). Block-wide; ends with a barrier.
+__device__ __forceinline__ uint2 stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
+                                             int cb0, int nb, int slab_lo, int slab_hi,
+                                             uint32_t* rbase, uint32_t* cpre,
+                                             uint32_t* s_tmp, int tid, int lane, int warp,
+                                             uint64_t keep) {
     const int Ns = P.Ns, K = P.K;
     const int sstride = P.n_slabs + 1;
-    uint32_t len = 0;
+    uint32_t len = 0, start = 0;
     if (tid < nb) {
         const int g = cb0 + tid;
         int i = 0;
@@ -299,15 +302,18 @@ __device__ __forceinline__ uint32_t stage_cells(const RerankParams& P, int64_t q
         const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
         const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
         const uint32_t b = ldg_keep_u32(sp + slab_lo, keep), e = ldg_keep_u32(sp + slab_hi, keep);
-        cbeg[tid] = uint32_t(i) * uint32_t(P.n) + b;
+        start = uint32_t(i) * uint32_t(P.n) + b;
         len = e - b;
     }
-    uint32_t total;
-    const uint32_t ex = block_excl_scan(len, s_tmp, total, lane, warp);
-    if (tid < nb) cpre[tid] = ex;
-    if (tid == 0) cpre[nb] = total;
+    uint2 tot;
+    const uint2 ex = block_excl_scan2(len, len != 0u ? 1u : 0u, s_tmp, tot, lane, warp);
+    if (len != 0u) {
+        cpre[ex.y] = ex.x;
+        rbase[ex.y] = start - ex.x;
+    }
+    if (tid <= 32) cpre[tot.y + uint32_t(tid)] = tid == 0 ? tot.x : 0xffffffffu;
     __syncthreads();
-    return total;
+    return tot;
 }
 
 // Cell whose run holds element `key` of the concatenation (largest c with cpre[c] <= key).
@@ -356,26 +362,51 @@ __device__ __forceinline__ void warp_merge(const float* ld, const uint32_t* li, 
     }
 }
 
+// Warp-aggregated append: lanes with `take` get consecutive slots after one atomicAdd on
+// *counter by the warp; returns the lane's slot (undefined where !take). All lanes call it.
+__device__ __forceinline__ uint32_t warp_append_slot(bool take, uint32_t* counter, int lane) {
+    const unsigned bal = __ballot_sync(kFull, take);
+    uint32_t base = 0;
+    if (bal) {
+        const int leader = __ffs(bal) - 1;
+        if (lane == leader) base = atomicAdd(counter, uint32_t(__popc(bal)));
+        base = __shfl_sync(kFull, base, leader);
+    }
+    return base + __popc(bal & ((1u << lane) - 1u));
+}
+
+// s_pre[i] = number of probed cells of query q in subspaces < i (one warp, all lanes).
+__device__ __forceinline__ void load_cell_prefix(const RerankParams& P, int64_t q, int* s_pre, int lane) {
+    int v = lane < P.Ns ? P.ncells[q * P.Ns + lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, off);
+        if (lane >= off) v += t;
+    }
+    if (lane < P.Ns) s_pre[lane + 1] = v;
+    if (lane == 0) s_pre[0] = 0;
+}
+
 // Shared-memory state of the counting phase of one (query, id range) unit.
 struct CountSmem {
     uint32_t* cnt;                 // 4-bit SC counters of the range
-    uint32_t* lst;                 // kRrWarps segments of kSegCap level entries
-    uint32_t* cbeg;                // staged run starts
-    uint32_t* cpre;                // staged run prefix
+    uint32_t* lst;                 // kListCap level entries
+    uint32_t* rbase;               // staged runs: id-array index minus the run's prefix
+    uint32_t* cpre;                // staged run boundaries (kCellBatch + kRunPad)
     uint32_t* ge;                  // [16] ids with SC >= j
     int* s_pre;                    // prefix of probed cells per subspace
     uint32_t* s_tmp;               // block-scan scratch
-    uint32_t* s_seg;               // entries per segment
-    uint32_t* s_segpre;            // prefix of segment sizes
-    uint32_t* s_app;               // segment overflow flag
+    uint32_t* s_listn;             // entries appended to lst
 };
 
 // Count the collisions of query q in ids [lo, hi) (slabs [slab_lo, slab_hi)) into sm.cnt,
 // fill ge[1..N_s] and the level list. SC[id] += 1 for every id of every probed cell; the
 // nibble's old value v says the id just reached level v + 1. Ids reaching a level >= 2 are
-// appended to a per-warp list segment with that level, so every id with SC >= j >= 2 is
-// there exactly once tagged j; first touches (level 1) are counted per lane. Returns true
-// if a segment overflowed (then ge[2..] were counted from the counters). Block-wide; all
+// appended to the list sm.lst with that level, so every id with SC >= j >= 2 is there
+// exactly once tagged j; ge[1] is the number of events minus the level >= 2 events (an id
+// with SC = c contributes c events, c - 1 of which reach a level >= 2). *sm.s_listn (zero on
+// entry) ends as the number of appends; more than kListCap means the list overflowed, and
+// then ge[2..] were counted from the counters. Returns true on overflow. Block-wide; all
 // threads return after a barrier with s_pre set by the caller.
 __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, int slab_lo, int slab_hi,
                                             int64_t lo, int words, const CountSmem& sm, uint64_t pol_keep,
@@ -383,91 +414,85 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
     const int Ns = P.Ns;
     const int total_cells = sm.s_pre[Ns];
     const int nbatch = (total_cells + kCellBatch - 1) / kCellBatch;
-    {
-        uint32_t c1 = 0;
-        uint32_t wapp = 0;                          // entries this warp appended
-        uint32_t* wseg = sm.lst + warp * kSegCap;   // this warp's list segment
-        for (int bt = 0; bt < nbatch; ++bt) {
-            const int cb0 = bt * kCellBatch;
-            const int nb = min(kCellBatch, total_cells - cb0);
-            const uint32_t total = stage_cells(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.cbeg,
-                                               sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
-            // warp w walks a contiguous share [e0, e1) of the concatenated runs; lane l takes
-            // elements e0 + l + 32 u, 16 per round, so all loads of a round are in flight
-            // together; the lane's cell pointer only moves forward
-            const uint32_t chunk = ((total + kRrWarps - 1) / kRrWarps + 31) & ~31u;
-            const uint32_t e0 = uint32_t(warp) * chunk;
-            const uint32_t e1 = min(total, e0 + chunk);
-            int c = e0 < e1 ? find_cell(sm.cpre, nb, e0 + lane < e1 ? e0 + lane : e1 - 1) : 0;
-            // the lane's current cell: where its run ends and the id-array index of element 0
-            uint32_t nxt = sm.cpre[c + 1];
-            uint32_t base = sm.cbeg[c] - sm.cpre[c];
-            for (uint32_t e = e0; e < e1; e += 32u * kWalkUnroll) {   // warp-uniform
-                uint32_t idv[kWalkUnroll];
+    const uint32_t lane_le = (2u << lane) - 1u;  // lanes 0..lane
+    const uint32_t last_idx = uint32_t(P.Ns) * uint32_t(P.n) - 1u;
+    for (int bt = 0; bt < nbatch; ++bt) {
+        const int cb0 = bt * kCellBatch;
+        const int nb = min(kCellBatch, total_cells - cb0);
+        const uint2 st = stage_cells(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.rbase,
+                                     sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
+        const uint32_t total = st.x, nr = st.y;
+        if (tid == 0 && total) atomicAdd(&sm.ge[1], total);   // minus the level >= 2 events below
+        // The concatenated runs are walked in rounds of kWalkUnroll windows of 32 consecutive
+        // elements, round g by warp g mod kRrWarps, with all loads of a round in flight. Lane
+        // u finds the run holding the first element of window u (binary search); in a window,
+        // lane j reads the j-th next run boundary, the boundaries inside the window form a bit
+        // mask, and a lane's run is the window's first run plus the mask bits at or below it
+        // (runs are non-empty, so at most 32 boundaries fall in a window). Every window is
+        // executed in full: lanes past the end load a valid id-array entry and add 0 to
+        // counter word 0.
+        constexpr uint32_t kRound = 32u * kWalkUnroll;
+        const uint32_t nrounds = (total + kRound - 1) / kRound;
+        for (uint32_t g = uint32_t(warp); g < nrounds; g += kRrWarps) {   // warp-uniform
+            const uint32_t e = g * kRound;
+            const uint32_t key = min(e + 32u * uint32_t(lane % kWalkUnroll), total - 1u);
+            const uint32_t cwl = uint32_t(find_cell(sm.cpre, int(nr), key));
+            uint32_t idv[kWalkUnroll];
 #pragma unroll
-                for (int u = 0; u < kWalkUnroll; ++u) {
-                    const uint32_t eu = e + lane + 32u * u;
-                    idv[u] = 0xffffffffu;
-                    if (eu < e1) {
-                        while (nxt <= eu) {
-                            ++c;
-                            nxt = sm.cpre[c + 1];
-                            base = sm.cbeg[c] - sm.cpre[c];
-                        }
-                        idv[u] = ldg_keep_u32(P.ids + (base + eu), pol_keep);
-                    }
-                }
-                // all counter atomics first (independent), then the ids that reached level
-                // >= 2 go to this warp's list segment (offsets by ballot)
-#pragma unroll
-                for (int u = 0; u < kWalkUnroll; ++u) {
-                    if (idv[u] != 0xffffffffu) {
-                        const uint32_t id = idv[u] - uint32_t(lo);
-                        const uint32_t sh = (id & 7u) << 2;
-                        const uint32_t v = (atomicAdd(&sm.cnt[id >> 3], 1u << sh) >> sh) & 15u;
-                        c1 += v == 0u;
-                        idv[u] = v != 0u ? (id | ((v + 1u) << kLevelShift)) : 0u;
-                    } else {
-                        idv[u] = 0u;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kWalkUnroll; ++u) {
-                    const unsigned bal = __ballot_sync(kFull, idv[u] != 0u);
-                    const uint32_t at = wapp + __popc(bal & ((1u << lane) - 1u));
-                    if (idv[u] && at < uint32_t(kSegCap)) wseg[at] = idv[u];
-                    wapp += __popc(bal);
-                }
+            for (int u = 0; u < kWalkUnroll; ++u) {
+                const uint32_t E = e + 32u * uint32_t(u);
+                const uint32_t cw = __shfl_sync(kFull, cwl, u);
+                const uint32_t pb = sm.cpre[cw + 1u + uint32_t(lane)] - E;   // >= 1 inside
+                const uint32_t mask = __reduce_or_sync(kFull, pb < 32u ? 1u << pb : 0u);
+                const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
+                const uint32_t x = min(sm.rbase[r] + E + uint32_t(lane), last_idx);
+                const uint32_t v = ldg_keep_u32(P.ids + x, pol_keep);
+                idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : 0xffffffffu;
             }
-            if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
+            // all counter atomics first (independent), then the ids that reached level >= 2
+            // go to the list: one reservation per round, offsets by ballot
+#pragma unroll
+            for (int u = 0; u < kWalkUnroll; ++u) {
+                const uint32_t id = idv[u];
+                const bool ok = id != 0xffffffffu;
+                const uint32_t sh = (id & 7u) << 2;
+                const uint32_t old = atomicAdd(&sm.cnt[ok ? id >> 3 : 0u], ok ? 1u << sh : 0u);
+                const uint32_t v = (old >> sh) & 15u;
+                idv[u] = (ok && v != 0u) ? (id | ((v + 1u) << kLevelShift)) : 0u;
+            }
+            unsigned bal[kWalkUnroll];
+            uint32_t napp = 0;
+#pragma unroll
+            for (int u = 0; u < kWalkUnroll; ++u) {
+                bal[u] = __ballot_sync(kFull, idv[u] != 0u);
+                napp += __popc(bal[u]);
+            }
+            uint32_t at = 0;
+            if (lane == 0 && napp) at = atomicAdd(sm.s_listn, napp);
+            at = __shfl_sync(kFull, at, 0);
+#pragma unroll
+            for (int u = 0; u < kWalkUnroll; ++u) {
+                const uint32_t a = at + __popc(bal[u] & (lane_le >> 1));
+                if (idv[u] != 0u && a < uint32_t(kListCap)) sm.lst[a] = idv[u];
+                at += __popc(bal[u]);
+            }
         }
-        const uint32_t t1 = __reduce_add_sync(kFull, c1);
-        if (lane == 0) {
-            if (t1) atomicAdd(&sm.ge[1], t1);
-            sm.s_seg[warp] = wapp;
-            if (wapp > uint32_t(kSegCap)) *sm.s_app = 1u;   // a segment overflowed
-        }
+        if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
     }
     __syncthreads();
-    const bool overflow = *sm.s_app != 0u;
-    if (tid == 0) {
-        uint32_t acc = 0;
-        for (int w = 0; w < kRrWarps; ++w) {
-            sm.s_segpre[w] = acc;
-            acc += min(sm.s_seg[w], uint32_t(kSegCap));
-        }
-        sm.s_segpre[kRrWarps] = acc;
-    }
-    __syncthreads();
-    const int napp = int(sm.s_segpre[kRrWarps]);
+    const uint32_t nlist = *sm.s_listn;
+    const bool overflow = nlist > uint32_t(kListCap);
     if (!overflow) {
-        for (int e = tid; e < napp; e += kRrThreads) {
-            int w = 0;
-            while (uint32_t(e) >= sm.s_segpre[w + 1]) ++w;
-            atomicAdd(&sm.ge[sm.lst[w * kSegCap + (e - int(sm.s_segpre[w]))] >> kLevelShift], 1u);
+        // lanes holding the same level form one group, whose lowest lane adds its size
+        for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
+            const uint32_t e = e0 + uint32_t(lane);
+            const uint32_t level = e < nlist ? sm.lst[e] >> kLevelShift : 0u;
+            const unsigned grp = __match_any_sync(kFull, level);
+            if (level != 0u && (grp & (lane_le >> 1)) == 0u) atomicAdd(&sm.ge[level], uint32_t(__popc(grp)));
         }
+        if (tid == 0 && nlist) atomicSub(&sm.ge[1], nlist);
     } else {
-        // a segment overflowed: count the levels from the counters themselves
+        // the list overflowed: count the levels from the counters themselves
         uint32_t gel[TACO_MAX_SUBSPACES];
 #pragma unroll
         for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
@@ -483,23 +508,19 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
                 }
             }
         }
+        uint32_t events = 0;   // level >= 2 events of this warp's words
 #pragma unroll
         for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
             if (j <= Ns) {
                 const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
+                events += v;
                 if (lane == 0 && v) atomicAdd(&sm.ge[j], v);
             }
         }
+        if (lane == 0 && events) atomicSub(&sm.ge[1], events);
     }
     __syncthreads();
     return overflow;
-}
-
-// Entry e of the concatenated list segments.
-__device__ __forceinline__ uint32_t seg_entry(const CountSmem& sm, int e) {
-    int w = 0;
-    while (uint32_t(e) >= sm.s_segpre[w + 1]) ++w;
-    return sm.lst[w * kSegCap + (e - int(sm.s_segpre[w]))];
 }
 
 // Debug: the SC of every touched id of the range (untouched ids stay at the caller's zero).
@@ -531,17 +552,15 @@ count_select_rerank_kernel(const RerankParams P) {
     float* qv = reinterpret_cast<float*>(smem + P.region_a);                     // d_pad
     uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);                   // buf_cap
     uint32_t* lst = buf + P.buf_cap;                                             // kListCap
-    uint32_t* cbeg = lst + kListCap;                                             // kCellBatch
-    uint32_t* cpre = cbeg + kCellBatch;                                          // kCellBatch+1
-    uint32_t* ge2 = cpre + kCellBatch + 4;                                       // [2][16]
+    uint32_t* rbase = lst + kListCap;                                            // kCellBatch
+    uint32_t* cpre = rbase + kCellBatch;                                         // kCellBatch+kRunPad
+    uint32_t* ge2 = cpre + kCellBatch + kRunPad;                                 // [2][16]
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ int s_last;
-    __shared__ uint32_t s_tmp[kRrWarps];
+    __shared__ uint32_t s_tmp[2 * kRrWarps];
     __shared__ uint32_t s_wcnt[2][kRrWarps];
     __shared__ uint32_t s_allge2[2][16 * 16];   // [parity][cta][level], filled by every CTA
     __shared__ uint32_t s_bufn, s_app;
-    __shared__ uint32_t s_seg[kRrWarps];
-    __shared__ uint32_t s_segpre[kRrWarps + 1];
     __shared__ uint32_t s_gs[TACO_MAX_SUBSPACES + 1];
 
     const int Ns = P.Ns;
@@ -560,13 +579,11 @@ count_select_rerank_kernel(const RerankParams P) {
     CountSmem csm;
     csm.cnt = cnt;
     csm.lst = lst;
-    csm.cbeg = cbeg;
+    csm.rbase = rbase;
     csm.cpre = cpre;
     csm.s_pre = s_pre;
     csm.s_tmp = s_tmp;
-    csm.s_seg = s_seg;
-    csm.s_segpre = s_segpre;
-    csm.s_app = &s_app;
+    csm.s_listn = &s_app;
 
     // counters start at zero; every query leaves them at zero again
     for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
@@ -583,13 +600,8 @@ count_select_rerank_kernel(const RerankParams P) {
         for (int j = tid; j < P.d_pad; j += kRrThreads)
             qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
         if (tid < 16) ge[tid] = 0u;
+        if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
         if (tid == 0) {
-            int acc = 0;
-            s_pre[0] = 0;
-            for (int i = 0; i < Ns; ++i) {
-                acc += P.ncells[q * Ns + i];
-                s_pre[i + 1] = acc;
-            }
             s_app = 0u;
             s_bufn = 0u;
         }
@@ -597,7 +609,6 @@ count_select_rerank_kernel(const RerankParams P) {
 
         // ---- 1. count the collisions of the probed cells' ids in this CTA's range
         const bool overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
-        const int napp = int(s_segpre[kRrWarps]);
         // push this CTA's level counts into row `cta` of every CTA's table
         if (tid < ncta * Ns) {
             const int r = tid / Ns, j = tid - r * Ns + 1;
@@ -674,10 +685,15 @@ count_select_rerank_kernel(const RerankParams P) {
         }
         if (last >= 2 && !overflow && mine <= uint32_t(P.buf_cap)) {
             // the candidates are the list entries tagged `last`
-            for (int e = tid; e < napp; e += kRrThreads) {
-                const uint32_t x = seg_entry(csm, e);
-                if (int(x >> kLevelShift) == last)
-                    buf[atomicAdd(&s_bufn, 1u)] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
+            {
+                const uint32_t nlist = s_app;   // <= kListCap: no overflow
+                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
+                    const uint32_t e = e0 + uint32_t(lane);
+                    const uint32_t x = e < nlist ? lst[e] : 0u;
+                    const bool take = e < nlist && int(x >> kLevelShift) == last;
+                    const uint32_t at = warp_append_slot(take, &s_bufn, lane);
+                    if (take) buf[at] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
+                }
             }
             // clear the counters for the next query
             uint4* c4 = reinterpret_cast<uint4*>(cnt);
@@ -792,15 +808,13 @@ count_lists_kernel(const RerankParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
     uint32_t* lst = reinterpret_cast<uint32_t*>(smem + P.region_a);          // kListCap
-    uint32_t* cbeg = lst + kListCap;                                         // kCellBatch
-    uint32_t* cpre = cbeg + kCellBatch;                                      // kCellBatch + 1
-    uint32_t* ge = cpre + kCellBatch + 4;                                    // [16]
+    uint32_t* rbase = lst + kListCap;                                        // kCellBatch
+    uint32_t* cpre = rbase + kCellBatch;                                     // kCellBatch + kRunPad
+    uint32_t* ge = cpre + kCellBatch + kRunPad;                              // [16]
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
-    __shared__ uint32_t s_tmp[kRrWarps];
-    __shared__ uint32_t s_seg[kRrWarps];
-    __shared__ uint32_t s_segpre[kRrWarps + 1];
+    __shared__ uint32_t s_tmp[2 * kRrWarps];
     __shared__ uint32_t s_app, s_outn, s_base;
-    CountSmem csm{cnt, lst, cbeg, cpre, ge, s_pre, s_tmp, s_seg, s_segpre, &s_app};
+    CountSmem csm{cnt, lst, rbase, cpre, ge, s_pre, s_tmp, &s_app};
     const int Ns = P.Ns;
     const uint64_t pol_keep = l2_policy_keep();
     for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
@@ -815,19 +829,13 @@ count_lists_kernel(const RerankParams P) {
         const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
         __syncthreads();   // the previous unit is finished with the shared state
         if (tid < 16) ge[tid] = 0u;
+        if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
         if (tid == 0) {
-            int acc = 0;
-            s_pre[0] = 0;
-            for (int i = 0; i < Ns; ++i) {
-                acc += P.ncells[q * Ns + i];
-                s_pre[i + 1] = acc;
-            }
             s_app = 0u;
             s_outn = 0u;
         }
         __syncthreads();
         const bool overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
-        const int napp = int(s_segpre[kRrWarps]);
         if (P.dbg_sc) debug_sc(P, q, lo, hi, words, cnt, tid);
         // reserve the unit's entries: ids with SC >= 2 number ge[2]
         if (tid == 0) {
@@ -847,11 +855,18 @@ count_lists_kernel(const RerankParams P) {
         const uint32_t base = s_base;
         if (base != 0xffffffffu) {
             // an id's final SC is its counter; its entry tagged with that level is unique
-            for (int e = tid; e < napp; e += kRrThreads) {
-                const uint32_t x = seg_entry(csm, e);
-                const uint32_t id = x & ((1u << kLevelShift) - 1u);
-                const uint32_t sc = (cnt[id >> 3] >> ((id & 7u) << 2)) & 15u;
-                if ((x >> kLevelShift) == sc) P.arena[base + atomicAdd(&s_outn, 1u)] = x;
+            const uint32_t nlist = s_app;   // <= kListCap: no overflow
+            for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
+                const uint32_t e = e0 + uint32_t(lane);
+                uint32_t x = 0;
+                bool take = false;
+                if (e < nlist) {
+                    x = lst[e];
+                    const uint32_t id = x & ((1u << kLevelShift) - 1u);
+                    take = (x >> kLevelShift) == ((cnt[id >> 3] >> ((id & 7u) << 2)) & 15u);
+                }
+                const uint32_t at = warp_append_slot(take, &s_outn, lane);
+                if (take) P.arena[base + at] = x;
             }
         }
         __syncthreads();
@@ -980,11 +995,14 @@ select_rerank_kernel(const RerankParams P) {
                     __syncthreads();
                 }
                 const uint32_t t = t0 + tid;
+                uint32_t x = 0;
+                bool take = false;
                 if (t < len) {
-                    const uint32_t x = P.arena[off + t];
-                    if (int(x >> kLevelShift) >= last)
-                        buf[atomicAdd(&s_bufn, 1u)] = rlo + (x & ((1u << kLevelShift) - 1u));
+                    x = P.arena[off + t];
+                    take = int(x >> kLevelShift) >= last;
                 }
+                const uint32_t at = warp_append_slot(take, &s_bufn, lane);
+                if (take) buf[at] = rlo + (x & ((1u << kLevelShift) - 1u));
                 __syncthreads();
             }
         }

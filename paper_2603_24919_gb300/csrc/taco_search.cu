@@ -36,10 +36,11 @@ probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict
                    QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                    int list_cap, uint16_t* __restrict__ cells_out,
                    int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out,
-                   uint8_t* __restrict__ dbg_probed) {
+                   uint8_t* __restrict__ dbg_probed, int redo_only) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int i = blockIdx.x;
     const int64_t q = blockIdx.y;
+    if (redo_only && ncells_out[size_t(q) * Ns + i] >= 0) return;   // the walk settled it
     const int K = sk * sk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long* list = reinterpret_cast<unsigned long long*>(sm);  // list_cap
@@ -214,6 +215,214 @@ probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict
     }
 }
 
+// Alg. 4 by merging sorted rows, one warp per (query, subspace). The second-half distances
+// d2 are sorted once; lane l owns the rows r = l + 32 e (first-half centroids), each with a
+// pointer into the sorted d2, so a row's next cell is its smallest unvisited key. A pop takes
+// the minimum over the row heads of (FP32 key bits, cell) (two warp min-reductions), which
+// visits the cells in the order of probe_cells_kernel's keys as long as no two cells share
+// a key; sizes are checked every kWalkBatch pops and the prefix stops at the cell where the
+// running size first reaches B. If another cell has exactly the key of that cell (its place
+// is then decided by the cell index among equal keys), or more than kWalkMaxPops pops are
+// needed, ncells is set to -1 and the histogram kernel redoes this (query, subspace).
+constexpr int kWalkThreads = 256;
+constexpr int kWalkBatch = 16;      // pops between size checks (<= 32)
+constexpr int kWalkMaxPops = 1024;
+
+template <int E>   // rows per lane: sqrtK <= 32 E, E in {1, 2, 4}
+__global__ void __launch_bounds__(kWalkThreads)
+probe_cells_walk_kernel(const float* __restrict__ qt, int Dp, const float* __restrict__ cent,
+                        int Ns, int s, int h1, int sk, const uint32_t* __restrict__ sizes,
+                        int64_t n, QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
+                        int64_t ntasks, uint16_t* __restrict__ cells_out,
+                        int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out) {
+    constexpr int W = kWalkThreads / 32;
+    constexpr int N = 32 * E;
+    __shared__ uint32_t s_bv[W][N];   // sorted d2 (FP32 bits)
+    __shared__ uint32_t s_bc[W][N];   // their second-half centroid indices
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = sk * sk;
+    for (int64_t task = int64_t(blockIdx.x) * W + warp; task < ntasks; task += int64_t(gridDim.x) * W) {
+        const int64_t q = task / Ns;
+        const int i = int(task - q * Ns);
+        const QueryParamsDev qp = params ? params[q] : defaults;
+        const int64_t budget = qp.budget;
+        uint16_t* out = cells_out + size_t(task) * K;
+        if (budget > n) {   // every cell
+            for (int c = lane; c < K; c += 32) out[c] = uint16_t(c);
+            if (lane == 0) {
+                ncells_out[task] = K;
+                retrieved_out[task] = n;
+            }
+            continue;
+        }
+        // Alg. 6 steps 4-5: squared distances of the two half-queries to their centroids
+        const float* qi = qt + q * Dp + size_t(i) * s;
+        float a[E];
+        uint32_t bk[E], bc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int t = lane + 32 * e;
+            float d1 = __int_as_float(0x7f800000), d2 = d1;
+            if (t < sk) {
+                const float* cc = cent + (size_t(i) * sk + t) * s;
+                float acc = 0.f;
+                for (int j = 0; j < h1; ++j) {
+                    const float df = qi[j] - cc[j];
+                    acc = fmaf(df, df, acc);
+                }
+                d1 = acc;
+                acc = 0.f;
+                for (int j = 0; j < s - h1; ++j) {
+                    const float df = qi[h1 + j] - cc[h1 + j];
+                    acc = fmaf(df, df, acc);
+                }
+                d2 = acc;
+            }
+            a[e] = d1;
+            bk[e] = t < sk ? __float_as_uint(d2) : 0xffffffffu;
+            bc[e] = uint32_t(t);
+        }
+        // bitonic sort of (bk, bc) ascending over the N slots, slot = 32 e + lane
+#pragma unroll
+        for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                if (j >= 32) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int f = e ^ (j >> 5);
+                        if (f > e) {
+                            const bool up = ((32 * e + lane) & k) == 0;
+                            const bool gt = bk[e] > bk[f] || (bk[e] == bk[f] && bc[e] > bc[f]);
+                            if (gt == up) {
+                                const uint32_t tk = bk[e], tc = bc[e];
+                                bk[e] = bk[f];
+                                bc[e] = bc[f];
+                                bk[f] = tk;
+                                bc[f] = tc;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const uint32_t ok = __shfl_xor_sync(kFull, bk[e], j);
+                        const uint32_t oc = __shfl_xor_sync(kFull, bc[e], j);
+                        const bool up = ((32 * e + lane) & k) == 0;
+                        const bool lower = (lane & j) == 0;
+                        const bool own_lt = bk[e] < ok || (bk[e] == ok && bc[e] < oc);
+                        const bool keep_own = (lower == up) ? own_lt : !own_lt;
+                        if (!keep_own) {
+                            bk[e] = ok;
+                            bc[e] = oc;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            s_bv[warp][32 * e + lane] = bk[e];
+            s_bc[warp][32 * e + lane] = bc[e];
+        }
+        __syncwarp();
+        // row heads (key bits, cell); exhausted or absent rows hold 0xffffffff
+        uint32_t hs[E], hc[E];
+        int jp[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int r = lane + 32 * e;
+            jp[e] = 0;
+            hs[e] = 0xffffffffu;
+            hc[e] = 0xffffffffu;
+            if (r < sk) {
+                hs[e] = __float_as_uint(a[e] + __uint_as_float(s_bv[warp][0]));
+                hc[e] = uint32_t(r * sk) + s_bc[warp][0];
+            }
+        }
+        uint32_t ls = hs[0], lc = hc[0];
+#pragma unroll
+        for (int e = 1; e < E; ++e)
+            if (hs[e] < ls || (hs[e] == ls && hc[e] < lc)) { ls = hs[e]; lc = hc[e]; }
+        const uint32_t* sz = sizes + size_t(i) * K;
+        unsigned long long cum = 0;
+        uint32_t prev_last = 0, rec_s = 0, rec_c = 0;
+        bool has_prev = false;
+        int nout = 0, pops = 0, status = 0;   // status: 1 settled, 2 redo
+        while (status == 0) {
+            int np = 0;
+            for (; np < kWalkBatch; ++np) {
+                const uint32_t ms = __reduce_min_sync(kFull, ls);
+                if (ms == 0xffffffffu) break;   // every cell visited
+                const uint32_t mc = __reduce_min_sync(kFull, ls == ms ? lc : 0xffffffffu);
+                if (lane == np) {
+                    rec_s = ms;
+                    rec_c = mc;
+                }
+                if (ls == ms && lc == mc) {   // this lane's row advances
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        if (hc[e] == mc) {
+                            const int jn = ++jp[e];
+                            if (jn < sk) {
+                                hs[e] = __float_as_uint(a[e] + __uint_as_float(s_bv[warp][jn]));
+                                hc[e] = uint32_t((lane + 32 * e) * sk) + s_bc[warp][jn];
+                            } else {
+                                hs[e] = 0xffffffffu;
+                                hc[e] = 0xffffffffu;
+                            }
+                        }
+                    }
+                    ls = hs[0];
+                    lc = hc[0];
+#pragma unroll
+                    for (int e = 1; e < E; ++e)
+                        if (hs[e] < ls || (hs[e] == ls && hc[e] < lc)) { ls = hs[e]; lc = hc[e]; }
+                }
+            }
+            pops += np;
+            // running size over this batch's pops
+            unsigned long long w = lane < np ? sz[rec_c] : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long v = __shfl_up_sync(kFull, w, off);
+                if (lane >= off) w += v;
+            }
+            const unsigned hit = __ballot_sync(kFull, lane < np && cum + w >= (unsigned long long)budget);
+            if (hit) {
+                const int x = __ffs(hit) - 1;
+                const uint32_t S = __shfl_sync(kFull, rec_s, x);
+                const bool tie = __ballot_sync(kFull, lane < np && lane != x && rec_s == S) != 0u ||
+                                 (has_prev && prev_last == S) ||
+                                 __reduce_min_sync(kFull, ls) == S;
+                if (tie) {
+                    status = 2;
+                } else {
+                    if (lane <= x) out[nout + lane] = uint16_t(rec_c);
+                    nout += x + 1;
+                    cum += __shfl_sync(kFull, w, x);
+                    status = 1;
+                }
+                break;
+            }
+            if (np > 0) {
+                if (lane < np) out[nout + lane] = uint16_t(rec_c);
+                nout += np;
+                cum += __shfl_sync(kFull, w, np - 1);
+                prev_last = __shfl_sync(kFull, rec_s, np - 1);
+                has_prev = true;
+            }
+            if (np < kWalkBatch) status = 1;                 // every cell visited
+            else if (pops >= kWalkMaxPops) status = 2;
+        }
+        if (lane == 0) {
+            ncells_out[task] = status == 2 ? -1 : nout;
+            retrieved_out[task] = (long long)cum;
+        }
+        __syncwarp();   // s_bv / s_bc are rewritten by the next task
+    }
+}
+
 // Same selection as probe_cells_kernel for K <= 256 * CPT cells, keeping each thread's CPT
 // keys and sizes in registers: the key range comes from the extremes of d1 and d2 (FP32
 // addition is monotone, so min1 + min2 and max1 + max2 bound every key), and the histogram,
@@ -225,10 +434,11 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
                        int64_t n, QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                        int list_cap, uint16_t* __restrict__ cells_out,
                        int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out,
-                       uint8_t* __restrict__ dbg_probed) {
+                       uint8_t* __restrict__ dbg_probed, int redo_only) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int i = blockIdx.x;
     const int64_t q = blockIdx.y;
+    if (redo_only && ncells_out[size_t(q) * Ns + i] >= 0) return;   // the walk settled it
     const int K = sk * sk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long* list = reinterpret_cast<unsigned long long*>(sm);  // list_cap
@@ -587,11 +797,31 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
 
         dim3 grid(unsigned(ix->Ns), unsigned(L.nq));
         if (int rc = prof_begin(ix, 1, st, &pb, &pe)) return rc;
+        // the row-merge walk settles small budgets; the histogram kernel redoes what it flags
+        // (and does everything when the debug flags are wanted or the budget needs many pops)
+        bool walk = L.dbg.probed == nullptr && ix->sk <= 128;
+        if (walk && L.params == nullptr &&
+            double(L.defaults.budget) * double(K) > 0.5 * kWalkMaxPops * double(ix->n))
+            walk = false;
+        if (walk) {
+            const int64_t ntasks = L.nq * ix->Ns;
+            const unsigned blocks = unsigned((ntasks + kWalkThreads / 32 - 1) / (kWalkThreads / 32));
+#define TACO_PROBE_WALK(E)                                                                        \
+    probe_cells_walk_kernel<E><<<blocks, kWalkThreads, 0, st>>>(                                  \
+        L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
+        L.params, ntasks, L.cells, L.ncells, L.retrieved)
+            if (ix->sk <= 32) TACO_PROBE_WALK(1);
+            else if (ix->sk <= 64) TACO_PROBE_WALK(2);
+            else TACO_PROBE_WALK(4);
+#undef TACO_PROBE_WALK
+            TACO_CUDA(cudaGetLastError());
+        }
+        const int redo = walk ? 1 : 0;
         const int cpt = (K + kSelThreads - 1) / kSelThreads;
 #define TACO_PROBE_REG(N)                                                                         \
     probe_cells_reg_kernel<N><<<grid, kSelThreads, smem, st>>>(                                   \
         L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
-        L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed)
+        L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo)
         if (cpt <= 1) TACO_PROBE_REG(1);
         else if (cpt <= 2) TACO_PROBE_REG(2);
         else if (cpt <= 4) TACO_PROBE_REG(4);
@@ -600,7 +830,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         else
             probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
                 L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
-                L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed);
+                L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo);
 #undef TACO_PROBE_REG
         TACO_CUDA(cudaGetLastError());
         if (int rc = prof_end(ix, 1, st, pb, pe)) return rc;
@@ -661,7 +891,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit
             const size_t smem1 = P.region_a + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
-                                 size_t(kCellBatch + 4) * 4 + 16 * 4;
+                                 size_t(kCellBatch + kRunPad) * 4 + 16 * 4;
             static thread_local size_t c1_smem = 0;
             static thread_local int c1_blocks = 0;
             if (c1_smem != smem1) {
@@ -700,7 +930,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         }
         // cluster kernel: every query (single-pass form) or the flagged ones
         const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
-                            size_t(kListCap) * 4 + size_t(kCellBatch) * 4 + size_t(kCellBatch + 4) * 4 + 32 * 4;
+                            size_t(kListCap) * 4 + size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 32 * 4;
         cudaError_t e;
         if (int rc = prof_begin(ix, 4, st, &pb, &pe)) return rc;
         if (!bf16) {
