@@ -414,15 +414,14 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     const size_t lists = size_t(chunk) * ix->cluster * kListsPerCta * kk_max * 4;
     const size_t o_ld = off; off = align_up(off + lists);
     const size_t o_li = off; off = align_up(off + lists);
-    // two-pass form: per-unit level counts and lists (an arena of kArenaPerUnit ids per unit
-    // on average; units that do not fit send their query to the cluster kernel)
+    // two-pass form: per-unit level counts and lists (a fixed arena slot of kArenaPerUnit
+    // ids per unit; units that do not fit send their query to the cluster kernel)
     const size_t units = size_t(chunk) * ix->cluster;
     const size_t arena_cap = units * kArenaPerUnit;
     const size_t o_uge = off; off = align_up(off + units * 16 * 4);
     const size_t o_uoff = off; off = align_up(off + units * 4);
     const size_t o_ulen = off; off = align_up(off + units * 4);
     const size_t o_arena = off; off = align_up(off + arena_cap * 4);
-    const size_t o_aused = off; off = align_up(off + 4);
     const size_t o_qflag = off; off = align_up(off + size_t(chunk) * 4);
     const size_t o_par = off; off = align_up(off + (per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0));
     const size_t o_q = off; off = align_up(off + (q_dev ? 0 : size_t(chunk) * ix->d * 4));
@@ -464,8 +463,6 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         L.unit_off = reinterpret_cast<uint32_t*>(wb + o_uoff);
         L.unit_len = reinterpret_cast<uint32_t*>(wb + o_ulen);
         L.arena = reinterpret_cast<uint32_t*>(wb + o_arena);
-        L.arena_cap = uint32_t(std::min<size_t>(arena_cap, 0xffffffffu));
-        L.arena_used = reinterpret_cast<uint32_t*>(wb + o_aused);
         L.qflag = reinterpret_cast<uint32_t*>(wb + o_qflag);
         L.out_ids = id_dev ? out_ids + c0 * k_stride : reinterpret_cast<int64_t*>(wb + o_oi);
         L.out_dists = dist_dev ? out_dists + c0 * k_stride : reinterpret_cast<float*>(wb + o_od);

@@ -15,6 +15,7 @@
 namespace taco {
 
 static thread_local std::string g_last_error;
+thread_local const char* g_launch_step = "";
 
 int fail(int code, const char* fmt, ...) {
     char buf[1024];
@@ -28,7 +29,10 @@ int fail(int code, const char* fmt, ...) {
 
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     int code = (e == cudaErrorMemoryAllocation) ? TACO_ENOMEM : TACO_ECUDA;
-    return fail(code, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    const char* step = g_launch_step;
+    g_launch_step = "";
+    return fail(code, "%s failed%s%s: %s (%s:%d)", what, *step ? " at " : "", step, cudaGetErrorString(e),
+                file, line);
 }
 
 bool is_device_pointer(const void* p) {

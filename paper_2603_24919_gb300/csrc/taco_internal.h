@@ -40,6 +40,9 @@ struct QueryParamsDev {
 // Error reporting (thread-local message).
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+// The step of a kernel-launch helper that failed (attribute, occupancy, launch), for the
+// message of the caller's cuda_fail; set by the helpers before they return an error.
+extern thread_local const char* g_launch_step;
 #define TACO_CUDA(call)                                                        \
     do {                                                                       \
         cudaError_t e_ = (call);                                               \
@@ -130,9 +133,7 @@ struct SearchLaunch {
     uint32_t* unit_ge;         // device [nq][cluster][16]
     uint32_t* unit_off;        // device [nq][cluster]
     uint32_t* unit_len;        // device [nq][cluster]
-    uint32_t* arena;           // device [arena_cap]
-    uint32_t arena_cap;
-    uint32_t* arena_used;      // device [1]
+    uint32_t* arena;           // device [nq][cluster][kArenaPerUnit]
     uint32_t* qflag;           // device [nq]
     int64_t* out_ids;
     float* out_dists;

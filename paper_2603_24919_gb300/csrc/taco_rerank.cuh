@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 
 #include "taco_internal.h"
 
@@ -71,8 +72,6 @@ struct RerankParams {
     uint32_t* unit_off;     // [nq][n_ranges] start of the unit's entries in the arena
     uint32_t* unit_len;     // [nq][n_ranges] entries (ids with SC >= 2)
     uint32_t* arena;        // entries: id relative to the range | SC << 27
-    uint32_t* arena_used;   // [1] entries reserved so far
-    uint32_t arena_cap;
     uint32_t* qflag;        // [nq] set when a query needs the cluster kernel
     uint8_t* dbg_sc;
     int64_t* dbg_hist;
@@ -282,6 +281,21 @@ constexpr int kListCap = 4096;     // ids that reached a level >= 2 during count
 constexpr int kWalkUnroll = 8;     // id loads in flight per lane while counting (<= 32)
 constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
 
+// Compact the runs (start, len) held one per thread into the staged form described below:
+// the non-empty ones in thread order. Block-wide; ends with a barrier.
+__device__ __forceinline__ uint2 stage_runs(uint32_t start, uint32_t len, uint32_t* rbase, uint32_t* cpre,
+                                            uint32_t* s_tmp, int tid, int lane, int warp) {
+    uint2 tot;
+    const uint2 ex = block_excl_scan2(len, len != 0u ? 1u : 0u, s_tmp, tot, lane, warp);
+    if (len != 0u) {
+        cpre[ex.y] = ex.x;
+        rbase[ex.y] = start - ex.x;
+    }
+    if (tid <= 32) cpre[tot.y + uint32_t(tid)] = tid == 0 ? tot.x : 0xffffffffu;
+    __syncthreads();
+    return tot;
+}
+
 // Stage the non-empty id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
 // [slab_lo, slab_hi), in cell order. Element e of the concatenation lies in run r with
 // cpre[r] <= e < cpre[r + 1]; its id-array index is rbase[r] + e (uint32 arithmetic,
@@ -305,15 +319,7 @@ __device__ __forceinline__ uint2 stage_cells(const RerankParams& P, int64_t q, c
         start = uint32_t(i) * uint32_t(P.n) + b;
         len = e - b;
     }
-    uint2 tot;
-    const uint2 ex = block_excl_scan2(len, len != 0u ? 1u : 0u, s_tmp, tot, lane, warp);
-    if (len != 0u) {
-        cpre[ex.y] = ex.x;
-        rbase[ex.y] = start - ex.x;
-    }
-    if (tid <= 32) cpre[tot.y + uint32_t(tid)] = tid == 0 ? tot.x : 0xffffffffu;
-    __syncthreads();
-    return tot;
+    return stage_runs(start, len, rbase, cpre, s_tmp, tid, lane, warp);
 }
 
 // Cell whose run holds element `key` of the concatenation (largest c with cpre[c] <= key).
@@ -408,87 +414,83 @@ struct CountSmem {
 // entry) ends as the number of appends; more than kListCap means the list overflowed, and
 // then ge[2..] were counted from the counters. Returns true on overflow. Block-wide; all
 // threads return after a barrier with s_pre set by the caller.
-__device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, int slab_lo, int slab_hi,
-                                            int64_t lo, int words, const CountSmem& sm, uint64_t pol_keep,
-                                            int tid, int lane, int warp) {
-    const int Ns = P.Ns;
-    const int total_cells = sm.s_pre[Ns];
-    const int nbatch = (total_cells + kCellBatch - 1) / kCellBatch;
+// Walk one staged batch (total elements in nr non-empty runs) of the range starting at id
+// lo: counters, list appends and *sm.s_listn. The concatenated runs are walked in rounds of
+// kWalkUnroll windows of 32 consecutive elements, round g by warp g mod kRrWarps, with all
+// loads of a round in flight. Lane u finds the run holding the first element of window u
+// (binary search); in a window, lane j reads the j-th next run boundary, the boundaries
+// inside the window form a bit mask, and a lane's run is the window's first run plus the
+// mask bits at or below it (runs are non-empty, so at most 32 boundaries fall in a window).
+// Every window is executed in full: lanes past the end load a valid id-array entry and add
+// 0 to counter word 0. Warp-level; no barrier.
+__device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, uint32_t total, uint32_t nr,
+                                           const CountSmem& sm, uint64_t pol_keep, int lane, int warp) {
     const uint32_t lane_le = (2u << lane) - 1u;  // lanes 0..lane
     const uint32_t last_idx = uint32_t(P.Ns) * uint32_t(P.n) - 1u;
-    for (int bt = 0; bt < nbatch; ++bt) {
-        const int cb0 = bt * kCellBatch;
-        const int nb = min(kCellBatch, total_cells - cb0);
-        const uint2 st = stage_cells(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.rbase,
-                                     sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
-        const uint32_t total = st.x, nr = st.y;
-        if (tid == 0 && total) atomicAdd(&sm.ge[1], total);   // minus the level >= 2 events below
-        // The concatenated runs are walked in rounds of kWalkUnroll windows of 32 consecutive
-        // elements, round g by warp g mod kRrWarps, with all loads of a round in flight. Lane
-        // u finds the run holding the first element of window u (binary search); in a window,
-        // lane j reads the j-th next run boundary, the boundaries inside the window form a bit
-        // mask, and a lane's run is the window's first run plus the mask bits at or below it
-        // (runs are non-empty, so at most 32 boundaries fall in a window). Every window is
-        // executed in full: lanes past the end load a valid id-array entry and add 0 to
-        // counter word 0.
-        constexpr uint32_t kRound = 32u * kWalkUnroll;
-        const uint32_t nrounds = (total + kRound - 1) / kRound;
-        for (uint32_t g = uint32_t(warp); g < nrounds; g += kRrWarps) {   // warp-uniform
-            const uint32_t e = g * kRound;
-            const uint32_t key = min(e + 32u * uint32_t(lane % kWalkUnroll), total - 1u);
-            const uint32_t cwl = uint32_t(find_cell(sm.cpre, int(nr), key));
-            uint32_t idv[kWalkUnroll];
+    constexpr uint32_t kRound = 32u * kWalkUnroll;
+    const uint32_t nrounds = (total + kRound - 1) / kRound;
+    for (uint32_t g = uint32_t(warp); g < nrounds; g += kRrWarps) {   // warp-uniform
+        const uint32_t e = g * kRound;
+        const uint32_t key = min(e + 32u * uint32_t(lane % kWalkUnroll), total - 1u);
+        const uint32_t cwl = uint32_t(find_cell(sm.cpre, int(nr), key));
+        uint32_t idv[kWalkUnroll];
 #pragma unroll
-            for (int u = 0; u < kWalkUnroll; ++u) {
-                const uint32_t E = e + 32u * uint32_t(u);
-                const uint32_t cw = __shfl_sync(kFull, cwl, u);
-                const uint32_t pb = sm.cpre[cw + 1u + uint32_t(lane)] - E;   // >= 1 inside
-                const uint32_t mask = __reduce_or_sync(kFull, pb < 32u ? 1u << pb : 0u);
-                const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
-                const uint32_t x = min(sm.rbase[r] + E + uint32_t(lane), last_idx);
-                const uint32_t v = ldg_keep_u32(P.ids + x, pol_keep);
-                idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : 0xffffffffu;
-            }
-            // all counter atomics first (independent), then the ids that reached level >= 2
-            // go to the list: one reservation per round, offsets by ballot
-#pragma unroll
-            for (int u = 0; u < kWalkUnroll; ++u) {
-                const uint32_t id = idv[u];
-                const bool ok = id != 0xffffffffu;
-                const uint32_t sh = (id & 7u) << 2;
-                const uint32_t old = atomicAdd(&sm.cnt[ok ? id >> 3 : 0u], ok ? 1u << sh : 0u);
-                const uint32_t v = (old >> sh) & 15u;
-                idv[u] = (ok && v != 0u) ? (id | ((v + 1u) << kLevelShift)) : 0u;
-            }
-            unsigned bal[kWalkUnroll];
-            uint32_t napp = 0;
-#pragma unroll
-            for (int u = 0; u < kWalkUnroll; ++u) {
-                bal[u] = __ballot_sync(kFull, idv[u] != 0u);
-                napp += __popc(bal[u]);
-            }
-            uint32_t at = 0;
-            if (lane == 0 && napp) at = atomicAdd(sm.s_listn, napp);
-            at = __shfl_sync(kFull, at, 0);
-#pragma unroll
-            for (int u = 0; u < kWalkUnroll; ++u) {
-                const uint32_t a = at + __popc(bal[u] & (lane_le >> 1));
-                if (idv[u] != 0u && a < uint32_t(kListCap)) sm.lst[a] = idv[u];
-                at += __popc(bal[u]);
-            }
+        for (int u = 0; u < kWalkUnroll; ++u) {
+            const uint32_t E = e + 32u * uint32_t(u);
+            const uint32_t cw = __shfl_sync(kFull, cwl, u);
+            const uint32_t pb = sm.cpre[cw + 1u + uint32_t(lane)] - E;   // >= 1 inside
+            const uint32_t mask = __reduce_or_sync(kFull, pb < 32u ? 1u << pb : 0u);
+            const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
+            const uint32_t x = min(sm.rbase[r] + E + uint32_t(lane), last_idx);
+            const uint32_t v = ldg_keep_u32(P.ids + x, pol_keep);
+            idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : 0xffffffffu;
         }
-        if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
+        // all counter atomics first (independent), then the ids that reached level >= 2
+        // go to the list: one reservation per round, offsets by ballot
+#pragma unroll
+        for (int u = 0; u < kWalkUnroll; ++u) {
+            const uint32_t id = idv[u];
+            const bool ok = id != 0xffffffffu;
+            const uint32_t sh = (id & 7u) << 2;
+            const uint32_t old = atomicAdd(&sm.cnt[ok ? id >> 3 : 0u], ok ? 1u << sh : 0u);
+            const uint32_t v = (old >> sh) & 15u;
+            idv[u] = (ok && v != 0u) ? (id | ((v + 1u) << kLevelShift)) : 0u;
+        }
+        unsigned bal[kWalkUnroll];
+        uint32_t napp = 0;
+#pragma unroll
+        for (int u = 0; u < kWalkUnroll; ++u) {
+            bal[u] = __ballot_sync(kFull, idv[u] != 0u);
+            napp += __popc(bal[u]);
+        }
+        uint32_t at = 0;
+        if (lane == 0 && napp) at = atomicAdd(sm.s_listn, napp);
+        at = __shfl_sync(kFull, at, 0);
+#pragma unroll
+        for (int u = 0; u < kWalkUnroll; ++u) {
+            const uint32_t a = at + __popc(bal[u] & (lane_le >> 1));
+            if (idv[u] != 0u && a < uint32_t(kListCap)) sm.lst[a] = idv[u];
+            at += __popc(bal[u]);
+        }
     }
-    __syncthreads();
+}
+
+// After the walks of a range (and a barrier): ge[2..N_s] from the list, or from the
+// counters if the list overflowed; ge[1] loses the level >= 2 events. Returns true on
+// overflow. Block-wide; ends with a barrier.
+__device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, const CountSmem& sm,
+                                              int tid, int lane, int warp) {
+    const int Ns = P.Ns;
     const uint32_t nlist = *sm.s_listn;
     const bool overflow = nlist > uint32_t(kListCap);
     if (!overflow) {
         // lanes holding the same level form one group, whose lowest lane adds its size
+        const uint32_t lane_lt = (1u << lane) - 1u;
         for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
             const uint32_t e = e0 + uint32_t(lane);
             const uint32_t level = e < nlist ? sm.lst[e] >> kLevelShift : 0u;
             const unsigned grp = __match_any_sync(kFull, level);
-            if (level != 0u && (grp & (lane_le >> 1)) == 0u) atomicAdd(&sm.ge[level], uint32_t(__popc(grp)));
+            if (level != 0u && (grp & lane_lt) == 0u) atomicAdd(&sm.ge[level], uint32_t(__popc(grp)));
         }
         if (tid == 0 && nlist) atomicSub(&sm.ge[1], nlist);
     } else {
@@ -521,6 +523,24 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
     }
     __syncthreads();
     return overflow;
+}
+
+__device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, int slab_lo, int slab_hi,
+                                            int64_t lo, int words, const CountSmem& sm, uint64_t pol_keep,
+                                            int tid, int lane, int warp) {
+    const int total_cells = sm.s_pre[P.Ns];
+    const int nbatch = (total_cells + kCellBatch - 1) / kCellBatch;
+    for (int bt = 0; bt < nbatch; ++bt) {
+        const int cb0 = bt * kCellBatch;
+        const int nb = min(kCellBatch, total_cells - cb0);
+        const uint2 st = stage_cells(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.rbase,
+                                     sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
+        if (tid == 0 && st.x) atomicAdd(&sm.ge[1], st.x);   // minus the level >= 2 events later
+        walk_batch(P, lo, st.x, st.y, sm, pol_keep, lane, warp);
+        if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
+    }
+    __syncthreads();
+    return finish_levels(P, words, sm, tid, lane, warp);
 }
 
 // Debug: the SC of every touched id of the range (untouched ids stay at the caller's zero).
@@ -793,85 +813,136 @@ count_select_rerank_kernel(const RerankParams P) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Two-pass form. Pass 1 (count_lists_kernel): persistent CTAs take (query, id range) units;
-// each counts the unit's collisions in shared memory and writes the unit's level counts and
-// the compact list of its ids with SC >= 2 (id relative to the range | SC << 27) to global
-// memory. Pass 2 (select_rerank_kernel): one CTA per query sums the level counts of its
-// ranges, applies Alg. 5, keeps the list entries with SC >= last_collision and re-ranks
-// them. Queries whose threshold falls below 2, or whose lists did not fit, are flagged for
-// the cluster kernel above.
+// Two-pass form. Pass 1 (count_lists_kernel): persistent CTAs take queries and, for each,
+// its id ranges in turn (a (query, range) pair is a unit); a unit's collisions are counted
+// in shared memory and the unit's level counts and the compact list of its ids with
+// SC >= 2 (id relative to the range | SC << 27) go to global memory, the list into the
+// unit's fixed arena slot of kArenaPerUnit entries. Pass 2 (select_rerank_kernel): one CTA
+// per query sums the level counts of its ranges, applies Alg. 5, keeps the list entries
+// with SC >= last_collision and re-ranks them. Queries whose threshold falls below 2, or
+// whose lists did not fit, are flagged for the cluster kernel above.
 // ---------------------------------------------------------------------------------------
 #ifdef TACO_DEFINE_COUNT_LISTS   // defined by the one translation unit that launches it
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared memory of count_lists_kernel past the counters (bytes).
+constexpr size_t kCountListsExtra = size_t(2) * kCellBatch * 8 + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
+                                    size_t(kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
+
 __global__ void __launch_bounds__(kRrThreads, 2)
 count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* lst = reinterpret_cast<uint32_t*>(smem + P.region_a);          // kListCap
-    uint32_t* rbase = lst + kListCap;                                        // kCellBatch
-    uint32_t* cpre = rbase + kCellBatch;                                     // kCellBatch + kRunPad
-    uint32_t* ge = cpre + kCellBatch + kRunPad;                              // [16]
+    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
+    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);      // kListCap
+    uint32_t* rbase = lst + kListCap;                                         // kCellBatch
+    uint32_t* cpre = rbase + kCellBatch;                                      // kCellBatch + kRunPad
+    uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
+    uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * kRrWarps];
-    __shared__ uint32_t s_app, s_outn, s_base;
+    __shared__ uint32_t s_app, s_outn;
     CountSmem csm{cnt, lst, rbase, cpre, ge, s_pre, s_tmp, &s_app};
-    const int Ns = P.Ns;
+    const int Ns = P.Ns, K = P.K;
+    const int sstride = P.n_slabs + 1;
     const uint64_t pol_keep = l2_policy_keep();
     for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
-    const int64_t units = P.nq * P.n_ranges;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const int64_t q = u / P.n_ranges;
-        const int r = int(u - q * P.n_ranges);
-        const int slab_lo = r * P.slabs_per_cta;
-        const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
-        const int64_t lo = int64_t(slab_lo) << kSlabLog2;
-        const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
-        const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
-        __syncthreads();   // the previous unit is finished with the shared state
-        if (tid < 16) ge[tid] = 0u;
+    // the split bounds of every staged cell for range r, into pairs[buf] (asynchronous)
+    auto prefetch = [&](int total_cells, int r, int buf) {
+        const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
+        for (int t = tid; t < total_cells; t += kRrThreads) {
+            const uint32_t qc = qcell[t];
+            const uint32_t* sp = P.split + (size_t(qc >> 16) * K + (qc & 0xffffu)) * sstride;
+            cp_async4(&pairs[buf * kCellBatch + t].x, sp + slo);
+            cp_async4(&pairs[buf * kCellBatch + t].y, sp + shi);
+        }
+        cp_async_commit();
+    };
+    for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+        __syncthreads();   // the previous query is finished with the shared state
         if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
-        if (tid == 0) {
-            s_app = 0u;
-            s_outn = 0u;
-        }
         __syncthreads();
-        const bool overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
-        if (P.dbg_sc) debug_sc(P, q, lo, hi, words, cnt, tid);
-        // reserve the unit's entries: ids with SC >= 2 number ge[2]
-        if (tid == 0) {
-            const uint32_t need = overflow ? 0u : ge[2];
-            uint32_t base = 0xffffffffu;
-            if (!overflow) {
-                base = atomicAdd(P.arena_used, need);
-                if (base > P.arena_cap || need > P.arena_cap - base) base = 0xffffffffu;
+        const int total_cells = s_pre[Ns];
+        const bool staged = total_cells <= kCellBatch;   // one batch: cells kept for every range
+        if (staged) {
+            for (int t = tid; t < total_cells; t += kRrThreads) {
+                int i = 0;
+                while (t >= s_pre[i + 1]) ++i;
+                qcell[t] = (uint32_t(i) << 16) | P.cells[(q * Ns + i) * K + (t - s_pre[i])];
             }
-            s_base = base;
-            P.unit_off[u] = base;
-            P.unit_len[u] = base == 0xffffffffu ? 0u : need;
-            if (base == 0xffffffffu) P.qflag[q] = 1u;   // list lost: the query takes the cluster path
+            __syncthreads();
+            prefetch(total_cells, 0, 0);
         }
-        if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
-        __syncthreads();
-        const uint32_t base = s_base;
-        if (base != 0xffffffffu) {
-            // an id's final SC is its counter; its entry tagged with that level is unique
-            const uint32_t nlist = s_app;   // <= kListCap: no overflow
-            for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
-                const uint32_t e = e0 + uint32_t(lane);
-                uint32_t x = 0;
-                bool take = false;
-                if (e < nlist) {
-                    x = lst[e];
-                    const uint32_t id = x & ((1u << kLevelShift) - 1u);
-                    take = (x >> kLevelShift) == ((cnt[id >> 3] >> ((id & 7u) << 2)) & 15u);
+        for (int r = 0; r < P.n_ranges; ++r) {
+            const int64_t u = q * P.n_ranges + r;
+            const int slab_lo = r * P.slabs_per_cta;
+            const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
+            const int64_t lo = int64_t(slab_lo) << kSlabLog2;
+            const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
+            const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
+            if (tid < 16) ge[tid] = 0u;
+            if (tid == 0) {
+                s_app = 0u;
+                s_outn = 0u;
+            }
+            bool overflow;
+            if (staged) {
+                cp_async_wait_all();
+                __syncthreads();   // this range's bounds are in pairs[r & 1]
+                if (r + 1 < P.n_ranges) prefetch(total_cells, r + 1, (r + 1) & 1);
+                uint32_t start = 0, len = 0;
+                if (tid < total_cells) {
+                    const uint2 be = pairs[(r & 1) * kCellBatch + tid];
+                    start = (qcell[tid] >> 16) * uint32_t(P.n) + be.x;
+                    len = be.y - be.x;
                 }
-                const uint32_t at = warp_append_slot(take, &s_outn, lane);
-                if (take) P.arena[base + at] = x;
+                const uint2 st = stage_runs(start, len, rbase, cpre, s_tmp, tid, lane, warp);
+                if (tid == 0 && st.x) atomicAdd(&ge[1], st.x);   // minus the level >= 2 events later
+                walk_batch(P, lo, st.x, st.y, csm, pol_keep, lane, warp);
+                __syncthreads();
+                overflow = finish_levels(P, words, csm, tid, lane, warp);
+            } else {
+                __syncthreads();
+                overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
             }
+            if (P.dbg_sc) debug_sc(P, q, lo, hi, words, cnt, tid);
+            // the unit's entries (ids with SC >= 2) go to its fixed arena slot
+            const uint32_t need = ge[2];
+            const bool fits = !overflow && need <= uint32_t(kArenaPerUnit);
+            if (tid == 0) {
+                P.unit_off[u] = fits ? uint32_t(u) * uint32_t(kArenaPerUnit) : 0xffffffffu;
+                P.unit_len[u] = fits ? need : 0u;
+                if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the cluster path
+            }
+            if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
+            if (fits) {
+                // an id's final SC is its counter; its entry tagged with that level is unique
+                uint32_t* out = P.arena + size_t(u) * kArenaPerUnit;
+                const uint32_t nlist = s_app;   // <= kListCap: no overflow
+                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
+                    const uint32_t e = e0 + uint32_t(lane);
+                    uint32_t x = 0;
+                    bool take = false;
+                    if (e < nlist) {
+                        x = lst[e];
+                        const uint32_t id = x & ((1u << kLevelShift) - 1u);
+                        take = (x >> kLevelShift) == ((cnt[id >> 3] >> ((id & 7u) << 2)) & 15u);
+                    }
+                    const uint32_t at = warp_append_slot(take, &s_outn, lane);
+                    if (take) out[at] = x;
+                }
+            }
+            __syncthreads();
+            uint4* c4 = reinterpret_cast<uint4*>(cnt);
+            for (int w = tid; w < (words + 3) / 4; w += kRrThreads) c4[w] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
         }
-        __syncthreads();
-        uint4* c4 = reinterpret_cast<uint4*>(cnt);
-        for (int w = tid; w < (words + 3) / 4; w += kRrThreads) c4[w] = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -1063,23 +1134,26 @@ cudaError_t launch_select_rerank_t(const RerankParams& P, int64_t nq, size_t sme
     auto kern = select_rerank_kernel<G, R, BF16>;
     static thread_local size_t cached_smem = 0;
     static thread_local int cached_blocks = 0;
-    cudaError_t e;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return g_launch_step = "an earlier unchecked call", e;
     if (cached_smem != smem) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return g_launch_step = "cudaFuncSetAttribute", e;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSrThreads, smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return g_launch_step = "cudaOccupancyMaxActiveBlocksPerMultiprocessor", e;
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (per_sm * sms < 1) return g_launch_step = "occupancy (no block fits)", cudaErrorInvalidConfiguration;
         cached_blocks = per_sm * sms;
         cached_smem = smem;
-        if (cached_blocks < 1) return cudaErrorInvalidConfiguration;
     }
     const int64_t blocks = nq < cached_blocks ? nq : cached_blocks;
     kern<<<unsigned(blocks), kSrThreads, smem, st>>>(P);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) g_launch_step = "launch";
+    return e;
 }
 
 template <int G, int R, bool BF16>
@@ -1089,13 +1163,14 @@ cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size
     // persistent grid: as many clusters as can be resident at once (cached per shape)
     static thread_local size_t cached_smem = 0;
     static thread_local int cached_cluster = 0, cached_active = 0;
-    cudaError_t e;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return g_launch_step = "an earlier unchecked call", e;
     if (cached_smem != smem || cached_cluster != cluster) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return g_launch_step = "cudaFuncSetAttribute", e;
         if (cluster > 8) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) return g_launch_step = "cudaFuncSetAttribute (cluster size)", e;
         }
         cudaLaunchConfig_t occ = {};
         occ.gridDim = dim3(unsigned(cluster), 1, 1);
@@ -1110,8 +1185,8 @@ cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size
         occ.numAttrs = 1;
         int active = 0;
         e = cudaOccupancyMaxActiveClusters(&active, kern, &occ);
-        if (e != cudaSuccess) return e;
-        if (active < 1) return cudaErrorInvalidConfiguration;
+        if (e != cudaSuccess) return g_launch_step = "cudaOccupancyMaxActiveClusters", e;
+        if (active < 1) return g_launch_step = "occupancy (no cluster fits)", cudaErrorInvalidConfiguration;
         cached_smem = smem;
         cached_cluster = cluster;
         cached_active = active;
@@ -1130,8 +1205,13 @@ cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, kern, P);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    if (e != cudaSuccess) {
+        static thread_local char what[160];
+        snprintf(what, sizeof(what), "cudaLaunchKernelEx (cluster %d, grid %d x %lld, %zu B shared, %d active)",
+                 cluster, cluster, (long long)gy, smem, cached_active);
+        g_launch_step = what;
+    }
+    return e;
 }
 
 // One translation unit per (row type, R) instantiates the four G variants.

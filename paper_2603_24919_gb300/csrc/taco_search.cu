@@ -884,14 +884,10 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.unit_off = L.unit_off;
             P.unit_len = L.unit_len;
             P.arena = L.arena;
-            P.arena_cap = L.arena_cap;
-            P.arena_used = L.arena_used;
             P.qflag = L.qflag;
-            TACO_CUDA(cudaMemsetAsync(L.arena_used, 0, sizeof(uint32_t), st));
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit
-            const size_t smem1 = P.region_a + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
-                                 size_t(kCellBatch + kRunPad) * 4 + 16 * 4;
+            const size_t smem1 = P.region_a + kCountListsExtra;
             static thread_local size_t c1_smem = 0;
             static thread_local int c1_blocks = 0;
             if (c1_smem != smem1) {
@@ -905,9 +901,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                 c1_blocks = per_sm * sms;
                 c1_smem = smem1;
             }
-            const int64_t units = L.nq * ix->cluster;
             if (int rc = prof_begin(ix, 2, st, &pb, &pe)) return rc;
-            count_lists_kernel<<<unsigned(std::min<int64_t>(units, c1_blocks)), kRrThreads, smem1, st>>>(P);
+            count_lists_kernel<<<unsigned(std::min<int64_t>(L.nq, c1_blocks)), kRrThreads, smem1, st>>>(P);
             TACO_CUDA(cudaGetLastError());
             if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results
