@@ -48,7 +48,7 @@ K = 10
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="taco", choices=["taco", "reference"])
     ap.add_argument("--nq", type=int, default=None)
@@ -64,6 +64,25 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def shard(total, ws, rank):
+    """Half-open range of the units (queries) rank `rank` of `ws` answers: contiguous,
+    disjoint, covering [0, total), sizes differing by at most one."""
+    base, extra = divmod(total, ws)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def max_over_ranks(values, ws, device=None):
+    """Element-wise maximum of a list of floats over all ranks (identity when ws == 1)."""
+    if ws == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
 
 
 def log(*a):
@@ -196,7 +215,13 @@ def run_taco(args):
     if ws > 1:
         dist.barrier()
     t0 = time.time()
-    w, data, queries = make_workload(WORKLOAD, nq=args.nq)
+    # weak scaling: every rank answers its own batch of the per-rank size, drawn from one
+    # pool of ws * nq queries (rank r takes slice r); no collective on the data path
+    nq_rank = args.nq or 10_000
+    w, data, pool = make_workload(WORKLOAD, nq=nq_rank * ws)
+    lo, hi = shard(pool.shape[0], ws, rank)
+    queries = np.ascontiguousarray(pool[lo:hi])
+    del pool
     nq = queries.shape[0]
     log(f"[rank {rank}] workload {w.name}: n={w.n} d={w.d} nq={nq} ({time.time() - t0:.1f}s)")
     t0 = time.time()
@@ -280,15 +305,13 @@ def run_taco(args):
 
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.5)   # nvidia-smi is sampling before the timed region starts
     tot_b, per_b, kt_b, rec_b = run_steps("bf16", args.steps, args.warmup, profile=True)
     tot_f, per_f, kt_f, rec_f = run_steps("fp32", args.steps, args.warmup, profile=True)
     clk = clocks.stop()
 
     # max over ranks of the timed region
-    if ws > 1:
-        t = torch.tensor([tot_b, tot_f], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_b, tot_f = float(t[0]), float(t[1])
+    tot_b, tot_f = max_over_ranks([tot_b, tot_f], ws, device="cuda")
     value = ws * nq * args.steps / (tot_b * 1e-3)
     value_fp32 = ws * nq * args.steps / (tot_f * 1e-3)
 
@@ -308,10 +331,7 @@ def run_taco(args):
     for _ in range(args.steps):
         ix.search(qh, K, bud, tgt, precision="bf16", shortlist_mult=mult, out_ids=oi, out_dists=od)
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks([e2e_s], ws, device="cuda")[0]
     e2e_recall = recall_at(oi, truth, K)
 
     # ---- roofline of the dominant kernel ----------------------------------------------
