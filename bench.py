@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--alpha", type=float, default=None, help="skip calibration (both forms)")
     ap.add_argument("--beta", type=float, default=None)
+    ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving runs")
+    ap.add_argument("--serve-seconds", type=float, default=0.3,
+                    help="arrival span of each offered load in the serving runs")
     return ap.parse_args()
 
 
@@ -372,6 +375,10 @@ def run_taco(args):
         e1.synchronize()
         lat_small.append(e0.elapsed_time(e1))
 
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(ix, queries, truth, bud, tgt, mult, args.serve_seconds)
+
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -414,6 +421,8 @@ def run_taco(args):
                      "kernel_share": shares},
         "clocks": clk,
     }
+    if serving is not None:
+        line["serving"] = serving
     line["kernel_ms_per_step_fp32"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                        for k, v in kt_f.items() if v["launches"]}
     line["kernel_ms_per_step_bf16"] = {k: round(v["ms"] / max(args.steps, 1), 4)
@@ -427,6 +436,45 @@ def run_taco(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_serving(ix, queries, truth, bud, tgt, mult, span_s):
+    """Open-loop Poisson arrivals through the continuous-batching server (taco_server_*,
+    BF16 rows at the BF16 operating point): per offered load, achieved QPS and p50/p99
+    latency (arrival to results in host memory), and recall@10 of the served answers.
+    The mixed load draws k from {10, 100} per request."""
+    from paper_2603_24919_gb300 import TacoServer, query_params
+
+    rng = np.random.default_rng(1234)
+    nq = queries.shape[0]
+    kmax = 100
+    max_list = min(mult * kmax, 512)
+    out = []
+    with TacoServer(ix, max_batch=2048, slots=4, queue_capacity=16384, max_list=max_list,
+                    precision="bf16", max_wait_us=100, use_graphs=True) as srv:
+        def one(rate, mixed, n_req=None):
+            n_req = n_req or max(2000, int(rate * span_s))
+            rows = np.arange(n_req) % nq
+            ks = rng.choice([10, 100], size=n_req) if mixed else np.full(n_req, 10)
+            per = [query_params(int(k), bud, tgt, "bf16", "literal", mult) for k in ks]
+            arrival = np.cumsum(rng.exponential(1e9 / rate, size=n_req)).astype(np.int64)
+            ids, _, lat = srv.replay(queries[rows], per, arrival, kmax)
+            span = float(np.max(arrival + lat) - arrival[0]) * 1e-9
+            sel = ks == 10
+            return {"offered_qps": rate, "requests": int(n_req), "mixed_k": bool(mixed),
+                    "achieved_qps": round(n_req / span, 1),
+                    "p50_ms": round(float(np.percentile(lat, 50)) * 1e-6, 4),
+                    "p99_ms": round(float(np.percentile(lat, 99)) * 1e-6, 4),
+                    "recall_at_10": round(recall_at(ids[sel], truth[rows[sel]], K), 4)}
+        one(500_000, True, n_req=20_000)   # warm-up: graphs for the batch buckets
+        for rate in (10_000, 100_000, 200_000, 500_000, 1_000_000):
+            out.append(one(rate, False))
+        out.append(one(200_000, True))
+        st = srv.stats()
+    return {"server": "max_batch 2048, 4 slots, max_wait 100 us, CUDA graphs, BF16 rows",
+            "loads": out, "batches": st["batches"], "graph_launches": st["graph_launches"],
+            "max_in_flight": st["max_in_flight"],
+            "mean_batch": round(st["completed"] / max(st["batches"], 1), 1)}
 
 
 def cpu_baseline(ix, data, queries, w, op, seconds):
@@ -514,6 +562,10 @@ def run_reference(args):
     value = args.steps * per_step / total
     sample = (f"{per_step} queries per step of the {len(queries)}-query batch, alpha={alpha} "
               f"beta={beta}, single-threaded NumPy FP64 oracle")
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(ix, queries, truth, bud, tgt, mult, args.serve_seconds)
+
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,

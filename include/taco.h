@@ -41,6 +41,7 @@ extern "C" {
 #define TACO_ETIMEOUT (-4)  /* reserved: a bounded device wait gave up */
 #define TACO_ECAPACITY (-5) /* the request exceeds a compiled capacity (n, k, sqrt_k) */
 #define TACO_EIO (-6)       /* file could not be read or written, or has a bad format */
+#define TACO_EAGAIN (-7)    /* a server's request queue is full: collect results, then retry */
 
 /* ---- enums ------------------------------------------------------------------------- */
 #define TACO_PREC_FP32 0    /* re-rank candidates with FP32 distances */
@@ -210,6 +211,111 @@ int taco_profile_enable(taco_index* index, int32_t enable);
 /* taco_profile_read -- wait for the recorded events, add their elapsed times to *out
  * (host struct, overwritten) and, if reset != 0, clear the accumulated totals. */
 int taco_profile_read(taco_index* index, taco_kernel_times* out, int32_t reset);
+
+/* ---- serving loop ---------------------------------------------------------------------
+ * A server keeps an index resident and answers single-query requests (Alg. 6 per query)
+ * with continuous batching: a dispatcher thread packs the requests waiting in its queue
+ * into device batches and launches each on one of `slots` CUDA streams, each stream with
+ * its own device workspace and pinned staging, so batches that are admitted while others
+ * run overlap on the device; a completion thread hands results back as batches finish.
+ * A request's result depends on that request alone (its query and parameters), never on
+ * the batch it rode in. The paper has no serving loop; this is the deployment form of the
+ * same search kernels.
+ *
+ * Admission: a request enters the queue only if fewer than queue_capacity requests are
+ * held (else TACO_EAGAIN). A batch takes queued requests in arrival order while its
+ * device workspace (per-query probed-cell lists, collision-count level lists, top lists
+ * sized by the largest list length in the batch) fits the slot's slot_bytes and it has
+ * fewer than max_batch queries. A batch is dispatched when a slot is free and either no
+ * batch is running, the batch is full, or its oldest request has waited max_wait_us.
+ * With use_graphs, each slot replays a CUDA graph captured per (batch-size bucket, list
+ * bucket); batches are padded to the bucket with copies of their first request, whose
+ * results are dropped. The index must outlive the server, must not be freed or profiled
+ * while the server runs, and may still be searched directly (taco_search_batch) meanwhile.
+ */
+typedef struct taco_server taco_server;
+
+typedef struct {
+    int32_t max_batch;       /* queries per device batch, 1..16384 */
+    int32_t slots;           /* device batches in flight at once, 1..8 */
+    int32_t queue_capacity;  /* requests held at once (queued, running, or done but not yet
+                                collected by taco_server_wait), >= max_batch */
+    int32_t max_list;        /* largest list length a request may need: k, or for BF16
+                                min(shortlist_mult * k, TACO_MAX_K); 1..TACO_MAX_K */
+    int32_t precision;       /* TACO_PREC_* of every request */
+    int32_t select_rule;     /* TACO_SELECT_* of every request */
+    int64_t max_wait_us;     /* longest a queued request waits for its batch to fill, >= 0 */
+    int64_t slot_bytes;      /* device workspace per slot; 0 = enough for max_batch queries
+                                at max_list. Smaller values admit fewer queries per batch */
+    int32_t use_graphs;      /* nonzero: replay captured CUDA graphs (see above) */
+    int32_t reserved;        /* must be 0 */
+} taco_server_params;
+
+/* Timing of one request, steady clock in nanoseconds. */
+typedef struct {
+    int64_t submit_ns;       /* taco_server_submit accepted it */
+    int64_t dispatch_ns;     /* its batch was launched */
+    int64_t done_ns;         /* its batch's results reached host memory */
+    int32_t batch_size;      /* real queries in that batch */
+    int32_t slot;            /* the slot (stream) that ran it */
+} taco_request_info;
+
+typedef struct {
+    int64_t submitted, completed, rejected;   /* requests accepted / answered / EAGAIN */
+    int64_t batches, graph_launches, graph_captures;
+    int64_t max_batch_seen;                   /* largest batch launched */
+    int64_t max_in_flight;                    /* most batches running at once */
+    int64_t slot_bytes;                       /* device workspace per slot */
+} taco_server_stats;
+
+/*
+ * taco_server_create -- start a server on `index` (the current device must be the index's).
+ * Allocates every slot's stream, device workspace and pinned staging, and starts the
+ * dispatcher and completion threads. Errors: TACO_EINVAL (bad parameters), TACO_ENOMEM,
+ * TACO_ECUDA, TACO_ECAPACITY (slot_bytes too small for one query at max_list).
+ */
+int taco_server_create(const taco_index* index, const taco_server_params* params,
+                       taco_server** out);
+
+/*
+ * taco_server_submit -- queue one request. query: host pointer, [d] float32 (copied before
+ * return). params: host pointer; its precision and select_rule must match the server's and
+ * its list length must not exceed max_list. On success *ticket names the request.
+ * Returns TACO_EAGAIN when queue_capacity requests are held.
+ */
+int taco_server_submit(taco_server* server, const float* query, const taco_query_params* params,
+                       uint64_t* ticket);
+
+/*
+ * taco_server_wait -- wait up to timeout_us (< 0: no limit) for request `ticket`, then copy
+ * its result to host buffers ids [k_stride] int64 and dists [k_stride] float32 (ascending
+ * by (distance, id); -1 / +inf past min(k, |C|)) and, if info is not NULL, its timing.
+ * Collecting frees the request's place in the queue; each ticket is collected once.
+ * Returns TACO_ETIMEOUT if the request is not done in time (it stays queued), TACO_EINVAL
+ * for an unknown or already collected ticket or k_stride < k, or the error of its batch.
+ */
+int taco_server_wait(taco_server* server, uint64_t ticket, int64_t timeout_us, int32_t k_stride,
+                     int64_t* ids, float* dists, taco_request_info* info);
+
+/* taco_server_get_stats -- counters since creation (host output). */
+int taco_server_get_stats(taco_server* server, taco_server_stats* stats);
+
+/*
+ * taco_server_replay -- open-loop load driver over a server: submits query j (row j of the
+ * host array queries [nq][d], parameters params[j]) at arrival_ns[j] nanoseconds after the
+ * call starts (arrival_ns ascending), retrying on TACO_EAGAIN, while a second thread
+ * collects the results in order into ids / dists [nq][k_stride] and latency_ns[nq] =
+ * completion time - arrival time (queueing included). Returns after every request is
+ * answered, with the first error met, if any.
+ */
+int taco_server_replay(taco_server* server, const float* queries, int64_t nq,
+                       const taco_query_params* params, const int64_t* arrival_ns,
+                       int32_t k_stride, int64_t* ids, float* dists, int64_t* latency_ns);
+
+/* taco_server_destroy -- stop accepting requests, finish the batches in flight, join the
+ * threads and free every slot (NULL is a no-op). Requests still queued and uncollected
+ * results are dropped. No other call on the server may be running or follow. */
+void taco_server_destroy(taco_server* server);
 
 /* taco_free_index -- release an index and all its device memory (NULL is a no-op). */
 void taco_free_index(taco_index* index);

@@ -16,6 +16,7 @@ from .taco import (  # noqa: F401
     SIGNATURES,
     TacoError,
     TacoIndex,
+    TacoServer,
     load_library,
     query_params,
 )

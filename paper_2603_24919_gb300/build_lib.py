@@ -39,6 +39,7 @@ def _units():
         ("taco_search.o", "taco_search.cu", []),
         ("taco_api.o", "taco_api.cu", []),
         ("taco_noalloc.o", "taco_noalloc.cu", []),
+        ("taco_server.o", "taco_server.cu", []),
     ]
     for bf16 in (0, 1):
         for r in (1, 4, 16):

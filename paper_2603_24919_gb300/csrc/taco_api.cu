@@ -336,7 +336,9 @@ int ensure_workspace(taco_index* ix, size_t bytes, size_t host_bytes) {
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-int check_params(const taco_query_params& q, int k_stride) {
+}  // namespace
+
+int taco::check_query_params(const taco_query_params& q, int k_stride) {
     if (q.k < 1 || q.k > k_stride) return fail(TACO_EINVAL, "k = %d must be in [1, k_stride = %d]", q.k, k_stride);
     if (q.k > TACO_MAX_K) return fail(TACO_ECAPACITY, "k = %d exceeds %d", q.k, TACO_MAX_K);
     if (q.budget < 1) return fail(TACO_EINVAL, "budget must be >= 1");
@@ -350,7 +352,7 @@ int check_params(const taco_query_params& q, int k_stride) {
     return TACO_OK;
 }
 
-int list_len(const taco_query_params& q) {
+int taco::query_list_len(const taco_query_params& q) {
     if (q.precision == TACO_PREC_BF16) {
         const int64_t m = int64_t(q.k) * q.shortlist_mult;
         return int(std::min<int64_t>(std::max<int64_t>(m, q.k), TACO_MAX_K));
@@ -358,16 +360,60 @@ int list_len(const taco_query_params& q) {
     return q.k;
 }
 
-QueryParamsDev to_dev(const taco_query_params& q) {
+QueryParamsDev taco::query_params_dev(const taco_query_params& q) {
     QueryParamsDev r;
     r.k = q.k;
     r.select_rule = q.select_rule;
     r.budget = q.budget;
     r.rerank_target = q.rerank_target;
-    r.kk = list_len(q);
+    r.kk = query_list_len(q);
     r.pad = 0;
     return r;
 }
+
+SearchLayout taco::plan_search(const taco_index* ix, int64_t chunk, int kk_max, int64_t n_params,
+                               bool stage_queries, bool stage_ids, bool stage_dists, int k_stride) {
+    const int Ns = ix->Ns, K = ix->K;
+    SearchLayout l;
+    size_t off = 0;
+    l.qt = off; off = align_up(off + size_t(chunk) * ix->Dp * 4);
+    l.cells = off; off = align_up(off + size_t(chunk) * Ns * K * 2);
+    l.nc = off; off = align_up(off + size_t(chunk) * Ns * 4);
+    l.ret = off; off = align_up(off + size_t(chunk) * Ns * 8);
+    const size_t lists = size_t(chunk) * ix->cluster * kListsPerCta * kk_max * 4;
+    l.ld = off; off = align_up(off + lists);
+    l.li = off; off = align_up(off + lists);
+    // two-pass form: per-unit level counts and lists (a fixed arena slot of kArenaPerUnit
+    // ids per unit; units that do not fit send their query to the cluster kernel)
+    const size_t units = size_t(chunk) * ix->cluster;
+    l.uge = off; off = align_up(off + units * 16 * 4);
+    l.uoff = off; off = align_up(off + units * 4);
+    l.ulen = off; off = align_up(off + units * 4);
+    l.arena = off; off = align_up(off + units * kArenaPerUnit * 4);
+    l.qflag = off; off = align_up(off + size_t(chunk) * 4);
+    l.par = off; off = align_up(off + size_t(n_params) * sizeof(QueryParamsDev));
+    l.q = off; off = align_up(off + (stage_queries ? size_t(chunk) * ix->d * 4 : 0));
+    l.oi = off; off = align_up(off + (stage_ids ? size_t(chunk) * k_stride * 8 : 0));
+    l.od = off; off = align_up(off + (stage_dists ? size_t(chunk) * k_stride * 4 : 0));
+    l.total = off;
+    return l;
+}
+
+void taco::bind_workspace(SearchLaunch& L, const SearchLayout& lay, char* wb) {
+    L.qt = reinterpret_cast<float*>(wb + lay.qt);
+    L.cells = reinterpret_cast<uint16_t*>(wb + lay.cells);
+    L.ncells = reinterpret_cast<int32_t*>(wb + lay.nc);
+    L.retrieved = reinterpret_cast<int64_t*>(wb + lay.ret);
+    L.lists_d = reinterpret_cast<float*>(wb + lay.ld);
+    L.lists_i = reinterpret_cast<uint32_t*>(wb + lay.li);
+    L.unit_ge = reinterpret_cast<uint32_t*>(wb + lay.uge);
+    L.unit_off = reinterpret_cast<uint32_t*>(wb + lay.uoff);
+    L.unit_len = reinterpret_cast<uint32_t*>(wb + lay.ulen);
+    L.arena = reinterpret_cast<uint32_t*>(wb + lay.arena);
+    L.qflag = reinterpret_cast<uint32_t*>(wb + lay.qflag);
+}
+
+namespace {
 
 int search_impl(const taco_index* cix, const float* queries, int64_t nq, const taco_query_params* per_query,
                 const taco_query_params* defaults, int32_t k_stride, int64_t* out_ids, float* out_dists,
@@ -384,14 +430,14 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     int kk_max = 0;
     if (per_query) {
         for (int64_t j = 0; j < nq; ++j) {
-            TRY(check_params(per_query[j], k_stride));
+            TRY(check_query_params(per_query[j], k_stride));
             if (per_query[j].precision != precision || per_query[j].select_rule != head.select_rule)
                 return fail(TACO_EINVAL, "precision and select_rule must be uniform in a batch");
-            kk_max = std::max(kk_max, list_len(per_query[j]));
+            kk_max = std::max(kk_max, query_list_len(per_query[j]));
         }
     } else {
-        TRY(check_params(*defaults, k_stride));
-        kk_max = list_len(*defaults);
+        TRY(check_query_params(*defaults, k_stride));
+        kk_max = query_list_len(*defaults);
     }
     if (precision == TACO_PREC_BF16 && !ix->d_data_bf16)
         return fail(TACO_EINVAL, "BF16 search needs an index built with keep_bf16");
@@ -405,36 +451,16 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     std::lock_guard<std::mutex> lock(ix->ws_mu);
     const int64_t chunk = std::min<int64_t>(nq, kQueryChunk);
     const int Ns = ix->Ns, K = ix->K;
-    // device workspace layout
-    size_t off = 0;
-    const size_t o_qt = off; off = align_up(off + size_t(chunk) * ix->Dp * 4);
-    const size_t o_cells = off; off = align_up(off + size_t(chunk) * Ns * K * 2);
-    const size_t o_nc = off; off = align_up(off + size_t(chunk) * Ns * 4);
-    const size_t o_ret = off; off = align_up(off + size_t(chunk) * Ns * 8);
-    const size_t lists = size_t(chunk) * ix->cluster * kListsPerCta * kk_max * 4;
-    const size_t o_ld = off; off = align_up(off + lists);
-    const size_t o_li = off; off = align_up(off + lists);
-    // two-pass form: per-unit level counts and lists (a fixed arena slot of kArenaPerUnit
-    // ids per unit; units that do not fit send their query to the cluster kernel)
-    const size_t units = size_t(chunk) * ix->cluster;
-    const size_t arena_cap = units * kArenaPerUnit;
-    const size_t o_uge = off; off = align_up(off + units * 16 * 4);
-    const size_t o_uoff = off; off = align_up(off + units * 4);
-    const size_t o_ulen = off; off = align_up(off + units * 4);
-    const size_t o_arena = off; off = align_up(off + arena_cap * 4);
-    const size_t o_qflag = off; off = align_up(off + size_t(chunk) * 4);
-    const size_t o_par = off; off = align_up(off + (per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0));
-    const size_t o_q = off; off = align_up(off + (q_dev ? 0 : size_t(chunk) * ix->d * 4));
-    const size_t o_oi = off; off = align_up(off + (id_dev ? 0 : size_t(chunk) * k_stride * 8));
-    const size_t o_od = off; off = align_up(off + (dist_dev ? 0 : size_t(chunk) * k_stride * 4));
+    const SearchLayout lay = plan_search(ix, chunk, kk_max, per_query ? nq : 0, !q_dev, !id_dev, !dist_dev,
+                                         k_stride);
     const size_t host_need = per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0;
-    TRY(ensure_workspace(ix, off, host_need));
+    TRY(ensure_workspace(ix, lay.total, host_need));
     char* wb = static_cast<char*>(ix->ws.base);
     QueryParamsDev* dparams = nullptr;
     if (per_query) {
         QueryParamsDev* hp = static_cast<QueryParamsDev*>(ix->ws.host_pinned);
-        for (int64_t j = 0; j < nq; ++j) hp[j] = to_dev(per_query[j]);
-        dparams = reinterpret_cast<QueryParamsDev*>(wb + o_par);
+        for (int64_t j = 0; j < nq; ++j) hp[j] = query_params_dev(per_query[j]);
+        dparams = reinterpret_cast<QueryParamsDev*>(wb + lay.par);
         TACO_CUDA(cudaMemcpyAsync(dparams, hp, size_t(nq) * sizeof(QueryParamsDev), cudaMemcpyHostToDevice, st));
     }
     for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
@@ -445,27 +471,17 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         if (q_dev) {
             L.queries = queries + c0 * ix->d;
         } else {
-            float* dq = reinterpret_cast<float*>(wb + o_q);
+            float* dq = reinterpret_cast<float*>(wb + lay.q);
             TACO_CUDA(cudaMemcpyAsync(dq, queries + c0 * ix->d, size_t(cn) * ix->d * 4, cudaMemcpyHostToDevice, st));
             L.queries = dq;
         }
-        L.defaults = to_dev(head);
+        L.defaults = query_params_dev(head);
         L.params = dparams ? dparams + c0 : nullptr;
         L.precision = precision;
         L.kk_max = kk_max;
-        L.qt = reinterpret_cast<float*>(wb + o_qt);
-        L.cells = reinterpret_cast<uint16_t*>(wb + o_cells);
-        L.ncells = reinterpret_cast<int32_t*>(wb + o_nc);
-        L.retrieved = reinterpret_cast<int64_t*>(wb + o_ret);
-        L.lists_d = reinterpret_cast<float*>(wb + o_ld);
-        L.lists_i = reinterpret_cast<uint32_t*>(wb + o_li);
-        L.unit_ge = reinterpret_cast<uint32_t*>(wb + o_uge);
-        L.unit_off = reinterpret_cast<uint32_t*>(wb + o_uoff);
-        L.unit_len = reinterpret_cast<uint32_t*>(wb + o_ulen);
-        L.arena = reinterpret_cast<uint32_t*>(wb + o_arena);
-        L.qflag = reinterpret_cast<uint32_t*>(wb + o_qflag);
-        L.out_ids = id_dev ? out_ids + c0 * k_stride : reinterpret_cast<int64_t*>(wb + o_oi);
-        L.out_dists = dist_dev ? out_dists + c0 * k_stride : reinterpret_cast<float*>(wb + o_od);
+        bind_workspace(L, lay, wb);
+        L.out_ids = id_dev ? out_ids + c0 * k_stride : reinterpret_cast<int64_t*>(wb + lay.oi);
+        L.out_dists = dist_dev ? out_dists + c0 * k_stride : reinterpret_cast<float*>(wb + lay.od);
         L.k_stride = k_stride;
         if (dbg) {
             L.dbg.query_t = dbg->query_t ? dbg->query_t + c0 * ix->Dp : nullptr;

@@ -51,6 +51,11 @@ extern thread_local const char* g_launch_step;
 
 bool is_device_pointer(const void* p);
 
+// Raise a kernel's dynamic shared memory limit to at least `bytes` on the current device.
+// The limit only ever grows, process-wide, so launches prepared by different threads (a
+// server's dispatcher, callers of the batch API) never lower it under one another.
+cudaError_t ensure_dynamic_smem(const void* func, size_t bytes);
+
 // Host FP64 linear algebra (build side).
 void jacobi_eigen(int d, std::vector<double>& a, std::vector<double>& vecs,
                   std::vector<double>& vals);
@@ -139,8 +144,25 @@ struct SearchLaunch {
     float* out_dists;
     int k_stride;
     taco_debug_out dbg;        // device pointers, already offset to this chunk
+    bool skip_profile;         // record no profiling events (launches that may be captured)
 };
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
+
+// Byte offsets of one launch group's device workspace (each 256-byte aligned).
+struct SearchLayout {
+    size_t qt, cells, nc, ret, ld, li, uge, uoff, ulen, arena, qflag, par, q, oi, od;
+    size_t total;
+};
+// Workspace of `chunk` queries with lists of kk_max entries; `n_params` per-query parameter
+// records, and staging for queries / ids / distances when the caller's are not on the device.
+SearchLayout plan_search(const taco_index* ix, int64_t chunk, int kk_max, int64_t n_params,
+                         bool stage_queries, bool stage_ids, bool stage_dists, int k_stride);
+// The workspace pointers of a SearchLaunch over `wb` laid out by `lay` (two-pass form).
+void bind_workspace(SearchLaunch& L, const SearchLayout& lay, char* wb);
+// Device form of the query parameters and the list length they need.
+int check_query_params(const taco_query_params& q, int k_stride);
+int query_list_len(const taco_query_params& q);
+QueryParamsDev query_params_dev(const taco_query_params& q);
 // Event pair around one kernel launch when profiling is enabled (no-op otherwise).
 int prof_begin(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t* b, cudaEvent_t* e);
 int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent_t e);

@@ -953,7 +953,7 @@ constexpr int kSrWarps = kSrThreads / 32;
 constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
 
 template <int G, int R, bool BF16>
-__global__ void __launch_bounds__(kSrThreads)
+__global__ void __launch_bounds__(kSrThreads, 4)
 select_rerank_kernel(const RerankParams P) {
     constexpr int CPW = 32 / G;
     constexpr int U = 2;
@@ -1091,11 +1091,14 @@ select_rerank_kernel(const RerankParams P) {
         __syncthreads();
         if (warp == 0) warp_merge(Ld, Li, kkc, kSrWarps, kk, Md, Mi, lane);
         __syncthreads();
+        // the query's own shortlist: the first qp.kk of the merged list (a batch's lists
+        // are as long as its longest one; a shorter shortlist is a prefix of them)
+        const int kq = min(qp.kk, kk);
         if constexpr (BF16) {
             // exact FP32 distances of the shortlist, then rank sort by (distance, id)
             const int nf4 = P.d_pad / 4;
             const float4* q4 = reinterpret_cast<const float4*>(qv);
-            for (int e = warp; e < kk; e += kSrWarps) {
+            for (int e = warp; e < kq; e += kSrWarps) {
                 const uint32_t id = Mi[e];
                 float acc = 0.f;
                 if (id != kNoId) {
@@ -1110,11 +1113,11 @@ select_rerank_kernel(const RerankParams P) {
                 }
             }
             __syncthreads();
-            for (int e = tid; e < kk; e += kSrThreads) {
+            for (int e = tid; e < kq; e += kSrThreads) {
                 const float x = Xd[e];
                 const uint32_t xid = Xi[e];
                 int rank = 0;
-                for (int f = 0; f < kk; ++f)
+                for (int f = 0; f < kq; ++f)
                     rank += lt_pair(Xd[f], Xi[f], x, xid) || (Xd[f] == x && Xi[f] == xid && f < e);
                 Md[rank] = x;
                 Mi[rank] = xid;
@@ -1122,7 +1125,7 @@ select_rerank_kernel(const RerankParams P) {
             __syncthreads();
         }
         for (int t = tid; t < P.k_stride; t += kSrThreads) {
-            const bool ok = t < qp.k && t < kk && Mi[t] != kNoId;
+            const bool ok = t < qp.k && t < kq && Mi[t] != kNoId;
             P.out_ids[q * P.k_stride + t] = ok ? int64_t(Mi[t]) : int64_t(-1);
             P.out_dists[q * P.k_stride + t] = ok ? sqrtf(Md[t]) : __int_as_float(0x7f800000);
         }
@@ -1137,7 +1140,7 @@ cudaError_t launch_select_rerank_t(const RerankParams& P, int64_t nq, size_t sme
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return g_launch_step = "an earlier unchecked call", e;
     if (cached_smem != smem) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
         if (e != cudaSuccess) return g_launch_step = "cudaFuncSetAttribute", e;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSrThreads, smem);
@@ -1166,7 +1169,7 @@ cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return g_launch_step = "an earlier unchecked call", e;
     if (cached_smem != smem || cached_cluster != cluster) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
         if (e != cudaSuccess) return g_launch_step = "cudaFuncSetAttribute", e;
         if (cluster > 8) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -10,6 +10,10 @@
 // and walks it to the exact threshold key T. Cells with key <= T are the probed set.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <algorithm>
 #include <cstdint>
 
@@ -623,6 +627,15 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
     }
 }
 
+// Shared memory of one warp of final_merge_kernel: the lists and merge buffers, rounded up
+// to 16 bytes, then the query row (d_pad floats; d_pad is a multiple of 8).
+__host__ __device__ __forceinline__ size_t merge_head_bytes(int ncta, int kkc) {
+    return (size_t(ncta) * kkc * 8 + size_t(4) * kkc * 4 + 15) & ~size_t(15);
+}
+__host__ __device__ __forceinline__ size_t merge_warp_bytes(int ncta, int kkc, int d_pad) {
+    return merge_head_bytes(ncta, kkc) + size_t(d_pad) * 4;
+}
+
 // Per query, one warp merges the top lists of every warp of the cluster (Alg. 6 step 9:
 // the k nearest candidates) and writes the result: first the kRrWarps lists of each CTA,
 // then the cluster's CTA lists. For BF16 rows the merged list is a shortlist: the warp
@@ -641,14 +654,14 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
     const int64_t q = int64_t(blockIdx.x) * nw + warp;
     if (q >= nq) return;
     if (qmask && !qmask[q]) return;
-    const size_t per_warp = size_t(ncta) * kkc * 8 + size_t(4) * kkc * 4 + size_t(d_pad) * 4;
-    float* cd = reinterpret_cast<float*>(fm + warp * per_warp);   // [ncta][kkc]
+    float* cd = reinterpret_cast<float*>(fm + warp * merge_warp_bytes(ncta, kkc, d_pad));   // [ncta][kkc]
     uint32_t* ci = reinterpret_cast<uint32_t*>(cd + ncta * kkc);  // [ncta][kkc]
     float* od = reinterpret_cast<float*>(ci + ncta * kkc);
     uint32_t* oi = reinterpret_cast<uint32_t*>(od + kkc);
     float* xd = reinterpret_cast<float*>(oi + kkc);
     uint32_t* xi = reinterpret_cast<uint32_t*>(xd + kkc);
-    float* qv = reinterpret_cast<float*>(xi + kkc);
+    // the query row is read as float4: it starts on a 16-byte boundary
+    float* qv = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(cd) + merge_head_bytes(ncta, kkc));
     const QueryParamsDev qp = params ? params[q] : defaults;
     for (int r = 0; r < ncta; ++r) {
         const size_t row = (size_t(q) * ncta + r) * kRrWarps * kk;
@@ -657,19 +670,22 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
     __syncwarp();
     warp_merge(cd, ci, kkc, ncta, kk, od, oi, lane);
     __syncwarp();
+    // the query's own shortlist: the first qp.kk of the merged list (lists are as long as
+    // the batch's longest; a shorter shortlist is a prefix of them)
+    const int kq = min(qp.kk, kk);
     if constexpr (BF16) {
         for (int j = lane; j < d_pad; j += 32) qv[j] = j < d ? queries[q * d + j] : 0.f;
         __syncwarp();
         const int nf4 = d_pad / 4;
         const float4* q4 = reinterpret_cast<const float4*>(qv);
-        for (int e0 = 0; e0 < kk; e0 += 4) {
+        for (int e0 = 0; e0 < kq; e0 += 4) {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             for (int f = lane; f < nf4; f += 32) {
                 float4 r[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int e = e0 + u;
-                    const uint32_t id = e < kk ? oi[e] : kNoId;
+                    const uint32_t id = e < kq ? oi[e] : kNoId;
                     r[u] = id != kNoId ? __ldg(reinterpret_cast<const float4*>(data + size_t(id) * d_pad) + f)
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -681,7 +697,7 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
 #pragma unroll
                 for (int off = 16; off; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
                 const int e = e0 + u;
-                if (lane == 0 && e < kk) {
+                if (lane == 0 && e < kq) {
                     xd[e] = oi[e] != kNoId ? acc[u] : __int_as_float(0x7f800000);
                     xi[e] = oi[e];
                 }
@@ -689,11 +705,11 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
         }
         __syncwarp();
         // rank sort (ties between padding entries by position)
-        for (int e = lane; e < kk; e += 32) {
+        for (int e = lane; e < kq; e += 32) {
             const float x = xd[e];
             const uint32_t xid = xi[e];
             int rank = 0;
-            for (int f = 0; f < kk; ++f)
+            for (int f = 0; f < kq; ++f)
                 rank += lt_pair(xd[f], xi[f], x, xid) || (xd[f] == x && xi[f] == xid && f < e);
             od[rank] = x;
             oi[rank] = xid;
@@ -701,7 +717,7 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
         __syncwarp();
     }
     for (int t = lane; t < k_stride; t += 32) {
-        const bool ok = t < qp.k && t < kk && oi[t] != kNoId;
+        const bool ok = t < qp.k && t < kq && oi[t] != kNoId;
         out_ids[q * k_stride + t] = ok ? int64_t(oi[t]) : int64_t(-1);
         out_dists[q * k_stride + t] = ok ? sqrtf(od[t]) : __int_as_float(0x7f800000);
     }
@@ -754,10 +770,24 @@ static cudaEvent_t prof_event(Profiler& pr) {
     return pr.pool[pr.used++];
 }
 
+cudaError_t ensure_dynamic_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[{func, dev}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 int prof_begin(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t* b, cudaEvent_t* e) {
     (void)slot;
     *b = *e = nullptr;
-    if (!ix->prof.enabled) return TACO_OK;
+    if (!ix || !ix->prof.enabled) return TACO_OK;
     *b = prof_event(ix->prof);
     *e = prof_event(ix->prof);
     if (!*b || !*e) return fail(TACO_ECUDA, "cudaEventCreate failed");
@@ -774,12 +804,13 @@ int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent
 
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
     taco_index* ix = const_cast<taco_index*>(L.ix);
+    taco_index* pix = L.skip_profile ? nullptr : ix;   // profiling target (none: no events)
     cudaEvent_t pb, pe;
     const int K = ix->K;
     // 1. transform (Alg. 6 step 1)
-    if (int rc = prof_begin(ix, 0, st, &pb, &pe)) return rc;
+    if (int rc = prof_begin(pix, 0, st, &pb, &pe)) return rc;
     TACO_CUDA(launch_project(L.queries, L.nq, ix->d, ix->d, ix->d_obar, ix->d_B, ix->Dp, L.qt, st));
-    if (int rc = prof_end(ix, 0, st, pb, pe)) return rc;
+    if (int rc = prof_end(pix, 0, st, pb, pe)) return rc;
     if (L.dbg.query_t)
         TACO_CUDA(cudaMemcpyAsync(L.dbg.query_t, L.qt, size_t(L.nq) * ix->Dp * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
@@ -789,14 +820,13 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         const size_t smem = size_t(cap) * 8 + kSelBins * 4 + size_t(2) * ix->sk * 4;
         static thread_local bool attr_set = false;
         if (smem > 48 * 1024 && !attr_set) {
-            TACO_CUDA(cudaFuncSetAttribute(probe_cells_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+            TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(probe_cells_kernel), 200 * 1024));
             attr_set = true;
         }
         // the register variant handles K <= 4096, whose list needs at most 48 KB
 
         dim3 grid(unsigned(ix->Ns), unsigned(L.nq));
-        if (int rc = prof_begin(ix, 1, st, &pb, &pe)) return rc;
+        if (int rc = prof_begin(pix, 1, st, &pb, &pe)) return rc;
         // the row-merge walk settles small budgets; the histogram kernel redoes what it flags
         // (and does everything when the debug flags are wanted or the budget needs many pops)
         bool walk = L.dbg.probed == nullptr && ix->sk <= 128;
@@ -833,7 +863,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                 L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo);
 #undef TACO_PROBE_REG
         TACO_CUDA(cudaGetLastError());
-        if (int rc = prof_end(ix, 1, st, pb, pe)) return rc;
+        if (int rc = prof_end(pix, 1, st, pb, pe)) return rc;
         if (L.dbg.retrieved_num)
             TACO_CUDA(cudaMemcpyAsync(L.dbg.retrieved_num, L.retrieved,
                                       size_t(L.nq) * ix->Ns * sizeof(int64_t),
@@ -891,8 +921,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             static thread_local size_t c1_smem = 0;
             static thread_local int c1_blocks = 0;
             if (c1_smem != smem1) {
-                TACO_CUDA(cudaFuncSetAttribute(count_lists_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(smem1)));
+                TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(count_lists_kernel), smem1));
                 int per_sm = 0, sms = 0;
                 TACO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, count_lists_kernel, kRrThreads,
                                                                         smem1));
@@ -901,15 +930,15 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                 c1_blocks = per_sm * sms;
                 c1_smem = smem1;
             }
-            if (int rc = prof_begin(ix, 2, st, &pb, &pe)) return rc;
+            if (int rc = prof_begin(pix, 2, st, &pb, &pe)) return rc;
             count_lists_kernel<<<unsigned(std::min<int64_t>(L.nq, c1_blocks)), kRrThreads, smem1, st>>>(P);
             TACO_CUDA(cudaGetLastError());
-            if (int rc = prof_end(ix, 2, st, pb, pe)) return rc;
+            if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results
             const size_t smem2 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 +
                                  size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4;
             cudaError_t e;
-            if (int rc = prof_begin(ix, 3, st, &pb, &pe)) return rc;
+            if (int rc = prof_begin(pix, 3, st, &pb, &pe)) return rc;
             if (!bf16) {
                 e = R == 1 ? launch_select_b0_r1(G, P, L.nq, smem2, st)
                     : R == 4 ? launch_select_b0_r4(G, P, L.nq, smem2, st)
@@ -920,14 +949,14 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                              : launch_select_b1_r16(G, P, L.nq, smem2, st);
             }
             if (e != cudaSuccess) return cuda_fail(e, "select_rerank launch", __FILE__, __LINE__);
-            if (int rc = prof_end(ix, 3, st, pb, pe)) return rc;
+            if (int rc = prof_end(pix, 3, st, pb, pe)) return rc;
             P.qmask = L.qflag;   // the cluster kernel below only answers flagged queries
         }
         // cluster kernel: every query (single-pass form) or the flagged ones
         const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
                             size_t(kListCap) * 4 + size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 32 * 4;
         cudaError_t e;
-        if (int rc = prof_begin(ix, 4, st, &pb, &pe)) return rc;
+        if (int rc = prof_begin(pix, 4, st, &pb, &pe)) return rc;
         if (!bf16) {
             e = R == 1 ? launch_rerank_b0_r1(G, P, ix->cluster, L.nq, smem, st)
                 : R == 4 ? launch_rerank_b0_r4(G, P, ix->cluster, L.nq, smem, st)
@@ -938,21 +967,20 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                          : launch_rerank_b1_r16(G, P, ix->cluster, L.nq, smem, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "count_select_rerank launch", __FILE__, __LINE__);
-        if (int rc = prof_end(ix, 4, st, pb, pe)) return rc;
+        if (int rc = prof_end(pix, 4, st, pb, pe)) return rc;
         // merge of the cluster kernel's lists (and BF16 shortlist re-rank)
-        const size_t per_warp = size_t(ix->cluster) * P.kkc * 8 + size_t(4) * P.kkc * 4 + size_t(ix->d_pad) * 4;
+        const size_t per_warp = merge_warp_bytes(ix->cluster, P.kkc, ix->d_pad);
         int fw = 8;
         while (fw > 1 && size_t(fw) * per_warp > 160 * 1024) fw >>= 1;
         const size_t fsm = size_t(fw) * per_warp;
         auto fk = bf16 ? final_merge_kernel<true> : final_merge_kernel<false>;
-        if (fsm > 48 * 1024)
-            TACO_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm)));
-        if (int rc = prof_begin(ix, 5, st, &pb, &pe)) return rc;
+        if (fsm > 48 * 1024) TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(fk), fsm));
+        if (int rc = prof_begin(pix, 5, st, &pb, &pe)) return rc;
         fk<<<unsigned((L.nq + fw - 1) / fw), fw * 32, fsm, st>>>(
             L.lists_d, L.lists_i, ix->cluster, P.kk, P.kkc, L.queries, ix->d, ix->d_pad, ix->d_data,
             L.defaults, L.params, L.nq, L.out_ids, L.out_dists, L.k_stride, P.qmask);
         TACO_CUDA(cudaGetLastError());
-        if (int rc = prof_end(ix, 5, st, pb, pe)) return rc;
+        if (int rc = prof_end(pix, 5, st, pb, pe)) return rc;
     }
     return TACO_OK;
 }

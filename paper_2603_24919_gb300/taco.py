@@ -15,7 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtaco.so")
 
 OK = 0
-EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO = -1, -2, -3, -4, -5, -6
+EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO, EAGAIN = -1, -2, -3, -4, -5, -6, -7
 PREC_FP32, PREC_BF16 = 0, 1
 SELECT_LITERAL, SELECT_PROSE = 0, 1
 MAX_SUBSPACES, MAX_SQRT_K, MAX_K = 15, 128, 512
@@ -55,6 +55,25 @@ class DebugOut(C.Structure):
                 ("last_collision", C.c_void_p), ("candidate_num", C.c_void_p)]
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("queue_capacity", C.c_int32),
+                ("max_list", C.c_int32), ("precision", C.c_int32), ("select_rule", C.c_int32),
+                ("max_wait_us", C.c_int64), ("slot_bytes", C.c_int64), ("use_graphs", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("submit_ns", C.c_int64), ("dispatch_ns", C.c_int64), ("done_ns", C.c_int64),
+                ("batch_size", C.c_int32), ("slot", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
+                ("batches", C.c_int64), ("graph_launches", C.c_int64),
+                ("graph_captures", C.c_int64), ("max_batch_seen", C.c_int64),
+                ("max_in_flight", C.c_int64), ("slot_bytes", C.c_int64)]
+
+
 NUM_KERNELS = 6
 KERNEL_NAMES = ("project", "probe_cells", "count_lists", "select_rerank", "cluster_count_select",
                 "final_merge")
@@ -87,6 +106,15 @@ SIGNATURES = {
     "taco_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "taco_profile_read": (C.c_int, [C.c_void_p, C.POINTER(KernelTimes), C.c_int32]),
     "taco_free_index": (None, [C.c_void_p]),
+    "taco_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
+    "taco_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(QueryParams),
+                                     C.POINTER(C.c_uint64)]),
+    "taco_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.POINTER(RequestInfo)]),
+    "taco_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "taco_server_replay": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "taco_server_destroy": (None, [C.c_void_p]),
     "taco_last_error": (C.c_char_p, []),
 }
 
@@ -339,3 +367,83 @@ class TacoIndex:
             _stream_handle(stream)))
         dbg["ids"], dbg["dists"] = out_ids, out_dists
         return dbg
+
+
+class TacoServer:
+    """Continuous-batching request loop over a resident index (taco_server_* in the C ABI).
+
+    Requests are single host queries; the library's dispatcher thread batches them onto
+    `slots` CUDA streams and a completion thread hands back each request's result."""
+
+    def __init__(self, index, max_batch=256, slots=2, queue_capacity=None, max_list=10,
+                 precision="fp32", select_rule="literal", max_wait_us=200, slot_bytes=0,
+                 use_graphs=True):
+        self.index = index   # keeps the index alive while the server runs
+        self.d = index.info()["d"]
+        p = ServerParams(int(max_batch), int(slots), int(queue_capacity or 4 * max_batch),
+                         int(max_list), _PREC.get(precision, precision),
+                         _RULE.get(select_rule, select_rule), int(max_wait_us), int(slot_bytes),
+                         int(bool(use_graphs)), 0)
+        h = C.c_void_p()
+        _check(load_library().taco_server_create(index._h, C.byref(p), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().taco_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, query, k, budget, rerank_target, precision="fp32", select_rule="literal",
+               shortlist_mult=4):
+        """Queue one query (host array [d]); returns its ticket. Raises TacoError with code
+        EAGAIN when the queue is full."""
+        q = np.ascontiguousarray(query, dtype=np.float32).reshape(-1)
+        assert q.shape[0] == self.d
+        p = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult)
+        t = C.c_uint64()
+        _check(load_library().taco_server_submit(self._h, q.ctypes.data, C.byref(p), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket, k_stride, timeout_us=-1):
+        """(ids int64 [k_stride], dists float32 [k_stride], info dict) of a request."""
+        ids = np.empty(k_stride, dtype=np.int64)
+        dists = np.empty(k_stride, dtype=np.float32)
+        info = RequestInfo()
+        _check(load_library().taco_server_wait(self._h, C.c_uint64(ticket), int(timeout_us),
+                                               int(k_stride), ids.ctypes.data, dists.ctypes.data,
+                                               C.byref(info)))
+        return ids, dists, {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+
+    def replay(self, queries, per_query, arrival_ns, k_stride):
+        """Open-loop replay: query j is submitted arrival_ns[j] ns after the start. Returns
+        (ids [nq,k_stride], dists [nq,k_stride], latency_ns [nq])."""
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        nq = q.shape[0]
+        arr = (QueryParams * nq)()
+        for j, item in enumerate(per_query):
+            arr[j] = item if isinstance(item, QueryParams) else query_params(**item)
+        arrival = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        ids = np.empty((nq, k_stride), dtype=np.int64)
+        dists = np.empty((nq, k_stride), dtype=np.float32)
+        lat = np.empty(nq, dtype=np.int64)
+        _check(load_library().taco_server_replay(
+            self._h, q.ctypes.data, nq, C.cast(arr, C.c_void_p), arrival.ctypes.data,
+            int(k_stride), ids.ctypes.data, dists.ctypes.data, lat.ctypes.data))
+        return ids, dists, lat
+
+    def stats(self):
+        st = ServerStats()
+        _check(load_library().taco_server_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}

@@ -54,6 +54,10 @@ def test_last_error_empty_and_null_args(lib):
     out = ctypes.c_void_p()
     assert lib.taco_load_index(b"/nonexistent/file", 0, None, ctypes.byref(out)) == T.EIO
     lib.taco_free_index(None)
+    out = ctypes.c_void_p()
+    assert lib.taco_server_create(None, None, ctypes.byref(out)) == T.EINVAL
+    assert lib.taco_server_submit(None, None, None, None) == T.EINVAL
+    lib.taco_server_destroy(None)
 
 
 _LAYOUT_C = r"""
@@ -70,6 +74,10 @@ int main(void) {
   S(taco_index_info); P(taco_index_info, d_pad); P(taco_index_info, cluster_size);
   P(taco_index_info, device_bytes);
   S(taco_debug_out); P(taco_debug_out, candidate_num);
+  S(taco_server_params); P(taco_server_params, max_wait_us); P(taco_server_params, slot_bytes);
+  P(taco_server_params, use_graphs);
+  S(taco_request_info); P(taco_request_info, batch_size); P(taco_request_info, slot);
+  S(taco_server_stats); P(taco_server_stats, slot_bytes);
   return 0;
 }
 """
@@ -85,7 +93,8 @@ def test_struct_layouts_match_header():
     want = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
     cmap = {"taco_build_params": T.BuildParams, "taco_query_params": T.QueryParams,
             "taco_index_parts": T.IndexParts, "taco_index_info": T.IndexInfo,
-            "taco_debug_out": T.DebugOut}
+            "taco_debug_out": T.DebugOut, "taco_server_params": T.ServerParams,
+            "taco_request_info": T.RequestInfo, "taco_server_stats": T.ServerStats}
     for key, val in want.items():
         if "." in key:
             s, f = key.split(".")

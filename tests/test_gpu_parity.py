@@ -143,6 +143,26 @@ def test_per_query_uneven_batch(tiny):
         assert np.array_equal(a_ids.cpu().numpy()[0], ids[j, :p["k"]])
 
 
+def test_per_query_uneven_bf16_batch_equals_alone(tiny):
+    """BF16 rows with per-query k and shortlist: each query's shortlist is its own, so its
+    answer in a mixed batch equals its answer alone."""
+    w, data, queries, oix, ix = tiny
+    rng = np.random.default_rng(1)
+    pq = [dict(k=int(rng.choice([1, 10, 50])), budget=int(rng.choice([200, 1000, 3000])),
+               rerank_target=int(rng.choice([50, 200, 1000])), precision="bf16",
+               shortlist_mult=int(rng.choice([1, 2, 4]))) for _ in range(24)]
+    kmax = max(p["k"] for p in pq)
+    q = torch.from_numpy(queries[:24]).cuda()
+    ids, dists = ix.search(q, 10, 1000, 200, precision="bf16", per_query=pq, k_stride=kmax)
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    for j, p in enumerate(pq):
+        a_ids, a_d = ix.search(q[j:j + 1], p["k"], p["budget"], p["rerank_target"],
+                               precision="bf16", shortlist_mult=p["shortlist_mult"], k_stride=kmax)
+        assert np.array_equal(a_ids.cpu().numpy()[0], ids[j]), j
+        ok = np.isfinite(dists[j])
+        np.testing.assert_allclose(a_d.cpu().numpy()[0][ok], dists[j][ok], rtol=1e-5)
+
+
 def test_host_pointers_match_device(tiny):
     w, data, queries, oix, ix = tiny
     ids_h, d_h = ix.search(queries[:50], 10, w.budget, w.rerank_target)      # numpy in/out
