@@ -41,7 +41,7 @@ WORKLOAD = "sift1m"
 ALPHAS = [0.01, 0.02, 0.03, 0.05, 0.08, 0.1]
 BETAS = [0.001, 0.002, 0.005, 0.01]
 RECALL_TARGET = 0.95
-SHORTLIST_MULTS = [1, 2, 4]   # BF16 form: exact FP32 re-rank of mult * k
+SHORTLIST_MULTS = {"bf16": [1, 2, 4], "fp8": [2, 4, 8]}   # exact FP32 re-rank of mult * k
 K = 10
 
 
@@ -229,13 +229,14 @@ def run_taco(args):
     log(f"[rank {rank}] workload {w.name}: n={w.n} d={w.d} nq={nq} ({time.time() - t0:.1f}s)")
     t0 = time.time()
     ix = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=20, seed=1,
-                         keep_bf16=True)
+                         keep_bf16=True, keep_fp8=True)
     torch.cuda.synchronize()
     info = ix.info()
     log(f"[rank {rank}] index built in {time.time() - t0:.1f}s: {info}")
     q_dev = torch.from_numpy(queries).cuda()
     data_dev = torch.from_numpy(data).cuda()
     truth = exact_knn_gpu(torch, data_dev, q_dev, data, queries, K)
+    truth_d = np.sqrt(((data[truth].astype(np.float64) - queries[:, None, :].astype(np.float64)) ** 2).sum(-1))
     del data_dev
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
@@ -255,10 +256,10 @@ def run_taco(args):
 
     # ---- calibration: per form, the fastest grid point meeting the recall target ------
     calib = {}
-    for prec in ("fp32", "bf16"):
+    for prec in ("fp32", "bf16", "fp8"):
         best = None
         grid = [(args.alpha, args.beta)] if args.alpha else [(a, b) for a in ALPHAS for b in BETAS]
-        mults = SHORTLIST_MULTS if prec == "bf16" else [4]
+        mults = SHORTLIST_MULTS.get(prec, [4])
         for a, b in grid:
             for mult in mults:
                 rec, qps, ms = timed(prec, a, b, 2, mult)
@@ -303,20 +304,30 @@ def run_taco(args):
         per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
         total = evs[0].elapsed_time(evs[-1])
         kt = ix.profile_read(reset=True) if profile else None
-        rec = recall_at(out_ids.cpu().numpy(), truth, K)
+        ids_np, d_np = out_ids.cpu().numpy(), out_d.cpu().numpy()
+        rec = recall_at(ids_np, truth, K)
+        ok = truth_d > 0
+        mre = float(np.mean(np.where(ok, (d_np.astype(np.float64) - truth_d) / np.where(ok, truth_d, 1), 0)))
+        precision_stats[prec] = {"recall_at_10": round(rec, 4), "mre": round(mre, 6),
+                                 "alpha": a, "beta": b, "shortlist_mult": mult}
         return total, per, kt, rec
 
+    precision_stats = {}
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)   # nvidia-smi is sampling before the timed region starts
     tot_b, per_b, kt_b, rec_b = run_steps("bf16", args.steps, args.warmup, profile=True)
     tot_f, per_f, kt_f, rec_f = run_steps("fp32", args.steps, args.warmup, profile=True)
+    tot_8, per_8, kt_8, rec_8 = run_steps("fp8", args.steps, args.warmup, profile=True)
     clk = clocks.stop()
 
     # max over ranks of the timed region
-    tot_b, tot_f = max_over_ranks([tot_b, tot_f], ws, device="cuda")
+    tot_b, tot_f, tot_8 = max_over_ranks([tot_b, tot_f, tot_8], ws, device="cuda")
     value = ws * nq * args.steps / (tot_b * 1e-3)
     value_fp32 = ws * nq * args.steps / (tot_f * 1e-3)
+    value_fp8 = ws * nq * args.steps / (tot_8 * 1e-3)
+    for prec, tot in (("fp32", tot_f), ("bf16", tot_b), ("fp8", tot_8)):
+        precision_stats[prec]["qps"] = round(ws * nq * args.steps / (tot * 1e-3), 1)
 
     # ---- end to end through the C ABI with host buffers --------------------------------
     a, b = calib["bf16"]["alpha"], calib["bf16"]["beta"]
@@ -397,21 +408,25 @@ def run_taco(args):
                    "global_batch": ws * nq, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (512 MB FP32 / 256 MB BF16 rows gathered)",
                    "operating_point": calib},
-        "recall_at_10": {"bf16": round(rec_b, 4), "fp32": round(rec_f, 4)},
+        "recall_at_10": {"bf16": round(rec_b, 4), "fp32": round(rec_f, 4), "fp8": round(rec_8, 4)},
         "fp32_qps": round(value_fp32, 1),
+        "fp8_qps": round(value_fp8, 1),
         "bf16_over_fp32": round(value / value_fp32, 3),
+        "precision_forms": precision_stats,
         "latency_ms": {"batch": nq,
                        "p50": round(float(np.percentile(per_b, 50)), 4),
                        "p99": round(float(np.percentile(per_b, 99)), 4),
                        "fp32_p50": round(float(np.percentile(per_f, 50)), 4),
                        "fp32_p99": round(float(np.percentile(per_f, 99)), 4),
+                       "fp8_p50": round(float(np.percentile(per_8, 50)), 4),
+                       "fp8_p99": round(float(np.percentile(per_8, 99)), 4),
                        "batch64_p50": round(float(np.percentile(lat_small, 50)), 4),
                        "batch64_p99": round(float(np.percentile(lat_small, 99)), 4)},
         "e2e": {"value": round(ws * nq * args.steps / e2e_s, 1), "unit": "queries/s",
                 "h2d_bytes_per_step": int(queries.nbytes),
                 "d2h_bytes_per_step": int(nq * K * (8 + 4)),
                 "recall_at_10": round(e2e_recall, 4)},
-        "gpu_launches": int(sum(v["launches"] for v in kt_b.values())),
+        "gpu_launches": int(sum(v["launches"] for v in kt_b.values())),   # BF16 timed region
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(dominant, "bf16"), "peak_kind": peak_kind,
@@ -427,6 +442,8 @@ def run_taco(args):
                                        for k, v in kt_f.items() if v["launches"]}
     line["kernel_ms_per_step_bf16"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                        for k, v in kt_b.items() if v["launches"]}
+    line["kernel_ms_per_step_fp8"] = {k: round(v["ms"] / max(args.steps, 1), 4)
+                                      for k, v in kt_8.items() if v["launches"]}
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(ix, data, queries, w, calib["fp32"], args.cpu_seconds)

@@ -46,6 +46,14 @@ extern "C" {
 /* ---- enums ------------------------------------------------------------------------- */
 #define TACO_PREC_FP32 0    /* re-rank candidates with FP32 distances */
 #define TACO_PREC_BF16 1    /* re-rank with a BF16 copy of D, then exact FP32 on a shortlist */
+#define TACO_PREC_FP8 2     /* re-rank with an FP8-e4m3 copy of the transformed points B^T (o - o_bar)
+                               (one scale per subspace; distances in the N_s*s transformed
+                               dimensions, equal to the original ones when N_s*s = d by Lemma 1,
+                               a lower bound otherwise), then exact FP32 on a shortlist */
+
+/* Row copies an index keeps besides the FP32 rows (bit mask, the keep_rows arguments). */
+#define TACO_ROWS_BF16 1    /* BF16 copy of D, [n][d_pad] */
+#define TACO_ROWS_FP8 2     /* FP8-e4m3 copy of B^T (o - o_bar), [n][N_s*s rounded up to 16] */
 
 #define TACO_SELECT_LITERAL 0 /* Alg. 5 as printed: stop at j when h[j] > R - sum_{j'>=j} h */
 #define TACO_SELECT_PROSE 1   /* Alg. 5 as described: stop when sum_{j'>=j} h[j'] > R */
@@ -64,7 +72,7 @@ typedef struct {
     int32_t sqrt_k;        /* sqrt(K): centroids per half-subspace, 1..TACO_MAX_SQRT_K */
     int32_t kmeans_iters;  /* t: Lloyd iterations of each half-subspace k-means */
     uint64_t seed;         /* seeds the k-means initial centroids */
-    int32_t keep_bf16;     /* nonzero: also keep a BF16 copy of D for TACO_PREC_BF16 */
+    int32_t keep_rows;     /* TACO_ROWS_* mask: row copies for TACO_PREC_BF16 / TACO_PREC_FP8 */
     int32_t reserved;      /* must be 0 */
 } taco_build_params;
 
@@ -75,7 +83,7 @@ typedef struct {
     int64_t budget;        /* collision budget per subspace: B = ceil(alpha * n) >= 1 (Alg. 4) */
     int64_t rerank_target; /* R = floor(beta * n) >= 0 (Alg. 5) */
     int32_t select_rule;   /* TACO_SELECT_*; must be the same for every query of a batch */
-    int32_t shortlist_mult;/* TACO_PREC_BF16: exact FP32 re-rank of min(mult*k, TACO_MAX_K) */
+    int32_t shortlist_mult;/* TACO_PREC_BF16 / _FP8: exact FP32 re-rank of min(mult*k, TACO_MAX_K) */
 } taco_query_params;
 
 /* An index given by its parts (e.g. built elsewhere); all pointers are host pointers. */
@@ -96,6 +104,8 @@ typedef struct {
     int32_t has_bf16;
     int32_t n_slabs;           /* id slabs of 32768 points (collision-counter granularity) */
     int32_t cluster_size;      /* CTAs that share one query's counters */
+    int32_t has_fp8;           /* FP8 rows kept (TACO_ROWS_FP8) */
+    int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s rounded up to 16) */
     int64_t device_bytes;      /* device memory owned by the index, workspace excluded */
 } taco_index_info;
 
@@ -124,10 +134,13 @@ int taco_build_index(const float* data, int64_t n, int32_t d, const taco_build_p
 /*
  * taco_index_create -- make an index from given parts (Alg. 3 output) and the data D.
  *   data host or device [n][d] float32; parts host pointers as in taco_index_parts.
+ *   keep_rows TACO_ROWS_* mask of the reduced-precision row copies to build.
  * Cell lists are rebuilt from codes with ids ascending in every cell. Synchronises `stream`.
+ * FP8 rows: every point is transformed (Alg. 1), each subspace's scale is its largest
+ * |coordinate| / 448 (the e4m3 maximum), and coordinates are rounded to nearest e4m3.
  */
 int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts,
-                      int32_t keep_bf16, void* stream, taco_index** out);
+                      int32_t keep_rows, void* stream, taco_index** out);
 
 /*
  * taco_search_batch -- Alg. 6 for nq queries.
@@ -190,7 +203,7 @@ int taco_index_export(const taco_index* index, double* o_bar, double* B, double*
 /* taco_save_index / taco_load_index -- binary file with the parts and D (little endian).
  * Loading rebuilds the device index; taco_load_index synchronises `stream`. */
 int taco_save_index(const taco_index* index, const char* path);
-int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_index** out);
+int taco_load_index(const char* path, int32_t keep_rows, void* stream, taco_index** out);
 
 /* Per-kernel device time of the search path, accumulated while profiling is enabled.
  * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 collision counting

@@ -10,6 +10,7 @@ from .taco import (  # noqa: F401
     MAX_SQRT_K,
     MAX_SUBSPACES,
     PREC_BF16,
+    PREC_FP8,
     PREC_FP32,
     SELECT_LITERAL,
     SELECT_PROSE,

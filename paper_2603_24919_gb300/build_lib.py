@@ -41,7 +41,7 @@ def _units():
         ("taco_noalloc.o", "taco_noalloc.cu", []),
         ("taco_server.o", "taco_server.cu", []),
     ]
-    for bf16 in (0, 1):
+    for bf16 in (0, 1, 2):
         for r in (1, 4, 16):
             units.append((f"taco_rerank_b{bf16}_r{r}.o", "taco_rerank_inst.cu",
                           [f"-DTACO_INST_BF16={bf16}", f"-DTACO_INST_R={r}"]))

@@ -34,6 +34,8 @@ int dev_alloc(T** p, size_t count, int64_t* acct) {
 void free_device(taco_index* ix) {
     cudaFree(ix->d_data);
     cudaFree(ix->d_data_bf16);
+    cudaFree(ix->d_data_fp8);
+    cudaFree(ix->d_fp8_scale);
     cudaFree(ix->d_obar);
     cudaFree(ix->d_B);
     cudaFree(ix->d_cent);
@@ -95,7 +97,63 @@ void set_geometry(taco_index* ix, int64_t n, int d, int Ns, int s, int sk) {
 
 // Everything downstream of the parts: cell lists (ids ascending per cell), slab split
 // table, device copies of transform and centroids, optional BF16 rows.
-int finish_index(taco_index* ix, int keep_bf16, cudaStream_t st) {
+// FP8-e4m3 rows of the transformed points with one scale per subspace (largest |x'| of the
+// subspace over all points / 448): two passes of the transform over chunks of points.
+int build_fp8_rows(taco_index* ix, cudaStream_t st) {
+    const int64_t n = ix->n;
+    const int Dp = ix->Dp;
+    ix->dp8 = (Dp + 15) & ~15;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t(256) << 20) / (int64_t(Dp) * 4)));
+    float* tmp = nullptr;
+    unsigned* maxbits = nullptr;
+    TACO_CUDA(cudaMalloc(&tmp, size_t(chunk) * Dp * 4));
+    struct Free {
+        void* a;
+        void* b;
+        ~Free() {
+            cudaFree(a);
+            cudaFree(b);
+        }
+    } guard{tmp, nullptr};
+    TACO_CUDA(cudaMalloc(&maxbits, size_t(Dp) * 4));
+    guard.b = maxbits;
+    TACO_CUDA(cudaMemsetAsync(maxbits, 0, size_t(Dp) * 4, st));
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t cn = std::min(chunk, n - c0);
+        TACO_CUDA(launch_project(ix->d_data + c0 * ix->d_pad, cn, ix->d, ix->d_pad, ix->d_obar, ix->d_B, Dp, tmp, st));
+        TACO_CUDA(launch_absmax_cols(tmp, cn, Dp, maxbits, st));
+    }
+    std::vector<unsigned> mb(Dp);
+    TACO_CUDA(cudaMemcpyAsync(mb.data(), maxbits, size_t(Dp) * 4, cudaMemcpyDeviceToHost, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    std::vector<float> sc(size_t(2) * ix->dp8, 0.f);   // [scale | 1/scale]
+    for (int i = 0; i < ix->Ns; ++i) {
+        float m = 0.f;
+        for (int c = i * ix->s; c < (i + 1) * ix->s; ++c) {
+            float v;
+            std::memcpy(&v, &mb[c], 4);
+            m = std::max(m, v);
+        }
+        const float scale = m > 0.f ? m / 448.f : 1.f;
+        for (int c = i * ix->s; c < (i + 1) * ix->s; ++c) {
+            sc[c] = scale;
+            sc[ix->dp8 + c] = 1.f / scale;
+        }
+    }
+    TRY(dev_alloc(&ix->d_fp8_scale, sc.size(), &ix->device_bytes));
+    TACO_CUDA(cudaMemcpyAsync(ix->d_fp8_scale, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice, st));
+    TRY(dev_alloc(&ix->d_data_fp8, size_t(n) * ix->dp8, &ix->device_bytes));
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t cn = std::min(chunk, n - c0);
+        TACO_CUDA(launch_project(ix->d_data + c0 * ix->d_pad, cn, ix->d, ix->d_pad, ix->d_obar, ix->d_B, Dp, tmp, st));
+        TACO_CUDA(launch_quantize_fp8(tmp, cn, Dp, ix->dp8, ix->d_fp8_scale + ix->dp8,
+                                      ix->d_data_fp8 + size_t(c0) * ix->dp8, st));
+    }
+    TACO_CUDA(cudaStreamSynchronize(st));   // sc dies on return; tmp is freed after the kernels
+    return TACO_OK;
+}
+
+int finish_index(taco_index* ix, int keep_rows, cudaStream_t st) {
     const int64_t n = ix->n;
     const int Ns = ix->Ns, K = ix->K;
     TRY(configure_search(ix));
@@ -141,10 +199,12 @@ int finish_index(taco_index* ix, int keep_bf16, cudaStream_t st) {
     TACO_CUDA(cudaMemcpyAsync(ix->d_obar, ob.data(), ob.size() * 4, cudaMemcpyHostToDevice, st));
     TACO_CUDA(cudaMemcpyAsync(ix->d_B, Bf.data(), Bf.size() * 4, cudaMemcpyHostToDevice, st));
     TACO_CUDA(cudaMemcpyAsync(ix->d_cent, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice, st));
-    if (keep_bf16) {
+    if (keep_rows & ~(TACO_ROWS_BF16 | TACO_ROWS_FP8)) return fail(TACO_EINVAL, "unknown keep_rows bits 0x%x", keep_rows);
+    if (keep_rows & TACO_ROWS_BF16) {
         TRY(dev_alloc(&ix->d_data_bf16, size_t(n) * ix->d_pad, &ix->device_bytes));
         TACO_CUDA(launch_to_bf16(ix->d_data, ix->d_data_bf16, size_t(n) * ix->d_pad, st));
     }
+    if (keep_rows & TACO_ROWS_FP8) TRY(build_fp8_rows(ix, st));
     TACO_CUDA(cudaStreamSynchronize(st));  // host vectors above die on return
     return TACO_OK;
 }
@@ -288,12 +348,12 @@ int build_impl(const float* data, int64_t n, int32_t d, const taco_build_params*
     TACO_CUDA(cudaMemcpyAsync(ix->codes.data(), dcodes, ix->codes.size() * 2, cudaMemcpyDeviceToHost, st));
     TACO_CUDA(cudaStreamSynchronize(st));
     ix->centroids.assign(cent.begin(), cent.end());
-    TRY(finish_index(ix.get(), p->keep_bf16, st));
+    TRY(finish_index(ix.get(), p->keep_rows, st));
     *out = ix.release();
     return TACO_OK;
 }
 
-int create_impl(const float* data, int64_t n, int32_t d, const taco_index_parts* parts, int keep_bf16,
+int create_impl(const float* data, int64_t n, int32_t d, const taco_index_parts* parts, int keep_rows,
                 cudaStream_t st, taco_index** out) {
     if (!data || !parts || !out || !parts->o_bar || !parts->B || !parts->centroids || !parts->codes)
         return fail(TACO_EINVAL, "null argument");
@@ -311,7 +371,7 @@ int create_impl(const float* data, int64_t n, int32_t d, const taco_index_parts*
     ix->eigvals.assign(d, 0.0);
     ix->alloc.assign(ix->Dp, -1);
     TRY(upload_data(ix.get(), data, st));
-    TRY(finish_index(ix.get(), keep_bf16, st));
+    TRY(finish_index(ix.get(), keep_rows, st));
     *out = ix.release();
     return TACO_OK;
 }
@@ -345,15 +405,15 @@ int taco::check_query_params(const taco_query_params& q, int k_stride) {
     if (q.rerank_target < 0) return fail(TACO_EINVAL, "rerank_target must be >= 0");
     if (q.select_rule != TACO_SELECT_LITERAL && q.select_rule != TACO_SELECT_PROSE)
         return fail(TACO_EINVAL, "unknown select_rule %d", q.select_rule);
-    if (q.precision != TACO_PREC_FP32 && q.precision != TACO_PREC_BF16)
+    if (q.precision != TACO_PREC_FP32 && q.precision != TACO_PREC_BF16 && q.precision != TACO_PREC_FP8)
         return fail(TACO_EINVAL, "unknown precision %d", q.precision);
-    if (q.precision == TACO_PREC_BF16 && q.shortlist_mult < 1)
-        return fail(TACO_EINVAL, "shortlist_mult must be >= 1 for BF16");
+    if (q.precision != TACO_PREC_FP32 && q.shortlist_mult < 1)
+        return fail(TACO_EINVAL, "shortlist_mult must be >= 1 for BF16 and FP8");
     return TACO_OK;
 }
 
 int taco::query_list_len(const taco_query_params& q) {
-    if (q.precision == TACO_PREC_BF16) {
+    if (q.precision == TACO_PREC_BF16 || q.precision == TACO_PREC_FP8) {
         const int64_t m = int64_t(q.k) * q.shortlist_mult;
         return int(std::min<int64_t>(std::max<int64_t>(m, q.k), TACO_MAX_K));
     }
@@ -440,7 +500,9 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         kk_max = query_list_len(*defaults);
     }
     if (precision == TACO_PREC_BF16 && !ix->d_data_bf16)
-        return fail(TACO_EINVAL, "BF16 search needs an index built with keep_bf16");
+        return fail(TACO_EINVAL, "BF16 search needs an index with BF16 rows (TACO_ROWS_BF16)");
+    if (precision == TACO_PREC_FP8 && !ix->d_data_fp8)
+        return fail(TACO_EINVAL, "FP8 search needs an index with FP8 rows (TACO_ROWS_FP8)");
     int cur_dev = 0;
     TACO_CUDA(cudaGetDevice(&cur_dev));
     if (cur_dev != ix->device) return fail(TACO_EINVAL, "current device %d is not the index's device %d", cur_dev, ix->device);
@@ -515,9 +577,9 @@ int taco_build_index(const float* data, int64_t n, int32_t d, const taco_build_p
     return build_impl(data, n, d, params, static_cast<cudaStream_t>(stream), out);
 }
 
-int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts, int32_t keep_bf16,
+int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts, int32_t keep_rows,
                       void* stream, taco_index** out) {
-    return create_impl(data, n, d, parts, keep_bf16, static_cast<cudaStream_t>(stream), out);
+    return create_impl(data, n, d, parts, keep_rows, static_cast<cudaStream_t>(stream), out);
 }
 
 int taco_search_batch(const taco_index* index, const float* queries, int64_t nq, const taco_query_params* per_query,
@@ -546,6 +608,8 @@ int taco_index_get_info(const taco_index* ix, taco_index_info* info) {
     info->has_bf16 = ix->d_data_bf16 != nullptr;
     info->n_slabs = ix->n_slabs;
     info->cluster_size = ix->cluster;
+    info->has_fp8 = ix->d_data_fp8 != nullptr;
+    info->fp8_pitch = ix->dp8;
     info->device_bytes = ix->device_bytes;
     return TACO_OK;
 }
@@ -584,7 +648,7 @@ int taco_save_index(const taco_index* ix, const char* path) {
     return TACO_OK;
 }
 
-int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_index** out) {
+int taco_load_index(const char* path, int32_t keep_rows, void* stream, taco_index** out) {
     if (!path || !out) return fail(TACO_EINVAL, "null argument");
     *out = nullptr;
     FILE* f = std::fopen(path, "rb");
@@ -611,7 +675,7 @@ int taco_load_index(const char* path, int32_t keep_bf16, void* stream, taco_inde
     if (!ok) return fail(TACO_EIO, "%s is truncated", path);
     taco_index_parts parts = {ob.data(), B.data(), cent.data(), codes.data(), Ns, s, sk, 0};
     taco_index* ix = nullptr;
-    TRY(create_impl(data.data(), n, d, &parts, keep_bf16, static_cast<cudaStream_t>(stream), &ix));
+    TRY(create_impl(data.data(), n, d, &parts, keep_rows, static_cast<cudaStream_t>(stream), &ix));
     ix->eigvals = ev;
     ix->alloc = alloc;
     *out = ix;

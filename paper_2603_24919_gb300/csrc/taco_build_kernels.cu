@@ -1,6 +1,7 @@
 // Device kernels of the index build (Alg. 1 steps 2-3 and 6-11, Alg. 3 steps 6-9) and the
 // query projection of Alg. 6 step 1, which uses the same transform kernel.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -375,6 +376,48 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, size_t count, cudaStream_t st) {
     const size_t blocks = std::min<size_t>((count + 255) / 256, 152 * 64);
     to_bf16_kernel<<<unsigned(blocks), 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+// Column-wise max |Y| (FP8 scales). Non-negative floats order like their bit patterns.
+__global__ void absmax_cols_kernel(const float* __restrict__ Y, int64_t rows, int Dp,
+                                   unsigned* __restrict__ maxbits) {
+    for (int c = threadIdx.x; c < Dp; c += blockDim.x) {
+        float m = 0.f;
+        for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) m = fmaxf(m, fabsf(Y[r * Dp + c]));
+        atomicMax(&maxbits[c], __float_as_uint(m));
+    }
+}
+
+cudaError_t launch_absmax_cols(const float* Y, int64_t rows, int Dp, unsigned* maxbits,
+                               cudaStream_t st) {
+    const int threads = Dp < 1024 ? ((Dp + 31) / 32) * 32 : 1024;
+    const int64_t blocks = std::min<int64_t>(rows, 152 * 16);
+    if (blocks < 1) return cudaSuccess;
+    absmax_cols_kernel<<<unsigned(blocks), threads, 0, st>>>(Y, rows, Dp, maxbits);
+    return cudaGetLastError();
+}
+
+// e4m3 rows, round to nearest with saturation to the finite range.
+__global__ void quantize_fp8_kernel(const float* __restrict__ Y, int64_t rows, int Dp, int dp8,
+                                    const float* __restrict__ inv_scale, uint8_t* __restrict__ out) {
+    const size_t total = size_t(rows) * dp8;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const size_t r = i / size_t(dp8);
+        const int c = int(i - r * size_t(dp8));
+        uint8_t v = 0;
+        if (c < Dp) v = __nv_cvt_float_to_fp8(Y[r * Dp + c] * inv_scale[c], __NV_SATFINITE, __NV_E4M3);
+        out[i] = v;
+    }
+}
+
+cudaError_t launch_quantize_fp8(const float* Y, int64_t rows, int Dp, int dp8,
+                                const float* inv_scale, uint8_t* out, cudaStream_t st) {
+    const size_t count = size_t(rows) * dp8;
+    const size_t blocks = std::min<size_t>((count + 255) / 256, 152 * 64);
+    if (blocks < 1) return cudaSuccess;
+    quantize_fp8_kernel<<<unsigned(blocks), 256, 0, st>>>(Y, rows, Dp, dp8, inv_scale, out);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,9 @@ struct taco_index {
     // device arrays
     float* d_data = nullptr;            // [n][d_pad]
     __nv_bfloat16* d_data_bf16 = nullptr;  // [n][d_pad] or null
+    uint8_t* d_data_fp8 = nullptr;      // [n][dp8] e4m3 of B^T (o - o_bar), or null
+    float* d_fp8_scale = nullptr;       // [2][dp8]: per-dimension scale (its subspace's), 1/scale
+    int dp8 = 0;                        // Dp rounded up to 16
     float* d_obar = nullptr;            // [d]
     float* d_B = nullptr;               // [d][Dp]
     float* d_cent = nullptr;            // [Ns][sk][s]
@@ -119,6 +122,12 @@ cudaError_t launch_kmeans(const float* T, int64_t n, int Dp, int Ns, int s, int 
                           uint16_t* codes_out, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, size_t count,
                            cudaStream_t st);
+// Largest |Y[r][c]| of every column into maxbits[c] (float bits; atomicMax, caller zeroes).
+cudaError_t launch_absmax_cols(const float* Y, int64_t rows, int Dp, unsigned* maxbits,
+                               cudaStream_t st);
+// out[r][c] = e4m3(Y[r][c] * inv_scale[c]) for c < Dp, 0 for Dp <= c < dp8.
+cudaError_t launch_quantize_fp8(const float* Y, int64_t rows, int Dp, int dp8,
+                                const float* inv_scale, uint8_t* out, cudaStream_t st);
 
 struct SearchLaunch {
     const taco_index* ix;

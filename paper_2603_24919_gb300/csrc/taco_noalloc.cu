@@ -65,7 +65,7 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     if (q.precision != TACO_PREC_FP32 && q.precision != TACO_PREC_BF16)
         return fail(TACO_EINVAL, "unknown precision %d", q.precision);
     if (q.precision == TACO_PREC_BF16 && (q.shortlist_mult < 1 || !index->d_data_bf16))
-        return fail(TACO_EINVAL, "BF16 needs shortlist_mult >= 1 and an index with keep_bf16");
+        return fail(TACO_EINVAL, "BF16 needs shortlist_mult >= 1 and an index with BF16 rows");
     if (nq > kQueryChunk)
         return fail(TACO_ECAPACITY, "nq = %lld exceeds %lld queries per call", (long long)nq,
                     (long long)kQueryChunk);

@@ -26,6 +26,8 @@
 
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -46,6 +48,10 @@ struct RerankParams {
     const float* queries;   // [nq][d]
     const float* data;      // [n][d_pad]
     const __nv_bfloat16* data_bf16;  // [n][d_pad]
+    const uint8_t* data_fp8;   // [n][dp8] e4m3 of the transformed points
+    const float* fp8_scale;    // [2][dp8] per-dimension scale, then 1/scale
+    const float* qt;           // [nq][Dp] transformed queries
+    int Dp, dp8;
     const uint32_t* ids;    // [Ns][n]
     const uint32_t* split;  // [Ns][K][n_slabs+1]
     const uint16_t* cells;  // [nq][Ns][K]
@@ -154,10 +160,13 @@ __device__ __forceinline__ float sq4(float4 o, float4 q, float acc) {
     return fmaf(dx, dx, acc);
 }
 
-// Row chunk = 16 bytes: 4 floats or 8 bf16.
-template <bool BF16>
+// Row kinds of the re-rank: FP32 rows, BF16 rows, FP8-e4m3 rows of the transformed points.
+constexpr int kRowF32 = 0, kRowBF16 = 1, kRowFP8 = 2;
+
+// Row chunk = 16 bytes: 4 floats, 8 bf16 or 16 e4m3.
+template <int RK>
 struct RowChunk {
-    static constexpr int kElems = BF16 ? 8 : 4;
+    static constexpr int kElems = RK == kRowF32 ? 4 : (RK == kRowBF16 ? 8 : 16);
 };
 
 // L2 eviction policies: candidate rows are read once per query and streamed (evict
@@ -186,14 +195,17 @@ __device__ __forceinline__ uint32_t ldg_keep_u32(const uint32_t* p, uint64_t pol
     return r;
 }
 
-template <bool BF16>
+// Squared distance contribution of one 16-byte row chunk f. FP32 / BF16: qv is the query
+// (d_pad floats). FP8: qv holds (q'_c / scale_c, scale_c^2) pairs of the transformed query,
+// so the chunk adds sum_c scale_c^2 (q'_c / scale_c - x8_c)^2 = sum_c (q'_c - scale_c x8_c)^2.
+template <int RK>
 __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, float acc) {
-    if constexpr (!BF16) {
+    if constexpr (RK == kRowF32) {
         const float4 o = make_float4(__uint_as_float(raw.x), __uint_as_float(raw.y),
                                      __uint_as_float(raw.z), __uint_as_float(raw.w));
         const float4 q = reinterpret_cast<const float4*>(qv)[f];
         return sq4(o, q, acc);
-    } else {
+    } else if constexpr (RK == kRowBF16) {
         const float4 q0 = reinterpret_cast<const float4*>(qv)[2 * f];
         const float4 q1 = reinterpret_cast<const float4*>(qv)[2 * f + 1];
         const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&raw);
@@ -203,12 +215,29 @@ __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, f
         const float2 a3 = __bfloat1622float2(b[3]);
         acc = sq4(make_float4(a0.x, a0.y, a1.x, a1.y), q0, acc);
         return sq4(make_float4(a2.x, a2.y, a3.x, a3.y), q1, acc);
+    } else {
+        const float4* qw = reinterpret_cast<const float4*>(qv) + 8 * f;   // 2 dims per float4
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const __half2 x2(__nv_cvt_fp8x2_to_halfraw2(
+                    __nv_fp8x2_storage_t((w4[u] >> (16 * h)) & 0xffffu), __NV_E4M3));
+                const float2 x = __half22float2(x2);
+                const float4 p = qw[2 * u + h];   // (qs_a, w_a, qs_b, w_b)
+                const float da = p.x - x.x, db = p.z - x.y;
+                acc = fmaf(p.y * da, da, acc);
+                acc = fmaf(p.w * db, db, acc);
+            }
+        }
+        return acc;
     }
 }
 
 // Squared distances of up to CPW*U queued candidates to the query, G lanes per row.
 // Lane-group leaders (gl == 0) end with the full sums; val/cid tell which are real.
-template <int G, bool BF16>
+template <int G, int RK>
 __device__ __forceinline__ void gather_distances(const unsigned char* base, size_t row_bytes,
                                                  int nch, const float* qv, const uint32_t* buf,
                                                  int b0, int m, float (&acc)[2], uint32_t (&cid)[2],
@@ -239,7 +268,7 @@ __device__ __forceinline__ void gather_distances(const unsigned char* base, size
 #pragma unroll
             for (int ch = 0; ch < CH; ++ch) {
                 const int f = f0 + ch * G + gl;
-                if (f < nch) acc[u] = chunk_dist<BF16>(raw[u][ch], qv, f, acc[u]);
+                if (f < nch) acc[u] = chunk_dist<RK>(raw[u][ch], qv, f, acc[u]);
             }
     }
 #pragma unroll
@@ -952,7 +981,7 @@ constexpr int kSrThreads = 256;
 constexpr int kSrWarps = kSrThreads / 32;
 constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
 
-template <int G, int R, bool BF16>
+template <int G, int R, int RK>
 __global__ void __launch_bounds__(kSrThreads, 4)
 select_rerank_kernel(const RerankParams P) {
     constexpr int CPW = 32 / G;
@@ -964,25 +993,37 @@ select_rerank_kernel(const RerankParams P) {
     uint32_t* Li = reinterpret_cast<uint32_t*>(Ld + kSrWarps * kkc);    // [kSrWarps][kkc]
     float* Md = reinterpret_cast<float*>(Li + kSrWarps * kkc);          // [kkc] merged
     uint32_t* Mi = reinterpret_cast<uint32_t*>(Md + kkc);
-    float* Xd = reinterpret_cast<float*>(Mi + kkc);                     // [kkc] exact (BF16)
+    float* Xd = reinterpret_cast<float*>(Mi + kkc);                     // [kkc] exact (BF16, FP8)
     uint32_t* Xi = reinterpret_cast<uint32_t*>(Xd + kkc);
     float* qv = reinterpret_cast<float*>(Xi + kkc);                     // d_pad
     uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);          // kSrBuf
+    float* qf = reinterpret_cast<float*>(buf + kSrBuf);                 // FP8: [dp8][2]
     __shared__ uint32_t s_gs[TACO_MAX_SUBSPACES + 2];
     __shared__ int s_last;
     __shared__ uint32_t s_bufn;
     __shared__ uint32_t s_flag;
     const int Ns = P.Ns, nr = P.n_ranges, kk = P.kk;
     const int gid = lane / G, gl = lane % G;
-    const int nch = P.d_pad / RowChunk<BF16>::kElems;
-    const size_t row_bytes = size_t(P.d_pad) * (BF16 ? 2 : 4);
-    const unsigned char* rows = BF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
-                                     : reinterpret_cast<const unsigned char*>(P.data);
+    constexpr bool kFP8 = RK == kRowFP8;
+    const int nch = (kFP8 ? P.dp8 : P.d_pad) / RowChunk<RK>::kElems;
+    const size_t row_bytes = kFP8 ? size_t(P.dp8) : size_t(P.d_pad) * (RK == kRowBF16 ? 2 : 4);
+    const unsigned char* rows = RK == kRowBF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
+                                : kFP8         ? P.data_fp8
+                                               : reinterpret_cast<const unsigned char*>(P.data);
+    const float* qd = kFP8 ? qf : qv;   // what the candidate distances compare against
     const uint64_t pol_stream = l2_policy_stream();
     for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
         const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
         __syncthreads();
         for (int j = tid; j < P.d_pad; j += kSrThreads) qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
+        if constexpr (kFP8) {
+            // (q'_c / scale_c, scale_c^2); zero past N_s * s
+            for (int j = tid; j < P.dp8; j += kSrThreads) {
+                const float sc = P.fp8_scale[j];
+                qf[2 * j] = j < P.Dp ? P.qt[q * P.Dp + j] * P.fp8_scale[P.dp8 + j] : 0.f;
+                qf[2 * j + 1] = j < P.Dp ? sc * sc : 0.f;
+            }
+        }
         if (tid <= TACO_MAX_SUBSPACES + 1) s_gs[tid] = 0u;
         if (tid == 0) {
             s_bufn = 0u;
@@ -1033,7 +1074,7 @@ select_rerank_kernel(const RerankParams P) {
                 float acc[U];
                 uint32_t cid[U];
                 bool val[U];
-                gather_distances<G, BF16>(rows, row_bytes, nch, qv, buf, b0, m, acc, cid, val, gid, gl,
+                gather_distances<G, RK>(rows, row_bytes, nch, qd, buf, b0, m, acc, cid, val, gid, gl,
                                           pol_stream);
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
@@ -1094,7 +1135,7 @@ select_rerank_kernel(const RerankParams P) {
         // the query's own shortlist: the first qp.kk of the merged list (a batch's lists
         // are as long as its longest one; a shorter shortlist is a prefix of them)
         const int kq = min(qp.kk, kk);
-        if constexpr (BF16) {
+        if constexpr (RK != kRowF32) {
             // exact FP32 distances of the shortlist, then rank sort by (distance, id)
             const int nf4 = P.d_pad / 4;
             const float4* q4 = reinterpret_cast<const float4*>(qv);
@@ -1132,9 +1173,9 @@ select_rerank_kernel(const RerankParams P) {
     }
 }
 
-template <int G, int R, bool BF16>
+template <int G, int R, int RK>
 cudaError_t launch_select_rerank_t(const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
-    auto kern = select_rerank_kernel<G, R, BF16>;
+    auto kern = select_rerank_kernel<G, R, RK>;
     static thread_local size_t cached_smem = 0;
     static thread_local int cached_blocks = 0;
     cudaError_t e = cudaGetLastError();
@@ -1230,5 +1271,9 @@ TACO_DECLARE_RERANK(1, 1)
 TACO_DECLARE_RERANK(1, 4)
 TACO_DECLARE_RERANK(1, 16)
 #undef TACO_DECLARE_RERANK
+// FP8 rows: the select / re-rank pass only (fallback queries re-rank with FP32 rows).
+cudaError_t launch_select_b2_r1(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
+cudaError_t launch_select_b2_r4(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
+cudaError_t launch_select_b2_r16(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
 
 }  // namespace taco

@@ -1,5 +1,6 @@
-// Instantiates the fused count/select/re-rank kernel for one (row type, R) pair, chosen by
-// -DTACO_INST_BF16=<0|1> -DTACO_INST_R=<1|4|16>; the build compiles this file six times.
+// Instantiates the re-rank kernels for one (row kind, R) pair, chosen by
+// -DTACO_INST_BF16=<0 FP32 | 1 BF16 | 2 FP8> -DTACO_INST_R=<1|4|16>; the build compiles this
+// file nine times. FP8 rows have the select / re-rank pass only.
 #include "taco_rerank.cuh"
 
 #ifndef TACO_INST_BF16
@@ -16,6 +17,7 @@
 
 namespace taco {
 
+#if TACO_INST_BF16 != 2
 cudaError_t TACO_FN(int G, const RerankParams& P, int cluster, int64_t nq, size_t smem,
                     cudaStream_t st) {
     constexpr bool kBf16 = TACO_INST_BF16 != 0;
@@ -28,13 +30,15 @@ cudaError_t TACO_FN(int G, const RerankParams& P, int cluster, int64_t nq, size_
     }
 }
 
+#endif
+
 cudaError_t TACO_FN2(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
-    constexpr bool kBf16 = TACO_INST_BF16 != 0;
+    constexpr int kRow = TACO_INST_BF16;
     switch (G) {
-        case 4: return launch_select_rerank_t<4, TACO_INST_R, kBf16>(P, nq, smem, st);
-        case 8: return launch_select_rerank_t<8, TACO_INST_R, kBf16>(P, nq, smem, st);
-        case 16: return launch_select_rerank_t<16, TACO_INST_R, kBf16>(P, nq, smem, st);
-        case 32: return launch_select_rerank_t<32, TACO_INST_R, kBf16>(P, nq, smem, st);
+        case 4: return launch_select_rerank_t<4, TACO_INST_R, kRow>(P, nq, smem, st);
+        case 8: return launch_select_rerank_t<8, TACO_INST_R, kRow>(P, nq, smem, st);
+        case 16: return launch_select_rerank_t<16, TACO_INST_R, kRow>(P, nq, smem, st);
+        case 32: return launch_select_rerank_t<32, TACO_INST_R, kRow>(P, nq, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }

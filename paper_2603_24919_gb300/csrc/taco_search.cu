@@ -871,11 +871,19 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
     }
     // 3. count, select, re-rank (Alg. 6 steps 7-9, Alg. 5)
     {
+        // FP8 rows serve the select / re-rank pass; queries on the fallback cluster path
+        // re-rank with FP32 rows
+        const bool fp8 = L.precision == TACO_PREC_FP8;
         const bool bf16 = L.precision == TACO_PREC_BF16;
         RerankParams P = {};
         P.queries = L.queries;
         P.data = ix->d_data;
         P.data_bf16 = ix->d_data_bf16;
+        P.data_fp8 = ix->d_data_fp8;
+        P.fp8_scale = ix->d_fp8_scale;
+        P.qt = L.qt;
+        P.Dp = ix->Dp;
+        P.dp8 = ix->dp8;
         P.ids = ix->d_ids;
         P.split = ix->d_split;
         P.cells = L.cells;
@@ -908,6 +916,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
+        const int Gs = fp8 ? pick_g(ix->dp8 / 16) : G;   // lanes per row of the select pass
         const bool two_pass = L.unit_ge != nullptr;
         if (two_pass) {
             P.unit_ge = L.unit_ge;
@@ -936,10 +945,14 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results
             const size_t smem2 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 +
-                                 size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4;
+                                 size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0);
             cudaError_t e;
             if (int rc = prof_begin(pix, 3, st, &pb, &pe)) return rc;
-            if (!bf16) {
+            if (fp8) {
+                e = R == 1 ? launch_select_b2_r1(Gs, P, L.nq, smem2, st)
+                    : R == 4 ? launch_select_b2_r4(Gs, P, L.nq, smem2, st)
+                             : launch_select_b2_r16(Gs, P, L.nq, smem2, st);
+            } else if (!bf16) {
                 e = R == 1 ? launch_select_b0_r1(G, P, L.nq, smem2, st)
                     : R == 4 ? launch_select_b0_r4(G, P, L.nq, smem2, st)
                              : launch_select_b0_r16(G, P, L.nq, smem2, st);

@@ -335,9 +335,10 @@ int taco_server_create(const taco_index* index, const taco_server_params* params
     if (p.queue_capacity < p.max_batch || p.queue_capacity >= kMaxQueue)
         return fail(TACO_EINVAL, "queue_capacity must be in [max_batch, %d)", kMaxQueue);
     if (p.max_list < 1 || p.max_list > TACO_MAX_K) return fail(TACO_EINVAL, "max_list must be in [1, %d]", TACO_MAX_K);
-    if (p.precision != TACO_PREC_FP32 && p.precision != TACO_PREC_BF16) return fail(TACO_EINVAL, "unknown precision");
-    if (p.precision == TACO_PREC_BF16 && !index->d_data_bf16)
-        return fail(TACO_EINVAL, "BF16 serving needs an index built with keep_bf16");
+    if (p.precision != TACO_PREC_FP32 && p.precision != TACO_PREC_BF16 && p.precision != TACO_PREC_FP8)
+        return fail(TACO_EINVAL, "unknown precision");
+    if ((p.precision == TACO_PREC_BF16 && !index->d_data_bf16) || (p.precision == TACO_PREC_FP8 && !index->d_data_fp8))
+        return fail(TACO_EINVAL, "the index has no row copy for the server's precision");
     if (p.select_rule != TACO_SELECT_LITERAL && p.select_rule != TACO_SELECT_PROSE)
         return fail(TACO_EINVAL, "unknown select_rule");
     if (p.max_wait_us < 0 || p.slot_bytes < 0 || p.reserved != 0) return fail(TACO_EINVAL, "bad max_wait_us, slot_bytes or reserved");

@@ -16,17 +16,18 @@ LIB_PATH = os.path.join(_PKG, "libtaco.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO, EAGAIN = -1, -2, -3, -4, -5, -6, -7
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+ROWS_BF16, ROWS_FP8 = 1, 2
 SELECT_LITERAL, SELECT_PROSE = 0, 1
 MAX_SUBSPACES, MAX_SQRT_K, MAX_K = 15, 128, 512
 
-_PREC = {"fp32": PREC_FP32, "bf16": PREC_BF16}
+_PREC = {"fp32": PREC_FP32, "bf16": PREC_BF16, "fp8": PREC_FP8}
 _RULE = {"literal": SELECT_LITERAL, "prose": SELECT_PROSE}
 
 
 class BuildParams(C.Structure):
     _fields_ = [("n_subspaces", C.c_int32), ("sub_dim", C.c_int32), ("sqrt_k", C.c_int32),
-                ("kmeans_iters", C.c_int32), ("seed", C.c_uint64), ("keep_bf16", C.c_int32),
+                ("kmeans_iters", C.c_int32), ("seed", C.c_uint64), ("keep_rows", C.c_int32),
                 ("reserved", C.c_int32)]
 
 
@@ -46,7 +47,7 @@ class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("n_subspaces", C.c_int32),
                 ("sub_dim", C.c_int32), ("sqrt_k", C.c_int32), ("d_pad", C.c_int32),
                 ("has_bf16", C.c_int32), ("n_slabs", C.c_int32), ("cluster_size", C.c_int32),
-                ("device_bytes", C.c_int64)]
+                ("has_fp8", C.c_int32), ("fp8_pitch", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 class DebugOut(C.Structure):
@@ -194,6 +195,11 @@ def _as_f32(x):
     return np.ascontiguousarray(x, dtype=np.float32)
 
 
+def _rows(keep_bf16, keep_fp8):
+    """TACO_ROWS_* mask of the row copies an index keeps."""
+    return (ROWS_BF16 if keep_bf16 else 0) | (ROWS_FP8 if keep_fp8 else 0)
+
+
 def query_params(k, budget, rerank_target, precision="fp32", select_rule="literal",
                  shortlist_mult=4):
     return QueryParams(int(k), _PREC.get(precision, precision), int(budget), int(rerank_target),
@@ -209,18 +215,19 @@ class TacoIndex:
     # ---- construction --------------------------------------------------------------
     @classmethod
     def build(cls, data, n_subspaces, sub_dim, sqrt_k, kmeans_iters=20, seed=0, keep_bf16=True,
-              stream=None):
+              keep_fp8=False, stream=None):
         lib = load_library()
         x = _as_f32(data)
         n, d = x.shape
-        p = BuildParams(n_subspaces, sub_dim, sqrt_k, kmeans_iters, seed, int(bool(keep_bf16)), 0)
+        p = BuildParams(n_subspaces, sub_dim, sqrt_k, kmeans_iters, seed,
+                        _rows(keep_bf16, keep_fp8), 0)
         out = C.c_void_p()
         _check(lib.taco_build_index(_ptr(x), n, d, C.byref(p), _stream_handle(stream), C.byref(out)))
         return cls(out.value)
 
     @classmethod
     def from_parts(cls, data, o_bar, B, centroids, codes, n_subspaces, sub_dim, sqrt_k,
-                   keep_bf16=True, stream=None):
+                   keep_bf16=True, keep_fp8=False, stream=None):
         lib = load_library()
         x = _as_f32(data)
         n, d = x.shape
@@ -233,14 +240,14 @@ class TacoIndex:
         parts = IndexParts(ob.ctypes.data, Bm.ctypes.data, ce.ctypes.data, co.ctypes.data,
                            n_subspaces, sub_dim, sqrt_k, 0)
         out = C.c_void_p()
-        _check(lib.taco_index_create(_ptr(x), n, d, C.byref(parts), int(bool(keep_bf16)),
+        _check(lib.taco_index_create(_ptr(x), n, d, C.byref(parts), _rows(keep_bf16, keep_fp8),
                                      _stream_handle(stream), C.byref(out)))
         return cls(out.value)
 
     @classmethod
-    def load(cls, path, keep_bf16=True, stream=None):
+    def load(cls, path, keep_bf16=True, keep_fp8=False, stream=None):
         out = C.c_void_p()
-        _check(load_library().taco_load_index(os.fsencode(path), int(bool(keep_bf16)),
+        _check(load_library().taco_load_index(os.fsencode(path), _rows(keep_bf16, keep_fp8),
                                               _stream_handle(stream), C.byref(out)))
         return cls(out.value)
 

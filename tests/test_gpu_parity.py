@@ -292,3 +292,62 @@ def test_bf16_recall_close_to_fp32(tiny):
     bi = b_ids.cpu().numpy()
     exact = np.sqrt(((data[bi].astype(np.float64) - queries[:, None, :]) ** 2).sum(-1))
     assert np.allclose(b_d.cpu().numpy(), exact, rtol=1e-5)
+
+
+# ------------------------------------------------------------------ FP8 rows (precision form)
+@pytest.fixture(scope="module")
+def tiny_fp8(tiny):
+    w, data, queries, oix, _ = tiny
+    ix = TacoIndex.from_parts(data, oix.o_bar, oix.B, oix.centroids, oix.codes.astype(np.uint16),
+                              oix.n_subspaces, oix.sub_dim, oix.sqrt_k, keep_bf16=False,
+                              keep_fp8=True)
+    yield ix
+    ix.close()
+
+
+def test_fp8_shortlist_covering_the_candidates_matches_oracle(tiny, tiny_fp8):
+    """When the shortlist holds every candidate, the exact FP32 re-rank sees all of C, so the
+    FP8 form returns the oracle's result under the FP32 acceptance rule."""
+    w, data, queries, oix, _ = tiny
+    ix = tiny_fp8
+    info = ix.info()
+    assert info["has_fp8"] == 1 and info["fp8_pitch"] % 16 == 0 and info["has_bf16"] == 0
+    b, t = w.budget, 100
+    q = torch.from_numpy(queries).cuda()
+    ids, dists = ix.search(q, 10, b, t, precision="fp8", shortlist_mult=51)   # 510 >= |C|
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    rep = ParityReport()
+    used = 0
+    for j in range(len(queries)):
+        tr = O.search_one(oix, data, queries[j], 10, b, t)
+        if min(tr.probe_margin) < 1e-5 or tr.candidate_num > 510:
+            continue
+        used += 1
+        compare_topk(rep, tr.ids, tr.dists, tr.kth_margin, ids[j], dists[j], 10)
+    assert used >= len(queries) // 2, used
+
+
+def test_fp8_recall_close_to_fp32(tiny, tiny_fp8):
+    """FP8-e4m3 rows with per-subspace scales and an exact FP32 re-rank of a 4k shortlist
+    lose at most 0.02 of recall@10 against the FP32 form; distances are exact FP32 ones."""
+    w, data, queries, oix, ix32 = tiny
+    q = torch.from_numpy(queries).cuda()
+    t_ids, _ = O.brute_force_knn(data, queries, 10)
+    f_ids, _ = ix32.search(q, 10, w.budget, w.rerank_target)
+    e_ids, e_d = tiny_fp8.search(q, 10, w.budget, w.rerank_target, precision="fp8",
+                                 shortlist_mult=4)
+    rf = O.recall(f_ids.cpu().numpy(), t_ids, 10)
+    re = O.recall(e_ids.cpu().numpy(), t_ids, 10)
+    assert re >= rf - 0.02, (re, rf)
+    ei = e_ids.cpu().numpy()
+    ok = ei >= 0
+    exact = np.sqrt(((data[np.where(ok, ei, 0)].astype(np.float64) - queries[:, None, :]) ** 2).sum(-1))
+    assert np.allclose(e_d.cpu().numpy()[ok], exact[ok], rtol=1e-5)
+
+
+def test_fp8_needs_fp8_rows(tiny):
+    w, data, queries, oix, ix = tiny   # built with BF16 rows only
+    q = torch.from_numpy(queries[:4]).cuda()
+    with pytest.raises(Exception) as err:
+        ix.search(q, 10, w.budget, w.rerank_target, precision="fp8")
+    assert "FP8" in str(err.value)
