@@ -84,6 +84,11 @@ typedef struct {
     int64_t rerank_target; /* R = floor(beta * n) >= 0 (Alg. 5) */
     int32_t select_rule;   /* TACO_SELECT_*; must be the same for every query of a batch */
     int32_t shortlist_mult;/* TACO_PREC_BF16 / _FP8: exact FP32 re-rank of min(mult*k, TACO_MAX_K) */
+    int32_t probe_precision;/* query x centroid distances (Alg. 6 steps 4-5): TACO_PREC_FP32 on CUDA
+                               cores, or TACO_PREC_BF16: BF16 operands on the tcgen05 tensor
+                               cores with FP32 accumulation (needs taco_index_info.has_centroid_tc).
+                               Must be the same for every query of a batch */
+    int32_t reserved;      /* must be 0 */
 } taco_query_params;
 
 /* An index given by its parts (e.g. built elsewhere); all pointers are host pointers. */
@@ -106,6 +111,9 @@ typedef struct {
     int32_t cluster_size;      /* CTAs that share one query's counters */
     int32_t has_fp8;           /* FP8 rows kept (TACO_ROWS_FP8) */
     int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s rounded up to 16) */
+    int32_t has_centroid_tc;   /* the tcgen05 centroid block is available (sqrt_k <= 128 and the
+                                  operands of 128 queries fit shared memory) */
+    int32_t reserved;
     int64_t device_bytes;      /* device memory owned by the index, workspace excluded */
 } taco_index_info;
 
@@ -180,6 +188,25 @@ int taco_search_batch_noalloc(const taco_index* index, const float* queries, int
                               const taco_query_params* params, int32_t k_stride,
                               int64_t* out_ids, float* out_dists, void* stream);
 
+/*
+ * taco_centroid_distances -- the query x centroid distance block of Alg. 6 steps 4-5 alone:
+ *   qt     device, [nq][N_s*s] float32 transformed queries B^T (q - o_bar).
+ *   out    device, [nq][N_s][2][sqrt_k] float32: out[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2,
+ *          half h = 0 the first floor(s/2) dimensions of subspace i, h = 1 the rest.
+ *   probe_precision  TACO_PREC_FP32 (CUDA cores, sum of squared differences) or TACO_PREC_BF16
+ *          (tcgen05 tensor cores: BF16 operands, FP32 accumulation of |q|^2 + |c|^2 - 2 q.c,
+ *          clamped at 0; TACO_EINVAL unless has_centroid_tc).
+ * Asynchronous on `stream`. A bounded device wait that gives up sets the status word read by
+ * taco_device_status.
+ */
+int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq,
+                            int32_t probe_precision, float* out, void* stream);
+
+/* taco_device_status -- synchronise the device and read (clear != 0: then reset) the index's
+ * device status word: 0 = no device-side wait ever gave up, 1 = one did (its results are not
+ * valid). Kernels never trap; they record the failure here and return. */
+int taco_device_status(const taco_index* index, int32_t* status, int32_t clear);
+
 /* taco_search_debug -- taco_search_batch that also writes the intermediate results
  * selected in *debug (device pointers). Test aid; same errors as taco_search_batch. */
 int taco_search_debug(const taco_index* index, const float* queries, int64_t nq,
@@ -209,8 +236,9 @@ int taco_load_index(const char* path, int32_t keep_rows, void* stream, taco_inde
  * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 collision counting
  * into per-range level lists (Def. 6), 3 selection and re-rank (Alg. 5, Alg. 6 step 9),
  * 4 cluster kernel (counting, selection and re-rank for queries whose threshold is below 2,
- * or for every query in taco_search_batch_noalloc), 5 merge of the cluster kernel's lists. */
-#define TACO_NUM_KERNELS 6
+ * or for every query in taco_search_batch_noalloc), 5 merge of the cluster kernel's lists,
+ * 6 query x centroid block on the tensor cores (probe_precision TACO_PREC_BF16). */
+#define TACO_NUM_KERNELS 7
 typedef struct {
     int64_t launches[TACO_NUM_KERNELS];
     double ms[TACO_NUM_KERNELS];
@@ -261,7 +289,7 @@ typedef struct {
     int64_t slot_bytes;      /* device workspace per slot; 0 = enough for max_batch queries
                                 at max_list. Smaller values admit fewer queries per batch */
     int32_t use_graphs;      /* nonzero: replay captured CUDA graphs (see above) */
-    int32_t reserved;        /* must be 0 */
+    int32_t probe_precision; /* taco_query_params.probe_precision of every request */
 } taco_server_params;
 
 /* Timing of one request, steady clock in nanoseconds. */

@@ -40,6 +40,7 @@ def _units():
         ("taco_api.o", "taco_api.cu", []),
         ("taco_noalloc.o", "taco_noalloc.cu", []),
         ("taco_server.o", "taco_server.cu", []),
+        ("taco_tc.o", "taco_tc.cu", []),
     ]
     for bf16 in (0, 1, 2):
         for r in (1, 4, 16):

@@ -36,6 +36,9 @@ void free_device(taco_index* ix) {
     cudaFree(ix->d_data_bf16);
     cudaFree(ix->d_data_fp8);
     cudaFree(ix->d_fp8_scale);
+    cudaFree(ix->d_cent_tc);
+    cudaFree(ix->d_cent_tc_norm);
+    cudaFree(ix->d_status);
     cudaFree(ix->d_obar);
     cudaFree(ix->d_B);
     cudaFree(ix->d_cent);
@@ -205,6 +208,12 @@ int finish_index(taco_index* ix, int keep_rows, cudaStream_t st) {
         TACO_CUDA(launch_to_bf16(ix->d_data, ix->d_data_bf16, size_t(n) * ix->d_pad, st));
     }
     if (keep_rows & TACO_ROWS_FP8) TRY(build_fp8_rows(ix, st));
+    if (!ix->d_status) {
+        TRY(dev_alloc(&ix->d_status, 1, &ix->device_bytes));
+        TACO_CUDA(cudaMemsetAsync(ix->d_status, 0, sizeof(int), st));
+    }
+    TACO_CUDA(cudaStreamSynchronize(st));
+    TRY(build_centroid_tc(ix));
     TACO_CUDA(cudaStreamSynchronize(st));  // host vectors above die on return
     return TACO_OK;
 }
@@ -409,6 +418,9 @@ int taco::check_query_params(const taco_query_params& q, int k_stride) {
         return fail(TACO_EINVAL, "unknown precision %d", q.precision);
     if (q.precision != TACO_PREC_FP32 && q.shortlist_mult < 1)
         return fail(TACO_EINVAL, "shortlist_mult must be >= 1 for BF16 and FP8");
+    if (q.probe_precision != TACO_PREC_FP32 && q.probe_precision != TACO_PREC_BF16)
+        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32 or TACO_PREC_BF16");
+    if (q.reserved != 0) return fail(TACO_EINVAL, "reserved field must be 0");
     return TACO_OK;
 }
 
@@ -432,7 +444,8 @@ QueryParamsDev taco::query_params_dev(const taco_query_params& q) {
 }
 
 SearchLayout taco::plan_search(const taco_index* ix, int64_t chunk, int kk_max, int64_t n_params,
-                               bool stage_queries, bool stage_ids, bool stage_dists, int k_stride) {
+                               bool stage_queries, bool stage_ids, bool stage_dists, int k_stride,
+                               bool centroid_tc) {
     const int Ns = ix->Ns, K = ix->K;
     SearchLayout l;
     size_t off = 0;
@@ -455,6 +468,7 @@ SearchLayout taco::plan_search(const taco_index* ix, int64_t chunk, int kk_max, 
     l.q = off; off = align_up(off + (stage_queries ? size_t(chunk) * ix->d * 4 : 0));
     l.oi = off; off = align_up(off + (stage_ids ? size_t(chunk) * k_stride * 8 : 0));
     l.od = off; off = align_up(off + (stage_dists ? size_t(chunk) * k_stride * 4 : 0));
+    l.hd = off; off = align_up(off + (centroid_tc ? size_t(chunk) * ix->Ns * 2 * ix->sk * 4 : 0));
     l.total = off;
     return l;
 }
@@ -471,6 +485,7 @@ void taco::bind_workspace(SearchLaunch& L, const SearchLayout& lay, char* wb) {
     L.unit_len = reinterpret_cast<uint32_t*>(wb + lay.ulen);
     L.arena = reinterpret_cast<uint32_t*>(wb + lay.arena);
     L.qflag = reinterpret_cast<uint32_t*>(wb + lay.qflag);
+    L.hd = reinterpret_cast<float*>(wb + lay.hd);
 }
 
 namespace {
@@ -491,8 +506,9 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     if (per_query) {
         for (int64_t j = 0; j < nq; ++j) {
             TRY(check_query_params(per_query[j], k_stride));
-            if (per_query[j].precision != precision || per_query[j].select_rule != head.select_rule)
-                return fail(TACO_EINVAL, "precision and select_rule must be uniform in a batch");
+            if (per_query[j].precision != precision || per_query[j].select_rule != head.select_rule ||
+                per_query[j].probe_precision != head.probe_precision)
+                return fail(TACO_EINVAL, "precision, probe_precision and select_rule must be uniform in a batch");
             kk_max = std::max(kk_max, query_list_len(per_query[j]));
         }
     } else {
@@ -503,6 +519,8 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         return fail(TACO_EINVAL, "BF16 search needs an index with BF16 rows (TACO_ROWS_BF16)");
     if (precision == TACO_PREC_FP8 && !ix->d_data_fp8)
         return fail(TACO_EINVAL, "FP8 search needs an index with FP8 rows (TACO_ROWS_FP8)");
+    const bool ctc = head.probe_precision == TACO_PREC_BF16;
+    if (ctc && !ix->d_cent_tc) return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
     int cur_dev = 0;
     TACO_CUDA(cudaGetDevice(&cur_dev));
     if (cur_dev != ix->device) return fail(TACO_EINVAL, "current device %d is not the index's device %d", cur_dev, ix->device);
@@ -514,7 +532,7 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     const int64_t chunk = std::min<int64_t>(nq, kQueryChunk);
     const int Ns = ix->Ns, K = ix->K;
     const SearchLayout lay = plan_search(ix, chunk, kk_max, per_query ? nq : 0, !q_dev, !id_dev, !dist_dev,
-                                         k_stride);
+                                         k_stride, ctc);
     const size_t host_need = per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0;
     TRY(ensure_workspace(ix, lay.total, host_need));
     char* wb = static_cast<char*>(ix->ws.base);
@@ -542,6 +560,7 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         L.precision = precision;
         L.kk_max = kk_max;
         bind_workspace(L, lay, wb);
+        L.centroid_tc = ctc;
         L.out_ids = id_dev ? out_ids + c0 * k_stride : reinterpret_cast<int64_t*>(wb + lay.oi);
         L.out_dists = dist_dev ? out_dists + c0 * k_stride : reinterpret_cast<float*>(wb + lay.od);
         L.k_stride = k_stride;
@@ -610,6 +629,8 @@ int taco_index_get_info(const taco_index* ix, taco_index_info* info) {
     info->cluster_size = ix->cluster;
     info->has_fp8 = ix->d_data_fp8 != nullptr;
     info->fp8_pitch = ix->dp8;
+    info->has_centroid_tc = ix->d_cent_tc != nullptr;
+    info->reserved = 0;
     info->device_bytes = ix->device_bytes;
     return TACO_OK;
 }
@@ -679,6 +700,32 @@ int taco_load_index(const char* path, int32_t keep_rows, void* stream, taco_inde
     ix->eigvals = ev;
     ix->alloc = alloc;
     *out = ix;
+    return TACO_OK;
+}
+
+int taco_centroid_distances(const taco_index* ix, const float* qt, int64_t nq, int32_t probe_precision, float* out,
+                            void* stream) {
+    if (!ix) return fail(TACO_EINVAL, "null index");
+    if (nq < 0) return fail(TACO_EINVAL, "nq < 0");
+    if (nq == 0) return TACO_OK;
+    if (!qt || !out || !is_device_pointer(qt) || !is_device_pointer(out))
+        return fail(TACO_EINVAL, "qt and out must be device pointers");
+    if (probe_precision != TACO_PREC_FP32 && probe_precision != TACO_PREC_BF16)
+        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32 or TACO_PREC_BF16");
+    if (probe_precision == TACO_PREC_BF16 && !ix->d_cent_tc)
+        return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
+    TACO_CUDA(launch_centroid_dist(ix, qt, nq, probe_precision == TACO_PREC_BF16, out,
+                                   static_cast<cudaStream_t>(stream)));
+    return TACO_OK;
+}
+
+int taco_device_status(const taco_index* ix, int32_t* status, int32_t clear) {
+    if (!ix || !status) return fail(TACO_EINVAL, "null argument");
+    TACO_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    TACO_CUDA(cudaMemcpy(&v, ix->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear) TACO_CUDA(cudaMemset(ix->d_status, 0, sizeof(int)));
+    *status = v;
     return TACO_OK;
 }
 

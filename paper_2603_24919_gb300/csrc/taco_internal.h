@@ -96,6 +96,9 @@ struct taco_index {
     uint8_t* d_data_fp8 = nullptr;      // [n][dp8] e4m3 of B^T (o - o_bar), or null
     float* d_fp8_scale = nullptr;       // [2][dp8]: per-dimension scale (its subspace's), 1/scale
     int dp8 = 0;                        // Dp rounded up to 16
+    uint8_t* d_cent_tc = nullptr;       // [2 N_s] BF16 centroid operands in the tcgen05 layout
+    float* d_cent_tc_norm = nullptr;    // [2 N_s][N] squared norms of those BF16 centroids
+    int* d_status = nullptr;            // device status word: 1 = a bounded device wait gave up
     float* d_obar = nullptr;            // [d]
     float* d_B = nullptr;               // [d][Dp]
     float* d_cent = nullptr;            // [Ns][sk][s]
@@ -129,6 +132,13 @@ cudaError_t launch_absmax_cols(const float* Y, int64_t rows, int Dp, unsigned* m
 cudaError_t launch_quantize_fp8(const float* Y, int64_t rows, int Dp, int dp8,
                                 const float* inv_scale, uint8_t* out, cudaStream_t st);
 
+// Query x centroid distance block (Alg. 6 steps 4-5) as a separate kernel:
+// hd[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2, FP32 on CUDA cores or BF16 on tcgen05.
+bool centroid_tc_supported(const taco_index* ix);
+int build_centroid_tc(taco_index* ix);
+cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t nq, bool tensor_cores,
+                                 float* hd, cudaStream_t st);
+
 struct SearchLaunch {
     const taco_index* ix;
     const float* queries;      // device [nq][d]
@@ -154,18 +164,21 @@ struct SearchLaunch {
     int k_stride;
     taco_debug_out dbg;        // device pointers, already offset to this chunk
     bool skip_profile;         // record no profiling events (launches that may be captured)
+    bool centroid_tc;          // centroid distances from the tcgen05 block into hd
+    float* hd;                 // device [nq][Ns][2][sk] (centroid_tc)
 };
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
 
 // Byte offsets of one launch group's device workspace (each 256-byte aligned).
 struct SearchLayout {
-    size_t qt, cells, nc, ret, ld, li, uge, uoff, ulen, arena, qflag, par, q, oi, od;
+    size_t qt, cells, nc, ret, ld, li, uge, uoff, ulen, arena, qflag, par, q, oi, od, hd;
     size_t total;
 };
 // Workspace of `chunk` queries with lists of kk_max entries; `n_params` per-query parameter
 // records, and staging for queries / ids / distances when the caller's are not on the device.
 SearchLayout plan_search(const taco_index* ix, int64_t chunk, int kk_max, int64_t n_params,
-                         bool stage_queries, bool stage_ids, bool stage_dists, int k_stride);
+                         bool stage_queries, bool stage_ids, bool stage_dists, int k_stride,
+                         bool centroid_tc = false);
 // The workspace pointers of a SearchLaunch over `wb` laid out by `lay` (two-pass form).
 void bind_workspace(SearchLaunch& L, const SearchLayout& lay, char* wb);
 // Device form of the query parameters and the list length they need.

@@ -64,6 +64,8 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
         return fail(TACO_EINVAL, "unknown select_rule %d", q.select_rule);
     if (q.precision != TACO_PREC_FP32 && q.precision != TACO_PREC_BF16)
         return fail(TACO_EINVAL, "unknown precision %d", q.precision);
+    if (q.probe_precision != TACO_PREC_FP32)
+        return fail(TACO_EINVAL, "taco_search_batch_noalloc computes centroid distances in FP32 only");
     if (q.precision == TACO_PREC_BF16 && (q.shortlist_mult < 1 || !index->d_data_bf16))
         return fail(TACO_EINVAL, "BF16 needs shortlist_mult >= 1 and an index with BF16 rows");
     if (nq > kQueryChunk)

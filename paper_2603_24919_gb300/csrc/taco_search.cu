@@ -36,6 +36,7 @@ __device__ __forceinline__ unsigned long long cell_key(const float* d1, const fl
 
 __global__ void __launch_bounds__(kSelThreads)
 probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict__ cent,
+                   const float* __restrict__ hd,
                    int Ns, int s, int h1, int sk, const uint32_t* __restrict__ sizes, int64_t n,
                    QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                    int list_cap, uint16_t* __restrict__ cells_out,
@@ -67,9 +68,13 @@ probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict
         const int off = h ? h1 : 0, len = h ? s - h1 : h1;
         const float* cc = cent + (size_t(i) * sk + c) * s + off;
         float acc = 0.f;
-        for (int j = 0; j < len; ++j) {
-            const float df = qi[off + j] - cc[j];
-            acc = fmaf(df, df, acc);
+        if (hd) {   // from the separate centroid block
+            acc = hd[(size_t(q) * Ns + i) * 2 * sk + t];
+        } else {
+            for (int j = 0; j < len; ++j) {
+                const float df = qi[off + j] - cc[j];
+                acc = fmaf(df, df, acc);
+            }
         }
         (h ? d2 : d1)[c] = acc;
     }
@@ -235,6 +240,7 @@ constexpr int kWalkMaxPops = 1024;
 template <int E>   // rows per lane: sqrtK <= 32 E, E in {1, 2, 4}
 __global__ void __launch_bounds__(kWalkThreads)
 probe_cells_walk_kernel(const float* __restrict__ qt, int Dp, const float* __restrict__ cent,
+                   const float* __restrict__ hd,
                         int Ns, int s, int h1, int sk, const uint32_t* __restrict__ sizes,
                         int64_t n, QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                         int64_t ntasks, uint16_t* __restrict__ cells_out,
@@ -267,7 +273,10 @@ probe_cells_walk_kernel(const float* __restrict__ qt, int Dp, const float* __res
         for (int e = 0; e < E; ++e) {
             const int t = lane + 32 * e;
             float d1 = __int_as_float(0x7f800000), d2 = d1;
-            if (t < sk) {
+            if (t < sk && hd) {   // from the separate centroid block
+                d1 = hd[(size_t(q) * Ns + i) * 2 * sk + t];
+                d2 = hd[(size_t(q) * Ns + i) * 2 * sk + sk + t];
+            } else if (t < sk) {
                 const float* cc = cent + (size_t(i) * sk + t) * s;
                 float acc = 0.f;
                 for (int j = 0; j < h1; ++j) {
@@ -434,6 +443,7 @@ probe_cells_walk_kernel(const float* __restrict__ qt, int Dp, const float* __res
 template <int CPT>
 __global__ void __launch_bounds__(kSelThreads)
 probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __restrict__ cent,
+                   const float* __restrict__ hd,
                        int Ns, int s, int h1, int sk, const uint32_t* __restrict__ sizes,
                        int64_t n, QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                        int list_cap, uint16_t* __restrict__ cells_out,
@@ -471,9 +481,13 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
         const int off = h ? h1 : 0, len = h ? s - h1 : h1;
         const float* cc = cent + (size_t(i) * sk + c) * s + off;
         float acc = 0.f;
-        for (int j = 0; j < len; ++j) {
-            const float df = qi[off + j] - cc[j];
-            acc = fmaf(df, df, acc);
+        if (hd) {   // from the separate centroid block
+            acc = hd[(size_t(q) * Ns + i) * 2 * sk + t];
+        } else {
+            for (int j = 0; j < len; ++j) {
+                const float df = qi[off + j] - cc[j];
+                acc = fmaf(df, df, acc);
+            }
         }
         (h ? d2 : d1)[c] = acc;
     }
@@ -814,6 +828,14 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
     if (L.dbg.query_t)
         TACO_CUDA(cudaMemcpyAsync(L.dbg.query_t, L.qt, size_t(L.nq) * ix->Dp * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
+    // 1b. the query x centroid block on the tensor cores (probe_precision BF16)
+    const float* hd = nullptr;
+    if (L.centroid_tc) {
+        if (int rc = prof_begin(pix, 6, st, &pb, &pe)) return rc;
+        TACO_CUDA(launch_centroid_dist(ix, L.qt, L.nq, true, L.hd, st));
+        if (int rc = prof_end(pix, 6, st, pb, pe)) return rc;
+        hd = L.hd;
+    }
     // 2. per (query, subspace) probed cells (Alg. 6 steps 3-6, Alg. 4)
     {
         const int cap = next_pow2(K);
@@ -838,7 +860,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             const unsigned blocks = unsigned((ntasks + kWalkThreads / 32 - 1) / (kWalkThreads / 32));
 #define TACO_PROBE_WALK(E)                                                                        \
     probe_cells_walk_kernel<E><<<blocks, kWalkThreads, 0, st>>>(                                  \
-        L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
+        L.qt, ix->Dp, ix->d_cent, hd, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
         L.params, ntasks, L.cells, L.ncells, L.retrieved)
             if (ix->sk <= 32) TACO_PROBE_WALK(1);
             else if (ix->sk <= 64) TACO_PROBE_WALK(2);
@@ -850,7 +872,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         const int cpt = (K + kSelThreads - 1) / kSelThreads;
 #define TACO_PROBE_REG(N)                                                                         \
     probe_cells_reg_kernel<N><<<grid, kSelThreads, smem, st>>>(                                   \
-        L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
+        L.qt, ix->Dp, ix->d_cent, hd, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
         L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo)
         if (cpt <= 1) TACO_PROBE_REG(1);
         else if (cpt <= 2) TACO_PROBE_REG(2);
@@ -859,7 +881,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         else if (cpt <= 16) TACO_PROBE_REG(16);
         else
             probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
-                L.qt, ix->Dp, ix->d_cent, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
+                L.qt, ix->Dp, ix->d_cent, hd, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
                 L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo);
 #undef TACO_PROBE_REG
         TACO_CUDA(cudaGetLastError());

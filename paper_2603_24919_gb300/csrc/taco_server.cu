@@ -118,7 +118,7 @@ namespace {
 size_t batch_bytes(const taco_server* S, int n, int kk) {
     const int nl = S->p.use_graphs ? size_bucket(n, S->p.max_batch) : n;
     const int kl = S->p.use_graphs ? list_bucket(kk) : kk;
-    return plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out).total;
+    return plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out, S->p.probe_precision == TACO_PREC_BF16).total;
 }
 
 // Enqueue one batch of nl staged queries on the slot's stream (also used under capture).
@@ -137,6 +137,7 @@ int enqueue_batch(taco_server* S, Slot& sl, const SearchLayout& lay, int nl, int
     L.precision = S->p.precision;
     L.kk_max = kl;
     bind_workspace(L, lay, wb);
+    L.centroid_tc = S->p.probe_precision == TACO_PREC_BF16;
     L.out_ids = reinterpret_cast<int64_t*>(wb + lay.oi);
     L.out_dists = reinterpret_cast<float*>(wb + lay.od);
     L.k_stride = S->k_out;
@@ -158,7 +159,8 @@ int launch_batch(taco_server* S, Slot& sl, int kk_max, int64_t* n_launch, int64_
         std::memcpy(sl.h_q + size_t(j) * S->d, S->q_store.data() + size_t(src) * S->d, size_t(S->d) * 4);
         sl.h_p[j] = query_params_dev(S->reqs[src].p);
     }
-    const SearchLayout lay = plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out);
+    const SearchLayout lay = plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out,
+                                         S->p.probe_precision == TACO_PREC_BF16);
     const std::pair<int, int> key(nl, kl);
     auto it = sl.graphs.find(key);
     if (it != sl.graphs.end()) {
@@ -315,8 +317,9 @@ void release_slots(taco_server* S) {
 
 int check_request(const taco_server* S, const taco_query_params& q) {
     if (int rc = check_query_params(q, TACO_MAX_K)) return rc;
-    if (q.precision != S->p.precision || q.select_rule != S->p.select_rule)
-        return fail(TACO_EINVAL, "precision and select_rule must match the server's");
+    if (q.precision != S->p.precision || q.select_rule != S->p.select_rule ||
+        q.probe_precision != S->p.probe_precision)
+        return fail(TACO_EINVAL, "precision, probe_precision and select_rule must match the server's");
     if (query_list_len(q) > S->p.max_list)
         return fail(TACO_EINVAL, "list length %d exceeds the server's max_list %d", query_list_len(q), S->p.max_list);
     return TACO_OK;
@@ -341,7 +344,11 @@ int taco_server_create(const taco_index* index, const taco_server_params* params
         return fail(TACO_EINVAL, "the index has no row copy for the server's precision");
     if (p.select_rule != TACO_SELECT_LITERAL && p.select_rule != TACO_SELECT_PROSE)
         return fail(TACO_EINVAL, "unknown select_rule");
-    if (p.max_wait_us < 0 || p.slot_bytes < 0 || p.reserved != 0) return fail(TACO_EINVAL, "bad max_wait_us, slot_bytes or reserved");
+    if (p.max_wait_us < 0 || p.slot_bytes < 0) return fail(TACO_EINVAL, "bad max_wait_us or slot_bytes");
+    if (p.probe_precision != TACO_PREC_FP32 && p.probe_precision != TACO_PREC_BF16)
+        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32 or TACO_PREC_BF16");
+    if (p.probe_precision == TACO_PREC_BF16 && !index->d_cent_tc)
+        return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
     int dev = 0;
     TACO_CUDA(cudaGetDevice(&dev));
     if (dev != index->device) return fail(TACO_EINVAL, "current device %d is not the index's device %d", dev, index->device);

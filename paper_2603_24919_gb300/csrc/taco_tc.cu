@@ -1,0 +1,339 @@
+// Query x centroid distance block of Alg. 6 steps 4-5 on the tcgen05 tensor cores.
+//
+// For every subspace i and half h the squared distances of the transformed half-queries to
+// the sqrt(K) half-centroids form a dense product: dist[q][c] = |q|^2 + |c|^2 - 2 q.c with
+// Q_{i,h} [nq x len] and C_{i,h} [sqrt(K) x len]. One CTA (4 warps) takes 128 queries and
+// walks the 2 N_s (subspace, half) pairs: the pair's centroid operand (BF16, already in the
+// tensor-core shared-memory layout, built with the index) arrives by a bulk asynchronous copy
+// (cp.async.bulk, completion counted on an mbarrier), the threads write the BF16 half-queries,
+// one thread issues the MMAs (kind::f16, M = 128, N = sqrt(K) rounded up to 16, K steps of 16)
+// into a tensor-memory accumulator and commits them to a second mbarrier, and each warp reads
+// its 32 accumulator lanes back (tcgen05.ld) and writes the distances. Every wait is bounded:
+// on a timeout the kernel records 1 in the index's status word and leaves the pair loop.
+//
+// Operands are BF16 with FP32 accumulation, so this is the precision form of the block; the
+// FP32 path computes the same distances on CUDA cores (centroid_dist_simt_kernel and the
+// fused code of the probe kernels).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "taco_internal.h"
+
+namespace taco {
+namespace {
+
+constexpr int kTcM = 128;        // queries per CTA (MMA M; one TMEM lane per query)
+constexpr int kTcThreads = 128;  // 4 warps: warp w reads TMEM lanes 32 w .. 32 w + 31
+constexpr uint32_t kTcWaitPolls = 1u << 22;   // bounded mbarrier waits (~0.3 s with backoff)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzle: 8-row x 16-byte core
+// matrices; `lbo` = byte distance between core matrices adjacent along K, `sbo` = between
+// core matrices adjacent along M / N; bit 46 = descriptor version of tcgen05.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((addr & 0x3ffffu) >> 4) | (uint64_t((lbo & 0x3ffffu) >> 4) << 16) |
+           (uint64_t((sbo & 0x3ffffu) >> 4) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A (bits 7-9 = 1)
+// and B (bits 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t instr_desc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of `parity` to complete; false after kTcWaitPolls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kTcWaitPolls; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 32) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bulk asynchronous global -> shared copy (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane (load and wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+struct TcGeom {
+    int Ns, s, h1, sk, Dp;
+    int N;    // sqrt_k rounded up to 16 (>= 16): MMA N
+    int KH;   // longer half rounded up to 16: MMA K
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, const uint8_t* __restrict__ cimg,
+                        const float* __restrict__ cnorm, float* __restrict__ hd, int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                                 // [128 / 8][KH / 8] core matrices
+    unsigned char* sB = smem + size_t(kTcM) * g.KH * 2;       // [N / 8][KH / 8] core matrices
+    __shared__ __align__(8) uint64_t bar_load, bar_mma;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t q = int64_t(blockIdx.x) * kTcM + tid;      // this thread's query (TMEM lane tid)
+    const uint32_t ncols = g.N <= 32 ? 32u : (g.N <= 64 ? 64u : 128u);
+    if (warp == 0) tmem_alloc(&s_tmem, ncols);
+    if (tid == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = instr_desc_bf16(kTcM, g.N);
+    const uint32_t bbytes = uint32_t(g.N) * g.KH * 2;
+    const int kc = g.KH / 8;                                  // core matrices along K
+    const uint32_t sbo = uint32_t(kc) * 128u;
+    const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
+    uint32_t phase = 0;
+    for (int p = 0; p < 2 * g.Ns; ++p) {
+        const int i = p >> 1, h = p & 1;
+        const int off = h ? g.h1 : 0, len = h ? g.s - g.h1 : g.h1;
+        if (tid == 0) {
+            mbar_expect_tx(&bar_load, bbytes);
+            bulk_g2s(sB, cimg + size_t(p) * bbytes, bbytes, &bar_load);
+        }
+        // this thread's half-query in BF16 (row tid of A) and its squared norm
+        float qn = 0.f;
+        const float* src = qt + q * g.Dp + size_t(i) * g.s + off;
+        for (int c8 = 0; c8 < kc; ++c8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const int k0 = c8 * 8 + e;
+                const float x0 = (q < nq && k0 < len) ? src[k0] : 0.f;
+                const float x1 = (q < nq && k0 + 1 < len) ? src[k0 + 1] : 0.f;
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+                const float2 r = __bfloat1622float2(b2);
+                qn = fmaf(r.x, r.x, qn);
+                qn = fmaf(r.y, r.y, qn);
+                uint32_t u;
+                memcpy(&u, &b2, 4);
+                w[e >> 1] = u;
+            }
+            *reinterpret_cast<uint4*>(sA + ((tid >> 3) * kc + c8) * 128 + (tid & 7) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A visible to the MMA
+        __syncthreads();
+        int failed = 0;
+        if (tid == 0) {
+            if (mbar_wait(&bar_load, phase)) {
+                tc_fence_after();
+                for (int t = 0; t < g.KH / 16; ++t)
+                    mma_bf16(tmem, smem_desc(aaddr + t * 256, 128, sbo), smem_desc(baddr + t * 256, 128, sbo),
+                             idesc, t > 0 ? 1u : 0u);
+                mma_commit(&bar_mma);
+            } else {
+                failed = 1;
+            }
+        }
+        if (__syncthreads_or(failed)) {
+            if (tid == 0) atomicExch(status, 1);
+            break;
+        }
+        failed = mbar_wait(&bar_mma, phase) ? 0 : 1;
+        if (__syncthreads_or(failed)) {
+            if (tid == 0) atomicExch(status, 1);
+            break;
+        }
+        tc_fence_after();
+        const float* cn = cnorm + size_t(p) * g.N;
+        float* out = hd + ((q * g.Ns + i) * 2 + h) * g.sk;
+        for (int c0 = 0; c0 < g.N; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
+            if (q < nq) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int c = c0 + e;
+                    if (c < g.sk) out[c] = fmaxf(qn + cn[c] - 2.f * v[e], 0.f);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();   // A, B and the accumulator are free for the next pair
+        phase ^= 1u;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+// The same block in FP32 on CUDA cores, sum of squared differences (one thread per
+// (query, pair, centroid)).
+__global__ void centroid_dist_simt_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g,
+                                          const float* __restrict__ cent, float* __restrict__ hd) {
+    const int64_t total = nq * 2 * g.Ns * g.sk;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int c = int(t % g.sk);
+        const int64_t r = t / g.sk;
+        const int h = int(r % 2);
+        const int i = int((r / 2) % g.Ns);
+        const int64_t q = r / (2 * g.Ns);
+        const int off = h ? g.h1 : 0, len = h ? g.s - g.h1 : g.h1;
+        const float* qi = qt + q * g.Dp + size_t(i) * g.s + off;
+        const float* cc = cent + (size_t(i) * g.sk + c) * g.s + off;
+        float acc = 0.f;
+        for (int j = 0; j < len; ++j) {
+            const float df = qi[j] - cc[j];
+            acc = fmaf(df, df, acc);
+        }
+        hd[t] = acc;
+    }
+}
+
+TcGeom geom_of(const taco_index* ix) {
+    TcGeom g;
+    g.Ns = ix->Ns;
+    g.s = ix->s;
+    g.h1 = ix->h1;
+    g.sk = ix->sk;
+    g.Dp = ix->Dp;
+    g.N = std::max(16, (ix->sk + 15) / 16 * 16);
+    g.KH = std::max(16, (std::max(ix->h1, ix->s - ix->h1) + 15) / 16 * 16);
+    return g;
+}
+
+size_t tc_smem_bytes(const TcGeom& g) {
+    // operands, and at least a quarter of the SM's shared memory so that at most four CTAs
+    // (4 x 128 TMEM columns) share an SM
+    return std::max<size_t>(size_t(kTcM + g.N) * g.KH * 2, 57 * 1024);
+}
+
+}  // namespace
+
+bool centroid_tc_supported(const taco_index* ix) {
+    const TcGeom g = geom_of(ix);
+    return g.N <= 128 && size_t(kTcM + g.N) * g.KH * 2 <= size_t(200) * 1024;
+}
+
+int build_centroid_tc(taco_index* ix) {
+    if (!centroid_tc_supported(ix)) return TACO_OK;   // the tensor-core block is not offered
+    const TcGeom g = geom_of(ix);
+    const int P = 2 * g.Ns, kc = g.KH / 8;
+    const size_t bbytes = size_t(g.N) * g.KH * 2;
+    std::vector<uint8_t> img(size_t(P) * bbytes, 0);
+    std::vector<float> norm(size_t(P) * g.N, 0.f);
+    for (int p = 0; p < P; ++p) {
+        const int i = p >> 1, h = p & 1;
+        const int off = h ? g.h1 : 0, len = h ? g.s - g.h1 : g.h1;
+        for (int n = 0; n < g.sk; ++n) {
+            float acc = 0.f;
+            for (int k = 0; k < len; ++k) {
+                const float x = float(ix->centroids[(size_t(i) * g.sk + n) * g.s + off + k]);
+                const __nv_bfloat16 b = __float2bfloat16_rn(x);
+                const float r = __bfloat162float(b);
+                acc += r * r;
+                uint16_t bits;
+                std::memcpy(&bits, &b, 2);
+                const size_t at = size_t(p) * bbytes + size_t((n / 8) * kc + k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+                std::memcpy(&img[at], &bits, 2);
+            }
+            norm[size_t(p) * g.N + n] = acc;
+        }
+    }
+    cudaError_t e = cudaMalloc(&ix->d_cent_tc, img.size());
+    if (e == cudaSuccess) e = cudaMalloc(&ix->d_cent_tc_norm, norm.size() * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tensor-core centroids)", __FILE__, __LINE__);
+    ix->device_bytes += int64_t(img.size() + norm.size() * 4);
+    TACO_CUDA(cudaMemcpy(ix->d_cent_tc, img.data(), img.size(), cudaMemcpyHostToDevice));
+    TACO_CUDA(cudaMemcpy(ix->d_cent_tc_norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice));
+    return TACO_OK;
+}
+
+cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t nq, bool tensor_cores, float* hd,
+                                 cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    const TcGeom g = geom_of(ix);
+    if (tensor_cores) {
+        if (!ix->d_cent_tc) return cudaErrorNotSupported;
+        const size_t smem = tc_smem_bytes(g);
+        cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(centroid_dist_tc_kernel), smem);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = (nq + kTcM - 1) / kTcM;
+        centroid_dist_tc_kernel<<<unsigned(blocks), kTcThreads, smem, st>>>(qt, nq, g, ix->d_cent_tc,
+                                                                           ix->d_cent_tc_norm, hd, ix->d_status);
+        return cudaGetLastError();
+    }
+    const int64_t total = nq * 2 * g.Ns * g.sk;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 32);
+    centroid_dist_simt_kernel<<<unsigned(blocks), 256, 0, st>>>(qt, nq, g, ix->d_cent, hd);
+    return cudaGetLastError();
+}
+
+}  // namespace taco

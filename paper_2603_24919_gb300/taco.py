@@ -34,7 +34,8 @@ class BuildParams(C.Structure):
 class QueryParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("precision", C.c_int32), ("budget", C.c_int64),
                 ("rerank_target", C.c_int64), ("select_rule", C.c_int32),
-                ("shortlist_mult", C.c_int32)]
+                ("shortlist_mult", C.c_int32), ("probe_precision", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class IndexParts(C.Structure):
@@ -47,7 +48,8 @@ class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("n_subspaces", C.c_int32),
                 ("sub_dim", C.c_int32), ("sqrt_k", C.c_int32), ("d_pad", C.c_int32),
                 ("has_bf16", C.c_int32), ("n_slabs", C.c_int32), ("cluster_size", C.c_int32),
-                ("has_fp8", C.c_int32), ("fp8_pitch", C.c_int32), ("device_bytes", C.c_int64)]
+                ("has_fp8", C.c_int32), ("fp8_pitch", C.c_int32), ("has_centroid_tc", C.c_int32),
+                ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 class DebugOut(C.Structure):
@@ -60,7 +62,7 @@ class ServerParams(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("queue_capacity", C.c_int32),
                 ("max_list", C.c_int32), ("precision", C.c_int32), ("select_rule", C.c_int32),
                 ("max_wait_us", C.c_int64), ("slot_bytes", C.c_int64), ("use_graphs", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("probe_precision", C.c_int32)]
 
 
 class RequestInfo(C.Structure):
@@ -75,9 +77,9 @@ class ServerStats(C.Structure):
                 ("max_in_flight", C.c_int64), ("slot_bytes", C.c_int64)]
 
 
-NUM_KERNELS = 6
+NUM_KERNELS = 7
 KERNEL_NAMES = ("project", "probe_cells", "count_lists", "select_rerank", "cluster_count_select",
-                "final_merge")
+                "final_merge", "centroid_tc")
 
 
 class KernelTimes(C.Structure):
@@ -107,6 +109,9 @@ SIGNATURES = {
     "taco_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "taco_profile_read": (C.c_int, [C.c_void_p, C.POINTER(KernelTimes), C.c_int32]),
     "taco_free_index": (None, [C.c_void_p]),
+    "taco_centroid_distances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                          C.c_void_p, C.c_void_p]),
+    "taco_device_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
     "taco_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
     "taco_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(QueryParams),
                                      C.POINTER(C.c_uint64)]),
@@ -201,9 +206,10 @@ def _rows(keep_bf16, keep_fp8):
 
 
 def query_params(k, budget, rerank_target, precision="fp32", select_rule="literal",
-                 shortlist_mult=4):
+                 shortlist_mult=4, probe_precision="fp32"):
     return QueryParams(int(k), _PREC.get(precision, precision), int(budget), int(rerank_target),
-                       _RULE.get(select_rule, select_rule), int(shortlist_mult))
+                       _RULE.get(select_rule, select_rule), int(shortlist_mult),
+                       _PREC.get(probe_precision, probe_precision), 0)
 
 
 class TacoIndex:
@@ -297,10 +303,11 @@ class TacoIndex:
 
     # ---- search --------------------------------------------------------------------
     def _prepare(self, queries, k, budget, rerank_target, precision, select_rule,
-                 shortlist_mult, per_query, k_stride):
+                 shortlist_mult, per_query, k_stride, probe_precision="fp32"):
         q = _as_f32(queries)
         nq = q.shape[0]
-        defaults = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult)
+        defaults = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult,
+                                probe_precision)
         pq = None
         if per_query is not None:
             arr = (QueryParams * nq)()
@@ -326,15 +333,35 @@ class TacoIndex:
 
     def search(self, queries, k, budget, rerank_target, precision="fp32", select_rule="literal",
                shortlist_mult=4, per_query=None, k_stride=None, out_ids=None, out_dists=None,
-               stream=None):
+               stream=None, probe_precision="fp32"):
         """Alg. 6 for a batch; returns (ids int64 [nq,k_stride], dists float32 [nq,k_stride])."""
         q, nq, defaults, pq, k_stride = self._prepare(queries, k, budget, rerank_target, precision,
-                                                      select_rule, shortlist_mult, per_query, k_stride)
+                                                      select_rule, shortlist_mult, per_query, k_stride,
+                                                      probe_precision)
         out_ids, out_dists = self._outputs(q, nq, k_stride, out_ids, out_dists)
         _check(load_library().taco_search_batch(
             self._h, _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
             C.byref(defaults), k_stride, _ptr(out_ids), _ptr(out_dists), _stream_handle(stream)))
         return out_ids, out_dists
+
+    def centroid_distances(self, qt, probe_precision="fp32", stream=None):
+        """taco_centroid_distances: [nq, N_s, 2, sqrt_k] squared half-distances of the
+        transformed queries qt (CUDA [nq, N_s*s]) to the centroids."""
+        torch = _torch()
+        inf = self.info()
+        nq = int(qt.shape[0])
+        out = torch.empty((nq, inf["n_subspaces"], 2, inf["sqrt_k"]), dtype=torch.float32,
+                          device=qt.device)
+        _check(load_library().taco_centroid_distances(
+            self._h, _ptr(qt.contiguous()), nq, _PREC.get(probe_precision, probe_precision),
+            _ptr(out), _stream_handle(stream)))
+        return out
+
+    def device_status(self, clear=True):
+        """The index's device status word (0 = no bounded device wait gave up)."""
+        v = C.c_int32()
+        _check(load_library().taco_device_status(self._h, C.byref(v), int(bool(clear))))
+        return int(v.value)
 
     def search_noalloc(self, queries, out_ids, out_dists, k, budget, rerank_target,
                        precision="fp32", select_rule="literal", shortlist_mult=4, stream=None):
@@ -348,11 +375,12 @@ class TacoIndex:
 
     def search_debug(self, queries, k, budget, rerank_target, precision="fp32",
                      select_rule="literal", shortlist_mult=4, per_query=None, k_stride=None,
-                     want_sc=True, stream=None):
+                     want_sc=True, stream=None, probe_precision="fp32"):
         """search() plus every intermediate result (device tensors); queries on CUDA."""
         torch = _torch()
         q, nq, defaults, pq, k_stride = self._prepare(queries, k, budget, rerank_target, precision,
-                                                      select_rule, shortlist_mult, per_query, k_stride)
+                                                      select_rule, shortlist_mult, per_query, k_stride,
+                                                      probe_precision)
         assert _is_cuda_tensor(q), "search_debug needs CUDA queries"
         inf = self.info()
         ns, K, n = inf["n_subspaces"], inf["sqrt_k"] ** 2, inf["n"]
@@ -384,13 +412,14 @@ class TacoServer:
 
     def __init__(self, index, max_batch=256, slots=2, queue_capacity=None, max_list=10,
                  precision="fp32", select_rule="literal", max_wait_us=200, slot_bytes=0,
-                 use_graphs=True):
+                 use_graphs=True, probe_precision="fp32"):
         self.index = index   # keeps the index alive while the server runs
         self.d = index.info()["d"]
+        self.probe_precision = probe_precision
         p = ServerParams(int(max_batch), int(slots), int(queue_capacity or 4 * max_batch),
                          int(max_list), _PREC.get(precision, precision),
                          _RULE.get(select_rule, select_rule), int(max_wait_us), int(slot_bytes),
-                         int(bool(use_graphs)), 0)
+                         int(bool(use_graphs)), _PREC.get(probe_precision, probe_precision))
         h = C.c_void_p()
         _check(load_library().taco_server_create(index._h, C.byref(p), C.byref(h)))
         self._h = h
@@ -418,7 +447,8 @@ class TacoServer:
         EAGAIN when the queue is full."""
         q = np.ascontiguousarray(query, dtype=np.float32).reshape(-1)
         assert q.shape[0] == self.d
-        p = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult)
+        p = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult,
+                         self.probe_precision)
         t = C.c_uint64()
         _check(load_library().taco_server_submit(self._h, q.ctypes.data, C.byref(p), C.byref(t)))
         return t.value

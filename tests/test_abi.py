@@ -70,13 +70,14 @@ int main(void) {
   S(taco_build_params); P(taco_build_params, seed); P(taco_build_params, keep_rows);
   S(taco_query_params); P(taco_query_params, budget); P(taco_query_params, rerank_target);
   P(taco_query_params, select_rule); P(taco_query_params, shortlist_mult);
+  P(taco_query_params, probe_precision);
   S(taco_index_parts); P(taco_index_parts, codes); P(taco_index_parts, sqrt_k);
   S(taco_index_info); P(taco_index_info, d_pad); P(taco_index_info, cluster_size);
-  P(taco_index_info, has_fp8); P(taco_index_info, fp8_pitch);
+  P(taco_index_info, has_fp8); P(taco_index_info, fp8_pitch); P(taco_index_info, has_centroid_tc);
   P(taco_index_info, device_bytes);
   S(taco_debug_out); P(taco_debug_out, candidate_num);
   S(taco_server_params); P(taco_server_params, max_wait_us); P(taco_server_params, slot_bytes);
-  P(taco_server_params, use_graphs);
+  P(taco_server_params, use_graphs); P(taco_server_params, probe_precision);
   S(taco_request_info); P(taco_request_info, batch_size); P(taco_request_info, slot);
   S(taco_server_stats); P(taco_server_stats, slot_bytes);
   return 0;
