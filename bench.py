@@ -41,7 +41,11 @@ WORKLOAD = "sift1m"
 ALPHAS = [0.01, 0.02, 0.03, 0.05, 0.08, 0.1]
 BETAS = [0.001, 0.002, 0.005, 0.01]
 RECALL_TARGET = 0.95
-SHORTLIST_MULTS = {"bf16": [1, 2, 4], "fp8": [2, 4, 8]}   # exact FP32 re-rank of mult * k
+SHORTLIST_MULTS = {"bf16": [1, 2, 4], "fp8": [2, 4, 8], "bf16_tc": [1, 2, 4]}   # FP32 re-rank of mult * k
+# search arguments of each form: rows of the candidate re-rank, and the query x centroid block
+FORMS = {"fp32": dict(precision="fp32"), "bf16": dict(precision="bf16"),
+         "fp8": dict(precision="fp8"),
+         "bf16_tc": dict(precision="bf16", probe_precision="bf16")}   # tcgen05 centroid block
 K = 10
 
 
@@ -243,12 +247,12 @@ def run_taco(args):
 
     def timed(prec, a, b, reps, mult=4):
         bud, tgt = budget_from_alpha(a, w.n), target_from_beta(b, w.n)
-        ids, _ = ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult)
+        ids, _ = ix.search(q_dev, K, bud, tgt, shortlist_mult=mult, **FORMS[prec])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ids, _ = ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult)
+            ids, _ = ix.search(q_dev, K, bud, tgt, shortlist_mult=mult, **FORMS[prec])
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
@@ -256,7 +260,7 @@ def run_taco(args):
 
     # ---- calibration: per form, the fastest grid point meeting the recall target ------
     calib = {}
-    for prec in ("fp32", "bf16", "fp8"):
+    for prec in FORMS:
         best = None
         grid = [(args.alpha, args.beta)] if args.alpha else [(a, b) for a in ALPHAS for b in BETAS]
         mults = SHORTLIST_MULTS.get(prec, [4])
@@ -280,8 +284,8 @@ def run_taco(args):
         out_ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
         out_d = torch.empty((nq, K), dtype=torch.float32, device="cuda")
         for _ in range(warmup):
-            ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult, out_ids=out_ids,
-                      out_dists=out_d)
+            ix.search(q_dev, K, bud, tgt, shortlist_mult=mult, out_ids=out_ids, out_dists=out_d,
+                      **FORMS[prec])
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -292,8 +296,8 @@ def run_taco(args):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         evs[0].record(stream)
         for s in range(steps):
-            ix.search(q_dev, K, bud, tgt, precision=prec, shortlist_mult=mult, out_ids=out_ids,
-                      out_dists=out_d)
+            ix.search(q_dev, K, bud, tgt, shortlist_mult=mult, out_ids=out_ids, out_dists=out_d,
+                      **FORMS[prec])
             evs[s + 1].record(stream)
         torch.cuda.synchronize()
         if profile:
@@ -319,14 +323,16 @@ def run_taco(args):
     tot_b, per_b, kt_b, rec_b = run_steps("bf16", args.steps, args.warmup, profile=True)
     tot_f, per_f, kt_f, rec_f = run_steps("fp32", args.steps, args.warmup, profile=True)
     tot_8, per_8, kt_8, rec_8 = run_steps("fp8", args.steps, args.warmup, profile=True)
+    tot_t, per_t, kt_t, rec_t = run_steps("bf16_tc", args.steps, args.warmup, profile=True)
     clk = clocks.stop()
+    device_status = ix.device_status()
 
     # max over ranks of the timed region
-    tot_b, tot_f, tot_8 = max_over_ranks([tot_b, tot_f, tot_8], ws, device="cuda")
+    tot_b, tot_f, tot_8, tot_t = max_over_ranks([tot_b, tot_f, tot_8, tot_t], ws, device="cuda")
     value = ws * nq * args.steps / (tot_b * 1e-3)
     value_fp32 = ws * nq * args.steps / (tot_f * 1e-3)
     value_fp8 = ws * nq * args.steps / (tot_8 * 1e-3)
-    for prec, tot in (("fp32", tot_f), ("bf16", tot_b), ("fp8", tot_8)):
+    for prec, tot in (("fp32", tot_f), ("bf16", tot_b), ("fp8", tot_8), ("bf16_tc", tot_t)):
         precision_stats[prec]["qps"] = round(ws * nq * args.steps / (tot * 1e-3), 1)
 
     # ---- end to end through the C ABI with host buffers --------------------------------
@@ -408,7 +414,8 @@ def run_taco(args):
                    "global_batch": ws * nq, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (512 MB FP32 / 256 MB BF16 rows gathered)",
                    "operating_point": calib},
-        "recall_at_10": {"bf16": round(rec_b, 4), "fp32": round(rec_f, 4), "fp8": round(rec_8, 4)},
+        "recall_at_10": {"bf16": round(rec_b, 4), "fp32": round(rec_f, 4), "fp8": round(rec_8, 4),
+                         "bf16_tc": round(rec_t, 4)},
         "fp32_qps": round(value_fp32, 1),
         "fp8_qps": round(value_fp8, 1),
         "bf16_over_fp32": round(value / value_fp32, 3),
@@ -444,6 +451,9 @@ def run_taco(args):
                                        for k, v in kt_b.items() if v["launches"]}
     line["kernel_ms_per_step_fp8"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                       for k, v in kt_8.items() if v["launches"]}
+    line["kernel_ms_per_step_bf16_tc"] = {k: round(v["ms"] / max(args.steps, 1), 4)
+                                          for k, v in kt_t.items() if v["launches"]}
+    line["device_status"] = device_status   # 0: no bounded device wait gave up
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(ix, data, queries, w, calib["fp32"], args.cpu_seconds)

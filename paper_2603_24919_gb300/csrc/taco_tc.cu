@@ -3,13 +3,17 @@
 // For every subspace i and half h the squared distances of the transformed half-queries to
 // the sqrt(K) half-centroids form a dense product: dist[q][c] = |q|^2 + |c|^2 - 2 q.c with
 // Q_{i,h} [nq x len] and C_{i,h} [sqrt(K) x len]. One CTA (4 warps) takes 128 queries and
-// walks the 2 N_s (subspace, half) pairs: the pair's centroid operand (BF16, already in the
-// tensor-core shared-memory layout, built with the index) arrives by a bulk asynchronous copy
-// (cp.async.bulk, completion counted on an mbarrier), the threads write the BF16 half-queries,
-// one thread issues the MMAs (kind::f16, M = 128, N = sqrt(K) rounded up to 16, K steps of 16)
-// into a tensor-memory accumulator and commits them to a second mbarrier, and each warp reads
-// its 32 accumulator lanes back (tcgen05.ld) and writes the distances. Every wait is bounded:
-// on a timeout the kernel records 1 in the index's status word and leaves the pair loop.
+// a stage of its 2 N_s (subspace, half) pairs: the centroid operands (BF16, already in the tensor-core
+// shared-memory layout, built with the index) arrive by bulk asynchronous copy (cp.async.bulk,
+// completion counted on an mbarrier), the threads write the BF16 half-queries, and one
+// thread issues the MMAs (kind::f16, M = 128, N = sqrt(K) rounded up to 16, K steps of 16)
+// into tensor-memory accumulators and commits them to a second mbarrier, and each warp reads
+// its 32 accumulator lanes back (tcgen05.ld) and writes the distances from registers. A CTA
+// takes one stage of up to 128 / N pairs (an accumulator of N TMEM columns per pair, so four
+// CTAs share an SM's 512 columns): one bulk copy brings the stage's centroid operands, the
+// threads stage its query dimensions with coalesced loads, and one commit covers its MMAs.
+// Every wait is bounded: on a timeout the kernel records 1 in the index's status word and
+// leaves the stage loop.
 //
 // Operands are BF16 with FP32 accumulation, so this is the precision form of the block; the
 // FP32 path computes the same distances on CUDA cores (centroid_dist_simt_kernel and the
@@ -130,17 +134,22 @@ struct TcGeom {
     int KH;   // longer half rounded up to 16: MMA K
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, const uint8_t* __restrict__ cimg,
+__global__ void __launch_bounds__(kTcThreads, 4)
+centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int G, const uint8_t* __restrict__ cimg,
                         const float* __restrict__ cnorm, float* __restrict__ hd, int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                                 // [128 / 8][KH / 8] core matrices
-    unsigned char* sB = smem + size_t(kTcM) * g.KH * 2;       // [N / 8][KH / 8] core matrices
+    const uint32_t abytes = uint32_t(kTcM) * g.KH * 2;       // one pair's A: [128 / 8][KH / 8] core matrices
+    const uint32_t bbytes = uint32_t(g.N) * g.KH * 2;         // one pair's B: [N / 8][KH / 8] core matrices
+    unsigned char* sA = smem;                                 // G pairs' A
+    unsigned char* sB = smem + size_t(G) * abytes;            // G pairs' B
+    float* sQ = reinterpret_cast<float*>(sB + size_t(G) * bbytes);   // [128][W + 1] query dims
     __shared__ __align__(8) uint64_t bar_load, bar_mma;
     __shared__ uint32_t s_tmem;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t q = int64_t(blockIdx.x) * kTcM + tid;      // this thread's query (TMEM lane tid)
-    const uint32_t ncols = g.N <= 32 ? 32u : (g.N <= 64 ? 64u : 128u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t q0 = int64_t(blockIdx.x) * kTcM;
+    const int P = 2 * g.Ns;
+    uint32_t ncols = 32;
+    while (ncols < uint32_t(G * g.N)) ncols <<= 1;           // G * N <= 128 (or one pair of N = 128)
     if (warp == 0) tmem_alloc(&s_tmem, ncols);
     if (tid == 0) {
         mbar_init(&bar_load, 1);
@@ -152,38 +161,47 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, cons
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = instr_desc_bf16(kTcM, g.N);
-    const uint32_t bbytes = uint32_t(g.N) * g.KH * 2;
     const int kc = g.KH / 8;                                  // core matrices along K
     const uint32_t sbo = uint32_t(kc) * 128u;
-    const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
     uint32_t phase = 0;
-    for (int p = 0; p < 2 * g.Ns; ++p) {
-        const int i = p >> 1, h = p & 1;
-        const int off = h ? g.h1 : 0, len = h ? g.s - g.h1 : g.h1;
+    for (int p0 = int(blockIdx.y) * G; p0 < P; p0 += int(gridDim.y) * G) {   // this CTA's stages
+        const int np = min(G, P - p0);
+        // the stage's centroid operands: one bulk copy (pairs are contiguous in the image)
         if (tid == 0) {
-            mbar_expect_tx(&bar_load, bbytes);
-            bulk_g2s(sB, cimg + size_t(p) * bbytes, bbytes, &bar_load);
+            mbar_expect_tx(&bar_load, uint32_t(np) * bbytes);
+            bulk_g2s(sB, cimg + size_t(p0) * bbytes, uint32_t(np) * bbytes, &bar_load);
         }
-        // this thread's half-query in BF16 (row tid of A) and its squared norm
-        float qn = 0.f;
-        const float* src = qt + q * g.Dp + size_t(i) * g.s + off;
-        for (int c8 = 0; c8 < kc; ++c8) {
-            uint32_t w[4];
+        // the stage's query dimensions: one contiguous range [d0, d0 + W) of every row, staged
+        // with coalesced loads (a warp per row, 4 rows in flight per warp), row pitch W + 1
+        const int pl = p0 + np - 1;
+        const int d0 = (p0 >> 1) * g.s + ((p0 & 1) ? g.h1 : 0);
+        const int W = (pl >> 1) * g.s + ((pl & 1) ? g.s : g.h1) - d0;
+#pragma unroll 8
+        for (int m = warp; m < kTcM; m += kTcThreads / 32) {
+            const bool ok = q0 + m < nq;
+            const float* src = qt + (q0 + m) * g.Dp + d0;
+            for (int j = lane; j < W; j += 32) sQ[m * (W + 1) + j] = ok ? src[j] : 0.f;
+        }
+        __syncthreads();
+        // this thread's BF16 half-queries (row tid of each pair's A), zero past a half's length
+        for (int pp = 0; pp < np; ++pp) {
+            const int p = p0 + pp, h = p & 1;
+            const int len = h ? g.s - g.h1 : g.h1;
+            const int base = (p >> 1) * g.s + (h ? g.h1 : 0) - d0;
+            const float* x = sQ + tid * (W + 1) + base;
+            unsigned char* dst = sA + size_t(pp) * abytes + (tid >> 3) * kc * 128 + (tid & 7) * 16;
+            for (int c8 = 0; c8 < kc; ++c8) {
+                uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                const int k0 = c8 * 8 + e;
-                const float x0 = (q < nq && k0 < len) ? src[k0] : 0.f;
-                const float x1 = (q < nq && k0 + 1 < len) ? src[k0 + 1] : 0.f;
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
-                const float2 r = __bfloat1622float2(b2);
-                qn = fmaf(r.x, r.x, qn);
-                qn = fmaf(r.y, r.y, qn);
-                uint32_t u;
-                memcpy(&u, &b2, 4);
-                w[e >> 1] = u;
+                for (int e = 0; e < 8; e += 2) {
+                    const int k = c8 * 8 + e;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(k < len ? x[k] : 0.f, k + 1 < len ? x[k + 1] : 0.f);
+                    uint32_t u;
+                    memcpy(&u, &b2, 4);
+                    w[e >> 1] = u;
+                }
+                *reinterpret_cast<uint4*>(dst + c8 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            *reinterpret_cast<uint4*>(sA + ((tid >> 3) * kc + c8) * 128 + (tid & 7) * 16) =
-                make_uint4(w[0], w[1], w[2], w[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A visible to the MMA
         __syncthreads();
@@ -191,9 +209,13 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, cons
         if (tid == 0) {
             if (mbar_wait(&bar_load, phase)) {
                 tc_fence_after();
-                for (int t = 0; t < g.KH / 16; ++t)
-                    mma_bf16(tmem, smem_desc(aaddr + t * 256, 128, sbo), smem_desc(baddr + t * 256, 128, sbo),
-                             idesc, t > 0 ? 1u : 0u);
+                for (int pp = 0; pp < np; ++pp) {
+                    const uint32_t aaddr = smem_u32(sA + size_t(pp) * abytes);
+                    const uint32_t baddr = smem_u32(sB + size_t(pp) * bbytes);
+                    for (int t = 0; t < g.KH / 16; ++t)
+                        mma_bf16(tmem + uint32_t(pp * g.N), smem_desc(aaddr + t * 256, 128, sbo),
+                                 smem_desc(baddr + t * 256, 128, sbo), idesc, t > 0 ? 1u : 0u);
+                }
                 mma_commit(&bar_mma);
             } else {
                 failed = 1;
@@ -209,21 +231,46 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, cons
             break;
         }
         tc_fence_after();
-        const float* cn = cnorm + size_t(p) * g.N;
-        float* out = hd + ((q * g.Ns + i) * 2 + h) * g.sk;
-        for (int c0 = 0; c0 < g.N; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
-            if (q < nq) {
+        for (int pp = 0; pp < np; ++pp) {
+            const int p = p0 + pp, i = p >> 1, h = p & 1;
+            // |q|^2 of this row's BF16 half-query, from the A operand itself
+            float qn = 0.f;
+            const unsigned char* row = sA + size_t(pp) * abytes + (tid >> 3) * kc * 128 + (tid & 7) * 16;
+            for (int c8 = 0; c8 < kc; ++c8) {
+                const uint4 u = *reinterpret_cast<const uint4*>(row + c8 * 128);
+                const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int c = c0 + e;
-                    if (c < g.sk) out[c] = fmaxf(qn + cn[c] - 2.f * v[e], 0.f);
+                for (int e = 0; e < 4; ++e) {
+                    const float2 f = __bfloat1622float2(b2[e]);
+                    qn = fmaf(f.x, f.x, qn);
+                    qn = fmaf(f.y, f.y, qn);
+                }
+            }
+            const float* cn = cnorm + size_t(p) * g.N;
+            const int64_t q = q0 + tid;                       // TMEM lane tid = this query
+            float* out = hd + ((q * g.Ns + i) * 2 + h) * g.sk;
+            const bool vec = (g.sk & 3) == 0;                 // rows start on 16 bytes
+            for (int c0 = 0; c0 < g.N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(pp * g.N + c0), v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] = fmaxf(qn + __ldg(cn + c0 + e) - 2.f * v[e], 0.f);
+                if (q < nq) {
+                    if (vec) {
+#pragma unroll
+                        for (int e = 0; e < 16; e += 4)
+                            if (c0 + e < g.sk)
+                                *reinterpret_cast<float4*>(out + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (c0 + e < g.sk) out[c0 + e] = v[e];
+                    }
                 }
             }
         }
         tc_fence_before();
-        __syncthreads();   // A, B and the accumulator are free for the next pair
+        __syncthreads();   // A, B and the accumulators are free for the next stage
         phase ^= 1u;
     }
     tc_fence_before();
@@ -269,17 +316,37 @@ TcGeom geom_of(const taco_index* ix) {
     return g;
 }
 
-size_t tc_smem_bytes(const TcGeom& g) {
-    // operands, and at least a quarter of the SM's shared memory so that at most four CTAs
-    // (4 x 128 TMEM columns) share an SM
-    return std::max<size_t>(size_t(kTcM + g.N) * g.KH * 2, 57 * 1024);
+constexpr size_t kTcStageBytes = size_t(54) * 1024;   // operands of one stage (4 CTAs per SM)
+
+// Bytes of one pair in a stage: its A and B operands and its query dimensions (at most the
+// longer half) in the staging tile.
+size_t tc_pair_bytes(const TcGeom& g) {
+    return size_t(kTcM + g.N) * g.KH * 2 + size_t(kTcM) * std::max(g.h1, g.s - g.h1) * 4;
+}
+
+// Pairs per stage (one stage per CTA): four CTAs share an SM, so a stage's accumulators fit
+// 128 of the 512 TMEM columns and its operands a quarter of the shared memory; the many
+// small CTAs spread the block over every SM.
+int tc_pairs_per_stage(const TcGeom& g) {
+    const int by_tmem = std::max(1, 128 / g.N);
+    const int by_smem = int(kTcStageBytes / tc_pair_bytes(g));
+    return std::max(1, std::min({by_tmem, by_smem, 2 * g.Ns}));
+}
+
+size_t tc_smem_bytes(const TcGeom& g, int G) {
+    // the stage's operands and staging tile (row pitch W + 1 <= G * longer half + 1), and at
+    // least a fifth of the SM's shared memory so that at most four CTAs (4 x 128 TMEM columns)
+    // share an SM
+    const size_t ops = size_t(G) * (kTcM + g.N) * g.KH * 2;
+    const size_t tile = size_t(kTcM) * (size_t(G) * std::max(g.h1, g.s - g.h1) + 1) * 4;
+    return std::max<size_t>(ops + tile, 46 * 1024);
 }
 
 }  // namespace
 
 bool centroid_tc_supported(const taco_index* ix) {
     const TcGeom g = geom_of(ix);
-    return g.N <= 128 && size_t(kTcM + g.N) * g.KH * 2 <= size_t(200) * 1024;
+    return g.N <= 128 && tc_pair_bytes(g) + size_t(kTcM) * 4 <= size_t(200) * 1024;
 }
 
 int build_centroid_tc(taco_index* ix) {
@@ -322,11 +389,14 @@ cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t 
     const TcGeom g = geom_of(ix);
     if (tensor_cores) {
         if (!ix->d_cent_tc) return cudaErrorNotSupported;
-        const size_t smem = tc_smem_bytes(g);
+        const int G = tc_pairs_per_stage(g);
+        const size_t smem = tc_smem_bytes(g, G);
         cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(centroid_dist_tc_kernel), smem);
         if (e != cudaSuccess) return e;
-        const int64_t blocks = (nq + kTcM - 1) / kTcM;
-        centroid_dist_tc_kernel<<<unsigned(blocks), kTcThreads, smem, st>>>(qt, nq, g, ix->d_cent_tc,
+        // one CTA per (128 queries, stage of pairs): the stages of a query tile run on
+        // different SMs
+        const dim3 grid(unsigned((nq + kTcM - 1) / kTcM), unsigned((2 * g.Ns + G - 1) / G));
+        centroid_dist_tc_kernel<<<grid, kTcThreads, smem, st>>>(qt, nq, g, G, ix->d_cent_tc,
                                                                            ix->d_cent_tc_norm, hd, ix->d_status);
         return cudaGetLastError();
     }
