@@ -43,6 +43,7 @@ BETAS = [0.001, 0.002, 0.005, 0.01]
 RECALL_TARGET = 0.95
 SHORTLIST_MULTS = {"bf16": [1, 2, 4], "fp8": [2, 4, 8], "bf16_tc": [1, 2, 4]}   # FP32 re-rank of mult * k
 # search arguments of each form: rows of the candidate re-rank, and the query x centroid block
+HEADLINE = "bf16_tc"
 FORMS = {"fp32": dict(precision="fp32"), "bf16": dict(precision="bf16"),
          "fp8": dict(precision="fp8"),
          "bf16_tc": dict(precision="bf16", probe_precision="bf16")}   # tcgen05 centroid block
@@ -320,10 +321,11 @@ def run_taco(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)   # nvidia-smi is sampling before the timed region starts
-    tot_b, per_b, kt_b, rec_b = run_steps("bf16", args.steps, args.warmup, profile=True)
+    # headline form: BF16 rows with the query x centroid block on the tensor cores
+    tot_b, per_b, kt_b, rec_b = run_steps(HEADLINE, args.steps, args.warmup, profile=True)
     tot_f, per_f, kt_f, rec_f = run_steps("fp32", args.steps, args.warmup, profile=True)
     tot_8, per_8, kt_8, rec_8 = run_steps("fp8", args.steps, args.warmup, profile=True)
-    tot_t, per_t, kt_t, rec_t = run_steps("bf16_tc", args.steps, args.warmup, profile=True)
+    tot_t, per_t, kt_t, rec_t = run_steps("bf16", args.steps, args.warmup, profile=True)
     clk = clocks.stop()
     device_status = ix.device_status()
 
@@ -332,30 +334,30 @@ def run_taco(args):
     value = ws * nq * args.steps / (tot_b * 1e-3)
     value_fp32 = ws * nq * args.steps / (tot_f * 1e-3)
     value_fp8 = ws * nq * args.steps / (tot_8 * 1e-3)
-    for prec, tot in (("fp32", tot_f), ("bf16", tot_b), ("fp8", tot_8), ("bf16_tc", tot_t)):
+    for prec, tot in (("fp32", tot_f), (HEADLINE, tot_b), ("fp8", tot_8), ("bf16", tot_t)):
         precision_stats[prec]["qps"] = round(ws * nq * args.steps / (tot * 1e-3), 1)
 
     # ---- end to end through the C ABI with host buffers --------------------------------
-    a, b = calib["bf16"]["alpha"], calib["bf16"]["beta"]
-    mult = calib["bf16"]["shortlist_mult"]
+    a, b = calib[HEADLINE]["alpha"], calib[HEADLINE]["beta"]
+    mult = calib[HEADLINE]["shortlist_mult"]
     bud, tgt = budget_from_alpha(a, w.n), target_from_beta(b, w.n)
     q_host = torch.from_numpy(queries).pin_memory()
     o_ids = torch.empty((nq, K), dtype=torch.int64).pin_memory()
     o_d = torch.empty((nq, K), dtype=torch.float32).pin_memory()
     qh, oi, od = q_host.numpy(), o_ids.numpy(), o_d.numpy()
     for _ in range(max(1, args.warmup)):
-        ix.search(qh, K, bud, tgt, precision="bf16", shortlist_mult=mult, out_ids=oi, out_dists=od)
+        ix.search(qh, K, bud, tgt, shortlist_mult=mult, out_ids=oi, out_dists=od, **FORMS[HEADLINE])
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ix.search(qh, K, bud, tgt, precision="bf16", shortlist_mult=mult, out_ids=oi, out_dists=od)
+        ix.search(qh, K, bud, tgt, shortlist_mult=mult, out_ids=oi, out_dists=od, **FORMS[HEADLINE])
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks([e2e_s], ws, device="cuda")[0]
     e2e_recall = recall_at(oi, truth, K)
 
     # ---- roofline of the dominant kernel ----------------------------------------------
-    dbg = ix.search_debug(q_dev, K, bud, tgt, precision="bf16", shortlist_mult=mult,
+    dbg = ix.search_debug(q_dev, K, bud, tgt, shortlist_mult=mult, **FORMS[HEADLINE],
                           want_sc=False)
     torch.cuda.synchronize()
     retrieved = int(dbg["retrieved_num"].sum().item())
@@ -387,7 +389,7 @@ def run_taco(args):
     for s in range(0, min(nq, 64 * 100), 64):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ix.search(q_dev[s:s + 64], K, bud, tgt, precision="bf16", shortlist_mult=mult)
+        ix.search(q_dev[s:s + 64], K, bud, tgt, shortlist_mult=mult, **FORMS[HEADLINE])
         e1.record(stream)
         e1.synchronize()
         lat_small.append(e0.elapsed_time(e1))
@@ -395,6 +397,7 @@ def run_taco(args):
     serving = None
     if not args.no_serving:
         serving = run_serving(ix, queries, truth, bud, tgt, mult, args.serve_seconds)
+    device_status = max(device_status, ix.device_status())
 
     line = {
         "metric": METRIC,
@@ -408,14 +411,16 @@ def run_taco(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "bf16",
+        "form": "BF16 rows (exact FP32 re-rank of the shortlist), query x centroid block on tcgen05 "
+                "(BF16 operands, FP32 accumulation); fp32_qps = plain FP32 path",
         "data": "synthetic",
         "config": {"workload": "sift1m-like: n=1,000,000 d=128 integer GMM, nq=10,000 per step, "
                                "k=10, N_s=8, s=16, sqrtK=64",
                    "global_batch": ws * nq, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (512 MB FP32 / 256 MB BF16 rows gathered)",
                    "operating_point": calib},
-        "recall_at_10": {"bf16": round(rec_b, 4), "fp32": round(rec_f, 4), "fp8": round(rec_8, 4),
-                         "bf16_tc": round(rec_t, 4)},
+        "recall_at_10": {HEADLINE: round(rec_b, 4), "fp32": round(rec_f, 4), "fp8": round(rec_8, 4),
+                         "bf16_simt_probe": round(rec_t, 4)},
         "fp32_qps": round(value_fp32, 1),
         "fp8_qps": round(value_fp8, 1),
         "bf16_over_fp32": round(value / value_fp32, 3),
@@ -437,7 +442,7 @@ def run_taco(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(dominant, "bf16"), "peak_kind": peak_kind,
-                     "kernel": f"{dominant} (bf16 form)",
+                     "kernel": f"{dominant} ({HEADLINE} form)",
                      "algorithmic_bytes_per_launch": int(alg_bytes),
                      "launch_ms": round(launch_ms, 4),
                      "kernel_share": shares},
@@ -447,12 +452,12 @@ def run_taco(args):
         line["serving"] = serving
     line["kernel_ms_per_step_fp32"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                        for k, v in kt_f.items() if v["launches"]}
-    line["kernel_ms_per_step_bf16"] = {k: round(v["ms"] / max(args.steps, 1), 4)
+    line[f"kernel_ms_per_step_{HEADLINE}"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                        for k, v in kt_b.items() if v["launches"]}
     line["kernel_ms_per_step_fp8"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                       for k, v in kt_8.items() if v["launches"]}
-    line["kernel_ms_per_step_bf16_tc"] = {k: round(v["ms"] / max(args.steps, 1), 4)
-                                          for k, v in kt_t.items() if v["launches"]}
+    line["kernel_ms_per_step_bf16_simt_probe"] = {k: round(v["ms"] / max(args.steps, 1), 4)
+                                                  for k, v in kt_t.items() if v["launches"]}
     line["device_status"] = device_status   # 0: no bounded device wait gave up
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -478,12 +483,14 @@ def run_serving(ix, queries, truth, bud, tgt, mult, span_s):
     max_list = min(mult * kmax, 512)
     out = []
     with TacoServer(ix, max_batch=2048, slots=4, queue_capacity=16384, max_list=max_list,
-                    precision="bf16", max_wait_us=100, use_graphs=True) as srv:
+                    precision="bf16", max_wait_us=100, use_graphs=True,
+                    probe_precision=FORMS[HEADLINE].get("probe_precision", "fp32")) as srv:
         def one(rate, mixed, n_req=None):
             n_req = n_req or max(2000, int(rate * span_s))
             rows = np.arange(n_req) % nq
             ks = rng.choice([10, 100], size=n_req) if mixed else np.full(n_req, 10)
-            per = [query_params(int(k), bud, tgt, "bf16", "literal", mult) for k in ks]
+            per = [query_params(int(k), bud, tgt, "bf16", "literal", mult,
+                                FORMS[HEADLINE].get("probe_precision", "fp32")) for k in ks]
             arrival = np.cumsum(rng.exponential(1e9 / rate, size=n_req)).astype(np.int64)
             ids, _, lat = srv.replay(queries[rows], per, arrival, kmax)
             span = float(np.max(arrival + lat) - arrival[0]) * 1e-9
@@ -498,7 +505,8 @@ def run_serving(ix, queries, truth, bud, tgt, mult, span_s):
             out.append(one(rate, False))
         out.append(one(200_000, True))
         st = srv.stats()
-    return {"server": "max_batch 2048, 4 slots, max_wait 100 us, CUDA graphs, BF16 rows",
+    return {"server": "max_batch 2048, 4 slots, max_wait 100 us, CUDA graphs, BF16 rows, "
+                      "tcgen05 centroid block",
             "loads": out, "batches": st["batches"], "graph_launches": st["graph_launches"],
             "max_in_flight": st["max_in_flight"],
             "mean_batch": round(st["completed"] / max(st["batches"], 1), 1)}
@@ -592,6 +600,7 @@ def run_reference(args):
     serving = None
     if not args.no_serving:
         serving = run_serving(ix, queries, truth, bud, tgt, mult, args.serve_seconds)
+    device_status = max(device_status, ix.device_status())
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
