@@ -46,14 +46,15 @@ extern "C" {
 /* ---- enums ------------------------------------------------------------------------- */
 #define TACO_PREC_FP32 0    /* re-rank candidates with FP32 distances */
 #define TACO_PREC_BF16 1    /* re-rank with a BF16 copy of D, then exact FP32 on a shortlist */
-#define TACO_PREC_FP8 2     /* re-rank with an FP8-e4m3 copy of the transformed points B^T (o - o_bar)
-                               (one scale per subspace; distances in the N_s*s transformed
-                               dimensions, equal to the original ones when N_s*s = d by Lemma 1,
-                               a lower bound otherwise), then exact FP32 on a shortlist */
+#define TACO_PREC_FP8 2     /* re-rank with an FP8-e4m3 copy of the points, then exact FP32 on a
+                               shortlist: of the transformed points B^T (o - o_bar) with one
+                               scale per subspace when N_s*s = d (distances preserved, Lemma 1),
+                               else of the centred points o - o_bar with one scale per block of
+                               16 dimensions */
 
 /* Row copies an index keeps besides the FP32 rows (bit mask, the keep_rows arguments). */
 #define TACO_ROWS_BF16 1    /* BF16 copy of D, [n][d_pad] */
-#define TACO_ROWS_FP8 2     /* FP8-e4m3 copy of B^T (o - o_bar), [n][N_s*s rounded up to 16] */
+#define TACO_ROWS_FP8 2     /* FP8-e4m3 copy, [n][fp8_pitch] (see TACO_PREC_FP8) */
 
 #define TACO_SELECT_LITERAL 0 /* Alg. 5 as printed: stop at j when h[j] > R - sum_{j'>=j} h */
 #define TACO_SELECT_PROSE 1   /* Alg. 5 as described: stop when sum_{j'>=j} h[j'] > R */
@@ -110,7 +111,8 @@ typedef struct {
     int32_t n_slabs;           /* id slabs of 32768 points (collision-counter granularity) */
     int32_t cluster_size;      /* CTAs that share one query's counters */
     int32_t has_fp8;           /* FP8 rows kept (TACO_ROWS_FP8) */
-    int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s rounded up to 16) */
+    int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s, or d when N_s*s < d,
+                                  rounded up to 16) */
     int32_t has_centroid_tc;   /* the tcgen05 centroid block is available (sqrt_k <= 128 and the
                                   operands of 128 queries fit shared memory) */
     int32_t reserved;
@@ -144,8 +146,9 @@ int taco_build_index(const float* data, int64_t n, int32_t d, const taco_build_p
  *   data host or device [n][d] float32; parts host pointers as in taco_index_parts.
  *   keep_rows TACO_ROWS_* mask of the reduced-precision row copies to build.
  * Cell lists are rebuilt from codes with ids ascending in every cell. Synchronises `stream`.
- * FP8 rows: every point is transformed (Alg. 1), each subspace's scale is its largest
- * |coordinate| / 448 (the e4m3 maximum), and coordinates are rounded to nearest e4m3.
+ * FP8 rows: every point is transformed (Alg. 1) or centred (see TACO_PREC_FP8), each group's
+ * scale is its largest |coordinate| / 448 (the e4m3 maximum), and coordinates are rounded to
+ * nearest e4m3.
  */
 int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts,
                       int32_t keep_rows, void* stream, taco_index** out);
@@ -206,6 +209,31 @@ int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq
  * device status word: 0 = no device-side wait ever gave up, 1 = one did (its results are not
  * valid). Kernels never trap; they record the failure here and return. */
 int taco_device_status(const taco_index* index, int32_t* status, int32_t clear);
+
+/* Launch layout chosen by taco_autotune. */
+typedef struct {
+    int32_t slabs_per_range;   /* counter slabs (2^15 ids, 16 KB of 4-bit counters each) per id
+                                  range of the two-pass collision counting */
+    int32_t n_ranges;          /* id ranges per query */
+    int32_t lanes_per_row;     /* lanes gathering one candidate row in the re-rank (0 = auto) */
+    int32_t probe_walk;        /* -1: row-merge walk for small budgets (auto), 0: histogram only */
+    double ms_before;          /* mean ms of one search of the sample before tuning */
+    double ms_after;           /* with the chosen layout */
+    int32_t trials;            /* searches timed */
+    int32_t reserved;
+} taco_tune_result;
+
+/*
+ * taco_autotune -- time searches of a sample batch (queries: device [nq][d]; params: one
+ * struct for the batch) on `stream` over the launch layouts above (coordinate descent: counter
+ * layout, then lanes per row for the params' row kind, then probe strategy; each candidate:
+ * one untimed and `reps` timed searches) and keep the fastest for this index's later
+ * searches. The layout changes no result beyond the FP32 summation order of a candidate's
+ * distance. reps <= 0 restores the default layout. Synchronises `stream`; must not run while
+ * other searches or a server use the index. Profiling must be off (TACO_EINVAL).
+ */
+int taco_autotune(taco_index* index, const float* queries, int64_t nq, const taco_query_params* params,
+                  int32_t reps, void* stream, taco_tune_result* out);
 
 /* taco_search_debug -- taco_search_batch that also writes the intermediate results
  * selected in *debug (device pointers). Test aid; same errors as taco_search_batch. */
@@ -271,8 +299,9 @@ int taco_profile_read(taco_index* index, taco_kernel_times* out, int32_t reset);
  * batch is running, the batch is full, or its oldest request has waited max_wait_us.
  * With use_graphs, each slot replays a CUDA graph captured per (batch-size bucket, list
  * bucket); batches are padded to the bucket with copies of their first request, whose
- * results are dropped. The index must outlive the server, must not be freed or profiled
- * while the server runs, and may still be searched directly (taco_search_batch) meanwhile.
+ * results are dropped. The index must outlive the server, must not be freed, profiled or
+ * autotuned while the server runs, and may still be searched directly (taco_search_batch)
+ * meanwhile.
  */
 typedef struct taco_server taco_server;
 

@@ -100,16 +100,21 @@ void set_geometry(taco_index* ix, int64_t n, int d, int Ns, int s, int sk) {
 
 // Everything downstream of the parts: cell lists (ids ascending per cell), slab split
 // table, device copies of transform and centroids, optional BF16 rows.
-// FP8-e4m3 rows of the transformed points with one scale per subspace (largest |x'| of the
-// subspace over all points / 448): two passes of the transform over chunks of points.
+// FP8-e4m3 rows with one scale per group of dimensions (the group's largest |coordinate|
+// over all points / 448). When N_s * s = d the rows are the transformed points B^T (o - o_bar)
+// and a group is a subspace (distances are preserved, Lemma 1); otherwise the transform
+// drops dimensions, so the rows are the centred points o - o_bar and a group is a block of
+// 16 dimensions. Two passes over chunks of points: scales, then quantisation.
 int build_fp8_rows(taco_index* ix, cudaStream_t st) {
     const int64_t n = ix->n;
-    const int Dp = ix->Dp;
-    ix->dp8 = (Dp + 15) & ~15;
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t(256) << 20) / (int64_t(Dp) * 4)));
+    const bool transformed = ix->Dp == ix->d;
+    const int cols = transformed ? ix->Dp : ix->d;   // FP8 coordinates per point
+    ix->fp8_space = transformed ? 0 : 1;
+    ix->dp8 = (cols + 15) & ~15;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t(256) << 20) / (int64_t(cols) * 4)));
     float* tmp = nullptr;
     unsigned* maxbits = nullptr;
-    TACO_CUDA(cudaMalloc(&tmp, size_t(chunk) * Dp * 4));
+    TACO_CUDA(cudaMalloc(&tmp, size_t(chunk) * cols * 4));
     struct Free {
         void* a;
         void* b;
@@ -118,27 +123,34 @@ int build_fp8_rows(taco_index* ix, cudaStream_t st) {
             cudaFree(b);
         }
     } guard{tmp, nullptr};
-    TACO_CUDA(cudaMalloc(&maxbits, size_t(Dp) * 4));
+    TACO_CUDA(cudaMalloc(&maxbits, size_t(cols) * 4));
     guard.b = maxbits;
-    TACO_CUDA(cudaMemsetAsync(maxbits, 0, size_t(Dp) * 4, st));
+    TACO_CUDA(cudaMemsetAsync(maxbits, 0, size_t(cols) * 4, st));
+    auto coords = [&](int64_t c0, int64_t cn) -> cudaError_t {   // the chunk's coordinates into tmp
+        if (transformed)
+            return launch_project(ix->d_data + c0 * ix->d_pad, cn, ix->d, ix->d_pad, ix->d_obar, ix->d_B, cols, tmp, st);
+        return launch_center(ix->d_data + c0 * ix->d_pad, cn, ix->d, ix->d_pad, ix->d_obar, tmp, st);
+    };
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t cn = std::min(chunk, n - c0);
-        TACO_CUDA(launch_project(ix->d_data + c0 * ix->d_pad, cn, ix->d, ix->d_pad, ix->d_obar, ix->d_B, Dp, tmp, st));
-        TACO_CUDA(launch_absmax_cols(tmp, cn, Dp, maxbits, st));
+        TACO_CUDA(coords(c0, cn));
+        TACO_CUDA(launch_absmax_cols(tmp, cn, cols, maxbits, st));
     }
-    std::vector<unsigned> mb(Dp);
-    TACO_CUDA(cudaMemcpyAsync(mb.data(), maxbits, size_t(Dp) * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned> mb(cols);
+    TACO_CUDA(cudaMemcpyAsync(mb.data(), maxbits, size_t(cols) * 4, cudaMemcpyDeviceToHost, st));
     TACO_CUDA(cudaStreamSynchronize(st));
     std::vector<float> sc(size_t(2) * ix->dp8, 0.f);   // [scale | 1/scale]
-    for (int i = 0; i < ix->Ns; ++i) {
+    const int group = transformed ? ix->s : 16;
+    for (int g0 = 0; g0 < cols; g0 += group) {
+        const int g1 = std::min(cols, g0 + group);
         float m = 0.f;
-        for (int c = i * ix->s; c < (i + 1) * ix->s; ++c) {
+        for (int c = g0; c < g1; ++c) {
             float v;
             std::memcpy(&v, &mb[c], 4);
             m = std::max(m, v);
         }
         const float scale = m > 0.f ? m / 448.f : 1.f;
-        for (int c = i * ix->s; c < (i + 1) * ix->s; ++c) {
+        for (int c = g0; c < g1; ++c) {
             sc[c] = scale;
             sc[ix->dp8 + c] = 1.f / scale;
         }
@@ -148,8 +160,8 @@ int build_fp8_rows(taco_index* ix, cudaStream_t st) {
     TRY(dev_alloc(&ix->d_data_fp8, size_t(n) * ix->dp8, &ix->device_bytes));
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t cn = std::min(chunk, n - c0);
-        TACO_CUDA(launch_project(ix->d_data + c0 * ix->d_pad, cn, ix->d, ix->d_pad, ix->d_obar, ix->d_B, Dp, tmp, st));
-        TACO_CUDA(launch_quantize_fp8(tmp, cn, Dp, ix->dp8, ix->d_fp8_scale + ix->dp8,
+        TACO_CUDA(coords(c0, cn));
+        TACO_CUDA(launch_quantize_fp8(tmp, cn, cols, ix->dp8, ix->d_fp8_scale + ix->dp8,
                                       ix->d_data_fp8 + size_t(c0) * ix->dp8, st));
     }
     TACO_CUDA(cudaStreamSynchronize(st));   // sc dies on return; tmp is freed after the kernels
@@ -456,13 +468,14 @@ SearchLayout taco::plan_search(const taco_index* ix, int64_t chunk, int kk_max, 
     const size_t lists = size_t(chunk) * ix->cluster * kListsPerCta * kk_max * 4;
     l.ld = off; off = align_up(off + lists);
     l.li = off; off = align_up(off + lists);
-    // two-pass form: per-unit level counts and lists (a fixed arena slot of kArenaPerUnit
-    // ids per unit; units that do not fit send their query to the cluster kernel)
-    const size_t units = size_t(chunk) * ix->cluster;
+    // two-pass form: per-unit level counts and lists (a fixed arena slot of kArenaPerSlab
+    // ids per slab of the unit's range; units that do not fit send their query to the
+    // cluster kernel)
+    const size_t units = size_t(chunk) * ix->tp_ranges;
     l.uge = off; off = align_up(off + units * 16 * 4);
     l.uoff = off; off = align_up(off + units * 4);
     l.ulen = off; off = align_up(off + units * 4);
-    l.arena = off; off = align_up(off + units * kArenaPerUnit * 4);
+    l.arena = off; off = align_up(off + units * kArenaPerSlab * ix->tp_spc * 4);
     l.qflag = off; off = align_up(off + size_t(chunk) * 4);
     l.par = off; off = align_up(off + size_t(n_params) * sizeof(QueryParamsDev));
     l.q = off; off = align_up(off + (stage_queries ? size_t(chunk) * ix->d * 4 : 0));

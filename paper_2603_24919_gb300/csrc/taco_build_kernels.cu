@@ -379,6 +379,25 @@ cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, size_t count, c
     return cudaGetLastError();
 }
 
+__global__ void center_kernel(const float* __restrict__ X, int64_t rows, int d, int64_t ldx,
+                              const float* __restrict__ obar, float* __restrict__ Y) {
+    const size_t total = size_t(rows) * d;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        const size_t r = i / size_t(d);
+        const int c = int(i - r * size_t(d));
+        Y[i] = X[r * ldx + c] - obar[c];
+    }
+}
+
+cudaError_t launch_center(const float* X, int64_t rows, int d, int64_t ldx, const float* obar, float* Y,
+                          cudaStream_t st) {
+    const size_t count = size_t(rows) * d;
+    const size_t blocks = std::min<size_t>((count + 255) / 256, 152 * 64);
+    if (blocks < 1) return cudaSuccess;
+    center_kernel<<<unsigned(blocks), 256, 0, st>>>(X, rows, d, ldx, obar, Y);
+    return cudaGetLastError();
+}
+
 // Column-wise max |Y| (FP8 scales). Non-negative floats order like their bit patterns.
 __global__ void absmax_cols_kernel(const float* __restrict__ Y, int64_t rows, int Dp,
                                    unsigned* __restrict__ maxbits) {

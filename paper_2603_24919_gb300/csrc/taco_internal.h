@@ -25,8 +25,8 @@ constexpr int kSlabBytes = kSlabWords * 4;
 constexpr int64_t kQueryChunk = 16384;
 // Top lists each CTA of a query's cluster writes (one per warp of the fused kernel).
 constexpr int kListsPerCta = 16;
-// Average list entries (ids with SC >= 2) reserved per (query, id range) unit.
-constexpr size_t kArenaPerUnit = 2048;
+// List entries (ids with SC >= 2) reserved per counter slab of a (query, id range) unit.
+constexpr size_t kArenaPerSlab = 512;
 
 struct QueryParamsDev {
     int32_t k;
@@ -84,7 +84,11 @@ struct taco_index {
     int64_t n = 0;
     int d = 0, d_pad = 0, Ns = 0, s = 0, sk = 0, K = 0, Dp = 0, h1 = 0;
     int n_slabs = 0;
-    int cluster = 1, slabs_per_cta = 1;
+    int cluster = 1, slabs_per_cta = 1;   // layout of the single-pass cluster kernel
+    // Tuned launch choices (taco_autotune; defaults from configure_search):
+    int tp_spc = 1, tp_ranges = 1;        // slabs per id range of the two-pass counting, ranges
+    int tp_lanes[3] = {0, 0, 0};          // lanes per row of the re-rank per row kind (0: auto)
+    int tp_walk = -1;                     // probe by row-merge walk: -1 auto, 0 never, 1 when it fits
     int device = 0;
     // host copies of the parts
     std::vector<double> o_bar, B, eigvals, centroids;
@@ -93,9 +97,10 @@ struct taco_index {
     // device arrays
     float* d_data = nullptr;            // [n][d_pad]
     __nv_bfloat16* d_data_bf16 = nullptr;  // [n][d_pad] or null
-    uint8_t* d_data_fp8 = nullptr;      // [n][dp8] e4m3 of B^T (o - o_bar), or null
-    float* d_fp8_scale = nullptr;       // [2][dp8]: per-dimension scale (its subspace's), 1/scale
-    int dp8 = 0;                        // Dp rounded up to 16
+    uint8_t* d_data_fp8 = nullptr;      // [n][dp8] e4m3 rows (fp8_space), or null
+    float* d_fp8_scale = nullptr;       // [2][dp8]: per-dimension scale (its group's), 1/scale
+    int dp8 = 0;                        // FP8 coordinates per row rounded up to 16
+    int fp8_space = 0;                  // 0: B^T (o - o_bar) (N_s s = d), 1: o - o_bar
     uint8_t* d_cent_tc = nullptr;       // [2 N_s] BF16 centroid operands in the tcgen05 layout
     float* d_cent_tc_norm = nullptr;    // [2 N_s][N] squared norms of those BF16 centroids
     int* d_status = nullptr;            // device status word: 1 = a bounded device wait gave up
@@ -125,6 +130,9 @@ cudaError_t launch_kmeans(const float* T, int64_t n, int Dp, int Ns, int s, int 
                           uint16_t* codes_out, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, size_t count,
                            cudaStream_t st);
+// Y[r][c] = X[r][c] - obar[c] (X row pitch ldx, Y row pitch d).
+cudaError_t launch_center(const float* X, int64_t rows, int d, int64_t ldx, const float* obar, float* Y,
+                          cudaStream_t st);
 // Largest |Y[r][c]| of every column into maxbits[c] (float bits; atomicMax, caller zeroes).
 cudaError_t launch_absmax_cols(const float* Y, int64_t rows, int Dp, unsigned* maxbits,
                                cudaStream_t st);
@@ -154,10 +162,10 @@ struct SearchLaunch {
     float* lists_d;            // device [nq][cluster][kListsPerCta][kk_max]
     uint32_t* lists_i;         // device [nq][cluster][kListsPerCta][kk_max]
     // two-pass form (null unit_ge: cluster kernel for every query)
-    uint32_t* unit_ge;         // device [nq][cluster][16]
-    uint32_t* unit_off;        // device [nq][cluster]
-    uint32_t* unit_len;        // device [nq][cluster]
-    uint32_t* arena;           // device [nq][cluster][kArenaPerUnit]
+    uint32_t* unit_ge;         // device [nq][tp_ranges][16]
+    uint32_t* unit_off;        // device [nq][tp_ranges]
+    uint32_t* unit_len;        // device [nq][tp_ranges]
+    uint32_t* arena;           // device [nq][tp_ranges][kArenaPerSlab * tp_spc]
     uint32_t* qflag;           // device [nq]
     int64_t* out_ids;
     float* out_dists;

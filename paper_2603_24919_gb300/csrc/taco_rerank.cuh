@@ -51,7 +51,9 @@ struct RerankParams {
     const uint8_t* data_fp8;   // [n][dp8] e4m3 of the transformed points
     const float* fp8_scale;    // [2][dp8] per-dimension scale, then 1/scale
     const float* qt;           // [nq][Dp] transformed queries
+    const float* obar;         // [d] data mean (FP8 rows of the centred points)
     int Dp, dp8;
+    int fp8_space;             // 0: FP8 rows of B^T (o - o_bar), 1: of o - o_bar
     const uint32_t* ids;    // [Ns][n]
     const uint32_t* split;  // [Ns][K][n_slabs+1]
     const uint16_t* cells;  // [nq][Ns][K]
@@ -73,7 +75,8 @@ struct RerankParams {
     float* out_dists;
     int k_stride;
     // two-pass form: per (query, id range) unit
-    int n_ranges;           // id ranges per query (= cluster size)
+    int n_ranges;           // id ranges per query
+    uint32_t arena_per_unit;  // arena entries reserved per unit
     uint32_t* unit_ge;      // [nq][n_ranges][16] ids with SC >= j, j = 1..N_s
     uint32_t* unit_off;     // [nq][n_ranges] start of the unit's entries in the arena
     uint32_t* unit_len;     // [nq][n_ranges] entries (ids with SC >= 2)
@@ -846,7 +849,7 @@ count_select_rerank_kernel(const RerankParams P) {
 // its id ranges in turn (a (query, range) pair is a unit); a unit's collisions are counted
 // in shared memory and the unit's level counts and the compact list of its ids with
 // SC >= 2 (id relative to the range | SC << 27) go to global memory, the list into the
-// unit's fixed arena slot of kArenaPerUnit entries. Pass 2 (select_rerank_kernel): one CTA
+// unit's fixed arena slot of arena_per_unit entries. Pass 2 (select_rerank_kernel): one CTA
 // per query sums the level counts of its ranges, applies Alg. 5, keeps the list entries
 // with SC >= last_collision and re-ranks them. Queries whose threshold falls below 2, or
 // whose lists did not fit, are flagged for the cluster kernel above.
@@ -943,16 +946,16 @@ count_lists_kernel(const RerankParams P) {
             if (P.dbg_sc) debug_sc(P, q, lo, hi, words, cnt, tid);
             // the unit's entries (ids with SC >= 2) go to its fixed arena slot
             const uint32_t need = ge[2];
-            const bool fits = !overflow && need <= uint32_t(kArenaPerUnit);
+            const bool fits = !overflow && need <= P.arena_per_unit;
             if (tid == 0) {
-                P.unit_off[u] = fits ? uint32_t(u) * uint32_t(kArenaPerUnit) : 0xffffffffu;
+                P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
                 P.unit_len[u] = fits ? need : 0u;
                 if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the cluster path
             }
             if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
             if (fits) {
                 // an id's final SC is its counter; its entry tagged with that level is unique
-                uint32_t* out = P.arena + size_t(u) * kArenaPerUnit;
+                uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
                 const uint32_t nlist = s_app;   // <= kListCap: no overflow
                 for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
                     const uint32_t e = e0 + uint32_t(lane);
@@ -1017,11 +1020,15 @@ select_rerank_kernel(const RerankParams P) {
         __syncthreads();
         for (int j = tid; j < P.d_pad; j += kSrThreads) qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
         if constexpr (kFP8) {
-            // (q'_c / scale_c, scale_c^2); zero past N_s * s
+            // (x_c / scale_c, scale_c^2) of the query in the FP8 rows' space: the transformed
+            // query q' (zero past N_s * s) or the centred query q - o_bar (zero past d)
+            const int cols = P.fp8_space ? P.d : P.Dp;
             for (int j = tid; j < P.dp8; j += kSrThreads) {
                 const float sc = P.fp8_scale[j];
-                qf[2 * j] = j < P.Dp ? P.qt[q * P.Dp + j] * P.fp8_scale[P.dp8 + j] : 0.f;
-                qf[2 * j + 1] = j < P.Dp ? sc * sc : 0.f;
+                float x = 0.f;
+                if (j < cols) x = P.fp8_space ? P.queries[q * P.d + j] - P.obar[j] : P.qt[q * P.Dp + j];
+                qf[2 * j] = j < cols ? x * P.fp8_scale[P.dp8 + j] : 0.f;
+                qf[2 * j + 1] = j < cols ? sc * sc : 0.f;
             }
         }
         if (tid <= TACO_MAX_SUBSPACES + 1) s_gs[tid] = 0u;

@@ -765,6 +765,8 @@ int configure_search(taco_index* ix) {
     if (spc > ix->n_slabs) spc = ix->n_slabs;
     ix->cluster = cluster;
     ix->slabs_per_cta = spc;
+    ix->tp_spc = spc;   // the two-pass counting starts from the cluster layout
+    ix->tp_ranges = cluster;
     return TACO_OK;
 }
 
@@ -851,8 +853,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         if (int rc = prof_begin(pix, 1, st, &pb, &pe)) return rc;
         // the row-merge walk settles small budgets; the histogram kernel redoes what it flags
         // (and does everything when the debug flags are wanted or the budget needs many pops)
-        bool walk = L.dbg.probed == nullptr && ix->sk <= 128;
-        if (walk && L.params == nullptr &&
+        bool walk = L.dbg.probed == nullptr && ix->sk <= 128 && ix->tp_walk != 0;
+        if (walk && ix->tp_walk < 0 && L.params == nullptr &&
             double(L.defaults.budget) * double(K) > 0.5 * kWalkMaxPops * double(ix->n))
             walk = false;
         if (walk) {
@@ -906,6 +908,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.qt = L.qt;
         P.Dp = ix->Dp;
         P.dp8 = ix->dp8;
+        P.obar = ix->d_obar;
+        P.fp8_space = ix->fp8_space;
         P.ids = ix->d_ids;
         P.split = ix->d_split;
         P.cells = L.cells;
@@ -938,9 +942,17 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         if (L.dbg.sc) TACO_CUDA(cudaMemsetAsync(L.dbg.sc, 0, size_t(L.nq) * ix->n, st));
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
-        const int Gs = fp8 ? pick_g(ix->dp8 / 16) : G;   // lanes per row of the select pass
+        const int rk = fp8 ? 2 : (bf16 ? 1 : 0);
+        const int Gs = ix->tp_lanes[rk] ? ix->tp_lanes[rk]                    // lanes per row of
+                                        : (fp8 ? pick_g(ix->dp8 / 16) : G);   // the select pass
         const bool two_pass = L.unit_ge != nullptr;
         if (two_pass) {
+            // the two-pass range layout (tuned): tp_spc slabs of counters per range
+            P.slabs_per_cta = ix->tp_spc;
+            P.counter_words = ix->tp_spc * kSlabWords;
+            P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
+            P.n_ranges = ix->tp_ranges;
+            P.arena_per_unit = uint32_t(kArenaPerSlab) * uint32_t(ix->tp_spc);
             P.unit_ge = L.unit_ge;
             P.unit_off = L.unit_off;
             P.unit_len = L.unit_len;
@@ -975,17 +987,21 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                     : R == 4 ? launch_select_b2_r4(Gs, P, L.nq, smem2, st)
                              : launch_select_b2_r16(Gs, P, L.nq, smem2, st);
             } else if (!bf16) {
-                e = R == 1 ? launch_select_b0_r1(G, P, L.nq, smem2, st)
-                    : R == 4 ? launch_select_b0_r4(G, P, L.nq, smem2, st)
-                             : launch_select_b0_r16(G, P, L.nq, smem2, st);
+                e = R == 1 ? launch_select_b0_r1(Gs, P, L.nq, smem2, st)
+                    : R == 4 ? launch_select_b0_r4(Gs, P, L.nq, smem2, st)
+                             : launch_select_b0_r16(Gs, P, L.nq, smem2, st);
             } else {
-                e = R == 1 ? launch_select_b1_r1(G, P, L.nq, smem2, st)
-                    : R == 4 ? launch_select_b1_r4(G, P, L.nq, smem2, st)
-                             : launch_select_b1_r16(G, P, L.nq, smem2, st);
+                e = R == 1 ? launch_select_b1_r1(Gs, P, L.nq, smem2, st)
+                    : R == 4 ? launch_select_b1_r4(Gs, P, L.nq, smem2, st)
+                             : launch_select_b1_r16(Gs, P, L.nq, smem2, st);
             }
             if (e != cudaSuccess) return cuda_fail(e, "select_rerank launch", __FILE__, __LINE__);
             if (int rc = prof_end(pix, 3, st, pb, pe)) return rc;
             P.qmask = L.qflag;   // the cluster kernel below only answers flagged queries
+            P.slabs_per_cta = ix->slabs_per_cta;   // back to the cluster layout
+            P.counter_words = ix->slabs_per_cta * kSlabWords;
+            P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
+            P.n_ranges = ix->cluster;
         }
         // cluster kernel: every query (single-pass form) or the flagged ones
         const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +

@@ -93,6 +93,7 @@ struct taco_server {
     taco_server_params p = {};
     int d = 0;
     int k_out = 0;                     // row length of the staged results (= max_list)
+    size_t ws_bytes = 0;               // device workspace allocated per slot
     std::mutex mu;
     std::condition_variable cv_dispatch;   // queue or slots changed
     std::condition_variable cv_complete;   // a batch was launched
@@ -247,12 +248,24 @@ void dispatch_loop(taco_server* S) {
         while (!S->pending.empty() && int(sl.reqs.size()) < S->p.max_batch) {
             const int r = S->pending.front();
             const int kk2 = std::max(kk_max, S->reqs[r].kk);
-            if (!sl.reqs.empty() && batch_bytes(S, int(sl.reqs.size()) + 1, kk2) > size_t(S->p.slot_bytes)) break;
+            if (batch_bytes(S, int(sl.reqs.size()) + 1, kk2) > S->ws_bytes) {
+                if (!sl.reqs.empty()) break;
+                // not even alone (the index's layout grew since the server started)
+                S->pending.pop_front();
+                Request& R = S->reqs[r];
+                R.rc = fail(TACO_ECAPACITY, "a request no longer fits the slot workspace");
+                R.info.dispatch_ns = R.info.done_ns = now_ns();
+                R.state = kDone;
+                S->st.completed++;
+                S->cv_done.notify_all();
+                continue;
+            }
             sl.reqs.push_back(r);
             kk_max = kk2;
             S->pending.pop_front();
             S->reqs[r].state = kRunning;
         }
+        if (sl.reqs.empty()) continue;   // every request taken was refused
         sl.busy = true;
         sl.dispatch_ns = now_ns();
         const int nb = int(sl.reqs.size());
@@ -366,6 +379,7 @@ int taco_server_create(const taco_index* index, const taco_server_params* params
                     (long long)p.slot_bytes, p.max_list);
     }
     const size_t ws_bytes = std::min(size_t(S->p.slot_bytes), worst);
+    S->ws_bytes = ws_bytes;
     S->st.slot_bytes = int64_t(ws_bytes);
     try {
         S->reqs.resize(size_t(p.queue_capacity));

@@ -77,6 +77,13 @@ class ServerStats(C.Structure):
                 ("max_in_flight", C.c_int64), ("slot_bytes", C.c_int64)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("slabs_per_range", C.c_int32), ("n_ranges", C.c_int32),
+                ("lanes_per_row", C.c_int32), ("probe_walk", C.c_int32),
+                ("ms_before", C.c_double), ("ms_after", C.c_double), ("trials", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 NUM_KERNELS = 7
 KERNEL_NAMES = ("project", "probe_cells", "count_lists", "select_rerank", "cluster_count_select",
                 "final_merge", "centroid_tc")
@@ -112,6 +119,8 @@ SIGNATURES = {
     "taco_centroid_distances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                           C.c_void_p, C.c_void_p]),
     "taco_device_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
+    "taco_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(QueryParams),
+                                C.c_int32, C.c_void_p, C.POINTER(TuneResult)]),
     "taco_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
     "taco_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(QueryParams),
                                      C.POINTER(C.c_uint64)]),
@@ -356,6 +365,20 @@ class TacoIndex:
             self._h, _ptr(qt.contiguous()), nq, _PREC.get(probe_precision, probe_precision),
             _ptr(out), _stream_handle(stream)))
         return out
+
+    def autotune(self, queries, k, budget, rerank_target, precision="fp32", select_rule="literal",
+                 shortlist_mult=4, probe_precision="fp32", reps=3, stream=None):
+        """taco_autotune on a sample batch (CUDA queries); reps <= 0 restores the defaults.
+        Returns the chosen layout and the sample's time before and after."""
+        p = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult,
+                         probe_precision)
+        r = TuneResult()
+        q = queries if queries is not None else None
+        nq = int(q.shape[0]) if q is not None else 0
+        _check(load_library().taco_autotune(self._h, _ptr(q) if q is not None else None, nq,
+                                            C.byref(p), int(reps), _stream_handle(stream),
+                                            C.byref(r)))
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
 
     def device_status(self, clear=True):
         """The index's device status word (0 = no bounded device wait gave up)."""

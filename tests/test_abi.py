@@ -80,6 +80,7 @@ int main(void) {
   P(taco_server_params, use_graphs); P(taco_server_params, probe_precision);
   S(taco_request_info); P(taco_request_info, batch_size); P(taco_request_info, slot);
   S(taco_server_stats); P(taco_server_stats, slot_bytes);
+  S(taco_tune_result); P(taco_tune_result, ms_before); P(taco_tune_result, trials);
   return 0;
 }
 """
@@ -96,7 +97,8 @@ def test_struct_layouts_match_header():
     cmap = {"taco_build_params": T.BuildParams, "taco_query_params": T.QueryParams,
             "taco_index_parts": T.IndexParts, "taco_index_info": T.IndexInfo,
             "taco_debug_out": T.DebugOut, "taco_server_params": T.ServerParams,
-            "taco_request_info": T.RequestInfo, "taco_server_stats": T.ServerStats}
+            "taco_request_info": T.RequestInfo, "taco_server_stats": T.ServerStats,
+            "taco_tune_result": T.TuneResult}
     for key, val in want.items():
         if "." in key:
             s, f = key.split(".")

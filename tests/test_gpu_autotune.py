@@ -1,0 +1,74 @@
+"""taco_autotune: it times searches of a sample over counter layouts, lanes per row and probe
+strategies, keeps the fastest, and the searches that follow still match the FP64 oracle
+under the parity rule (the layout is exact integer work; only the FP32 summation order of a
+distance may change). reps <= 0 restores the default layout."""
+import numpy as np
+import pytest
+
+from oracle import taco_oracle as O
+from synth import budget_from_alpha, target_from_beta
+from tests.parity_util import ParityReport, compare_query, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2603_24919_gb300 import TacoIndex, build_lib  # noqa: E402
+
+build_lib.build()
+
+
+@pytest.fixture(scope="module")
+def multislab():
+    rng = np.random.default_rng(91)
+    n, d = 300_001, 32
+    centres = rng.uniform(0, 60, size=(200, d))
+    data = (centres[rng.integers(0, 200, n)] + 5 * rng.standard_normal((n, d))).astype(np.float32)
+    queries = (centres[rng.integers(0, 200, 40)] + 5 * rng.standard_normal((40, d))).astype(np.float32)
+    oix = O.create_index(data, 4, 8, 32, kmeans_iters=6, seed=9)
+    ix = TacoIndex.from_parts(data, oix.o_bar, oix.B, oix.centroids, oix.codes.astype(np.uint16),
+                              4, 8, 32, keep_bf16=True)
+    yield data, queries, oix, ix
+    ix.close()
+
+
+def _parity(ix, oix, data, queries, k, b, t):
+    q = torch.from_numpy(queries).cuda()
+    dbg = to_numpy(ix.search_debug(q, k, b, t))
+    rep = ParityReport()
+    for j, qq in enumerate(queries):
+        compare_query(rep, O.search_one(oix, data, qq, k, b, t), dbg, j, k, oix.n)
+    assert rep.excluded_queries <= 0.25 * rep.queries, rep
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_autotune_keeps_parity(multislab, precision):
+    data, queries, oix, ix = multislab
+    b, t = budget_from_alpha(0.05, oix.n), target_from_beta(0.01, oix.n)
+    q = torch.from_numpy(queries).cuda()
+    before_ids, _ = ix.search(q, 10, b, t, precision=precision, shortlist_mult=2)
+    r = ix.autotune(q, 10, b, t, precision=precision, shortlist_mult=2, reps=2)
+    assert r["trials"] >= 5 and 0 < r["ms_after"] <= r["ms_before"]
+    assert r["slabs_per_range"] in (1, 2, 4, 8) and r["n_ranges"] * r["slabs_per_range"] >= 10
+    assert r["lanes_per_row"] in (0, 4, 8, 16, 32) and r["probe_walk"] in (-1, 0)
+    _parity(ix, oix, data, queries, 10, b, t)
+    after_ids, _ = ix.search(q, 10, b, t, precision=precision, shortlist_mult=2)
+    same = (before_ids == after_ids).all(dim=1).float().mean().item()
+    assert same >= 0.9   # only near-ties of FP32 distances may reorder
+    d = ix.autotune(None, 10, b, t, reps=0)
+    assert d["slabs_per_range"] * d["n_ranges"] >= 10 and d["lanes_per_row"] == 0
+    assert ix.device_status() == 0
+
+
+def test_every_counter_layout_matches_oracle(multislab):
+    """Force each counter layout through the tuner's reset-and-trial path by tuning on
+    different samples, and check parity after each."""
+    data, queries, oix, ix = multislab
+    b, t = budget_from_alpha(0.02, oix.n), target_from_beta(0.005, oix.n)
+    q = torch.from_numpy(queries).cuda()
+    for sample in (q[:8], q[8:24], q):
+        ix.autotune(sample, 10, b, t, reps=1)
+        _parity(ix, oix, data, queries[:16], 10, b, t)
+    ix.autotune(None, 10, b, t, reps=0)

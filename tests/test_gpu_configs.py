@@ -1,0 +1,98 @@
+"""The other workload geometries at sizes the oracle answers in seconds: the 960-d power-law
+workload (N_s = 10, s = 96, halves of 48), the 96-d unit-normalised mixture (N_s = 6, s = 8)
+and the 256-d anisotropic mixture (N_s = 6, s = 8, so N_s * s = 48 < d).
+
+For each, the library builds the index (Alg. 1-3 on the GPU) and the FP64 oracle answers
+sampled queries on the exported index: the FP32 path must match it under the parity rule
+of tests/parity_util.py (probed cells, SC-scores, Alg. 5 counts and threshold, |C|, ids and
+distances). The precision forms (BF16 rows, FP8 rows, the tcgen05 centroid block) are held
+to recall@10 within 0.02 of the FP32 form against exact k-NN, with exact FP32 distances of
+the ids they return. The 96-d case also runs a batch whose k and budgets differ per query and
+checks each query against its answer alone."""
+import numpy as np
+import pytest
+
+from oracle import taco_oracle as O
+from synth import budget_from_alpha, make_workload, target_from_beta
+from tests.parity_util import ParityReport, compare_query, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2603_24919_gb300 import TacoIndex, build_lib  # noqa: E402
+
+build_lib.build()
+
+CASES = {"gist1m": 100_000, "deep10m": 400_000, "deep5m256": 300_000}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    name = request.param
+    w, data, queries = make_workload(name, n=CASES[name], nq=24)
+    ix = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=10, seed=3,
+                         keep_bf16=True, keep_fp8=True)
+    ex = ix.export()
+    oix = O.index_from_parts(ex["o_bar"], ex["B"], ex["centroids"], ex["codes"], w.n_subspaces,
+                             w.sub_dim, w.sqrt_k)
+    b = budget_from_alpha(w.alpha, len(data))
+    t = target_from_beta(w.beta, len(data))
+    yield name, w, data, queries, oix, ix, b, t
+    ix.close()
+
+
+def test_fp32_parity(case):
+    name, w, data, queries, oix, ix, b, t = case
+    q = torch.from_numpy(queries).cuda()
+    dbg = to_numpy(ix.search_debug(q, 10, b, t))
+    rep = ParityReport()
+    for j, qq in enumerate(queries):
+        tr = O.search_one(oix, data, qq, 10, b, t)
+        compare_query(rep, tr, dbg, j, 10, oix.n)
+    assert rep.excluded_queries <= 0.25 * rep.queries, rep
+    assert ix.device_status() == 0
+
+
+@pytest.mark.parametrize("form", [dict(precision="bf16", shortlist_mult=2),
+                                  dict(precision="fp8", shortlist_mult=4),
+                                  dict(precision="bf16", shortlist_mult=2, probe_precision="bf16")])
+def test_precision_forms_recall(case, form):
+    name, w, data, queries, oix, ix, b, t = case
+    q = torch.from_numpy(queries).cuda()
+    t_ids, t_d = O.brute_force_knn(data, queries, 10)
+    f_ids, _ = ix.search(q, 10, b, t)
+    p_ids, p_d = ix.search(q, 10, b, t, **form)
+    p_ids, p_d = p_ids.cpu().numpy(), p_d.cpu().numpy()
+    rf = O.recall(f_ids.cpu().numpy(), t_ids, 10)
+    rp = O.recall(p_ids, t_ids, 10)
+    assert rp >= rf - 0.02, (name, form, rp, rf)
+    ok = p_ids >= 0
+    exact = np.sqrt(((data[np.where(ok, p_ids, 0)].astype(np.float64) - queries[:, None, :]) ** 2).sum(-1))
+    assert np.allclose(p_d[ok], exact[ok], rtol=1e-5)
+    mre = O.mean_relative_error(np.where(ok, p_d, t_d), t_d)
+    assert -1e-6 <= mre < 0.5   # returned distances are FP32, the truth FP64
+    assert ix.device_status() == 0
+
+
+def test_uneven_batch_equals_alone(case):
+    name, w, data, queries, oix, ix, b, t = case
+    if name != "deep10m":
+        pytest.skip("the batched uneven form is the 96-d workload's")
+    rng = np.random.default_rng(5)
+    pq = [dict(k=int(rng.choice([1, 10, 50, 100])), budget=int(b * rng.choice([0.5, 1, 2])),
+               rerank_target=int(t * rng.choice([0.5, 1, 2])), precision="bf16",
+               shortlist_mult=2, probe_precision="bf16") for _ in range(len(queries))]
+    q = torch.from_numpy(queries).cuda()
+    ids, dists = ix.search(q, 10, b, t, per_query=pq, k_stride=100, precision="bf16",
+                           probe_precision="bf16")
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    for j, p in enumerate(pq):
+        a_ids, a_d = ix.search(q[j:j + 1], p["k"], p["budget"], p["rerank_target"],
+                               precision="bf16", shortlist_mult=2, probe_precision="bf16",
+                               k_stride=100)
+        assert np.array_equal(a_ids.cpu().numpy()[0], ids[j]), j
+        fin = np.isfinite(dists[j])
+        np.testing.assert_allclose(a_d.cpu().numpy()[0][fin], dists[j][fin], rtol=1e-5)

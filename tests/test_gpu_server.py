@@ -140,7 +140,8 @@ def test_poisson_replay_overlaps_batches(index):
 def test_admission_by_workspace_bytes_and_queue(index):
     w, queries, ix = index
     p = dict(k=10, budget=1000, rerank_target=200)
-    with TacoServer(ix, max_batch=64, slots=1, queue_capacity=64, max_list=10) as big:
+    with TacoServer(ix, max_batch=64, slots=1, queue_capacity=64, max_list=10,
+                    use_graphs=False) as big:
         full = big.stats()["slot_bytes"]
     # a workspace that holds about 8 queries: batches stay below it
     with TacoServer(ix, max_batch=64, slots=1, queue_capacity=64, max_list=10,
