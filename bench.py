@@ -317,6 +317,15 @@ def run_taco(args):
                                  "alpha": a, "beta": b, "shortlist_mult": mult}
         return total, per, kt, rec
 
+    # autotune the launch layout at the headline operating point (the FP32 form's lanes per
+    # row are tuned at its own point); the timed runs below use the tuned layout
+    tune = {}
+    for prec in ("fp32", HEADLINE):
+        a_, b_, m_ = calib[prec]["alpha"], calib[prec]["beta"], calib[prec]["shortlist_mult"]
+        tune[prec] = ix.autotune(q_dev, K, budget_from_alpha(a_, w.n), target_from_beta(b_, w.n),
+                                 shortlist_mult=m_, reps=3, **FORMS[prec])
+    log(f"[rank {rank}] autotune: {tune}")
+
     precision_stats = {}
     clocks = ClockSampler(local)
     clocks.start()
@@ -450,6 +459,7 @@ def run_taco(args):
     }
     if serving is not None:
         line["serving"] = serving
+    line["autotune"] = tune
     line["kernel_ms_per_step_fp32"] = {k: round(v["ms"] / max(args.steps, 1), 4)
                                        for k, v in kt_f.items() if v["launches"]}
     line[f"kernel_ms_per_step_{HEADLINE}"] = {k: round(v["ms"] / max(args.steps, 1), 4)

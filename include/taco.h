@@ -217,6 +217,8 @@ typedef struct {
     int32_t n_ranges;          /* id ranges per query */
     int32_t lanes_per_row;     /* lanes gathering one candidate row in the re-rank (0 = auto) */
     int32_t probe_walk;        /* -1: row-merge walk for small budgets (auto), 0: histogram only */
+    int32_t count_warps;       /* warps per CTA of the counting pass (16 or 32) */
+    int32_t reserved0;
     double ms_before;          /* mean ms of one search of the sample before tuning */
     double ms_after;           /* with the chosen layout */
     int32_t trials;            /* searches timed */
@@ -226,7 +228,7 @@ typedef struct {
 /*
  * taco_autotune -- time searches of a sample batch (queries: device [nq][d]; params: one
  * struct for the batch) on `stream` over the launch layouts above (coordinate descent: counter
- * layout, then lanes per row for the params' row kind, then probe strategy; each candidate:
+ * layout, counting CTA size, lanes per row for the params' row kind, probe strategy; each candidate:
  * one untimed and `reps` timed searches) and keep the fastest for this index's later
  * searches. The layout changes no result beyond the FP32 summation order of a candidate's
  * distance. reps <= 0 restores the default layout. Synchronises `stream`; must not run while

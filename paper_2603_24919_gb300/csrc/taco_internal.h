@@ -89,6 +89,7 @@ struct taco_index {
     int tp_spc = 1, tp_ranges = 1;        // slabs per id range of the two-pass counting, ranges
     int tp_lanes[3] = {0, 0, 0};          // lanes per row of the re-rank per row kind (0: auto)
     int tp_walk = -1;                     // probe by row-merge walk: -1 auto, 0 never, 1 when it fits
+    int tp_count_warps = 16;              // warps per CTA of the counting pass (16 or 32)
     int device = 0;
     // host copies of the parts
     std::vector<double> o_bar, B, eigvals, centroids;

@@ -281,7 +281,8 @@ __device__ __forceinline__ void gather_distances(const unsigned char* base, size
     }
 }
 
-// Exclusive scan of two values over the block; tmp holds 2 * kRrWarps entries.
+// Exclusive scan of two values over the block; tmp holds 2 * NW entries.
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ uint2 block_excl_scan2(uint32_t a, uint32_t b, uint32_t* tmp, uint2& total,
                                                   int lane, int warp) {
     uint32_t ia = a, ib = b;
@@ -290,12 +291,12 @@ __device__ __forceinline__ uint2 block_excl_scan2(uint32_t a, uint32_t b, uint32
         const uint32_t ta = __shfl_up_sync(kFull, ia, off), tb = __shfl_up_sync(kFull, ib, off);
         if (lane >= off) { ia += ta; ib += tb; }
     }
-    if (lane == 31) { tmp[warp] = ia; tmp[kRrWarps + warp] = ib; }
+    if (lane == 31) { tmp[warp] = ia; tmp[NW + warp] = ib; }
     __syncthreads();
     uint32_t pa = 0, pb = 0, sa = 0, sb = 0;
 #pragma unroll
-    for (int w = 0; w < kRrWarps; ++w) {
-        const uint32_t xa = tmp[w], xb = tmp[kRrWarps + w];
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t xa = tmp[w], xb = tmp[NW + w];
         pa += w < warp ? xa : 0u;
         pb += w < warp ? xb : 0u;
         sa += xa;
@@ -315,10 +316,11 @@ constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range |
 
 // Compact the runs (start, len) held one per thread into the staged form described below:
 // the non-empty ones in thread order. Block-wide; ends with a barrier.
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ uint2 stage_runs(uint32_t start, uint32_t len, uint32_t* rbase, uint32_t* cpre,
                                             uint32_t* s_tmp, int tid, int lane, int warp) {
     uint2 tot;
-    const uint2 ex = block_excl_scan2(len, len != 0u ? 1u : 0u, s_tmp, tot, lane, warp);
+    const uint2 ex = block_excl_scan2<NW>(len, len != 0u ? 1u : 0u, s_tmp, tot, lane, warp);
     if (len != 0u) {
         cpre[ex.y] = ex.x;
         rbase[ex.y] = start - ex.x;
@@ -333,6 +335,7 @@ __device__ __forceinline__ uint2 stage_runs(uint32_t start, uint32_t len, uint32
 // cpre[r] <= e < cpre[r + 1]; its id-array index is rbase[r] + e (uint32 arithmetic,
 // N_s * n < 2^32). cpre[nr] = total and cpre[nr + 1 .. nr + 32] = 0xffffffff. Returns
 // (total, nr). Block-wide; ends with a barrier.
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ uint2 stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
                                              int cb0, int nb, int slab_lo, int slab_hi,
                                              uint32_t* rbase, uint32_t* cpre,
@@ -351,7 +354,7 @@ __device__ __forceinline__ uint2 stage_cells(const RerankParams& P, int64_t q, c
         start = uint32_t(i) * uint32_t(P.n) + b;
         len = e - b;
     }
-    return stage_runs(start, len, rbase, cpre, s_tmp, tid, lane, warp);
+    return stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
 }
 
 // Cell whose run holds element `key` of the concatenation (largest c with cpre[c] <= key).
@@ -448,20 +451,21 @@ struct CountSmem {
 // threads return after a barrier with s_pre set by the caller.
 // Walk one staged batch (total elements in nr non-empty runs) of the range starting at id
 // lo: counters, list appends and *sm.s_listn. The concatenated runs are walked in rounds of
-// kWalkUnroll windows of 32 consecutive elements, round g by warp g mod kRrWarps, with all
+// kWalkUnroll windows of 32 consecutive elements, round g by warp g mod NW, with all
 // loads of a round in flight. Lane u finds the run holding the first element of window u
 // (binary search); in a window, lane j reads the j-th next run boundary, the boundaries
 // inside the window form a bit mask, and a lane's run is the window's first run plus the
 // mask bits at or below it (runs are non-empty, so at most 32 boundaries fall in a window).
 // Every window is executed in full: lanes past the end load a valid id-array entry and add
 // 0 to counter word 0. Warp-level; no barrier.
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, uint32_t total, uint32_t nr,
                                            const CountSmem& sm, uint64_t pol_keep, int lane, int warp) {
     const uint32_t lane_le = (2u << lane) - 1u;  // lanes 0..lane
     const uint32_t last_idx = uint32_t(P.Ns) * uint32_t(P.n) - 1u;
     constexpr uint32_t kRound = 32u * kWalkUnroll;
     const uint32_t nrounds = (total + kRound - 1) / kRound;
-    for (uint32_t g = uint32_t(warp); g < nrounds; g += kRrWarps) {   // warp-uniform
+    for (uint32_t g = uint32_t(warp); g < nrounds; g += NW) {   // warp-uniform
         const uint32_t e = g * kRound;
         const uint32_t key = min(e + 32u * uint32_t(lane % kWalkUnroll), total - 1u);
         const uint32_t cwl = uint32_t(find_cell(sm.cpre, int(nr), key));
@@ -510,6 +514,7 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
 // After the walks of a range (and a barrier): ge[2..N_s] from the list, or from the
 // counters if the list overflowed; ge[1] loses the level >= 2 events. Returns true on
 // overflow. Block-wide; ends with a barrier.
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, const CountSmem& sm,
                                               int tid, int lane, int warp) {
     const int Ns = P.Ns;
@@ -518,7 +523,7 @@ __device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, 
     if (!overflow) {
         // lanes holding the same level form one group, whose lowest lane adds its size
         const uint32_t lane_lt = (1u << lane) - 1u;
-        for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
+        for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += (NW * 32)) {
             const uint32_t e = e0 + uint32_t(lane);
             const uint32_t level = e < nlist ? sm.lst[e] >> kLevelShift : 0u;
             const unsigned grp = __match_any_sync(kFull, level);
@@ -530,7 +535,7 @@ __device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, 
         uint32_t gel[TACO_MAX_SUBSPACES];
 #pragma unroll
         for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
-        for (int w = tid; w < words; w += kRrThreads) {
+        for (int w = tid; w < words; w += (NW * 32)) {
             const uint32_t x = sm.cnt[w];
             if (x == 0u) continue;
             const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
@@ -557,6 +562,7 @@ __device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, 
     return overflow;
 }
 
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, int slab_lo, int slab_hi,
                                             int64_t lo, int words, const CountSmem& sm, uint64_t pol_keep,
                                             int tid, int lane, int warp) {
@@ -565,20 +571,21 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
     for (int bt = 0; bt < nbatch; ++bt) {
         const int cb0 = bt * kCellBatch;
         const int nb = min(kCellBatch, total_cells - cb0);
-        const uint2 st = stage_cells(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.rbase,
+        const uint2 st = stage_cells<NW>(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.rbase,
                                      sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
         if (tid == 0 && st.x) atomicAdd(&sm.ge[1], st.x);   // minus the level >= 2 events later
-        walk_batch(P, lo, st.x, st.y, sm, pol_keep, lane, warp);
+        walk_batch<NW>(P, lo, st.x, st.y, sm, pol_keep, lane, warp);
         if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
     }
     __syncthreads();
-    return finish_levels(P, words, sm, tid, lane, warp);
+    return finish_levels<NW>(P, words, sm, tid, lane, warp);
 }
 
 // Debug: the SC of every touched id of the range (untouched ids stay at the caller's zero).
+template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ void debug_sc(const RerankParams& P, int64_t q, int64_t lo, int64_t hi,
                                         int words, const uint32_t* cnt, int tid) {
-    for (int w = tid; w < words; w += kRrThreads) {
+    for (int w = tid; w < words; w += (NW * 32)) {
         const uint32_t x = cnt[w];
         if (!x) continue;
         const int64_t id0 = lo + (int64_t(w) << 3);
@@ -866,7 +873,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr size_t kCountListsExtra = size_t(2) * kCellBatch * 8 + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
                                     size_t(kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
 
-__global__ void __launch_bounds__(kRrThreads, 2)
+template <int NW>   // warps per CTA: 16 (two CTAs per SM) or 32 (one)
+__global__ void __launch_bounds__(NW * 32, NW == 16 ? 2 : 1)
 count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -878,17 +886,17 @@ count_lists_kernel(const RerankParams P) {
     uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
     uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
-    __shared__ uint32_t s_tmp[2 * kRrWarps];
+    __shared__ uint32_t s_tmp[2 * NW];
     __shared__ uint32_t s_app, s_outn;
     CountSmem csm{cnt, lst, rbase, cpre, ge, s_pre, s_tmp, &s_app};
     const int Ns = P.Ns, K = P.K;
     const int sstride = P.n_slabs + 1;
     const uint64_t pol_keep = l2_policy_keep();
-    for (int w = tid; w < P.counter_words; w += kRrThreads) cnt[w] = 0u;
+    for (int w = tid; w < P.counter_words; w += (NW * 32)) cnt[w] = 0u;
     // the split bounds of every staged cell for range r, into pairs[buf] (asynchronous)
     auto prefetch = [&](int total_cells, int r, int buf) {
         const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
-        for (int t = tid; t < total_cells; t += kRrThreads) {
+        for (int t = tid; t < total_cells; t += (NW * 32)) {
             const uint32_t qc = qcell[t];
             const uint32_t* sp = P.split + (size_t(qc >> 16) * K + (qc & 0xffffu)) * sstride;
             cp_async4(&pairs[buf * kCellBatch + t].x, sp + slo);
@@ -903,7 +911,7 @@ count_lists_kernel(const RerankParams P) {
         const int total_cells = s_pre[Ns];
         const bool staged = total_cells <= kCellBatch;   // one batch: cells kept for every range
         if (staged) {
-            for (int t = tid; t < total_cells; t += kRrThreads) {
+            for (int t = tid; t < total_cells; t += (NW * 32)) {
                 int i = 0;
                 while (t >= s_pre[i + 1]) ++i;
                 qcell[t] = (uint32_t(i) << 16) | P.cells[(q * Ns + i) * K + (t - s_pre[i])];
@@ -934,16 +942,16 @@ count_lists_kernel(const RerankParams P) {
                     start = (qcell[tid] >> 16) * uint32_t(P.n) + be.x;
                     len = be.y - be.x;
                 }
-                const uint2 st = stage_runs(start, len, rbase, cpre, s_tmp, tid, lane, warp);
+                const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
                 if (tid == 0 && st.x) atomicAdd(&ge[1], st.x);   // minus the level >= 2 events later
-                walk_batch(P, lo, st.x, st.y, csm, pol_keep, lane, warp);
+                walk_batch<NW>(P, lo, st.x, st.y, csm, pol_keep, lane, warp);
                 __syncthreads();
-                overflow = finish_levels(P, words, csm, tid, lane, warp);
+                overflow = finish_levels<NW>(P, words, csm, tid, lane, warp);
             } else {
                 __syncthreads();
-                overflow = count_phase(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
+                overflow = count_phase<NW>(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
             }
-            if (P.dbg_sc) debug_sc(P, q, lo, hi, words, cnt, tid);
+            if (P.dbg_sc) debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
             // the unit's entries (ids with SC >= 2) go to its fixed arena slot
             const uint32_t need = ge[2];
             const bool fits = !overflow && need <= P.arena_per_unit;
@@ -957,7 +965,7 @@ count_lists_kernel(const RerankParams P) {
                 // an id's final SC is its counter; its entry tagged with that level is unique
                 uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
                 const uint32_t nlist = s_app;   // <= kListCap: no overflow
-                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += kRrThreads) {
+                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += (NW * 32)) {
                     const uint32_t e = e0 + uint32_t(lane);
                     uint32_t x = 0;
                     bool take = false;
@@ -972,7 +980,7 @@ count_lists_kernel(const RerankParams P) {
             }
             __syncthreads();
             uint4* c4 = reinterpret_cast<uint4*>(cnt);
-            for (int w = tid; w < (words + 3) / 4; w += kRrThreads) c4[w] = make_uint4(0, 0, 0, 0);
+            for (int w = tid; w < (words + 3) / 4; w += (NW * 32)) c4[w] = make_uint4(0, 0, 0, 0);
             __syncthreads();
         }
     }

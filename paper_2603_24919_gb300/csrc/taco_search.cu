@@ -959,22 +959,24 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.arena = L.arena;
             P.qflag = L.qflag;
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
-            // pass 1: counting per (query, id range) unit
+            // pass 1: counting per (query, id range) unit; 512 or 1024 threads per CTA (tuned)
             const size_t smem1 = P.region_a + kCountListsExtra;
-            static thread_local size_t c1_smem = 0;
-            static thread_local int c1_blocks = 0;
-            if (c1_smem != smem1) {
-                TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(count_lists_kernel), smem1));
+            const int nw1 = ix->tp_count_warps == 32 ? 32 : 16;
+            auto k1 = nw1 == 32 ? count_lists_kernel<32> : count_lists_kernel<16>;
+            static thread_local size_t c1_smem[2] = {0, 0};
+            static thread_local int c1_blocks[2] = {0, 0};
+            const int c1 = nw1 == 32 ? 1 : 0;
+            if (c1_smem[c1] != smem1) {
+                TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(k1), smem1));
                 int per_sm = 0, sms = 0;
-                TACO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, count_lists_kernel, kRrThreads,
-                                                                        smem1));
+                TACO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, nw1 * 32, smem1));
                 TACO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
                 if (per_sm < 1) return fail(TACO_ECAPACITY, "count_lists_kernel does not fit an SM");
-                c1_blocks = per_sm * sms;
-                c1_smem = smem1;
+                c1_blocks[c1] = per_sm * sms;
+                c1_smem[c1] = smem1;
             }
             if (int rc = prof_begin(pix, 2, st, &pb, &pe)) return rc;
-            count_lists_kernel<<<unsigned(std::min<int64_t>(L.nq, c1_blocks)), kRrThreads, smem1, st>>>(P);
+            k1<<<unsigned(std::min<int64_t>(L.nq, c1_blocks[c1])), nw1 * 32, smem1, st>>>(P);
             TACO_CUDA(cudaGetLastError());
             if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results

@@ -80,7 +80,7 @@ class ServerStats(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("slabs_per_range", C.c_int32), ("n_ranges", C.c_int32),
                 ("lanes_per_row", C.c_int32), ("probe_walk", C.c_int32),
-                ("ms_before", C.c_double), ("ms_after", C.c_double), ("trials", C.c_int32),
+                ("count_warps", C.c_int32), ("reserved0", C.c_int32), ("ms_before", C.c_double), ("ms_after", C.c_double), ("trials", C.c_int32),
                 ("reserved", C.c_int32)]
 
 
@@ -378,7 +378,7 @@ class TacoIndex:
         _check(load_library().taco_autotune(self._h, _ptr(q) if q is not None else None, nq,
                                             C.byref(p), int(reps), _stream_handle(stream),
                                             C.byref(r)))
-        return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_ if not f.startswith("reserved")}
 
     def device_status(self, clear=True):
         """The index's device status word (0 = no bounded device wait gave up)."""

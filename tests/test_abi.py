@@ -80,7 +80,8 @@ int main(void) {
   P(taco_server_params, use_graphs); P(taco_server_params, probe_precision);
   S(taco_request_info); P(taco_request_info, batch_size); P(taco_request_info, slot);
   S(taco_server_stats); P(taco_server_stats, slot_bytes);
-  S(taco_tune_result); P(taco_tune_result, ms_before); P(taco_tune_result, trials);
+  S(taco_tune_result); P(taco_tune_result, count_warps); P(taco_tune_result, ms_before);
+  P(taco_tune_result, trials);
   return 0;
 }
 """

@@ -53,12 +53,14 @@ def test_autotune_keeps_parity(multislab, precision):
     assert r["trials"] >= 5 and 0 < r["ms_after"] <= r["ms_before"]
     assert r["slabs_per_range"] in (1, 2, 4, 8) and r["n_ranges"] * r["slabs_per_range"] >= 10
     assert r["lanes_per_row"] in (0, 4, 8, 16, 32) and r["probe_walk"] in (-1, 0)
+    assert r["count_warps"] in (16, 32)
     _parity(ix, oix, data, queries, 10, b, t)
     after_ids, _ = ix.search(q, 10, b, t, precision=precision, shortlist_mult=2)
     same = (before_ids == after_ids).all(dim=1).float().mean().item()
     assert same >= 0.9   # only near-ties of FP32 distances may reorder
     d = ix.autotune(None, 10, b, t, reps=0)
     assert d["slabs_per_range"] * d["n_ranges"] >= 10 and d["lanes_per_row"] == 0
+    assert d["count_warps"] == 16
     assert ix.device_status() == 0
 
 
