@@ -109,7 +109,8 @@ typedef struct {
     int32_t d_pad;             /* row pitch of the device copy of D, in elements */
     int32_t has_bf16;
     int32_t n_slabs;           /* id slabs of 32768 points (collision-counter granularity) */
-    int32_t cluster_size;      /* CTAs that share one query's counters */
+    int32_t cluster_size;      /* CTAs that share one query's counters in the cluster kernel;
+                                  0 when n is too large for a cluster (codes fallback) */
     int32_t has_fp8;           /* FP8 rows kept (TACO_ROWS_FP8) */
     int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s, or d when N_s*s < d,
                                   rounded up to 16) */
@@ -182,6 +183,7 @@ int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
  * clearing between calls. Limits: nq <= 16384 and the batch's scratch (about
  * 4*N_s*s + 2*N_s*K + 12*N_s + 128*C*kk bytes per query, C the index's cluster size and
  * kk the k of the query or its BF16 shortlist) must fit the array, else TACO_ECAPACITY.
+ * TACO_ECAPACITY also for an index whose cluster_size is 0 (n above 16 x 12 x 2^15 points).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture. All calls share the array, so calls
  * that overlap on the GPU (other streams, other threads) race: serialise them.
@@ -204,6 +206,20 @@ int taco_search_batch_noalloc(const taco_index* index, const float* queries, int
  */
 int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq,
                             int32_t probe_precision, float* out, void* stream);
+
+/*
+ * taco_index_set_option -- set a launch option of the index.
+ *   TACO_OPT_CODES_FALLBACK: value != 0 answers the queries the two-pass search cannot finish
+ *   (Alg. 5 threshold below 2, or a level list past its slot) by the codes fallback: SC-scores
+ *   recomputed from the cell codes of every probed point and bitmaps of the probed cells
+ *   (keeps a device copy of the codes, 2 bytes per point and subspace); value 0 uses the
+ *   cluster kernel (all of a query's counters in one thread-block cluster's shared memory).
+ *   An index whose n is too large for any cluster (more than 16 x 12 slabs of 2^15 points)
+ *   always uses the codes fallback (TACO_ECAPACITY for value 0).
+ * Must not run while searches or a server use the index.
+ */
+#define TACO_OPT_CODES_FALLBACK 1
+int taco_index_set_option(taco_index* index, int32_t option, int32_t value);
 
 /* taco_device_status -- synchronise the device and read (clear != 0: then reset) the index's
  * device status word: 0 = no device-side wait ever gave up, 1 = one did (its results are not

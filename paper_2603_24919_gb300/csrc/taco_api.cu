@@ -39,6 +39,7 @@ void free_device(taco_index* ix) {
     cudaFree(ix->d_cent_tc);
     cudaFree(ix->d_cent_tc_norm);
     cudaFree(ix->d_status);
+    cudaFree(ix->d_codes);
     cudaFree(ix->d_obar);
     cudaFree(ix->d_B);
     cudaFree(ix->d_cent);
@@ -100,6 +101,16 @@ void set_geometry(taco_index* ix, int64_t n, int d, int Ns, int s, int sk) {
 
 // Everything downstream of the parts: cell lists (ids ascending per cell), slab split
 // table, device copies of transform and centroids, optional BF16 rows.
+// Device copy of the cell codes, for the codes fallback of flagged queries.
+int enable_codes_fallback(taco_index* ix) {
+    if (!ix->d_codes) {
+        TRY(dev_alloc(&ix->d_codes, ix->codes.size(), &ix->device_bytes));
+        TACO_CUDA(cudaMemcpy(ix->d_codes, ix->codes.data(), ix->codes.size() * 2, cudaMemcpyHostToDevice));
+    }
+    ix->codes_fallback = true;
+    return TACO_OK;
+}
+
 // FP8-e4m3 rows with one scale per group of dimensions (the group's largest |coordinate|
 // over all points / 448). When N_s * s = d the rows are the transformed points B^T (o - o_bar)
 // and a group is a subspace (distances are preserved, Lemma 1); otherwise the transform
@@ -226,6 +237,7 @@ int finish_index(taco_index* ix, int keep_rows, cudaStream_t st) {
     }
     TACO_CUDA(cudaStreamSynchronize(st));
     TRY(build_centroid_tc(ix));
+    if (ix->cluster == 0) TRY(enable_codes_fallback(ix));   // no cluster layout fits this n
     TACO_CUDA(cudaStreamSynchronize(st));  // host vectors above die on return
     return TACO_OK;
 }
@@ -477,6 +489,7 @@ SearchLayout taco::plan_search(const taco_index* ix, int64_t chunk, int kk_max, 
     l.ulen = off; off = align_up(off + units * 4);
     l.arena = off; off = align_up(off + units * kArenaPerSlab * ix->tp_spc * 4);
     l.qflag = off; off = align_up(off + size_t(chunk) * 4);
+    l.qlast = off; off = align_up(off + size_t(chunk) * 4);
     l.par = off; off = align_up(off + size_t(n_params) * sizeof(QueryParamsDev));
     l.q = off; off = align_up(off + (stage_queries ? size_t(chunk) * ix->d * 4 : 0));
     l.oi = off; off = align_up(off + (stage_ids ? size_t(chunk) * k_stride * 8 : 0));
@@ -498,6 +511,7 @@ void taco::bind_workspace(SearchLaunch& L, const SearchLayout& lay, char* wb) {
     L.unit_len = reinterpret_cast<uint32_t*>(wb + lay.ulen);
     L.arena = reinterpret_cast<uint32_t*>(wb + lay.arena);
     L.qflag = reinterpret_cast<uint32_t*>(wb + lay.qflag);
+    L.qlast = reinterpret_cast<int32_t*>(wb + lay.qlast);
     L.hd = reinterpret_cast<float*>(wb + lay.hd);
 }
 
@@ -729,6 +743,16 @@ int taco_centroid_distances(const taco_index* ix, const float* qt, int64_t nq, i
         return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
     TACO_CUDA(launch_centroid_dist(ix, qt, nq, probe_precision == TACO_PREC_BF16, out,
                                    static_cast<cudaStream_t>(stream)));
+    return TACO_OK;
+}
+
+int taco_index_set_option(taco_index* ix, int32_t option, int32_t value) {
+    if (!ix) return fail(TACO_EINVAL, "null index");
+    if (option != TACO_OPT_CODES_FALLBACK) return fail(TACO_EINVAL, "unknown option %d", option);
+    std::lock_guard<std::mutex> lock(ix->ws_mu);
+    if (value) return enable_codes_fallback(ix);
+    if (ix->cluster == 0) return fail(TACO_ECAPACITY, "n = %lld has no cluster layout: the codes fallback stays", (long long)ix->n);
+    ix->codes_fallback = false;
     return TACO_OK;
 }
 

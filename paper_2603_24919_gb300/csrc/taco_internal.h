@@ -90,6 +90,11 @@ struct taco_index {
     int tp_lanes[3] = {0, 0, 0};          // lanes per row of the re-rank per row kind (0: auto)
     int tp_walk = -1;                     // probe by row-merge walk: -1 auto, 0 never, 1 when it fits
     int tp_count_warps = 16;              // warps per CTA of the counting pass (16 or 32)
+    // Fallback for flagged queries: the cluster kernel (all counters of a query in one
+    // cluster's shared memory) or, when n is too large for that (cluster == 0) or when
+    // chosen (taco_index_set_option), the codes fallback of select_rerank_kernel.
+    bool codes_fallback = false;
+    uint16_t* d_codes = nullptr;          // [Ns][n] cell of every point (codes fallback)
     int device = 0;
     // host copies of the parts
     std::vector<double> o_bar, B, eigvals, centroids;
@@ -168,6 +173,7 @@ struct SearchLaunch {
     uint32_t* unit_len;        // device [nq][tp_ranges]
     uint32_t* arena;           // device [nq][tp_ranges][kArenaPerSlab * tp_spc]
     uint32_t* qflag;           // device [nq]
+    int32_t* qlast;            // device [nq] Alg. 5 threshold of flagged queries
     int64_t* out_ids;
     float* out_dists;
     int k_stride;
@@ -180,7 +186,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
 
 // Byte offsets of one launch group's device workspace (each 256-byte aligned).
 struct SearchLayout {
-    size_t qt, cells, nc, ret, ld, li, uge, uoff, ulen, arena, qflag, par, q, oi, od, hd;
+    size_t qt, cells, nc, ret, ld, li, uge, uoff, ulen, arena, qflag, qlast, par, q, oi, od, hd;
     size_t total;
 };
 // Workspace of `chunk` queries with lists of kk_max entries; `n_params` per-query parameter

@@ -72,6 +72,9 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
         return fail(TACO_ECAPACITY, "nq = %lld exceeds %lld queries per call", (long long)nq,
                     (long long)kQueryChunk);
     taco_index* ix = const_cast<taco_index*>(index);
+    if (ix->cluster == 0)
+        return fail(TACO_ECAPACITY, "n = %lld is too large for the single-pass kernel of this entry point",
+                    (long long)ix->n);
     int dev = 0;
     TACO_CUDA(cudaGetDevice(&dev));
     if (dev != ix->device) return fail(TACO_EINVAL, "current device %d is not the index's device %d", dev, ix->device);

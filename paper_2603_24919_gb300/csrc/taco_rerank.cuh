@@ -81,7 +81,10 @@ struct RerankParams {
     uint32_t* unit_off;     // [nq][n_ranges] start of the unit's entries in the arena
     uint32_t* unit_len;     // [nq][n_ranges] entries (ids with SC >= 2)
     uint32_t* arena;        // entries: id relative to the range | SC << 27
-    uint32_t* qflag;        // [nq] set when a query needs the cluster kernel
+    uint32_t* qflag;        // [nq] set when a query needs the fallback (cluster or codes)
+    int32_t* qlast;         // [nq] last_collision of Alg. 5 of every flagged query
+    const uint16_t* codes;  // [Ns][n] cell of every point (codes fallback)
+    int fb_mode;            // select_rerank_kernel: 0 two-pass pass 2, 1 codes fallback
     uint8_t* dbg_sc;
     int64_t* dbg_hist;
     int32_t* dbg_last;
@@ -1009,10 +1012,17 @@ select_rerank_kernel(const RerankParams P) {
     float* qv = reinterpret_cast<float*>(Xi + kkc);                     // d_pad
     uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);          // kSrBuf
     float* qf = reinterpret_cast<float*>(buf + kSrBuf);                 // FP8: [dp8][2]
+    // codes fallback: probed-cell bitmaps [Ns][K / 32] and one batch of cells' runs
+    uint32_t* fbm = reinterpret_cast<uint32_t*>(qf + (RK == kRowFP8 ? 2 * P.dp8 : 0));
+    uint32_t* fpre = fbm + P.Ns * ((P.K + 31) / 32);                    // [kSrThreads + 1]
+    uint32_t* fst = fpre + kSrThreads + 1;                              // [kSrThreads]
+    uint32_t* fsub = fst + kSrThreads;                                  // [kSrThreads]
+    __shared__ int s_fpre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_gs[TACO_MAX_SUBSPACES + 2];
     __shared__ int s_last;
     __shared__ uint32_t s_bufn;
     __shared__ uint32_t s_flag;
+    __shared__ uint32_t s_tmp2[2 * kSrWarps];
     const int Ns = P.Ns, nr = P.n_ranges, kk = P.kk;
     const int gid = lane / G, gl = lane % G;
     constexpr bool kFP8 = RK == kRowFP8;
@@ -1043,8 +1053,11 @@ select_rerank_kernel(const RerankParams P) {
         if (tid == 0) {
             s_bufn = 0u;
             s_flag = P.qflag[q];
+            if (P.fb_mode) s_last = P.qlast[q];
         }
         __syncthreads();
+        if (P.fb_mode && !s_flag) continue;   // the fallback answers flagged queries only
+        if (!P.fb_mode) {
         // Alg. 5 over the summed level counts of the query's ranges
         if (tid < Ns) {
             uint32_t v = 0;
@@ -1076,9 +1089,11 @@ select_rerank_kernel(const RerankParams P) {
                 s_flag = 1u;
                 P.qflag[q] = 1u;   // candidates below level 2 are not in the lists
             }
+            if (s_flag && P.qlast) P.qlast[q] = last;
         }
         __syncthreads();
-        if (s_flag) continue;   // answered by the cluster kernel
+        if (s_flag) continue;   // answered by the fallback
+        }   // !fb_mode
         const int last = s_last;
         WarpTop<R> top;
         top.init();
@@ -1108,19 +1123,101 @@ select_rerank_kernel(const RerankParams P) {
                 }
             }
         };
+        // flush the candidate buffer if a tile of kSrThreads more might not fit (block-wide)
+        auto make_room = [&]() {
+            if (s_bufn + kSrThreads > uint32_t(kSrBuf)) {
+                __syncthreads();
+                rerank_buffer(int(s_bufn));
+                __syncthreads();
+                if (tid == 0) s_bufn = 0u;
+                __syncthreads();
+            }
+        };
+        if (P.fb_mode) {
+            // codes fallback: SC(id) = #subspaces i with code_i(id) probed (Def. 6), from the
+            // cell codes and per-subspace bitmaps of the probed cells; every probed id is
+            // taken once (in the first subspace that probed it) if SC >= last; last <= 0
+            // takes every point (Alg. 5 reaching level 0)
+            if (last <= 0) {
+                for (int64_t t0 = 0; t0 < P.n; t0 += kSrThreads) {
+                    make_room();
+                    const int64_t id = t0 + tid;
+                    const bool take = id < P.n;
+                    const uint32_t at = warp_append_slot(take, &s_bufn, lane);
+                    if (take) buf[at] = uint32_t(id);
+                    __syncthreads();
+                }
+            } else {
+                const int Kw = (P.K + 31) / 32;
+                if (warp == 0) load_cell_prefix(P, q, s_fpre, lane);
+                for (int w = tid; w < Ns * Kw; w += kSrThreads) fbm[w] = 0u;
+                __syncthreads();
+                const int total_cells = s_fpre[Ns];
+                for (int t = tid; t < total_cells; t += kSrThreads) {
+                    int i = 0;
+                    while (t >= s_fpre[i + 1]) ++i;
+                    const int c = P.cells[(q * Ns + i) * P.K + (t - s_fpre[i])];
+                    atomicOr(&fbm[i * Kw + (c >> 5)], 1u << (c & 31));
+                }
+                __syncthreads();
+                const int sstride = P.n_slabs + 1;
+                for (int cb0 = 0; cb0 < total_cells; cb0 += kSrThreads) {
+                    // this batch's cells: their full id runs, prefix of their lengths
+                    uint32_t len = 0;
+                    const int g = cb0 + tid;
+                    if (g < total_cells) {
+                        int i = 0;
+                        while (g >= s_fpre[i + 1]) ++i;
+                        const int c = P.cells[(q * Ns + i) * P.K + (g - s_fpre[i])];
+                        const uint32_t* sp = P.split + (size_t(i) * P.K + c) * sstride;
+                        fst[tid] = uint32_t(i) * uint32_t(P.n) + sp[0];
+                        fsub[tid] = uint32_t(i);
+                        len = sp[P.n_slabs] - sp[0];
+                    }
+                    uint2 tot;
+                    const uint2 ex = block_excl_scan2<kSrWarps>(len, 0u, s_tmp2, tot, lane, warp);
+                    fpre[tid] = ex.x;
+                    if (tid == 0) fpre[kSrThreads] = tot.x;
+                    __syncthreads();
+                    const int nb = min(kSrThreads, total_cells - cb0);
+                    for (uint32_t e0 = 0; e0 < tot.x; e0 += kSrThreads) {
+                        make_room();
+                        const uint32_t e = e0 + uint32_t(tid);
+                        bool take = false;
+                        uint32_t id = 0;
+                        if (e < tot.x) {
+                            int lo_c = 0, hi_c = nb - 1;   // the cell holding element e
+                            while (lo_c < hi_c) {
+                                const int mid = (lo_c + hi_c + 1) >> 1;
+                                if (fpre[mid] <= e) lo_c = mid;
+                                else hi_c = mid - 1;
+                            }
+                            id = P.ids[fst[lo_c] + (e - fpre[lo_c])];
+                            const int own = int(fsub[lo_c]);
+                            int sc = 0;
+                            bool dup = false;
+                            for (int i = 0; i < Ns; ++i) {
+                                const uint32_t c = P.codes[size_t(i) * P.n + id];
+                                const bool p = (fbm[i * Kw + (c >> 5)] >> (c & 31)) & 1u;
+                                sc += p;
+                                dup |= p && i < own;
+                            }
+                            take = !dup && sc >= last;
+                        }
+                        const uint32_t at = warp_append_slot(take, &s_bufn, lane);
+                        if (take) buf[at] = id;
+                        __syncthreads();
+                    }
+                }
+            }
+        } else
         // candidates: list entries with SC >= last, range by range, in tiles of kSrThreads;
         // the buffer is re-ranked and emptied before a tile that would not fit
         for (int r = 0; r < nr; ++r) {
             const uint32_t off = P.unit_off[q * nr + r], len = P.unit_len[q * nr + r];
             const uint32_t rlo = uint32_t(int64_t(r * P.slabs_per_cta) << kSlabLog2);
             for (uint32_t t0 = 0; t0 < len; t0 += kSrThreads) {
-                if (s_bufn + kSrThreads > uint32_t(kSrBuf)) {
-                    __syncthreads();
-                    rerank_buffer(int(s_bufn));
-                    __syncthreads();
-                    if (tid == 0) s_bufn = 0u;
-                    __syncthreads();
-                }
+                make_room();
                 const uint32_t t = t0 + tid;
                 uint32_t x = 0;
                 bool take = false;
@@ -1191,8 +1288,12 @@ select_rerank_kernel(const RerankParams P) {
 template <int G, int R, int RK>
 cudaError_t launch_select_rerank_t(const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
     auto kern = select_rerank_kernel<G, R, RK>;
-    static thread_local size_t cached_smem = 0;
-    static thread_local int cached_blocks = 0;
+    // two cached shapes per instance: the two-pass form and the codes fallback
+    static thread_local size_t cached_smem_v[2] = {0, 0};
+    static thread_local int cached_blocks_v[2] = {0, 0};
+    const int slot = P.fb_mode ? 1 : 0;
+    size_t& cached_smem = cached_smem_v[slot];
+    int& cached_blocks = cached_blocks_v[slot];
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return g_launch_step = "an earlier unchecked call", e;
     if (cached_smem != smem) {

@@ -758,9 +758,15 @@ int configure_search(taco_index* ix) {
         spc = (ix->n_slabs + 15) / 16;
         cluster = (ix->n_slabs + spc - 1) / spc;
     }
-    if (spc > 12 || cluster > 16)
-        return fail(TACO_ECAPACITY, "n = %lld needs more than 16 x 12 counter slabs",
-                    (long long)ix->n);
+    if (spc > 12 || cluster > 16) {
+        // no cluster holds a query's counters: the two-pass form counts in ranges of 12
+        // slabs and flagged queries take the codes fallback
+        ix->cluster = 0;
+        ix->slabs_per_cta = 0;
+        ix->tp_spc = std::min(12, ix->n_slabs);
+        ix->tp_ranges = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
+        return TACO_OK;
+    }
     if (cluster < 1) cluster = 1;
     if (spc > ix->n_slabs) spc = ix->n_slabs;
     ix->cluster = cluster;
@@ -958,6 +964,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.unit_len = L.unit_len;
             P.arena = L.arena;
             P.qflag = L.qflag;
+            P.qlast = L.qlast;
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit; 512 or 1024 threads per CTA (tuned)
             const size_t smem1 = P.region_a + kCountListsExtra;
@@ -1005,6 +1012,35 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
             P.n_ranges = ix->cluster;
         }
+        if (two_pass && ix->codes_fallback) {
+            // codes fallback for the flagged queries: the select pass again, in fallback mode
+            P.fb_mode = 1;
+            P.codes = ix->d_codes;
+            P.slabs_per_cta = ix->tp_spc;
+            P.n_ranges = ix->tp_ranges;
+            const size_t smem3 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 + size_t(ix->d_pad) * 4 +
+                                 size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0) +
+                                 size_t(ix->Ns) * ((K + 31) / 32) * 4 + size_t(3 * kSrThreads + 1) * 4;
+            cudaError_t e;
+            if (int rc = prof_begin(pix, 4, st, &pb, &pe)) return rc;
+            if (fp8) {
+                e = R == 1 ? launch_select_b2_r1(Gs, P, L.nq, smem3, st)
+                    : R == 4 ? launch_select_b2_r4(Gs, P, L.nq, smem3, st)
+                             : launch_select_b2_r16(Gs, P, L.nq, smem3, st);
+            } else if (!bf16) {
+                e = R == 1 ? launch_select_b0_r1(Gs, P, L.nq, smem3, st)
+                    : R == 4 ? launch_select_b0_r4(Gs, P, L.nq, smem3, st)
+                             : launch_select_b0_r16(Gs, P, L.nq, smem3, st);
+            } else {
+                e = R == 1 ? launch_select_b1_r1(Gs, P, L.nq, smem3, st)
+                    : R == 4 ? launch_select_b1_r4(Gs, P, L.nq, smem3, st)
+                             : launch_select_b1_r16(Gs, P, L.nq, smem3, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "codes fallback launch", __FILE__, __LINE__);
+            if (int rc = prof_end(pix, 4, st, pb, pe)) return rc;
+            return TACO_OK;
+        }
+        if (ix->cluster == 0) return fail(TACO_ECAPACITY, "no cluster layout for n = %lld", (long long)ix->n);
         // cluster kernel: every query (single-pass form) or the flagged ones
         const size_t smem = P.region_a + size_t(ix->d_pad) * 4 + size_t(P.buf_cap) * 4 +
                             size_t(kListCap) * 4 + size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 32 * 4;

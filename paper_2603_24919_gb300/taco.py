@@ -18,6 +18,7 @@ OK = 0
 EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO, EAGAIN = -1, -2, -3, -4, -5, -6, -7
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 ROWS_BF16, ROWS_FP8 = 1, 2
+OPT_CODES_FALLBACK = 1
 SELECT_LITERAL, SELECT_PROSE = 0, 1
 MAX_SUBSPACES, MAX_SQRT_K, MAX_K = 15, 128, 512
 
@@ -119,6 +120,7 @@ SIGNATURES = {
     "taco_centroid_distances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                           C.c_void_p, C.c_void_p]),
     "taco_device_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
+    "taco_index_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "taco_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(QueryParams),
                                 C.c_int32, C.c_void_p, C.POINTER(TuneResult)]),
     "taco_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
@@ -379,6 +381,11 @@ class TacoIndex:
                                             C.byref(p), int(reps), _stream_handle(stream),
                                             C.byref(r)))
         return {f: getattr(r, f) for f, _ in TuneResult._fields_ if not f.startswith("reserved")}
+
+    def set_codes_fallback(self, enable=True):
+        """taco_index_set_option(TACO_OPT_CODES_FALLBACK): answer flagged queries from the cell
+        codes instead of the cluster kernel."""
+        _check(load_library().taco_index_set_option(self._h, OPT_CODES_FALLBACK, int(bool(enable))))
 
     def device_status(self, clear=True):
         """The index's device status word (0 = no bounded device wait gave up)."""
