@@ -33,12 +33,13 @@ def index():
     ix.close()
 
 
-def _mixed_params(n, precision, seed):
+def _mixed_params(n, precision, seed, probe_precision="fp32"):
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n):
         p = dict(k=int(rng.choice(KS)), budget=int(rng.choice([200, 1000, 3000])),
-                 rerank_target=int(rng.choice([50, 200, 1000])), precision=precision)
+                 rerank_target=int(rng.choice([50, 200, 1000])), precision=precision,
+                 probe_precision=probe_precision)
         if precision == "bf16":
             p["shortlist_mult"] = int(rng.choice([1, 2, 4]))
         out.append(p)
@@ -53,7 +54,7 @@ def _alone(ix, queries, params, k_stride):
         q = torch.from_numpy(queries[j:j + 1]).cuda()
         a_i, a_d = ix.search(q, p["k"], p["budget"], p["rerank_target"],
                              precision=p["precision"], shortlist_mult=p.get("shortlist_mult", 4),
-                             k_stride=k_stride)
+                             probe_precision=p.get("probe_precision", "fp32"), k_stride=k_stride)
         ids[j], dists[j] = a_i.cpu().numpy()[0], a_d.cpu().numpy()[0]
     return ids, dists
 
@@ -70,25 +71,30 @@ def _assert_same(ids, dists, ref_ids, ref_d):
     np.testing.assert_allclose(dists[fin], ref_d[fin], rtol=1e-5)
 
 
-@pytest.mark.parametrize("precision,use_graphs", [("fp32", True), ("bf16", True), ("fp32", False)])
-def test_results_alone_equal_results_in_the_mix(index, precision, use_graphs):
+@pytest.mark.parametrize("precision,use_graphs,probe", [("fp32", True, "fp32"), ("bf16", True, "fp32"),
+                                                        ("fp32", False, "fp32"), ("bf16", True, "bf16")])
+def test_results_alone_equal_results_in_the_mix(index, precision, use_graphs, probe):
+    """probe = "bf16": the tcgen05 centroid block (bulk copies, mbarriers, tensor memory)
+    inside the captured graphs."""
     w, queries, ix = index
     n = 240
-    params = _mixed_params(n, precision, seed=7)
+    params = _mixed_params(n, precision, seed=7, probe_precision=probe)
     k_stride = max(KS)
     ref_ids, ref_d = _alone(ix, queries, params, k_stride)
     got_ids = np.zeros_like(ref_ids)
     got_d = np.zeros_like(ref_d)
     infos = [None] * n
     with TacoServer(ix, max_batch=32, slots=3, queue_capacity=64, max_list=_max_list(params),
-                    precision=precision, max_wait_us=300, use_graphs=use_graphs) as srv:
+                    precision=precision, max_wait_us=300, use_graphs=use_graphs,
+                    probe_precision=probe) as srv:
         def client(rows):
             # each client keeps a few requests outstanding, so batches mix clients
             pend = []
             for j in rows:
                 while True:
                     try:
-                        pend.append((j, srv.submit(queries[j], **params[j])))
+                        pj = {k_: v for k_, v in params[j].items() if k_ != "probe_precision"}
+                        pend.append((j, srv.submit(queries[j], **pj)))
                         break
                     except TacoError as e:
                         assert e.code == T.EAGAIN
