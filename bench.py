@@ -263,10 +263,15 @@ def run_taco(args):
         return recall_at(ids.cpu().numpy(), truth, K), nq / (ms * 1e-3), ms
 
     # ---- calibration: per form, the fastest grid point meeting the recall target ------
+    # the two forms the metric compares (plain FP32, the headline BF16 form) are calibrated on
+    # the whole grid; the other precision forms at the headline's (alpha, beta), over their
+    # shortlist lengths
     calib = {}
-    for prec in FORMS:
+    for prec in ["fp32", HEADLINE] + [f for f in FORMS if f not in ("fp32", HEADLINE)]:
         best = None
         grid = [(args.alpha, args.beta)] if args.alpha else [(a, b) for a in ALPHAS for b in BETAS]
+        if prec not in ("fp32", HEADLINE):
+            grid = [(calib[HEADLINE]["alpha"], calib[HEADLINE]["beta"])]
         mults = SHORTLIST_MULTS.get(prec, [4])
         for a, b in grid:
             for mult in mults:
