@@ -375,6 +375,15 @@ int taco_server_submit(taco_server* server, const float* query, const taco_query
                        uint64_t* ticket);
 
 /*
+ * taco_server_submit_many -- queue m requests in one call (queries: host [m][d], params: host
+ * [m]; tickets: host [m] out). Takes requests in order while the queue has places, sets
+ * *accepted to how many, and returns TACO_EAGAIN if that is fewer than m (the rest were not
+ * queued). One lock acquisition and one wake-up for the whole burst.
+ */
+int taco_server_submit_many(taco_server* server, const float* queries, int64_t m,
+                            const taco_query_params* params, uint64_t* tickets, int64_t* accepted);
+
+/*
  * taco_server_wait -- wait up to timeout_us (< 0: no limit) for request `ticket`, then copy
  * its result to host buffers ids [k_stride] int64 and dists [k_stride] float32 (ascending
  * by (distance, id); -1 / +inf past min(k, |C|)) and, if info is not NULL, its timing.
@@ -391,10 +400,12 @@ int taco_server_get_stats(taco_server* server, taco_server_stats* stats);
 /*
  * taco_server_replay -- open-loop load driver over a server: submits query j (row j of the
  * host array queries [nq][d], parameters params[j]) at arrival_ns[j] nanoseconds after the
- * call starts (arrival_ns ascending), retrying on TACO_EAGAIN, while a second thread
+ * call starts (arrival_ns ascending; all requests already due go in one
+ * taco_server_submit_many burst), retrying what the queue refuses, while the calling thread
  * collects the results in order into ids / dists [nq][k_stride] and latency_ns[nq] =
  * completion time - arrival time (queueing included). Returns after every request is
- * answered, with the first error met, if any.
+ * answered, with the first error met, if any. No other thread may collect (taco_server_wait)
+ * this call's tickets.
  */
 int taco_server_replay(taco_server* server, const float* queries, int64_t nq,
                        const taco_query_params* params, const int64_t* arrival_ns,

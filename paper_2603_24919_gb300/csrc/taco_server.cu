@@ -428,33 +428,66 @@ int taco_server_create(const taco_index* index, const taco_server_params* params
     return TACO_OK;
 }
 
+namespace {
+
+// Queue requests [0, m) under the lock while places are free; returns how many.
+int64_t enqueue_locked(taco_server* S, const float* queries, int64_t m, const taco_query_params* params,
+                       uint64_t* tickets) {
+    const int64_t t = now_ns();
+    int64_t j = 0;
+    for (; j < m && !S->free_pos.empty(); ++j) {
+        const int r = S->free_pos.back();
+        S->free_pos.pop_back();
+        Request& R = S->reqs[r];
+        R.ticket = (++S->seq << kTicketShift) | uint64_t(r);
+        R.state = kQueued;
+        R.p = params[j];
+        R.kk = query_list_len(params[j]);
+        R.rc = TACO_OK;
+        R.info = taco_request_info{};
+        R.info.submit_ns = t;
+        std::memcpy(S->q_store.data() + size_t(r) * S->d, queries + size_t(j) * S->d, size_t(S->d) * 4);
+        S->pending.push_back(r);
+        tickets[j] = R.ticket;
+    }
+    S->st.submitted += j;
+    return j;
+}
+
+}  // namespace
+
 int taco_server_submit(taco_server* S, const float* query, const taco_query_params* params, uint64_t* ticket) {
     if (!S || !query || !params || !ticket) return fail(TACO_EINVAL, "null argument");
     if (int rc = check_request(S, *params)) return rc;
     std::unique_lock<std::mutex> lk(S->mu);
     if (S->stop) return fail(TACO_EINVAL, "the server is stopping");
     if (S->fatal) return fail(S->fatal, "the server stopped after a device error");
-    if (S->free_pos.empty()) {
+    if (enqueue_locked(S, query, 1, params, ticket) == 0) {
         S->st.rejected++;
         return fail(TACO_EAGAIN, "the request queue is full (%d requests held)", S->p.queue_capacity);
     }
-    const int r = S->free_pos.back();
-    S->free_pos.pop_back();
-    Request& R = S->reqs[r];
-    R.ticket = (++S->seq << kTicketShift) | uint64_t(r);
-    R.state = kQueued;
-    R.p = *params;
-    R.kk = query_list_len(*params);
-    R.rc = TACO_OK;
-    R.info = taco_request_info{};
-    R.info.submit_ns = now_ns();
-    std::memcpy(S->q_store.data() + size_t(r) * S->d, query, size_t(S->d) * 4);
-    S->pending.push_back(r);
-    S->st.submitted++;
-    *ticket = R.ticket;
     lk.unlock();
     S->cv_dispatch.notify_one();
     return TACO_OK;
+}
+
+int taco_server_submit_many(taco_server* S, const float* queries, int64_t m, const taco_query_params* params,
+                            uint64_t* tickets, int64_t* accepted) {
+    if (!S || !queries || !params || !tickets || !accepted || m < 0) return fail(TACO_EINVAL, "null argument or m < 0");
+    *accepted = 0;
+    for (int64_t j = 0; j < m; ++j)
+        if (int rc = check_request(S, params[j])) return rc;
+    if (m == 0) return TACO_OK;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->stop) return fail(TACO_EINVAL, "the server is stopping");
+    if (S->fatal) return fail(S->fatal, "the server stopped after a device error");
+    *accepted = enqueue_locked(S, queries, m, params, tickets);
+    if (*accepted < m) S->st.rejected += m - *accepted;
+    lk.unlock();
+    if (*accepted) S->cv_dispatch.notify_one();
+    return *accepted == m ? TACO_OK
+                          : fail(TACO_EAGAIN, "the request queue took %lld of %lld requests", (long long)*accepted,
+                                 (long long)m);
 }
 
 int taco_server_wait(taco_server* S, uint64_t ticket, int64_t timeout_us, int32_t k_stride, int64_t* ids,
@@ -508,55 +541,78 @@ int taco_server_replay(taco_server* S, const float* queries, int64_t nq, const t
         if (int rc = check_request(S, params[j])) return rc;
     }
     std::vector<uint64_t> tickets(size_t(nq), 0);
-    std::vector<int64_t> arrive(size_t(nq), 0);
-    std::mutex tm;
-    std::condition_variable tcv;
-    int64_t submitted = 0;
+    std::atomic<int64_t> submitted(0);
     std::atomic<int> first_rc(TACO_OK);
     const int64_t t0 = now_ns();
+    // producer: every request due by now goes in one call (a burst), the rest waits
     std::thread producer([&] {
-        for (int64_t j = 0; j < nq; ++j) {
+        int64_t j = 0;
+        while (j < nq) {
             const int64_t due = t0 + arrival_ns[j];
-            while (now_ns() < due) {
-                const int64_t left = due - now_ns();
-                if (left > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(left - 100000));
+            int64_t now = now_ns();
+            if (now < due) {
+                if (due - now > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(due - now - 100000));
+                continue;
             }
-            uint64_t tk = 0;
-            int rc;
-            while ((rc = taco_server_submit(S, queries + size_t(j) * S->d, &params[j], &tk)) == TACO_EAGAIN)
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
+            int64_t e = j + 1;
+            while (e < nq && t0 + arrival_ns[e] <= now) ++e;
+            int64_t got = 0;
+            const int rc = taco_server_submit_many(S, queries + size_t(j) * S->d, e - j, params + j,
+                                                   tickets.data() + j, &got);
+            j += got;
+            submitted.store(j, std::memory_order_release);
             {
-                std::lock_guard<std::mutex> g(tm);
-                if (rc != TACO_OK) {
-                    int z = TACO_OK;
-                    first_rc.compare_exchange_strong(z, rc);
-                    submitted = nq;   // stop the collector after what was submitted
-                    tcv.notify_all();
-                    return;
-                }
-                tickets[size_t(j)] = tk;
-                arrive[size_t(j)] = due;
-                submitted = j + 1;
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->cv_done.notify_all();   // the collector waits for submissions on this condition
             }
-            tcv.notify_all();
+            if (rc == TACO_EAGAIN) {
+                std::this_thread::sleep_for(std::chrono::microseconds(5));
+            } else if (rc != TACO_OK) {
+                int z = TACO_OK;
+                first_rc.compare_exchange_strong(z, rc);
+                break;
+            }
         }
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->cv_done.notify_all();
     });
-    for (int64_t j = 0; j < nq; ++j) {
-        uint64_t tk;
-        {
-            std::unique_lock<std::mutex> g(tm);
-            tcv.wait(g, [&] { return submitted > j; });
-            tk = tickets[size_t(j)];
+    // collector: takes every finished request in order under one lock acquisition
+    int64_t j = 0;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        while (j < nq) {
+            const int64_t sub = submitted.load(std::memory_order_acquire);
+            if (j >= sub) {
+                if (first_rc.load() != TACO_OK) break;
+                S->cv_done.wait_for(lk, std::chrono::microseconds(200));
+                continue;
+            }
+            const uint64_t tk = tickets[size_t(j)];
+            const uint64_t r = tk & ((uint64_t(1) << kTicketShift) - 1u);
+            Request& R = S->reqs[r];
+            if (R.state != kDone) {
+                S->cv_done.wait_for(lk, std::chrono::microseconds(200));
+                continue;
+            }
+            int64_t* oi = ids + size_t(j) * k_stride;
+            float* od = dists + size_t(j) * k_stride;
+            const int64_t* src_i = S->id_store.data() + r * S->k_out;
+            const float* src_d = S->d_store.data() + r * S->k_out;
+            for (int t = 0; t < k_stride; ++t) {
+                const bool in = R.rc == TACO_OK && t < R.p.k;
+                oi[t] = in ? src_i[t] : -1;
+                od[t] = in ? src_d[t] : __builtin_huge_valf();
+            }
+            latency_ns[j] = R.info.done_ns - (t0 + arrival_ns[j]);
+            if (R.rc != TACO_OK) {
+                int z = TACO_OK;
+                first_rc.compare_exchange_strong(z, R.rc);
+            }
+            R.state = kFree;
+            R.ticket = 0;
+            S->free_pos.push_back(int(r));
+            ++j;
         }
-        if (tk == 0) break;   // the producer stopped on an error
-        taco_request_info info;
-        const int rc = taco_server_wait(S, tk, -1, k_stride, ids + size_t(j) * k_stride, dists + size_t(j) * k_stride,
-                                        &info);
-        if (rc != TACO_OK) {
-            int z = TACO_OK;
-            first_rc.compare_exchange_strong(z, rc);
-        }
-        latency_ns[j] = info.done_ns - arrive[size_t(j)];
     }
     producer.join();
     const int rc = first_rc.load();

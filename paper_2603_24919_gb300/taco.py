@@ -126,6 +126,8 @@ SIGNATURES = {
     "taco_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
     "taco_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(QueryParams),
                                      C.POINTER(C.c_uint64)]),
+    "taco_server_submit_many": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_void_p, C.POINTER(C.c_int64)]),
     "taco_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.POINTER(RequestInfo)]),
     "taco_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
@@ -482,6 +484,23 @@ class TacoServer:
         t = C.c_uint64()
         _check(load_library().taco_server_submit(self._h, q.ctypes.data, C.byref(p), C.byref(t)))
         return t.value
+
+    def submit_many(self, queries, per_query):
+        """Queue a burst of host queries [m, d] with per-request parameter dicts; returns the
+        tickets of the accepted prefix (all m unless the queue filled)."""
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        m = q.shape[0]
+        arr = (QueryParams * m)()
+        for j, item in enumerate(per_query):
+            arr[j] = item if isinstance(item, QueryParams) else query_params(
+                **dict(item, probe_precision=item.get("probe_precision", self.probe_precision)))
+        tickets = np.zeros(m, dtype=np.uint64)
+        got = C.c_int64()
+        rc = load_library().taco_server_submit_many(self._h, q.ctypes.data, m, C.cast(arr, C.c_void_p),
+                                                    tickets.ctypes.data, C.byref(got))
+        if rc not in (OK, EAGAIN):
+            _check(rc)
+        return [int(t) for t in tickets[:got.value]]
 
     def wait(self, ticket, k_stride, timeout_us=-1):
         """(ids int64 [k_stride], dists float32 [k_stride], info dict) of a request."""

@@ -181,3 +181,26 @@ def test_wait_timeout_and_bad_tickets(index):
         with pytest.raises(TacoError) as err:   # precision must match the server's
             srv.submit(queries[0], 10, 1000, 200, precision="bf16")
         assert err.value.code == T.EINVAL
+
+
+def test_submit_many_takes_a_prefix_and_matches_alone(index):
+    w, queries, ix = index
+    params = _mixed_params(100, "fp32", seed=5)
+    k_stride = max(KS)
+    ref_ids, ref_d = _alone(ix, queries, params, k_stride)
+    with TacoServer(ix, max_batch=32, slots=2, queue_capacity=64, max_list=_max_list(params),
+                    max_wait_us=50) as srv:
+        tickets = srv.submit_many(queries[:100], params)
+        assert len(tickets) == 64            # the queue holds 64
+        got = {}
+        for j, t in enumerate(tickets):
+            got[j] = srv.wait(t, k_stride)[:2]
+        tickets2 = srv.submit_many(queries[64:100], params[64:100])
+        assert len(tickets2) == 36
+        for j, t in enumerate(tickets2):
+            got[64 + j] = srv.wait(t, k_stride)[:2]
+        st = srv.stats()
+    ids = np.stack([got[j][0] for j in range(100)])
+    dists = np.stack([got[j][1] for j in range(100)])
+    _assert_same(ids, dists, ref_ids, ref_d)
+    assert st["rejected"] == 36 and st["completed"] == 100
