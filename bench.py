@@ -519,7 +519,7 @@ def run_serving(ix, queries, truth, bud, tgt, mult, span_s):
                     "p99_ms": round(float(np.percentile(lat, 99)) * 1e-6, 4),
                     "recall_at_10": round(recall_at(ids[sel], truth[rows[sel]], K), 4)}
         one(500_000, True, n_req=20_000)   # warm-up: graphs for the batch buckets
-        for rate in (10_000, 100_000, 200_000, 500_000, 1_000_000):
+        for rate in (10_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000):
             out.append(one(rate, False))
         out.append(one(200_000, True))
         st = srv.stats()
