@@ -186,9 +186,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the counting kernel (its code and constants)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_24919_gb300", "csrc")
-    for name in ("taco_rerank.cuh", "taco_search.cu"):
+    for name in ("taco_rerank.cuh", "taco_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

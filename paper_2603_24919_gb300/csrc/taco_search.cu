@@ -824,6 +824,23 @@ int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent
     return TACO_OK;
 }
 
+// The select / re-rank kernel for a row kind (0 FP32, 1 BF16, 2 FP8), register-list size R
+// (1, 4, 16) and G lanes per row.
+static cudaError_t launch_select(int rk, int R, int G, const RerankParams& P, int64_t nq, size_t smem,
+                                 cudaStream_t st) {
+    if (rk == 2)
+        return R == 1 ? launch_select_b2_r1(G, P, nq, smem, st)
+               : R == 4 ? launch_select_b2_r4(G, P, nq, smem, st)
+                        : launch_select_b2_r16(G, P, nq, smem, st);
+    if (rk == 1)
+        return R == 1 ? launch_select_b1_r1(G, P, nq, smem, st)
+               : R == 4 ? launch_select_b1_r4(G, P, nq, smem, st)
+                        : launch_select_b1_r16(G, P, nq, smem, st);
+    return R == 1 ? launch_select_b0_r1(G, P, nq, smem, st)
+           : R == 4 ? launch_select_b0_r4(G, P, nq, smem, st)
+                    : launch_select_b0_r16(G, P, nq, smem, st);
+}
+
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
     taco_index* ix = const_cast<taco_index*>(L.ix);
     taco_index* pix = L.skip_profile ? nullptr : ix;   // profiling target (none: no events)
@@ -989,21 +1006,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             // pass 2: Alg. 5, candidates, re-rank, results
             const size_t smem2 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 +
                                  size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0);
-            cudaError_t e;
             if (int rc = prof_begin(pix, 3, st, &pb, &pe)) return rc;
-            if (fp8) {
-                e = R == 1 ? launch_select_b2_r1(Gs, P, L.nq, smem2, st)
-                    : R == 4 ? launch_select_b2_r4(Gs, P, L.nq, smem2, st)
-                             : launch_select_b2_r16(Gs, P, L.nq, smem2, st);
-            } else if (!bf16) {
-                e = R == 1 ? launch_select_b0_r1(Gs, P, L.nq, smem2, st)
-                    : R == 4 ? launch_select_b0_r4(Gs, P, L.nq, smem2, st)
-                             : launch_select_b0_r16(Gs, P, L.nq, smem2, st);
-            } else {
-                e = R == 1 ? launch_select_b1_r1(Gs, P, L.nq, smem2, st)
-                    : R == 4 ? launch_select_b1_r4(Gs, P, L.nq, smem2, st)
-                             : launch_select_b1_r16(Gs, P, L.nq, smem2, st);
-            }
+            const cudaError_t e = launch_select(rk, R, Gs, P, L.nq, smem2, st);
             if (e != cudaSuccess) return cuda_fail(e, "select_rerank launch", __FILE__, __LINE__);
             if (int rc = prof_end(pix, 3, st, pb, pe)) return rc;
             P.qmask = L.qflag;   // the cluster kernel below only answers flagged queries
@@ -1021,21 +1025,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             const size_t smem3 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 + size_t(ix->d_pad) * 4 +
                                  size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0) +
                                  size_t(ix->Ns) * ((K + 31) / 32) * 4 + size_t(3 * kSrThreads + 1) * 4;
-            cudaError_t e;
             if (int rc = prof_begin(pix, 4, st, &pb, &pe)) return rc;
-            if (fp8) {
-                e = R == 1 ? launch_select_b2_r1(Gs, P, L.nq, smem3, st)
-                    : R == 4 ? launch_select_b2_r4(Gs, P, L.nq, smem3, st)
-                             : launch_select_b2_r16(Gs, P, L.nq, smem3, st);
-            } else if (!bf16) {
-                e = R == 1 ? launch_select_b0_r1(Gs, P, L.nq, smem3, st)
-                    : R == 4 ? launch_select_b0_r4(Gs, P, L.nq, smem3, st)
-                             : launch_select_b0_r16(Gs, P, L.nq, smem3, st);
-            } else {
-                e = R == 1 ? launch_select_b1_r1(Gs, P, L.nq, smem3, st)
-                    : R == 4 ? launch_select_b1_r4(Gs, P, L.nq, smem3, st)
-                             : launch_select_b1_r16(Gs, P, L.nq, smem3, st);
-            }
+            const cudaError_t e = launch_select(rk, R, Gs, P, L.nq, smem3, st);
             if (e != cudaSuccess) return cuda_fail(e, "codes fallback launch", __FILE__, __LINE__);
             if (int rc = prof_end(pix, 4, st, pb, pe)) return rc;
             return TACO_OK;
