@@ -384,7 +384,7 @@ def run_taco(args):
     entries = int(dbg["collision_num"][:, 2:].sum().item())   # ids with SC >= 2 (level lists)
     shortlist = min(mult * K, 512)
     d_pad = info["d_pad"]
-    nr = info["cluster_size"]
+    nr = tune[HEADLINE]["n_ranges"]   # id ranges per query of the tuned two-pass layout
     io = nq * (w.d * 4 + K * 12)
     alg = {   # algorithmic bytes per launch (one launch = the whole batch)
         "count_lists": 4 * retrieved + 8 * ncells + 4 * entries + nq * nr * 72,
@@ -463,6 +463,10 @@ def run_taco(args):
                      "kernel": f"{dominant} ({HEADLINE} form)",
                      "algorithmic_bytes_per_launch": int(alg_bytes),
                      "launch_ms": round(launch_ms, 4),
+                     # count_lists work per query: one shared-memory counter atomic per
+                     # retrieved id, one level-list append per id reaching SC >= 2
+                     "smem_atomics_per_query": round(retrieved / nq, 1),
+                     "list_entries_per_query": round(entries / nq, 1),
                      "kernel_share": shares},
         "clocks": clk,
     }
@@ -753,7 +757,7 @@ def run_workload(args):
                       "batch_ms_p50": round(float(np.percentile(per_ms, 50)), 3),
                       "batch_ms_p99": round(float(np.percentile(per_ms, 99)), 3),
                       "autotune": {k_: tune[k_] for k_ in ("slabs_per_range", "lanes_per_row",
-                                                           "count_warps")}}
+                                                           "count_warps", "walk_unroll")}}
         log(f"[{name}] {fname}: {out[fname]}")
     serving = None
     if name == "deep5m256":

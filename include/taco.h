@@ -216,9 +216,19 @@ int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq
  *   cluster kernel (all of a query's counters in one thread-block cluster's shared memory).
  *   An index whose n is too large for any cluster (more than 16 x 12 slabs of 2^15 points)
  *   always uses the codes fallback (TACO_ECAPACITY for value 0).
+ *   TACO_OPT_SLABS_PER_RANGE: counter slabs per id range of the two-pass counting, 1 .. 12
+ *   (n_ranges follows; TACO_ECAPACITY at search time if the counters do not fit an SM).
+ *   TACO_OPT_COUNT_WARPS: warps per counting CTA, 16 or 32.
+ *   TACO_OPT_WALK_UNROLL: id loads in flight per lane in the counting walk, 8 or 16 (16 takes
+ *   effect with 16 warps only).
+ *   The last three are the choices taco_autotune makes; they change no result beyond the FP32
+ *   summation order of a distance. Other values: TACO_EINVAL.
  * Must not run while searches or a server use the index.
  */
 #define TACO_OPT_CODES_FALLBACK 1
+#define TACO_OPT_SLABS_PER_RANGE 2
+#define TACO_OPT_COUNT_WARPS 3
+#define TACO_OPT_WALK_UNROLL 4
 int taco_index_set_option(taco_index* index, int32_t option, int32_t value);
 
 /* taco_device_status -- synchronise the device and read (clear != 0: then reset) the index's
@@ -234,7 +244,7 @@ typedef struct {
     int32_t lanes_per_row;     /* lanes gathering one candidate row in the re-rank (0 = auto) */
     int32_t probe_walk;        /* -1: row-merge walk for small budgets (auto), 0: histogram only */
     int32_t count_warps;       /* warps per CTA of the counting pass (16 or 32) */
-    int32_t reserved0;
+    int32_t walk_unroll;       /* id loads in flight per lane in its walk (8, or 16 with 16 warps) */
     double ms_before;          /* mean ms of one search of the sample before tuning */
     double ms_after;           /* with the chosen layout */
     int32_t trials;            /* searches timed */
@@ -244,8 +254,9 @@ typedef struct {
 /*
  * taco_autotune -- time searches of a sample batch (queries: device [nq][d]; params: one
  * struct for the batch) on `stream` over the launch layouts above (coordinate descent: counter
- * layout, counting CTA size, lanes per row for the params' row kind, probe strategy; each candidate:
- * one untimed and `reps` timed searches) and keep the fastest for this index's later
+ * layout, counting CTA size and walk depth, lanes per row for the params' row kind, probe
+ * strategy; each candidate: one untimed and `reps` timed searches) and keep the fastest for
+ * this index's later
  * searches. The layout changes no result beyond the FP32 summation order of a candidate's
  * distance. reps <= 0 restores the default layout. Synchronises `stream`; must not run while
  * other searches or a server use the index. Profiling must be off (TACO_EINVAL).

@@ -748,8 +748,24 @@ int taco_centroid_distances(const taco_index* ix, const float* qt, int64_t nq, i
 
 int taco_index_set_option(taco_index* ix, int32_t option, int32_t value) {
     if (!ix) return fail(TACO_EINVAL, "null index");
-    if (option != TACO_OPT_CODES_FALLBACK) return fail(TACO_EINVAL, "unknown option %d", option);
     std::lock_guard<std::mutex> lock(ix->ws_mu);
+    switch (option) {
+        case TACO_OPT_CODES_FALLBACK: break;
+        case TACO_OPT_SLABS_PER_RANGE:
+            if (value < 1 || value > 12) return fail(TACO_EINVAL, "slabs per range %d not in 1..12", value);
+            ix->tp_spc = std::min<int>(value, ix->n_slabs);
+            ix->tp_ranges = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
+            return TACO_OK;
+        case TACO_OPT_COUNT_WARPS:
+            if (value != 16 && value != 32) return fail(TACO_EINVAL, "count warps %d: 16 or 32", value);
+            ix->tp_count_warps = value;
+            return TACO_OK;
+        case TACO_OPT_WALK_UNROLL:
+            if (value != 8 && value != 16) return fail(TACO_EINVAL, "walk unroll %d: 8 or 16", value);
+            ix->tp_walk_unroll = value;
+            return TACO_OK;
+        default: return fail(TACO_EINVAL, "unknown option %d", option);
+    }
     if (value) return enable_codes_fallback(ix);
     if (ix->cluster == 0) return fail(TACO_ECAPACITY, "n = %lld has no cluster layout: the codes fallback stays", (long long)ix->n);
     ix->codes_fallback = false;

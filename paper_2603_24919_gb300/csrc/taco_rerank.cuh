@@ -460,21 +460,23 @@ struct CountSmem {
 // inside the window form a bit mask, and a lane's run is the window's first run plus the
 // mask bits at or below it (runs are non-empty, so at most 32 boundaries fall in a window).
 // Every window is executed in full: lanes past the end load a valid id-array entry and add
-// 0 to counter word 0. Warp-level; no barrier.
-template <int NW = kRrWarps>   // warps of the block
+// 0 to counter word 0. WU windows per round (WU id loads in flight per lane). Warp-level; no
+// barrier.
+template <int NW = kRrWarps, int WU = kWalkUnroll>   // warps of the block, windows per round
 __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, uint32_t total, uint32_t nr,
                                            const CountSmem& sm, uint64_t pol_keep, int lane, int warp) {
+    static_assert(WU >= 1 && WU <= 32, "one lane finds the run of each window of a round");
     const uint32_t lane_le = (2u << lane) - 1u;  // lanes 0..lane
     const uint32_t last_idx = uint32_t(P.Ns) * uint32_t(P.n) - 1u;
-    constexpr uint32_t kRound = 32u * kWalkUnroll;
+    constexpr uint32_t kRound = 32u * WU;
     const uint32_t nrounds = (total + kRound - 1) / kRound;
     for (uint32_t g = uint32_t(warp); g < nrounds; g += NW) {   // warp-uniform
         const uint32_t e = g * kRound;
-        const uint32_t key = min(e + 32u * uint32_t(lane % kWalkUnroll), total - 1u);
+        const uint32_t key = min(e + 32u * uint32_t(lane % WU), total - 1u);
         const uint32_t cwl = uint32_t(find_cell(sm.cpre, int(nr), key));
-        uint32_t idv[kWalkUnroll];
+        uint32_t idv[WU];
 #pragma unroll
-        for (int u = 0; u < kWalkUnroll; ++u) {
+        for (int u = 0; u < WU; ++u) {
             const uint32_t E = e + 32u * uint32_t(u);
             const uint32_t cw = __shfl_sync(kFull, cwl, u);
             const uint32_t pb = sm.cpre[cw + 1u + uint32_t(lane)] - E;   // >= 1 inside
@@ -487,7 +489,7 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
         // all counter atomics first (independent), then the ids that reached level >= 2
         // go to the list: one reservation per round, offsets by ballot
 #pragma unroll
-        for (int u = 0; u < kWalkUnroll; ++u) {
+        for (int u = 0; u < WU; ++u) {
             const uint32_t id = idv[u];
             const bool ok = id != 0xffffffffu;
             const uint32_t sh = (id & 7u) << 2;
@@ -495,10 +497,10 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
             const uint32_t v = (old >> sh) & 15u;
             idv[u] = (ok && v != 0u) ? (id | ((v + 1u) << kLevelShift)) : 0u;
         }
-        unsigned bal[kWalkUnroll];
+        unsigned bal[WU];
         uint32_t napp = 0;
 #pragma unroll
-        for (int u = 0; u < kWalkUnroll; ++u) {
+        for (int u = 0; u < WU; ++u) {
             bal[u] = __ballot_sync(kFull, idv[u] != 0u);
             napp += __popc(bal[u]);
         }
@@ -506,12 +508,44 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
         if (lane == 0 && napp) at = atomicAdd(sm.s_listn, napp);
         at = __shfl_sync(kFull, at, 0);
 #pragma unroll
-        for (int u = 0; u < kWalkUnroll; ++u) {
+        for (int u = 0; u < WU; ++u) {
             const uint32_t a = at + __popc(bal[u] & (lane_le >> 1));
             if (idv[u] != 0u && a < uint32_t(kListCap)) sm.lst[a] = idv[u];
             at += __popc(bal[u]);
         }
     }
+}
+
+// The level list overflowed: ge[2..N_s] from the counters themselves (SWAR compare of the
+// eight nibbles of a word against each level), and ge[1] loses the level >= 2 events.
+// Block-wide over the counter words; no barrier.
+template <int NW = kRrWarps>   // warps of the block
+__device__ __forceinline__ void levels_from_counters(int Ns, int words, const CountSmem& sm, int tid, int lane) {
+    uint32_t gel[TACO_MAX_SUBSPACES];
+#pragma unroll
+    for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
+    for (int w = tid; w < words; w += (NW * 32)) {
+        const uint32_t x = sm.cnt[w];
+        if (x == 0u) continue;
+        const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
+#pragma unroll
+        for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+            if (j <= Ns) {
+                const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
+                gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
+            }
+        }
+    }
+    uint32_t events = 0;   // level >= 2 events of this warp's words
+#pragma unroll
+    for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+        if (j <= Ns) {
+            const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
+            events += v;
+            if (lane == 0 && v) atomicAdd(&sm.ge[j], v);
+        }
+    }
+    if (lane == 0 && events) atomicSub(&sm.ge[1], events);
 }
 
 // After the walks of a range (and a barrier): ge[2..N_s] from the list, or from the
@@ -520,7 +554,6 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
 template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, const CountSmem& sm,
                                               int tid, int lane, int warp) {
-    const int Ns = P.Ns;
     const uint32_t nlist = *sm.s_listn;
     const bool overflow = nlist > uint32_t(kListCap);
     if (!overflow) {
@@ -534,38 +567,15 @@ __device__ __forceinline__ bool finish_levels(const RerankParams& P, int words, 
         }
         if (tid == 0 && nlist) atomicSub(&sm.ge[1], nlist);
     } else {
-        // the list overflowed: count the levels from the counters themselves
-        uint32_t gel[TACO_MAX_SUBSPACES];
-#pragma unroll
-        for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
-        for (int w = tid; w < words; w += (NW * 32)) {
-            const uint32_t x = sm.cnt[w];
-            if (x == 0u) continue;
-            const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
-#pragma unroll
-            for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
-                if (j <= Ns) {
-                    const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
-                    gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
-                }
-            }
-        }
-        uint32_t events = 0;   // level >= 2 events of this warp's words
-#pragma unroll
-        for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
-            if (j <= Ns) {
-                const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
-                events += v;
-                if (lane == 0 && v) atomicAdd(&sm.ge[j], v);
-            }
-        }
-        if (lane == 0 && events) atomicSub(&sm.ge[1], events);
+        levels_from_counters<NW>(P.Ns, words, sm, tid, lane);
     }
     __syncthreads();
     return overflow;
 }
 
-template <int NW = kRrWarps>   // warps of the block
+// FINISH = false: return after the last walk, without a barrier and without the level
+// counts (the caller counts them); the return value is then meaningless.
+template <int NW = kRrWarps, int WU = kWalkUnroll, bool FINISH = true>
 __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, int slab_lo, int slab_hi,
                                             int64_t lo, int words, const CountSmem& sm, uint64_t pol_keep,
                                             int tid, int lane, int warp) {
@@ -577,9 +587,10 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
         const uint2 st = stage_cells<NW>(P, q, sm.s_pre, cb0, nb, slab_lo, slab_hi, sm.rbase,
                                      sm.cpre, sm.s_tmp, tid, lane, warp, pol_keep);
         if (tid == 0 && st.x) atomicAdd(&sm.ge[1], st.x);   // minus the level >= 2 events later
-        walk_batch<NW>(P, lo, st.x, st.y, sm, pol_keep, lane, warp);
+        walk_batch<NW, WU>(P, lo, st.x, st.y, sm, pol_keep, lane, warp);
         if (bt + 1 < nbatch) __syncthreads();   // staging is reused by the next batch
     }
+    if (!FINISH) return false;
     __syncthreads();
     return finish_levels<NW>(P, words, sm, tid, lane, warp);
 }
@@ -876,8 +887,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr size_t kCountListsExtra = size_t(2) * kCellBatch * 8 + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
                                     size_t(kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
 
-template <int NW>   // warps per CTA: 16 (two CTAs per SM) or 32 (one)
-__global__ void __launch_bounds__(NW * 32, NW == 16 ? 2 : 1)
+// NW warps per CTA (16: two CTAs per SM where the counters fit, 32: one); WU windows of 32
+// ids per walk round (16 loads in flight per lane: one CTA of 16 warps per SM, up to 128
+// registers a thread).
+template <int NW, int WU>
+__global__ void __launch_bounds__(NW * 32, (NW == 16 && WU <= kWalkUnroll) ? 2 : 1)
 count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -934,7 +948,6 @@ count_lists_kernel(const RerankParams P) {
                 s_app = 0u;
                 s_outn = 0u;
             }
-            bool overflow;
             if (staged) {
                 cp_async_wait_all();
                 __syncthreads();   // this range's bounds are in pairs[r & 1]
@@ -947,41 +960,48 @@ count_lists_kernel(const RerankParams P) {
                 }
                 const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
                 if (tid == 0 && st.x) atomicAdd(&ge[1], st.x);   // minus the level >= 2 events later
-                walk_batch<NW>(P, lo, st.x, st.y, csm, pol_keep, lane, warp);
-                __syncthreads();
-                overflow = finish_levels<NW>(P, words, csm, tid, lane, warp);
+                walk_batch<NW, WU>(P, lo, st.x, st.y, csm, pol_keep, lane, warp);
             } else {
                 __syncthreads();
-                overflow = count_phase<NW>(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
+                count_phase<NW, WU, false>(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
             }
+            __syncthreads();   // the range's counters and level list are final
             if (P.dbg_sc) debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
-            // the unit's entries (ids with SC >= 2) go to its fixed arena slot
+            // One pass over the level list: the level counts ge[2..N_s] (an entry tagged j is
+            // an id that reached level j) and the unit's entries into its fixed arena slot (an
+            // id's final SC is its counter; its entry tagged with that level is unique, so the
+            // slot receives ge[2] entries). Entries past the slot are dropped; the unit is then
+            // marked lost below.
+            const uint32_t nlist = s_app;
+            const bool overflow = nlist > uint32_t(kListCap);
+            if (!overflow) {
+                uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
+                const uint32_t lane_lt = (1u << lane) - 1u;
+                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += (NW * 32)) {
+                    const uint32_t e = e0 + uint32_t(lane);
+                    const uint32_t x = e < nlist ? lst[e] : 0u;
+                    const uint32_t level = x >> kLevelShift;   // >= 2 for an entry, 0 past the end
+                    // lanes holding the same level form one group, whose lowest lane adds its size
+                    const unsigned grp = __match_any_sync(kFull, level);
+                    if (level != 0u && (grp & lane_lt) == 0u) atomicAdd(&ge[level], uint32_t(__popc(grp)));
+                    const uint32_t id = x & ((1u << kLevelShift) - 1u);
+                    const bool take = level != 0u && level == ((cnt[id >> 3] >> ((id & 7u) << 2)) & 15u);
+                    const uint32_t at = warp_append_slot(take, &s_outn, lane);
+                    if (take && at < P.arena_per_unit) out[at] = x;
+                }
+                if (tid == 0 && nlist) atomicSub(&ge[1], nlist);
+            } else {
+                levels_from_counters<NW>(Ns, words, csm, tid, lane);
+            }
+            __syncthreads();   // ge and the counters are read; the counters may be cleared
             const uint32_t need = ge[2];
             const bool fits = !overflow && need <= P.arena_per_unit;
             if (tid == 0) {
                 P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
                 P.unit_len[u] = fits ? need : 0u;
-                if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the cluster path
+                if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the fallback
             }
             if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
-            if (fits) {
-                // an id's final SC is its counter; its entry tagged with that level is unique
-                uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
-                const uint32_t nlist = s_app;   // <= kListCap: no overflow
-                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += (NW * 32)) {
-                    const uint32_t e = e0 + uint32_t(lane);
-                    uint32_t x = 0;
-                    bool take = false;
-                    if (e < nlist) {
-                        x = lst[e];
-                        const uint32_t id = x & ((1u << kLevelShift) - 1u);
-                        take = (x >> kLevelShift) == ((cnt[id >> 3] >> ((id & 7u) << 2)) & 15u);
-                    }
-                    const uint32_t at = warp_append_slot(take, &s_outn, lane);
-                    if (take) out[at] = x;
-                }
-            }
-            __syncthreads();
             uint4* c4 = reinterpret_cast<uint4*>(cnt);
             for (int w = tid; w < (words + 3) / 4; w += (NW * 32)) c4[w] = make_uint4(0, 0, 0, 0);
             __syncthreads();

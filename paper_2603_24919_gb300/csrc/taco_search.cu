@@ -986,10 +986,12 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             // pass 1: counting per (query, id range) unit; 512 or 1024 threads per CTA (tuned)
             const size_t smem1 = P.region_a + kCountListsExtra;
             const int nw1 = ix->tp_count_warps == 32 ? 32 : 16;
-            auto k1 = nw1 == 32 ? count_lists_kernel<32> : count_lists_kernel<16>;
-            static thread_local size_t c1_smem[2] = {0, 0};
-            static thread_local int c1_blocks[2] = {0, 0};
-            const int c1 = nw1 == 32 ? 1 : 0;
+            // variants: 16 warps x 8 windows per walk round, 32 x 8, 16 x 16
+            const int c1 = nw1 == 32 ? 1 : (ix->tp_walk_unroll == 16 ? 2 : 0);
+            auto k1 = c1 == 1 ? count_lists_kernel<32, 8> : (c1 == 2 ? count_lists_kernel<16, 16>
+                                                                   : count_lists_kernel<16, 8>);
+            static thread_local size_t c1_smem[3] = {0, 0, 0};
+            static thread_local int c1_blocks[3] = {0, 0, 0};
             if (c1_smem[c1] != smem1) {
                 TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(k1), smem1));
                 int per_sm = 0, sms = 0;

@@ -4,7 +4,8 @@
 //     (16 KB of 4-bit counters per slab in shared memory; fewer slabs per range = more,
 //     smaller units per query and more resident CTAs; more = fewer units, longer walks),
 //   - the lanes that gather one candidate row in the select / re-rank pass (4 .. 32),
-//   - the threads of a counting CTA (512 or 1024),
+//   - the threads of a counting CTA (512 or 1024) and the depth of its walk (8 or 16 id loads
+//     in flight per lane; 16 only with 512 threads, one CTA per SM),
 //   - whether small budgets are probed by the row-merge walk or always by the histogram
 //     kernel.
 // The choices change no result beyond the summation order of a candidate's FP32 distance
@@ -21,7 +22,7 @@ using namespace taco;
 namespace {
 
 struct Choice {
-    int spc, ranges, lanes, walk, warps;
+    int spc, ranges, lanes, walk, warps, unroll;
 };
 
 void apply(taco_index* ix, const Choice& c, int rk) {
@@ -30,6 +31,7 @@ void apply(taco_index* ix, const Choice& c, int rk) {
     ix->tp_lanes[rk] = c.lanes;
     ix->tp_walk = c.walk;
     ix->tp_count_warps = c.warps;
+    ix->tp_walk_unroll = c.unroll;
 }
 
 // Mean ms of one search of the sample after one untimed search; <0 on failure.
@@ -53,11 +55,11 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
                              int32_t reps, void* stream, taco_tune_result* out) {
     if (!ix || !params || !out) return fail(TACO_EINVAL, "null argument");
     const int rk = params->precision == TACO_PREC_FP8 ? 2 : (params->precision == TACO_PREC_BF16 ? 1 : 0);
-    const Choice defaults{ix->slabs_per_cta, ix->cluster, 0, -1, 16};
+    const Choice defaults{ix->slabs_per_cta, ix->cluster, 0, -1, 16, 8};
     if (reps <= 0) {   // back to the defaults
         apply(ix, defaults, rk);
         for (int& l : ix->tp_lanes) l = 0;
-        *out = taco_tune_result{defaults.spc, defaults.ranges, 0, -1, 16, 0, 0.0, 0.0, 0, 0};
+        *out = taco_tune_result{defaults.spc, defaults.ranges, 0, -1, 16, 8, 0.0, 0.0, 0, 0};
         return TACO_OK;
     }
     if (!queries || nq < 1 || !is_device_pointer(queries)) return fail(TACO_EINVAL, "need device queries, nq >= 1");
@@ -84,7 +86,7 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
     TACO_CUDA(cudaEventCreate(&e0));
     TACO_CUDA(cudaEventCreate(&e1));
 
-    Choice cur{ix->tp_spc, ix->tp_ranges, ix->tp_lanes[rk], ix->tp_walk, ix->tp_count_warps};
+    Choice cur{ix->tp_spc, ix->tp_ranges, ix->tp_lanes[rk], ix->tp_walk, ix->tp_count_warps, ix->tp_walk_unroll};
     double ms_before = 0.0;
     if (int rc = time_search(ix, queries, nq, *params, ids, dists, reps, st, e0, e1, &ms_before)) return rc;
     double best = ms_before;
@@ -113,11 +115,13 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
             return rc;
         }
     }
-    // 1b. threads of the counting CTA (512: two CTAs per SM where they fit; 1024: one)
-    for (int warps : {16, 32}) {
-        if (warps == cur.warps) continue;
+    // 1b. threads of the counting CTA (512: two CTAs per SM where they fit; 1024: one) and
+    //     the depth of its walk (16 loads in flight per lane: one 512-thread CTA per SM)
+    for (const int2 v : {make_int2(16, 8), make_int2(32, 8), make_int2(16, 16)}) {
+        if (v.x == cur.warps && v.y == cur.unroll) continue;
         Choice c = cur;
-        c.warps = warps;
+        c.warps = v.x;
+        c.unroll = v.y;
         if (int rc = trial(c)) {
             apply(ix, cur, rk);
             return rc;
@@ -144,6 +148,6 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
         }
     }
     apply(ix, cur, rk);
-    *out = taco_tune_result{cur.spc, cur.ranges, cur.lanes, cur.walk, cur.warps, 0, ms_before, best, trials, 0};
+    *out = taco_tune_result{cur.spc, cur.ranges, cur.lanes, cur.walk, cur.warps, cur.unroll, ms_before, best, trials, 0};
     return TACO_OK;
 }

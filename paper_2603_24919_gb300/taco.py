@@ -19,6 +19,9 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO, EAGAIN = -1, -2, -3, -4, -5, -6
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 ROWS_BF16, ROWS_FP8 = 1, 2
 OPT_CODES_FALLBACK = 1
+OPT_SLABS_PER_RANGE = 2
+OPT_COUNT_WARPS = 3
+OPT_WALK_UNROLL = 4
 SELECT_LITERAL, SELECT_PROSE = 0, 1
 MAX_SUBSPACES, MAX_SQRT_K, MAX_K = 15, 128, 512
 
@@ -81,7 +84,7 @@ class ServerStats(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("slabs_per_range", C.c_int32), ("n_ranges", C.c_int32),
                 ("lanes_per_row", C.c_int32), ("probe_walk", C.c_int32),
-                ("count_warps", C.c_int32), ("reserved0", C.c_int32), ("ms_before", C.c_double), ("ms_after", C.c_double), ("trials", C.c_int32),
+                ("count_warps", C.c_int32), ("walk_unroll", C.c_int32), ("ms_before", C.c_double), ("ms_after", C.c_double), ("trials", C.c_int32),
                 ("reserved", C.c_int32)]
 
 
@@ -388,6 +391,15 @@ class TacoIndex:
         """taco_index_set_option(TACO_OPT_CODES_FALLBACK): answer flagged queries from the cell
         codes instead of the cluster kernel."""
         _check(load_library().taco_index_set_option(self._h, OPT_CODES_FALLBACK, int(bool(enable))))
+
+    def set_count_layout(self, slabs_per_range=None, count_warps=None, walk_unroll=None):
+        """taco_index_set_option for the counting layout taco_autotune chooses (slabs of
+        counters per id range, warps per counting CTA, loads in flight per lane)."""
+        lib = load_library()
+        for opt, v in ((OPT_SLABS_PER_RANGE, slabs_per_range), (OPT_COUNT_WARPS, count_warps),
+                       (OPT_WALK_UNROLL, walk_unroll)):
+            if v is not None:
+                _check(lib.taco_index_set_option(self._h, opt, int(v)))
 
     def device_status(self, clear=True):
         """The index's device status word (0 = no bounded device wait gave up)."""

@@ -80,7 +80,8 @@ int main(void) {
   P(taco_server_params, use_graphs); P(taco_server_params, probe_precision);
   S(taco_request_info); P(taco_request_info, batch_size); P(taco_request_info, slot);
   S(taco_server_stats); P(taco_server_stats, slot_bytes);
-  S(taco_tune_result); P(taco_tune_result, count_warps); P(taco_tune_result, ms_before);
+  S(taco_tune_result); P(taco_tune_result, count_warps); P(taco_tune_result, walk_unroll);
+  P(taco_tune_result, ms_before);
   P(taco_tune_result, trials);
   return 0;
 }
@@ -106,3 +107,11 @@ def test_struct_layouts_match_header():
             assert getattr(cmap[s], f).offset == int(val), key
         else:
             assert ctypes.sizeof(cmap[key]) == int(val), key
+
+
+def test_option_constants_match_header():
+    hdr = open(os.path.join(build_lib.INCLUDE, "taco.h")).read()
+    opts = dict(re.findall(r"#define TACO_(OPT_\w+) (\d+)", hdr))
+    assert set(opts) == {"OPT_CODES_FALLBACK", "OPT_SLABS_PER_RANGE", "OPT_COUNT_WARPS", "OPT_WALK_UNROLL"}
+    for name, val in opts.items():
+        assert getattr(T, name) == int(val), name

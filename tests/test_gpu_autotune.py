@@ -1,7 +1,8 @@
-"""taco_autotune: it times searches of a sample over counter layouts, lanes per row and probe
-strategies, keeps the fastest, and the searches that follow still match the FP64 oracle
-under the parity rule (the layout is exact integer work; only the FP32 summation order of a
-distance may change). reps <= 0 restores the default layout."""
+"""taco_autotune: it times searches of a sample over counter layouts, counting CTA sizes and
+walk depths, lanes per row and probe strategies, keeps the fastest, and the searches that
+follow still match the FP64 oracle under the parity rule (the layout is exact integer work;
+only the FP32 summation order of a distance may change). reps <= 0 restores the default
+layout. Every counting variant, forced through taco_index_set_option, matches the oracle."""
 import numpy as np
 import pytest
 
@@ -53,14 +54,14 @@ def test_autotune_keeps_parity(multislab, precision):
     assert r["trials"] >= 5 and 0 < r["ms_after"] <= r["ms_before"]
     assert r["slabs_per_range"] in (1, 2, 4, 8) and r["n_ranges"] * r["slabs_per_range"] >= 10
     assert r["lanes_per_row"] in (0, 4, 8, 16, 32) and r["probe_walk"] in (-1, 0)
-    assert r["count_warps"] in (16, 32)
+    assert r["count_warps"] in (16, 32) and r["walk_unroll"] in (8, 16)
     _parity(ix, oix, data, queries, 10, b, t)
     after_ids, _ = ix.search(q, 10, b, t, precision=precision, shortlist_mult=2)
     same = (before_ids == after_ids).all(dim=1).float().mean().item()
     assert same >= 0.9   # only near-ties of FP32 distances may reorder
     d = ix.autotune(None, 10, b, t, reps=0)
     assert d["slabs_per_range"] * d["n_ranges"] >= 10 and d["lanes_per_row"] == 0
-    assert d["count_warps"] == 16
+    assert d["count_warps"] == 16 and d["walk_unroll"] == 8
     assert ix.device_status() == 0
 
 
@@ -74,3 +75,28 @@ def test_every_counter_layout_matches_oracle(multislab):
         ix.autotune(sample, 10, b, t, reps=1)
         _parity(ix, oix, data, queries[:16], 10, b, t)
     ix.autotune(None, 10, b, t, reps=0)
+
+
+@pytest.mark.parametrize("spc,warps,unroll", [(4, 16, 8), (4, 32, 8), (4, 16, 16), (12, 16, 16),
+                                              (1, 16, 16), (8, 32, 16)])
+def test_forced_count_variants_match_oracle(multislab, spc, warps, unroll):
+    """Each (slabs per range, warps, walk depth) variant of the counting pass, including
+    one-slab ranges and a range wider than the index (12 > 10 slabs)."""
+    data, queries, oix, ix = multislab
+    b, t = budget_from_alpha(0.03, oix.n), target_from_beta(0.005, oix.n)
+    ix.set_count_layout(slabs_per_range=spc, count_warps=warps, walk_unroll=unroll)
+    try:
+        _parity(ix, oix, data, queries[:20], 10, b, t)
+        assert ix.device_status() == 0
+    finally:
+        ix.autotune(None, 10, b, t, reps=0)
+
+
+def test_count_layout_rejects_bad_values(multislab):
+    from paper_2603_24919_gb300 import TacoError
+    data, queries, oix, ix = multislab
+    for kw in (dict(slabs_per_range=0), dict(slabs_per_range=13), dict(count_warps=8),
+               dict(walk_unroll=12)):
+        with pytest.raises(TacoError) as err:
+            ix.set_count_layout(**kw)
+        assert err.value.code == -1
