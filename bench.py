@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--alpha", type=float, default=None, help="skip calibration (both forms)")
     ap.add_argument("--beta", type=float, default=None)
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving runs")
+    ap.add_argument("--count-layout", default=None, metavar="SLABS,WARPS,UNROLL",
+                    help="use this counting layout instead of autotuning it (profiler runs, "
+                         "whose timings mislead the tuner)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="sift1m (the headline line) or deep10m / deep5m256 / gist1m (their "
                          "own line: batched uneven form, serving form, precision form)")
@@ -331,6 +334,12 @@ def run_taco(args):
     tune = {}
     for prec in ("fp32", HEADLINE):
         a_, b_, m_ = calib[prec]["alpha"], calib[prec]["beta"], calib[prec]["shortlist_mult"]
+        if args.count_layout:
+            spc, warps, unroll = (int(x) for x in args.count_layout.split(","))
+            ix.set_count_layout(slabs_per_range=spc, count_warps=warps, walk_unroll=unroll)
+            tune[prec] = {"slabs_per_range": spc, "n_ranges": -(-info["n_slabs"] // spc),
+                          "count_warps": warps, "walk_unroll": unroll, "forced": True}
+            continue
         tune[prec] = ix.autotune(q_dev, K, budget_from_alpha(a_, w.n), target_from_beta(b_, w.n),
                                  shortlist_mult=m_, reps=3, **FORMS[prec])
     log(f"[rank {rank}] autotune: {tune}")
