@@ -200,6 +200,18 @@ __device__ __forceinline__ uint32_t ldg_keep_u32(const uint32_t* p, uint64_t pol
     asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
     return r;
 }
+// PTX shl / shr clamp a shift amount above 32 to 32, so a shift by >= 32 gives 0 (a C++
+// shift by >= 32 is undefined).
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("shr.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
 
 // Squared distance contribution of one 16-byte row chunk f. FP32 / BF16: qv is the query
 // (d_pad floats). FP8: qv holds (q'_c / scale_c, scale_c^2) pairs of the transformed query,
@@ -316,6 +328,7 @@ constexpr int kBufCap = 4096;      // candidate ids buffered per re-rank round (
 constexpr int kListCap = 4096;     // ids that reached a level >= 2 during counting
 constexpr int kWalkUnroll = 8;     // id loads in flight per lane while counting (<= 32)
 constexpr int kLevelShift = 27;    // list entry: id relative to the CTA range | level << 27
+constexpr uint32_t kPastEnd = 0x80000000u;   // walk lane past the end (relative ids < 12 * 2^15 < 2^26)
 
 // Compact the runs (start, len) held one per thread into the staged form described below:
 // the non-empty ones in thread order. Block-wide; ends with a barrier.
@@ -480,22 +493,22 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
             const uint32_t E = e + 32u * uint32_t(u);
             const uint32_t cw = __shfl_sync(kFull, cwl, u);
             const uint32_t pb = sm.cpre[cw + 1u + uint32_t(lane)] - E;   // >= 1 inside
-            const uint32_t mask = __reduce_or_sync(kFull, pb < 32u ? 1u << pb : 0u);
+            const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));   // 0 for pb >= 32
             const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
             const uint32_t x = min(sm.rbase[r] + E + uint32_t(lane), last_idx);
             const uint32_t v = ldg_keep_u32(P.ids + x, pol_keep);
-            idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : 0xffffffffu;
+            idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : kPastEnd;
         }
         // all counter atomics first (independent), then the ids that reached level >= 2
-        // go to the list: one reservation per round, offsets by ballot
+        // go to the list: one reservation per round, offsets by ballot. A lane past the end
+        // (kPastEnd) gets nibble shift 32 and word 0: it adds 0 and reads level 0.
 #pragma unroll
         for (int u = 0; u < WU; ++u) {
             const uint32_t id = idv[u];
-            const bool ok = id != 0xffffffffu;
-            const uint32_t sh = (id & 7u) << 2;
-            const uint32_t old = atomicAdd(&sm.cnt[ok ? id >> 3 : 0u], ok ? 1u << sh : 0u);
-            const uint32_t v = (old >> sh) & 15u;
-            idv[u] = (ok && v != 0u) ? (id | ((v + 1u) << kLevelShift)) : 0u;
+            const uint32_t sh = ((id << 2) & 28u) | (id >> 26);
+            const uint32_t old = atomicAdd(&sm.cnt[(id & ~kPastEnd) >> 3], shl_clamped(1u, sh));
+            const uint32_t v = shr_clamped(old, sh) & 15u;
+            idv[u] = v != 0u ? (id | ((v + 1u) << kLevelShift)) : 0u;
         }
         unsigned bal[WU];
         uint32_t napp = 0;
