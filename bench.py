@@ -545,15 +545,107 @@ def run_serving(ix, queries, truth, bud, tgt, mult, span_s):
 
 
 def cpu_baseline(ix, data, queries, w, op, seconds):
-    """The FP64 oracle's query routine (Alg. 6) on the host, over the same index (exported
-    from the library), data and queries, for a bounded sample of queries."""
-    from oracle import taco_oracle as O
+    """The FP64 oracle's query routine (Alg. 6) on the host cores, over the same index
+    (exported from the library), data and queries, for a bounded sample of queries."""
+    ex = ix.export()
+    parts = {k: ex[k] for k in ("o_bar", "B", "centroids", "codes")}
+    return cpu_baseline_parts(parts, data, queries, (w.n_subspaces, w.sub_dim, w.sqrt_k), op,
+                              seconds)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:   # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(tmpdir, geom, k, bud, tgt, start, stride, seconds, barrier, out):
+    """One process of the CPU baseline: the oracle index from the shared parts, then queries
+    start, start + stride, ... for `seconds` after every process is ready."""
+    try:
+        import numpy as np_
+        from oracle import taco_oracle as O
+        ld = lambda name: np_.load(os.path.join(tmpdir, name + ".npy"), mmap_mode="r")
+        oix = O.index_from_parts(ld("o_bar"), ld("B"), ld("centroids"), ld("codes"), *geom)
+        data, queries = ld("data"), ld("queries")
+        barrier.wait(timeout=150)
+        t0 = time.perf_counter()
+        done, j = 0, start
+        while j < len(queries) and time.perf_counter() - t0 < seconds:
+            O.search_one(oix, data, np_.asarray(queries[j]), k, bud, tgt)
+            done += 1
+            j += stride
+        out.put((start, done, time.perf_counter() - t0, None))
+    except Exception as e:   # reported to the parent, which falls back to one process
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        out.put((start, 0, 0.0, repr(e)))
+
+
+def cpu_baseline_parts(parts, data, queries, geom, op, seconds, procs=None):
+    """Time the oracle's query routine in `procs` spawned processes (default: every host core
+    this process may run on), one NumPy thread each, queries dealt round-robin; every process
+    starts its clock at a common barrier and runs for `seconds`. QPS = queries answered / the
+    longest process time. Falls back to one process if the pool cannot run."""
+    import multiprocessing as mp
+    import queue as queue_mod
+    import shutil
+    import tempfile
+
     from synth import budget_from_alpha, target_from_beta
 
-    ex = ix.export()
-    oix = O.index_from_parts(ex["o_bar"], ex["B"], ex["centroids"], ex["codes"],
-                             w.n_subspaces, w.sub_dim, w.sqrt_k)
-    bud, tgt = budget_from_alpha(op["alpha"], w.n), target_from_beta(op["beta"], w.n)
+    n = parts["codes"].shape[1]
+    bud, tgt = budget_from_alpha(op["alpha"], n), target_from_beta(op["beta"], n)
+    procs = procs or host_cores()
+    what = f"fp32 operating point alpha={op['alpha']} beta={op['beta']}, NumPy FP64"
+    tmpdir = tempfile.mkdtemp(prefix="taco_cpu_")
+    ps = []
+    try:
+        if procs > 1:
+            for name, arr in list(parts.items()) + [("data", data), ("queries", queries)]:
+                np.save(os.path.join(tmpdir, name + ".npy"), np.ascontiguousarray(arr))
+            ctx = mp.get_context("spawn")
+            barrier, out = ctx.Barrier(procs), ctx.Queue()
+            saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                    "MKL_NUM_THREADS")}
+            os.environ.update({v: "1" for v in saved})
+            try:
+                for r in range(procs):
+                    p = ctx.Process(target=_oracle_worker,
+                                    args=(tmpdir, geom, K, bud, tgt, r, procs, seconds, barrier, out),
+                                    daemon=True)
+                    p.start()
+                    ps.append(p)
+            finally:
+                for v, old in saved.items():
+                    if old is None:
+                        os.environ.pop(v, None)
+                    else:
+                        os.environ[v] = old
+            deadline = time.time() + 200 + seconds   # setup (bounded by the barrier) + timing
+            res = [out.get(timeout=max(1.0, deadline - time.time())) for _ in range(procs)]
+            errs = [r[3] for r in res if r[3]]
+            if not errs:
+                done = sum(r[1] for r in res)
+                el = max(r[2] for r in res)
+                return {"value": round(done / el, 3), "unit": "queries/s", "cores": procs,
+                        "kind": "oracle",
+                        "sample": f"{done} of {len(queries)} queries dealt round-robin to {procs} "
+                                  f"processes for {seconds:.0f} s, {what}, one thread each"}
+            log(f"cpu baseline: process pool failed ({errs[0]}); timing one process")
+    except (OSError, queue_mod.Empty, RuntimeError) as e:
+        log(f"cpu baseline: process pool failed ({e!r}); timing one process")
+    finally:
+        for p in ps:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.kill()
+        shutil.rmtree(tmpdir, ignore_errors=True)
+    from oracle import taco_oracle as O
+    oix = O.index_from_parts(parts["o_bar"], parts["B"], parts["centroids"], parts["codes"], *geom)
     t0 = time.perf_counter()
     done = 0
     while done < len(queries) and time.perf_counter() - t0 < seconds:
@@ -561,8 +653,7 @@ def cpu_baseline(ix, data, queries, w, op, seconds):
         done += 1
     el = time.perf_counter() - t0
     return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {len(queries)} queries, fp32 operating point "
-                      f"alpha={op['alpha']} beta={op['beta']}, single-threaded NumPy FP64"}
+            "sample": f"first {done} of {len(queries)} queries, {what}, single process"}
 
 
 # ------------------------------------------------------------------------ reference arm
@@ -629,11 +720,6 @@ def run_reference(args):
     value = args.steps * per_step / total
     sample = (f"{per_step} queries per step of the {len(queries)}-query batch, alpha={alpha} "
               f"beta={beta}, single-threaded NumPy FP64 oracle")
-    serving = None
-    if not args.no_serving:
-        serving = run_serving(ix, queries, truth, bud, tgt, mult, args.serve_seconds)
-    device_status = max(device_status, ix.device_status())
-
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
