@@ -560,90 +560,143 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def _oracle_worker(tmpdir, geom, k, bud, tgt, start, stride, seconds, barrier, out):
-    """One process of the CPU baseline: the oracle index from the shared parts, then queries
-    start, start + stride, ... for `seconds` after every process is ready."""
+def _oracle_worker(tmpdir, geom, k, bud, tgt, inq, out):
+    """One process of the oracle pool: builds the oracle index from the parts saved in
+    tmpdir, reports ready, then answers tasks from inq until None:
+      ("deadline", start, stride, seconds): queries start, start + stride, ... for `seconds`;
+      ("list", indices): those queries.
+    Each task reports (queries answered, seconds, error or None)."""
     try:
         import numpy as np_
         from oracle import taco_oracle as O
         ld = lambda name: np_.load(os.path.join(tmpdir, name + ".npy"), mmap_mode="r")
         oix = O.index_from_parts(ld("o_bar"), ld("B"), ld("centroids"), ld("codes"), *geom)
         data, queries = ld("data"), ld("queries")
-        barrier.wait(timeout=150)
-        t0 = time.perf_counter()
-        done, j = 0, start
-        while j < len(queries) and time.perf_counter() - t0 < seconds:
-            O.search_one(oix, data, np_.asarray(queries[j]), k, bud, tgt)
-            done += 1
-            j += stride
-        out.put((start, done, time.perf_counter() - t0, None))
-    except Exception as e:   # reported to the parent, which falls back to one process
+    except Exception as e:   # reported to the parent
+        out.put(("ready", repr(e)))
+        return
+    out.put(("ready", None))
+    while True:
+        task = inq.get()
+        if task is None:
+            return
         try:
-            barrier.abort()
-        except Exception:
-            pass
-        out.put((start, 0, 0.0, repr(e)))
+            t0 = time.perf_counter()
+            done = 0
+            if task[0] == "deadline":
+                _, j, stride, seconds = task
+                while j < len(queries) and time.perf_counter() - t0 < seconds:
+                    O.search_one(oix, data, np_.asarray(queries[j]), k, bud, tgt)
+                    done += 1
+                    j += stride
+            else:
+                for j in task[1]:
+                    O.search_one(oix, data, np_.asarray(queries[j]), k, bud, tgt)
+                    done += 1
+            out.put(("done", done, time.perf_counter() - t0, None))
+        except Exception as e:
+            out.put(("done", 0, 0.0, repr(e)))
 
 
-def cpu_baseline_parts(parts, data, queries, geom, op, seconds, procs=None):
-    """Time the oracle's query routine in `procs` spawned processes (default: every host core
-    this process may run on), one NumPy thread each, queries dealt round-robin; every process
-    starts its clock at a common barrier and runs for `seconds`. QPS = queries answered / the
-    longest process time. Falls back to one process if the pool cannot run."""
-    import multiprocessing as mp
-    import queue as queue_mod
-    import shutil
-    import tempfile
+class OraclePool:
+    """`procs` spawned processes answering queries with the FP64 oracle's query routine, one
+    NumPy thread each, over one index whose parts (and the data and queries) are shared
+    through memory-mapped files. Raises RuntimeError if a process fails or times out."""
 
-    from synth import budget_from_alpha, target_from_beta
+    def __init__(self, parts, data, queries, geom, bud, tgt, procs, setup_timeout=300.0):
+        import multiprocessing as mp
+        import tempfile
 
-    n = parts["codes"].shape[1]
-    bud, tgt = budget_from_alpha(op["alpha"], n), target_from_beta(op["beta"], n)
-    procs = procs or host_cores()
-    what = f"fp32 operating point alpha={op['alpha']} beta={op['beta']}, NumPy FP64"
-    tmpdir = tempfile.mkdtemp(prefix="taco_cpu_")
-    ps = []
-    try:
-        if procs > 1:
+        self.procs = procs
+        self.tmpdir = tempfile.mkdtemp(prefix="taco_oracle_")
+        self.ps, self.inqs = [], []
+        try:
             for name, arr in list(parts.items()) + [("data", data), ("queries", queries)]:
-                np.save(os.path.join(tmpdir, name + ".npy"), np.ascontiguousarray(arr))
+                np.save(os.path.join(self.tmpdir, name + ".npy"), np.ascontiguousarray(arr))
             ctx = mp.get_context("spawn")
-            barrier, out = ctx.Barrier(procs), ctx.Queue()
+            self.out = ctx.Queue()
             saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
                                                     "MKL_NUM_THREADS")}
             os.environ.update({v: "1" for v in saved})
             try:
-                for r in range(procs):
+                for _ in range(procs):
+                    q = ctx.Queue()
                     p = ctx.Process(target=_oracle_worker,
-                                    args=(tmpdir, geom, K, bud, tgt, r, procs, seconds, barrier, out),
-                                    daemon=True)
+                                    args=(self.tmpdir, geom, K, bud, tgt, q, self.out), daemon=True)
                     p.start()
-                    ps.append(p)
+                    self.ps.append(p)
+                    self.inqs.append(q)
             finally:
                 for v, old in saved.items():
                     if old is None:
                         os.environ.pop(v, None)
                     else:
                         os.environ[v] = old
-            deadline = time.time() + 200 + seconds   # setup (bounded by the barrier) + timing
-            res = [out.get(timeout=max(1.0, deadline - time.time())) for _ in range(procs)]
-            errs = [r[3] for r in res if r[3]]
-            if not errs:
-                done = sum(r[1] for r in res)
-                el = max(r[2] for r in res)
-                return {"value": round(done / el, 3), "unit": "queries/s", "cores": procs,
-                        "kind": "oracle",
-                        "sample": f"{done} of {len(queries)} queries dealt round-robin to {procs} "
-                                  f"processes for {seconds:.0f} s, {what}, one thread each"}
-            log(f"cpu baseline: process pool failed ({errs[0]}); timing one process")
-    except (OSError, queue_mod.Empty, RuntimeError) as e:
-        log(f"cpu baseline: process pool failed ({e!r}); timing one process")
-    finally:
-        for p in ps:
+            for _ in range(procs):
+                msg = self._get(setup_timeout)
+                if msg[1] is not None:
+                    raise RuntimeError(f"oracle process setup failed: {msg[1]}")
+        except BaseException:
+            self.close()
+            raise
+
+    def _get(self, timeout):
+        import queue as queue_mod
+        try:
+            return self.out.get(timeout=timeout)
+        except queue_mod.Empty:
+            raise RuntimeError("oracle process did not answer in time") from None
+
+    def run(self, tasks, timeout):
+        """One task per process, all dispatched at once; returns (answered, longest time)."""
+        for q, t in zip(self.inqs, tasks):
+            q.put(t)
+        res = [self._get(timeout) for _ in tasks]
+        errs = [r[3] for r in res if r[3]]
+        if errs:
+            raise RuntimeError(f"oracle process failed: {errs[0]}")
+        return sum(r[1] for r in res), max(r[2] for r in res)
+
+    def close(self):
+        import shutil
+        for q in self.inqs:
+            try:
+                q.put(None)
+            except Exception:
+                pass
+        for p in self.ps:
             p.join(timeout=5)
             if p.is_alive():
                 p.kill()
-        shutil.rmtree(tmpdir, ignore_errors=True)
+        self.ps, self.inqs = [], []
+        shutil.rmtree(self.tmpdir, ignore_errors=True)
+
+
+def cpu_baseline_parts(parts, data, queries, geom, op, seconds, procs=None):
+    """Time the oracle's query routine in `procs` spawned processes (default: every host core
+    this process may run on), queries dealt round-robin, all started together and run for
+    `seconds`. QPS = queries answered / the longest process time. Falls back to this process
+    alone if the pool cannot run."""
+    from synth import budget_from_alpha, target_from_beta
+
+    n = parts["codes"].shape[1]
+    bud, tgt = budget_from_alpha(op["alpha"], n), target_from_beta(op["beta"], n)
+    procs = procs or host_cores()
+    what = f"fp32 operating point alpha={op['alpha']} beta={op['beta']}, NumPy FP64"
+    if procs > 1:
+        try:
+            pool = OraclePool(parts, data, queries, geom, bud, tgt, procs)
+            try:
+                done, el = pool.run([("deadline", r, procs, seconds) for r in range(procs)],
+                                    timeout=seconds + 120)
+            finally:
+                pool.close()
+            return {"value": round(done / el, 3), "unit": "queries/s", "cores": procs,
+                    "kind": "oracle",
+                    "sample": f"{done} of {len(queries)} queries dealt round-robin to {procs} "
+                              f"processes for {seconds:.0f} s, {what}, one thread each"}
+        except (OSError, RuntimeError) as e:
+            log(f"cpu baseline: process pool failed ({e}); timing one process")
     from oracle import taco_oracle as O
     oix = O.index_from_parts(parts["o_bar"], parts["B"], parts["centroids"], parts["codes"], *geom)
     t0 = time.perf_counter()
@@ -704,22 +757,42 @@ def run_reference(args):
     # beta 0.001); the oracle is not calibrated itself
     alpha, beta = (args.alpha or 0.01), (args.beta or 0.001)
     bud, tgt = budget_from_alpha(alpha, w.n), target_from_beta(beta, w.n)
-    per_step = max(1, int(os.environ.get("TACO_REF_QUERIES_PER_STEP", "4")))
-    qi = 0
-    for _ in range(args.warmup):
-        O.search_one(oix, data, queries[qi % len(queries)], K, bud, tgt)
-        qi += 1
+    per_step = max(1, int(os.environ.get("TACO_REF_QUERIES_PER_STEP", "2")))   # per process
+    procs = host_cores()
+    nqs = len(queries)
     times = []
-    for _ in range(args.steps):
-        t1 = time.perf_counter()
-        for _ in range(per_step):
-            O.search_one(oix, data, queries[qi % len(queries)], K, bud, tgt)
-            qi += 1
-        times.append(time.perf_counter() - t1)
+    pool = None
+    if procs > 1:
+        try:
+            pool = OraclePool({"o_bar": mu, "B": B, "centroids": cent, "codes": codes}, data, queries,
+                              (w.n_subspaces, w.sub_dim, w.sqrt_k), bud, tgt, procs)
+        except (OSError, RuntimeError) as e:
+            log(f"[reference] process pool failed ({e}); timing one process")
+            procs, pool = 1, None
+    try:
+        qi = 0
+        for step in range(args.warmup + args.steps):
+            if pool is not None:   # per_step queries in each process, all dispatched at once
+                tasks = [("list", [(qi + r * per_step + j) % nqs for j in range(per_step)])
+                         for r in range(procs)]
+                t1 = time.perf_counter()
+                pool.run(tasks, timeout=600)
+                el = time.perf_counter() - t1
+            else:
+                t1 = time.perf_counter()
+                for j in range(per_step):
+                    O.search_one(oix, data, queries[(qi + j) % nqs], K, bud, tgt)
+                el = time.perf_counter() - t1
+            qi += procs * per_step
+            if step >= args.warmup:
+                times.append(el)
+    finally:
+        if pool is not None:
+            pool.close()
     total = sum(times)
-    value = args.steps * per_step / total
-    sample = (f"{per_step} queries per step of the {len(queries)}-query batch, alpha={alpha} "
-              f"beta={beta}, single-threaded NumPy FP64 oracle")
+    value = args.steps * procs * per_step / total
+    sample = (f"{per_step} queries per process and step ({procs} processes, one NumPy thread "
+              f"each) of the {nqs}-query batch, alpha={alpha} beta={beta}, FP64 oracle")
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -728,7 +801,7 @@ def run_reference(args):
         "config": {"workload": "sift1m-like: n=1,000,000 d=128 integer GMM, nq=10,000, k=10, "
                                "N_s=8, s=16, sqrtK=64", "parallelism": "host cores"},
         "impl": "reference",
-        "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1,
+        "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": procs,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
