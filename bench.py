@@ -695,8 +695,8 @@ def cpu_baseline_parts(parts, data, queries, geom, op, seconds, procs=None):
                     "kind": "oracle",
                     "sample": f"{done} of {len(queries)} queries dealt round-robin to {procs} "
                               f"processes for {seconds:.0f} s, {what}, one thread each"}
-        except (OSError, RuntimeError) as e:
-            log(f"cpu baseline: process pool failed ({e}); timing one process")
+        except Exception as e:   # any failure of the pool: the single-process timing below
+            log(f"cpu baseline: process pool failed ({e!r}); timing one process")
     from oracle import taco_oracle as O
     oix = O.index_from_parts(parts["o_bar"], parts["B"], parts["centroids"], parts["codes"], *geom)
     t0 = time.perf_counter()
@@ -760,17 +760,16 @@ def run_reference(args):
     per_step = max(1, int(os.environ.get("TACO_REF_QUERIES_PER_STEP", "2")))   # per process
     procs = host_cores()
     nqs = len(queries)
-    times = []
     pool = None
     if procs > 1:
         try:
             pool = OraclePool({"o_bar": mu, "B": B, "centroids": cent, "codes": codes}, data, queries,
                               (w.n_subspaces, w.sub_dim, w.sqrt_k), bud, tgt, procs)
-        except (OSError, RuntimeError) as e:
-            log(f"[reference] process pool failed ({e}); timing one process")
+        except Exception as e:   # any failure of the pool: time this process alone
+            log(f"[reference] process pool failed ({e!r}); timing one process")
             procs, pool = 1, None
-    try:
-        qi = 0
+    def measure(pool, procs):
+        times, qi = [], 0
         for step in range(args.warmup + args.steps):
             if pool is not None:   # per_step queries in each process, all dispatched at once
                 tasks = [("list", [(qi + r * per_step + j) % nqs for j in range(per_step)])
@@ -786,6 +785,15 @@ def run_reference(args):
             qi += procs * per_step
             if step >= args.warmup:
                 times.append(el)
+        return times
+
+    try:
+        times = measure(pool, procs)
+    except Exception as e:   # a pool process failed: time this process alone
+        log(f"[reference] process pool failed ({e!r}); timing one process")
+        pool.close()
+        procs, pool = 1, None
+        times = measure(None, 1)
     finally:
         if pool is not None:
             pool.close()

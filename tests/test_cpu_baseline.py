@@ -34,3 +34,18 @@ def test_single_process_fallback():
     r = bench.cpu_baseline_parts(parts, data, queries, (w.n_subspaces, w.sub_dim, w.sqrt_k), op,
                                  seconds=0.5, procs=1)
     assert r["cores"] == 1 and r["value"] > 0 and "single process" in r["sample"]
+
+
+def test_pool_failure_falls_back_to_one_process(monkeypatch):
+    """A pool that fails (here: a process that raises at start-up) leaves the baseline to
+    this process alone instead of losing the bench line."""
+    w, data, queries, parts = _parts()
+
+    class Broken:
+        def __init__(self, *a, **k):
+            raise ValueError("injected start-up failure")
+
+    monkeypatch.setattr(bench, "OraclePool", Broken)
+    r = bench.cpu_baseline_parts(parts, data, queries, (w.n_subspaces, w.sub_dim, w.sqrt_k),
+                                 {"alpha": 0.05, "beta": 0.01}, seconds=0.5, procs=4)
+    assert r["cores"] == 1 and r["value"] > 0 and "single process" in r["sample"]
