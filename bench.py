@@ -198,6 +198,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def ncu_limiter(kernel):
+    """The ncu reading of what bounds `kernel` from the committed summary, if it was taken on
+    the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_sift1m.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        lim = json.load(f).get("limiter")
+    if not lim or lim.get("source_hash") != kernel_source_hash():
+        return None
+    return {k: v for k, v in lim.items() if k != "source_hash"}
+
+
 def ncu_traffic(kernel, precision):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
     the current kernel source; else None."""
@@ -469,6 +482,7 @@ def run_taco(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(dominant, "bf16"), "peak_kind": peak_kind,
+                     "limiter": ncu_limiter(dominant),
                      "kernel": f"{dominant} ({HEADLINE} form)",
                      "algorithmic_bytes_per_launch": int(alg_bytes),
                      "launch_ms": round(launch_ms, 4),
