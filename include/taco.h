@@ -256,9 +256,8 @@ typedef struct {
  * struct for the batch) on `stream` over the launch layouts above (coordinate descent: counter
  * layout, counting CTA size and walk depth, lanes per row for the params' row kind, probe
  * strategy; each candidate: one untimed and `reps` timed searches) and keep the fastest for
- * this index's later
- * searches. The layout changes no result beyond the FP32 summation order of a candidate's
- * distance. reps <= 0 restores the default layout. Synchronises `stream`; must not run while
+ * this index's later searches. The layout changes no result beyond the FP32 summation order
+ * of a candidate's distance. reps <= 0 restores the default layout. Synchronises `stream`; must not run while
  * other searches or a server use the index. Profiling must be off (TACO_EINVAL).
  */
 int taco_autotune(taco_index* index, const float* queries, int64_t nq, const taco_query_params* params,
@@ -292,8 +291,10 @@ int taco_load_index(const char* path, int32_t keep_rows, void* stream, taco_inde
 /* Per-kernel device time of the search path, accumulated while profiling is enabled.
  * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 collision counting
  * into per-range level lists (Def. 6), 3 selection and re-rank (Alg. 5, Alg. 6 step 9),
- * 4 cluster kernel (counting, selection and re-rank for queries whose threshold is below 2,
- * or for every query in taco_search_batch_noalloc), 5 merge of the cluster kernel's lists,
+ * 4 fallback for the queries the two-pass form cannot finish (threshold below 2, or a level
+ * list past its slot): the cluster kernel, or the codes fallback (TACO_OPT_CODES_FALLBACK);
+ * the cluster kernel answers every query in taco_search_batch_noalloc; 5 merge of the
+ * cluster kernel's lists,
  * 6 query x centroid block on the tensor cores (probe_precision TACO_PREC_BF16). */
 #define TACO_NUM_KERNELS 7
 typedef struct {
