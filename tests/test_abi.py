@@ -58,6 +58,10 @@ def test_last_error_empty_and_null_args(lib):
     assert lib.taco_server_create(None, None, ctypes.byref(out)) == T.EINVAL
     assert lib.taco_server_submit(None, None, None, None) == T.EINVAL
     lib.taco_server_destroy(None)
+    for opt in (T.OPT_CODES_FALLBACK, T.OPT_SLABS_PER_RANGE, T.OPT_COUNT_WARPS, T.OPT_WALK_UNROLL):
+        assert lib.taco_index_set_option(None, opt, 1) == T.EINVAL
+    assert lib.taco_autotune(None, None, 0, None, 1, None, None) == T.EINVAL
+    assert b"null" in lib.taco_last_error()
 
 
 _LAYOUT_C = r"""
