@@ -415,6 +415,9 @@ def run_taco(args):
         "cluster_count_select": 4 * retrieved + 8 * ncells + cand * d_pad * 2 + io,
         "probe_cells": nq * w.n_subspaces * (w.sqrt_k ** 2) * 4 + 2 * ncells,
     }
+    # algorithmic bytes of the whole path (BF16 rows: 2 B per candidate coordinate)
+    path_bytes = (4 * retrieved + 4 * ncells + cand * w.d * 2
+                  + nq * min(mult * K, 512) * w.d * 4 + nq * (w.d * 4 + K * 12))
     dominant = max((k for k in kt_b if kt_b[k]["launches"]), key=lambda k: kt_b[k]["ms"])
     kk = kt_b[dominant]
     launch_ms = kk["ms"] / max(kk["launches"], 1)
@@ -491,6 +494,12 @@ def run_taco(args):
                      "smem_atomics_per_query": round(retrieved / nq, 1),
                      "list_entries_per_query": round(entries / nq, 1),
                      "kernel_share": shares},
+        # the whole path against HBM: the method's algorithmic bytes per query (ids of the
+        # probed cells, their offsets, the candidate rows at the form's width, the exact
+        # shortlist rows, the query and the results) x queries per second
+        "path_roofline": {"bytes_per_query": round(path_bytes / nq, 1),
+                          "achieved": round(path_bytes / nq * value / 1e9, 1), "peak": peak,
+                          "unit": "GB/s", "frac": round(path_bytes / nq * value / 1e9 / peak, 4)},
         "clocks": clk,
     }
     if serving is not None:
