@@ -179,6 +179,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def algorithmic_bytes(nq, retrieved, ncells, cand, entries, d, d_pad, k, mult, n_ranges,
+                      n_subspaces, sqrt_k):
+    """Algorithmic bytes of one launch of each search kernel over a batch of nq queries
+    (BF16 candidate rows, the headline form), and of the whole path ("path"): the ids of the
+    probed cells (retrieved: their total over the batch and subspaces), the cells' offsets
+    (ncells probed cells), the candidate rows (cand candidates), the exact FP32 shortlist of
+    min(mult * k, 512) rows, each query's row and its k results; entries = level-list
+    entries (ids with SC >= 2); 72 B of unit state per (query, id range)."""
+    shortlist = min(mult * k, 512)
+    io = nq * (d * 4 + k * 12)
+    units = nq * n_ranges * 72
+    return {
+        "count_lists": 4 * retrieved + 8 * ncells + 4 * entries + units,
+        "select_rerank": cand * d_pad * 2 + nq * shortlist * d_pad * 4 + 4 * entries + units + io,
+        "cluster_count_select": 4 * retrieved + 8 * ncells + cand * d_pad * 2 + io,
+        "probe_cells": nq * n_subspaces * (sqrt_k ** 2) * 4 + 2 * ncells,
+        "path": 4 * retrieved + 4 * ncells + cand * d * 2 + nq * shortlist * d * 4 + io,
+    }
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -404,20 +424,10 @@ def run_taco(args):
     ncells = int(dbg["probed"].sum(dtype=torch.int64).item())
     cand = int(dbg["candidate_num"].sum().item())
     entries = int(dbg["collision_num"][:, 2:].sum().item())   # ids with SC >= 2 (level lists)
-    shortlist = min(mult * K, 512)
-    d_pad = info["d_pad"]
-    nr = tune[HEADLINE]["n_ranges"]   # id ranges per query of the tuned two-pass layout
-    io = nq * (w.d * 4 + K * 12)
-    alg = {   # algorithmic bytes per launch (one launch = the whole batch)
-        "count_lists": 4 * retrieved + 8 * ncells + 4 * entries + nq * nr * 72,
-        "select_rerank": cand * d_pad * 2 + nq * shortlist * d_pad * 4 + 4 * entries
-                         + nq * nr * 72 + io,
-        "cluster_count_select": 4 * retrieved + 8 * ncells + cand * d_pad * 2 + io,
-        "probe_cells": nq * w.n_subspaces * (w.sqrt_k ** 2) * 4 + 2 * ncells,
-    }
-    # algorithmic bytes of the whole path (BF16 rows: 2 B per candidate coordinate)
-    path_bytes = (4 * retrieved + 4 * ncells + cand * w.d * 2
-                  + nq * min(mult * K, 512) * w.d * 4 + nq * (w.d * 4 + K * 12))
+    alg = algorithmic_bytes(nq, retrieved, ncells, cand, entries, d=w.d, d_pad=info["d_pad"], k=K,
+                            mult=mult, n_ranges=tune[HEADLINE]["n_ranges"],
+                            n_subspaces=w.n_subspaces, sqrt_k=w.sqrt_k)
+    path_bytes = alg.pop("path")
     dominant = max((k for k in kt_b if kt_b[k]["launches"]), key=lambda k: kt_b[k]["ms"])
     kk = kt_b[dominant]
     launch_ms = kk["ms"] / max(kk["launches"], 1)

@@ -75,3 +75,35 @@ def test_clock_sampler_parsing():
     r = s.stop()
     assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
     assert r["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_algorithmic_bytes_formulas():
+    """Per-launch algorithmic bytes on a hand-counted batch: 2 queries, 1,000 retrieved ids,
+    30 probed cells, 50 candidates, 20 level-list entries, d = 128, k = 10, shortlist 2k."""
+    a = bench.algorithmic_bytes(2, 1000, 30, 50, 20, d=128, d_pad=128, k=10, mult=2, n_ranges=3,
+                                n_subspaces=8, sqrt_k=64)
+    io = 2 * (128 * 4 + 10 * 12)
+    assert a["count_lists"] == 4000 + 240 + 80 + 2 * 3 * 72
+    assert a["select_rerank"] == 50 * 256 + 2 * 20 * 512 + 80 + 2 * 3 * 72 + io
+    assert a["probe_cells"] == 2 * 8 * 4096 * 4 + 60
+    assert a["path"] == 4000 + 120 + 50 * 256 + 2 * 20 * 512 + io
+    # the shortlist is capped at 512 rows
+    b = bench.algorithmic_bytes(1, 0, 0, 0, 0, d=8, d_pad=8, k=100, mult=8, n_ranges=1,
+                                n_subspaces=1, sqrt_k=1)
+    assert b["path"] == 512 * 8 * 4 + 8 * 4 + 100 * 12
+
+
+def test_ncu_figures_follow_the_kernel_source(monkeypatch):
+    """Traffic and limiter come from the committed summary only while its source hash is
+    the current one."""
+    import json
+    import os
+    j = json.load(open(os.path.join(bench.ROOT, "profiles", "count_lists_sift1m.json")))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: j["bf16"]["source_hash"])
+    assert bench.ncu_traffic("count_lists", "bf16") == j["bf16"]["dram_bytes_per_launch_full_batch"]
+    if j.get("limiter", {}).get("source_hash") == j["bf16"]["source_hash"]:
+        assert bench.ncu_limiter("count_lists")["issue_active_pct"] > 0
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
+    assert bench.ncu_traffic("count_lists", "bf16") is None
+    assert bench.ncu_limiter("count_lists") is None
+    assert bench.ncu_traffic("no_such_kernel", "bf16") is None
