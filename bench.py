@@ -67,7 +67,8 @@ def parse():
                          "whose timings mislead the tuner)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="sift1m (the headline line) or deep10m / deep5m256 / gist1m (their "
-                         "own line: batched uneven form, serving form, precision form)")
+                         "own line: batched uneven form, serving form, precision form); with "
+                         "--impl reference any workload of synth (e.g. tiny20k)")
     ap.add_argument("--serve-seconds", type=float, default=0.3,
                     help="arrival span of each offered load in the serving runs")
     return ap.parse_args()
@@ -760,7 +761,7 @@ def run_reference(args):
     from synth import budget_from_alpha, make_workload, target_from_beta
 
     t0 = time.time()
-    w, data, queries = make_workload(WORKLOAD, nq=args.nq)
+    w, data, queries = make_workload(args.workload, nq=args.nq)
     # the oracle's own index (Alg. 1-3 in FP64); k-means halves run in a spawn pool
     mu, sigma = O.mean_and_covariance(data)
     lam, xi = O.spectral_decomposition(sigma)
@@ -788,7 +789,10 @@ def run_reference(args):
     log(f"[reference] oracle index built in {time.time() - t0:.1f}s")
     # the operating point the GPU calibration selects on this workload (alpha 0.01,
     # beta 0.001); the oracle is not calibrated itself
-    alpha, beta = (args.alpha or 0.01), (args.beta or 0.001)
+    if args.workload == WORKLOAD:
+        alpha, beta = (args.alpha or 0.01), (args.beta or 0.001)
+    else:   # another workload: its own nominal operating point
+        alpha, beta = (args.alpha or w.alpha), (args.beta or w.beta)
     bud, tgt = budget_from_alpha(alpha, w.n), target_from_beta(beta, w.n)
     per_step = max(1, int(os.environ.get("TACO_REF_QUERIES_PER_STEP", "2")))   # per process
     procs = host_cores()
@@ -839,8 +843,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "sift1m-like: n=1,000,000 d=128 integer GMM, nq=10,000, k=10, "
-                               "N_s=8, s=16, sqrtK=64", "parallelism": "host cores"},
+        "config": {"workload": ("sift1m-like: n=1,000,000 d=128 integer GMM, nq=10,000, k=10, "
+                                "N_s=8, s=16, sqrtK=64") if args.workload == WORKLOAD else
+                               (f"{w.name}: n={w.n:,} d={w.d}, nq={nqs:,}, k={K}, N_s={w.n_subspaces}, "
+                                f"s={w.sub_dim}, sqrtK={w.sqrt_k}"),
+                   "parallelism": "host cores"},
         "impl": "reference",
         "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": procs,
                          "kind": "oracle", "sample": sample},
