@@ -289,6 +289,8 @@ int taco_save_index(const taco_index* index, const char* path);
 int taco_load_index(const char* path, int32_t keep_rows, void* stream, taco_index** out);
 
 /* Per-kernel device time of the search path, accumulated while profiling is enabled.
+ * launches[] counts kernel launches (slot 1 counts both probe kernels when the row-merge walk
+ * runs before the histogram kernel; one event pair times them together).
  * Kernel slots: 0 transform (Alg. 6 step 1), 1 cell probe (Alg. 4), 2 collision counting
  * into per-range level lists (Def. 6), 3 selection and re-rank (Alg. 5, Alg. 6 step 9),
  * 4 fallback for the queries the two-pass form cannot finish (threshold below 2, or a level

@@ -797,8 +797,9 @@ int taco_profile_read(taco_index* ix, taco_kernel_times* out, int32_t reset) {
         TACO_CUDA(cudaEventSynchronize(p.second.second));
         float ms = 0.f;
         TACO_CUDA(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
-        pr.ms[p.first] += ms;
-        pr.launches[p.first] += 1;
+        const int slot = p.first & 0xff;            // bits 8 and up: kernels under the pair
+        pr.ms[slot] += ms;
+        pr.launches[slot] += std::max(1, p.first >> 8);
     }
     pr.pending.clear();
     pr.used = 0;

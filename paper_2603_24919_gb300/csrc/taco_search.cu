@@ -824,6 +824,12 @@ int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent
     return TACO_OK;
 }
 
+// prof_end for an event pair around `kernels` launches of one slot (the slot's launch count
+// grows by that many; taco_profile_read takes the count from bits 8 and up of the entry).
+static int prof_end_n(taco_index* ix, int slot, int kernels, cudaStream_t st, cudaEvent_t b, cudaEvent_t e) {
+    return prof_end(ix, slot | (kernels << 8), st, b, e);
+}
+
 // The select / re-rank kernel for a row kind (0 FP32, 1 BF16, 2 FP8), register-list size R
 // (1, 4, 16) and G lanes per row.
 static cudaError_t launch_select(int rk, int R, int G, const RerankParams& P, int64_t nq, size_t smem,
@@ -910,7 +916,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                 L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo);
 #undef TACO_PROBE_REG
         TACO_CUDA(cudaGetLastError());
-        if (int rc = prof_end(pix, 1, st, pb, pe)) return rc;
+        if (int rc = prof_end_n(pix, 1, walk ? 2 : 1, st, pb, pe)) return rc;   // walk + histogram kernel
         if (L.dbg.retrieved_num)
             TACO_CUDA(cudaMemcpyAsync(L.dbg.retrieved_num, L.retrieved,
                                       size_t(L.nq) * ix->Ns * sizeof(int64_t),
