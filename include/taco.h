@@ -217,7 +217,8 @@ int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq
  *   An index whose n is too large for any cluster (more than 16 x 12 slabs of 2^15 points)
  *   always uses the codes fallback (TACO_ECAPACITY for value 0).
  *   TACO_OPT_SLABS_PER_RANGE: counter slabs per id range of the two-pass counting, 1 .. 12
- *   (n_ranges follows; TACO_ECAPACITY at search time if the counters do not fit an SM).
+ *   (a value above the index's n_slabs acts as n_slabs; n_ranges follows; TACO_ECAPACITY at
+ *   search time if the counters do not fit an SM).
  *   TACO_OPT_COUNT_WARPS: warps per counting CTA, 16 or 32.
  *   TACO_OPT_WALK_UNROLL: id loads in flight per lane in the counting walk, 8 or 16 (16 takes
  *   effect with 16 warps only).
