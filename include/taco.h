@@ -171,6 +171,40 @@ int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
                       int32_t k_stride, int64_t* out_ids, float* out_dists, void* stream);
 
 /*
+ * Per-query parameters resident on the device, for batches searched again and again (a
+ * benchmark loop, a fixed request mix, a captured CUDA graph). taco_search_batch with a
+ * per_query array converts and copies the nq records on every call and synchronises the
+ * stream afterwards (its pinned staging is reused); a taco_params batch does that once.
+ * The paper has no counterpart: this only moves Alg. 6's per-query inputs (k, B, R of Alg. 4
+ * and Alg. 5) to the device ahead of time.
+ */
+typedef struct taco_params taco_params;
+
+/*
+ * taco_params_create -- check the nq host records per_query (as taco_search_batch does, with
+ * k <= TACO_MAX_K; precision, select_rule and probe_precision uniform), copy them to device
+ * memory allocated here, and return the handle in *out. Synchronises `stream`. The handle is
+ * tied to `index` and to nq. Errors: TACO_EINVAL, TACO_ECAPACITY (k > TACO_MAX_K), TACO_ENOMEM.
+ */
+int taco_params_create(const taco_index* index, const taco_query_params* per_query, int64_t nq,
+                       void* stream, taco_params** out);
+
+/* taco_params_free -- release a parameter batch (NULL is a no-op). No search using it may be
+ * running or queued. */
+void taco_params_free(taco_params* params);
+
+/*
+ * taco_search_batch_params -- taco_search_batch for the params->nq queries with the prepared
+ * per-query parameters (query j uses record j). Arguments and results as taco_search_batch;
+ * k_stride must be >= every prepared k. Nothing is copied from the host and the call does not
+ * synchronise the stream unless an output is a host pointer. With device queries and outputs
+ * and a workspace already large enough (an earlier call of the same shape), the call only
+ * enqueues kernels, so it can be captured in a CUDA graph.
+ */
+int taco_search_batch_params(const taco_index* index, const float* queries, const taco_params* params,
+                             int32_t k_stride, int64_t* out_ids, float* out_dists, void* stream);
+
+/*
  * taco_search_batch_noalloc -- taco_search_batch for callers that may not allocate device
  * memory (a process whose device memory is owned by its own pool or framework, or a
  * request path where a cudaMalloc, which can synchronise the device, is not allowed).
@@ -180,9 +214,12 @@ int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
  * Scratch lives in a fixed 64 MiB array in device memory that every GPU which loads the
  * library holds until the process exits; the call itself calls no allocating routine.
  * Every scratch byte read by a call is written earlier in the same call, so nothing needs
- * clearing between calls. Limits: nq <= 16384 and the batch's scratch (about
- * 4*N_s*s + 2*N_s*K + 12*N_s + 128*C*kk bytes per query, C the index's cluster size and
- * kk the k of the query or its BF16 shortlist) must fit the array, else TACO_ECAPACITY.
+ * clearing between calls. Limits: nq <= 16384 and the batch's scratch must fit the array,
+ * else TACO_ECAPACITY. The scratch is six regions, each rounded up to 256 bytes, of
+ * nq*4*Dp, nq*2*N_s*K, nq*4*N_s, nq*8*N_s and twice nq*64*C*kk bytes, where Dp is N_s*s,
+ * C the index's cluster_size and kk the k of the query or its BF16 shortlist
+ * min(shortlist_mult*k, TACO_MAX_K). FP8 rows (TACO_PREC_FP8) and the tensor-core centroid
+ * block (probe_precision TACO_PREC_BF16) are refused with TACO_EINVAL.
  * TACO_ECAPACITY also for an index whose cluster_size is 0 (n above 16 x 12 x 2^15 points).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture. All calls share the array, so calls

@@ -15,9 +15,11 @@ from .taco import (  # noqa: F401
     SELECT_LITERAL,
     SELECT_PROSE,
     SIGNATURES,
+    PreparedParams,
     TacoError,
     TacoIndex,
     TacoServer,
     load_library,
+    query_param_array,
     query_params,
 )

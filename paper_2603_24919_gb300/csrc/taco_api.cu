@@ -519,18 +519,27 @@ namespace {
 
 int search_impl(const taco_index* cix, const float* queries, int64_t nq, const taco_query_params* per_query,
                 const taco_query_params* defaults, int32_t k_stride, int64_t* out_ids, float* out_dists,
-                const taco_debug_out* dbg, cudaStream_t st) {
+                const taco_debug_out* dbg, cudaStream_t st, const taco_params* prepared = nullptr) {
     if (!cix) return fail(TACO_EINVAL, "null index");
     taco_index* ix = const_cast<taco_index*>(cix);
     if (nq < 0) return fail(TACO_EINVAL, "nq < 0");
     if (nq == 0) return TACO_OK;
     if (!queries || !out_ids || !out_dists) return fail(TACO_EINVAL, "null queries or outputs");
-    if (!per_query && !defaults) return fail(TACO_EINVAL, "per_query and defaults are both NULL");
+    if (!per_query && !defaults && !prepared) return fail(TACO_EINVAL, "per_query and defaults are both NULL");
     if (k_stride < 1) return fail(TACO_EINVAL, "k_stride < 1");
-    const taco_query_params& head = per_query ? per_query[0] : *defaults;
+    if (prepared) {
+        if (prepared->index != cix) return fail(TACO_EINVAL, "the parameters were prepared for another index");
+        if (prepared->nq != nq) return fail(TACO_EINVAL, "%lld queries for %lld prepared parameter records",
+                                            (long long)nq, (long long)prepared->nq);
+        if (prepared->k_max > k_stride)
+            return fail(TACO_EINVAL, "a prepared query has k = %d > k_stride = %d", prepared->k_max, k_stride);
+    }
+    const taco_query_params& head = prepared ? prepared->head : (per_query ? per_query[0] : *defaults);
     const int precision = head.precision;
     int kk_max = 0;
-    if (per_query) {
+    if (prepared) {
+        kk_max = prepared->kk_max;
+    } else if (per_query) {
         for (int64_t j = 0; j < nq; ++j) {
             TRY(check_query_params(per_query[j], k_stride));
             if (per_query[j].precision != precision || per_query[j].select_rule != head.select_rule ||
@@ -558,17 +567,18 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     std::lock_guard<std::mutex> lock(ix->ws_mu);
     const int64_t chunk = std::min<int64_t>(nq, kQueryChunk);
     const int Ns = ix->Ns, K = ix->K;
-    const SearchLayout lay = plan_search(ix, chunk, kk_max, per_query ? nq : 0, !q_dev, !id_dev, !dist_dev,
-                                         k_stride, ctc);
+    const SearchLayout lay = plan_search(ix, chunk, kk_max, (per_query && !prepared) ? nq : 0, !q_dev, !id_dev,
+                                         !dist_dev, k_stride, ctc);
     const size_t host_need = per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0;
     TRY(ensure_workspace(ix, lay.total, host_need));
     char* wb = static_cast<char*>(ix->ws.base);
-    QueryParamsDev* dparams = nullptr;
-    if (per_query) {
+    const QueryParamsDev* dparams = prepared ? prepared->d_params : nullptr;
+    if (per_query && !prepared) {
         QueryParamsDev* hp = static_cast<QueryParamsDev*>(ix->ws.host_pinned);
         for (int64_t j = 0; j < nq; ++j) hp[j] = query_params_dev(per_query[j]);
-        dparams = reinterpret_cast<QueryParamsDev*>(wb + lay.par);
-        TACO_CUDA(cudaMemcpyAsync(dparams, hp, size_t(nq) * sizeof(QueryParamsDev), cudaMemcpyHostToDevice, st));
+        QueryParamsDev* dp = reinterpret_cast<QueryParamsDev*>(wb + lay.par);
+        TACO_CUDA(cudaMemcpyAsync(dp, hp, size_t(nq) * sizeof(QueryParamsDev), cudaMemcpyHostToDevice, st));
+        dparams = dp;
     }
     for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
         const int64_t cn = std::min(chunk, nq - c0);
@@ -608,7 +618,8 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
             TACO_CUDA(cudaMemcpyAsync(out_dists + c0 * k_stride, L.out_dists, size_t(cn) * k_stride * 4,
                                       cudaMemcpyDeviceToHost, st));
     }
-    if (!id_dev || !dist_dev || per_query) TACO_CUDA(cudaStreamSynchronize(st));
+    // host outputs, or the pinned parameter staging that the next call reuses
+    if (!id_dev || !dist_dev || (per_query && !prepared)) TACO_CUDA(cudaStreamSynchronize(st));
     return TACO_OK;
 }
 
@@ -633,6 +644,55 @@ int taco_search_batch(const taco_index* index, const float* queries, int64_t nq,
                       void* stream) {
     return search_impl(index, queries, nq, per_query, defaults, k_stride, out_ids, out_dists, nullptr,
                        static_cast<cudaStream_t>(stream));
+}
+
+int taco_params_create(const taco_index* index, const taco_query_params* per_query, int64_t nq, void* stream,
+                       taco_params** out) {
+    if (!index || !per_query || !out) return fail(TACO_EINVAL, "null index, parameters or output");
+    if (nq < 1) return fail(TACO_EINVAL, "nq must be >= 1");
+    *out = nullptr;
+    std::unique_ptr<taco_params> p(new taco_params());
+    p->index = index;
+    p->nq = nq;
+    p->head = per_query[0];
+    std::vector<QueryParamsDev> host(static_cast<size_t>(nq));
+    for (int64_t j = 0; j < nq; ++j) {
+        const taco_query_params& q = per_query[j];
+        TRY(check_query_params(q, TACO_MAX_K));
+        if (q.precision != p->head.precision || q.select_rule != p->head.select_rule ||
+            q.probe_precision != p->head.probe_precision)
+            return fail(TACO_EINVAL, "precision, probe_precision and select_rule must be uniform in a batch");
+        p->kk_max = std::max(p->kk_max, query_list_len(q));
+        p->k_max = std::max(p->k_max, q.k);
+        host[j] = query_params_dev(q);
+    }
+    int dev = 0;
+    TACO_CUDA(cudaGetDevice(&dev));
+    if (dev != index->device) return fail(TACO_EINVAL, "current device %d is not the index's device %d", dev, index->device);
+    QueryParamsDev* d = nullptr;
+    if (cudaMalloc(&d, host.size() * sizeof(QueryParamsDev)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TACO_ENOMEM, "cannot allocate %lld parameter records", (long long)nq);
+    }
+    p->d_params = d;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TACO_CUDA(cudaMemcpyAsync(d, host.data(), host.size() * sizeof(QueryParamsDev), cudaMemcpyHostToDevice, st));
+    TACO_CUDA(cudaStreamSynchronize(st));   // the host records go out of scope
+    *out = p.release();
+    return TACO_OK;
+}
+
+void taco_params_free(taco_params* p) {
+    if (!p) return;
+    cudaFree(const_cast<QueryParamsDev*>(p->d_params));
+    delete p;
+}
+
+int taco_search_batch_params(const taco_index* index, const float* queries, const taco_params* params,
+                             int32_t k_stride, int64_t* out_ids, float* out_dists, void* stream) {
+    if (!params) return fail(TACO_EINVAL, "null parameters");
+    return search_impl(index, queries, params->nq, nullptr, nullptr, k_stride, out_ids, out_dists, nullptr,
+                       static_cast<cudaStream_t>(stream), params);
 }
 
 int taco_search_debug(const taco_index* index, const float* queries, int64_t nq, const taco_query_params* per_query,

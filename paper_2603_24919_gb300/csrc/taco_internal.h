@@ -123,6 +123,16 @@ struct taco_index {
     taco::Profiler prof;
 };
 
+// Per-query parameters copied to the device once (taco_params_create).
+struct taco_params {
+    const taco_index* index = nullptr;
+    int64_t nq = 0;
+    const taco::QueryParamsDev* d_params = nullptr;   // device [nq]
+    taco_query_params head{};                         // the batch-uniform fields (query 0)
+    int kk_max = 0;                                   // longest list any query needs
+    int k_max = 0;                                    // largest k
+};
+
 namespace taco {
 
 // Kernel launchers (return cudaGetLastError of the launch).

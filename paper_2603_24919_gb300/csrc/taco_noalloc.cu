@@ -57,17 +57,14 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     if (!is_device_pointer(queries) || !is_device_pointer(out_ids) || !is_device_pointer(out_dists))
         return fail(TACO_EINVAL, "taco_search_batch_noalloc takes device pointers only");
     const taco_query_params& q = *params;
-    if (q.k < 1 || q.k > k_stride) return fail(TACO_EINVAL, "k = %d must be in [1, k_stride = %d]", q.k, k_stride);
-    if (q.k > TACO_MAX_K) return fail(TACO_ECAPACITY, "k = %d exceeds %d", q.k, TACO_MAX_K);
-    if (q.budget < 1 || q.rerank_target < 0) return fail(TACO_EINVAL, "budget must be >= 1, rerank_target >= 0");
-    if (q.select_rule != TACO_SELECT_LITERAL && q.select_rule != TACO_SELECT_PROSE)
-        return fail(TACO_EINVAL, "unknown select_rule %d", q.select_rule);
-    if (q.precision != TACO_PREC_FP32 && q.precision != TACO_PREC_BF16)
-        return fail(TACO_EINVAL, "unknown precision %d", q.precision);
+    // the checks of taco_search_batch, then what this entry point does not support
+    if (int rc = check_query_params(q, k_stride)) return rc;
+    if (q.precision == TACO_PREC_FP8)
+        return fail(TACO_EINVAL, "taco_search_batch_noalloc re-ranks with FP32 or BF16 rows only");
     if (q.probe_precision != TACO_PREC_FP32)
         return fail(TACO_EINVAL, "taco_search_batch_noalloc computes centroid distances in FP32 only");
-    if (q.precision == TACO_PREC_BF16 && (q.shortlist_mult < 1 || !index->d_data_bf16))
-        return fail(TACO_EINVAL, "BF16 needs shortlist_mult >= 1 and an index with BF16 rows");
+    if (q.precision == TACO_PREC_BF16 && !index->d_data_bf16)
+        return fail(TACO_EINVAL, "BF16 needs an index with BF16 rows");
     if (nq > kQueryChunk)
         return fail(TACO_ECAPACITY, "nq = %lld exceeds %lld queries per call", (long long)nq,
                     (long long)kQueryChunk);
@@ -83,14 +80,12 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     const size_t per_cells = up256(size_t(nq) * ix->Ns * ix->K * 2);
     const size_t per_nc = up256(size_t(nq) * ix->Ns * 4);
     const size_t per_ret = up256(size_t(nq) * ix->Ns * 8);
-    const int kk = q.precision == TACO_PREC_BF16
-                       ? int(std::min<int64_t>(std::max<int64_t>(int64_t(q.k) * q.shortlist_mult, q.k), TACO_MAX_K))
-                       : q.k;
+    const int kk = query_list_len(q);
     const size_t per_list = up256(size_t(nq) * ix->cluster * kListsPerCta * kk * 4);
     const size_t need = per_qt + per_cells + per_nc + per_ret + 2 * per_list;
     if (need > kNoAllocScratchBytes) {
         const size_t one = size_t(ix->Dp) * 4 + size_t(ix->Ns) * ix->K * 2 + size_t(ix->Ns) * 12 +
-                           size_t(ix->cluster) * kListsPerCta * kk * 8;
+                           size_t(ix->cluster) * kListsPerCta * kk * 8;   // per query, unrounded
         return fail(TACO_ECAPACITY,
                     "nq = %lld needs %zu bytes of scratch; the fixed scratch holds %zu bytes "
                     "(about %zu queries of this index per call)",
@@ -104,13 +99,7 @@ extern "C" int taco_search_batch_noalloc(const taco_index* index, const float* q
     L.ix = ix;
     L.queries = queries;
     L.nq = nq;
-    QueryParamsDev d;
-    d.k = q.k;
-    d.select_rule = q.select_rule;
-    d.budget = q.budget;
-    d.rerank_target = q.rerank_target;
-    d.kk = kk;
-    d.pad = 0;
+    const QueryParamsDev d = query_params_dev(q);
     L.defaults = d;
     L.params = nullptr;
     L.precision = q.precision;

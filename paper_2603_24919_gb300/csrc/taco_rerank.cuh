@@ -679,6 +679,10 @@ count_select_rerank_kernel(const RerankParams P) {
     for (int64_t q = blockIdx.y; q < P.nq; q += gridDim.y, par ^= 1) {
         if (P.qmask && !P.qmask[q]) continue;   // same decision in every CTA of the cluster
         const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
+        // this query's list length: its k or shortlist (lists are allotted the batch's
+        // longest, kk; a query's answer is the first qp.kk of its merged list, and each
+        // warp's first qp.kk entries hold its qp.kk nearest)
+        const int kq = min(qp.kk, kk);
         uint32_t* ge = ge2 + 16 * par;
         uint32_t* s_allge = s_allge2[par];
         csm.ge = ge;
@@ -757,8 +761,8 @@ count_select_rerank_kernel(const RerankParams P) {
                         const float x = __shfl_sync(kFull, acc[u], src);
                         const uint32_t xi = __shfl_sync(kFull, cid[u], src);
                         if (lt_pair(x, xi, kth_d, kth_i)) {
-                            top.insert(x, xi, kk, lane);
-                            top.kth(kk, kth_d, kth_i);
+                            top.insert(x, xi, kq, lane);
+                            top.kth(kq, kth_d, kth_i);
                         }
                     }
                 }
@@ -1128,6 +1132,8 @@ select_rerank_kernel(const RerankParams P) {
         if (s_flag) continue;   // answered by the fallback
         }   // !fb_mode
         const int last = s_last;
+        // this query's list length (see the cluster kernel): each warp keeps its qp.kk nearest
+        const int kq = min(qp.kk, kk);
         WarpTop<R> top;
         top.init();
         float kth_d = __int_as_float(0x7f800000);
@@ -1149,8 +1155,8 @@ select_rerank_kernel(const RerankParams P) {
                         const float x = __shfl_sync(kFull, acc[uu], src);
                         const uint32_t xi = __shfl_sync(kFull, cid[uu], src);
                         if (lt_pair(x, xi, kth_d, kth_i)) {
-                            top.insert(x, xi, kk, lane);
-                            top.kth(kk, kth_d, kth_i);
+                            top.insert(x, xi, kq, lane);
+                            top.kth(kq, kth_d, kth_i);
                         }
                     }
                 }
@@ -1275,11 +1281,10 @@ select_rerank_kernel(const RerankParams P) {
             }
         }
         __syncthreads();
-        if (warp == 0) warp_merge(Ld, Li, kkc, kSrWarps, kk, Md, Mi, lane);
+        if (warp == 0) warp_merge(Ld, Li, kkc, kSrWarps, kq, Md, Mi, lane);
         __syncthreads();
-        // the query's own shortlist: the first qp.kk of the merged list (a batch's lists
+        // the query's own shortlist: the first qp.kk (kq) of the merged list (a batch's lists
         // are as long as its longest one; a shorter shortlist is a prefix of them)
-        const int kq = min(qp.kk, kk);
         if constexpr (RK != kRowF32) {
             // exact FP32 distances of the shortlist, then rank sort by (distance, id)
             const int nf4 = P.d_pad / 4;

@@ -41,7 +41,7 @@ probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict
                    QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                    int list_cap, uint16_t* __restrict__ cells_out,
                    int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out,
-                   uint8_t* __restrict__ dbg_probed, int redo_only) {
+                   int redo_only) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int i = blockIdx.x;
     const int64_t q = blockIdx.y;
@@ -212,7 +212,6 @@ probe_cells_kernel(const float* __restrict__ qt, int Dp, const float* __restrict
             cells_out[qi_off * K + wbase + __popc(bal & ((1u << lane) - 1u))] = uint16_t(cell);
             ret += sz[cell];
         }
-        if (dbg_probed && cell < K) dbg_probed[qi_off * K + cell] = take ? 1 : 0;
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) ret += __shfl_xor_sync(0xffffffffu, ret, off);
@@ -448,7 +447,7 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
                        int64_t n, QueryParamsDev defaults, const QueryParamsDev* __restrict__ params,
                        int list_cap, uint16_t* __restrict__ cells_out,
                        int32_t* __restrict__ ncells_out, int64_t* __restrict__ retrieved_out,
-                       uint8_t* __restrict__ dbg_probed, int redo_only) {
+                       int redo_only) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int i = blockIdx.x;
     const int64_t q = blockIdx.y;
@@ -629,7 +628,6 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
             cells_out[qi_off * K + wbase + __popc(bal & ((1u << lane) - 1u))] = uint16_t(cell);
             ret += kw[u];
         }
-        if (dbg_probed && cell < K) dbg_probed[qi_off * K + cell] = take ? 1 : 0;
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) ret += __shfl_xor_sync(0xffffffffu, ret, off);
@@ -639,6 +637,18 @@ probe_cells_reg_kernel(const float* __restrict__ qt, int Dp, const float* __rest
         ncells_out[qi_off] = s_cnt;
         retrieved_out[qi_off] = (long long)s_ret;
     }
+}
+
+// Debug output of Alg. 4: flags[pair][cell] = 1 for the cells the probe step wrote for that
+// (query, subspace) pair, whichever probe kernel settled it; one warp per pair. The flags
+// were zeroed by the caller.
+__global__ void __launch_bounds__(256)
+expand_probed_kernel(const uint16_t* __restrict__ cells, const int32_t* __restrict__ ncells, int K,
+                     int64_t pairs, uint8_t* __restrict__ flags) {
+    const int64_t p = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    if (p >= pairs) return;
+    const int m = ncells[p];
+    for (int t = threadIdx.x & 31; t < m; t += 32) flags[size_t(p) * K + cells[size_t(p) * K + t]] = 1;
 }
 
 // Shared memory of one warp of final_merge_kernel: the lists and merge buffers, rounded up
@@ -881,8 +891,9 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         dim3 grid(unsigned(ix->Ns), unsigned(L.nq));
         if (int rc = prof_begin(pix, 1, st, &pb, &pe)) return rc;
         // the row-merge walk settles small budgets; the histogram kernel redoes what it flags
-        // (and does everything when the debug flags are wanted or the budget needs many pops)
-        bool walk = L.dbg.probed == nullptr && ix->sk <= 128 && ix->tp_walk != 0;
+        // (and does everything when the budget needs many pops). Debug outputs change nothing
+        // here: the probed-cell flags are expanded afterwards from the cells this step wrote.
+        bool walk = ix->sk <= 128 && ix->tp_walk != 0;
         if (walk && ix->tp_walk < 0 && L.params == nullptr &&
             double(L.defaults.budget) * double(K) > 0.5 * kWalkMaxPops * double(ix->n))
             walk = false;
@@ -904,7 +915,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
 #define TACO_PROBE_REG(N)                                                                         \
     probe_cells_reg_kernel<N><<<grid, kSelThreads, smem, st>>>(                                   \
         L.qt, ix->Dp, ix->d_cent, hd, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n, L.defaults, \
-        L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo)
+        L.params, cap, L.cells, L.ncells, L.retrieved, redo)
         if (cpt <= 1) TACO_PROBE_REG(1);
         else if (cpt <= 2) TACO_PROBE_REG(2);
         else if (cpt <= 4) TACO_PROBE_REG(4);
@@ -913,10 +924,17 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         else
             probe_cells_kernel<<<grid, kSelThreads, smem, st>>>(
                 L.qt, ix->Dp, ix->d_cent, hd, ix->Ns, ix->s, ix->h1, ix->sk, ix->d_sizes, ix->n,
-                L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, L.dbg.probed, redo);
+                L.defaults, L.params, cap, L.cells, L.ncells, L.retrieved, redo);
 #undef TACO_PROBE_REG
         TACO_CUDA(cudaGetLastError());
         if (int rc = prof_end_n(pix, 1, walk ? 2 : 1, st, pb, pe)) return rc;   // walk + histogram kernel
+        if (L.dbg.probed) {
+            TACO_CUDA(cudaMemsetAsync(L.dbg.probed, 0, size_t(L.nq) * ix->Ns * K, st));
+            const int64_t pairs = L.nq * ix->Ns;
+            expand_probed_kernel<<<unsigned((pairs + 7) / 8), 256, 0, st>>>(L.cells, L.ncells, K, pairs,
+                                                                         L.dbg.probed);
+            TACO_CUDA(cudaGetLastError());
+        }
         if (L.dbg.retrieved_num)
             TACO_CUDA(cudaMemcpyAsync(L.dbg.retrieved_num, L.retrieved,
                                       size_t(L.nq) * ix->Ns * sizeof(int64_t),

@@ -106,6 +106,11 @@ SIGNATURES = {
     "taco_search_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                     C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "taco_params_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]),
+    "taco_params_free": (None, [C.c_void_p]),
+    "taco_search_batch_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "taco_search_batch_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
                                             C.POINTER(QueryParams), C.c_int32, C.c_void_p,
                                             C.c_void_p, C.c_void_p]),
@@ -216,6 +221,36 @@ def _as_f32(x):
     return np.ascontiguousarray(x, dtype=np.float32)
 
 
+def check_noalloc_args(queries, out_ids, out_dists, d):
+    """Raise ValueError unless the buffers of search_noalloc have the layout the C entry
+    point reads and writes: queries float32 [nq, d], out_ids int64 and out_dists float32 with
+    the same [rows >= nq, k_stride] shape, all contiguous CUDA tensors (the entry point reads
+    and writes them through raw pointers, so a wrong dtype or a short buffer would be read
+    with the wrong layout or written past its end)."""
+    torch = _torch()
+    want = (("queries", queries, torch.float32), ("out_ids", out_ids, torch.int64),
+            ("out_dists", out_dists, torch.float32))
+    for name, t, dt in want:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, not {t.dtype}")
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be 2-D, not {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    nq = queries.shape[0]
+    if queries.shape[1] != d:
+        raise ValueError(f"queries have {queries.shape[1]} columns, the index d = {d}")
+    if out_ids.shape != out_dists.shape:
+        raise ValueError(f"out_ids {tuple(out_ids.shape)} and out_dists {tuple(out_dists.shape)} differ")
+    if out_ids.shape[0] < nq:
+        raise ValueError(f"outputs have {out_ids.shape[0]} rows for {nq} queries")
+    for name, t, _ in want:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+
+
 def _rows(keep_bf16, keep_fp8):
     """TACO_ROWS_* mask of the row copies an index keeps."""
     return (ROWS_BF16 if keep_bf16 else 0) | (ROWS_FP8 if keep_fp8 else 0)
@@ -226,6 +261,15 @@ def query_params(k, budget, rerank_target, precision="fp32", select_rule="litera
     return QueryParams(int(k), _PREC.get(precision, precision), int(budget), int(rerank_target),
                        _RULE.get(select_rule, select_rule), int(shortlist_mult),
                        _PREC.get(probe_precision, probe_precision), 0)
+
+
+def query_param_array(per_query):
+    """A C array of QueryParams from QueryParams structs or dicts of query_params arguments
+    (build it once to pass the same per-query parameters to many searches)."""
+    arr = (QueryParams * len(per_query))()
+    for j, item in enumerate(per_query):
+        arr[j] = item if isinstance(item, QueryParams) else query_params(**item)
+    return arr
 
 
 class TacoIndex:
@@ -326,9 +370,12 @@ class TacoIndex:
                                 probe_precision)
         pq = None
         if per_query is not None:
-            arr = (QueryParams * nq)()
-            for j, item in enumerate(per_query):
-                arr[j] = item if isinstance(item, QueryParams) else query_params(**item)
+            if isinstance(per_query, C.Array) and per_query._type_ is QueryParams:
+                arr = per_query   # already in the C layout (see query_param_array)
+            else:
+                arr = query_param_array(per_query)
+            if len(arr) != nq:
+                raise ValueError(f"{len(arr)} parameter records for {nq} queries")
             pq = arr
             kmax = max(arr[j].k for j in range(nq)) if nq else k
         else:
@@ -358,6 +405,24 @@ class TacoIndex:
         _check(load_library().taco_search_batch(
             self._h, _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
             C.byref(defaults), k_stride, _ptr(out_ids), _ptr(out_dists), _stream_handle(stream)))
+        return out_ids, out_dists
+
+    def prepare(self, per_query, stream=None):
+        """taco_params_create: the per-query parameters (QueryParams or dicts for query_params)
+        copied to the device once; pass the result to search_prepared."""
+        return PreparedParams(self, per_query, stream)
+
+    def search_prepared(self, queries, params, k_stride=None, out_ids=None, out_dists=None,
+                        stream=None):
+        """taco_search_batch_params: Alg. 6 for the prepared batch (queries [params.nq, d])."""
+        q = _as_f32(queries)
+        if q.shape[0] != params.nq:
+            raise ValueError(f"{q.shape[0]} queries for {params.nq} prepared records")
+        k_stride = int(k_stride or params.k_max)
+        out_ids, out_dists = self._outputs(q, params.nq, k_stride, out_ids, out_dists)
+        _check(load_library().taco_search_batch_params(
+            self._h, _ptr(q), params.handle, k_stride, _ptr(out_ids), _ptr(out_dists),
+            _stream_handle(stream)))
         return out_ids, out_dists
 
     def centroid_distances(self, qt, probe_precision="fp32", stream=None):
@@ -410,7 +475,10 @@ class TacoIndex:
     def search_noalloc(self, queries, out_ids, out_dists, k, budget, rerank_target,
                        precision="fp32", select_rule="literal", shortlist_mult=4, stream=None):
         """taco_search_batch_noalloc: CUDA queries and caller-owned CUDA outputs; the
-        library allocates nothing (its scratch is a fixed device array)."""
+        library allocates nothing (its scratch is a fixed device array). The tensors are
+        checked first and used as given (no copy is made): queries float32 [nq, d], out_ids
+        int64 and out_dists float32 [>= nq, k_stride], all contiguous CUDA tensors."""
+        check_noalloc_args(queries, out_ids, out_dists, self.info()["d"])
         p = query_params(k, budget, rerank_target, precision, select_rule, shortlist_mult)
         _check(load_library().taco_search_batch_noalloc(
             self._h, _ptr(queries), int(queries.shape[0]), C.byref(p), int(out_ids.shape[1]),
@@ -446,6 +514,31 @@ class TacoIndex:
             _stream_handle(stream)))
         dbg["ids"], dbg["dists"] = out_ids, out_dists
         return dbg
+
+
+class PreparedParams:
+    """Per-query parameters resident on the device (taco_params_create / taco_params_free)."""
+
+    def __init__(self, index, per_query, stream=None):
+        self.index = index   # the handle is tied to the index: keep it alive
+        self.nq = len(per_query)
+        arr = per_query if isinstance(per_query, C.Array) else query_param_array(per_query)
+        self.k_max = max(arr[j].k for j in range(self.nq))
+        out = C.c_void_p()
+        _check(load_library().taco_params_create(index._h, C.cast(arr, C.c_void_p), self.nq,
+                                                 _stream_handle(stream), C.byref(out)))
+        self.handle = out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().taco_params_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class TacoServer:

@@ -18,3 +18,14 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Print the parity exclusion counts of every GPU parity check that ran."""
+    mod = sys.modules.get("tests.parity_util")
+    reports = getattr(mod, "REPORTS", None) if mod else None
+    if not reports:
+        return
+    terminalreporter.write_sep("-", "parity exclusions (FP64 near-ties; bound 5 % of queries)")
+    for name, rep in reports:
+        terminalreporter.write_line(f"{name}: {rep}")

@@ -7,11 +7,22 @@ Acceptance rule (the method's FP32 path against the FP64 oracle):
     gap between the k-th and (k+1)-th candidate distance): such cases are counted and
     reported, not compared;
   * returned distances agree within TOL_DIST relative.
+
+How often the exclusion may apply is bounded too (MAX_EXCLUDED): a query counts as excluded
+when its probed set really differs from the oracle's in a subspace whose FP64 margin is below
+TOL_MARGIN, or when its k-th and (k+1)-th candidate distances are that close. Over the
+oracle's own margins on the 20k x 128 workload (100 queries), 0-8 % of queries have some
+subspace margin below 1e-5 (8 % only at alpha = 0.5) and at most 1 % a k-th margin below it;
+an FP32 key flips its order with a neighbour only for a small part of those, so a test that
+excludes more than 5 % of its queries fails. Every report is also collected in REPORTS and
+printed at the end of the pytest run (tests/conftest.py), so the counts reach the log.
 """
 import numpy as np
 
 TOL_MARGIN = 1e-5
 TOL_DIST = 1e-5
+MAX_EXCLUDED = 0.05
+REPORTS = []   # (test name, ParityReport) of every check_exclusions call
 
 
 class ParityReport:
@@ -28,13 +39,25 @@ class ParityReport:
                 f"excluded_queries={self.excluded_queries} excluded_topk={self.excluded_topk}")
 
 
+def check_exclusions(rep, name, frac=MAX_EXCLUDED):
+    """Assert that at most `frac` of the compared queries (at least one query) were excluded,
+    for either reason, and record the report for the end-of-run summary."""
+    REPORTS.append((name, repr(rep)))
+    allowed = max(1, int(frac * rep.queries))
+    assert rep.queries > 0, f"{name}: no query compared ({rep})"
+    assert rep.excluded_queries <= allowed and rep.excluded_topk <= allowed, (
+        f"{name}: more than {frac:.0%} of {rep.queries} queries excluded at FP64 near-ties: {rep}")
+    return rep
+
+
 def probed_sets(gpu_probed_row):
     """[N_s][K] uint8 -> list of sorted cell arrays."""
     return [np.nonzero(r)[0] for r in gpu_probed_row]
 
 
-def compare_query(rep, trace, gpu, j, k, n, check_sc=True):
-    """Compare GPU debug outputs of query j (numpy dict) with one oracle trace."""
+def compare_query(rep, trace, gpu, j, k, n, check_sc=True, check_topk=True):
+    """Compare GPU debug outputs of query j (numpy dict) with one oracle trace (the top k
+    too unless check_topk is False)."""
     rep.queries += 1
     ns = len(trace.probed)
     all_sets_equal = True
@@ -57,7 +80,8 @@ def compare_query(rep, trace, gpu, j, k, n, check_sc=True):
     assert np.array_equal(gpu["collision_num"][j], trace.collision_num), (j, gpu["collision_num"][j], trace.collision_num)
     assert int(gpu["last_collision"][j]) == trace.last_collision, j
     assert int(gpu["candidate_num"][j]) == trace.candidate_num, j
-    compare_topk(rep, trace.ids, trace.dists, trace.kth_margin, gpu["ids"][j], gpu["dists"][j], k)
+    if check_topk:
+        compare_topk(rep, trace.ids, trace.dists, trace.kth_margin, gpu["ids"][j], gpu["dists"][j], k)
 
 
 def compare_topk(rep, o_ids, o_dists, kth_margin, g_ids, g_dists, k):

@@ -119,3 +119,59 @@ def test_option_constants_match_header():
     assert set(opts) == {"OPT_CODES_FALLBACK", "OPT_SLABS_PER_RANGE", "OPT_COUNT_WARPS", "OPT_WALK_UNROLL"}
     for name, val in opts.items():
         assert getattr(T, name) == int(val), name
+
+
+# ------------------------------------------------ search_noalloc: buffers checked before the call
+def _noalloc_bufs(torch, nq=4, d=8, ks=5):
+    return (torch.zeros((nq, d), dtype=torch.float32), torch.zeros((nq, ks), dtype=torch.int64),
+            torch.zeros((nq, ks), dtype=torch.float32))
+
+
+@pytest.mark.parametrize("case", ["queries_dtype", "queries_cols", "queries_noncontig",
+                                  "ids_dtype", "dists_dtype", "ids_short", "shape_mismatch",
+                                  "ids_1d", "not_tensor", "not_cuda"])
+def test_noalloc_rejects_bad_buffers(case):
+    """Every buffer search_noalloc hands to the entry point is checked before any library call:
+    a wrong dtype, a short or mis-shaped output or a non-contiguous or host tensor raises
+    ValueError (the entry point would otherwise read or write through the raw pointer)."""
+    torch = pytest.importorskip("torch")
+    q, ids, dists = _noalloc_bufs(torch)
+    msg = {"queries_dtype": "queries must be", "queries_cols": "columns",
+           "queries_noncontig": "contiguous", "ids_dtype": "out_ids must be",
+           "dists_dtype": "out_dists must be", "ids_short": "rows for",
+           "shape_mismatch": "differ", "ids_1d": "2-D", "not_tensor": "torch tensor",
+           "not_cuda": "CUDA"}[case]
+    d = 8
+    if case == "queries_dtype":
+        q = q.half()
+    elif case == "queries_cols":
+        d = 9
+    elif case == "queries_noncontig":
+        q = torch.zeros((8, 4), dtype=torch.float32).t()
+    elif case == "ids_dtype":
+        ids = ids.int()
+    elif case == "dists_dtype":
+        dists = dists.double()
+    elif case == "ids_short":
+        ids, dists = ids[:3], dists[:3]
+    elif case == "shape_mismatch":
+        dists = torch.zeros((4, 6), dtype=torch.float32)
+    elif case == "ids_1d":
+        ids = ids.reshape(-1)
+    elif case == "not_tensor":
+        q = q.numpy()
+    with pytest.raises(ValueError) as err:
+        T.check_noalloc_args(q, ids, dists, d)
+    assert msg in str(err.value)
+
+
+def test_noalloc_method_checks_before_calling(monkeypatch):
+    """TacoIndex.search_noalloc runs the check before it touches the library."""
+    torch = pytest.importorskip("torch")
+    ix = T.TacoIndex(None)
+    monkeypatch.setattr(ix, "info", lambda: {"d": 8})
+    monkeypatch.setattr(T, "load_library", lambda: pytest.fail("library called"))
+    q, ids, dists = _noalloc_bufs(torch)
+    with pytest.raises(ValueError):
+        ix.search_noalloc(q, ids.int(), dists, 5, 10, 1)
+    ix._h = None

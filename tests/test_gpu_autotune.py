@@ -8,7 +8,7 @@ import pytest
 
 from oracle import taco_oracle as O
 from synth import budget_from_alpha, target_from_beta
-from tests.parity_util import ParityReport, compare_query, to_numpy
+from tests.parity_util import ParityReport, check_exclusions, compare_query, to_numpy
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,7 @@ def _parity(ix, oix, data, queries, k, b, t):
     rep = ParityReport()
     for j, qq in enumerate(queries):
         compare_query(rep, O.search_one(oix, data, qq, k, b, t), dbg, j, k, oix.n)
-    assert rep.excluded_queries <= 0.25 * rep.queries, rep
+    check_exclusions(rep, f"autotune k={k} b={b} t={t}")
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])

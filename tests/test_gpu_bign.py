@@ -12,7 +12,7 @@ import pytest
 
 from oracle import taco_oracle as O
 from synth import budget_from_alpha, make_workload, target_from_beta
-from tests.parity_util import ParityReport, compare_query, to_numpy
+from tests.parity_util import ParityReport, check_exclusions, compare_query, to_numpy
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -31,7 +31,7 @@ def _check(ix, oix, data, queries, k, b, t, **kw):
     rep = ParityReport()
     for j, qq in enumerate(queries):
         compare_query(rep, O.search_one(oix, data, qq, k, b, t), dbg, j, k, oix.n)
-    assert rep.excluded_queries <= 0.25 * rep.queries, rep
+    check_exclusions(rep, f"codes fallback k={k} b={b} t={t}")
     assert ix.device_status() == 0
     return dbg
 

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import taco_oracle as O
 from synth import budget_from_alpha, make_workload, target_from_beta
-from tests.parity_util import ParityReport, compare_query, compare_topk, to_numpy
+from tests.parity_util import ParityReport, check_exclusions, compare_query, to_numpy
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,13 +36,12 @@ def _run(ix, oix, data, queries, k, budget, target, rule="literal", per_query=No
     return to_numpy(dbg)
 
 
-def _check_all(oix, data, queries, gpu, k, budget, target, rule="literal", max_excl=0.25):
+def _check_all(oix, data, queries, gpu, k, budget, target, name, rule="literal"):
     rep = ParityReport()
     for j, q in enumerate(queries):
         t = O.search_one(oix, data, q, k, budget, target, rule)
         compare_query(rep, t, gpu, j, k, oix.n)
-    assert rep.excluded_queries <= max_excl * max(rep.queries, 1), rep
-    return rep
+    return check_exclusions(rep, name)
 
 
 # ------------------------------------------------------------------ tiny workload (20k x 128)
@@ -62,8 +61,7 @@ def test_tiny_parity_all_intermediates(tiny):
     qt = O.transform(queries, oix.o_bar, oix.B)
     scale = np.abs(qt).max()
     assert np.abs(gpu["query_t"] - qt).max() <= 1e-5 * scale
-    rep = _check_all(oix, data, queries, gpu, w.k, w.budget, w.rerank_target)
-    print(rep)
+    _check_all(oix, data, queries, gpu, w.k, w.budget, w.rerank_target, "tiny all intermediates")
 
 
 @pytest.mark.parametrize("rule", ["literal", "prose"])
@@ -78,7 +76,7 @@ def test_tiny_parity_budget_grid(tiny, rule, alpha, beta):
         tr = O.search_one(oix, data, q, 10, b, t, rule)
         big += tr.n_candidates > 4096
         compare_query(rep, tr, gpu, j, 10, oix.n)
-    assert rep.excluded_queries <= 10, rep
+    check_exclusions(rep, f"tiny grid {rule} alpha={alpha} beta={beta}")
     if alpha == 0.5:
         assert big > 0   # exercises the path for more candidates than one buffer holds
 
@@ -91,7 +89,7 @@ def test_tiny_parity_k(tiny, k):
     for j, q in enumerate(queries[:20]):
         compare_query(rep, O.search_one(oix, data, q, k, w.budget, 2000), gpu, j, k, oix.n,
                       check_sc=False)
-    assert rep.excluded_queries <= 5, rep
+    check_exclusions(rep, f"tiny k={k}")
 
 
 def test_full_budget_is_exact_knn(tiny):
@@ -129,18 +127,17 @@ def test_per_query_uneven_batch(tiny):
                        rerank_target=int(rng.choice([50, 200, 1000]))))
     kmax = max(p["k"] for p in pq)
     q = torch.from_numpy(queries[:24]).cuda()
-    ids, dists = ix.search(q, 10, 1000, 200, per_query=pq, k_stride=kmax)
-    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    gpu = to_numpy(ix.search_debug(q, 10, 1000, 200, per_query=pq, k_stride=kmax))
+    ids = gpu["ids"]
     rep = ParityReport()
     for j, p in enumerate(pq):
         t = O.search_one(oix, data, queries[j], p["k"], p["budget"], p["rerank_target"])
-        if min(t.probe_margin) < 1e-5:
-            continue
-        compare_topk(rep, t.ids, t.dists, t.kth_margin, ids[j], dists[j], p["k"])
+        compare_query(rep, t, gpu, j, p["k"], oix.n)
         assert np.all(ids[j, p["k"]:] == -1)
         # the same query alone gives the same answer
         a_ids, _ = ix.search(q[j:j + 1], p["k"], p["budget"], p["rerank_target"])
         assert np.array_equal(a_ids.cpu().numpy()[0], ids[j, :p["k"]])
+    check_exclusions(rep, "tiny uneven batch")
 
 
 def test_per_query_uneven_bf16_batch_equals_alone(tiny):
@@ -224,7 +221,7 @@ def ragged():
 def test_ragged_parity(ragged, budget, target, k):
     data, queries, oix, ix = ragged
     gpu = _run(ix, oix, data, queries, k, budget, target)
-    _check_all(oix, data, queries, gpu, k, budget, target)
+    _check_all(oix, data, queries, gpu, k, budget, target, f"ragged budget={budget} target={target} k={k}")
 
 
 # --------------------------------------------------- several slabs: a cluster of CTAs per query
@@ -248,7 +245,7 @@ def test_multislab_parity(multislab, k):
     assert info["cluster_size"] > 1 and info["n_slabs"] == 10
     b, t = budget_from_alpha(0.05, oix.n), target_from_beta(0.01, oix.n)
     gpu = _run(ix, oix, data, queries, k, b, t)
-    _check_all(oix, data, queries, gpu, k, b, t)
+    _check_all(oix, data, queries, gpu, k, b, t, f"multislab k={k}")
 
 
 def test_multislab_all_points(multislab):
@@ -268,14 +265,11 @@ def test_bf16_integer_data_matches_oracle():
     ix = _import(oix, data)
     b, t = budget_from_alpha(0.05, oix.n), target_from_beta(0.01, oix.n)
     q = torch.from_numpy(queries).cuda()
-    ids, dists = ix.search(q, 10, b, t, precision="bf16", shortlist_mult=4)
-    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    gpu = to_numpy(ix.search_debug(q, 10, b, t, precision="bf16", shortlist_mult=4))
     rep = ParityReport()
     for j in range(len(queries)):
-        tr = O.search_one(oix, data, queries[j], 10, b, t)
-        if min(tr.probe_margin) < 1e-5:
-            continue
-        compare_topk(rep, tr.ids, tr.dists, tr.kth_margin, ids[j], dists[j], 10)
+        compare_query(rep, O.search_one(oix, data, queries[j], 10, b, t), gpu, j, 10, oix.n)
+    check_exclusions(rep, "bf16 on integer data")
     ix.close()
 
 
@@ -314,16 +308,15 @@ def test_fp8_shortlist_covering_the_candidates_matches_oracle(tiny, tiny_fp8):
     assert info["has_fp8"] == 1 and info["fp8_pitch"] % 16 == 0 and info["has_bf16"] == 0
     b, t = w.budget, 100
     q = torch.from_numpy(queries).cuda()
-    ids, dists = ix.search(q, 10, b, t, precision="fp8", shortlist_mult=51)   # 510 >= |C|
-    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    gpu = to_numpy(ix.search_debug(q, 10, b, t, precision="fp8", shortlist_mult=51))   # 510
     rep = ParityReport()
     used = 0
     for j in range(len(queries)):
         tr = O.search_one(oix, data, queries[j], 10, b, t)
-        if min(tr.probe_margin) < 1e-5 or tr.candidate_num > 510:
-            continue
-        used += 1
-        compare_topk(rep, tr.ids, tr.dists, tr.kth_margin, ids[j], dists[j], 10)
+        covered = tr.candidate_num <= 510   # the shortlist holds all of C
+        used += covered
+        compare_query(rep, tr, gpu, j, 10, oix.n, check_topk=covered)
+    check_exclusions(rep, "fp8 shortlist covering C")
     assert used >= len(queries) // 2, used
 
 
