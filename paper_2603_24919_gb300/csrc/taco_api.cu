@@ -68,10 +68,11 @@ int check_geometry(int64_t n, int d, int Ns, int s, int sk) {
         return fail(TACO_EINVAL, "n_subspaces = %d must be in [1, %d]", Ns, TACO_MAX_SUBSPACES);
     if (s < 2) return fail(TACO_EINVAL, "sub_dim = %d must be >= 2", s);
     if (int64_t(Ns) * s > d) return fail(TACO_EINVAL, "n_subspaces * sub_dim > d");
-    if (int64_t(Ns) * n >= (int64_t(1) << 32))
-        return fail(TACO_ECAPACITY, "n_subspaces * n must be below 2^32 (32-bit id-list offsets)");
     if (sk < 1 || sk > TACO_MAX_SQRT_K)
         return fail(TACO_EINVAL, "sqrt_k = %d must be in [1, %d]", sk, TACO_MAX_SQRT_K);
+    // the padded cell lists of all subspaces (at most 3 pad ids per cell) take 32-bit offsets
+    if (int64_t(Ns) * (n + 3 * int64_t(sk) * sk) >= (int64_t(1) << 32))
+        return fail(TACO_ECAPACITY, "n_subspaces * (n + 3 K) must be below 2^32 (32-bit id-list offsets)");
     return TACO_OK;
 }
 
@@ -184,7 +185,11 @@ int finish_index(taco_index* ix, int keep_rows, cudaStream_t st) {
     const int Ns = ix->Ns, K = ix->K;
     TRY(configure_search(ix));
     const int ns1 = ix->n_slabs + 1;
-    std::vector<uint32_t> sizes(size_t(Ns) * K, 0), ids(size_t(Ns) * n), split(size_t(Ns) * K * ns1);
+    // Cell lists of all subspaces in one array: subspace after subspace, cell after cell, each
+    // list starting on a 16-byte boundary (a multiple of 4 ids) and padded to the next one with
+    // kIdPad, so the counting walk reads any run of a list in aligned 4-id chunks. The split
+    // table holds absolute positions in that array.
+    std::vector<uint32_t> sizes(size_t(Ns) * K, 0), split(size_t(Ns) * K * ns1);
     for (int i = 0; i < Ns; ++i) {
         const uint16_t* code = ix->codes.data() + size_t(i) * n;
         uint32_t* sz = sizes.data() + size_t(i) * K;
@@ -192,22 +197,26 @@ int finish_index(taco_index* ix, int keep_rows, cudaStream_t st) {
             if (code[p] >= K) return fail(TACO_EINVAL, "code %d of point %lld >= K", int(code[p]), (long long)p);
             ++sz[code[p]];
         }
-        std::vector<uint32_t> start(K + 1, 0);
-        for (int c = 0; c < K; ++c) start[c + 1] = start[c] + sz[c];
-        std::vector<uint32_t> cur(start.begin(), start.end() - 1);
-        uint32_t* idl = ids.data() + size_t(i) * n;
-        for (int64_t p = 0; p < n; ++p) idl[cur[code[p]]++] = uint32_t(p);  // ascending ids
+    }
+    std::vector<uint32_t> cstart(size_t(Ns) * K + 1, 0);
+    for (size_t j = 0; j < size_t(Ns) * K; ++j) cstart[j + 1] = cstart[j] + ((sizes[j] + 3u) & ~3u);
+    std::vector<uint32_t> ids(cstart.back(), kIdPad);
+    for (int i = 0; i < Ns; ++i) {
+        const uint16_t* code = ix->codes.data() + size_t(i) * n;
+        std::vector<uint32_t> cur(cstart.begin() + size_t(i) * K, cstart.begin() + size_t(i + 1) * K);
+        for (int64_t p = 0; p < n; ++p) ids[cur[code[p]]++] = uint32_t(p);  // ascending ids
         uint32_t* sp = split.data() + size_t(i) * K * ns1;
         for (int c = 0; c < K; ++c) {
-            const uint32_t* b = idl + start[c];
-            const uint32_t* e = idl + start[c + 1];
+            const size_t j = size_t(i) * K + c;
+            const uint32_t* b = ids.data() + cstart[j];
+            const uint32_t* e = b + sizes[j];
             for (int sl = 0; sl < ns1; ++sl) {
                 const int64_t bound = std::min<int64_t>(int64_t(sl) << kSlabLog2, n);
-                sp[size_t(c) * ns1 + sl] =
-                    uint32_t(std::lower_bound(b, e, uint32_t(bound)) - idl);
+                sp[size_t(c) * ns1 + sl] = uint32_t(std::lower_bound(b, e, uint32_t(bound)) - ids.data());
             }
         }
     }
+    ix->n_ids = int64_t(ids.size());
     TRY(dev_alloc(&ix->d_sizes, sizes.size(), &ix->device_bytes));
     TRY(dev_alloc(&ix->d_ids, ids.size(), &ix->device_bytes));
     TRY(dev_alloc(&ix->d_split, split.size(), &ix->device_bytes));
@@ -821,7 +830,7 @@ int taco_index_set_option(taco_index* ix, int32_t option, int32_t value) {
             ix->tp_count_warps = value;
             return TACO_OK;
         case TACO_OPT_WALK_UNROLL:
-            if (value != 8 && value != 16) return fail(TACO_EINVAL, "walk unroll %d: 8 or 16", value);
+            if (value != 4 && value != 8) return fail(TACO_EINVAL, "walk unroll %d: 4 or 8", value);
             ix->tp_walk_unroll = value;
             return TACO_OK;
         default: return fail(TACO_EINVAL, "unknown option %d", option);

@@ -1,0 +1,319 @@
+// Collision counting of the two-pass search (Alg. 6 step 7, Def. 6), pass 1.
+//
+// Persistent CTAs take queries and, for each, its id ranges in turn (a (query, range) pair is
+// a unit). A unit's collisions are counted in 4-bit shared-memory counters; the ids whose
+// count reaches 2 are listed once, and after the walk every listed id is tagged with its
+// final count (its SC-score) and written to the unit's fixed arena slot, together with the
+// unit's level counts ge[j] = #{ids of the range with SC >= j}. Pass 2 (select_rerank_kernel)
+// sums the level counts of a query's ranges, applies Alg. 5 and re-ranks the listed ids with
+// SC >= last_collision. Queries whose threshold falls below 2, or whose lists do not fit,
+// are flagged for a fallback.
+//
+// The cell lists are stored 16-byte aligned and padded to a multiple of 4 ids (with kIdPad),
+// so the run of a probed cell that falls in the unit's id range is covered by whole 4-id
+// chunks of its own list: the walk loads one chunk (uint4) per lane and keeps the ids that
+// lie in the range (the chunk's other ids belong to the same cell's neighbouring ranges, or
+// are padding, and fail the range test).
+#pragma once
+
+#include "taco_rerank.cuh"
+
+namespace taco {
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+
+constexpr int kChunkListCap = 4096;   // ids that reached SC = 2 in a unit (listed once each)
+
+// Shared memory of count_lists_kernel past the counters (bytes): split bounds of the staged
+// cells for two ranges, the level list, the staged chunk runs, the exact-level histogram
+// and the staged cells.
+constexpr size_t kCountListsExtra = size_t(2) * kCellBatch * 8 + size_t(kChunkListCap) * 4 +
+                                    size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 16 * 4 +
+                                    size_t(kCellBatch) * 4;
+
+// The chunk run of id positions [b, e) of one cell list: chunks [b / 4, ceil(e / 4)), none
+// when the run is empty. Cell lists start on chunk boundaries, so the chunks stay inside the
+// cell's padded list.
+__device__ __forceinline__ void chunk_run(uint32_t b, uint32_t e, uint32_t& start, uint32_t& len) {
+    start = b >> 2;
+    len = e > b ? ((e + 3u) >> 2) - start : 0u;
+}
+
+// Walk one staged batch of chunk runs (total chunks in nr non-empty runs; run r covers
+// chunks rbase[r] + [cpre[r], cpre[r + 1]) of the id array). Every id of a chunk that lies in
+// the unit's range [lo, lo + rlen) adds 1 to its 4-bit counter; the shared-memory atomic's
+// old value tells when an id reaches 2, and such an id is appended (relative to lo) to the
+// level list, once. The concatenated chunks are walked in rounds of WU windows of 32 chunks
+// (one chunk per lane and window, WU loads of 16 bytes in flight per lane), round g by warp
+// g mod NW. Lane u finds the run of the first chunk of window u (binary search); in a window,
+// lane j reads the j-th next run boundary, the boundaries inside the window form a bit mask,
+// and a lane's run is the window's first run plus the mask bits at or below it (runs are
+// non-empty, so at most 32 boundaries fall in a window). Lanes past the end load a valid
+// chunk and count nothing. Appends beyond kChunkListCap are dropped (the caller sees the
+// overflow in *s_app). Warp-level; no barrier.
+template <int NW, int WU>
+__device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint32_t last_chunk, uint32_t lo,
+                                            uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
+                                            uint32_t* lst, uint32_t* s_app, const uint32_t* cpre,
+                                            const uint32_t* rbase, uint64_t pol, int lane, int warp) {
+    static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU list bits a lane");
+    const uint32_t lane_le = (2u << lane) - 1u;   // lanes 0..lane
+    constexpr uint32_t kRound = 32u * WU;
+    const uint32_t nrounds = (total + kRound - 1) / kRound;
+    for (uint32_t g = uint32_t(warp); g < nrounds; g += NW) {   // warp-uniform
+        const uint32_t e0 = g * kRound;
+        const uint32_t key = min(e0 + 32u * uint32_t(lane % WU), total - 1u);
+        const uint32_t cwl = uint32_t(find_cell(cpre, int(nr), key));
+        uint4 v[WU];
+        uint32_t live = 0;   // bit u: this lane's chunk of window u is inside the batch
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+            const uint32_t E = e0 + 32u * uint32_t(u);
+            const uint32_t cw = __shfl_sync(kFull, cwl, u);
+            const uint32_t pb = cpre[cw + 1u + uint32_t(lane)] - E;                 // >= 1 inside
+            const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));     // 0 for pb >= 32
+            const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
+            const uint32_t x = min(rbase[r] + E + uint32_t(lane), last_chunk);
+            v[u] = ldg_keep_u4(ids4 + x, pol);
+            live |= (E + uint32_t(lane) < total ? 1u : 0u) << u;
+        }
+        // count: all atomics of the round are independent; an id whose old count is 1 has
+        // just reached 2 and is kept (relative to lo) for the list
+        uint32_t amask = 0;
+        uint32_t rel[WU][4];
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+            const uint32_t w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const uint32_t x = w4[h] - lo;
+                const bool ok = ((live >> u) & 1u) && x < rlen;
+                const uint32_t sh = (x & 7u) << 2;
+                uint32_t old = 0;
+                if (ok) old = atomicAdd(&cnt[x >> 3], 1u << sh);
+                amask |= (((old >> sh) & 15u) == 1u ? 1u : 0u) << (4 * u + h);
+                rel[u][h] = x;
+            }
+        }
+        // append the ids that reached 2: one reservation per warp and round
+        if (__any_sync(kFull, amask != 0u)) {
+            const uint32_t na = __popc(amask);
+            uint32_t incl = na;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += t;
+            }
+            const uint32_t tot = __shfl_sync(kFull, incl, 31);
+            uint32_t base = 0;
+            if (lane == 31) base = atomicAdd(s_app, tot);
+            uint32_t pos = __shfl_sync(kFull, base, 31) + incl - na;
+#pragma unroll
+            for (int u = 0; u < WU; ++u)
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                    if ((amask >> (4 * u + h)) & 1u) {
+                        if (pos < uint32_t(kChunkListCap)) lst[pos] = rel[u][h];
+                        ++pos;
+                    }
+        }
+    }
+}
+
+// ge[2..N_s] from the counters themselves (SWAR compare of the eight nibbles of a word against
+// each level), for a unit whose list overflowed. Block-wide over the counter words; adds into
+// ge; no barrier.
+template <int NW>
+__device__ __forceinline__ void ge_from_counters(int Ns, int words, const uint32_t* cnt, uint32_t* ge, int tid,
+                                                 int lane) {
+    uint32_t gel[TACO_MAX_SUBSPACES];
+#pragma unroll
+    for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
+    for (int w = tid; w < words; w += NW * 32) {
+        const uint32_t x = cnt[w];
+        if (x == 0u) continue;
+        const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
+#pragma unroll
+        for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+            if (j <= Ns) {
+                const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
+                gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
+        if (j <= Ns) {
+            const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
+            if (lane == 0 && v) atomicAdd(&ge[j], v);
+        }
+    }
+}
+
+// NW warps per CTA, WU windows of 32 chunks per walk round.
+template <int NW, int WU>
+__global__ void __launch_bounds__(NW * 32, (NW == 16 && WU <= 4) ? 2 : 1)
+count_lists_kernel(const RerankParams P) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
+    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);      // kChunkListCap
+    uint32_t* rbase = lst + kChunkListCap;                                    // kCellBatch
+    uint32_t* cpre = rbase + kCellBatch;                                      // kCellBatch + kRunPad
+    uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
+    uint32_t* qcell = ge + 16;                                                // kCellBatch
+    __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
+    __shared__ uint32_t s_tmp[2 * NW];
+    __shared__ uint32_t s_app, s_outn, s_ev;
+    __shared__ uint32_t s_h[16];   // ids of the unit with SC exactly s (s >= 2), from the list
+    const int Ns = P.Ns, K = P.K;
+    const int sstride = P.n_slabs + 1;
+    const uint64_t pol_keep = l2_policy_keep();
+    const uint4* ids4 = reinterpret_cast<const uint4*>(P.ids);
+    const uint32_t last_chunk = uint32_t(P.n_ids / 4) - 1u;
+    for (int w = tid; w < P.counter_words; w += NW * 32) cnt[w] = 0u;
+    // the split bounds of every staged cell for range r, into pairs[buf] (asynchronous)
+    auto prefetch = [&](int total_cells, int r, int buf) {
+        const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
+        for (int t = tid; t < total_cells; t += NW * 32) {
+            const uint32_t qc = qcell[t];
+            const uint32_t* sp = P.split + (size_t(qc >> 16) * K + (qc & 0xffffu)) * sstride;
+            cp_async4(&pairs[buf * kCellBatch + t].x, sp + slo);
+            cp_async4(&pairs[buf * kCellBatch + t].y, sp + shi);
+        }
+        cp_async_commit();
+    };
+    // stage the chunk runs of id positions [b, e) (one per thread, e = b when none), add the
+    // ids they hold in the range to s_ev, and walk them
+    auto stage_and_walk = [&](uint32_t b, uint32_t e, uint32_t lo, uint32_t rlen) {
+        uint32_t start, len;
+        chunk_run(b, e, start, len);
+        const uint32_t ev = __reduce_add_sync(kFull, e - b);
+        if (lane == 0 && ev) atomicAdd(&s_ev, ev);
+        const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
+        if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, lo, rlen, st.x, st.y, cnt, lst, &s_app, cpre, rbase,
+                                      pol_keep, lane, warp);
+    };
+    for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+        __syncthreads();   // the previous query is finished with the shared state
+        if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
+        __syncthreads();
+        const int total_cells = s_pre[Ns];
+        const bool staged = total_cells <= kCellBatch;   // one batch: cells kept for every range
+        if (staged) {
+            for (int t = tid; t < total_cells; t += NW * 32) {
+                int i = 0;
+                while (t >= s_pre[i + 1]) ++i;
+                qcell[t] = (uint32_t(i) << 16) | P.cells[(q * Ns + i) * K + (t - s_pre[i])];
+            }
+            __syncthreads();
+            prefetch(total_cells, 0, 0);
+        }
+        for (int r = 0; r < P.n_ranges; ++r) {
+            const int64_t u = q * P.n_ranges + r;
+            const int slab_lo = r * P.slabs_per_cta;
+            const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
+            const int64_t lo = int64_t(slab_lo) << kSlabLog2;
+            const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
+            const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
+            const uint32_t rlen = uint32_t(hi - lo);
+            if (tid < 16) {
+                ge[tid] = 0u;
+                s_h[tid] = 0u;
+            }
+            if (tid == 0) {
+                s_app = 0u;
+                s_outn = 0u;
+                s_ev = 0u;
+            }
+            if (staged) {
+                cp_async_wait_all();
+                __syncthreads();   // this range's bounds are in pairs[r & 1]
+                if (r + 1 < P.n_ranges) prefetch(total_cells, r + 1, (r + 1) & 1);
+                uint32_t b = 0, e = 0;
+                if (tid < total_cells) {
+                    const uint2 be = pairs[(r & 1) * kCellBatch + tid];
+                    b = be.x;
+                    e = be.y;
+                }
+                stage_and_walk(b, e, uint32_t(lo), rlen);
+            } else {
+                for (int cb0 = 0; cb0 < total_cells; cb0 += kCellBatch) {
+                    __syncthreads();   // the staging of the previous batch is walked
+                    uint32_t b = 0, e = 0;
+                    const int g = cb0 + tid;
+                    if (tid < kCellBatch && g < total_cells) {
+                        int i = 0;
+                        while (g >= s_pre[i + 1]) ++i;
+                        const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
+                        const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
+                        b = ldg_keep_u32(sp + slab_lo, pol_keep);
+                        e = ldg_keep_u32(sp + slab_hi, pol_keep);
+                    }
+                    stage_and_walk(b, e, uint32_t(lo), rlen);
+                }
+            }
+            __syncthreads();   // the range's counters and level list are final
+            if (P.dbg_sc) debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
+            // every listed id has SC >= 2 and is listed once: its final count is its level;
+            // the histogram of levels and the tagged entries in the unit's arena slot
+            const uint32_t nlist = s_app;
+            const bool overflow = nlist > uint32_t(kChunkListCap);
+            if (!overflow) {
+                uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
+                const uint32_t lane_lt = (1u << lane) - 1u;
+                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += NW * 32) {
+                    const uint32_t e = e0 + uint32_t(lane);
+                    const uint32_t id = e < nlist ? lst[e] : 0u;
+                    const uint32_t level = e < nlist ? (cnt[id >> 3] >> ((id & 7u) << 2)) & 15u : 0u;
+                    const unsigned grp = __match_any_sync(kFull, level);
+                    if (level != 0u && (grp & lane_lt) == 0u) atomicAdd(&s_h[level], uint32_t(__popc(grp)));
+                    const uint32_t at = warp_append_slot(level != 0u, &s_outn, lane);
+                    if (level != 0u && at < P.arena_per_unit) out[at] = id | (level << kLevelShift);
+                }
+            } else {
+                ge_from_counters<NW>(Ns, words, cnt, ge, tid, lane);
+            }
+            __syncthreads();   // s_h / ge and the counters are read; the counters may be cleared
+            if (tid == 0) {
+                // ge[j] = ids with SC >= j; ids with SC = s contribute s - 1 events beyond
+                // their first, so ge[1] = events - sum_{j >= 2} ge[j]
+                if (!overflow) {
+                    uint32_t acc = 0;
+                    for (int j = Ns; j >= 2; --j) {
+                        acc += s_h[j];
+                        ge[j] = acc;
+                    }
+                }
+                uint32_t extra = 0;
+                for (int j = 2; j <= Ns; ++j) extra += ge[j];
+                ge[1] = s_ev - extra;
+                const uint32_t need = ge[2];
+                const bool fits = !overflow && need <= P.arena_per_unit;
+                P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
+                P.unit_len[u] = fits ? need : 0u;
+                if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the fallback
+            }
+            uint4* c4 = reinterpret_cast<uint4*>(cnt);
+            for (int w = tid; w < (words + 3) / 4; w += NW * 32) c4[w] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
+        }
+    }
+}
+
+}  // namespace taco

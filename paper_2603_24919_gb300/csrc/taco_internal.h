@@ -27,6 +27,9 @@ constexpr int64_t kQueryChunk = 16384;
 constexpr int kListsPerCta = 16;
 // List entries (ids with SC >= 2) reserved per counter slab of a (query, id range) unit.
 constexpr size_t kArenaPerSlab = 512;
+// Fill of the id-list padding (a cell's list is padded to a multiple of 4 ids); above every
+// point id, so a range test rejects it.
+constexpr uint32_t kIdPad = 0xffffffffu;
 
 struct QueryParamsDev {
     int32_t k;
@@ -90,7 +93,7 @@ struct taco_index {
     int tp_lanes[3] = {0, 0, 0};          // lanes per row of the re-rank per row kind (0: auto)
     int tp_walk = -1;                     // probe by row-merge walk: -1 auto, 0 never, 1 when it fits
     int tp_count_warps = 16;              // warps per CTA of the counting pass (16 or 32)
-    int tp_walk_unroll = 8;               // windows of 32 ids per round of its walk (8 or 16)
+    int tp_walk_unroll = 4;               // windows of 32 four-id chunks per round of its walk (4 or 8)
     // Fallback for flagged queries: the cluster kernel (all counters of a query in one
     // cluster's shared memory) or, when n is too large for that (cluster == 0) or when
     // chosen (taco_index_set_option), the codes fallback of select_rerank_kernel.
@@ -115,8 +118,9 @@ struct taco_index {
     float* d_B = nullptr;               // [d][Dp]
     float* d_cent = nullptr;            // [Ns][sk][s]
     uint32_t* d_sizes = nullptr;        // [Ns][K]
-    uint32_t* d_ids = nullptr;          // [Ns][n]
-    uint32_t* d_split = nullptr;        // [Ns][K][n_slabs + 1]
+    uint32_t* d_ids = nullptr;          // [n_ids]: cell lists, each 16-byte aligned and padded
+    uint32_t* d_split = nullptr;        // [Ns][K][n_slabs + 1] absolute positions in d_ids
+    int64_t n_ids = 0;                  // length of d_ids (N_s n plus the padding)
     int64_t device_bytes = 0;
     std::mutex ws_mu;
     taco::Workspace ws;

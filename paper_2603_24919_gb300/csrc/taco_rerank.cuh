@@ -54,8 +54,9 @@ struct RerankParams {
     const float* obar;         // [d] data mean (FP8 rows of the centred points)
     int Dp, dp8;
     int fp8_space;             // 0: FP8 rows of B^T (o - o_bar), 1: of o - o_bar
-    const uint32_t* ids;    // [Ns][n]
-    const uint32_t* split;  // [Ns][K][n_slabs+1]
+    const uint32_t* ids;    // [n_ids] cell lists (16-byte aligned, padded with kIdPad)
+    const uint32_t* split;  // [Ns][K][n_slabs+1] absolute positions in ids
+    int64_t n_ids;
     const uint16_t* cells;  // [nq][Ns][K]
     const int32_t* ncells;  // [nq][Ns]
     const QueryParamsDev* params;
@@ -348,8 +349,8 @@ __device__ __forceinline__ uint2 stage_runs(uint32_t start, uint32_t len, uint32
 
 // Stage the non-empty id runs of probed cells [cb0, cb0 + nb) of query q that fall in slabs
 // [slab_lo, slab_hi), in cell order. Element e of the concatenation lies in run r with
-// cpre[r] <= e < cpre[r + 1]; its id-array index is rbase[r] + e (uint32 arithmetic,
-// N_s * n < 2^32). cpre[nr] = total and cpre[nr + 1 .. nr + 32] = 0xffffffff. Returns
+// cpre[r] <= e < cpre[r + 1]; its id-array index is rbase[r] + e (uint32 arithmetic:
+// the id array holds fewer than 2^32 entries). cpre[nr] = total and cpre[nr + 1 .. nr + 32] = 0xffffffff. Returns
 // (total, nr). Block-wide; ends with a barrier.
 template <int NW = kRrWarps>   // warps of the block
 __device__ __forceinline__ uint2 stage_cells(const RerankParams& P, int64_t q, const int* s_pre,
@@ -367,7 +368,7 @@ __device__ __forceinline__ uint2 stage_cells(const RerankParams& P, int64_t q, c
         const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
         const uint32_t* sp = P.split + (size_t(i) * K + cell) * sstride;
         const uint32_t b = ldg_keep_u32(sp + slab_lo, keep), e = ldg_keep_u32(sp + slab_hi, keep);
-        start = uint32_t(i) * uint32_t(P.n) + b;
+        start = b;   // absolute position in the id array
         len = e - b;
     }
     return stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
@@ -480,7 +481,7 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
                                            const CountSmem& sm, uint64_t pol_keep, int lane, int warp) {
     static_assert(WU >= 1 && WU <= 32, "one lane finds the run of each window of a round");
     const uint32_t lane_le = (2u << lane) - 1u;  // lanes 0..lane
-    const uint32_t last_idx = uint32_t(P.Ns) * uint32_t(P.n) - 1u;
+    const uint32_t last_idx = uint32_t(P.n_ids) - 1u;
     constexpr uint32_t kRound = 32u * WU;
     const uint32_t nrounds = (total + kRound - 1) / kRound;
     for (uint32_t g = uint32_t(warp); g < nrounds; g += NW) {   // warp-uniform
@@ -883,150 +884,13 @@ count_select_rerank_kernel(const RerankParams P) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Two-pass form. Pass 1 (count_lists_kernel): persistent CTAs take queries and, for each,
-// its id ranges in turn (a (query, range) pair is a unit); a unit's collisions are counted
-// in shared memory and the unit's level counts and the compact list of its ids with
-// SC >= 2 (id relative to the range | SC << 27) go to global memory, the list into the
-// unit's fixed arena slot of arena_per_unit entries. Pass 2 (select_rerank_kernel): one CTA
-// per query sums the level counts of its ranges, applies Alg. 5, keeps the list entries
-// with SC >= last_collision and re-ranks them. Queries whose threshold falls below 2, or
-// whose lists did not fit, are flagged for the cluster kernel above.
+// Two-pass form. Pass 1 (count_lists_kernel, taco_count.cuh) counts the collisions of each
+// (query, id range) unit and writes the unit's level counts and its ids with SC >= 2 (id
+// relative to the range | SC << 27) to the unit's arena slot. Pass 2 (select_rerank_kernel,
+// below): one CTA per query sums the level counts of its ranges, applies Alg. 5, keeps the
+// arena entries with SC >= last_collision and re-ranks them. Queries whose threshold falls
+// below 2, or whose lists did not fit, are flagged for a fallback.
 // ---------------------------------------------------------------------------------------
-#ifdef TACO_DEFINE_COUNT_LISTS   // defined by the one translation unit that launches it
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Shared memory of count_lists_kernel past the counters (bytes).
-constexpr size_t kCountListsExtra = size_t(2) * kCellBatch * 8 + size_t(kListCap) * 4 + size_t(kCellBatch) * 4 +
-                                    size_t(kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
-
-// NW warps per CTA (16: two CTAs per SM where the counters fit, 32: one); WU windows of 32
-// ids per walk round (16 loads in flight per lane: one CTA of 16 warps per SM, up to 128
-// registers a thread).
-template <int NW, int WU>
-__global__ void __launch_bounds__(NW * 32, (NW == 16 && WU <= kWalkUnroll) ? 2 : 1)
-count_lists_kernel(const RerankParams P) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
-    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
-    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);      // kListCap
-    uint32_t* rbase = lst + kListCap;                                         // kCellBatch
-    uint32_t* cpre = rbase + kCellBatch;                                      // kCellBatch + kRunPad
-    uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
-    uint32_t* qcell = ge + 16;                                                // kCellBatch
-    __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
-    __shared__ uint32_t s_tmp[2 * NW];
-    __shared__ uint32_t s_app, s_outn;
-    CountSmem csm{cnt, lst, rbase, cpre, ge, s_pre, s_tmp, &s_app};
-    const int Ns = P.Ns, K = P.K;
-    const int sstride = P.n_slabs + 1;
-    const uint64_t pol_keep = l2_policy_keep();
-    for (int w = tid; w < P.counter_words; w += (NW * 32)) cnt[w] = 0u;
-    // the split bounds of every staged cell for range r, into pairs[buf] (asynchronous)
-    auto prefetch = [&](int total_cells, int r, int buf) {
-        const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
-        for (int t = tid; t < total_cells; t += (NW * 32)) {
-            const uint32_t qc = qcell[t];
-            const uint32_t* sp = P.split + (size_t(qc >> 16) * K + (qc & 0xffffu)) * sstride;
-            cp_async4(&pairs[buf * kCellBatch + t].x, sp + slo);
-            cp_async4(&pairs[buf * kCellBatch + t].y, sp + shi);
-        }
-        cp_async_commit();
-    };
-    for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
-        __syncthreads();   // the previous query is finished with the shared state
-        if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
-        __syncthreads();
-        const int total_cells = s_pre[Ns];
-        const bool staged = total_cells <= kCellBatch;   // one batch: cells kept for every range
-        if (staged) {
-            for (int t = tid; t < total_cells; t += (NW * 32)) {
-                int i = 0;
-                while (t >= s_pre[i + 1]) ++i;
-                qcell[t] = (uint32_t(i) << 16) | P.cells[(q * Ns + i) * K + (t - s_pre[i])];
-            }
-            __syncthreads();
-            prefetch(total_cells, 0, 0);
-        }
-        for (int r = 0; r < P.n_ranges; ++r) {
-            const int64_t u = q * P.n_ranges + r;
-            const int slab_lo = r * P.slabs_per_cta;
-            const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
-            const int64_t lo = int64_t(slab_lo) << kSlabLog2;
-            const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
-            const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
-            if (tid < 16) ge[tid] = 0u;
-            if (tid == 0) {
-                s_app = 0u;
-                s_outn = 0u;
-            }
-            if (staged) {
-                cp_async_wait_all();
-                __syncthreads();   // this range's bounds are in pairs[r & 1]
-                if (r + 1 < P.n_ranges) prefetch(total_cells, r + 1, (r + 1) & 1);
-                uint32_t start = 0, len = 0;
-                if (tid < total_cells) {
-                    const uint2 be = pairs[(r & 1) * kCellBatch + tid];
-                    start = (qcell[tid] >> 16) * uint32_t(P.n) + be.x;
-                    len = be.y - be.x;
-                }
-                const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-                if (tid == 0 && st.x) atomicAdd(&ge[1], st.x);   // minus the level >= 2 events later
-                walk_batch<NW, WU>(P, lo, st.x, st.y, csm, pol_keep, lane, warp);
-            } else {
-                __syncthreads();
-                count_phase<NW, WU, false>(P, q, slab_lo, slab_hi, lo, words, csm, pol_keep, tid, lane, warp);
-            }
-            __syncthreads();   // the range's counters and level list are final
-            if (P.dbg_sc) debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
-            // One pass over the level list: the level counts ge[2..N_s] (an entry tagged j is
-            // an id that reached level j) and the unit's entries into its fixed arena slot (an
-            // id's final SC is its counter; its entry tagged with that level is unique, so the
-            // slot receives ge[2] entries). Entries past the slot are dropped; the unit is then
-            // marked lost below.
-            const uint32_t nlist = s_app;
-            const bool overflow = nlist > uint32_t(kListCap);
-            if (!overflow) {
-                uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
-                const uint32_t lane_lt = (1u << lane) - 1u;
-                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += (NW * 32)) {
-                    const uint32_t e = e0 + uint32_t(lane);
-                    const uint32_t x = e < nlist ? lst[e] : 0u;
-                    const uint32_t level = x >> kLevelShift;   // >= 2 for an entry, 0 past the end
-                    // lanes holding the same level form one group, whose lowest lane adds its size
-                    const unsigned grp = __match_any_sync(kFull, level);
-                    if (level != 0u && (grp & lane_lt) == 0u) atomicAdd(&ge[level], uint32_t(__popc(grp)));
-                    const uint32_t id = x & ((1u << kLevelShift) - 1u);
-                    const bool take = level != 0u && level == ((cnt[id >> 3] >> ((id & 7u) << 2)) & 15u);
-                    const uint32_t at = warp_append_slot(take, &s_outn, lane);
-                    if (take && at < P.arena_per_unit) out[at] = x;
-                }
-                if (tid == 0 && nlist) atomicSub(&ge[1], nlist);
-            } else {
-                levels_from_counters<NW>(Ns, words, csm, tid, lane);
-            }
-            __syncthreads();   // ge and the counters are read; the counters may be cleared
-            const uint32_t need = ge[2];
-            const bool fits = !overflow && need <= P.arena_per_unit;
-            if (tid == 0) {
-                P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
-                P.unit_len[u] = fits ? need : 0u;
-                if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the fallback
-            }
-            if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
-            uint4* c4 = reinterpret_cast<uint4*>(cnt);
-            for (int w = tid; w < (words + 3) / 4; w += (NW * 32)) c4[w] = make_uint4(0, 0, 0, 0);
-            __syncthreads();
-        }
-    }
-}
-
-#endif  // TACO_DEFINE_COUNT_LISTS
 
 constexpr int kSrThreads = 256;
 constexpr int kSrWarps = kSrThreads / 32;
@@ -1209,7 +1073,7 @@ select_rerank_kernel(const RerankParams P) {
                         while (g >= s_fpre[i + 1]) ++i;
                         const int c = P.cells[(q * Ns + i) * P.K + (g - s_fpre[i])];
                         const uint32_t* sp = P.split + (size_t(i) * P.K + c) * sstride;
-                        fst[tid] = uint32_t(i) * uint32_t(P.n) + sp[0];
+                        fst[tid] = sp[0];
                         fsub[tid] = uint32_t(i);
                         len = sp[P.n_slabs] - sp[0];
                     }
@@ -1249,25 +1113,47 @@ select_rerank_kernel(const RerankParams P) {
                     }
                 }
             }
-        } else
-        // candidates: list entries with SC >= last, range by range, in tiles of kSrThreads;
+        } else {
+        // candidates: the list entries with SC >= last of all the query's ranges as one
+        // sequence (range r's entries are upre[r] .. upre[r + 1] - 1), in tiles of kSrThreads;
         // the buffer is re-ranked and emptied before a tile that would not fit
-        for (int r = 0; r < nr; ++r) {
-            const uint32_t off = P.unit_off[q * nr + r], len = P.unit_len[q * nr + r];
-            const uint32_t rlo = uint32_t(int64_t(r * P.slabs_per_cta) << kSlabLog2);
-            for (uint32_t t0 = 0; t0 < len; t0 += kSrThreads) {
-                make_room();
-                const uint32_t t = t0 + tid;
-                uint32_t x = 0;
-                bool take = false;
-                if (t < len) {
-                    x = P.arena[off + t];
-                    take = int(x >> kLevelShift) >= last;
-                }
-                const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-                if (take) buf[at] = rlo + (x & ((1u << kLevelShift) - 1u));
-                __syncthreads();
+        uint32_t* upre = fbm;            // [nr + 1] (the fallback's bitmaps are not in use)
+        uint32_t* uoff = upre + nr + 1;  // [nr]
+        uint32_t nent = 0;
+        for (int r0 = 0; r0 < nr; r0 += kSrThreads) {
+            const int r = r0 + tid;
+            uint32_t len = 0;
+            if (r < nr) {
+                len = P.unit_len[q * nr + r];
+                uoff[r] = P.unit_off[q * nr + r];
             }
+            uint2 tot;
+            const uint2 ex = block_excl_scan2<kSrWarps>(len, 0u, s_tmp2, tot, lane, warp);
+            if (r < nr) upre[r] = nent + ex.x;
+            nent += tot.x;
+        }
+        if (tid == 0) upre[nr] = nent;
+        __syncthreads();
+        for (uint32_t t0 = 0; t0 < nent; t0 += kSrThreads) {
+            make_room();
+            const uint32_t t = t0 + tid;
+            uint32_t x = 0, rlo = 0;
+            bool take = false;
+            if (t < nent) {
+                int lo_r = 0, hi_r = nr - 1;   // the range holding entry t
+                while (lo_r < hi_r) {
+                    const int mid = (lo_r + hi_r + 1) >> 1;
+                    if (upre[mid] <= t) lo_r = mid;
+                    else hi_r = mid - 1;
+                }
+                x = P.arena[uoff[lo_r] + (t - upre[lo_r])];
+                take = int(x >> kLevelShift) >= last;
+                rlo = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
+            }
+            const uint32_t at = warp_append_slot(take, &s_bufn, lane);
+            if (take) buf[at] = rlo + (x & ((1u << kLevelShift) - 1u));
+            __syncthreads();
+        }
         }
         __syncthreads();
         rerank_buffer(int(s_bufn));

@@ -18,7 +18,7 @@
 #include <cstdint>
 
 #include "taco_internal.h"
-#define TACO_DEFINE_COUNT_LISTS
+#include "taco_count.cuh"
 #include "taco_rerank.cuh"
 
 namespace taco {
@@ -959,6 +959,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.fp8_space = ix->fp8_space;
         P.ids = ix->d_ids;
         P.split = ix->d_split;
+        P.n_ids = ix->n_ids;
         P.cells = L.cells;
         P.ncells = L.ncells;
         P.params = L.params;
@@ -1010,10 +1011,10 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             // pass 1: counting per (query, id range) unit; 512 or 1024 threads per CTA (tuned)
             const size_t smem1 = P.region_a + kCountListsExtra;
             const int nw1 = ix->tp_count_warps == 32 ? 32 : 16;
-            // variants: 16 warps x 8 windows per walk round, 32 x 8, 16 x 16
-            const int c1 = nw1 == 32 ? 1 : (ix->tp_walk_unroll == 16 ? 2 : 0);
-            auto k1 = c1 == 1 ? count_lists_kernel<32, 8> : (c1 == 2 ? count_lists_kernel<16, 16>
-                                                                   : count_lists_kernel<16, 8>);
+            // variants: 16 warps x 4 chunk windows per walk round, 32 x 4, 16 x 8
+            const int c1 = nw1 == 32 ? 1 : (ix->tp_walk_unroll == 8 ? 2 : 0);
+            auto k1 = c1 == 1 ? count_lists_kernel<32, 4> : (c1 == 2 ? count_lists_kernel<16, 8>
+                                                                   : count_lists_kernel<16, 4>);
             static thread_local size_t c1_smem[3] = {0, 0, 0};
             static thread_local int c1_blocks[3] = {0, 0, 0};
             if (c1_smem[c1] != smem1) {
@@ -1031,7 +1032,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results
             const size_t smem2 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 +
-                                 size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0);
+                                 size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0) +
+                                 size_t(2 * P.n_ranges + 1) * 4;   // the ranges' list offsets
             if (int rc = prof_begin(pix, 3, st, &pb, &pe)) return rc;
             const cudaError_t e = launch_select(rk, R, Gs, P, L.nq, smem2, st);
             if (e != cudaSuccess) return cuda_fail(e, "select_rerank launch", __FILE__, __LINE__);

@@ -4,8 +4,8 @@
 //     (16 KB of 4-bit counters per slab in shared memory; fewer slabs per range = more,
 //     smaller units per query and more resident CTAs; more = fewer units, longer walks),
 //   - the lanes that gather one candidate row in the select / re-rank pass (4 .. 32),
-//   - the threads of a counting CTA (512 or 1024) and the depth of its walk (8 or 16 id loads
-//     in flight per lane; 16 only with 512 threads, one CTA per SM),
+//   - the threads of a counting CTA (512 or 1024) and the depth of its walk (4 or 8 loads of
+//     four ids in flight per lane; 8 only with 512 threads),
 //   - whether small budgets are probed by the row-merge walk or always by the histogram
 //     kernel.
 // The choices change no result beyond the summation order of a candidate's FP32 distance
@@ -55,11 +55,11 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
                              int32_t reps, void* stream, taco_tune_result* out) {
     if (!ix || !params || !out) return fail(TACO_EINVAL, "null argument");
     const int rk = params->precision == TACO_PREC_FP8 ? 2 : (params->precision == TACO_PREC_BF16 ? 1 : 0);
-    const Choice defaults{ix->slabs_per_cta, ix->cluster, 0, -1, 16, 8};
+    const Choice defaults{ix->slabs_per_cta, ix->cluster, 0, -1, 16, 4};
     if (reps <= 0) {   // back to the defaults
         apply(ix, defaults, rk);
         for (int& l : ix->tp_lanes) l = 0;
-        *out = taco_tune_result{defaults.spc, defaults.ranges, 0, -1, 16, 8, 0.0, 0.0, 0, 0};
+        *out = taco_tune_result{defaults.spc, defaults.ranges, 0, -1, 16, 4, 0.0, 0.0, 0, 0};
         return TACO_OK;
     }
     if (!queries || nq < 1 || !is_device_pointer(queries)) return fail(TACO_EINVAL, "need device queries, nq >= 1");
@@ -105,7 +105,8 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
         return TACO_OK;
     };
     // 1. counter layout: slabs per range (16 KB each) up to what a CTA's shared memory holds
-    for (int spc : {1, 2, 4, 8, 12}) {
+    //    (up to 5 slabs, two 512-thread counting CTAs share an SM)
+    for (int spc : {1, 2, 4, 5, 8, 12}) {
         if (spc > ix->n_slabs || spc == cur.spc) continue;
         Choice c = cur;
         c.spc = spc;
@@ -116,8 +117,8 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
         }
     }
     // 1b. threads of the counting CTA (512: two CTAs per SM where they fit; 1024: one) and
-    //     the depth of its walk (16 loads in flight per lane: one 512-thread CTA per SM)
-    for (const int2 v : {make_int2(16, 8), make_int2(32, 8), make_int2(16, 16)}) {
+    //     the depth of its walk (8 chunk loads in flight per lane: one 512-thread CTA per SM)
+    for (const int2 v : {make_int2(16, 4), make_int2(32, 4), make_int2(16, 8)}) {
         if (v.x == cur.warps && v.y == cur.unroll) continue;
         Choice c = cur;
         c.warps = v.x;

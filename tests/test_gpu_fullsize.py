@@ -1,8 +1,8 @@
 """Parity at full size: the 1M x 128 integer-GMM workload with its 10,000-query batch, run
 through taco_search_batch in one call at the operating point the benchmark times on it
 (alpha = 0.01, beta = 0.001; FP32 with shortlist 4k, BF16 with shortlist k), in the counting
-layout the tuner picks there (31 slabs of 2^15 ids, 12 per id range, so 3 ranges; 16 warps,
-16-deep walk).
+layout of 31 slabs of 2^15 ids, 12 per id range (3 ranges), 16 warps and 8 chunk loads in
+flight per lane.
 
 The index is built by the library (Alg. 1-3 on the GPU) and exported; the FP64 oracle
 answers sampled queries one by one on that same index (its transform, centroids and cell
@@ -32,7 +32,7 @@ build_lib.build()
 
 ALPHA, BETA, K = 0.01, 0.001, 10
 FORMS = [("fp32", 4), ("bf16", 1)]
-LAYOUT = dict(slabs_per_range=12, count_warps=16, walk_unroll=16)
+LAYOUT = dict(slabs_per_range=12, count_warps=16, walk_unroll=8)
 SAMPLE = np.linspace(0, 9999, 256).astype(np.int64)
 SC_SAMPLE = SAMPLE[::16]
 

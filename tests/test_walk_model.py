@@ -1,5 +1,7 @@
-"""CPU model of the counting walk's index arithmetic (`walk_batch` in csrc/taco_rerank.cuh),
-checked against the direct definition on adversarial run-length mixes.
+"""CPU model of the counting walks' index arithmetic, checked against the direct definition
+on adversarial run-length mixes: `walk_batch` (csrc/taco_rerank.cuh, the cluster kernel;
+elements are ids) and `walk_chunks` (csrc/taco_count.cuh, the counting pass; elements are
+4-id chunks of the 16-byte aligned, padded cell lists, filtered by the unit's id range).
 
 The staged runs of one batch are non-empty id-array runs (start_r, len_r), concatenated in
 order; element e lies in run r with cpre[r] <= e < cpre[r + 1] and has id-array index
@@ -110,3 +112,75 @@ def test_walk_maps_every_element_to_its_id(mix, wu):
         cpre, rbase, total, nr = stage(lengths, starts)
         got = walk_indices(cpre, rbase, total, nr, wu, last_idx=2**32 - 1)
         assert got == direct_indices(lengths, starts), (mix, wu, m)
+
+
+# ------------------------------------------------------------ the chunk walk (count_lists_kernel)
+PAD = 0xFFFFFFFF
+
+
+def padded_lists(codes, n_cells):
+    """Cell lists of one subspace laid out as the library does: ids ascending per cell, each
+    list starting at a multiple of 4 and padded to the next one with 0xffffffff; returns the
+    array and the start of every cell."""
+    ids, starts = [], []
+    for c in range(n_cells):
+        starts.append(len(ids))
+        members = [int(p) for p in np.nonzero(codes == c)[0]]
+        ids += members + [PAD] * ((-len(members)) % 4)
+    return np.array(ids, dtype=np.int64), starts
+
+
+@pytest.mark.parametrize("wu", [4, 8])
+@pytest.mark.parametrize("n_cells,n", [(7, 3000), (64, 20000), (300, 5000)])
+def test_chunk_walk_counts_exactly_the_probed_ids_of_the_range(wu, n_cells, n):
+    """The chunk runs [b / 4, ceil(e / 4)) of the probed cells' runs in a range, walked with
+    the window/mask lookup and filtered by the range test, visit every id of those runs once
+    and nothing else (padding and the cells' ids of other ranges fail the test). Counting
+    with an append when a count reaches 2 lists every id with SC >= 2 exactly once, and
+    ge[1] = events - sum_{j >= 2} ge[j]."""
+    rng = np.random.default_rng(n_cells * 1000 + wu)
+    ns = 4
+    lists = [padded_lists(rng.integers(0, n_cells, n), n_cells) for _ in range(ns)]
+    base, arrays = 0, []
+    for arr, st in lists:   # subspaces one after another (each a multiple of 4 long)
+        arrays.append((base, st))
+        base += len(arr)
+    allids = np.concatenate([a for a, _ in lists])
+    last_chunk = len(allids) // 4 - 1
+    slab = 997   # a range of ids [lo, hi)
+    for lo in range(0, n, slab * 3):
+        hi = min(lo + slab * 3, n)
+        probed = [sorted(rng.choice(n_cells, size=max(1, n_cells // 3), replace=False)) for _ in range(ns)]
+        starts, lengths, want = [], [], []
+        for i in range(ns):
+            off, st = arrays[i]
+            arr = lists[i][0]
+            for c in probed[i]:
+                end = st[c + 1] if c + 1 < n_cells else len(arr)
+                cell = arr[st[c]:end]
+                real = cell[cell != PAD]
+                b = off + st[c] + int(np.searchsorted(real, lo))
+                e = off + st[c] + int(np.searchsorted(real, hi))
+                want += [int(x) for x in real if lo <= x < hi]
+                s0, ln = b >> 2, (((e + 3) >> 2) - (b >> 2)) if e > b else 0
+                starts.append(s0)
+                lengths.append(ln)
+        if sum(lengths) == 0:
+            continue
+        cpre, rbase, total, nr = stage(lengths, starts)
+        chunks = walk_indices(cpre, rbase, total, nr, wu, last_idx=last_chunk)
+        got, cnt, listed = [], {}, []
+        for e_, x in sorted(chunks.items()):
+            for h in range(4):
+                v = int(allids[4 * x + h])
+                rel = (v - lo) & M32
+                if rel < hi - lo:
+                    got.append(v)
+                    old = cnt.get(rel, 0)
+                    cnt[rel] = old + 1
+                    if old == 1:
+                        listed.append(rel)
+        assert sorted(got) == sorted(want)
+        assert sorted(listed) == sorted(r for r, c in cnt.items() if c >= 2)
+        ge = {j: sum(1 for c in cnt.values() if c >= j) for j in range(1, ns + 1)}
+        assert ge[1] == len(got) - sum(ge[j] for j in range(2, ns + 1))
