@@ -118,6 +118,11 @@ typedef struct {
                                   operands of 128 queries fit shared memory) */
     int32_t reserved;
     int64_t device_bytes;      /* device memory owned by the index, workspace excluded */
+    int64_t n_ids;             /* length of the cell-list array (taco_index_lists) */
+    double build_ms_transform; /* wall time of Alg. 1 (mean, covariance, eigensystem, Alg. 2,
+                                  projection of D); 0 for an index made from its parts */
+    double build_ms_index;     /* wall time of the rest of the build: k-means of Alg. 3, the
+                                  cell lists and slab table, the reduced-precision row copies */
 } taco_index_info;
 
 /* Optional device outputs of taco_search_debug (any may be NULL). */
@@ -321,6 +326,20 @@ int taco_index_get_info(const taco_index* index, taco_index_info* info);
  */
 int taco_index_export(const taco_index* index, double* o_bar, double* B, double* eigvals,
                       int32_t* alloc, double* centroids, uint16_t* codes);
+
+/*
+ * taco_index_lists -- copy the index's cell lists (Alg. 3's IMI) to host buffers (any may be
+ * NULL; inspection and test aid):
+ *   sizes [N_s][K] u32       |IMI_i[cell]|
+ *   split [N_s][K][n_slabs + 1] u32: position in ids of the first id >= t * 2^15 of the cell's
+ *                            list (t = n_slabs: the end of the list)
+ *   ids   [info.n_ids] u32   the lists, subspace after subspace and cell after cell, ids
+ *                            ascending; each list starts at a multiple of 4 and is padded to the
+ *                            next one with 0xffffffff.
+ * The lists are built on the device (a stable counting sort of the ids by cell code, one slab
+ * of 2^15 ids at a time). Synchronises the device.
+ */
+int taco_index_lists(const taco_index* index, uint32_t* sizes, uint32_t* split, uint32_t* ids);
 
 /* taco_save_index / taco_load_index -- binary file with the parts and D (little endian).
  * Loading rebuilds the device index; taco_load_index synchronises `stream`. */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -180,49 +181,51 @@ int build_fp8_rows(taco_index* ix, cudaStream_t st) {
     return TACO_OK;
 }
 
-int finish_index(taco_index* ix, int keep_rows, cudaStream_t st) {
+int finish_index(taco_index* ix, int keep_rows, cudaStream_t st, const uint16_t* dcodes = nullptr) {
     const int64_t n = ix->n;
     const int Ns = ix->Ns, K = ix->K;
     TRY(configure_search(ix));
     const int ns1 = ix->n_slabs + 1;
-    // Cell lists of all subspaces in one array: subspace after subspace, cell after cell, each
-    // list starting on a 16-byte boundary (a multiple of 4 ids) and padded to the next one with
-    // kIdPad, so the counting walk reads any run of a list in aligned 4-id chunks. The split
-    // table holds absolute positions in that array.
-    std::vector<uint32_t> sizes(size_t(Ns) * K, 0), split(size_t(Ns) * K * ns1);
-    for (int i = 0; i < Ns; ++i) {
-        const uint16_t* code = ix->codes.data() + size_t(i) * n;
-        uint32_t* sz = sizes.data() + size_t(i) * K;
-        for (int64_t p = 0; p < n; ++p) {
-            if (code[p] >= K) return fail(TACO_EINVAL, "code %d of point %lld >= K", int(code[p]), (long long)p);
-            ++sz[code[p]];
+    // Cell lists of all subspaces in one array, built on the device (launch_build_lists):
+    // subspace after subspace, cell after cell, ids ascending, each list starting on a
+    // 16-byte boundary (a multiple of 4 ids) and padded to the next one with kIdPad, so the
+    // counting walk reads any run of a list in aligned 4-id chunks. The slab table holds
+    // absolute positions in that array.
+    const uint16_t* dc = dcodes;
+    uint16_t* tmp_codes = nullptr;
+    uint32_t* scratch = nullptr;
+    uint32_t* dstart = nullptr;
+    struct Tmp {
+        uint16_t** c;
+        uint32_t** s;
+        uint32_t** t;
+        ~Tmp() {
+            cudaFree(*c);
+            cudaFree(*s);
+            cudaFree(*t);
         }
+    } tmp{&tmp_codes, &scratch, &dstart};
+    for (size_t j = 0; j < ix->codes.size(); ++j)
+        if (ix->codes[j] >= K)
+            return fail(TACO_EINVAL, "code %d of point %lld >= K", int(ix->codes[j]), (long long)(j % size_t(n)));
+    if (!dc) {
+        TRY(dev_alloc(&tmp_codes, ix->codes.size(), nullptr));
+        TACO_CUDA(cudaMemcpyAsync(tmp_codes, ix->codes.data(), ix->codes.size() * 2, cudaMemcpyHostToDevice, st));
+        dc = tmp_codes;
     }
-    std::vector<uint32_t> cstart(size_t(Ns) * K + 1, 0);
-    for (size_t j = 0; j < size_t(Ns) * K; ++j) cstart[j + 1] = cstart[j] + ((sizes[j] + 3u) & ~3u);
-    std::vector<uint32_t> ids(cstart.back(), kIdPad);
-    for (int i = 0; i < Ns; ++i) {
-        const uint16_t* code = ix->codes.data() + size_t(i) * n;
-        std::vector<uint32_t> cur(cstart.begin() + size_t(i) * K, cstart.begin() + size_t(i + 1) * K);
-        for (int64_t p = 0; p < n; ++p) ids[cur[code[p]]++] = uint32_t(p);  // ascending ids
-        uint32_t* sp = split.data() + size_t(i) * K * ns1;
-        for (int c = 0; c < K; ++c) {
-            const size_t j = size_t(i) * K + c;
-            const uint32_t* b = ids.data() + cstart[j];
-            const uint32_t* e = b + sizes[j];
-            for (int sl = 0; sl < ns1; ++sl) {
-                const int64_t bound = std::min<int64_t>(int64_t(sl) << kSlabLog2, n);
-                sp[size_t(c) * ns1 + sl] = uint32_t(std::lower_bound(b, e, uint32_t(bound)) - ids.data());
-            }
-        }
-    }
-    ix->n_ids = int64_t(ids.size());
-    TRY(dev_alloc(&ix->d_sizes, sizes.size(), &ix->device_bytes));
-    TRY(dev_alloc(&ix->d_ids, ids.size(), &ix->device_bytes));
-    TRY(dev_alloc(&ix->d_split, split.size(), &ix->device_bytes));
-    TACO_CUDA(cudaMemcpyAsync(ix->d_sizes, sizes.data(), sizes.size() * 4, cudaMemcpyHostToDevice, st));
-    TACO_CUDA(cudaMemcpyAsync(ix->d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, st));
-    TACO_CUDA(cudaMemcpyAsync(ix->d_split, split.data(), split.size() * 4, cudaMemcpyHostToDevice, st));
+    const size_t m = size_t(Ns) * K;
+    const size_t ids_cap = size_t(Ns) * size_t(n) + 3 * m;   // every list padded by at most 3
+    TRY(dev_alloc(&scratch, size_t(lists_scratch_words(n, Ns, K)), nullptr));
+    TRY(dev_alloc(&dstart, m + 1, nullptr));
+    TRY(dev_alloc(&ix->d_sizes, m, &ix->device_bytes));
+    TRY(dev_alloc(&ix->d_ids, ids_cap, &ix->device_bytes));
+    TRY(dev_alloc(&ix->d_split, m * ns1, &ix->device_bytes));
+    TACO_CUDA(cudaMemsetAsync(ix->d_ids, 0xff, ids_cap * 4, st));   // kIdPad
+    TACO_CUDA(launch_build_lists(dc, n, Ns, K, scratch, ix->d_sizes, dstart, ix->d_split, ix->d_ids, st));
+    uint32_t total = 0;
+    TACO_CUDA(cudaMemcpyAsync(&total, dstart + m, 4, cudaMemcpyDeviceToHost, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    ix->n_ids = int64_t(total);
     // FP32 copies of o_bar, B, centroids for the query path
     std::vector<float> ob(ix->d), Bf(size_t(ix->d) * ix->Dp), cf(ix->centroids.size());
     for (int j = 0; j < ix->d; ++j) ob[j] = float(ix->o_bar[j]);
@@ -311,6 +314,8 @@ int build_impl(const float* data, int64_t n, int32_t d, const taco_build_params*
     TACO_CUDA(cudaGetDevice(&ix->device));
     set_geometry(ix.get(), n, d, p->n_subspaces, p->sub_dim, p->sqrt_k);
     TRY(upload_data(ix.get(), data, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    const auto t0 = std::chrono::steady_clock::now();
     // Alg. 1 steps 2-3: mean and covariance, FP64 accumulation on the device
     double* dsum = nullptr;
     double* dcov = nullptr;
@@ -371,6 +376,8 @@ int build_impl(const float* data, int64_t n, int32_t d, const taco_build_params*
     TRY(dev_alloc(&dT, size_t(n) * Dp, nullptr));
     std::unique_ptr<float, void (*)(float*)> g3(dT, [](float* q) { cudaFree(q); });
     TACO_CUDA(launch_project(ix->d_data, n, d, ix->d_pad, ix->d_obar, ix->d_B, Dp, dT, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    const auto t1 = std::chrono::steady_clock::now();
     // Alg. 3 steps 4-9: k-means on both halves of every subspace
     const int P = 2 * p->n_subspaces;
     std::vector<int64_t> init(size_t(P) * p->sqrt_k);
@@ -390,7 +397,10 @@ int build_impl(const float* data, int64_t n, int32_t d, const taco_build_params*
     TACO_CUDA(cudaMemcpyAsync(ix->codes.data(), dcodes, ix->codes.size() * 2, cudaMemcpyDeviceToHost, st));
     TACO_CUDA(cudaStreamSynchronize(st));
     ix->centroids.assign(cent.begin(), cent.end());
-    TRY(finish_index(ix.get(), p->keep_rows, st));
+    TRY(finish_index(ix.get(), p->keep_rows, st, dcodes));
+    const auto t2 = std::chrono::steady_clock::now();
+    ix->build_ms_transform = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    ix->build_ms_index = std::chrono::duration<double, std::milli>(t2 - t1).count();
     *out = ix.release();
     return TACO_OK;
 }
@@ -413,7 +423,10 @@ int create_impl(const float* data, int64_t n, int32_t d, const taco_index_parts*
     ix->eigvals.assign(d, 0.0);
     ix->alloc.assign(ix->Dp, -1);
     TRY(upload_data(ix.get(), data, st));
+    TACO_CUDA(cudaStreamSynchronize(st));
+    const auto t0 = std::chrono::steady_clock::now();
     TRY(finish_index(ix.get(), keep_rows, st));
+    ix->build_ms_index = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = ix.release();
     return TACO_OK;
 }
@@ -497,7 +510,7 @@ SearchLayout taco::plan_search(const taco_index* ix, int64_t chunk, int kk_max, 
     l.uoff = off; off = align_up(off + units * 4);
     l.ulen = off; off = align_up(off + units * 4);
     l.arena = off; off = align_up(off + units * kArenaPerSlab * ix->tp_spc * 4);
-    l.qflag = off; off = align_up(off + size_t(chunk) * 4);
+    l.qflag = off; off = align_up(off + size_t(chunk + 2) * 4);   // flags, then 2 query counters
     l.qlast = off; off = align_up(off + size_t(chunk) * 4);
     l.par = off; off = align_up(off + size_t(n_params) * sizeof(QueryParamsDev));
     l.q = off; off = align_up(off + (stage_queries ? size_t(chunk) * ix->d * 4 : 0));
@@ -728,6 +741,18 @@ int taco_index_get_info(const taco_index* ix, taco_index_info* info) {
     info->has_centroid_tc = ix->d_cent_tc != nullptr;
     info->reserved = 0;
     info->device_bytes = ix->device_bytes;
+    info->n_ids = ix->n_ids;
+    info->build_ms_transform = ix->build_ms_transform;
+    info->build_ms_index = ix->build_ms_index;
+    return TACO_OK;
+}
+
+int taco_index_lists(const taco_index* ix, uint32_t* sizes, uint32_t* split, uint32_t* ids) {
+    if (!ix) return fail(TACO_EINVAL, "null index");
+    const size_t m = size_t(ix->Ns) * ix->K;
+    if (sizes) TACO_CUDA(cudaMemcpy(sizes, ix->d_sizes, m * 4, cudaMemcpyDeviceToHost));
+    if (split) TACO_CUDA(cudaMemcpy(split, ix->d_split, m * (ix->n_slabs + 1) * 4, cudaMemcpyDeviceToHost));
+    if (ids) TACO_CUDA(cudaMemcpy(ids, ix->d_ids, size_t(ix->n_ids) * 4, cudaMemcpyDeviceToHost));
     return TACO_OK;
 }
 

@@ -440,4 +440,142 @@ cudaError_t launch_quantize_fp8(const float* Y, int64_t rows, int Dp, int dp8,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Cell lists of Alg. 3 (IMI[cell].append(j) for j = 0..n-1, so ids ascend in every cell),
+// built on the device as a stable counting sort of the point ids by cell code, one slab of
+// 2^15 ids at a time: per (subspace, slab) the cells' counts, then per cell the running
+// position of each slab in the cell's list (which is the slab table), then a stable scatter
+// of every slab in id order. Each cell's list starts on a multiple of 4 ids and is padded
+// with kIdPad (the caller fills the array with it first).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(512)
+lists_count_kernel(const uint16_t* __restrict__ codes, int64_t n, int K, int n_slabs,
+                   uint32_t* __restrict__ counts) {
+    extern __shared__ uint32_t h[];
+    const int t = blockIdx.x, i = blockIdx.y;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) h[c] = 0u;
+    __syncthreads();
+    const int64_t lo = int64_t(t) << kSlabLog2, hi = min(lo + kSlabIds, n);
+    const uint16_t* ci = codes + size_t(i) * n;
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) atomicAdd(&h[ci[p]], 1u);
+    __syncthreads();
+    uint32_t* out = counts + (size_t(i) * n_slabs + t) * K;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) out[c] = h[c];
+}
+
+// sizes[j] = sum over slabs of counts, j = i * K + c (one thread per cell).
+__global__ void lists_size_kernel(const uint32_t* __restrict__ counts, int K, int n_slabs, int Ns,
+                                  uint32_t* __restrict__ sizes) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= int64_t(Ns) * K) return;
+    const int i = int(j / K), c = int(j - int64_t(i) * K);
+    uint32_t s = 0;
+    for (int t = 0; t < n_slabs; ++t) s += counts[(size_t(i) * n_slabs + t) * K + c];
+    sizes[j] = s;
+}
+
+// start[j] = sum over j' < j of the padded sizes (sizes rounded up to 4), start[m] = total;
+// one block, each thread a contiguous segment of the m cells.
+__global__ void __launch_bounds__(1024)
+lists_start_kernel(const uint32_t* __restrict__ sizes, int64_t m, uint32_t* __restrict__ start) {
+    __shared__ uint32_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t seg = (m + 1023) / 1024;
+    const int64_t a = min(m, int64_t(tid) * seg), b = min(m, a + seg);
+    uint32_t s = 0;
+    for (int64_t j = a; j < b; ++j) s += (sizes[j] + 3u) & ~3u;
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {   // inclusive scan of the segment sums
+        const uint32_t v = tid >= off ? part[tid - off] : 0u;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[tid] - s;
+    for (int64_t j = a; j < b; ++j) {
+        start[j] = run;
+        run += (sizes[j] + 3u) & ~3u;
+    }
+    if (tid == 1023) start[m] = part[1023];
+}
+
+// Per cell, the position in the id array where each slab's ids begin: split[j][t], and the
+// end of the cell's ids split[j][n_slabs]; counts is overwritten with the same positions
+// (the scatter's starting points). One thread per cell.
+__global__ void lists_split_kernel(uint32_t* __restrict__ counts, const uint32_t* __restrict__ start, int K,
+                                   int n_slabs, int Ns, uint32_t* __restrict__ split) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= int64_t(Ns) * K) return;
+    const int i = int(j / K), c = int(j - int64_t(i) * K);
+    uint32_t run = start[j];
+    uint32_t* sp = split + size_t(j) * (n_slabs + 1);
+    for (int t = 0; t < n_slabs; ++t) {
+        uint32_t& ct = counts[(size_t(i) * n_slabs + t) * K + c];
+        const uint32_t v = ct;
+        sp[t] = run;
+        ct = run;
+        run += v;
+    }
+    sp[n_slabs] = run;
+}
+
+// Stable scatter of slab t of subspace i: one warp walks the slab's ids in order, 32 at a
+// time; lanes with equal codes are ranked by lane (ids ascend with the lane) and the group's
+// lowest lane advances the cell's position.
+__global__ void __launch_bounds__(32)
+lists_scatter_kernel(const uint16_t* __restrict__ codes, int64_t n, int K, int n_slabs,
+                     const uint32_t* __restrict__ pos0, uint32_t* __restrict__ ids) {
+    extern __shared__ uint32_t pos[];
+    const int t = blockIdx.x, i = blockIdx.y, lane = threadIdx.x;
+    const uint32_t* src = pos0 + (size_t(i) * n_slabs + t) * K;
+    for (int c = lane; c < K; c += 32) pos[c] = src[c];
+    __syncwarp();
+    const int64_t lo = int64_t(t) << kSlabLog2, hi = min(lo + kSlabIds, n);
+    const uint16_t* ci = codes + size_t(i) * n;
+    const uint32_t lane_lt = (1u << lane) - 1u;
+    for (int64_t p0 = lo; p0 < hi; p0 += 32) {
+        const int64_t p = p0 + lane;
+        const bool ok = p < hi;
+        const uint32_t c = ok ? uint32_t(ci[p]) : 0x10000u + uint32_t(lane);   // past the end: alone
+        const unsigned grp = __match_any_sync(0xffffffffu, c);
+        if (ok) {
+            const uint32_t at = pos[c] + __popc(grp & lane_lt);
+            ids[at] = uint32_t(p);
+        }
+        __syncwarp();
+        if (ok && (grp & lane_lt) == 0u) pos[c] += __popc(grp);
+        __syncwarp();
+    }
+}
+
+int64_t lists_scratch_words(int64_t n, int Ns, int K) {
+    const int64_t n_slabs = (n + kSlabIds - 1) / kSlabIds;
+    return int64_t(Ns) * n_slabs * K + int64_t(Ns) * K + 1;
+}
+
+cudaError_t launch_build_lists(const uint16_t* codes, int64_t n, int Ns, int K, uint32_t* scratch,
+                               uint32_t* sizes, uint32_t* start, uint32_t* split, uint32_t* ids,
+                               cudaStream_t st) {
+    const int n_slabs = int((n + kSlabIds - 1) / kSlabIds);
+    uint32_t* counts = scratch;   // [Ns][n_slabs][K]
+    const size_t smem = size_t(K) * 4;
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(lists_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(lists_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    const dim3 grid{unsigned(n_slabs), unsigned(Ns), 1u};
+    lists_count_kernel<<<grid, 512, smem, st>>>(codes, n, K, n_slabs, counts);
+    const int64_t m = int64_t(Ns) * K;
+    const unsigned cb = unsigned((m + 255) / 256);
+    lists_size_kernel<<<cb, 256, 0, st>>>(counts, K, n_slabs, Ns, sizes);
+    lists_start_kernel<<<1, 1024, 0, st>>>(sizes, m, start);
+    lists_split_kernel<<<cb, 256, 0, st>>>(counts, start, K, n_slabs, Ns, split);
+    lists_scatter_kernel<<<grid, 32, smem, st>>>(codes, n, K, n_slabs, counts, ids);
+    return cudaGetLastError();
+}
+
 }  // namespace taco

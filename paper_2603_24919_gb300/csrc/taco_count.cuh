@@ -37,10 +37,16 @@ __device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
 
 constexpr int kChunkListCap = 4096;   // ids that reached SC = 2 in a unit (listed once each)
 
+// Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address into L2;
+// no completion to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Shared memory of count_lists_kernel past the counters (bytes): split bounds of the staged
-// cells for two ranges, the level list, the staged chunk runs, the exact-level histogram
+// cells for three ranges, the level list, the staged chunk runs, the exact-level histogram
 // and the staged cells.
-constexpr size_t kCountListsExtra = size_t(2) * kCellBatch * 8 + size_t(kChunkListCap) * 4 +
+constexpr size_t kCountListsExtra = size_t(3) * kCellBatch * 8 + size_t(kChunkListCap) * 4 +
                                     size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 16 * 4 +
                                     size_t(kCellBatch) * 4;
 
@@ -170,8 +176,8 @@ count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
-    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
-    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);      // kChunkListCap
+    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [3][kCellBatch]
+    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 3 * kCellBatch);      // kChunkListCap
     uint32_t* rbase = lst + kChunkListCap;                                    // kCellBatch
     uint32_t* cpre = rbase + kCellBatch;                                      // kCellBatch + kRunPad
     uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
@@ -197,6 +203,17 @@ count_lists_kernel(const RerankParams P) {
         }
         cp_async_commit();
     };
+    // the id chunks of every staged cell's run in range r (bounds in pairs[buf]) into L2, so
+    // that range r's walk, one range later, finds them there (the id lists of a large index
+    // do not stay in L2)
+    auto prefetch_ids = [&](int total_cells, int buf) {
+        for (int t = tid; t < total_cells; t += NW * 32) {
+            const uint2 be = pairs[buf * kCellBatch + t];
+            uint32_t start, len;
+            chunk_run(be.x, be.y, start, len);
+            if (len) prefetch_l2_bulk(ids4 + start, len * 16u);
+        }
+    };
     // stage the chunk runs of id positions [b, e) (one per thread, e = b when none), add the
     // ids they hold in the range to s_ev, and walk them
     auto stage_and_walk = [&](uint32_t b, uint32_t e, uint32_t lo, uint32_t rlen) {
@@ -208,7 +225,8 @@ count_lists_kernel(const RerankParams P) {
         if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, lo, rlen, st.x, st.y, cnt, lst, &s_app, cpre, rbase,
                                       pol_keep, lane, warp);
     };
-    for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+    __shared__ int64_t s_next;
+    for (int64_t q = blockIdx.x; q < P.nq; q = next_query(P.work, &s_next)) {
         __syncthreads();   // the previous query is finished with the shared state
         if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
         __syncthreads();
@@ -221,7 +239,8 @@ count_lists_kernel(const RerankParams P) {
                 qcell[t] = (uint32_t(i) << 16) | P.cells[(q * Ns + i) * K + (t - s_pre[i])];
             }
             __syncthreads();
-            prefetch(total_cells, 0, 0);
+            prefetch(total_cells, 0, 0);   // bounds of ranges 0 and 1 (a pipeline two deep)
+            if (P.n_ranges > 1) prefetch(total_cells, 1, 1);
         }
         for (int r = 0; r < P.n_ranges; ++r) {
             const int64_t u = q * P.n_ranges + r;
@@ -242,11 +261,12 @@ count_lists_kernel(const RerankParams P) {
             }
             if (staged) {
                 cp_async_wait_all();
-                __syncthreads();   // this range's bounds are in pairs[r & 1]
-                if (r + 1 < P.n_ranges) prefetch(total_cells, r + 1, (r + 1) & 1);
+                __syncthreads();   // the bounds of ranges r and r + 1 are in pairs[r % 3], pairs[(r + 1) % 3]
+                if (r + 1 < P.n_ranges) prefetch_ids(total_cells, (r + 1) % 3);
+                if (r + 2 < P.n_ranges) prefetch(total_cells, r + 2, (r + 2) % 3);
                 uint32_t b = 0, e = 0;
                 if (tid < total_cells) {
-                    const uint2 be = pairs[(r & 1) * kCellBatch + tid];
+                    const uint2 be = pairs[(r % 3) * kCellBatch + tid];
                     b = be.x;
                     e = be.y;
                 }

@@ -121,6 +121,8 @@ struct taco_index {
     uint32_t* d_ids = nullptr;          // [n_ids]: cell lists, each 16-byte aligned and padded
     uint32_t* d_split = nullptr;        // [Ns][K][n_slabs + 1] absolute positions in d_ids
     int64_t n_ids = 0;                  // length of d_ids (N_s n plus the padding)
+    double build_ms_transform = 0.0;    // Alg. 1 part of the build (wall time)
+    double build_ms_index = 0.0;        // k-means, cell lists, row copies (wall time)
     int64_t device_bytes = 0;
     std::mutex ws_mu;
     taco::Workspace ws;
@@ -161,6 +163,15 @@ cudaError_t launch_absmax_cols(const float* Y, int64_t rows, int Dp, unsigned* m
 cudaError_t launch_quantize_fp8(const float* Y, int64_t rows, int Dp, int dp8,
                                 const float* inv_scale, uint8_t* out, cudaStream_t st);
 
+// Cell lists of Alg. 3 on the device from the cell codes [Ns][n]: sizes [Ns * K], the padded
+// list starts [Ns * K + 1] (start[Ns * K] = total ids with padding), the slab table
+// [Ns * K][n_slabs + 1] and the ids (pre-filled with kIdPad by the caller). scratch holds
+// lists_scratch_words(n, Ns, K) words.
+int64_t lists_scratch_words(int64_t n, int Ns, int K);
+cudaError_t launch_build_lists(const uint16_t* codes, int64_t n, int Ns, int K, uint32_t* scratch,
+                               uint32_t* sizes, uint32_t* start, uint32_t* split, uint32_t* ids,
+                               cudaStream_t st);
+
 // Query x centroid distance block (Alg. 6 steps 4-5) as a separate kernel:
 // hd[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2, FP32 on CUDA cores or BF16 on tcgen05.
 bool centroid_tc_supported(const taco_index* ix);
@@ -187,7 +198,7 @@ struct SearchLaunch {
     uint32_t* unit_off;        // device [nq][tp_ranges]
     uint32_t* unit_len;        // device [nq][tp_ranges]
     uint32_t* arena;           // device [nq][tp_ranges][kArenaPerSlab * tp_spc]
-    uint32_t* qflag;           // device [nq]
+    uint32_t* qflag;           // device [nq + 2]: flags, then the passes' query counters
     int32_t* qlast;            // device [nq] Alg. 5 threshold of flagged queries
     int64_t* out_ids;
     float* out_dists;

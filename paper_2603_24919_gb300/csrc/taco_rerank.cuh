@@ -83,6 +83,7 @@ struct RerankParams {
     uint32_t* unit_len;     // [nq][n_ranges] entries (ids with SC >= 2)
     uint32_t* arena;        // entries: id relative to the range | SC << 27
     uint32_t* qflag;        // [nq] set when a query needs the fallback (cluster or codes)
+    uint32_t* work;         // [2] zeroed query counters of the counting and the select pass
     int32_t* qlast;         // [nq] last_collision of Alg. 5 of every flagged query
     const uint16_t* codes;  // [Ns][n] cell of every point (codes fallback)
     int fb_mode;            // select_rerank_kernel: 0 two-pass pass 2, 1 codes fallback
@@ -91,6 +92,16 @@ struct RerankParams {
     int32_t* dbg_last;
     int64_t* dbg_cand;
 };
+
+// The next query of a persistent CTA: the grid's first gridDim.x queries are the CTAs' own,
+// later ones are handed out in order by an atomic counter (zeroed before the launch), so a
+// CTA that drew light queries takes more of them. Block-wide (two barriers).
+__device__ __forceinline__ int64_t next_query(uint32_t* counter, int64_t* s_next) {
+    __syncthreads();   // every thread holds the current query in a register
+    if (threadIdx.x == 0) *s_next = int64_t(gridDim.x) + int64_t(atomicAdd(counter, 1u));
+    __syncthreads();
+    return *s_next;
+}
 
 __device__ __forceinline__ bool lt_pair(float a, uint32_t ia, float b, uint32_t ib) {
     return a < b || (a == b && ia < ib);
@@ -934,7 +945,10 @@ select_rerank_kernel(const RerankParams P) {
                                                : reinterpret_cast<const unsigned char*>(P.data);
     const float* qd = kFP8 ? qf : qv;   // what the candidate distances compare against
     const uint64_t pol_stream = l2_policy_stream();
-    for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+    __shared__ int64_t s_next;
+    // two-pass form: queries handed out by a counter; codes fallback: a fixed stride
+    for (int64_t q = blockIdx.x; q < P.nq;
+         q = P.fb_mode ? q + gridDim.x : next_query(P.work + 1, &s_next)) {
         const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
         __syncthreads();
         for (int j = tid; j < P.d_pad; j += kSrThreads) qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;

@@ -1007,7 +1007,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.arena = L.arena;
             P.qflag = L.qflag;
             P.qlast = L.qlast;
-            TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq) * sizeof(uint32_t), st));
+            P.work = L.qflag + L.nq;   // the two query counters follow the flags
+            TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq + 2) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit; 512 or 1024 threads per CTA (tuned)
             const size_t smem1 = P.region_a + kCountListsExtra;
             const int nw1 = ix->tp_count_warps == 32 ? 32 : 16;

@@ -53,7 +53,8 @@ class IndexInfo(C.Structure):
                 ("sub_dim", C.c_int32), ("sqrt_k", C.c_int32), ("d_pad", C.c_int32),
                 ("has_bf16", C.c_int32), ("n_slabs", C.c_int32), ("cluster_size", C.c_int32),
                 ("has_fp8", C.c_int32), ("fp8_pitch", C.c_int32), ("has_centroid_tc", C.c_int32),
-                ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
+                ("reserved", C.c_int32), ("device_bytes", C.c_int64), ("n_ids", C.c_int64),
+                ("build_ms_transform", C.c_double), ("build_ms_index", C.c_double)]
 
 
 class DebugOut(C.Structure):
@@ -118,6 +119,7 @@ SIGNATURES = {
                                     C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
                                     C.POINTER(DebugOut), C.c_void_p]),
     "taco_index_get_info": (C.c_int, [C.c_void_p, C.POINTER(IndexInfo)]),
+    "taco_index_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "taco_index_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     "taco_save_index": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -336,6 +338,17 @@ class TacoIndex:
         inf = IndexInfo()
         _check(load_library().taco_index_get_info(self._h, C.byref(inf)))
         return {f: getattr(inf, f) for f, _ in IndexInfo._fields_}
+
+    def lists(self):
+        """taco_index_lists: the device cell lists as NumPy arrays (sizes [N_s, K], split
+        [N_s, K, n_slabs + 1], ids [n_ids])."""
+        inf = self.info()
+        ns, K = inf["n_subspaces"], inf["sqrt_k"] ** 2
+        out = {"sizes": np.zeros((ns, K), dtype=np.uint32),
+               "split": np.zeros((ns, K, inf["n_slabs"] + 1), dtype=np.uint32),
+               "ids": np.zeros(inf["n_ids"], dtype=np.uint32)}
+        _check(load_library().taco_index_lists(self._h, *[out[k].ctypes.data for k in ("sizes", "split", "ids")]))
+        return out
 
     def export(self):
         inf = self.info()

@@ -78,7 +78,7 @@ int main(void) {
   S(taco_index_parts); P(taco_index_parts, codes); P(taco_index_parts, sqrt_k);
   S(taco_index_info); P(taco_index_info, d_pad); P(taco_index_info, cluster_size);
   P(taco_index_info, has_fp8); P(taco_index_info, fp8_pitch); P(taco_index_info, has_centroid_tc);
-  P(taco_index_info, device_bytes);
+  P(taco_index_info, device_bytes); P(taco_index_info, n_ids); P(taco_index_info, build_ms_index);
   S(taco_debug_out); P(taco_debug_out, candidate_num);
   S(taco_server_params); P(taco_server_params, max_wait_us); P(taco_server_params, slot_bytes);
   P(taco_server_params, use_graphs); P(taco_server_params, probe_precision);

@@ -89,3 +89,45 @@ def test_built_index_recall(built, target):
     o_ids, _, _ = O.search(oix, data, queries, 10, w.budget, target)
     rec_o = O.recall(o_ids, t_ids, 10)
     assert rec >= rec_o - 0.05, (rec, rec_o)
+
+
+def _host_lists(codes, n_slabs, K):
+    """The cell lists as the index lays them out, built on the host from the codes: per
+    subspace and cell the ids ascending (Alg. 3's IMI[cell].append(j) for j = 0..n-1), each
+    list at a multiple of 4 and padded with 0xffffffff, and the slab table of absolute
+    positions of the first id >= t * 2^15 (t = n_slabs: the list's end)."""
+    ns, n = codes.shape
+    sizes = np.zeros((ns, K), dtype=np.int64)
+    split = np.zeros((ns, K, n_slabs + 1), dtype=np.int64)
+    ids, pos = [], 0
+    bounds = np.minimum(np.arange(n_slabs + 1, dtype=np.int64) << 15, n)
+    for i in range(ns):
+        order = np.argsort(codes[i], kind="stable")
+        cuts = np.searchsorted(codes[i][order], np.arange(K + 1))
+        for c in range(K):
+            cell = order[cuts[c]:cuts[c + 1]]
+            sizes[i, c] = len(cell)
+            split[i, c] = pos + np.searchsorted(cell, bounds)
+            ids.append(cell)
+            pad = (-len(cell)) % 4
+            ids.append(np.full(pad, 0xFFFFFFFF, dtype=np.int64))
+            pos += len(cell) + pad
+    return sizes, split, np.concatenate(ids)
+
+
+@pytest.mark.parametrize("n,sk", [(20_000, 16), (100_003, 7), (300_001, 32)])
+def test_device_cell_lists_equal_host_construction(n, sk):
+    """The cell lists and slab table built on the device (a stable counting sort by code, one
+    2^15-id slab at a time) equal the host construction from the exported codes, including a
+    ragged last slab, odd sqrt_k and empty cells; the build reports its two phase times."""
+    w, data, _ = make_workload("tiny20k", n=n, nq=1)
+    ix = TacoIndex.build(data[:, :32], 4, 8, sk, kmeans_iters=4, seed=7)
+    inf = ix.info()
+    got = ix.lists()
+    sizes, split, ids = _host_lists(ix.export()["codes"].astype(np.int64), inf["n_slabs"], sk * sk)
+    assert inf["n_ids"] == len(ids)
+    np.testing.assert_array_equal(got["sizes"], sizes)
+    np.testing.assert_array_equal(got["split"], split)
+    np.testing.assert_array_equal(got["ids"].astype(np.int64), ids)
+    assert inf["build_ms_transform"] > 0 and inf["build_ms_index"] > 0
+    ix.close()
