@@ -903,357 +903,6 @@ count_select_rerank_kernel(const RerankParams P) {
 // below 2, or whose lists did not fit, are flagged for a fallback.
 // ---------------------------------------------------------------------------------------
 
-constexpr int kSrThreads = 256;
-constexpr int kSrWarps = kSrThreads / 32;
-constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
-
-template <int G, int R, int RK>
-__global__ void __launch_bounds__(kSrThreads, 4)
-select_rerank_kernel(const RerankParams P) {
-    constexpr int CPW = 32 / G;
-    constexpr int U = 2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int kkc = P.kkc;
-    float* Ld = reinterpret_cast<float*>(smem);                        // [kSrWarps][kkc]
-    uint32_t* Li = reinterpret_cast<uint32_t*>(Ld + kSrWarps * kkc);    // [kSrWarps][kkc]
-    float* Md = reinterpret_cast<float*>(Li + kSrWarps * kkc);          // [kkc] merged
-    uint32_t* Mi = reinterpret_cast<uint32_t*>(Md + kkc);
-    float* Xd = reinterpret_cast<float*>(Mi + kkc);                     // [kkc] exact (BF16, FP8)
-    uint32_t* Xi = reinterpret_cast<uint32_t*>(Xd + kkc);
-    float* qv = reinterpret_cast<float*>(Xi + kkc);                     // d_pad
-    uint32_t* buf = reinterpret_cast<uint32_t*>(qv + P.d_pad);          // kSrBuf
-    float* qf = reinterpret_cast<float*>(buf + kSrBuf);                 // FP8: [dp8][2]
-    // codes fallback: probed-cell bitmaps [Ns][K / 32] and one batch of cells' runs
-    uint32_t* fbm = reinterpret_cast<uint32_t*>(qf + (RK == kRowFP8 ? 2 * P.dp8 : 0));
-    uint32_t* fpre = fbm + P.Ns * ((P.K + 31) / 32);                    // [kSrThreads + 1]
-    uint32_t* fst = fpre + kSrThreads + 1;                              // [kSrThreads]
-    uint32_t* fsub = fst + kSrThreads;                                  // [kSrThreads]
-    __shared__ int s_fpre[TACO_MAX_SUBSPACES + 1];
-    __shared__ uint32_t s_gs[TACO_MAX_SUBSPACES + 2];
-    __shared__ int s_last;
-    __shared__ uint32_t s_bufn;
-    __shared__ uint32_t s_flag;
-    __shared__ uint32_t s_tmp2[2 * kSrWarps];
-    const int Ns = P.Ns, nr = P.n_ranges, kk = P.kk;
-    const int gid = lane / G, gl = lane % G;
-    constexpr bool kFP8 = RK == kRowFP8;
-    const int nch = (kFP8 ? P.dp8 : P.d_pad) / RowChunk<RK>::kElems;
-    const size_t row_bytes = kFP8 ? size_t(P.dp8) : size_t(P.d_pad) * (RK == kRowBF16 ? 2 : 4);
-    const unsigned char* rows = RK == kRowBF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
-                                : kFP8         ? P.data_fp8
-                                               : reinterpret_cast<const unsigned char*>(P.data);
-    const float* qd = kFP8 ? qf : qv;   // what the candidate distances compare against
-    const uint64_t pol_stream = l2_policy_stream();
-    __shared__ int64_t s_next;
-    // two-pass form: queries handed out by a counter; codes fallback: a fixed stride
-    for (int64_t q = blockIdx.x; q < P.nq;
-         q = P.fb_mode ? q + gridDim.x : next_query(P.work + 1, &s_next)) {
-        const QueryParamsDev qp = P.params ? P.params[q] : P.defaults;
-        __syncthreads();
-        for (int j = tid; j < P.d_pad; j += kSrThreads) qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
-        if constexpr (kFP8) {
-            // (x_c / scale_c, scale_c^2) of the query in the FP8 rows' space: the transformed
-            // query q' (zero past N_s * s) or the centred query q - o_bar (zero past d)
-            const int cols = P.fp8_space ? P.d : P.Dp;
-            for (int j = tid; j < P.dp8; j += kSrThreads) {
-                const float sc = P.fp8_scale[j];
-                float x = 0.f;
-                if (j < cols) x = P.fp8_space ? P.queries[q * P.d + j] - P.obar[j] : P.qt[q * P.Dp + j];
-                qf[2 * j] = j < cols ? x * P.fp8_scale[P.dp8 + j] : 0.f;
-                qf[2 * j + 1] = j < cols ? sc * sc : 0.f;
-            }
-        }
-        if (tid <= TACO_MAX_SUBSPACES + 1) s_gs[tid] = 0u;
-        if (tid == 0) {
-            s_bufn = 0u;
-            s_flag = P.qflag[q];
-            if (P.fb_mode) s_last = P.qlast[q];
-        }
-        __syncthreads();
-        if (P.fb_mode && !s_flag) continue;   // the fallback answers flagged queries only
-        if (!P.fb_mode) {
-        // Alg. 5 over the summed level counts of the query's ranges
-        if (tid < Ns) {
-            uint32_t v = 0;
-            for (int r = 0; r < nr; ++r) v += P.unit_ge[(q * nr + r) * 16 + tid + 1];
-            s_gs[tid + 1] = v;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            long long gs[TACO_MAX_SUBSPACES + 2];
-            gs[0] = P.n;
-            for (int j = 1; j <= Ns; ++j) gs[j] = s_gs[j];
-            gs[Ns + 1] = 0;
-            int last = Ns;
-            long long cand = 0;
-            for (int j = Ns; j >= 0; --j) {
-                const long long h = gs[j] - gs[j + 1];
-                cand += h;
-                const bool go = qp.select_rule == TACO_SELECT_LITERAL ? (h <= qp.rerank_target - cand)
-                                                                     : (cand <= qp.rerank_target);
-                if (go) --last;
-                else break;
-            }
-            s_last = last;
-            if (P.dbg_hist)
-                for (int j = 0; j <= Ns; ++j) P.dbg_hist[q * (Ns + 1) + j] = gs[j] - gs[j + 1];
-            if (P.dbg_last) P.dbg_last[q] = last;
-            if (P.dbg_cand) P.dbg_cand[q] = cand;
-            if (last < 2) {
-                s_flag = 1u;
-                P.qflag[q] = 1u;   // candidates below level 2 are not in the lists
-            }
-            if (s_flag && P.qlast) P.qlast[q] = last;
-        }
-        __syncthreads();
-        if (s_flag) continue;   // answered by the fallback
-        }   // !fb_mode
-        const int last = s_last;
-        // this query's list length (see the cluster kernel): each warp keeps its qp.kk nearest
-        const int kq = min(qp.kk, kk);
-        WarpTop<R> top;
-        top.init();
-        float kth_d = __int_as_float(0x7f800000);
-        uint32_t kth_i = kNoId;
-        auto rerank_buffer = [&](int m) {
-            for (int b0 = warp * CPW * U; b0 < m; b0 += kSrWarps * CPW * U) {
-                float acc[U];
-                uint32_t cid[U];
-                bool val[U];
-                gather_distances<G, RK>(rows, row_bytes, nch, qd, buf, b0, m, acc, cid, val, gid, gl,
-                                          pol_stream);
-#pragma unroll
-                for (int uu = 0; uu < U; ++uu) {
-                    const bool better = val[uu] && gl == 0 && lt_pair(acc[uu], cid[uu], kth_d, kth_i);
-                    unsigned bal = __ballot_sync(kFull, better);
-                    while (bal) {
-                        const int src = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                        const float x = __shfl_sync(kFull, acc[uu], src);
-                        const uint32_t xi = __shfl_sync(kFull, cid[uu], src);
-                        if (lt_pair(x, xi, kth_d, kth_i)) {
-                            top.insert(x, xi, kq, lane);
-                            top.kth(kq, kth_d, kth_i);
-                        }
-                    }
-                }
-            }
-        };
-        // flush the candidate buffer if a tile of kSrThreads more might not fit (block-wide)
-        auto make_room = [&]() {
-            if (s_bufn + kSrThreads > uint32_t(kSrBuf)) {
-                __syncthreads();
-                rerank_buffer(int(s_bufn));
-                __syncthreads();
-                if (tid == 0) s_bufn = 0u;
-                __syncthreads();
-            }
-        };
-        if (P.fb_mode) {
-            // codes fallback: SC(id) = #subspaces i with code_i(id) probed (Def. 6), from the
-            // cell codes and per-subspace bitmaps of the probed cells; every probed id is
-            // taken once (in the first subspace that probed it) if SC >= last; last <= 0
-            // takes every point (Alg. 5 reaching level 0)
-            if (last <= 0) {
-                for (int64_t t0 = 0; t0 < P.n; t0 += kSrThreads) {
-                    make_room();
-                    const int64_t id = t0 + tid;
-                    const bool take = id < P.n;
-                    const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-                    if (take) buf[at] = uint32_t(id);
-                    __syncthreads();
-                }
-            } else {
-                const int Kw = (P.K + 31) / 32;
-                if (warp == 0) load_cell_prefix(P, q, s_fpre, lane);
-                for (int w = tid; w < Ns * Kw; w += kSrThreads) fbm[w] = 0u;
-                __syncthreads();
-                const int total_cells = s_fpre[Ns];
-                for (int t = tid; t < total_cells; t += kSrThreads) {
-                    int i = 0;
-                    while (t >= s_fpre[i + 1]) ++i;
-                    const int c = P.cells[(q * Ns + i) * P.K + (t - s_fpre[i])];
-                    atomicOr(&fbm[i * Kw + (c >> 5)], 1u << (c & 31));
-                }
-                __syncthreads();
-                const int sstride = P.n_slabs + 1;
-                for (int cb0 = 0; cb0 < total_cells; cb0 += kSrThreads) {
-                    // this batch's cells: their full id runs, prefix of their lengths
-                    uint32_t len = 0;
-                    const int g = cb0 + tid;
-                    if (g < total_cells) {
-                        int i = 0;
-                        while (g >= s_fpre[i + 1]) ++i;
-                        const int c = P.cells[(q * Ns + i) * P.K + (g - s_fpre[i])];
-                        const uint32_t* sp = P.split + (size_t(i) * P.K + c) * sstride;
-                        fst[tid] = sp[0];
-                        fsub[tid] = uint32_t(i);
-                        len = sp[P.n_slabs] - sp[0];
-                    }
-                    uint2 tot;
-                    const uint2 ex = block_excl_scan2<kSrWarps>(len, 0u, s_tmp2, tot, lane, warp);
-                    fpre[tid] = ex.x;
-                    if (tid == 0) fpre[kSrThreads] = tot.x;
-                    __syncthreads();
-                    const int nb = min(kSrThreads, total_cells - cb0);
-                    for (uint32_t e0 = 0; e0 < tot.x; e0 += kSrThreads) {
-                        make_room();
-                        const uint32_t e = e0 + uint32_t(tid);
-                        bool take = false;
-                        uint32_t id = 0;
-                        if (e < tot.x) {
-                            int lo_c = 0, hi_c = nb - 1;   // the cell holding element e
-                            while (lo_c < hi_c) {
-                                const int mid = (lo_c + hi_c + 1) >> 1;
-                                if (fpre[mid] <= e) lo_c = mid;
-                                else hi_c = mid - 1;
-                            }
-                            id = P.ids[fst[lo_c] + (e - fpre[lo_c])];
-                            const int own = int(fsub[lo_c]);
-                            int sc = 0;
-                            bool dup = false;
-                            for (int i = 0; i < Ns; ++i) {
-                                const uint32_t c = P.codes[size_t(i) * P.n + id];
-                                const bool p = (fbm[i * Kw + (c >> 5)] >> (c & 31)) & 1u;
-                                sc += p;
-                                dup |= p && i < own;
-                            }
-                            take = !dup && sc >= last;
-                        }
-                        const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-                        if (take) buf[at] = id;
-                        __syncthreads();
-                    }
-                }
-            }
-        } else {
-        // candidates: the list entries with SC >= last of all the query's ranges as one
-        // sequence (range r's entries are upre[r] .. upre[r + 1] - 1), in tiles of kSrThreads;
-        // the buffer is re-ranked and emptied before a tile that would not fit
-        uint32_t* upre = fbm;            // [nr + 1] (the fallback's bitmaps are not in use)
-        uint32_t* uoff = upre + nr + 1;  // [nr]
-        uint32_t nent = 0;
-        for (int r0 = 0; r0 < nr; r0 += kSrThreads) {
-            const int r = r0 + tid;
-            uint32_t len = 0;
-            if (r < nr) {
-                len = P.unit_len[q * nr + r];
-                uoff[r] = P.unit_off[q * nr + r];
-            }
-            uint2 tot;
-            const uint2 ex = block_excl_scan2<kSrWarps>(len, 0u, s_tmp2, tot, lane, warp);
-            if (r < nr) upre[r] = nent + ex.x;
-            nent += tot.x;
-        }
-        if (tid == 0) upre[nr] = nent;
-        __syncthreads();
-        for (uint32_t t0 = 0; t0 < nent; t0 += kSrThreads) {
-            make_room();
-            const uint32_t t = t0 + tid;
-            uint32_t x = 0, rlo = 0;
-            bool take = false;
-            if (t < nent) {
-                int lo_r = 0, hi_r = nr - 1;   // the range holding entry t
-                while (lo_r < hi_r) {
-                    const int mid = (lo_r + hi_r + 1) >> 1;
-                    if (upre[mid] <= t) lo_r = mid;
-                    else hi_r = mid - 1;
-                }
-                x = P.arena[uoff[lo_r] + (t - upre[lo_r])];
-                take = int(x >> kLevelShift) >= last;
-                rlo = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
-            }
-            const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-            if (take) buf[at] = rlo + (x & ((1u << kLevelShift) - 1u));
-            __syncthreads();
-        }
-        }
-        __syncthreads();
-        rerank_buffer(int(s_bufn));
-        // warp lists -> one sorted list
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-            const int e = rr * 32 + lane;
-            if (e < kk) {
-                Ld[warp * kkc + e] = top.d[rr];
-                Li[warp * kkc + e] = top.i[rr];
-            }
-        }
-        __syncthreads();
-        if (warp == 0) warp_merge(Ld, Li, kkc, kSrWarps, kq, Md, Mi, lane);
-        __syncthreads();
-        // the query's own shortlist: the first qp.kk (kq) of the merged list (a batch's lists
-        // are as long as its longest one; a shorter shortlist is a prefix of them)
-        if constexpr (RK != kRowF32) {
-            // exact FP32 distances of the shortlist, then rank sort by (distance, id)
-            const int nf4 = P.d_pad / 4;
-            const float4* q4 = reinterpret_cast<const float4*>(qv);
-            for (int e = warp; e < kq; e += kSrWarps) {
-                const uint32_t id = Mi[e];
-                float acc = 0.f;
-                if (id != kNoId) {
-                    const float4* row = reinterpret_cast<const float4*>(P.data + size_t(id) * P.d_pad);
-                    for (int f = lane; f < nf4; f += 32) acc = sq4(__ldg(row + f), q4[f], acc);
-                }
-#pragma unroll
-                for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-                if (lane == 0) {
-                    Xd[e] = id != kNoId ? acc : __int_as_float(0x7f800000);
-                    Xi[e] = id;
-                }
-            }
-            __syncthreads();
-            for (int e = tid; e < kq; e += kSrThreads) {
-                const float x = Xd[e];
-                const uint32_t xid = Xi[e];
-                int rank = 0;
-                for (int f = 0; f < kq; ++f)
-                    rank += lt_pair(Xd[f], Xi[f], x, xid) || (Xd[f] == x && Xi[f] == xid && f < e);
-                Md[rank] = x;
-                Mi[rank] = xid;
-            }
-            __syncthreads();
-        }
-        for (int t = tid; t < P.k_stride; t += kSrThreads) {
-            const bool ok = t < qp.k && t < kq && Mi[t] != kNoId;
-            P.out_ids[q * P.k_stride + t] = ok ? int64_t(Mi[t]) : int64_t(-1);
-            P.out_dists[q * P.k_stride + t] = ok ? sqrtf(Md[t]) : __int_as_float(0x7f800000);
-        }
-    }
-}
-
-template <int G, int R, int RK>
-cudaError_t launch_select_rerank_t(const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
-    auto kern = select_rerank_kernel<G, R, RK>;
-    // two cached shapes per instance: the two-pass form and the codes fallback
-    static thread_local size_t cached_smem_v[2] = {0, 0};
-    static thread_local int cached_blocks_v[2] = {0, 0};
-    const int slot = P.fb_mode ? 1 : 0;
-    size_t& cached_smem = cached_smem_v[slot];
-    int& cached_blocks = cached_blocks_v[slot];
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return g_launch_step = "an earlier unchecked call", e;
-    if (cached_smem != smem) {
-        e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
-        if (e != cudaSuccess) return g_launch_step = "cudaFuncSetAttribute", e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSrThreads, smem);
-        if (e != cudaSuccess) return g_launch_step = "cudaOccupancyMaxActiveBlocksPerMultiprocessor", e;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (per_sm * sms < 1) return g_launch_step = "occupancy (no block fits)", cudaErrorInvalidConfiguration;
-        cached_blocks = per_sm * sms;
-        cached_smem = smem;
-    }
-    const int64_t blocks = nq < cached_blocks ? nq : cached_blocks;
-    kern<<<unsigned(blocks), kSrThreads, smem, st>>>(P);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) g_launch_step = "launch";
-    return e;
-}
-
 template <int G, int R, bool BF16>
 cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size_t smem,
                             cudaStream_t st) {
@@ -1315,9 +964,7 @@ cudaError_t launch_rerank_t(const RerankParams& P, int cluster, int64_t nq, size
 // One translation unit per (row type, R) instantiates the four G variants.
 #define TACO_DECLARE_RERANK(B, R)                                                            \
     cudaError_t launch_rerank_b##B##_r##R(int G, const RerankParams& P, int cluster, int64_t nq, \
-                                          size_t smem, cudaStream_t st);                         \
-    cudaError_t launch_select_b##B##_r##R(int G, const RerankParams& P, int64_t nq, size_t smem,  \
-                                          cudaStream_t st);
+                                          size_t smem, cudaStream_t st);
 TACO_DECLARE_RERANK(0, 1)
 TACO_DECLARE_RERANK(0, 4)
 TACO_DECLARE_RERANK(0, 16)
@@ -1325,9 +972,10 @@ TACO_DECLARE_RERANK(1, 1)
 TACO_DECLARE_RERANK(1, 4)
 TACO_DECLARE_RERANK(1, 16)
 #undef TACO_DECLARE_RERANK
-// FP8 rows: the select / re-rank pass only (fallback queries re-rank with FP32 rows).
-cudaError_t launch_select_b2_r1(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
-cudaError_t launch_select_b2_r4(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
-cudaError_t launch_select_b2_r16(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
+// The select / re-rank pass (taco_select.cuh) per row kind (FP8 rows have this pass only;
+// fallback queries re-rank with FP32 rows).
+cudaError_t launch_select_b0(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
+cudaError_t launch_select_b1(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
+cudaError_t launch_select_b2(int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st);
 
 }  // namespace taco

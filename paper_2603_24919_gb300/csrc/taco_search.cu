@@ -20,6 +20,7 @@
 #include "taco_internal.h"
 #include "taco_count.cuh"
 #include "taco_rerank.cuh"
+#include "taco_select.cuh"
 
 namespace taco {
 
@@ -840,21 +841,10 @@ static int prof_end_n(taco_index* ix, int slot, int kernels, cudaStream_t st, cu
     return prof_end(ix, slot | (kernels << 8), st, b, e);
 }
 
-// The select / re-rank kernel for a row kind (0 FP32, 1 BF16, 2 FP8), register-list size R
-// (1, 4, 16) and G lanes per row.
-static cudaError_t launch_select(int rk, int R, int G, const RerankParams& P, int64_t nq, size_t smem,
-                                 cudaStream_t st) {
-    if (rk == 2)
-        return R == 1 ? launch_select_b2_r1(G, P, nq, smem, st)
-               : R == 4 ? launch_select_b2_r4(G, P, nq, smem, st)
-                        : launch_select_b2_r16(G, P, nq, smem, st);
-    if (rk == 1)
-        return R == 1 ? launch_select_b1_r1(G, P, nq, smem, st)
-               : R == 4 ? launch_select_b1_r4(G, P, nq, smem, st)
-                        : launch_select_b1_r16(G, P, nq, smem, st);
-    return R == 1 ? launch_select_b0_r1(G, P, nq, smem, st)
-           : R == 4 ? launch_select_b0_r4(G, P, nq, smem, st)
-                    : launch_select_b0_r16(G, P, nq, smem, st);
+// The select / re-rank kernel for a row kind (0 FP32, 1 BF16, 2 FP8) with G lanes per row.
+static cudaError_t launch_select(int rk, int G, const RerankParams& P, int64_t nq, size_t smem, cudaStream_t st) {
+    return rk == 2 ? launch_select_b2(G, P, nq, smem, st)
+                   : (rk == 1 ? launch_select_b1(G, P, nq, smem, st) : launch_select_b0(G, P, nq, smem, st));
 }
 
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
@@ -1032,11 +1022,9 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             TACO_CUDA(cudaGetLastError());
             if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results
-            const size_t smem2 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 +
-                                 size_t(ix->d_pad) * 4 + size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0) +
-                                 size_t(2 * P.n_ranges + 1) * 4;   // the ranges' list offsets
+            const size_t smem2 = select_smem_bytes(P.kkc, ix->d_pad, fp8 ? ix->dp8 : 0, P.n_ranges, ix->Ns, K, false);
             if (int rc = prof_begin(pix, 3, st, &pb, &pe)) return rc;
-            const cudaError_t e = launch_select(rk, R, Gs, P, L.nq, smem2, st);
+            const cudaError_t e = launch_select(rk, Gs, P, L.nq, smem2, st);
             if (e != cudaSuccess) return cuda_fail(e, "select_rerank launch", __FILE__, __LINE__);
             if (int rc = prof_end(pix, 3, st, pb, pe)) return rc;
             P.qmask = L.qflag;   // the cluster kernel below only answers flagged queries
@@ -1051,11 +1039,9 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.codes = ix->d_codes;
             P.slabs_per_cta = ix->tp_spc;
             P.n_ranges = ix->tp_ranges;
-            const size_t smem3 = (size_t(2) * kSrWarps * P.kkc + 4 * size_t(P.kkc)) * 4 + size_t(ix->d_pad) * 4 +
-                                 size_t(kSrBuf) * 4 + (fp8 ? size_t(ix->dp8) * 8 : 0) +
-                                 size_t(ix->Ns) * ((K + 31) / 32) * 4 + size_t(3 * kSrThreads + 1) * 4;
+            const size_t smem3 = select_smem_bytes(P.kkc, ix->d_pad, fp8 ? ix->dp8 : 0, P.n_ranges, ix->Ns, K, true);
             if (int rc = prof_begin(pix, 4, st, &pb, &pe)) return rc;
-            const cudaError_t e = launch_select(rk, R, Gs, P, L.nq, smem3, st);
+            const cudaError_t e = launch_select(rk, Gs, P, L.nq, smem3, st);
             if (e != cudaSuccess) return cuda_fail(e, "codes fallback launch", __FILE__, __LINE__);
             if (int rc = prof_end(pix, 4, st, pb, pe)) return rc;
             return TACO_OK;
