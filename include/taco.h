@@ -261,9 +261,9 @@ int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq
  *   TACO_OPT_SLABS_PER_RANGE: counter slabs per id range of the two-pass counting, 1 .. 12
  *   (a value above the index's n_slabs acts as n_slabs; n_ranges follows; TACO_ECAPACITY at
  *   search time if the counters do not fit an SM).
- *   TACO_OPT_COUNT_WARPS: warps per counting CTA, 16 or 32.
- *   TACO_OPT_WALK_UNROLL: loads of four ids in flight per lane in the counting walk, 4 or 8
- *   (8 takes effect with 16 warps only).
+ *   TACO_OPT_COUNT_WARPS: warps per counting CTA, 8, 16 or 32.
+ *   TACO_OPT_WALK_UNROLL: loads of four ids in flight per lane in the counting walk, 2, 4 or 8
+ *   (8 takes effect with 16 warps only; an unbuilt pair runs 16 warps x 4).
  *   The last three are the choices taco_autotune makes; they change no result beyond the FP32
  *   summation order of a distance. Other values: TACO_EINVAL.
  * Must not run while searches or a server use the index.
@@ -286,9 +286,9 @@ typedef struct {
     int32_t n_ranges;          /* id ranges per query */
     int32_t lanes_per_row;     /* lanes gathering one candidate row in the re-rank (0 = auto) */
     int32_t probe_walk;        /* -1: row-merge walk for small budgets (auto), 0: histogram only */
-    int32_t count_warps;       /* warps per CTA of the counting pass (16 or 32) */
-    int32_t walk_unroll;       /* loads of four ids in flight per lane in its walk (4, or 8 with 16
-                                  warps) */
+    int32_t count_warps;       /* warps per CTA of the counting pass (8, 16 or 32) */
+    int32_t walk_unroll;       /* loads of four ids in flight per lane in its walk (2 or 4, or 8
+                                  with 16 warps) */
     double ms_before;          /* mean ms of one search of the sample before tuning */
     double ms_after;           /* with the chosen layout */
     int32_t trials;            /* searches timed */

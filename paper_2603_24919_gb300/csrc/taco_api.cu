@@ -851,11 +851,11 @@ int taco_index_set_option(taco_index* ix, int32_t option, int32_t value) {
             ix->tp_ranges = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
             return TACO_OK;
         case TACO_OPT_COUNT_WARPS:
-            if (value != 16 && value != 32) return fail(TACO_EINVAL, "count warps %d: 16 or 32", value);
+            if (value != 8 && value != 16 && value != 32) return fail(TACO_EINVAL, "count warps %d: 8, 16 or 32", value);
             ix->tp_count_warps = value;
             return TACO_OK;
         case TACO_OPT_WALK_UNROLL:
-            if (value != 4 && value != 8) return fail(TACO_EINVAL, "walk unroll %d: 4 or 8", value);
+            if (value != 2 && value != 4 && value != 8) return fail(TACO_EINVAL, "walk unroll %d: 2, 4 or 8", value);
             ix->tp_walk_unroll = value;
             return TACO_OK;
         default: return fail(TACO_EINVAL, "unknown option %d", option);

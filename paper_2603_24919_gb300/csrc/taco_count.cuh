@@ -37,6 +37,12 @@ __device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
 
 constexpr int kChunkListCap = 4096;   // ids that reached SC = 2 in a unit (listed once each)
 
+// Level-list capacity of a unit: its arena slot (a longer list would not fit the slot anyway),
+// at most kChunkListCap.
+__host__ __device__ __forceinline__ int count_list_cap(int slabs_per_range) {
+    return min(kChunkListCap, int(kArenaPerSlab) * slabs_per_range);
+}
+
 // Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address into L2;
 // no completion to wait for.
 __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
@@ -46,9 +52,10 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
 // Shared memory of count_lists_kernel past the counters (bytes): split bounds of the staged
 // cells for three ranges, the level list, the staged chunk runs, the exact-level histogram
 // and the staged cells.
-constexpr size_t kCountListsExtra = size_t(3) * kCellBatch * 8 + size_t(kChunkListCap) * 4 +
-                                    size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 16 * 4 +
-                                    size_t(kCellBatch) * 4;
+__host__ __device__ __forceinline__ size_t count_lists_extra(int slabs_per_range) {
+    return size_t(3) * kCellBatch * 8 + size_t(count_list_cap(slabs_per_range)) * 4 + size_t(kCellBatch) * 4 +
+           size_t(kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
+}
 
 // The chunk run of id positions [b, e) of one cell list: chunks [b / 4, ceil(e / 4)), none
 // when the run is empty. Cell lists start on chunk boundaries, so the chunks stay inside the
@@ -67,19 +74,26 @@ __device__ __forceinline__ void chunk_run(uint32_t b, uint32_t e, uint32_t& star
 // g mod NW. Lane u finds the run of the first chunk of window u (binary search); in a window,
 // lane j reads the j-th next run boundary, the boundaries inside the window form a bit mask,
 // and a lane's run is the window's first run plus the mask bits at or below it (runs are
-// non-empty, so at most 32 boundaries fall in a window). Lanes past the end load a valid
-// chunk and count nothing. Appends beyond kChunkListCap are dropped (the caller sees the
-// overflow in *s_app). Warp-level; no barrier.
+// non-empty, so at most 32 boundaries fall in a window). Rounds are handed to warps by a
+// shared counter (*s_round, zero on entry), so warps that drew short work take more. Lanes
+// past the end load a valid chunk and count nothing: their atomics add 0 to the lane's own
+// dummy word (dummy[lane], which stays 0), so no branch depends on the data. Appends beyond
+// list_cap are dropped (the caller sees the overflow in *s_app). Warp-level; no barrier.
 template <int NW, int WU>
 __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint32_t last_chunk, uint32_t lo,
                                             uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
-                                            uint32_t* lst, uint32_t* s_app, const uint32_t* cpre,
-                                            const uint32_t* rbase, uint64_t pol, int lane, int warp) {
+                                            uint32_t* dummy, uint32_t* lst, uint32_t list_cap, uint32_t* s_app,
+                                            uint32_t* s_round, const uint32_t* cpre, const uint32_t* rbase,
+                                            uint64_t pol, int lane) {
     static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU list bits a lane");
     const uint32_t lane_le = (2u << lane) - 1u;   // lanes 0..lane
     constexpr uint32_t kRound = 32u * WU;
     const uint32_t nrounds = (total + kRound - 1) / kRound;
-    for (uint32_t g = uint32_t(warp); g < nrounds; g += NW) {   // warp-uniform
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(s_round, 1u);
+        g = __shfl_sync(kFull, g, 0);   // warp-uniform
+        if (g >= nrounds) break;
         const uint32_t e0 = g * kRound;
         const uint32_t key = min(e0 + 32u * uint32_t(lane % WU), total - 1u);
         const uint32_t cwl = uint32_t(find_cell(cpre, int(nr), key));
@@ -108,8 +122,8 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
                 const uint32_t x = w4[h] - lo;
                 const bool ok = ((live >> u) & 1u) && x < rlen;
                 const uint32_t sh = (x & 7u) << 2;
-                uint32_t old = 0;
-                if (ok) old = atomicAdd(&cnt[x >> 3], 1u << sh);
+                uint32_t* word = ok ? &cnt[x >> 3] : &dummy[lane];
+                const uint32_t old = atomicAdd(word, ok ? 1u << sh : 0u);
                 amask |= (((old >> sh) & 15u) == 1u ? 1u : 0u) << (4 * u + h);
                 rel[u][h] = x;
             }
@@ -132,7 +146,7 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
 #pragma unroll
                 for (int h = 0; h < 4; ++h)
                     if ((amask >> (4 * u + h)) & 1u) {
-                        if (pos < uint32_t(kChunkListCap)) lst[pos] = rel[u][h];
+                        if (pos < list_cap) lst[pos] = rel[u][h];
                         ++pos;
                     }
         }
@@ -171,20 +185,22 @@ __device__ __forceinline__ void ge_from_counters(int Ns, int words, const uint32
 
 // NW warps per CTA, WU windows of 32 chunks per walk round.
 template <int NW, int WU>
-__global__ void __launch_bounds__(NW * 32, (NW == 16 && WU <= 4) ? 2 : 1)
+__global__ void __launch_bounds__(NW * 32, (NW == 8 || (NW == 16 && WU <= 4)) ? 2 : 1)
 count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+    const uint32_t list_cap = uint32_t(count_list_cap(P.slabs_per_cta));
     uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [3][kCellBatch]
-    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 3 * kCellBatch);      // kChunkListCap
-    uint32_t* rbase = lst + kChunkListCap;                                    // kCellBatch
+    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 3 * kCellBatch);      // list_cap
+    uint32_t* rbase = lst + list_cap;                                         // kCellBatch
     uint32_t* cpre = rbase + kCellBatch;                                      // kCellBatch + kRunPad
     uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
     uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * NW];
-    __shared__ uint32_t s_app, s_outn, s_ev;
+    __shared__ uint32_t s_app, s_outn, s_ev, s_round;
+    __shared__ uint32_t s_dummy[32];   // the atomics of lanes with nothing to count (stay 0)
     __shared__ uint32_t s_h[16];   // ids of the unit with SC exactly s (s >= 2), from the list
     const int Ns = P.Ns, K = P.K;
     const int sstride = P.n_slabs + 1;
@@ -192,6 +208,7 @@ count_lists_kernel(const RerankParams P) {
     const uint4* ids4 = reinterpret_cast<const uint4*>(P.ids);
     const uint32_t last_chunk = uint32_t(P.n_ids / 4) - 1u;
     for (int w = tid; w < P.counter_words; w += NW * 32) cnt[w] = 0u;
+    if (tid < 32) s_dummy[tid] = 0u;
     // the split bounds of every staged cell for range r, into pairs[buf] (asynchronous)
     auto prefetch = [&](int total_cells, int r, int buf) {
         const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
@@ -221,9 +238,10 @@ count_lists_kernel(const RerankParams P) {
         chunk_run(b, e, start, len);
         const uint32_t ev = __reduce_add_sync(kFull, e - b);
         if (lane == 0 && ev) atomicAdd(&s_ev, ev);
+        if (tid == 0) s_round = 0u;   // read after the staging's barriers
         const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-        if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, lo, rlen, st.x, st.y, cnt, lst, &s_app, cpre, rbase,
-                                      pol_keep, lane, warp);
+        if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, lo, rlen, st.x, st.y, cnt, s_dummy, lst, list_cap, &s_app,
+                                      &s_round, cpre, rbase, pol_keep, lane);
     };
     __shared__ int64_t s_next;
     for (int64_t q = blockIdx.x; q < P.nq; q = next_query(P.work, &s_next)) {
@@ -292,7 +310,7 @@ count_lists_kernel(const RerankParams P) {
             // every listed id has SC >= 2 and is listed once: its final count is its level;
             // the histogram of levels and the tagged entries in the unit's arena slot
             const uint32_t nlist = s_app;
-            const bool overflow = nlist > uint32_t(kChunkListCap);
+            const bool overflow = nlist > list_cap;
             if (!overflow) {
                 uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
                 const uint32_t lane_lt = (1u << lane) - 1u;

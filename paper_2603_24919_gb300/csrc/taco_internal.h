@@ -92,8 +92,8 @@ struct taco_index {
     int tp_spc = 1, tp_ranges = 1;        // slabs per id range of the two-pass counting, ranges
     int tp_lanes[3] = {0, 0, 0};          // lanes per row of the re-rank per row kind (0: auto)
     int tp_walk = -1;                     // probe by row-merge walk: -1 auto, 0 never, 1 when it fits
-    int tp_count_warps = 16;              // warps per CTA of the counting pass (16 or 32)
-    int tp_walk_unroll = 4;               // windows of 32 four-id chunks per round of its walk (4 or 8)
+    int tp_count_warps = 16;              // warps per CTA of the counting pass (8, 16 or 32)
+    int tp_walk_unroll = 4;               // windows of 32 four-id chunks per round of its walk (2, 4 or 8)
     // Fallback for flagged queries: the cluster kernel (all counters of a query in one
     // cluster's shared memory) or, when n is too large for that (cluster == 0) or when
     // chosen (taco_index_set_option), the codes fallback of select_rerank_kernel.

@@ -999,15 +999,26 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.qlast = L.qlast;
             P.work = L.qflag + L.nq;   // the two query counters follow the flags
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq + 2) * sizeof(uint32_t), st));
-            // pass 1: counting per (query, id range) unit; 512 or 1024 threads per CTA (tuned)
-            const size_t smem1 = P.region_a + kCountListsExtra;
-            const int nw1 = ix->tp_count_warps == 32 ? 32 : 16;
-            // variants: 16 warps x 4 chunk windows per walk round, 32 x 4, 16 x 8
-            const int c1 = nw1 == 32 ? 1 : (ix->tp_walk_unroll == 8 ? 2 : 0);
-            auto k1 = c1 == 1 ? count_lists_kernel<32, 4> : (c1 == 2 ? count_lists_kernel<16, 8>
-                                                                   : count_lists_kernel<16, 4>);
-            static thread_local size_t c1_smem[3] = {0, 0, 0};
-            static thread_local int c1_blocks[3] = {0, 0, 0};
+            // pass 1: counting per (query, id range) unit; 256, 512 or 1024 threads per CTA and
+            // 2, 4 or 8 chunk windows per walk round (tuned)
+            const size_t smem1 = P.region_a + count_lists_extra(P.slabs_per_cta);
+            struct CountVariant {
+                int nw, wu;
+                void (*fn)(const RerankParams);
+            };
+            static const CountVariant kVariants[] = {
+                {8, 2, count_lists_kernel<8, 2>},   {8, 4, count_lists_kernel<8, 4>},
+                {16, 2, count_lists_kernel<16, 2>}, {16, 4, count_lists_kernel<16, 4>},
+                {16, 8, count_lists_kernel<16, 8>}, {32, 2, count_lists_kernel<32, 2>},
+                {32, 4, count_lists_kernel<32, 4>}};
+            constexpr int kNumVariants = int(sizeof(kVariants) / sizeof(kVariants[0]));
+            int c1 = 3;   // 16 x 4 unless the tuned pair exists
+            for (int v = 0; v < kNumVariants; ++v)
+                if (kVariants[v].nw == ix->tp_count_warps && kVariants[v].wu == ix->tp_walk_unroll) c1 = v;
+            const int nw1 = kVariants[c1].nw;
+            auto k1 = kVariants[c1].fn;
+            static thread_local size_t c1_smem[kNumVariants] = {};
+            static thread_local int c1_blocks[kNumVariants] = {};
             if (c1_smem[c1] != smem1) {
                 TACO_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(k1), smem1));
                 int per_sm = 0, sms = 0;

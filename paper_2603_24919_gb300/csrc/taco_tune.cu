@@ -4,8 +4,8 @@
 //     (16 KB of 4-bit counters per slab in shared memory; fewer slabs per range = more,
 //     smaller units per query and more resident CTAs; more = fewer units, longer walks),
 //   - the lanes that gather one candidate row in the select / re-rank pass (4 .. 32),
-//   - the threads of a counting CTA (512 or 1024) and the depth of its walk (4 or 8 loads of
-//     four ids in flight per lane; 8 only with 512 threads),
+//   - the threads of a counting CTA (256, 512 or 1024) and the depth of its walk (2, 4 or 8
+//     loads of four ids in flight per lane),
 //   - whether small budgets are probed by the row-merge walk or always by the histogram
 //     kernel.
 // The choices change no result beyond the summation order of a candidate's FP32 distance
@@ -116,9 +116,11 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
             return rc;
         }
     }
-    // 1b. threads of the counting CTA (512: two CTAs per SM where they fit; 1024: one) and
-    //     the depth of its walk (8 chunk loads in flight per lane: one 512-thread CTA per SM)
-    for (const int2 v : {make_int2(16, 4), make_int2(32, 4), make_int2(16, 8)}) {
+    // 1b. threads of the counting CTA (256 or 512: two CTAs per SM where the counters fit;
+    //     1024: one) and the depth of its walk (2, 4 or 8 chunk loads in flight per lane; 8
+    //     only with 512 threads)
+    for (const int2 v : {make_int2(16, 4), make_int2(16, 2), make_int2(8, 2), make_int2(8, 4),
+                         make_int2(32, 2), make_int2(32, 4), make_int2(16, 8)}) {
         if (v.x == cur.warps && v.y == cur.unroll) continue;
         Choice c = cur;
         c.warps = v.x;

@@ -54,7 +54,7 @@ def test_autotune_keeps_parity(multislab, precision):
     assert r["trials"] >= 5 and 0 < r["ms_after"] <= r["ms_before"]
     assert r["slabs_per_range"] in (1, 2, 4, 5, 8) and r["n_ranges"] * r["slabs_per_range"] >= 10
     assert r["lanes_per_row"] in (0, 4, 8, 16, 32) and r["probe_walk"] in (-1, 0)
-    assert r["count_warps"] in (16, 32) and r["walk_unroll"] in (4, 8)
+    assert r["count_warps"] in (8, 16, 32) and r["walk_unroll"] in (2, 4, 8)
     _parity(ix, oix, data, queries, 10, b, t)
     after_ids, _ = ix.search(q, 10, b, t, precision=precision, shortlist_mult=2)
     same = (before_ids == after_ids).all(dim=1).float().mean().item()
@@ -78,7 +78,8 @@ def test_every_counter_layout_matches_oracle(multislab):
 
 
 @pytest.mark.parametrize("spc,warps,unroll", [(4, 16, 4), (4, 32, 4), (4, 16, 8), (12, 16, 8),
-                                              (1, 16, 8), (8, 32, 8), (5, 16, 4)])
+                                              (1, 16, 8), (8, 32, 2), (5, 16, 4), (5, 8, 2),
+                                              (3, 8, 4), (12, 16, 2)])
 def test_forced_count_variants_match_oracle(multislab, spc, warps, unroll):
     """Each (slabs per range, warps, walk depth) variant of the counting pass, including
     one-slab ranges and a range wider than the index (12 > 10 slabs)."""
@@ -95,7 +96,7 @@ def test_forced_count_variants_match_oracle(multislab, spc, warps, unroll):
 def test_count_layout_rejects_bad_values(multislab):
     from paper_2603_24919_gb300 import TacoError
     data, queries, oix, ix = multislab
-    for kw in (dict(slabs_per_range=0), dict(slabs_per_range=13), dict(count_warps=8),
+    for kw in (dict(slabs_per_range=0), dict(slabs_per_range=13), dict(count_warps=4),
                dict(walk_unroll=12)):
         with pytest.raises(TacoError) as err:
             ix.set_count_layout(**kw)
