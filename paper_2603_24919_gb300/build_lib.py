@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtaco.so")
+# the checked build: every search kernel bounds-checks its gathers and scatters and records a
+# failed check in the index's device status word (-DTACO_CHECKED); a test aid, not the product
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libtaco_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -57,17 +61,20 @@ def _deps_mtime():
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(verbose: bool = False, jobs: int | None = None, ptxas_verbose: bool = False) -> str:
-    """Build (or reuse) libtaco.so and return its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, ptxas_verbose: bool = False,
+          checked: bool = False) -> str:
+    """Build (or reuse) libtaco.so, or with checked=True libtaco_checked.so (bounds-checked
+    kernels, -DTACO_CHECKED), and return its path."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     newest = _deps_mtime()
     units = _units()
     todo = []
     for obj, src, extra in units:
-        out = os.path.join(BUILD, obj)
+        out = os.path.join(build_dir, obj)
         if not os.path.exists(out) or os.path.getmtime(out) < newest or ptxas_verbose:
-            flags = list(extra)
+            flags = list(extra) + (["-DTACO_CHECKED"] if checked else [])
             if ptxas_verbose:
                 flags += ["-Xptxas", "-v"]
             todo.append([nvcc, *ARCH, *NVCC_FLAGS, *flags, "-c", os.path.join(CSRC, src), "-o", out])
@@ -88,15 +95,15 @@ def build(verbose: bool = False, jobs: int | None = None, ptxas_verbose: bool = 
                 failed.append(cmd[-3])
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    objs = [os.path.join(BUILD, u[0]) for u in units]
-    if todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(map(os.path.getmtime, objs)):
-        tmp = LIB + ".tmp"
+    objs = [os.path.join(build_dir, u[0]) for u in units]
+    if todo or not os.path.exists(lib) or os.path.getmtime(lib) < max(map(os.path.getmtime, objs)):
+        tmp = lib + ".tmp"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
         p = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if p.returncode != 0:
             raise RuntimeError("link failed:\n" + p.stdout)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

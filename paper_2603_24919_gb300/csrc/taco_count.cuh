@@ -84,7 +84,7 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
                                             uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
                                             uint32_t* dummy, uint32_t* lst, uint32_t list_cap, uint32_t* s_app,
                                             uint32_t* s_round, const uint32_t* cpre, const uint32_t* rbase,
-                                            uint64_t pol, int lane) {
+                                            uint64_t pol, int lane, int* status, uint32_t counter_words) {
     static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU list bits a lane");
     const uint32_t lane_le = (2u << lane) - 1u;   // lanes 0..lane
     constexpr uint32_t kRound = 32u * WU;
@@ -106,9 +106,12 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
             const uint32_t pb = cpre[cw + 1u + uint32_t(lane)] - E;                 // >= 1 inside
             const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));     // 0 for pb >= 32
             const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
-            const uint32_t x = min(rbase[r] + E + uint32_t(lane), last_chunk);
+            const uint32_t xr = rbase[r] + E + uint32_t(lane);
+            const bool in = E + uint32_t(lane) < total;
+            TACO_CHECK(status, !in || xr <= last_chunk, kStatusCount);
+            const uint32_t x = min(xr, last_chunk);
             v[u] = ldg_keep_u4(ids4 + x, pol);
-            live |= (E + uint32_t(lane) < total ? 1u : 0u) << u;
+            live |= (in ? 1u : 0u) << u;
         }
         // count: all atomics of the round are independent; an id whose old count is 1 has
         // just reached 2 and is kept (relative to lo) for the list
@@ -120,7 +123,8 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const uint32_t x = w4[h] - lo;
-                const bool ok = ((live >> u) & 1u) && x < rlen;
+                const bool ok = ((live >> u) & 1u) && x < rlen &&
+                                TACO_CHECK(status, (x >> 3) < counter_words, kStatusCount);
                 const uint32_t sh = (x & 7u) << 2;
                 uint32_t* word = ok ? &cnt[x >> 3] : &dummy[lane];
                 const uint32_t old = atomicAdd(word, ok ? 1u << sh : 0u);
@@ -241,7 +245,7 @@ count_lists_kernel(const RerankParams P) {
         if (tid == 0) s_round = 0u;   // read after the staging's barriers
         const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
         if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, lo, rlen, st.x, st.y, cnt, s_dummy, lst, list_cap, &s_app,
-                                      &s_round, cpre, rbase, pol_keep, lane);
+                                      &s_round, cpre, rbase, pol_keep, lane, P.status, uint32_t(P.counter_words));
     };
     __shared__ int64_t s_next;
     for (int64_t q = blockIdx.x; q < P.nq; q = next_query(P.work, &s_next)) {
@@ -254,7 +258,9 @@ count_lists_kernel(const RerankParams P) {
             for (int t = tid; t < total_cells; t += NW * 32) {
                 int i = 0;
                 while (t >= s_pre[i + 1]) ++i;
-                qcell[t] = (uint32_t(i) << 16) | P.cells[(q * Ns + i) * K + (t - s_pre[i])];
+                const int j = t - s_pre[i];
+                qcell[t] = (uint32_t(i) << 16) |
+                           (TACO_CHECK(P.status, j < K, kStatusCount) ? P.cells[(q * Ns + i) * K + j] : 0u);
             }
             __syncthreads();
             prefetch(total_cells, 0, 0);   // bounds of ranges 0 and 1 (a pipeline two deep)
@@ -317,11 +323,14 @@ count_lists_kernel(const RerankParams P) {
                 for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += NW * 32) {
                     const uint32_t e = e0 + uint32_t(lane);
                     const uint32_t id = e < nlist ? lst[e] : 0u;
-                    const uint32_t level = e < nlist ? (cnt[id >> 3] >> ((id & 7u) << 2)) & 15u : 0u;
+                    const bool inr = e < nlist && TACO_CHECK(P.status, id < rlen, kStatusCount);
+                    const uint32_t level = inr ? (cnt[id >> 3] >> ((id & 7u) << 2)) & 15u : 0u;
                     const unsigned grp = __match_any_sync(kFull, level);
                     if (level != 0u && (grp & lane_lt) == 0u) atomicAdd(&s_h[level], uint32_t(__popc(grp)));
                     const uint32_t at = warp_append_slot(level != 0u, &s_outn, lane);
-                    if (level != 0u && at < P.arena_per_unit) out[at] = id | (level << kLevelShift);
+                    if (level != 0u && at < P.arena_per_unit &&
+                        TACO_CHECK(P.status, size_t(u) * P.arena_per_unit + at < P.arena_words, kStatusCount))
+                        out[at] = id | (level << kLevelShift);
                 }
             } else {
                 ge_from_counters<NW>(Ns, words, cnt, ge, tid, lane);

@@ -54,6 +54,22 @@ extern thread_local const char* g_launch_step;
 
 bool is_device_pointer(const void* p);
 
+// Device status word bits (taco_device_status): a bounded wait gave up, or (checked build) an
+// index of a gather or scatter fell outside its buffer in the named pass.
+constexpr int kStatusWait = 1;
+constexpr int kStatusCount = 2;     // counting pass
+constexpr int kStatusSelect = 4;    // select / re-rank pass and its codes fallback
+constexpr int kStatusCluster = 8;   // cluster kernel and the merge of its lists
+
+// Bounds checks of the checked build (compiled with -DTACO_CHECKED): a failed check records
+// its bit in the status word and the access it guards is skipped; nothing traps. Without the
+// flag every check is the constant true and compiles away.
+#ifdef TACO_CHECKED
+#define TACO_CHECK(status, cond, bit) ((cond) ? true : (atomicOr((status), (bit)), false))
+#else
+#define TACO_CHECK(status, cond, bit) true
+#endif
+
 // Raise a kernel's dynamic shared memory limit to at least `bytes` on the current device.
 // The limit only ever grows, process-wide, so launches prepared by different threads (a
 // server's dispatcher, callers of the batch API) never lower it under one another.

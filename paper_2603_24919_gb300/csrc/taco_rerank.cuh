@@ -84,6 +84,9 @@ struct RerankParams {
     uint32_t* arena;        // entries: id relative to the range | SC << 27
     uint32_t* qflag;        // [nq] set when a query needs the fallback (cluster or codes)
     uint32_t* work;         // [2] zeroed query counters of the counting and the select pass
+    int* status;            // the index's device status word (checked build: bounds bits)
+    size_t arena_words;     // entries of the arena (checked build)
+    size_t list_rows;       // rows of kk entries in lists_d / lists_i (checked build)
     int32_t* qlast;         // [nq] last_collision of Alg. 5 of every flagged query
     const uint16_t* codes;  // [Ns][n] cell of every point (codes fallback)
     int fb_mode;            // select_rerank_kernel: 0 two-pass pass 2, 1 codes fallback
@@ -507,7 +510,9 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
             const uint32_t pb = sm.cpre[cw + 1u + uint32_t(lane)] - E;   // >= 1 inside
             const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));   // 0 for pb >= 32
             const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
-            const uint32_t x = min(sm.rbase[r] + E + uint32_t(lane), last_idx);
+            const uint32_t xr = sm.rbase[r] + E + uint32_t(lane);
+            TACO_CHECK(P.status, E + uint32_t(lane) >= total || xr <= last_idx, kStatusCluster);
+            const uint32_t x = min(xr, last_idx);
             const uint32_t v = ldg_keep_u32(P.ids + x, pol_keep);
             idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : kPastEnd;
         }
@@ -794,7 +799,8 @@ count_select_rerank_kernel(const RerankParams P) {
                     const uint32_t x = e < nlist ? lst[e] : 0u;
                     const bool take = e < nlist && int(x >> kLevelShift) == last;
                     const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-                    if (take) buf[at] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
+                    if (take && TACO_CHECK(P.status, at < uint32_t(P.buf_cap), kStatusCluster))
+                        buf[at] = uint32_t(lo) + (x & ((1u << kLevelShift) - 1u));
                 }
             }
             // clear the counters for the next query
@@ -851,7 +857,8 @@ count_select_rerank_kernel(const RerankParams P) {
                 while (m8) {
                     const int j = __ffs(m8) - 1;
                     m8 &= m8 - 1;
-                    buf[at++] = uint32_t(id0 + j);
+                    if (TACO_CHECK(P.status, at < uint32_t(P.buf_cap), kStatusCluster)) buf[at] = uint32_t(id0 + j);
+                    ++at;
                 }
                 bufn += step_total;
                 wpar ^= 1;
@@ -884,7 +891,7 @@ count_select_rerank_kernel(const RerankParams P) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int e = r * 32 + lane;
-                if (e < kk) {
+                if (e < kk && TACO_CHECK(P.status, row + e < P.list_rows * size_t(kk), kStatusCluster)) {
                     P.lists_d[row + e] = top.d[r];
                     P.lists_i[row + e] = top.i[r];
                 }

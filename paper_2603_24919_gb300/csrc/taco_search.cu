@@ -950,6 +950,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         P.ids = ix->d_ids;
         P.split = ix->d_split;
         P.n_ids = ix->n_ids;
+        P.status = ix->d_status;
+        P.list_rows = size_t(L.nq) * ix->cluster * kListsPerCta;
         P.cells = L.cells;
         P.ncells = L.ncells;
         P.params = L.params;
@@ -991,6 +993,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
             P.n_ranges = ix->tp_ranges;
             P.arena_per_unit = uint32_t(kArenaPerSlab) * uint32_t(ix->tp_spc);
+            P.arena_words = size_t(L.nq) * ix->tp_ranges * P.arena_per_unit;
             P.unit_ge = L.unit_ge;
             P.unit_off = L.unit_off;
             P.unit_len = L.unit_len;

@@ -31,7 +31,7 @@ static __device__ __noinline__ void keep_nearest(const float* cd, const uint32_t
                                           float* Md, uint32_t* Mi, uint32_t* hist, uint32_t* s_cur,
                                           uint32_t* s_n, uint32_t* s_eq, uint32_t* s_bin,
                                           uint32_t* s_before, uint32_t* s_tmp, int tid, int lane,
-                                          int warp) {
+                                          int warp, int* status) {
     const int take = min(M, kq);
     if (M > kq) {
         uint32_t prefix = 0, need = uint32_t(kq);
@@ -85,6 +85,7 @@ static __device__ __noinline__ void keep_nearest(const float* cd, const uint32_t
             const uint32_t b = __float_as_uint(cd[i]);
             if (b < prefix) {
                 const uint32_t s = atomicAdd(s_n, 1u);
+                if (!TACO_CHECK(status, s < uint32_t(kkc), kStatusSelect)) continue;
                 Md[s] = cd[i];
                 Mi[s] = ci[i];
             } else if (b == prefix) {
@@ -103,6 +104,7 @@ static __device__ __noinline__ void keep_nearest(const float* cd, const uint32_t
             }
             if (keep) {
                 const uint32_t s = atomicAdd(s_n, 1u);
+                if (!TACO_CHECK(status, s < uint32_t(kkc), kStatusSelect)) continue;
                 Md[s] = cd[i];
                 Mi[s] = ci[i];
             }
@@ -267,6 +269,11 @@ select_rerank_kernel(const RerankParams P) {
         // the distance bits (ties by id) and a bitonic sort.
         if (tid == 0) s_cur = 0u;
         auto flush = [&](int m) {   // block-wide; ends with a barrier
+#ifdef TACO_CHECKED
+            for (int i = tid; i < m; i += kSrThreads)   // every candidate is a point of D
+                if (!TACO_CHECK(P.status, ci[i] < uint32_t(P.n), kStatusSelect)) ci[i] = 0u;
+            __syncthreads();
+#endif
             for (int b0 = warp * CPW * U; b0 < m; b0 += kSrWarps * CPW * U) {
                 float acc[U];
                 uint32_t cid[U];
@@ -284,7 +291,7 @@ select_rerank_kernel(const RerankParams P) {
             }
             __syncthreads();
             keep_nearest(cd, ci, m + cur, kq, kkc, Md, Mi, hist, &s_cur, &s_n, &s_eq, &s_bin, &s_before,
-                         s_tmp2, tid, lane, warp);
+                         s_tmp2, tid, lane, warp, P.status);
         };
         // flush the candidate buffer if a tile of kSrThreads more might not fit (block-wide)
         auto make_room = [&]() {
@@ -306,7 +313,7 @@ select_rerank_kernel(const RerankParams P) {
                     const int64_t id = t0 + tid;
                     const bool take = id < P.n;
                     const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-                    if (take) ci[at] = uint32_t(id);
+                    if (take && TACO_CHECK(P.status, at < uint32_t(kSrBuf), kStatusSelect)) ci[at] = uint32_t(id);
                     __syncthreads();
                 }
             } else {
@@ -354,7 +361,9 @@ select_rerank_kernel(const RerankParams P) {
                                 if (fpre[mid] <= e) lo_c = mid;
                                 else hi_c = mid - 1;
                             }
-                            id = P.ids[fst[lo_c] + (e - fpre[lo_c])];
+                            const uint32_t pos = fst[lo_c] + (e - fpre[lo_c]);
+                            id = TACO_CHECK(P.status, pos < uint64_t(P.n_ids), kStatusSelect) ? P.ids[pos] : 0u;
+                            if (!TACO_CHECK(P.status, id < uint32_t(P.n), kStatusSelect)) id = 0u;
                             const int own = int(fsub[lo_c]);
                             int sc = 0;
                             bool dup = false;
@@ -367,7 +376,7 @@ select_rerank_kernel(const RerankParams P) {
                             take = !dup && sc >= last;
                         }
                         const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-                        if (take) ci[at] = id;
+                        if (take && TACO_CHECK(P.status, at < uint32_t(kSrBuf), kStatusSelect)) ci[at] = id;
                         __syncthreads();
                     }
                 }
@@ -405,12 +414,13 @@ select_rerank_kernel(const RerankParams P) {
                     if (upre[mid] <= t) lo_r = mid;
                     else hi_r = mid - 1;
                 }
-                x = P.arena[uoff[lo_r] + (t - upre[lo_r])];
+                const size_t ap = size_t(uoff[lo_r]) + (t - upre[lo_r]);
+                x = TACO_CHECK(P.status, ap < P.arena_words, kStatusSelect) ? P.arena[ap] : 0u;
                 take = int(x >> kLevelShift) >= last;
                 rlo = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
             }
             const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-            if (take) ci[at] = rlo + (x & ((1u << kLevelShift) - 1u));
+            if (take && TACO_CHECK(P.status, at < uint32_t(kSrBuf), kStatusSelect)) ci[at] = rlo + (x & ((1u << kLevelShift) - 1u));
             __syncthreads();
         }
         }
@@ -419,22 +429,26 @@ select_rerank_kernel(const RerankParams P) {
         // Md / Mi: the query's nearest kq (its k, or its shortlist), sorted by (distance, id),
         // padded with (inf, kNoId) where it has fewer candidates
         if constexpr (RK != kRowF32) {
-            // exact FP32 distances of the shortlist, then rank sort by (distance, id)
-            const int nf4 = P.d_pad / 4;
-            const float4* q4 = reinterpret_cast<const float4*>(qv);
-            for (int e = warp; e < kq; e += kSrWarps) {
-                const uint32_t id = Mi[e];
-                float acc = 0.f;
-                if (id != kNoId) {
-                    const float4* row = reinterpret_cast<const float4*>(P.data + size_t(id) * P.d_pad);
-                    for (int f = lane; f < nf4; f += 32) acc = sq4(__ldg(row + f), q4[f], acc);
-                }
+            // exact FP32 distances of the shortlist (its real entries gathered like the
+            // candidate rows, G lanes a row), then rank sort by (distance, id)
+            const int nreal = min(int(s_cur), kq);
+            const unsigned char* rows32 = reinterpret_cast<const unsigned char*>(P.data);
+            for (int b0 = warp * CPW * U; b0 < nreal; b0 += kSrWarps * CPW * U) {
+                float acc[U];
+                uint32_t cid[U];
+                bool val[U];
+                gather_distances<G, kRowF32>(rows32, size_t(P.d_pad) * 4, P.d_pad / 4, qv, Mi, b0, nreal, acc, cid,
+                                             val, gid, gl, pol_stream);
 #pragma unroll
-                for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-                if (lane == 0) {
-                    Xd[e] = id != kNoId ? acc : __int_as_float(0x7f800000);
-                    Xi[e] = id;
-                }
+                for (int uu = 0; uu < U; ++uu)
+                    if (val[uu] && gl == 0) {
+                        Xd[b0 + uu * CPW + gid] = acc[uu];
+                        Xi[b0 + uu * CPW + gid] = cid[uu];
+                    }
+            }
+            for (int e = nreal + tid; e < kq; e += kSrThreads) {
+                Xd[e] = __int_as_float(0x7f800000);
+                Xi[e] = kNoId;
             }
             __syncthreads();
             for (int e = tid; e < kq; e += kSrThreads) {

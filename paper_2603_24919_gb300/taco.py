@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libtaco.so")
+# TACO_LIB selects another build of the library (the bounds-checked libtaco_checked.so)
+LIB_PATH = os.environ.get("TACO_LIB") or os.path.join(_PKG, "libtaco.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EIO, EAGAIN = -1, -2, -3, -4, -5, -6, -7
