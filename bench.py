@@ -470,11 +470,12 @@ def run_taco(args):
     for form in ("fp32", HEADLINE):
         calib[form] = calibrate(srch, form, SHORTLIST_MULTS.get(form, [1]), targets, recall_fn,
                                 f"rank {rank} {w.name}")["r0.95"]
-    # the other precision forms at the headline's (alpha, beta), over their shortlists
+    # the other precision forms (FP32 centroid distances, like the plain path) at the plain
+    # FP32 form's (alpha, beta), over their shortlists
     for form in ("bf16", "fp8"):
         pts = []
         for mult in SHORTLIST_MULTS[form]:
-            op = {k_: calib[HEADLINE][k_] for k_ in ("alpha", "beta")}
+            op = {k_: calib["fp32"][k_] for k_ in ("alpha", "beta")}
             ms = float(np.median(srch.timed(form, op["alpha"], op["beta"], mult, 3)))
             pts.append(dict(op, shortlist_mult=mult, recall=round(recall_fn(srch.ids(), K), 4),
                             qps=round(nq / (ms * 1e-3), 1)))
