@@ -35,7 +35,7 @@ __device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
     return r;
 }
 
-constexpr int kChunkListCap = 4096;   // ids that reached SC = 2 in a unit (listed once each)
+constexpr int kChunkListCap = 3584;   // ids that reached SC = 2 in a unit (listed once each)
 
 // Level-list capacity of a unit: its arena slot (a longer list would not fit the slot anyway),
 // at most kChunkListCap.
@@ -50,11 +50,11 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
 }
 
 // Shared memory of count_lists_kernel past the counters (bytes): split bounds of the staged
-// cells for three ranges, the level list, the staged chunk runs, the exact-level histogram
+// cells for two ranges, the level list, two staging buffers of chunk runs, the level counts
 // and the staged cells.
 __host__ __device__ __forceinline__ size_t count_lists_extra(int slabs_per_range) {
-    return size_t(3) * kCellBatch * 8 + size_t(count_list_cap(slabs_per_range)) * 4 + size_t(kCellBatch) * 4 +
-           size_t(kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
+    return size_t(2) * kCellBatch * 8 + size_t(count_list_cap(slabs_per_range)) * 4 + size_t(2) * kCellBatch * 4 +
+           size_t(2) * (kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
 }
 
 // The chunk run of id positions [b, e) of one cell list: chunks [b / 4, ceil(e / 4)), none
@@ -157,6 +157,55 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
     }
 }
 
+// One warp stages the chunk runs of the ncell staged cells of one range (their id-position
+// bounds in pr[]): the non-empty runs in cell order, run r covering chunks
+// rbase[r] + [cpre[r], cpre[r + 1]), cpre[nr] = total and cpre[nr + 1 .. nr + 32] =
+// 0xffffffff (the walk's boundary reads). Lane l takes the contiguous cells
+// [l per, (l + 1) per) so that cell order is kept. Returns (total chunks, nr) and the ids the
+// runs hold in the range (*ev). Warp-level; no barrier.
+__device__ __forceinline__ uint2 warp_stage(const uint2* pr, int ncell, uint32_t* rbase, uint32_t* cpre,
+                                            uint32_t* ev, int lane) {
+    const int per = (ncell + 31) >> 5;
+    const int c0 = min(ncell, lane * per), c1 = min(ncell, c0 + per);
+    uint32_t nrl = 0, totl = 0, evl = 0;
+    for (int c = c0; c < c1; ++c) {
+        const uint2 be = pr[c];
+        uint32_t start, len;
+        chunk_run(be.x, be.y, start, len);
+        nrl += len != 0u;
+        totl += len;
+        evl += be.y - be.x;
+    }
+    uint32_t inr = nrl, itot = totl;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t a = __shfl_up_sync(kFull, inr, off), b = __shfl_up_sync(kFull, itot, off);
+        if (lane >= off) {
+            inr += a;
+            itot += b;
+        }
+    }
+    uint32_t r = inr - nrl, t = itot - totl;
+    for (int c = c0; c < c1; ++c) {
+        const uint2 be = pr[c];
+        uint32_t start, len;
+        chunk_run(be.x, be.y, start, len);
+        if (len) {
+            cpre[r] = t;
+            rbase[r] = start - t;
+            ++r;
+            t += len;
+        }
+    }
+    const uint32_t nr = __shfl_sync(kFull, inr, 31), total = __shfl_sync(kFull, itot, 31);
+    __syncwarp();
+    cpre[nr + 1u + uint32_t(lane)] = 0xffffffffu;
+    if (lane == 0) cpre[nr] = total;
+    *ev = __reduce_add_sync(kFull, evl);
+    __syncwarp();
+    return make_uint2(total, nr);
+}
+
 // ge[2..N_s] from the counters themselves (SWAR compare of the eight nibbles of a word against
 // each level), for a unit whose list overflowed. Block-wide over the counter words; adds into
 // ge; no barrier.
@@ -188,24 +237,34 @@ __device__ __forceinline__ void ge_from_counters(int Ns, int words, const uint32
 }
 
 // NW warps per CTA, WU windows of 32 chunks per walk round.
+//
+// Ranges of a query are pipelined when its probed cells fit one staging batch (at most
+// kCellBatch cells): warp NW - 1 (the stager) owns the split bounds (asynchronous copies two
+// ranges ahead) and, while the other warps walk range r, prefetches range r + 1's id runs
+// into L2 and stages its chunk runs into the second staging buffer, then joins the walk.
+// A range then costs three barriers: walk done, level list read, counters cleared.
 template <int NW, int WU>
 __global__ void __launch_bounds__(NW * 32, (NW == 8 || (NW == 16 && WU <= 4)) ? 2 : 1)
 count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kStager = NW - 1;
+    constexpr int kPre = kCellBatch + kRunPad;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
     const uint32_t list_cap = uint32_t(count_list_cap(P.slabs_per_cta));
-    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [3][kCellBatch]
-    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 3 * kCellBatch);      // list_cap
-    uint32_t* rbase = lst + list_cap;                                         // kCellBatch
-    uint32_t* cpre = rbase + kCellBatch;                                      // kCellBatch + kRunPad
-    uint32_t* ge = cpre + kCellBatch + kRunPad;                               // [16]
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+    uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
+    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);      // list_cap
+    uint32_t* rbase = lst + list_cap;                                         // [2][kCellBatch]
+    uint32_t* cpre = rbase + 2 * kCellBatch;                                  // [2][kPre]
+    uint32_t* ge = cpre + 2 * kPre;                                           // [16]
     uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * NW];
-    __shared__ uint32_t s_app, s_outn, s_ev, s_round;
+    __shared__ uint32_t s_app, s_outn, s_round, s_ev;
+    __shared__ uint32_t s_tot2[2], s_nr2[2], s_ev2[2];   // staged batch of each buffer
     __shared__ uint32_t s_dummy[32];   // the atomics of lanes with nothing to count (stay 0)
-    __shared__ uint32_t s_h[16];   // ids of the unit with SC exactly s (s >= 2), from the list
+    __shared__ uint32_t s_h[16];       // ids of the unit with SC exactly s (s >= 2), from the list
+    __shared__ int64_t s_next;
     const int Ns = P.Ns, K = P.K;
     const int sstride = P.n_slabs + 1;
     const uint64_t pol_keep = l2_policy_keep();
@@ -213,41 +272,35 @@ count_lists_kernel(const RerankParams P) {
     const uint32_t last_chunk = uint32_t(P.n_ids / 4) - 1u;
     for (int w = tid; w < P.counter_words; w += NW * 32) cnt[w] = 0u;
     if (tid < 32) s_dummy[tid] = 0u;
-    // the split bounds of every staged cell for range r, into pairs[buf] (asynchronous)
-    auto prefetch = [&](int total_cells, int r, int buf) {
+    // stager: the split bounds of every staged cell for range r into pairs[slot] (asynchronous)
+    auto load_bounds = [&](int total_cells, int r, int slot) {
         const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
-        for (int t = tid; t < total_cells; t += NW * 32) {
+        for (int t = lane; t < total_cells; t += 32) {
             const uint32_t qc = qcell[t];
             const uint32_t* sp = P.split + (size_t(qc >> 16) * K + (qc & 0xffffu)) * sstride;
-            cp_async4(&pairs[buf * kCellBatch + t].x, sp + slo);
-            cp_async4(&pairs[buf * kCellBatch + t].y, sp + shi);
+            cp_async4(&pairs[slot * kCellBatch + t].x, sp + slo);
+            cp_async4(&pairs[slot * kCellBatch + t].y, sp + shi);
         }
         cp_async_commit();
     };
-    // the id chunks of every staged cell's run in range r (bounds in pairs[buf]) into L2, so
-    // that range r's walk, one range later, finds them there (the id lists of a large index
-    // do not stay in L2)
-    auto prefetch_ids = [&](int total_cells, int buf) {
-        for (int t = tid; t < total_cells; t += NW * 32) {
-            const uint2 be = pairs[buf * kCellBatch + t];
-            uint32_t start, len;
-            chunk_run(be.x, be.y, start, len);
-            if (len) prefetch_l2_bulk(ids4 + start, len * 16u);
+    // stager: range r's id runs (bounds in pairs[slot]) into L2, then its chunk runs into
+    // staging buffer `buf`
+    auto stage_range = [&](int total_cells, int slot, int buf, bool prefetch) {
+        const uint2* pr = pairs + slot * kCellBatch;
+        if (prefetch)
+            for (int t = lane; t < total_cells; t += 32) {
+                uint32_t start, len;
+                chunk_run(pr[t].x, pr[t].y, start, len);
+                if (len) prefetch_l2_bulk(ids4 + start, len * 16u);
+            }
+        uint32_t ev;
+        const uint2 st = warp_stage(pr, total_cells, rbase + buf * kCellBatch, cpre + buf * kPre, &ev, lane);
+        if (lane == 0) {
+            s_tot2[buf] = st.x;
+            s_nr2[buf] = st.y;
+            s_ev2[buf] = ev;
         }
     };
-    // stage the chunk runs of id positions [b, e) (one per thread, e = b when none), add the
-    // ids they hold in the range to s_ev, and walk them
-    auto stage_and_walk = [&](uint32_t b, uint32_t e, uint32_t lo, uint32_t rlen) {
-        uint32_t start, len;
-        chunk_run(b, e, start, len);
-        const uint32_t ev = __reduce_add_sync(kFull, e - b);
-        if (lane == 0 && ev) atomicAdd(&s_ev, ev);
-        if (tid == 0) s_round = 0u;   // read after the staging's barriers
-        const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-        if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, lo, rlen, st.x, st.y, cnt, s_dummy, lst, list_cap, &s_app,
-                                      &s_round, cpre, rbase, pol_keep, lane, P.status, uint32_t(P.counter_words));
-    };
-    __shared__ int64_t s_next;
     for (int64_t q = blockIdx.x; q < P.nq; q = next_query(P.work, &s_next)) {
         __syncthreads();   // the previous query is finished with the shared state
         if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
@@ -263,8 +316,17 @@ count_lists_kernel(const RerankParams P) {
                            (TACO_CHECK(P.status, j < K, kStatusCount) ? P.cells[(q * Ns + i) * K + j] : 0u);
             }
             __syncthreads();
-            prefetch(total_cells, 0, 0);   // bounds of ranges 0 and 1 (a pipeline two deep)
-            if (P.n_ranges > 1) prefetch(total_cells, 1, 1);
+            if (warp == kStager) {   // bounds of ranges 0 and 1, then range 0 staged
+                load_bounds(total_cells, 0, 0);
+                if (P.n_ranges > 1) {
+                    load_bounds(total_cells, 1, 1);
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                } else {
+                    cp_async_wait_all();
+                }
+                __syncwarp();
+                stage_range(total_cells, 0, 0, false);
+            }
         }
         for (int r = 0; r < P.n_ranges; ++r) {
             const int64_t u = q * P.n_ranges + r;
@@ -282,22 +344,24 @@ count_lists_kernel(const RerankParams P) {
                 s_app = 0u;
                 s_outn = 0u;
                 s_ev = 0u;
+                s_round = 0u;
             }
+            __syncthreads();   // range r's staging is visible; the counters and list are clear
             if (staged) {
-                cp_async_wait_all();
-                __syncthreads();   // the bounds of ranges r and r + 1 are in pairs[r % 3], pairs[(r + 1) % 3]
-                if (r + 1 < P.n_ranges) prefetch_ids(total_cells, (r + 1) % 3);
-                if (r + 2 < P.n_ranges) prefetch(total_cells, r + 2, (r + 2) % 3);
-                uint32_t b = 0, e = 0;
-                if (tid < total_cells) {
-                    const uint2 be = pairs[(r % 3) * kCellBatch + tid];
-                    b = be.x;
-                    e = be.y;
+                const int buf = r & 1;
+                if (warp == kStager && r + 1 < P.n_ranges) {
+                    cp_async_wait_all();   // the bounds of range r + 1 (pairs[(r + 1) & 1])
+                    __syncwarp();
+                    stage_range(total_cells, (r + 1) & 1, (r + 1) & 1, true);
+                    if (r + 2 < P.n_ranges) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
                 }
-                stage_and_walk(b, e, uint32_t(lo), rlen);
+                const uint32_t tot = s_tot2[buf];
+                if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, s_dummy, lst,
+                                             list_cap, &s_app, &s_round, cpre + buf * kPre, rbase + buf * kCellBatch,
+                                             pol_keep, lane, P.status, uint32_t(P.counter_words));
             } else {
                 for (int cb0 = 0; cb0 < total_cells; cb0 += kCellBatch) {
-                    __syncthreads();   // the staging of the previous batch is walked
+                    if (cb0) __syncthreads();   // the previous batch is walked
                     uint32_t b = 0, e = 0;
                     const int g = cb0 + tid;
                     if (tid < kCellBatch && g < total_cells) {
@@ -308,7 +372,15 @@ count_lists_kernel(const RerankParams P) {
                         b = ldg_keep_u32(sp + slab_lo, pol_keep);
                         e = ldg_keep_u32(sp + slab_hi, pol_keep);
                     }
-                    stage_and_walk(b, e, uint32_t(lo), rlen);
+                    uint32_t start, len;
+                    chunk_run(b, e, start, len);
+                    const uint32_t ev = __reduce_add_sync(kFull, e - b);
+                    if (lane == 0 && ev) atomicAdd(&s_ev, ev);
+                    if (tid == 0) s_round = 0u;   // read after the staging's barriers
+                    const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
+                    if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, s_dummy, lst,
+                                                  list_cap, &s_app, &s_round, cpre, rbase, pol_keep, lane, P.status,
+                                                  uint32_t(P.counter_words));
                 }
             }
             __syncthreads();   // the range's counters and level list are final
@@ -348,7 +420,7 @@ count_lists_kernel(const RerankParams P) {
                 }
                 uint32_t extra = 0;
                 for (int j = 2; j <= Ns; ++j) extra += ge[j];
-                ge[1] = s_ev - extra;
+                ge[1] = (staged ? s_ev2[r & 1] : s_ev) - extra;
                 const uint32_t need = ge[2];
                 const bool fits = !overflow && need <= P.arena_per_unit;
                 P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
