@@ -77,12 +77,13 @@ __device__ __forceinline__ void chunk_run(uint32_t b, uint32_t e, uint32_t& star
 // non-empty, so at most 32 boundaries fall in a window). Rounds are handed to warps by a
 // shared counter (*s_round, zero on entry), so warps that drew short work take more. Lanes
 // past the end load a valid chunk and count nothing: their atomics add 0 to the lane's own
-// dummy word (dummy[lane], which stays 0), so no branch depends on the data. Appends beyond
-// list_cap are dropped (the caller sees the overflow in *s_app). Warp-level; no barrier.
+// spare word cnt[counter_words + lane] (which stays 0), so no branch depends on the data and
+// every atomic is a shared-memory one on cnt. Appends beyond list_cap are dropped (the caller
+// sees the overflow in *s_app). Warp-level; no barrier.
 template <int NW, int WU>
 __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint32_t last_chunk, uint32_t lo,
                                             uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
-                                            uint32_t* dummy, uint32_t* lst, uint32_t list_cap, uint32_t* s_app,
+                                            uint32_t* lst, uint32_t list_cap, uint32_t* s_app,
                                             uint32_t* s_round, const uint32_t* cpre, const uint32_t* rbase,
                                             uint64_t pol, int lane, int* status, uint32_t counter_words) {
     static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU list bits a lane");
@@ -126,8 +127,8 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
                 const bool ok = ((live >> u) & 1u) && x < rlen &&
                                 TACO_CHECK(status, (x >> 3) < counter_words, kStatusCount);
                 const uint32_t sh = (x & 7u) << 2;
-                uint32_t* word = ok ? &cnt[x >> 3] : &dummy[lane];
-                const uint32_t old = atomicAdd(word, ok ? 1u << sh : 0u);
+                const uint32_t w = ok ? (x >> 3) : counter_words + uint32_t(lane);
+                const uint32_t old = atomicAdd(&cnt[w], ok ? 1u << sh : 0u);
                 amask |= (((old >> sh) & 15u) == 1u ? 1u : 0u) << (4 * u + h);
                 rel[u][h] = x;
             }
@@ -262,7 +263,6 @@ count_lists_kernel(const RerankParams P) {
     __shared__ uint32_t s_tmp[2 * NW];
     __shared__ uint32_t s_app, s_outn, s_round, s_ev;
     __shared__ uint32_t s_tot2[2], s_nr2[2], s_ev2[2];   // staged batch of each buffer
-    __shared__ uint32_t s_dummy[32];   // the atomics of lanes with nothing to count (stay 0)
     __shared__ uint32_t s_h[16];       // ids of the unit with SC exactly s (s >= 2), from the list
     __shared__ int64_t s_next;
     const int Ns = P.Ns, K = P.K;
@@ -270,8 +270,8 @@ count_lists_kernel(const RerankParams P) {
     const uint64_t pol_keep = l2_policy_keep();
     const uint4* ids4 = reinterpret_cast<const uint4*>(P.ids);
     const uint32_t last_chunk = uint32_t(P.n_ids / 4) - 1u;
-    for (int w = tid; w < P.counter_words; w += NW * 32) cnt[w] = 0u;
-    if (tid < 32) s_dummy[tid] = 0u;
+    // the counters and, past them, one spare word per lane for the walk's idle atomics
+    for (int w = tid; w < P.counter_words + 32; w += NW * 32) cnt[w] = 0u;
     // stager: the split bounds of every staged cell for range r into pairs[slot] (asynchronous)
     auto load_bounds = [&](int total_cells, int r, int slot) {
         const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
@@ -356,7 +356,7 @@ count_lists_kernel(const RerankParams P) {
                     if (r + 2 < P.n_ranges) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
                 }
                 const uint32_t tot = s_tot2[buf];
-                if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, s_dummy, lst,
+                if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, lst,
                                              list_cap, &s_app, &s_round, cpre + buf * kPre, rbase + buf * kCellBatch,
                                              pol_keep, lane, P.status, uint32_t(P.counter_words));
             } else {
@@ -378,7 +378,7 @@ count_lists_kernel(const RerankParams P) {
                     if (lane == 0 && ev) atomicAdd(&s_ev, ev);
                     if (tid == 0) s_round = 0u;   // read after the staging's barriers
                     const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-                    if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, s_dummy, lst,
+                    if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, lst,
                                                   list_cap, &s_app, &s_round, cpre, rbase, pol_keep, lane, P.status,
                                                   uint32_t(P.counter_words));
                 }

@@ -990,7 +990,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             // the two-pass range layout (tuned): tp_spc slabs of counters per range
             P.slabs_per_cta = ix->tp_spc;
             P.counter_words = ix->tp_spc * kSlabWords;
-            P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
+            P.region_a = size_t(P.counter_words) * 4 + 32 * 4;   // + the walk's 32 spare words
             P.n_ranges = ix->tp_ranges;
             P.arena_per_unit = uint32_t(kArenaPerSlab) * uint32_t(ix->tp_spc);
             P.arena_words = size_t(L.nq) * ix->tp_ranges * P.arena_per_unit;
