@@ -86,9 +86,12 @@ typedef struct {
     int32_t select_rule;   /* TACO_SELECT_*; must be the same for every query of a batch */
     int32_t shortlist_mult;/* TACO_PREC_BF16 / _FP8: exact FP32 re-rank of min(mult*k, TACO_MAX_K) */
     int32_t probe_precision;/* query x centroid distances (Alg. 6 steps 4-5): TACO_PREC_FP32 on CUDA
-                               cores, or TACO_PREC_BF16: BF16 operands on the tcgen05 tensor
-                               cores with FP32 accumulation (needs taco_index_info.has_centroid_tc).
-                               Must be the same for every query of a batch */
+                               cores; TACO_PREC_BF16: BF16 operands on the tcgen05 tensor cores
+                               with FP32 accumulation; TACO_PREC_FP8: E4M3 operands (kind::f8f6f4),
+                               each centroid half scaled by its (subspace, half)'s max |c| / 448
+                               and each half-query by its own max |q| / 448, FP32 accumulation
+                               (both need taco_index_info.has_centroid_tc). Must be the same for
+                               every query of a batch */
     int32_t reserved;      /* must be 0 */
 } taco_query_params;
 
@@ -114,8 +117,8 @@ typedef struct {
     int32_t has_fp8;           /* FP8 rows kept (TACO_ROWS_FP8) */
     int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s, or d when N_s*s < d,
                                   rounded up to 16) */
-    int32_t has_centroid_tc;   /* the tcgen05 centroid block is available (sqrt_k <= 128 and the
-                                  operands of 128 queries fit shared memory) */
+    int32_t has_centroid_tc;   /* the tcgen05 centroid blocks (BF16 and E4M3) are available
+                                  (sqrt_k <= 128 and the operands of 128 queries fit shared memory) */
     int32_t reserved;
     int64_t device_bytes;      /* device memory owned by the index, workspace excluded */
     int64_t n_ids;             /* length of the cell-list array (taco_index_lists) */
@@ -240,9 +243,12 @@ int taco_search_batch_noalloc(const taco_index* index, const float* queries, int
  *   qt     device, [nq][N_s*s] float32 transformed queries B^T (q - o_bar).
  *   out    device, [nq][N_s][2][sqrt_k] float32: out[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2,
  *          half h = 0 the first floor(s/2) dimensions of subspace i, h = 1 the rest.
- *   probe_precision  TACO_PREC_FP32 (CUDA cores, sum of squared differences) or TACO_PREC_BF16
+ *   probe_precision  TACO_PREC_FP32 (CUDA cores, sum of squared differences), TACO_PREC_BF16
  *          (tcgen05 tensor cores: BF16 operands, FP32 accumulation of |q|^2 + |c|^2 - 2 q.c,
- *          clamped at 0; TACO_EINVAL unless has_centroid_tc).
+ *          clamped at 0) or TACO_PREC_FP8 (tcgen05: E4M3 of c / s_c and q / s_q with s_c = max |c|
+ *          / 448 over the (subspace, half)'s centroids and s_q = max |q| / 448 over the half-query,
+ *          each value rounded to nearest even; |q|^2, |c|^2 and q.c of the rounded values times
+ *          the scales, FP32 accumulation). TACO_EINVAL unless has_centroid_tc.
  * Asynchronous on `stream`. A bounded device wait that gives up sets the status word read by
  * taco_device_status.
  */

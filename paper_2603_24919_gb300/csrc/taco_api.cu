@@ -39,6 +39,9 @@ void free_device(taco_index* ix) {
     cudaFree(ix->d_fp8_scale);
     cudaFree(ix->d_cent_tc);
     cudaFree(ix->d_cent_tc_norm);
+    cudaFree(ix->d_cent_tc8);
+    cudaFree(ix->d_cent_tc8_norm);
+    cudaFree(ix->d_cent_tc8_scale);
     cudaFree(ix->d_status);
     cudaFree(ix->d_codes);
     cudaFree(ix->d_obar);
@@ -464,8 +467,9 @@ int taco::check_query_params(const taco_query_params& q, int k_stride) {
         return fail(TACO_EINVAL, "unknown precision %d", q.precision);
     if (q.precision != TACO_PREC_FP32 && q.shortlist_mult < 1)
         return fail(TACO_EINVAL, "shortlist_mult must be >= 1 for BF16 and FP8");
-    if (q.probe_precision != TACO_PREC_FP32 && q.probe_precision != TACO_PREC_BF16)
-        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32 or TACO_PREC_BF16");
+    if (q.probe_precision != TACO_PREC_FP32 && q.probe_precision != TACO_PREC_BF16 &&
+        q.probe_precision != TACO_PREC_FP8)
+        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32, TACO_PREC_BF16 or TACO_PREC_FP8");
     if (q.reserved != 0) return fail(TACO_EINVAL, "reserved field must be 0");
     return TACO_OK;
 }
@@ -577,7 +581,7 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
         return fail(TACO_EINVAL, "BF16 search needs an index with BF16 rows (TACO_ROWS_BF16)");
     if (precision == TACO_PREC_FP8 && !ix->d_data_fp8)
         return fail(TACO_EINVAL, "FP8 search needs an index with FP8 rows (TACO_ROWS_FP8)");
-    const bool ctc = head.probe_precision == TACO_PREC_BF16;
+    const int ctc = head.probe_precision == TACO_PREC_BF16 ? 1 : (head.probe_precision == TACO_PREC_FP8 ? 2 : 0);
     if (ctc && !ix->d_cent_tc) return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
     int cur_dev = 0;
     TACO_CUDA(cudaGetDevice(&cur_dev));
@@ -590,7 +594,7 @@ int search_impl(const taco_index* cix, const float* queries, int64_t nq, const t
     const int64_t chunk = std::min<int64_t>(nq, kQueryChunk);
     const int Ns = ix->Ns, K = ix->K;
     const SearchLayout lay = plan_search(ix, chunk, kk_max, (per_query && !prepared) ? nq : 0, !q_dev, !id_dev,
-                                         !dist_dev, k_stride, ctc);
+                                         !dist_dev, k_stride, ctc != 0);
     const size_t host_need = per_query ? size_t(nq) * sizeof(QueryParamsDev) : 0;
     TRY(ensure_workspace(ix, lay.total, host_need));
     char* wb = static_cast<char*>(ix->ws.base);
@@ -831,12 +835,12 @@ int taco_centroid_distances(const taco_index* ix, const float* qt, int64_t nq, i
     if (nq == 0) return TACO_OK;
     if (!qt || !out || !is_device_pointer(qt) || !is_device_pointer(out))
         return fail(TACO_EINVAL, "qt and out must be device pointers");
-    if (probe_precision != TACO_PREC_FP32 && probe_precision != TACO_PREC_BF16)
-        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32 or TACO_PREC_BF16");
-    if (probe_precision == TACO_PREC_BF16 && !ix->d_cent_tc)
+    if (probe_precision != TACO_PREC_FP32 && probe_precision != TACO_PREC_BF16 && probe_precision != TACO_PREC_FP8)
+        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32, TACO_PREC_BF16 or TACO_PREC_FP8");
+    if (probe_precision != TACO_PREC_FP32 && !ix->d_cent_tc)
         return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
-    TACO_CUDA(launch_centroid_dist(ix, qt, nq, probe_precision == TACO_PREC_BF16, out,
-                                   static_cast<cudaStream_t>(stream)));
+    const int mode = probe_precision == TACO_PREC_BF16 ? 1 : (probe_precision == TACO_PREC_FP8 ? 2 : 0);
+    TACO_CUDA(launch_centroid_dist(ix, qt, nq, mode, out, static_cast<cudaStream_t>(stream)));
     return TACO_OK;
 }
 

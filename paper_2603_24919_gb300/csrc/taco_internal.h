@@ -129,6 +129,9 @@ struct taco_index {
     int fp8_space = 0;                  // 0: B^T (o - o_bar) (N_s s = d), 1: o - o_bar
     uint8_t* d_cent_tc = nullptr;       // [2 N_s] BF16 centroid operands in the tcgen05 layout
     float* d_cent_tc_norm = nullptr;    // [2 N_s][N] squared norms of those BF16 centroids
+    uint8_t* d_cent_tc8 = nullptr;      // [2 N_s] E4M3 centroid operands (c / scale of the pair)
+    float* d_cent_tc8_norm = nullptr;   // [2 N_s][N] squared norms of the values they stand for
+    float* d_cent_tc8_scale = nullptr;  // [2 N_s] scale of each pair (max |c| / 448)
     int* d_status = nullptr;            // device status word: 1 = a bounded device wait gave up
     float* d_obar = nullptr;            // [d]
     float* d_B = nullptr;               // [d][Dp]
@@ -189,10 +192,11 @@ cudaError_t launch_build_lists(const uint16_t* codes, int64_t n, int Ns, int K, 
                                cudaStream_t st);
 
 // Query x centroid distance block (Alg. 6 steps 4-5) as a separate kernel:
-// hd[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2, FP32 on CUDA cores or BF16 on tcgen05.
+// hd[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2, FP32 on CUDA cores or, on tcgen05, BF16 or E4M3
+// (per-pair / per-query scales) operands with FP32 accumulation.
 bool centroid_tc_supported(const taco_index* ix);
 int build_centroid_tc(taco_index* ix);
-cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t nq, bool tensor_cores,
+cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t nq, int mode,
                                  float* hd, cudaStream_t st);
 
 struct SearchLaunch {
@@ -221,8 +225,9 @@ struct SearchLaunch {
     int k_stride;
     taco_debug_out dbg;        // device pointers, already offset to this chunk
     bool skip_profile;         // record no profiling events (launches that may be captured)
-    bool centroid_tc;          // centroid distances from the tcgen05 block into hd
-    float* hd;                 // device [nq][Ns][2][sk] (centroid_tc)
+    int centroid_tc;           // centroid distances from a tcgen05 block into hd: 0 none,
+                               // 1 BF16 operands, 2 E4M3 operands
+    float* hd;                 // device [nq][Ns][2][sk] (centroid_tc != 0)
 };
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
 

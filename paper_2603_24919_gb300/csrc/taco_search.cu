@@ -863,7 +863,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
     const float* hd = nullptr;
     if (L.centroid_tc) {
         if (int rc = prof_begin(pix, 6, st, &pb, &pe)) return rc;
-        TACO_CUDA(launch_centroid_dist(ix, L.qt, L.nq, true, L.hd, st));
+        TACO_CUDA(launch_centroid_dist(ix, L.qt, L.nq, L.centroid_tc, L.hd, st));
         if (int rc = prof_end(pix, 6, st, pb, pe)) return rc;
         hd = L.hd;
     }

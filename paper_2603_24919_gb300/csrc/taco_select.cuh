@@ -20,6 +20,49 @@ constexpr int kSrThreads = 256;
 constexpr int kSrWarps = kSrThreads / 32;
 constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
 constexpr int kSelHist = 2048;   // bins of one radix pass of the selection (8 a thread)
+constexpr int kGatherRows = 4;   // rows a lane group gathers at once in the streaming pass
+
+// Squared distances of U queued candidates per lane group (G lanes a row, rows buf[b0 + u *
+// (32 / G) + group]): every 16-byte chunk load of the U rows is issued before any arithmetic
+// (chunks past G * CH per lane are loaded in further rounds). Lane-group leaders (gl == 0)
+// end with the sums; val / cid tell which are real.
+template <int G, int RK, int U, int CH>
+__device__ __forceinline__ void gather_rows(const unsigned char* base, size_t row_bytes, int nch, const float* qv,
+                                            const uint32_t* buf, int b0, int m, float (&acc)[U],
+                                            uint32_t (&cid)[U], bool (&val)[U], int gid, int gl, uint64_t pol) {
+    constexpr int CPW = 32 / G;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * CPW + gid;
+        val[u] = idx < m;
+        cid[u] = val[u] ? buf[idx] : 0u;
+        acc[u] = 0.f;
+    }
+    for (int f0 = 0; f0 < nch; f0 += G * CH) {
+        uint4 raw[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int ch = 0; ch < CH; ++ch) {
+                const int f = f0 + ch * G + gl;
+                raw[u][ch] = (val[u] && f < nch)
+                                 ? ldg_stream_u4(base + size_t(cid[u]) * row_bytes + size_t(f) * 16, pol)
+                                 : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int ch = 0; ch < CH; ++ch) {
+                const int f = f0 + ch * G + gl;
+                if (f < nch) acc[u] = chunk_dist<RK>(raw[u][ch], qv, f, acc[u]);
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int off = G / 2; off; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
+    }
+}
 
 // The kq nearest of the M (squared distance, id) pairs cd / ci go to Md / Mi[0, min(M, kq)),
 // sorted by (distance, id), and (inf, kNoId) fills Md / Mi up to kkc; *s_cur = min(M, kq).
@@ -157,7 +200,7 @@ inline size_t select_smem_bytes(int kkc, int d_pad, int dp8_or_0, int n_ranges, 
 
 
 template <int G, int RK>
-__global__ void __launch_bounds__(kSrThreads, 4)
+__global__ void __launch_bounds__(kSrThreads, 3)
 select_rerank_kernel(const RerankParams P) {
     constexpr int CPW = 32 / G;
     constexpr int U = 2;
@@ -274,14 +317,14 @@ select_rerank_kernel(const RerankParams P) {
                 if (!TACO_CHECK(P.status, ci[i] < uint32_t(P.n), kStatusSelect)) ci[i] = 0u;
             __syncthreads();
 #endif
-            for (int b0 = warp * CPW * U; b0 < m; b0 += kSrWarps * CPW * U) {
-                float acc[U];
-                uint32_t cid[U];
-                bool val[U];
-                gather_distances<G, RK>(rows, row_bytes, nch, qd, ci, b0, m, acc, cid, val, gid, gl,
-                                        pol_stream);
+            constexpr int UG = kGatherRows;
+            for (int b0 = warp * CPW * UG; b0 < m; b0 += kSrWarps * CPW * UG) {
+                float acc[UG];
+                uint32_t cid[UG];
+                bool val[UG];
+                gather_rows<G, RK, UG, 2>(rows, row_bytes, nch, qd, ci, b0, m, acc, cid, val, gid, gl, pol_stream);
 #pragma unroll
-                for (int uu = 0; uu < U; ++uu)
+                for (int uu = 0; uu < UG; ++uu)
                     if (val[uu] && gl == 0) cd[b0 + uu * CPW + gid] = acc[uu];
             }
             const int cur = int(s_cur);

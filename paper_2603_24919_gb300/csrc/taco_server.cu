@@ -119,7 +119,7 @@ namespace {
 size_t batch_bytes(const taco_server* S, int n, int kk) {
     const int nl = S->p.use_graphs ? size_bucket(n, S->p.max_batch) : n;
     const int kl = S->p.use_graphs ? list_bucket(kk) : kk;
-    return plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out, S->p.probe_precision == TACO_PREC_BF16).total;
+    return plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out, S->p.probe_precision != TACO_PREC_FP32).total;
 }
 
 // Enqueue one batch of nl staged queries on the slot's stream (also used under capture).
@@ -138,7 +138,7 @@ int enqueue_batch(taco_server* S, Slot& sl, const SearchLayout& lay, int nl, int
     L.precision = S->p.precision;
     L.kk_max = kl;
     bind_workspace(L, lay, wb);
-    L.centroid_tc = S->p.probe_precision == TACO_PREC_BF16;
+    L.centroid_tc = S->p.probe_precision == TACO_PREC_BF16 ? 1 : (S->p.probe_precision == TACO_PREC_FP8 ? 2 : 0);
     L.out_ids = reinterpret_cast<int64_t*>(wb + lay.oi);
     L.out_dists = reinterpret_cast<float*>(wb + lay.od);
     L.k_stride = S->k_out;
@@ -161,7 +161,7 @@ int launch_batch(taco_server* S, Slot& sl, int kk_max, int64_t* n_launch, int64_
         sl.h_p[j] = query_params_dev(S->reqs[src].p);
     }
     const SearchLayout lay = plan_search(S->ix, nl, kl, nl, true, true, true, S->k_out,
-                                         S->p.probe_precision == TACO_PREC_BF16);
+                                         S->p.probe_precision != TACO_PREC_FP32);
     const std::pair<int, int> key(nl, kl);
     auto it = sl.graphs.find(key);
     if (it != sl.graphs.end()) {
@@ -358,9 +358,10 @@ int taco_server_create(const taco_index* index, const taco_server_params* params
     if (p.select_rule != TACO_SELECT_LITERAL && p.select_rule != TACO_SELECT_PROSE)
         return fail(TACO_EINVAL, "unknown select_rule");
     if (p.max_wait_us < 0 || p.slot_bytes < 0) return fail(TACO_EINVAL, "bad max_wait_us or slot_bytes");
-    if (p.probe_precision != TACO_PREC_FP32 && p.probe_precision != TACO_PREC_BF16)
-        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32 or TACO_PREC_BF16");
-    if (p.probe_precision == TACO_PREC_BF16 && !index->d_cent_tc)
+    if (p.probe_precision != TACO_PREC_FP32 && p.probe_precision != TACO_PREC_BF16 &&
+        p.probe_precision != TACO_PREC_FP8)
+        return fail(TACO_EINVAL, "probe_precision must be TACO_PREC_FP32, TACO_PREC_BF16 or TACO_PREC_FP8");
+    if (p.probe_precision != TACO_PREC_FP32 && !index->d_cent_tc)
         return fail(TACO_EINVAL, "this index has no tensor-core centroid block");
     int dev = 0;
     TACO_CUDA(cudaGetDevice(&dev));

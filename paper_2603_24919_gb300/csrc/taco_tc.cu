@@ -19,9 +19,11 @@
 // FP32 path computes the same distances on CUDA cores (centroid_dist_simt_kernel and the
 // fused code of the probe kernels).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -51,6 +53,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // and B (bits 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 constexpr uint32_t instr_desc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format code 0 in bits 7-9 and
+// 10-12), FP32 accumulator, both K-major.
+constexpr uint32_t instr_desc_e4m3(int M, int N) {
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -109,6 +116,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// One MMA of kind::f8f6f4 (K = 32 one-byte elements).
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -131,18 +148,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 struct TcGeom {
     int Ns, s, h1, sk, Dp;
     int N;    // sqrt_k rounded up to 16 (>= 16): MMA N
-    int KH;   // longer half rounded up to 16: MMA K
+    int KH;   // longer half rounded up to 16 (BF16) or 32 (E4M3) elements: the operands' K extent
 };
 
+// E4M3 (the largest finite magnitude is 448) of x * inv, rounded to nearest even, saturating.
+__host__ __device__ __forceinline__ uint8_t to_e4m3(float x) {
+    return uint8_t(__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3));
+}
+__device__ __forceinline__ float e4m3_value(uint32_t byte) {
+    const __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_fp8_storage_t(byte), __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+// FP8 = false: BF16 operands, kind::f16. FP8 = true: E4M3 operands with one scale per
+// (query, pair) for A and per pair for B (cscale), kind::f8f6f4; the accumulator holds the
+// dot product of the scaled values, so q.c = acc * scale_q * scale_c.
+template <bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 4)
 centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int G, const uint8_t* __restrict__ cimg,
-                        const float* __restrict__ cnorm, float* __restrict__ hd, int* __restrict__ status) {
+                        const float* __restrict__ cnorm, const float* __restrict__ cscale, float* __restrict__ hd,
+                        int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t abytes = uint32_t(kTcM) * g.KH * 2;       // one pair's A: [128 / 8][KH / 8] core matrices
-    const uint32_t bbytes = uint32_t(g.N) * g.KH * 2;         // one pair's B: [N / 8][KH / 8] core matrices
+    constexpr uint32_t kEs = FP8 ? 1u : 2u;                   // bytes per element
+    const uint32_t abytes = uint32_t(kTcM) * g.KH * kEs;      // one pair's A: [128 / 8][KH bytes / 16] core matrices
+    const uint32_t bbytes = uint32_t(g.N) * g.KH * kEs;       // one pair's B: [N / 8][KH bytes / 16] core matrices
     unsigned char* sA = smem;                                 // G pairs' A
     unsigned char* sB = smem + size_t(G) * abytes;            // G pairs' B
-    float* sQ = reinterpret_cast<float*>(sB + size_t(G) * bbytes);   // [128][W + 1] query dims
+    float* sS = reinterpret_cast<float*>(sB + size_t(G) * bbytes);   // FP8: [G][128] query scales
+    float* sQ = sS + (FP8 ? size_t(G) * kTcM : 0);            // [128][W + 1] query dims
     __shared__ __align__(8) uint64_t bar_load, bar_mma;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -160,8 +193,8 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = instr_desc_bf16(kTcM, g.N);
-    const int kc = g.KH / 8;                                  // core matrices along K
+    const uint32_t idesc = FP8 ? instr_desc_e4m3(kTcM, g.N) : instr_desc_bf16(kTcM, g.N);
+    const int kc = int(g.KH * kEs / 16);                      // core matrices along K
     const uint32_t sbo = uint32_t(kc) * 128u;
     uint32_t phase = 0;
     for (int p0 = int(blockIdx.y) * G; p0 < P; p0 += int(gridDim.y) * G) {   // this CTA's stages
@@ -183,13 +216,31 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int 
             for (int j = lane; j < W; j += 32) sQ[m * (W + 1) + j] = ok ? src[j] : 0.f;
         }
         __syncthreads();
-        // this thread's BF16 half-queries (row tid of each pair's A), zero past a half's length
+        // this thread's half-queries (row tid of each pair's A), zero past a half's length:
+        // BF16, or E4M3 of x / scale with scale = max |x| / 448 of the row's half
         for (int pp = 0; pp < np; ++pp) {
             const int p = p0 + pp, h = p & 1;
             const int len = h ? g.s - g.h1 : g.h1;
             const int base = (p >> 1) * g.s + (h ? g.h1 : 0) - d0;
             const float* x = sQ + tid * (W + 1) + base;
             unsigned char* dst = sA + size_t(pp) * abytes + (tid >> 3) * kc * 128 + (tid & 7) * 16;
+            if constexpr (FP8) {
+                float amax = 0.f;
+                for (int k = 0; k < len; ++k) amax = fmaxf(amax, fabsf(x[k]));
+                const float inv = amax > 0.f ? 448.f / amax : 0.f;
+                sS[pp * kTcM + tid] = amax > 0.f ? amax / 448.f : 0.f;
+                for (int c16 = 0; c16 < kc; ++c16) {
+                    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int k = c16 * 16 + e;
+                        const uint32_t b = k < len ? to_e4m3(x[k] * inv) : 0u;
+                        w[e >> 2] |= b << (8 * (e & 3));
+                    }
+                    *reinterpret_cast<uint4*>(dst + c16 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                continue;
+            }
             for (int c8 = 0; c8 < kc; ++c8) {
                 uint32_t w[4];
 #pragma unroll
@@ -212,9 +263,13 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int 
                 for (int pp = 0; pp < np; ++pp) {
                     const uint32_t aaddr = smem_u32(sA + size_t(pp) * abytes);
                     const uint32_t baddr = smem_u32(sB + size_t(pp) * bbytes);
-                    for (int t = 0; t < g.KH / 16; ++t)
-                        mma_bf16(tmem + uint32_t(pp * g.N), smem_desc(aaddr + t * 256, 128, sbo),
-                                 smem_desc(baddr + t * 256, 128, sbo), idesc, t > 0 ? 1u : 0u);
+                    // one MMA per 32 bytes of K (16 BF16 or 32 E4M3 elements)
+                    for (int t = 0; t < int(g.KH * kEs / 32); ++t) {
+                        const uint64_t da = smem_desc(aaddr + t * 256, 128, sbo);
+                        const uint64_t db = smem_desc(baddr + t * 256, 128, sbo);
+                        if constexpr (FP8) mma_e4m3(tmem + uint32_t(pp * g.N), da, db, idesc, t > 0 ? 1u : 0u);
+                        else mma_bf16(tmem + uint32_t(pp * g.N), da, db, idesc, t > 0 ? 1u : 0u);
+                    }
                 }
                 mma_commit(&bar_mma);
             } else {
@@ -233,18 +288,32 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int 
         tc_fence_after();
         for (int pp = 0; pp < np; ++pp) {
             const int p = p0 + pp, i = p >> 1, h = p & 1;
-            // |q|^2 of this row's BF16 half-query, from the A operand itself
-            float qn = 0.f;
+            // |q|^2 of this row's half-query as the operand holds it, from the A operand itself
+            float qn = 0.f, dscale = 1.f;
             const unsigned char* row = sA + size_t(pp) * abytes + (tid >> 3) * kc * 128 + (tid & 7) * 16;
             for (int c8 = 0; c8 < kc; ++c8) {
                 const uint4 u = *reinterpret_cast<const uint4*>(row + c8 * 128);
-                const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+                if constexpr (FP8) {
+                    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float2 f = __bfloat1622float2(b2[e]);
-                    qn = fmaf(f.x, f.x, qn);
-                    qn = fmaf(f.y, f.y, qn);
+                    for (int e = 0; e < 16; ++e) {
+                        const float f = e4m3_value((w4[e >> 2] >> (8 * (e & 3))) & 0xffu);
+                        qn = fmaf(f, f, qn);
+                    }
+                } else {
+                    const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 f = __bfloat1622float2(b2[e]);
+                        qn = fmaf(f.x, f.x, qn);
+                        qn = fmaf(f.y, f.y, qn);
+                    }
                 }
+            }
+            if constexpr (FP8) {   // back to the unscaled values
+                const float sq = sS[pp * kTcM + tid];
+                qn *= sq * sq;
+                dscale = sq * __ldg(cscale + p);
             }
             const float* cn = cnorm + size_t(p) * g.N;
             const int64_t q = q0 + tid;                       // TMEM lane tid = this query
@@ -254,7 +323,7 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int 
                 float v[16];
                 tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(pp * g.N + c0), v);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) v[e] = fmaxf(qn + __ldg(cn + c0 + e) - 2.f * v[e], 0.f);
+                for (int e = 0; e < 16; ++e) v[e] = fmaxf(qn + __ldg(cn + c0 + e) - 2.f * (v[e] * dscale), 0.f);
                 if (q < nq) {
                     if (vec) {
 #pragma unroll
@@ -304,7 +373,7 @@ __global__ void centroid_dist_simt_kernel(const float* __restrict__ qt, int64_t 
     }
 }
 
-TcGeom geom_of(const taco_index* ix) {
+TcGeom geom_of(const taco_index* ix, bool fp8 = false) {
     TcGeom g;
     g.Ns = ix->Ns;
     g.s = ix->s;
@@ -312,57 +381,78 @@ TcGeom geom_of(const taco_index* ix) {
     g.sk = ix->sk;
     g.Dp = ix->Dp;
     g.N = std::max(16, (ix->sk + 15) / 16 * 16);
-    g.KH = std::max(16, (std::max(ix->h1, ix->s - ix->h1) + 15) / 16 * 16);
+    const int kq = fp8 ? 32 : 16;   // elements of one MMA's K (32 bytes)
+    g.KH = std::max(kq, (std::max(ix->h1, ix->s - ix->h1) + kq - 1) / kq * kq);
     return g;
 }
 
 constexpr size_t kTcStageBytes = size_t(54) * 1024;   // operands of one stage (4 CTAs per SM)
 
-// Bytes of one pair in a stage: its A and B operands and its query dimensions (at most the
-// longer half) in the staging tile.
-size_t tc_pair_bytes(const TcGeom& g) {
-    return size_t(kTcM + g.N) * g.KH * 2 + size_t(kTcM) * std::max(g.h1, g.s - g.h1) * 4;
+// Bytes of one pair in a stage: its A and B operands, its query dimensions (at most the
+// longer half) in the staging tile and, for E4M3, its 128 query scales.
+size_t tc_pair_bytes(const TcGeom& g, bool fp8) {
+    return size_t(kTcM + g.N) * g.KH * (fp8 ? 1 : 2) + size_t(kTcM) * std::max(g.h1, g.s - g.h1) * 4 +
+           (fp8 ? size_t(kTcM) * 4 : 0);
 }
 
 // Pairs per stage (one stage per CTA): four CTAs share an SM, so a stage's accumulators fit
 // 128 of the 512 TMEM columns and its operands a quarter of the shared memory; the many
 // small CTAs spread the block over every SM.
-int tc_pairs_per_stage(const TcGeom& g) {
+int tc_pairs_per_stage(const TcGeom& g, bool fp8) {
     const int by_tmem = std::max(1, 128 / g.N);
-    const int by_smem = int(kTcStageBytes / tc_pair_bytes(g));
+    const int by_smem = int(kTcStageBytes / tc_pair_bytes(g, fp8));
     return std::max(1, std::min({by_tmem, by_smem, 2 * g.Ns}));
 }
 
-size_t tc_smem_bytes(const TcGeom& g, int G) {
-    // the stage's operands and staging tile (row pitch W + 1 <= G * longer half + 1), and at
-    // least a fifth of the SM's shared memory so that at most four CTAs (4 x 128 TMEM columns)
-    // share an SM
-    const size_t ops = size_t(G) * (kTcM + g.N) * g.KH * 2;
+size_t tc_smem_bytes(const TcGeom& g, int G, bool fp8) {
+    // the stage's operands, query scales and staging tile (row pitch W + 1 <= G * longer half
+    // + 1), and at least a fifth of the SM's shared memory so that at most four CTAs (4 x 128
+    // TMEM columns) share an SM
+    const size_t ops = size_t(G) * (kTcM + g.N) * g.KH * (fp8 ? 1 : 2) + (fp8 ? size_t(G) * kTcM * 4 : 0);
     const size_t tile = size_t(kTcM) * (size_t(G) * std::max(g.h1, g.s - g.h1) + 1) * 4;
     return std::max<size_t>(ops + tile, 46 * 1024);
+}
+
+// Value of an E4M3 byte (sign, 4 exponent bits with bias 7, 3 mantissa bits; exponent 0 is
+// subnormal), for the centroid norms built on the host.
+float e4m3_host_value(uint8_t b) {
+    const int e = (b >> 3) & 15, m = b & 7;
+    const float v = e == 0 ? std::ldexp(float(m) / 8.f, -6) : std::ldexp(1.f + float(m) / 8.f, e - 7);
+    return (b & 0x80) ? -v : v;
 }
 
 }  // namespace
 
 bool centroid_tc_supported(const taco_index* ix) {
-    const TcGeom g = geom_of(ix);
-    return g.N <= 128 && tc_pair_bytes(g) + size_t(kTcM) * 4 <= size_t(200) * 1024;
+    const TcGeom g = geom_of(ix), g8 = geom_of(ix, true);
+    return g.N <= 128 && tc_pair_bytes(g, false) + size_t(kTcM) * 4 <= size_t(200) * 1024 &&
+           tc_pair_bytes(g8, true) + size_t(kTcM) * 4 <= size_t(200) * 1024;
 }
 
+// The centroid operands of both blocks, in the no-swizzle K-major core-matrix layout
+// ([2 N_s] pairs of [N / 8][K bytes / 16] core matrices of 8 rows x 16 bytes): BF16 values with
+// their squared norms, and E4M3 values of c / scale_p with scale_p = max |c| / 448 over the
+// pair's centroids, with the squared norms of the values they stand for (scale_p^2 sum e^2).
 int build_centroid_tc(taco_index* ix) {
-    if (!centroid_tc_supported(ix)) return TACO_OK;   // the tensor-core block is not offered
-    const TcGeom g = geom_of(ix);
-    const int P = 2 * g.Ns, kc = g.KH / 8;
-    const size_t bbytes = size_t(g.N) * g.KH * 2;
-    std::vector<uint8_t> img(size_t(P) * bbytes, 0);
-    std::vector<float> norm(size_t(P) * g.N, 0.f);
+    if (!centroid_tc_supported(ix)) return TACO_OK;   // the tensor-core blocks are not offered
+    const TcGeom g = geom_of(ix), g8 = geom_of(ix, true);
+    const int P = 2 * g.Ns, kc = g.KH / 8, kc8 = g8.KH / 16;
+    const size_t bbytes = size_t(g.N) * g.KH * 2, bbytes8 = size_t(g8.N) * g8.KH;
+    std::vector<uint8_t> img(size_t(P) * bbytes, 0), img8(size_t(P) * bbytes8, 0);
+    std::vector<float> norm(size_t(P) * g.N, 0.f), norm8(size_t(P) * g.N, 0.f), scale8(P, 0.f);
     for (int p = 0; p < P; ++p) {
         const int i = p >> 1, h = p & 1;
         const int off = h ? g.h1 : 0, len = h ? g.s - g.h1 : g.h1;
+        auto cval = [&](int n, int k) { return float(ix->centroids[(size_t(i) * g.sk + n) * g.s + off + k]); };
+        float amax = 0.f;
+        for (int n = 0; n < g.sk; ++n)
+            for (int k = 0; k < len; ++k) amax = std::max(amax, std::fabs(cval(n, k)));
+        const float inv = amax > 0.f ? 448.f / amax : 0.f, sc = amax > 0.f ? amax / 448.f : 0.f;
+        scale8[p] = sc;
         for (int n = 0; n < g.sk; ++n) {
-            float acc = 0.f;
+            float acc = 0.f, acc8 = 0.f;
             for (int k = 0; k < len; ++k) {
-                const float x = float(ix->centroids[(size_t(i) * g.sk + n) * g.s + off + k]);
+                const float x = cval(n, k);
                 const __nv_bfloat16 b = __float2bfloat16_rn(x);
                 const float r = __bfloat162float(b);
                 acc += r * r;
@@ -370,36 +460,52 @@ int build_centroid_tc(taco_index* ix) {
                 std::memcpy(&bits, &b, 2);
                 const size_t at = size_t(p) * bbytes + size_t((n / 8) * kc + k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
                 std::memcpy(&img[at], &bits, 2);
+                const uint8_t e8 = to_e4m3(x * inv);
+                const float r8 = e4m3_host_value(e8);
+                acc8 += r8 * r8;
+                img8[size_t(p) * bbytes8 + size_t((n / 8) * kc8 + k / 16) * 128 + (n % 8) * 16 + (k % 16)] = e8;
             }
             norm[size_t(p) * g.N + n] = acc;
+            norm8[size_t(p) * g.N + n] = acc8 * sc * sc;
         }
     }
     cudaError_t e = cudaMalloc(&ix->d_cent_tc, img.size());
     if (e == cudaSuccess) e = cudaMalloc(&ix->d_cent_tc_norm, norm.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ix->d_cent_tc8, img8.size());
+    if (e == cudaSuccess) e = cudaMalloc(&ix->d_cent_tc8_norm, norm8.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ix->d_cent_tc8_scale, scale8.size() * 4);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tensor-core centroids)", __FILE__, __LINE__);
-    ix->device_bytes += int64_t(img.size() + norm.size() * 4);
+    ix->device_bytes += int64_t(img.size() + norm.size() * 4 + img8.size() + norm8.size() * 4 + scale8.size() * 4);
     TACO_CUDA(cudaMemcpy(ix->d_cent_tc, img.data(), img.size(), cudaMemcpyHostToDevice));
     TACO_CUDA(cudaMemcpy(ix->d_cent_tc_norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice));
+    TACO_CUDA(cudaMemcpy(ix->d_cent_tc8, img8.data(), img8.size(), cudaMemcpyHostToDevice));
+    TACO_CUDA(cudaMemcpy(ix->d_cent_tc8_norm, norm8.data(), norm8.size() * 4, cudaMemcpyHostToDevice));
+    TACO_CUDA(cudaMemcpy(ix->d_cent_tc8_scale, scale8.data(), scale8.size() * 4, cudaMemcpyHostToDevice));
     return TACO_OK;
 }
 
-cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t nq, bool tensor_cores, float* hd,
+// mode: 0 FP32 on CUDA cores, 1 BF16 on tcgen05, 2 E4M3 on tcgen05.
+cudaError_t launch_centroid_dist(const taco_index* ix, const float* qt, int64_t nq, int mode, float* hd,
                                  cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
-    const TcGeom g = geom_of(ix);
-    if (tensor_cores) {
-        if (!ix->d_cent_tc) return cudaErrorNotSupported;
-        const int G = tc_pairs_per_stage(g);
-        const size_t smem = tc_smem_bytes(g, G);
-        cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(centroid_dist_tc_kernel), smem);
+    if (mode != 0) {
+        const bool fp8 = mode == 2;
+        if (!ix->d_cent_tc || (fp8 && !ix->d_cent_tc8)) return cudaErrorNotSupported;
+        const TcGeom g = geom_of(ix, fp8);
+        const int G = tc_pairs_per_stage(g, fp8);
+        const size_t smem = tc_smem_bytes(g, G, fp8);
+        auto kern = fp8 ? centroid_dist_tc_kernel<true> : centroid_dist_tc_kernel<false>;
+        cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
         if (e != cudaSuccess) return e;
         // one CTA per (128 queries, stage of pairs): the stages of a query tile run on
         // different SMs
         const dim3 grid(unsigned((nq + kTcM - 1) / kTcM), unsigned((2 * g.Ns + G - 1) / G));
-        centroid_dist_tc_kernel<<<grid, kTcThreads, smem, st>>>(qt, nq, g, G, ix->d_cent_tc,
-                                                                           ix->d_cent_tc_norm, hd, ix->d_status);
+        kern<<<grid, kTcThreads, smem, st>>>(qt, nq, g, G, fp8 ? ix->d_cent_tc8 : ix->d_cent_tc,
+                                             fp8 ? ix->d_cent_tc8_norm : ix->d_cent_tc_norm, ix->d_cent_tc8_scale, hd,
+                                             ix->d_status);
         return cudaGetLastError();
     }
+    const TcGeom g = geom_of(ix);
     const int64_t total = nq * 2 * g.Ns * g.sk;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 32);
     centroid_dist_simt_kernel<<<unsigned(blocks), 256, 0, st>>>(qt, nq, g, ix->d_cent, hd);

@@ -4,7 +4,10 @@ tensor cores, through taco_centroid_distances, and the search with probe_precisi
 FP32 block: equals the FP64 oracle's half distances within 1e-5 relative. BF16 block: BF16
 operands with FP32 accumulation of |q|^2 + |c|^2 - 2 q.c, checked against the FP64
 distances of the BF16-rounded operands within a bound set by FP32 rounding of the three
-terms. Geometries: the 20k x 128 workload (sqrt(K) = 16, halves of 8) and a ragged one
+terms. E4M3 block (kind::f8f6f4): operands c / s_c and q / s_q rounded to E4M3 (s_c = max |c|
+/ 448 over the (subspace, half)'s centroids, s_q = max |q| / 448 over the half-query, both in
+FP32), checked the same way against the FP64 distances of the values the rounded operands
+stand for. Geometries: the 20k x 128 workload (sqrt(K) = 16, halves of 8) and a ragged one
 (sqrt(K) = 7 padded to the MMA's N = 16, 15 subspaces with halves of 2 and 3 padded to K = 16)."""
 import numpy as np
 import pytest
@@ -85,6 +88,53 @@ def test_tensor_core_block_matches_bf16_operands(case):
             assert np.all(err <= 1e-5 * mag + 1e-5), (i, h, float((err / (mag + 1e-9)).max()))
 
 
+def _e4m3(x32):
+    """FP64 values of float32 x rounded to E4M3 (nearest, ties to even)."""
+    t = torch.from_numpy(np.ascontiguousarray(x32, dtype=np.float32))
+    return t.to(torch.float8_e4m3fn).to(torch.float64).numpy()
+
+
+def test_fp8_tensor_core_block_matches_e4m3_operands(case):
+    data, queries, oix, ix = case
+    qt = _qt(ix, queries, oix)
+    hd = ix.centroid_distances(qt, "fp8").cpu().numpy()
+    assert ix.device_status() == 0
+    q32 = qt.cpu().numpy().astype(np.float32)
+    c32 = oix.centroids.astype(np.float32)
+    h1, _ = O.half_dims(oix.sub_dim)
+    s = oix.sub_dim
+    f448 = np.float32(448)
+    for i in range(oix.n_subspaces):
+        for h, (a, b) in enumerate(((0, h1), (h1, s))):
+            qh, ch = q32[:, i * s + a:i * s + b], c32[i][:, a:b]
+            amq = np.abs(qh).max(1)
+            ok = amq > 0
+            sq = np.where(ok, amq / f448, np.float32(0)).astype(np.float32)
+            invq = np.where(ok, f448 / np.where(ok, amq, np.float32(1)), np.float32(0)).astype(np.float32)
+            amc = np.float32(np.abs(ch).max())
+            sc, invc = (amc / f448, f448 / amc) if amc > 0 else (np.float32(0), np.float32(0))
+            qv = _e4m3(qh * invq[:, None]) * sq.astype(np.float64)[:, None]
+            cv = _e4m3(ch * invc) * np.float64(sc)
+            ref = ((qv[:, None, :] - cv[None, :, :]) ** 2).sum(-1)
+            mag = (qv ** 2).sum(-1)[:, None] + (cv ** 2).sum(-1)[None, :]
+            err = np.abs(hd[:, i, h, :] - ref)
+            assert np.all(err <= 1e-5 * mag + 1e-5), (i, h, float((err / (mag + 1e-9)).max()))
+
+
+def test_fp8_probe_recall_close_to_fp32():
+    w, data, queries, oix, ix = _index("tiny20k", 20_000, 200, 8, 16, 16)
+    q = torch.from_numpy(queries).cuda()
+    t_ids, _ = O.brute_force_knn(data, queries, 10)
+    f_ids, _ = ix.search(q, 10, w.budget, w.rerank_target)
+    e_ids, _ = ix.search(q, 10, w.budget, w.rerank_target, precision="bf16", shortlist_mult=2,
+                         probe_precision="fp8")
+    rf = O.recall(f_ids.cpu().numpy(), t_ids, 10)
+    re = O.recall(e_ids.cpu().numpy(), t_ids, 10)
+    assert re >= rf - 0.03, (re, rf)
+    assert ix.device_status() == 0
+    ix.close()
+
+
 def test_full_budget_search_is_the_same_with_either_block():
     """With a budget above n every cell is probed whatever the distances, so the search
     with the tensor-core block returns exactly the FP32 block's result."""
@@ -93,6 +143,8 @@ def test_full_budget_search_is_the_same_with_either_block():
     a_ids, a_d = ix.search(q, 10, 2 * oix.n, 300)
     b_ids, b_d = ix.search(q, 10, 2 * oix.n, 300, probe_precision="bf16")
     assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
+    e_ids, e_d = ix.search(q, 10, 2 * oix.n, 300, probe_precision="fp8")
+    assert torch.equal(a_ids, e_ids) and torch.equal(a_d, e_d)
     assert ix.device_status() == 0
     ix.close()
 
