@@ -59,7 +59,8 @@ SHORTLIST_MULTS = {"bf16": [1, 2, 4], "fp8": [2, 4, 8], "bf16_tc": [1, 2, 4]}   
 HEADLINE = "bf16_tc"
 FORMS = {"fp32": dict(precision="fp32"), "bf16": dict(precision="bf16"),
          "fp8": dict(precision="fp8"),
-         "bf16_tc": dict(precision="bf16", probe_precision="bf16")}   # tcgen05 centroid block
+         "bf16_tc": dict(precision="bf16", probe_precision="bf16"),   # tcgen05 centroid block
+         "fp8_tc": dict(precision="fp8", probe_precision="fp8")}      # E4M3 rows and block
 K = 10
 
 
@@ -86,6 +87,13 @@ def parse():
                          "synth (e.g. tiny20k)")
     ap.add_argument("--serve-seconds", type=float, default=0.3,
                     help="arrival span of each offered load in the serving runs")
+    ap.add_argument("--ncu-case", default=None, metavar="FORM",
+                    help="profiling case (no calibration, tuning or timing): build --workload "
+                         "(deep10m by default; --nq queries), then run --steps searches of FORM "
+                         "(fp32, bf16, bf16_tc, fp8, fp8_tc) at --alpha / --beta, per-query k for "
+                         "deep10m, with --count-layout if given; for runs under a profiler")
+    ap.add_argument("--codes-fallback", action="store_true",
+                    help="with --ncu-case: answer flagged queries by the codes fallback")
     return ap.parse_args()
 
 
@@ -230,7 +238,7 @@ def kernel_source_hash():
     """Hash of the sources that define the counting kernel (its code and constants)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_24919_gb300", "csrc")
-    for name in ("taco_rerank.cuh", "taco_internal.h"):
+    for name in ("taco_count.cuh", "taco_select.cuh", "taco_rerank.cuh", "taco_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -1213,8 +1221,49 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ncu_case(args):
+    """A fixed search case for a profiler: the workload's index (row copies only for the
+    form's rows), --steps searches at (--alpha, --beta) with the form's shortlist 1 (FP8: 2)."""
+    import torch
+    from paper_2603_24919_gb300 import TacoIndex, build_lib
+    from synth import budget_from_alpha, make_workload, target_from_beta
+
+    torch.cuda.set_device(0)
+    build_lib.build()
+    form = FORMS[args.ncu_case]
+    name = args.workload
+    w, data, queries = make_workload(name, nq=args.nq)
+    n, nq = data.shape[0], queries.shape[0]
+    prec = form["precision"]
+    ix = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=20, seed=1,
+                         keep_bf16=prec == "bf16", keep_fp8=prec == "fp8")
+    del data
+    if args.count_layout:
+        spc, warps, unroll = (int(x) for x in args.count_layout.split(","))
+        ix.set_count_layout(slabs_per_range=spc, count_warps=warps, walk_unroll=unroll)
+    if args.codes_fallback:
+        ix.set_codes_fallback(True)
+    q = torch.from_numpy(queries).cuda()
+    a = args.alpha or REFERENCE_OP.get(name, (w.alpha, w.beta))[0]
+    b = args.beta or REFERENCE_OP.get(name, (w.alpha, w.beta))[1]
+    mult = 2 if prec == "fp8" else 1
+    ks = np.random.default_rng(4242).choice(KS_BATCHED, size=nq) if name == WORKLOAD else np.full(nq, K)
+    prep = ix.prepare([dict(k=int(k), budget=budget_from_alpha(a, n), rerank_target=target_from_beta(b, n),
+                            shortlist_mult=mult, **form) for k in ks])
+    for _ in range(args.steps):
+        ix.search_prepared(q, prep, k_stride=int(ks.max()))
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "workload": name, "n": n, "nq": nq, "alpha": a, "beta": b,
+                      "steps": args.steps, "device_status": ix.device_status()}), flush=True)
+    prep.close()
+    ix.close()
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != WORKLOAD:

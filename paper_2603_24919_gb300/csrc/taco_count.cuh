@@ -1,13 +1,15 @@
 // Collision counting of the two-pass search (Alg. 6 step 7, Def. 6), pass 1.
 //
 // Persistent CTAs take queries and, for each, its id ranges in turn (a (query, range) pair is
-// a unit). A unit's collisions are counted in 4-bit shared-memory counters; the ids whose
-// count reaches 2 are listed once, and after the walk every listed id is tagged with its
-// final count (its SC-score) and written to the unit's fixed arena slot, together with the
-// unit's level counts ge[j] = #{ids of the range with SC >= j}. Pass 2 (select_rerank_kernel)
-// sums the level counts of a query's ranges, applies Alg. 5 and re-ranks the listed ids with
-// SC >= last_collision. Queries whose threshold falls below 2, or whose lists do not fit,
-// are flagged for a fallback.
+// a unit). A unit's collisions are counted in 4-bit shared-memory counters. Each time an
+// id's count reaches a level j >= 2 (the shared-memory atomic's old value is j - 1), the id
+// (relative to the range) is appended to the unit's arena slot tagged with j: the entries
+// tagged j are then exactly the range's ids with SC >= j, one each, so the unit's level
+// counts ge[j] = #{ids with SC >= j} are the counts of the tags, ge[1] = events - entries,
+// and the candidates at an Alg. 5 threshold t >= 2 are the entries tagged t. Pass 2
+// (select_rerank_kernel) sums the level counts of a query's ranges, applies Alg. 5 and
+// re-ranks those entries. Queries whose threshold falls below 2, or whose entries do not fit
+// a slot, are flagged for a fallback.
 //
 // The cell lists are stored 16-byte aligned and padded to a multiple of 4 ids (with kIdPad),
 // so the run of a probed cell that falls in the unit's id range is covered by whole 4-id
@@ -35,26 +37,18 @@ __device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
     return r;
 }
 
-constexpr int kChunkListCap = 3584;   // ids that reached SC = 2 in a unit (listed once each)
-
-// Level-list capacity of a unit: its arena slot (a longer list would not fit the slot anyway),
-// at most kChunkListCap.
-__host__ __device__ __forceinline__ int count_list_cap(int slabs_per_range) {
-    return min(kChunkListCap, int(kArenaPerSlab) * slabs_per_range);
-}
-
 // Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address into L2;
 // no completion to wait for.
 __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Shared memory of count_lists_kernel past the counters (bytes): split bounds of the staged
-// cells for two ranges, the level list, two staging buffers of chunk runs, the level counts
-// and the staged cells.
-__host__ __device__ __forceinline__ size_t count_lists_extra(int slabs_per_range) {
-    return size_t(2) * kCellBatch * 8 + size_t(count_list_cap(slabs_per_range)) * 4 + size_t(2) * kCellBatch * 4 +
-           size_t(2) * (kCellBatch + kRunPad) * 4 + 16 * 4 + size_t(kCellBatch) * 4;
+// Shared memory of count_lists_kernel past the counters and their 32 spare words (bytes):
+// split bounds of the staged cells for two ranges, two staging buffers of chunk runs, the
+// level counts and the staged cells.
+__host__ __device__ __forceinline__ size_t count_lists_extra() {
+    return size_t(2) * kCellBatch * 8 + size_t(2) * kCellBatch * 4 + size_t(2) * (kCellBatch + kRunPad) * 4 +
+           16 * 4 + size_t(kCellBatch) * 4;
 }
 
 // The chunk run of id positions [b, e) of one cell list: chunks [b / 4, ceil(e / 4)), none
@@ -67,26 +61,27 @@ __device__ __forceinline__ void chunk_run(uint32_t b, uint32_t e, uint32_t& star
 
 // Walk one staged batch of chunk runs (total chunks in nr non-empty runs; run r covers
 // chunks rbase[r] + [cpre[r], cpre[r + 1]) of the id array). Every id of a chunk that lies in
-// the unit's range [lo, lo + rlen) adds 1 to its 4-bit counter; the shared-memory atomic's
-// old value tells when an id reaches 2, and such an id is appended (relative to lo) to the
-// level list, once. The concatenated chunks are walked in rounds of WU windows of 32 chunks
-// (one chunk per lane and window, WU loads of 16 bytes in flight per lane), round g by warp
-// g mod NW. Lane u finds the run of the first chunk of window u (binary search); in a window,
-// lane j reads the j-th next run boundary, the boundaries inside the window form a bit mask,
-// and a lane's run is the window's first run plus the mask bits at or below it (runs are
-// non-empty, so at most 32 boundaries fall in a window). Rounds are handed to warps by a
-// shared counter (*s_round, zero on entry), so warps that drew short work take more. Lanes
-// past the end load a valid chunk and count nothing: their atomics add 0 to the lane's own
-// spare word cnt[counter_words + lane] (which stays 0), so no branch depends on the data and
-// every atomic is a shared-memory one on cnt. Appends beyond list_cap are dropped (the caller
-// sees the overflow in *s_app). Warp-level; no barrier.
+// the unit's range [lo, lo + rlen) adds 1 to its 4-bit counter; when the atomic's old value
+// v is >= 1 the id has just reached level v + 1 >= 2 and is appended to the unit's arena slot
+// `out` as (id - lo) | (v + 1) << kLevelShift, and ge[v + 1] counts it. The concatenated
+// chunks are walked in rounds of WU windows of 32 chunks (one chunk per lane and window, WU
+// loads of 16 bytes in flight per lane). Lane u finds the run of the first chunk of window u
+// (binary search); in a window, lane j reads the j-th next run boundary, the boundaries
+// inside the window form a bit mask, and a lane's run is the window's first run plus the
+// mask bits at or below it (runs are non-empty, so at most 32 boundaries fall in a window).
+// Rounds are handed to warps by a shared counter (*s_round, zero on entry), so warps that
+// drew short work take more. Lanes past the end load a valid chunk and count nothing: their
+// atomics add 0 to the lane's own spare word cnt[counter_words + lane] (which stays 0), so
+// no branch depends on the data and every atomic is a shared-memory one on cnt. Entries
+// beyond `cap` are counted in *s_app but not stored (the caller sees the overflow).
+// Warp-level; no barrier.
 template <int NW, int WU>
 __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint32_t last_chunk, uint32_t lo,
                                             uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
-                                            uint32_t* lst, uint32_t list_cap, uint32_t* s_app,
+                                            uint32_t* out, uint32_t cap, uint32_t* ge, uint32_t* s_app,
                                             uint32_t* s_round, const uint32_t* cpre, const uint32_t* rbase,
                                             uint64_t pol, int lane, int* status, uint32_t counter_words) {
-    static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU list bits a lane");
+    static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU append bits a lane");
     const uint32_t lane_le = (2u << lane) - 1u;   // lanes 0..lane
     constexpr uint32_t kRound = 32u * WU;
     const uint32_t nrounds = (total + kRound - 1) / kRound;
@@ -114,8 +109,8 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
             v[u] = ldg_keep_u4(ids4 + x, pol);
             live |= (in ? 1u : 0u) << u;
         }
-        // count: all atomics of the round are independent; an id whose old count is 1 has
-        // just reached 2 and is kept (relative to lo) for the list
+        // count: all atomics of the round are independent; an id whose old count v is >= 1
+        // has just reached level v + 1 and is kept, tagged, for the arena
         uint32_t amask = 0;
         uint32_t rel[WU][4];
 #pragma unroll
@@ -129,11 +124,12 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
                 const uint32_t sh = (x & 7u) << 2;
                 const uint32_t w = ok ? (x >> 3) : counter_words + uint32_t(lane);
                 const uint32_t old = atomicAdd(&cnt[w], ok ? 1u << sh : 0u);
-                amask |= (((old >> sh) & 15u) == 1u ? 1u : 0u) << (4 * u + h);
-                rel[u][h] = x;
+                const uint32_t v = (old >> sh) & 15u;
+                amask |= (v != 0u ? 1u : 0u) << (4 * u + h);
+                rel[u][h] = x | ((v + 1u) << kLevelShift);
             }
         }
-        // append the ids that reached 2: one reservation per warp and round
+        // append the ids that reached a level >= 2: one reservation per warp and round
         if (__any_sync(kFull, amask != 0u)) {
             const uint32_t na = __popc(amask);
             uint32_t incl = na;
@@ -151,7 +147,8 @@ __device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint
 #pragma unroll
                 for (int h = 0; h < 4; ++h)
                     if ((amask >> (4 * u + h)) & 1u) {
-                        if (pos < list_cap) lst[pos] = rel[u][h];
+                        if (pos < cap) out[pos] = rel[u][h];
+                        atomicAdd(&ge[rel[u][h] >> kLevelShift], 1u);
                         ++pos;
                     }
         }
@@ -207,43 +204,14 @@ __device__ __forceinline__ uint2 warp_stage(const uint2* pr, int ncell, uint32_t
     return make_uint2(total, nr);
 }
 
-// ge[2..N_s] from the counters themselves (SWAR compare of the eight nibbles of a word against
-// each level), for a unit whose list overflowed. Block-wide over the counter words; adds into
-// ge; no barrier.
-template <int NW>
-__device__ __forceinline__ void ge_from_counters(int Ns, int words, const uint32_t* cnt, uint32_t* ge, int tid,
-                                                 int lane) {
-    uint32_t gel[TACO_MAX_SUBSPACES];
-#pragma unroll
-    for (int j = 0; j < TACO_MAX_SUBSPACES; ++j) gel[j] = 0;
-    for (int w = tid; w < words; w += NW * 32) {
-        const uint32_t x = cnt[w];
-        if (x == 0u) continue;
-        const uint32_t ev = x & 0x0f0f0f0fu, od = (x >> 4) & 0x0f0f0f0fu;
-#pragma unroll
-        for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
-            if (j <= Ns) {
-                const uint32_t add = (0x80u - uint32_t(j)) * 0x01010101u;
-                gel[j - 1] += __popc((ev + add) & 0x80808080u) + __popc((od + add) & 0x80808080u);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 2; j <= TACO_MAX_SUBSPACES; ++j) {
-        if (j <= Ns) {
-            const uint32_t v = __reduce_add_sync(kFull, gel[j - 1]);
-            if (lane == 0 && v) atomicAdd(&ge[j], v);
-        }
-    }
-}
-
 // NW warps per CTA, WU windows of 32 chunks per walk round.
 //
 // Ranges of a query are pipelined when its probed cells fit one staging batch (at most
 // kCellBatch cells): warp NW - 1 (the stager) owns the split bounds (asynchronous copies two
 // ranges ahead) and, while the other warps walk range r, prefetches range r + 1's id runs
-// into L2 and stages its chunk runs into the second staging buffer, then joins the walk.
-// A range then costs three barriers: walk done, level list read, counters cleared.
+// into L2 and stages its chunk runs into the second staging buffer, then joins the walk. A
+// range costs two barriers: after its walk (counters final), and after the unit's outputs
+// and the clearing of the counters.
 template <int NW, int WU>
 __global__ void __launch_bounds__(NW * 32, (NW == 8 || (NW == 16 && WU <= 4)) ? 2 : 1)
 count_lists_kernel(const RerankParams P) {
@@ -251,27 +219,31 @@ count_lists_kernel(const RerankParams P) {
     constexpr int kStager = NW - 1;
     constexpr int kPre = kCellBatch + kRunPad;
     extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t list_cap = uint32_t(count_list_cap(P.slabs_per_cta));
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);                        // counters + 32 spare
     uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
-    uint32_t* lst = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);      // list_cap
-    uint32_t* rbase = lst + list_cap;                                         // [2][kCellBatch]
+    uint32_t* rbase = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);    // [2][kCellBatch]
     uint32_t* cpre = rbase + 2 * kCellBatch;                                  // [2][kPre]
     uint32_t* ge = cpre + 2 * kPre;                                           // [16]
     uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * NW];
-    __shared__ uint32_t s_app, s_outn, s_round, s_ev;
+    __shared__ uint32_t s_app, s_round, s_ev;
     __shared__ uint32_t s_tot2[2], s_nr2[2], s_ev2[2];   // staged batch of each buffer
-    __shared__ uint32_t s_h[16];       // ids of the unit with SC exactly s (s >= 2), from the list
     __shared__ int64_t s_next;
     const int Ns = P.Ns, K = P.K;
     const int sstride = P.n_slabs + 1;
     const uint64_t pol_keep = l2_policy_keep();
     const uint4* ids4 = reinterpret_cast<const uint4*>(P.ids);
     const uint32_t last_chunk = uint32_t(P.n_ids / 4) - 1u;
+    const uint32_t cap = P.arena_per_unit;
     // the counters and, past them, one spare word per lane for the walk's idle atomics
     for (int w = tid; w < P.counter_words + 32; w += NW * 32) cnt[w] = 0u;
+    if (tid < 16) ge[tid] = 0u;
+    if (tid == 0) {
+        s_app = 0u;
+        s_round = 0u;
+        s_ev = 0u;
+    }
     // stager: the split bounds of every staged cell for range r into pairs[slot] (asynchronous)
     auto load_bounds = [&](int total_cells, int r, int slot) {
         const int slo = r * P.slabs_per_cta, shi = min(slo + P.slabs_per_cta, P.n_slabs);
@@ -327,6 +299,7 @@ count_lists_kernel(const RerankParams P) {
                 __syncwarp();
                 stage_range(total_cells, 0, 0, false);
             }
+            __syncthreads();   // range 0's staging is visible
         }
         for (int r = 0; r < P.n_ranges; ++r) {
             const int64_t u = q * P.n_ranges + r;
@@ -336,17 +309,9 @@ count_lists_kernel(const RerankParams P) {
             const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
             const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
             const uint32_t rlen = uint32_t(hi - lo);
-            if (tid < 16) {
-                ge[tid] = 0u;
-                s_h[tid] = 0u;
-            }
-            if (tid == 0) {
-                s_app = 0u;
-                s_outn = 0u;
-                s_ev = 0u;
-                s_round = 0u;
-            }
-            __syncthreads();   // range r's staging is visible; the counters and list are clear
+            uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
+            TACO_CHECK(P.status, (size_t(u) + 1) * P.arena_per_unit <= P.arena_words, kStatusCount);
+            // (the counters are clear, ge / s_app / s_round zero, range r staged)
             if (staged) {
                 const int buf = r & 1;
                 if (warp == kStager && r + 1 < P.n_ranges) {
@@ -356,9 +321,9 @@ count_lists_kernel(const RerankParams P) {
                     if (r + 2 < P.n_ranges) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
                 }
                 const uint32_t tot = s_tot2[buf];
-                if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, lst,
-                                             list_cap, &s_app, &s_round, cpre + buf * kPre, rbase + buf * kCellBatch,
-                                             pol_keep, lane, P.status, uint32_t(P.counter_words));
+                if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, out, cap, ge,
+                                             &s_app, &s_round, cpre + buf * kPre, rbase + buf * kCellBatch, pol_keep,
+                                             lane, P.status, uint32_t(P.counter_words));
             } else {
                 for (int cb0 = 0; cb0 < total_cells; cb0 += kCellBatch) {
                     if (cb0) __syncthreads();   // the previous batch is walked
@@ -378,59 +343,41 @@ count_lists_kernel(const RerankParams P) {
                     if (lane == 0 && ev) atomicAdd(&s_ev, ev);
                     if (tid == 0) s_round = 0u;   // read after the staging's barriers
                     const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-                    if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, lst,
-                                                  list_cap, &s_app, &s_round, cpre, rbase, pol_keep, lane, P.status,
+                    if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, out, cap, ge,
+                                                  &s_app, &s_round, cpre, rbase, pol_keep, lane, P.status,
                                                   uint32_t(P.counter_words));
                 }
             }
-            __syncthreads();   // the range's counters and level list are final
-            if (P.dbg_sc) debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
-            // every listed id has SC >= 2 and is listed once: its final count is its level;
-            // the histogram of levels and the tagged entries in the unit's arena slot
-            const uint32_t nlist = s_app;
-            const bool overflow = nlist > list_cap;
-            if (!overflow) {
-                uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
-                const uint32_t lane_lt = (1u << lane) - 1u;
-                for (uint32_t e0 = uint32_t(warp) * 32u; e0 < nlist; e0 += NW * 32) {
-                    const uint32_t e = e0 + uint32_t(lane);
-                    const uint32_t id = e < nlist ? lst[e] : 0u;
-                    const bool inr = e < nlist && TACO_CHECK(P.status, id < rlen, kStatusCount);
-                    const uint32_t level = inr ? (cnt[id >> 3] >> ((id & 7u) << 2)) & 15u : 0u;
-                    const unsigned grp = __match_any_sync(kFull, level);
-                    if (level != 0u && (grp & lane_lt) == 0u) atomicAdd(&s_h[level], uint32_t(__popc(grp)));
-                    const uint32_t at = warp_append_slot(level != 0u, &s_outn, lane);
-                    if (level != 0u && at < P.arena_per_unit &&
-                        TACO_CHECK(P.status, size_t(u) * P.arena_per_unit + at < P.arena_words, kStatusCount))
-                        out[at] = id | (level << kLevelShift);
-                }
-            } else {
-                ge_from_counters<NW>(Ns, words, cnt, ge, tid, lane);
+            __syncthreads();   // the range's counters, entries and level counts are final
+            if (P.dbg_sc) {
+                debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
+                __syncthreads();   // every counter is read before any is cleared
             }
-            __syncthreads();   // s_h / ge and the counters are read; the counters may be cleared
-            if (tid == 0) {
-                // ge[j] = ids with SC >= j; ids with SC = s contribute s - 1 events beyond
-                // their first, so ge[1] = events - sum_{j >= 2} ge[j]
-                if (!overflow) {
-                    uint32_t acc = 0;
-                    for (int j = Ns; j >= 2; --j) {
-                        acc += s_h[j];
-                        ge[j] = acc;
-                    }
+            if (warp == 0) {
+                // the unit's outputs: ge[1] = events - entries (an id with SC = s has s - 1
+                // entries), ge[j >= 2] = entries tagged j; then the shared state for the next range
+                const uint32_t apps = s_app;
+                const bool fits = apps <= cap;
+                if (lane == 0) {
+                    ge[1] = (staged ? s_ev2[r & 1] : s_ev) - apps;
+                    P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
+                    P.unit_len[u] = fits ? apps : 0u;
+                    if (!fits) P.qflag[q] = 1u;   // entries lost: the query takes the fallback
                 }
-                uint32_t extra = 0;
-                for (int j = 2; j <= Ns; ++j) extra += ge[j];
-                ge[1] = (staged ? s_ev2[r & 1] : s_ev) - extra;
-                const uint32_t need = ge[2];
-                const bool fits = !overflow && need <= P.arena_per_unit;
-                P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
-                P.unit_len[u] = fits ? need : 0u;
-                if (!fits) P.qflag[q] = 1u;   // list lost: the query takes the fallback
+                __syncwarp();
+                if (lane < 16) {
+                    P.unit_ge[u * 16 + lane] = ge[lane];
+                    ge[lane] = 0u;
+                }
+                if (lane == 0) {
+                    s_app = 0u;
+                    s_round = 0u;
+                    s_ev = 0u;
+                }
             }
             uint4* c4 = reinterpret_cast<uint4*>(cnt);
             for (int w = tid; w < (words + 3) / 4; w += NW * 32) c4[w] = make_uint4(0, 0, 0, 0);
-            __syncthreads();
-            if (tid < 16) P.unit_ge[u * 16 + tid] = ge[tid];
+            __syncthreads();   // counters clear, outputs written; range r + 1 is staged
         }
     }
 }

@@ -903,11 +903,12 @@ count_select_rerank_kernel(const RerankParams P) {
 
 // ---------------------------------------------------------------------------------------
 // Two-pass form. Pass 1 (count_lists_kernel, taco_count.cuh) counts the collisions of each
-// (query, id range) unit and writes the unit's level counts and its ids with SC >= 2 (id
-// relative to the range | SC << 27) to the unit's arena slot. Pass 2 (select_rerank_kernel,
-// below): one CTA per query sums the level counts of its ranges, applies Alg. 5, keeps the
-// arena entries with SC >= last_collision and re-ranks them. Queries whose threshold falls
-// below 2, or whose lists did not fit, are flagged for a fallback.
+// (query, id range) unit and writes the unit's level counts and, for every level j >= 2 an id
+// reaches, an entry (id relative to the range | j << 27) to the unit's arena slot. Pass 2
+// (select_rerank_kernel, taco_select.cuh): one CTA per query sums the level counts of its
+// ranges, applies Alg. 5, keeps the arena entries tagged last_collision and re-ranks them.
+// Queries whose threshold falls below 2, or whose entries did not fit, are flagged for a
+// fallback.
 // ---------------------------------------------------------------------------------------
 
 template <int G, int R, bool BF16>

@@ -1004,7 +1004,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq + 2) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit; 256, 512 or 1024 threads per CTA and
             // 2, 4 or 8 chunk windows per walk round (tuned)
-            const size_t smem1 = P.region_a + count_lists_extra(P.slabs_per_cta);
+            const size_t smem1 = P.region_a + count_lists_extra();
             struct CountVariant {
                 int nw, wu;
                 void (*fn)(const RerankParams);

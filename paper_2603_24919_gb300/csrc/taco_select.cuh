@@ -425,9 +425,10 @@ select_rerank_kernel(const RerankParams P) {
                 }
             }
         } else {
-        // candidates: the list entries with SC >= last of all the query's ranges as one
-        // sequence (range r's entries are upre[r] .. upre[r + 1] - 1), in tiles of kSrThreads;
-        // the buffer is re-ranked and emptied before a tile that would not fit
+        // candidates: the entries tagged last of all the query's ranges (range r's entries are
+        // upre[r] .. upre[r + 1] - 1 of one sequence; an id with SC = s >= 2 has one entry per
+        // level 2 .. s, so exactly the ids with SC >= last have one tagged last), in tiles of
+        // kSrThreads; the buffer is re-ranked and emptied before a tile that would not fit
         uint32_t* upre = fbm;            // [nr + 1] (the fallback's bitmaps are not in use)
         uint32_t* uoff = upre + nr + 1;  // [nr]
         uint32_t nent = 0;
@@ -459,7 +460,7 @@ select_rerank_kernel(const RerankParams P) {
                 }
                 const size_t ap = size_t(uoff[lo_r]) + (t - upre[lo_r]);
                 x = TACO_CHECK(P.status, ap < P.arena_words, kStatusSelect) ? P.arena[ap] : 0u;
-                take = int(x >> kLevelShift) >= last;
+                take = int(x >> kLevelShift) == last;   // one entry per id with SC >= last
                 rlo = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
             }
             const uint32_t at = warp_append_slot(take, &s_bufn, lane);

@@ -136,8 +136,9 @@ def test_chunk_walk_counts_exactly_the_probed_ids_of_the_range(wu, n_cells, n):
     """The chunk runs [b / 4, ceil(e / 4)) of the probed cells' runs in a range, walked with
     the window/mask lookup and filtered by the range test, visit every id of those runs once
     and nothing else (padding and the cells' ids of other ranges fail the test). Counting
-    with an append when a count reaches 2 lists every id with SC >= 2 exactly once, and
-    ge[1] = events - sum_{j >= 2} ge[j]."""
+    with an entry tagged j each time a count reaches a level j >= 2 gives, for every j, one
+    entry tagged j per id with SC >= j (so the candidates at threshold t are the entries
+    tagged t), and ge[1] = events - entries."""
     rng = np.random.default_rng(n_cells * 1000 + wu)
     ns = 4
     lists = [padded_lists(rng.integers(0, n_cells, n), n_cells) for _ in range(ns)]
@@ -169,7 +170,7 @@ def test_chunk_walk_counts_exactly_the_probed_ids_of_the_range(wu, n_cells, n):
             continue
         cpre, rbase, total, nr = stage(lengths, starts)
         chunks = walk_indices(cpre, rbase, total, nr, wu, last_idx=last_chunk)
-        got, cnt, listed = [], {}, []
+        got, cnt, entries = [], {}, []
         for e_, x in sorted(chunks.items()):
             for h in range(4):
                 v = int(allids[4 * x + h])
@@ -178,9 +179,11 @@ def test_chunk_walk_counts_exactly_the_probed_ids_of_the_range(wu, n_cells, n):
                     got.append(v)
                     old = cnt.get(rel, 0)
                     cnt[rel] = old + 1
-                    if old == 1:
-                        listed.append(rel)
+                    if old >= 1:
+                        entries.append((rel, old + 1))
         assert sorted(got) == sorted(want)
-        assert sorted(listed) == sorted(r for r, c in cnt.items() if c >= 2)
-        ge = {j: sum(1 for c in cnt.values() if c >= j) for j in range(1, ns + 1)}
-        assert ge[1] == len(got) - sum(ge[j] for j in range(2, ns + 1))
+        for j in range(2, ns + 1):
+            tagged = sorted(r for r, t in entries if t == j)
+            assert tagged == sorted(r for r, c in cnt.items() if c >= j), j
+        ge1 = sum(1 for c in cnt.values() if c >= 1)
+        assert ge1 == len(got) - len(entries)
