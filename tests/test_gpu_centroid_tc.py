@@ -8,7 +8,9 @@ terms. E4M3 block (kind::f8f6f4): operands c / s_c and q / s_q rounded to E4M3 (
 / 448 over the (subspace, half)'s centroids, s_q = max |q| / 448 over the half-query, both in
 FP32), checked the same way against the FP64 distances of the values the rounded operands
 stand for. Geometries: the 20k x 128 workload (sqrt(K) = 16, halves of 8) and a ragged one
-(sqrt(K) = 7 padded to the MMA's N = 16, 15 subspaces with halves of 2 and 3 padded to K = 16)."""
+(sqrt(K) = 7 padded to the MMA's N = 16, 15 subspaces with halves of 2 and 3 padded to K = 16)
+and a wide one in the 1M x 960 workload's shape (10 subspaces of 96 dims: halves of 48, three
+BF16 K-steps of 16 and an E4M3 K-step of 32 padded to 64; sqrt(K) = 64)."""
 import numpy as np
 import pytest
 
@@ -39,10 +41,12 @@ def _index(name, n, nq, ns, s, sk, d=None):
     return w, data, queries, oix, ix
 
 
-@pytest.fixture(scope="module", params=["tiny", "ragged"])
+@pytest.fixture(scope="module", params=["tiny", "ragged", "wide"])
 def case(request):
     if request.param == "tiny":
         w, data, queries, oix, ix = _index("tiny20k", 20_000, 300, 8, 16, 16)
+    elif request.param == "wide":
+        w, data, queries, oix, ix = _index("gist1m", 6_000, 130, 10, 96, 64)
     else:
         w, data, queries, oix, ix = _index("tiny20k", 5_003, 200, 15, 5, 7, d=100)
     yield data, queries, oix, ix
