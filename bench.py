@@ -1094,9 +1094,14 @@ WORKLOAD_FORMS = {
     "deep5m256": {"fp32": dict(precision="fp32"), "bf16_tc": dict(precision="bf16", probe_precision="bf16")},
 }
 WORKLOAD_MULTS = {"fp32": [1], "fp32_tc": [1], "bf16": [1, 2], "bf16_tc": [1, 2], "fp8": [2, 4], "fp8_tc": [2, 4]}
-# below the paper's alpha range too: on these stand-ins recall@10 saturates early
-WORKLOAD_GRID = [(a, b) for a in (0.0002, 0.0005, 0.001, 0.002, 0.005, 0.01, 0.02, 0.05)
-                 for b in (0.0001, 0.0002, 0.0005, 0.001, 0.002, 0.005)]
+# (alpha, beta) grids: the 5M x 256 grid reaches below the paper's alpha range (recall@10
+# saturates early on that stand-in); the 1M x 960 grid spans the paper's ranges
+WORKLOAD_GRIDS = {
+    "deep5m256": [(a, b) for a in (0.0002, 0.0005, 0.001, 0.002, 0.005, 0.01, 0.02, 0.05)
+                  for b in (0.0001, 0.0002, 0.0005, 0.001, 0.002, 0.005)],
+    "gist1m": [(a, b) for a in (0.002, 0.005, 0.01, 0.02, 0.05, 0.1)
+               for b in (0.0005, 0.001, 0.002, 0.005, 0.01, 0.02)],
+}
 
 
 def run_workload(args):
@@ -1135,6 +1140,7 @@ def run_workload(args):
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(4242)
     forms = dict(WORKLOAD_FORMS[name])
+    grid = WORKLOAD_GRIDS[name]
     ks = np.full(nq, K)
 
     def per(form, a, b):
@@ -1159,7 +1165,7 @@ def run_workload(args):
         best = None
         for mult in mults:
             f = dict(form, shortlist_mult=mult)
-            for a, b in WORKLOAD_GRID:
+            for a, b in grid:
                 r10, _, qps, _ = timed(f, a, b, reps)
                 if r10 >= target and (best is None or qps > best["qps"]):
                     best = {"alpha": a, "beta": b, "recall_at_10": r10, "qps": qps, "mult": mult}
@@ -1170,13 +1176,13 @@ def run_workload(args):
         best = fastest(forms[fname], RECALL_TARGET, WORKLOAD_MULTS[fname])
         met = best is not None
         if best is None:
-            best = {"alpha": WORKLOAD_GRID[-1][0], "beta": WORKLOAD_GRID[-1][1], "mult": WORKLOAD_MULTS[fname][-1]}
+            best = {"alpha": grid[-1][0], "beta": grid[-1][1], "mult": WORKLOAD_MULTS[fname][-1]}
         a, b = best["alpha"], best["beta"]
         form = forms[fname] = dict(forms[fname], shortlist_mult=best["mult"])
         tune = ix.autotune(q_dev, K, budget_from_alpha(a, n), target_from_beta(b, n), reps=2, **form)
         r10, mre, qps, per_ms = timed(form, a, b, max(args.steps // 5, 5))
         out[fname] = {"alpha": a, "beta": b, "shortlist_mult": best["mult"], "met": met,
-                      "on_grid_edge": (a, b) in (WORKLOAD_GRID[0], WORKLOAD_GRID[-1]),
+                      "on_grid_edge": (a, b) in (grid[0], grid[-1]),
                       "qps": round(float(qps), 1), "recall_at_10": round(r10, 4), "mre": round(mre, 6),
                       "batch_ms_p50": round(float(np.percentile(per_ms, 50)), 3),
                       "batch_ms_p99": round(float(np.percentile(per_ms, 99)), 3),
@@ -1188,14 +1194,15 @@ def run_workload(args):
         serving = {"server": "max_batch 2048, 4 slots, max_wait 100 us, CUDA graphs", "targets": {}, "loads": {}}
         for fname in ("bf16_tc", "fp32"):
             # each recall target mapped to the form's own fastest grid point meeting it on k = 10
+            # (alpha, beta, shortlist multiple) per target; the FP32 rows have no shortlist
             targets = {}
             for tgt_r in (0.9, 0.99):
-                best = fastest(forms[fname], tgt_r, [forms[fname]["shortlist_mult"]], reps=1)
-                targets[tgt_r] = (best["alpha"], best["beta"]) if best else WORKLOAD_GRID[-1]
+                best = fastest(forms[fname], tgt_r, WORKLOAD_MULTS[fname], reps=1)
+                targets[tgt_r] = (best["alpha"], best["beta"], best["mult"]) if best else grid[-1] + (1,)
             serving["targets"][fname] = {str(t): v for t, v in targets.items()}
             form = forms[fname]
-            mult = form.get("shortlist_mult", 1) if form["precision"] != "fp32" else 1
-            with TacoServer(ix, max_batch=2048, slots=4, queue_capacity=16384, max_list=min(mult * kmax, 512),
+            max_list = kmax if form["precision"] == "fp32" else min(max(v[2] for v in targets.values()) * kmax, 512)
+            with TacoServer(ix, max_batch=2048, slots=4, queue_capacity=16384, max_list=max_list,
                             precision=form["precision"], max_wait_us=100,
                             probe_precision=form.get("probe_precision", "fp32")) as srv:
                 loads = []
@@ -1206,7 +1213,7 @@ def run_workload(args):
                     tq = rng.choice([0.9, 0.99], size=n_req)
                     pq = [query_params(int(k), budget_from_alpha(targets[t][0], n),
                                        target_from_beta(targets[t][1], n), form["precision"],
-                                       "literal", mult, form.get("probe_precision", "fp32"))
+                                       "literal", targets[t][2], form.get("probe_precision", "fp32"))
                           for k, t in zip(kq, tq)]
                     arrival = np.cumsum(rng.exponential(1e9 / rate, size=n_req)).astype(np.int64)
                     ids, _, lat = srv.replay(queries[rows], pq, arrival, kmax)

@@ -228,7 +228,7 @@ int taco_search_batch_params(const taco_index* index, const float* queries, cons
  * C the index's cluster_size and kk the k of the query or its BF16 shortlist
  * min(shortlist_mult*k, TACO_MAX_K). FP8 rows (TACO_PREC_FP8) and the tensor-core centroid
  * block (probe_precision TACO_PREC_BF16) are refused with TACO_EINVAL.
- * TACO_ECAPACITY also for an index whose cluster_size is 0 (n above 16 x 12 x 2^15 points).
+ * TACO_ECAPACITY also for an index whose cluster_size is 0 (n above 16 x 11 x 2^15 points for d up to 1,300).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture. All calls share the array, so calls
  * that overlap on the GPU (other streams, other threads) race: serialise them.
@@ -262,7 +262,7 @@ int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq
  *   recomputed from the cell codes of every probed point and bitmaps of the probed cells
  *   (keeps a device copy of the codes, 2 bytes per point and subspace); value 0 uses the
  *   cluster kernel (all of a query's counters in one thread-block cluster's shared memory).
- *   An index whose n is too large for any cluster (more than 16 x 12 slabs of 2^15 points)
+ *   An index whose n is too large for any cluster (more than 16 x 11 slabs of 2^15 points)
  *   always uses the codes fallback (TACO_ECAPACITY for value 0).
  *   TACO_OPT_SLABS_PER_RANGE: counter slabs per id range of the two-pass counting, 1 .. 12
  *   (a value above the index's n_slabs acts as n_slabs; n_ranges follows; TACO_ECAPACITY at

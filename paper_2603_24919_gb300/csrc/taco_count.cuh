@@ -273,8 +273,16 @@ count_lists_kernel(const RerankParams P) {
             s_ev2[buf] = ev;
         }
     };
-    for (int64_t q = blockIdx.x; q < P.nq; q = next_query(P.work, &s_next)) {
-        __syncthreads();   // the previous query is finished with the shared state
+    // work item: ranges [rb, re) of query q (all its ranges unless a small batch splits them
+    // into range_parts runs so that more CTAs work on it)
+    const int parts = P.range_parts;
+    const int per_part = (P.n_ranges + parts - 1) / parts;
+    const int64_t items = P.nq * parts;
+    for (int64_t it = blockIdx.x; it < items; it = next_query(P.work, &s_next)) {
+        const int64_t q = it / parts;
+        const int rb = int(it % parts) * per_part;
+        const int re = min(P.n_ranges, rb + per_part);
+        __syncthreads();   // the previous item is finished with the shared state
         if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
         __syncthreads();
         const int total_cells = s_pre[Ns];
@@ -288,10 +296,10 @@ count_lists_kernel(const RerankParams P) {
                            (TACO_CHECK(P.status, j < K, kStatusCount) ? P.cells[(q * Ns + i) * K + j] : 0u);
             }
             __syncthreads();
-            if (warp == kStager) {   // bounds of ranges 0 and 1, then range 0 staged
-                load_bounds(total_cells, 0, 0);
-                if (P.n_ranges > 1) {
-                    load_bounds(total_cells, 1, 1);
+            if (warp == kStager && rb < re) {   // bounds of ranges rb and rb + 1, then rb staged
+                load_bounds(total_cells, rb, 0);
+                if (re - rb > 1) {
+                    load_bounds(total_cells, rb + 1, 1);
                     asm volatile("cp.async.wait_group 1;" ::: "memory");
                 } else {
                     cp_async_wait_all();
@@ -299,9 +307,9 @@ count_lists_kernel(const RerankParams P) {
                 __syncwarp();
                 stage_range(total_cells, 0, 0, false);
             }
-            __syncthreads();   // range 0's staging is visible
+            __syncthreads();   // range rb's staging is visible
         }
-        for (int r = 0; r < P.n_ranges; ++r) {
+        for (int r = rb; r < re; ++r) {
             const int64_t u = q * P.n_ranges + r;
             const int slab_lo = r * P.slabs_per_cta;
             const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
@@ -313,12 +321,12 @@ count_lists_kernel(const RerankParams P) {
             TACO_CHECK(P.status, (size_t(u) + 1) * P.arena_per_unit <= P.arena_words, kStatusCount);
             // (the counters are clear, ge / s_app / s_round zero, range r staged)
             if (staged) {
-                const int buf = r & 1;
-                if (warp == kStager && r + 1 < P.n_ranges) {
-                    cp_async_wait_all();   // the bounds of range r + 1 (pairs[(r + 1) & 1])
+                const int buf = (r - rb) & 1;   // staging buffer and bounds slot of range r
+                if (warp == kStager && r + 1 < re) {
+                    cp_async_wait_all();   // the bounds of range r + 1 (slot buf ^ 1)
                     __syncwarp();
-                    stage_range(total_cells, (r + 1) & 1, (r + 1) & 1, true);
-                    if (r + 2 < P.n_ranges) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
+                    stage_range(total_cells, buf ^ 1, buf ^ 1, true);
+                    if (r + 2 < re) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
                 }
                 const uint32_t tot = s_tot2[buf];
                 if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, out, cap, ge,
@@ -359,7 +367,7 @@ count_lists_kernel(const RerankParams P) {
                 const uint32_t apps = s_app;
                 const bool fits = apps <= cap;
                 if (lane == 0) {
-                    ge[1] = (staged ? s_ev2[r & 1] : s_ev) - apps;
+                    ge[1] = (staged ? s_ev2[(r - rb) & 1] : s_ev) - apps;
                     P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
                     P.unit_len[u] = fits ? apps : 0u;
                     if (!fits) P.qflag[q] = 1u;   // entries lost: the query takes the fallback

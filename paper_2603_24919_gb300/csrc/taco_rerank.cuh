@@ -77,11 +77,12 @@ struct RerankParams {
     int k_stride;
     // two-pass form: per (query, id range) unit
     int n_ranges;           // id ranges per query
+    int range_parts;        // count_lists_kernel: work items per query, each a run of its ranges
     uint32_t arena_per_unit;  // arena entries reserved per unit
     uint32_t* unit_ge;      // [nq][n_ranges][16] ids with SC >= j, j = 1..N_s
     uint32_t* unit_off;     // [nq][n_ranges] start of the unit's entries in the arena
-    uint32_t* unit_len;     // [nq][n_ranges] entries (ids with SC >= 2)
-    uint32_t* arena;        // entries: id relative to the range | SC << 27
+    uint32_t* unit_len;     // [nq][n_ranges] entries (one per level >= 2 an id reaches)
+    uint32_t* arena;        // entries: id relative to the range | level << 27
     uint32_t* qflag;        // [nq] set when a query needs the fallback (cluster or codes)
     uint32_t* work;         // [2] zeroed query counters of the counting and the select pass
     int* status;            // the index's device status word (checked build: bounds bits)

@@ -754,9 +754,21 @@ static int next_pow2(int x) {
     return p;
 }
 
+// The most counter slabs one CTA of the cluster kernel holds: its dynamic shared memory is
+// the counters plus the query row, the candidate buffer, the level list and the staging
+// arrays (the launch's byte count), and its static shared memory stays under 4 KB; all of it
+// must fit the 227 KB a CTA can opt into.
+static int cluster_spc_max(const taco_index* ix) {
+    const size_t beyond = size_t(ix->d_pad) * 4 + size_t(kBufCap) * 4 + size_t(kListCap) * 4 +
+                          size_t(kCellBatch) * 4 + size_t(kCellBatch + kRunPad) * 4 + 32 * 4 + 4096;
+    const size_t limit = size_t(227) * 1024;
+    return limit > beyond ? int((limit - beyond) / kSlabBytes) : 0;
+}
+
 // Cluster size and slabs per CTA for an index (called once at index creation).
 int configure_search(taco_index* ix) {
     ix->n_slabs = int((ix->n + kSlabIds - 1) / kSlabIds);
+    const int spc_max = std::min(12, cluster_spc_max(ix));
     // Aim for 4 slabs (64 KB of counters) per CTA so two clusters' CTAs share an SM.
     int spc = 4;
     int cluster = (ix->n_slabs + spc - 1) / spc;
@@ -765,11 +777,11 @@ int configure_search(taco_index* ix) {
         spc = (ix->n_slabs + 7) / 8;
         cluster = (ix->n_slabs + spc - 1) / spc;
     }
-    if (spc > 12) {
+    if (spc > spc_max) {
         spc = (ix->n_slabs + 15) / 16;
         cluster = (ix->n_slabs + spc - 1) / spc;
     }
-    if (spc > 12 || cluster > 16) {
+    if (spc > spc_max || cluster > 16) {
         // no cluster holds a query's counters: the two-pass form counts in ranges of 12
         // slabs and flagged queries take the codes fallback
         ix->cluster = 0;
@@ -1031,8 +1043,16 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                 c1_blocks[c1] = per_sm * sms;
                 c1_smem[c1] = smem1;
             }
+            // a batch smaller than the resident CTAs splits each query's ranges into runs
+            // (work items) so that more CTAs count it
+            P.range_parts = 1;
+            if (L.nq < c1_blocks[c1]) {
+                const int want = int(std::min<int64_t>(P.n_ranges, (c1_blocks[c1] + L.nq - 1) / L.nq));
+                const int per_part = (P.n_ranges + want - 1) / want;
+                P.range_parts = (P.n_ranges + per_part - 1) / per_part;
+            }
             if (int rc = prof_begin(pix, 2, st, &pb, &pe)) return rc;
-            k1<<<unsigned(std::min<int64_t>(L.nq, c1_blocks[c1])), nw1 * 32, smem1, st>>>(P);
+            k1<<<unsigned(std::min<int64_t>(L.nq * P.range_parts, c1_blocks[c1])), nw1 * 32, smem1, st>>>(P);
             TACO_CUDA(cudaGetLastError());
             if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
             // pass 2: Alg. 5, candidates, re-rank, results

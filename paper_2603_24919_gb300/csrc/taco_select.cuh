@@ -21,6 +21,7 @@ constexpr int kSrWarps = kSrThreads / 32;
 constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
 constexpr int kSelHist = 2048;   // bins of one radix pass of the selection (8 a thread)
 constexpr int kGatherRows = 4;   // rows a lane group gathers at once in the streaming pass
+constexpr int kEntryLoads = 4;   // arena entries a thread loads per tile of the candidate pass
 
 // Squared distances of U queued candidates per lane group (G lanes a row, rows buf[b0 + u *
 // (32 / G) + group]): every 16-byte chunk load of the U rows is issued before any arithmetic
@@ -337,8 +338,8 @@ select_rerank_kernel(const RerankParams P) {
                          s_tmp2, tid, lane, warp, P.status);
         };
         // flush the candidate buffer if a tile of kSrThreads more might not fit (block-wide)
-        auto make_room = [&]() {
-            if (s_bufn + kSrThreads > uint32_t(kSrBuf)) {
+        auto make_room = [&](uint32_t tile = uint32_t(kSrThreads)) {
+            if (s_bufn + tile > uint32_t(kSrBuf)) {
                 __syncthreads();
                 flush(int(s_bufn));
                 if (tid == 0) s_bufn = 0u;
@@ -428,7 +429,8 @@ select_rerank_kernel(const RerankParams P) {
         // candidates: the entries tagged last of all the query's ranges (range r's entries are
         // upre[r] .. upre[r + 1] - 1 of one sequence; an id with SC = s >= 2 has one entry per
         // level 2 .. s, so exactly the ids with SC >= last have one tagged last), in tiles of
-        // kSrThreads; the buffer is re-ranked and emptied before a tile that would not fit
+        // kEntryLoads x kSrThreads entries (each thread's loads of a tile are independent); the
+        // buffer is re-ranked and emptied before a tile that would not fit
         uint32_t* upre = fbm;            // [nr + 1] (the fallback's bitmaps are not in use)
         uint32_t* uoff = upre + nr + 1;  // [nr]
         uint32_t nent = 0;
@@ -446,25 +448,34 @@ select_rerank_kernel(const RerankParams P) {
         }
         if (tid == 0) upre[nr] = nent;
         __syncthreads();
-        for (uint32_t t0 = 0; t0 < nent; t0 += kSrThreads) {
-            make_room();
-            const uint32_t t = t0 + tid;
-            uint32_t x = 0, rlo = 0;
-            bool take = false;
-            if (t < nent) {
-                int lo_r = 0, hi_r = nr - 1;   // the range holding entry t
-                while (lo_r < hi_r) {
-                    const int mid = (lo_r + hi_r + 1) >> 1;
-                    if (upre[mid] <= t) lo_r = mid;
-                    else hi_r = mid - 1;
+        constexpr uint32_t kTile = uint32_t(kEntryLoads) * kSrThreads;
+        for (uint32_t t0 = 0; t0 < nent; t0 += kTile) {
+            make_room(kTile);
+            uint32_t x[kEntryLoads], rlo[kEntryLoads];
+#pragma unroll
+            for (int j = 0; j < kEntryLoads; ++j) {
+                const uint32_t t = t0 + uint32_t(j * kSrThreads + tid);
+                x[j] = 0u;
+                rlo[j] = 0xffffffffu;   // no entry
+                if (t < nent) {
+                    int lo_r = 0, hi_r = nr - 1;   // the range holding entry t
+                    while (lo_r < hi_r) {
+                        const int mid = (lo_r + hi_r + 1) >> 1;
+                        if (upre[mid] <= t) lo_r = mid;
+                        else hi_r = mid - 1;
+                    }
+                    const size_t ap = size_t(uoff[lo_r]) + (t - upre[lo_r]);
+                    x[j] = TACO_CHECK(P.status, ap < P.arena_words, kStatusSelect) ? P.arena[ap] : 0u;
+                    rlo[j] = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
                 }
-                const size_t ap = size_t(uoff[lo_r]) + (t - upre[lo_r]);
-                x = TACO_CHECK(P.status, ap < P.arena_words, kStatusSelect) ? P.arena[ap] : 0u;
-                take = int(x >> kLevelShift) == last;   // one entry per id with SC >= last
-                rlo = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
             }
-            const uint32_t at = warp_append_slot(take, &s_bufn, lane);
-            if (take && TACO_CHECK(P.status, at < uint32_t(kSrBuf), kStatusSelect)) ci[at] = rlo + (x & ((1u << kLevelShift) - 1u));
+#pragma unroll
+            for (int j = 0; j < kEntryLoads; ++j) {
+                const bool take = rlo[j] != 0xffffffffu && int(x[j] >> kLevelShift) == last;
+                const uint32_t at = warp_append_slot(take, &s_bufn, lane);
+                if (take && TACO_CHECK(P.status, at < uint32_t(kSrBuf), kStatusSelect))
+                    ci[at] = rlo[j] + (x[j] & ((1u << kLevelShift) - 1u));
+            }
             __syncthreads();
         }
         }

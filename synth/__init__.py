@@ -10,7 +10,7 @@ from .workloads import (  # noqa: F401
     make_workload,
     gmm_isotropic,
     gmm_integer,
-    powerlaw_rotated,
+    powerlaw_mixture,
     gmm_unit_normalised,
     gmm_anisotropic,
     budget_from_alpha,

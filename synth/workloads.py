@@ -64,19 +64,24 @@ def _haar_orthogonal(d, rng):
     return qm * np.sign(np.diag(r))[None, :]
 
 
-def powerlaw_rotated(n, d, exponent, seed, nq, q_seed, chunk=1 << 16):
-    """GIST-like anisotropic Gaussian: eigenvalues i^-exponent under a Haar rotation."""
+def powerlaw_mixture(n, d, n_comp, spread, exponent, seed, nq, q_seed, chunk=1 << 16):
+    """GIST-like: a mixture of n_comp components whose centres and within-component noise
+    are both anisotropic Gaussians with eigenvalues i^-exponent under one Haar rotation
+    (the noise scaled by spread), components chosen uniformly."""
     rng = _rng(seed)
     rot = _haar_orthogonal(d, rng)
     scale = np.sqrt(np.arange(1, d + 1, dtype=np.float64) ** (-exponent))
+    centres = (rng.standard_normal((n_comp, d)) * scale[None, :]) @ rot.T
     data = np.empty((n, d), dtype=np.float32)
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        z = rng.standard_normal((b - a, d)) * scale[None, :]
-        data[a:b] = z @ rot.T
+        comp = rng.integers(0, n_comp, size=b - a)
+        z = spread * rng.standard_normal((b - a, d)) * scale[None, :]
+        data[a:b] = centres[comp] + z @ rot.T
     qr = _rng(q_seed)
-    z = qr.standard_normal((nq, d)) * scale[None, :]
-    return data, (z @ rot.T).astype(np.float32)
+    comp = qr.integers(0, n_comp, size=nq)
+    z = spread * qr.standard_normal((nq, d)) * scale[None, :]
+    return data, (centres[comp] + z @ rot.T).astype(np.float32)
 
 
 def gmm_unit_normalised(n, d, n_comp, spread, seed, nq, q_seed, chunk=1 << 18):
@@ -157,7 +162,7 @@ class Workload:
 _GENERATORS = {
     "gmm_isotropic": gmm_isotropic,
     "gmm_integer": gmm_integer,
-    "powerlaw_rotated": powerlaw_rotated,
+    "powerlaw_mixture": powerlaw_mixture,
     "gmm_unit_normalised": gmm_unit_normalised,
     "gmm_anisotropic": gmm_anisotropic,
 }
@@ -177,8 +182,8 @@ WORKLOADS = {
                       seed=1002, q_seed=1003)),
     "gist1m": Workload(
         "gist1m", n=1_000_000, d=960, nq=1_000, n_subspaces=10, sub_dim=96, sqrt_k=64,
-        k=10, alpha=0.05, beta=0.005, gen="powerlaw_rotated",
-        gen_args=dict(exponent=1.2, seed=1003, q_seed=1004)),
+        k=10, alpha=0.05, beta=0.005, gen="powerlaw_mixture",
+        gen_args=dict(n_comp=1024, spread=0.5, exponent=1.2, seed=1003, q_seed=1004)),
     "deep10m": Workload(
         "deep10m", n=10_000_000, d=96, nq=4_096, n_subspaces=6, sub_dim=8, sqrt_k=64,
         k=100, alpha=0.02, beta=0.002, gen="gmm_unit_normalised",

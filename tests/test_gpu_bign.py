@@ -5,7 +5,7 @@ probed points (Def. 6) instead of the cluster kernel's shared-memory counters.
 Forced on the 20k x 128 workload and a multi-slab index, every intermediate and result must
 match the FP64 oracle under the parity rule for budgets and targets that reach each case
 (threshold 0 = all points, threshold 1, overflowing lists). An index with more points than
-any cluster's shared memory holds (6.4M > 16 x 12 x 2^15) uses it always: sampled queries
+any cluster's shared memory holds (6.4M > 16 x 11 x 2^15) uses it always: sampled queries
 match the oracle on the exported index, and the entry points that need a cluster refuse."""
 import numpy as np
 import pytest
@@ -97,3 +97,28 @@ def test_big_index_refuses_cluster_paths(big):
     with pytest.raises(TacoError) as err:
         ix.search_noalloc(q, ids, dists, 10, 1000, 100)
     assert err.value.code == -5
+
+
+def test_cluster_layout_fits_shared_memory():
+    """89 slabs (2.9M points): 8 CTAs of 12 slabs would need more shared memory than a CTA
+    can opt into, so the layout takes 15 CTAs of 6 slabs; queries whose threshold falls
+    below 2 are answered by the cluster kernel in that layout and match the oracle."""
+    rng = np.random.default_rng(321)
+    n, d = 2_900_000, 16
+    centres = rng.uniform(0, 100, size=(256, d)).astype(np.float32)
+    data = np.empty((n, d), dtype=np.float32)
+    for a in range(0, n, 1 << 20):
+        m = min(n, a + (1 << 20)) - a
+        data[a:a + m] = centres[rng.integers(0, 256, m)] + 3 * rng.standard_normal((m, d), dtype=np.float32)
+    queries = (centres[rng.integers(0, 256, 5)] + 3 * rng.standard_normal((5, d))).astype(np.float32)
+    ix = TacoIndex.build(data, 2, 8, 32, kmeans_iters=4, seed=7, keep_bf16=True)
+    try:
+        info = ix.info()
+        assert info["n_slabs"] == 89 and 8 < info["cluster_size"] <= 16
+        ex = ix.export()
+        oix = O.index_from_parts(ex["o_bar"], ex["B"], ex["centroids"], ex["codes"], 2, 8, 32)
+        # a target far above the ids with SC >= 2: threshold 1, every query flagged
+        dbg = _check(ix, oix, data, queries, 10, budget_from_alpha(0.001, n), target_from_beta(0.01, n))
+        assert np.all(dbg["last_collision"] <= 1)
+    finally:
+        ix.close()
