@@ -265,8 +265,9 @@ int taco_centroid_distances(const taco_index* index, const float* qt, int64_t nq
  *   An index whose n is too large for any cluster (more than 16 x 11 slabs of 2^15 points)
  *   always uses the codes fallback (TACO_ECAPACITY for value 0).
  *   TACO_OPT_SLABS_PER_RANGE: counter slabs per id range of the two-pass counting, 1 .. 12
- *   (a value above the index's n_slabs acts as n_slabs; n_ranges follows; TACO_ECAPACITY at
- *   search time if the counters do not fit an SM).
+ *   with 4-bit counters, and 13 .. 15 with 3-bit counters for an index of N_s <= 7 (a value
+ *   above the index's n_slabs acts as n_slabs; n_ranges follows; TACO_ECAPACITY at search
+ *   time if the counters do not fit an SM; TACO_EINVAL outside the range).
  *   TACO_OPT_COUNT_WARPS: warps per counting CTA, 8, 16 or 32.
  *   TACO_OPT_WALK_UNROLL: loads of four ids in flight per lane in the counting walk, 2, 4 or 8
  *   (8 takes effect with 16 warps only; an unbuilt pair runs 16 warps x 4).

@@ -126,7 +126,14 @@ int build_fp8_rows(taco_index* ix, cudaStream_t st) {
     const bool transformed = ix->Dp == ix->d;
     const int cols = transformed ? ix->Dp : ix->d;   // FP8 coordinates per point
     ix->fp8_space = transformed ? 0 : 1;
+    // row pitch: a power of two up to 64 bytes, else whole 128-byte lines, so that a row's
+    // gather reads only lines of its own (the pad bytes are E4M3 zeros with scale 0)
     ix->dp8 = (cols + 15) & ~15;
+    if (ix->dp8 <= 64) {
+        while (ix->dp8 & (ix->dp8 - 1)) ix->dp8 += 16;
+    } else {
+        ix->dp8 = (ix->dp8 + 127) & ~127;
+    }
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t(256) << 20) / (int64_t(cols) * 4)));
     float* tmp = nullptr;
     unsigned* maxbits = nullptr;
@@ -850,7 +857,9 @@ int taco_index_set_option(taco_index* ix, int32_t option, int32_t value) {
     switch (option) {
         case TACO_OPT_CODES_FALLBACK: break;
         case TACO_OPT_SLABS_PER_RANGE:
-            if (value < 1 || value > 12) return fail(TACO_EINVAL, "slabs per range %d not in 1..12", value);
+            // 13..15 slabs take 3-bit counters: only where a count cannot exceed 7
+            if (value < 1 || value > (ix->Ns <= 7 ? 15 : 12))
+                return fail(TACO_EINVAL, "slabs per range %d not in 1..%d", value, ix->Ns <= 7 ? 15 : 12);
             ix->tp_spc = std::min<int>(value, ix->n_slabs);
             ix->tp_ranges = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
             return TACO_OK;

@@ -37,6 +37,19 @@ __device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
     return r;
 }
 
+// Publication of a staged batch between warps of a CTA: release store / acquire load of a
+// shared-memory flag.
+__device__ __forceinline__ void st_release_cta(int* p, int v) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta(const int* p) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    int v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
 // Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address into L2;
 // no completion to wait for.
 __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
@@ -59,100 +72,186 @@ __device__ __forceinline__ void chunk_run(uint32_t b, uint32_t e, uint32_t& star
     len = e > b ? ((e + 3u) >> 2) - start : 0u;
 }
 
-// Walk one staged batch of chunk runs (total chunks in nr non-empty runs; run r covers
-// chunks rbase[r] + [cpre[r], cpre[r + 1]) of the id array). Every id of a chunk that lies in
-// the unit's range [lo, lo + rlen) adds 1 to its 4-bit counter; when the atomic's old value
-// v is >= 1 the id has just reached level v + 1 >= 2 and is appended to the unit's arena slot
-// `out` as (id - lo) | (v + 1) << kLevelShift, and ge[v + 1] counts it. The concatenated
-// chunks are walked in rounds of WU windows of 32 chunks (one chunk per lane and window, WU
-// loads of 16 bytes in flight per lane). Lane u finds the run of the first chunk of window u
-// (binary search); in a window, lane j reads the j-th next run boundary, the boundaries
-// inside the window form a bit mask, and a lane's run is the window's first run plus the
-// mask bits at or below it (runs are non-empty, so at most 32 boundaries fall in a window).
-// Rounds are handed to warps by a shared counter (*s_round, zero on entry), so warps that
-// drew short work take more. Lanes past the end load a valid chunk and count nothing: their
-// atomics add 0 to the lane's own spare word cnt[counter_words + lane] (which stays 0), so
-// no branch depends on the data and every atomic is a shared-memory one on cnt. Entries
-// beyond `cap` are counted in *s_app but not stored (the caller sees the overflow).
-// Warp-level; no barrier.
-template <int NW, int WU>
-__device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint32_t last_chunk, uint32_t lo,
-                                            uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
-                                            uint32_t* out, uint32_t cap, uint32_t* ge, uint32_t* s_app,
-                                            uint32_t* s_round, const uint32_t* cpre, const uint32_t* rbase,
-                                            uint64_t pol, int lane, int* status, uint32_t counter_words) {
-    static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU append bits a lane");
+// Packing of the shared-memory counters: CB = 4 bits, 8 counters a word (any N_s up to 15), or
+// CB = 3 bits, 10 counters in the low 30 bits of a word (N_s <= 7, so a count never exceeds 7;
+// 15 slabs of 2^15 ids fit the 192 KB that 12 slabs take at 4 bits).
+template <int CB>
+struct CounterGeom;
+template <>
+struct CounterGeom<4> {
+    static constexpr uint32_t kPer = 8, kMask = 15u;
+    __device__ __forceinline__ static uint32_t word(uint32_t x) { return x >> 3; }
+    __device__ __forceinline__ static uint32_t shift(uint32_t x, uint32_t w) { return (x - (w << 3)) << 2; }
+};
+template <>
+struct CounterGeom<3> {
+    static constexpr uint32_t kPer = 10, kMask = 7u;
+    // x / 10 for x < 2^30: the product with ceil(2^32 / 10) errs by less than 0.1 x / 2^30
+    __device__ __forceinline__ static uint32_t word(uint32_t x) { return __umulhi(x, 429496730u); }
+    __device__ __forceinline__ static uint32_t shift(uint32_t x, uint32_t w) { return (x - w * 10u) * 3u; }
+};
+
+// Counter words of a range of `ids` ids.
+__host__ __device__ __forceinline__ int counter_words_for(int64_t ids, int cb) {
+    const int64_t per = cb == 3 ? 10 : 8;
+    return int((ids + per - 1) / per);
+}
+
+// One walk round's loads, held in registers from the issue to the count (possibly across the
+// barriers between two ranges: a warp that finds no more rounds of range r takes the first
+// round it can of range r + 1, staged already, and issues its loads before it waits).
+template <int WU>
+struct WalkRound {
+    uint4 v[WU];
+    uint32_t live;   // bit u: this lane's chunk of window u is inside the batch
+    bool has;        // warp-uniform
+};
+
+// Issue the loads of round g (WU windows of 32 chunks) of a staged batch of chunk runs
+// (total chunks in nr non-empty runs; run r covers chunks rbase[r] + [cpre[r], cpre[r + 1])
+// of the id array). Lane u finds the run of the first chunk of window u (binary search); in a
+// window, lane j reads the j-th next run boundary, the boundaries inside the window form a
+// bit mask, and a lane's run is the window's first run plus the mask bits at or below it
+// (runs are non-empty, so at most 32 boundaries fall in a window). Lanes past the end load a
+// valid chunk and are not live.
+template <int WU>
+__device__ __forceinline__ void issue_round(WalkRound<WU>& R, const uint4* __restrict__ ids4, uint32_t last_chunk,
+                                            uint32_t g, uint32_t total, uint32_t nr, const uint32_t* cpre,
+                                            const uint32_t* rbase, uint64_t pol, int lane, int* status) {
     const uint32_t lane_le = (2u << lane) - 1u;   // lanes 0..lane
-    constexpr uint32_t kRound = 32u * WU;
-    const uint32_t nrounds = (total + kRound - 1) / kRound;
-    for (;;) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(s_round, 1u);
-        g = __shfl_sync(kFull, g, 0);   // warp-uniform
-        if (g >= nrounds) break;
-        const uint32_t e0 = g * kRound;
-        const uint32_t key = min(e0 + 32u * uint32_t(lane % WU), total - 1u);
-        const uint32_t cwl = uint32_t(find_cell(cpre, int(nr), key));
-        uint4 v[WU];
-        uint32_t live = 0;   // bit u: this lane's chunk of window u is inside the batch
+    const uint32_t e0 = g * 32u * WU;
+    const uint32_t key = min(e0 + 32u * uint32_t(lane % WU), total - 1u);
+    const uint32_t cwl = uint32_t(find_cell(cpre, int(nr), key));
+    R.live = 0;
 #pragma unroll
-        for (int u = 0; u < WU; ++u) {
-            const uint32_t E = e0 + 32u * uint32_t(u);
-            const uint32_t cw = __shfl_sync(kFull, cwl, u);
-            const uint32_t pb = cpre[cw + 1u + uint32_t(lane)] - E;                 // >= 1 inside
-            const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));     // 0 for pb >= 32
-            const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
-            const uint32_t xr = rbase[r] + E + uint32_t(lane);
-            const bool in = E + uint32_t(lane) < total;
-            TACO_CHECK(status, !in || xr <= last_chunk, kStatusCount);
-            const uint32_t x = min(xr, last_chunk);
-            v[u] = ldg_keep_u4(ids4 + x, pol);
-            live |= (in ? 1u : 0u) << u;
-        }
-        // count: all atomics of the round are independent; an id whose old count v is >= 1
-        // has just reached level v + 1 and is kept, tagged, for the arena
-        uint32_t amask = 0;
-        uint32_t rel[WU][4];
+    for (int u = 0; u < WU; ++u) {
+        const uint32_t E = e0 + 32u * uint32_t(u);
+        const uint32_t cw = __shfl_sync(kFull, cwl, u);
+        const uint32_t pb = cpre[cw + 1u + uint32_t(lane)] - E;                 // >= 1 inside
+        const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));     // 0 for pb >= 32
+        const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
+        const uint32_t xr = rbase[r] + E + uint32_t(lane);
+        const bool in = E + uint32_t(lane) < total;
+        (void)TACO_CHECK(status, !in || xr <= last_chunk, kStatusCount);
+        const uint32_t x = min(xr, last_chunk);
+        R.v[u] = ldg_keep_u4(ids4 + x, pol);
+        R.live |= (in ? 1u : 0u) << u;
+    }
+    R.has = true;
+}
+
+// Count a round whose loads are in R against the unit's range [lo, lo + rlen): every id of a
+// live chunk in the range adds 1 to its CB-bit counter; when the atomic's old value v is >= 1
+// the id has just reached level v + 1 >= 2 and is appended to the unit's arena slot `out` as
+// (id - lo) | (v + 1) << kLevelShift, and ge[v + 1] counts it. Ids outside the range (the
+// chunk's neighbours in the same cell list, padding) and idle lanes add 0 to the lane's own
+// spare word cnt[counter_words + lane] (which stays 0), so no branch depends on the data and
+// every atomic is a shared-memory one on cnt. Entries beyond `cap` are counted in *s_app but
+// not stored (the caller sees the overflow).
+template <int WU, int CB>
+__device__ __forceinline__ void count_round(WalkRound<WU>& R, uint32_t lo, uint32_t rlen, uint32_t* cnt,
+                                            uint32_t* out, uint32_t cap, uint32_t* ge, uint32_t* s_app, int lane,
+                                            int* status, uint32_t counter_words) {
+    using Geom = CounterGeom<CB>;
+    // all atomics of the round are independent
+    uint32_t amask = 0;
+    uint32_t rel[WU][4];
 #pragma unroll
-        for (int u = 0; u < WU; ++u) {
-            const uint32_t w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+    for (int u = 0; u < WU; ++u) {
+        const uint32_t w4[4] = {R.v[u].x, R.v[u].y, R.v[u].z, R.v[u].w};
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const uint32_t x = w4[h] - lo;
-                const bool ok = ((live >> u) & 1u) && x < rlen &&
-                                TACO_CHECK(status, (x >> 3) < counter_words, kStatusCount);
-                const uint32_t sh = (x & 7u) << 2;
-                const uint32_t w = ok ? (x >> 3) : counter_words + uint32_t(lane);
-                const uint32_t old = atomicAdd(&cnt[w], ok ? 1u << sh : 0u);
-                const uint32_t v = (old >> sh) & 15u;
-                amask |= (v != 0u ? 1u : 0u) << (4 * u + h);
-                rel[u][h] = x | ((v + 1u) << kLevelShift);
-            }
-        }
-        // append the ids that reached a level >= 2: one reservation per warp and round
-        if (__any_sync(kFull, amask != 0u)) {
-            const uint32_t na = __popc(amask);
-            uint32_t incl = na;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, off);
-                if (lane >= off) incl += t;
-            }
-            const uint32_t tot = __shfl_sync(kFull, incl, 31);
-            uint32_t base = 0;
-            if (lane == 31) base = atomicAdd(s_app, tot);
-            uint32_t pos = __shfl_sync(kFull, base, 31) + incl - na;
-#pragma unroll
-            for (int u = 0; u < WU; ++u)
-#pragma unroll
-                for (int h = 0; h < 4; ++h)
-                    if ((amask >> (4 * u + h)) & 1u) {
-                        if (pos < cap) out[pos] = rel[u][h];
-                        atomicAdd(&ge[rel[u][h] >> kLevelShift], 1u);
-                        ++pos;
-                    }
+        for (int h = 0; h < 4; ++h) {
+            const uint32_t x = w4[h] - lo;
+            const uint32_t xw = Geom::word(x);
+            const bool ok = ((R.live >> u) & 1u) && x < rlen &&
+                            TACO_CHECK(status, xw < counter_words, kStatusCount);
+            const uint32_t sh = Geom::shift(x, xw);
+            const uint32_t w = ok ? xw : counter_words + uint32_t(lane);
+            const uint32_t old = atomicAdd(&cnt[w], ok ? 1u << sh : 0u);
+            const uint32_t v = (old >> sh) & Geom::kMask;
+            amask |= (v != 0u ? 1u : 0u) << (4 * u + h);
+            rel[u][h] = x | ((v + 1u) << kLevelShift);
         }
     }
+    // append the ids that reached a level >= 2: one reservation per warp and round
+    if (__any_sync(kFull, amask != 0u)) {
+        const uint32_t na = __popc(amask);
+        uint32_t incl = na;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        uint32_t base = 0;
+        if (lane == 31) base = atomicAdd(s_app, tot);
+        uint32_t pos = __shfl_sync(kFull, base, 31) + incl - na;
+#pragma unroll
+        for (int u = 0; u < WU; ++u)
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                if ((amask >> (4 * u + h)) & 1u) {
+                    if (pos < cap) out[pos] = rel[u][h];
+                    atomicAdd(&ge[rel[u][h] >> kLevelShift], 1u);
+                    ++pos;
+                }
+    }
+    R.has = false;
+}
+
+// The next range of a work item, for the walk's carried round: its staged batch (valid once
+// *ready == index, which the stager publishes) and its round counter.
+struct NextBatch {
+    const uint32_t* cpre;
+    const uint32_t* rbase;
+    const uint32_t* total;
+    const uint32_t* nr;
+    uint32_t* s_round;
+    const int* ready;
+    int index;   // -1: no next range
+};
+
+// Walk one staged batch: rounds of WU windows handed to warps by a shared counter (*s_round,
+// zero on entry, or already counting the rounds that warps carried into this batch), so warps
+// that drew short work take more. Each warp keeps two rounds in flight: it issues the loads of
+// its next round before it counts the current one (the first current round is the one R
+// carries from the previous range, if any). A warp that finds no more rounds takes, if the
+// next range is staged, one round of it into R (issued, not counted). Warp-level; no barrier.
+template <int NW, int WU, int CB>
+__device__ __forceinline__ void walk_chunks(WalkRound<WU>& R, const uint4* __restrict__ ids4, uint32_t last_chunk,
+                                            uint32_t lo, uint32_t rlen, uint32_t total, uint32_t nr,
+                                            uint32_t* cnt, uint32_t* out, uint32_t cap, uint32_t* ge,
+                                            uint32_t* s_app, uint32_t* s_round, const uint32_t* cpre,
+                                            const uint32_t* rbase, const NextBatch& nx, uint64_t pol, int lane,
+                                            int* status, uint32_t counter_words) {
+    static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU append bits a lane");
+    constexpr uint32_t kRound = 32u * WU;
+    const uint32_t nrounds = (total + kRound - 1) / kRound;
+    auto claim = [&](uint32_t* counter) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(counter, 1u);
+        return __shfl_sync(kFull, g, 0);   // warp-uniform
+    };
+    if (!R.has) {
+        const uint32_t g = claim(s_round);
+        if (g < nrounds) issue_round<WU>(R, ids4, last_chunk, g, total, nr, cpre, rbase, pol, lane, status);
+    }
+    while (R.has) {
+        WalkRound<WU> N;
+        N.has = false;
+        const uint32_t g = claim(s_round);
+        if (g < nrounds) issue_round<WU>(N, ids4, last_chunk, g, total, nr, cpre, rbase, pol, lane, status);
+        count_round<WU, CB>(R, lo, rlen, cnt, out, cap, ge, s_app, lane, status, counter_words);
+        R = N;
+    }
+    if (nx.index < 0) return;
+    // the next range's first rounds, where it is staged: issued now, counted after the barriers
+    const bool ready = ld_acquire_cta(nx.ready) == nx.index;
+    if (!__all_sync(kFull, ready)) return;
+    const uint32_t ntot = *nx.total;
+    const uint32_t g = claim(nx.s_round);
+    if (g < (ntot + kRound - 1) / kRound)
+        issue_round<WU>(R, ids4, last_chunk, g, ntot, *nx.nr, nx.cpre, nx.rbase, pol, lane, status);
 }
 
 // One warp stages the chunk runs of the ncell staged cells of one range (their id-position
@@ -204,7 +303,7 @@ __device__ __forceinline__ uint2 warp_stage(const uint2* pr, int ncell, uint32_t
     return make_uint2(total, nr);
 }
 
-// NW warps per CTA, WU windows of 32 chunks per walk round.
+// NW warps per CTA, WU windows of 32 chunks per walk round, CB-bit counters.
 //
 // Ranges of a query are pipelined when its probed cells fit one staging batch (at most
 // kCellBatch cells): warp NW - 1 (the stager) owns the split bounds (asynchronous copies two
@@ -212,8 +311,8 @@ __device__ __forceinline__ uint2 warp_stage(const uint2* pr, int ncell, uint32_t
 // into L2 and stages its chunk runs into the second staging buffer, then joins the walk. A
 // range costs two barriers: after its walk (counters final), and after the unit's outputs
 // and the clearing of the counters.
-template <int NW, int WU>
-__global__ void __launch_bounds__(NW * 32, (NW == 8 || (NW == 16 && WU <= 4)) ? 2 : 1)
+template <int NW, int WU, int CB>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1)
 count_lists_kernel(const RerankParams P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kStager = NW - 1;
@@ -227,7 +326,9 @@ count_lists_kernel(const RerankParams P) {
     uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * NW];
-    __shared__ uint32_t s_app, s_round, s_ev;
+    __shared__ uint32_t s_app, s_ev;
+    __shared__ uint32_t s_rnd[2];   // walk round counters of the two staged ranges
+    __shared__ int s_ready;         // the range whose staging the stager has published
     __shared__ uint32_t s_tot2[2], s_nr2[2], s_ev2[2];   // staged batch of each buffer
     __shared__ int64_t s_next;
     const int Ns = P.Ns, K = P.K;
@@ -241,7 +342,7 @@ count_lists_kernel(const RerankParams P) {
     if (tid < 16) ge[tid] = 0u;
     if (tid == 0) {
         s_app = 0u;
-        s_round = 0u;
+        s_rnd[0] = s_rnd[1] = 0u;
         s_ev = 0u;
     }
     // stager: the split bounds of every staged cell for range r into pairs[slot] (asynchronous)
@@ -272,7 +373,11 @@ count_lists_kernel(const RerankParams P) {
             s_nr2[buf] = st.y;
             s_ev2[buf] = ev;
         }
+        __threadfence_block();
+        __syncwarp();
     };
+    WalkRound<WU> R;   // a round carried into the next range (see walk_chunks)
+    R.has = false;
     // work item: ranges [rb, re) of query q (all its ranges unless a small batch splits them
     // into range_parts runs so that more CTAs work on it)
     const int parts = P.range_parts;
@@ -284,6 +389,7 @@ count_lists_kernel(const RerankParams P) {
         const int re = min(P.n_ranges, rb + per_part);
         __syncthreads();   // the previous item is finished with the shared state
         if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
+        if (tid == 0) s_ready = -1;
         __syncthreads();
         const int total_cells = s_pre[Ns];
         const bool staged = total_cells <= kCellBatch;   // one batch: cells kept for every range
@@ -315,29 +421,35 @@ count_lists_kernel(const RerankParams P) {
             const int slab_hi = min(slab_lo + P.slabs_per_cta, P.n_slabs);
             const int64_t lo = int64_t(slab_lo) << kSlabLog2;
             const int64_t hi = min(int64_t(slab_hi) << kSlabLog2, P.n);
-            const int words = hi > lo ? int((hi - lo + 7) >> 3) : 0;
+            const int words = hi > lo ? counter_words_for(hi - lo, CB) : 0;
             const uint32_t rlen = uint32_t(hi - lo);
             uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
-            TACO_CHECK(P.status, (size_t(u) + 1) * P.arena_per_unit <= P.arena_words, kStatusCount);
-            // (the counters are clear, ge / s_app / s_round zero, range r staged)
+            (void)TACO_CHECK(P.status, (size_t(u) + 1) * P.arena_per_unit <= P.arena_words, kStatusCount);
+            // (the counters are clear, ge / s_app zero, range r staged, its round counter zero
+            // or counting the rounds that warps carried from range r - 1)
             if (staged) {
                 const int buf = (r - rb) & 1;   // staging buffer and bounds slot of range r
                 if (warp == kStager && r + 1 < re) {
                     cp_async_wait_all();   // the bounds of range r + 1 (slot buf ^ 1)
                     __syncwarp();
                     stage_range(total_cells, buf ^ 1, buf ^ 1, true);
+                    if (lane == 0) st_release_cta(&s_ready, r + 1);   // walkers may take its rounds
                     if (r + 2 < re) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
                 }
+                const NextBatch nx{cpre + (buf ^ 1) * kPre, rbase + (buf ^ 1) * kCellBatch, &s_tot2[buf ^ 1],
+                                   &s_nr2[buf ^ 1], &s_rnd[buf ^ 1], &s_ready, r + 1 < re ? r + 1 : -1};
                 const uint32_t tot = s_tot2[buf];
-                if (tot) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, out, cap, ge,
-                                             &s_app, &s_round, cpre + buf * kPre, rbase + buf * kCellBatch, pol_keep,
-                                             lane, P.status, uint32_t(P.counter_words));
+                if (tot) walk_chunks<NW, WU, CB>(R, ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, out, cap,
+                                                 ge, &s_app, &s_rnd[buf], cpre + buf * kPre, rbase + buf * kCellBatch,
+                                                 nx, pol_keep, lane, P.status, uint32_t(P.counter_words));
             } else {
-                for (int cb0 = 0; cb0 < total_cells; cb0 += kCellBatch) {
+                // batches of one cell per thread, at most kCellBatch (the staging arrays)
+                constexpr int kBatch = NW * 32 < kCellBatch ? NW * 32 : kCellBatch;
+                for (int cb0 = 0; cb0 < total_cells; cb0 += kBatch) {
                     if (cb0) __syncthreads();   // the previous batch is walked
                     uint32_t b = 0, e = 0;
                     const int g = cb0 + tid;
-                    if (tid < kCellBatch && g < total_cells) {
+                    if (tid < kBatch && g < total_cells) {
                         int i = 0;
                         while (g >= s_pre[i + 1]) ++i;
                         const int cell = P.cells[(q * Ns + i) * K + (g - s_pre[i])];
@@ -349,16 +461,17 @@ count_lists_kernel(const RerankParams P) {
                     chunk_run(b, e, start, len);
                     const uint32_t ev = __reduce_add_sync(kFull, e - b);
                     if (lane == 0 && ev) atomicAdd(&s_ev, ev);
-                    if (tid == 0) s_round = 0u;   // read after the staging's barriers
+                    if (tid == 0) s_rnd[0] = 0u;   // read after the staging's barriers
                     const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-                    if (st.x) walk_chunks<NW, WU>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, out, cap, ge,
-                                                  &s_app, &s_round, cpre, rbase, pol_keep, lane, P.status,
-                                                  uint32_t(P.counter_words));
+                    const NextBatch none{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1};
+                    if (st.x) walk_chunks<NW, WU, CB>(R, ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, out, cap,
+                                                      ge, &s_app, &s_rnd[0], cpre, rbase, none, pol_keep, lane,
+                                                      P.status, uint32_t(P.counter_words));
                 }
             }
             __syncthreads();   // the range's counters, entries and level counts are final
             if (P.dbg_sc) {
-                debug_sc<NW>(P, q, lo, hi, words, cnt, tid);
+                debug_sc<NW, CounterGeom<CB>::kPer, CB>(P, q, lo, hi, words, cnt, tid);
                 __syncthreads();   // every counter is read before any is cleared
             }
             if (warp == 0) {
@@ -379,7 +492,7 @@ count_lists_kernel(const RerankParams P) {
                 }
                 if (lane == 0) {
                     s_app = 0u;
-                    s_round = 0u;
+                    s_rnd[staged ? (r - rb) & 1 : 0] = 0u;   // range r's counter (the next one's may be in use)
                     s_ev = 0u;
                 }
             }

@@ -512,7 +512,7 @@ __device__ __forceinline__ void walk_batch(const RerankParams& P, int64_t lo, ui
             const uint32_t mask = __reduce_or_sync(kFull, shl_clamped(1u, pb));   // 0 for pb >= 32
             const uint32_t r = min(cw + __popc(mask & lane_le), nr - 1u);
             const uint32_t xr = sm.rbase[r] + E + uint32_t(lane);
-            TACO_CHECK(P.status, E + uint32_t(lane) >= total || xr <= last_idx, kStatusCluster);
+            (void)TACO_CHECK(P.status, E + uint32_t(lane) >= total || xr <= last_idx, kStatusCluster);
             const uint32_t x = min(xr, last_idx);
             const uint32_t v = ldg_keep_u32(P.ids + x, pol_keep);
             idv[u] = E + uint32_t(lane) < total ? v - uint32_t(lo) : kPastEnd;
@@ -627,15 +627,16 @@ __device__ __forceinline__ bool count_phase(const RerankParams& P, int64_t q, in
 }
 
 // Debug: the SC of every touched id of the range (untouched ids stay at the caller's zero).
-template <int NW = kRrWarps>   // warps of the block
+template <int NW = kRrWarps, int PER = 8, int CB = 4>   // warps of the block, counters a word, bits
 __device__ __forceinline__ void debug_sc(const RerankParams& P, int64_t q, int64_t lo, int64_t hi,
                                         int words, const uint32_t* cnt, int tid) {
+    constexpr uint32_t kMask = (1u << CB) - 1u;
     for (int w = tid; w < words; w += (NW * 32)) {
         const uint32_t x = cnt[w];
         if (!x) continue;
-        const int64_t id0 = lo + (int64_t(w) << 3);
-        for (int j = 0; j < 8 && id0 + j < hi; ++j)
-            if ((x >> (4 * j)) & 15u) P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (4 * j)) & 15u);
+        const int64_t id0 = lo + int64_t(w) * PER;
+        for (int j = 0; j < PER && id0 + j < hi; ++j)
+            if ((x >> (CB * j)) & kMask) P.dbg_sc[q * P.n + id0 + j] = uint8_t((x >> (CB * j)) & kMask);
     }
 }
 

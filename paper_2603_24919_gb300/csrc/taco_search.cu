@@ -783,10 +783,11 @@ int configure_search(taco_index* ix) {
     }
     if (spc > spc_max || cluster > 16) {
         // no cluster holds a query's counters: the two-pass form counts in ranges of 12
-        // slabs and flagged queries take the codes fallback
+        // slabs (15 with 3-bit counters where N_s <= 7) and flagged queries take the codes
+        // fallback
         ix->cluster = 0;
         ix->slabs_per_cta = 0;
-        ix->tp_spc = std::min(12, ix->n_slabs);
+        ix->tp_spc = std::min(ix->Ns <= 7 ? 15 : 12, ix->n_slabs);
         ix->tp_ranges = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
         return TACO_OK;
     }
@@ -1000,8 +1001,10 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         const bool two_pass = L.unit_ge != nullptr;
         if (two_pass) {
             // the two-pass range layout (tuned): tp_spc slabs of counters per range
+            // (4-bit counters up to 12 slabs, 3-bit counters for 13-15 slabs, N_s <= 7)
+            const int cb = ix->tp_spc > 12 ? 3 : 4;
             P.slabs_per_cta = ix->tp_spc;
-            P.counter_words = ix->tp_spc * kSlabWords;
+            P.counter_words = (counter_words_for(int64_t(ix->tp_spc) * kSlabIds, cb) + 3) & ~3;
             P.region_a = size_t(P.counter_words) * 4 + 32 * 4;   // + the walk's 32 spare words
             P.n_ranges = ix->tp_ranges;
             P.arena_per_unit = uint32_t(kArenaPerSlab) * uint32_t(ix->tp_spc);
@@ -1018,18 +1021,23 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             // 2, 4 or 8 chunk windows per walk round (tuned)
             const size_t smem1 = P.region_a + count_lists_extra();
             struct CountVariant {
-                int nw, wu;
+                int nw, wu, cb;
                 void (*fn)(const RerankParams);
             };
             static const CountVariant kVariants[] = {
-                {8, 2, count_lists_kernel<8, 2>},   {8, 4, count_lists_kernel<8, 4>},
-                {16, 2, count_lists_kernel<16, 2>}, {16, 4, count_lists_kernel<16, 4>},
-                {16, 8, count_lists_kernel<16, 8>}, {32, 2, count_lists_kernel<32, 2>},
-                {32, 4, count_lists_kernel<32, 4>}};
+                {8, 2, 4, count_lists_kernel<8, 2, 4>},   {8, 4, 4, count_lists_kernel<8, 4, 4>},
+                {16, 2, 4, count_lists_kernel<16, 2, 4>}, {16, 4, 4, count_lists_kernel<16, 4, 4>},
+                {16, 8, 4, count_lists_kernel<16, 8, 4>}, {32, 2, 4, count_lists_kernel<32, 2, 4>},
+                {32, 4, 4, count_lists_kernel<32, 4, 4>}, {8, 2, 3, count_lists_kernel<8, 2, 3>},
+                {8, 4, 3, count_lists_kernel<8, 4, 3>},   {16, 2, 3, count_lists_kernel<16, 2, 3>},
+                {16, 4, 3, count_lists_kernel<16, 4, 3>}, {16, 8, 3, count_lists_kernel<16, 8, 3>},
+                {32, 2, 3, count_lists_kernel<32, 2, 3>}, {32, 4, 3, count_lists_kernel<32, 4, 3>}};
             constexpr int kNumVariants = int(sizeof(kVariants) / sizeof(kVariants[0]));
-            int c1 = 3;   // 16 x 4 unless the tuned pair exists
+            int c1 = cb == 4 ? 3 : 10;   // 16 x 4 unless the tuned pair exists
             for (int v = 0; v < kNumVariants; ++v)
-                if (kVariants[v].nw == ix->tp_count_warps && kVariants[v].wu == ix->tp_walk_unroll) c1 = v;
+                if (kVariants[v].nw == ix->tp_count_warps && kVariants[v].wu == ix->tp_walk_unroll &&
+                    kVariants[v].cb == cb)
+                    c1 = v;
             const int nw1 = kVariants[c1].nw;
             auto k1 = kVariants[c1].fn;
             static thread_local size_t c1_smem[kNumVariants] = {};

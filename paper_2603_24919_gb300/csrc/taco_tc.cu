@@ -239,19 +239,20 @@ centroid_dist_tc_kernel(const float* __restrict__ qt, int64_t nq, TcGeom g, int 
                     }
                     *reinterpret_cast<uint4*>(dst + c16 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                continue;
-            }
-            for (int c8 = 0; c8 < kc; ++c8) {
-                uint32_t w[4];
+            } else {
+                for (int c8 = 0; c8 < kc; ++c8) {
+                    uint32_t w[4];
 #pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    const int k = c8 * 8 + e;
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(k < len ? x[k] : 0.f, k + 1 < len ? x[k + 1] : 0.f);
-                    uint32_t u;
-                    memcpy(&u, &b2, 4);
-                    w[e >> 1] = u;
+                    for (int e = 0; e < 8; e += 2) {
+                        const int k = c8 * 8 + e;
+                        const __nv_bfloat162 b2 =
+                            __floats2bfloat162_rn(k < len ? x[k] : 0.f, k + 1 < len ? x[k + 1] : 0.f);
+                        uint32_t u;
+                        memcpy(&u, &b2, 4);
+                        w[e >> 1] = u;
+                    }
+                    *reinterpret_cast<uint4*>(dst + c8 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                *reinterpret_cast<uint4*>(dst + c8 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A visible to the MMA

@@ -104,10 +104,11 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
         }
         return TACO_OK;
     };
-    // 1. counter layout: slabs per range (16 KB each) up to what a CTA's shared memory holds
-    //    (up to 5 slabs, two 512-thread counting CTAs share an SM)
-    for (int spc : {1, 2, 4, 5, 8, 12}) {
-        if (spc > ix->n_slabs || spc == cur.spc) continue;
+    // 1. counter layout: slabs per range (16 KB each at 4 bits) up to what a CTA's shared
+    //    memory holds (up to 5 slabs, two 512-thread counting CTAs share an SM); 15 slabs at
+    //    3 bits where N_s <= 7
+    for (int spc : {1, 2, 4, 5, 8, 12, 15}) {
+        if (spc > ix->n_slabs || spc == cur.spc || (spc > 12 && ix->Ns > 7)) continue;
         Choice c = cur;
         c.spc = spc;
         c.ranges = (ix->n_slabs + spc - 1) / spc;

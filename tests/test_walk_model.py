@@ -187,3 +187,68 @@ def test_chunk_walk_counts_exactly_the_probed_ids_of_the_range(wu, n_cells, n):
             assert tagged == sorted(r for r, c in cnt.items() if c >= j), j
         ge1 = sum(1 for c in cnt.values() if c >= 1)
         assert ge1 == len(got) - len(entries)
+
+
+# ------------------------------------------------------- counter packing and carried rounds
+def test_three_bit_counter_word_and_shift():
+    """3-bit counters (10 a word): word(x) = high 32 bits of x * ceil(2^32 / 10) equals
+    x // 10 for every id offset of a 15-slab range (and far beyond), shift = 3 (x mod 10) stays
+    inside the low 30 bits, and a count of at most 7 never carries into a neighbour."""
+    x = np.arange(0, 1 << 22, dtype=np.uint64)
+    word = (x * np.uint64(429496730)) >> np.uint64(32)
+    assert np.array_equal(word, x // np.uint64(10))
+    top = np.array([2**30 - 1, 2**30 - 10, 2**29 + 7], dtype=np.uint64)
+    assert np.array_equal((top * np.uint64(429496730)) >> np.uint64(32), top // np.uint64(10))
+    shift = (x[:1000] - word[:1000] * np.uint64(10)) * np.uint64(3)
+    assert shift.max() == 27
+    rng = np.random.default_rng(7)
+    for _ in range(200):   # ten counters packed by repeated adds, each at most 7
+        counts = rng.integers(0, 8, 10)
+        w = 0
+        for j, c in enumerate(counts):
+            for _ in range(int(c)):
+                old = w
+                w = (w + (1 << (3 * j))) & M32
+                assert (old >> (3 * j)) & 7 == ((w >> (3 * j)) & 7) - 1
+        assert [(w >> (3 * j)) & 7 for j in range(10)] == list(counts)
+        assert w < 2**30
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_carried_rounds_visit_every_round_once(seed):
+    """Rounds handed out by a counter per staged range; a warp that finds no more rounds of
+    range r takes one round of range r + 1 (if the stager has published it) and counts it
+    after the barriers. Under any interleaving, every round of every range is counted once,
+    and each in its own range."""
+    rng = np.random.default_rng(seed)
+    n_ranges, warps = int(rng.integers(1, 9)), int(rng.integers(1, 17))
+    nrounds = [int(v) for v in rng.integers(0, 40, n_ranges)]
+    counter = [0] * n_ranges
+    counted = []
+    carry = [None] * warps
+    for r in range(n_ranges):
+        published = False
+        active = list(range(warps))
+        pending = {w: carry[w] for w in range(warps)}
+        carry = [None] * warps
+        for w, c in pending.items():   # carried rounds are counted first, in range r
+            if c is not None:
+                assert c[0] == r
+                counted.append(c)
+        while active:
+            w = int(rng.choice(active))
+            if not published and rng.random() < 0.3:
+                published = True   # the stager publishes range r + 1 at some point
+            g = counter[r]
+            counter[r] += 1
+            if g < nrounds[r]:
+                counted.append((r, g))
+                continue
+            active.remove(w)
+            if r + 1 < n_ranges and published:
+                g2 = counter[r + 1]
+                counter[r + 1] += 1
+                if g2 < nrounds[r + 1]:
+                    carry[w] = (r + 1, g2)
+    assert all(c is None for c in carry)
+    assert sorted(counted) == [(r, g) for r in range(n_ranges) for g in range(nrounds[r])]
