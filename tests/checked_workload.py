@@ -1,6 +1,10 @@
 """Searches run under a chosen build of the library (TACO_LIB), for tests/test_gpu_checked.py.
 
-Usage: python tests/checked_workload.py OUT.npz. Runs, on seeded synthetic indexes: the FP32,
+Usage: python tests/checked_workload.py OUT.npz INDEX_FILE. The 1M x 128 index is built and
+saved to INDEX_FILE if the file does not exist, and every run searches the index loaded from
+that file, so that runs under two builds search the same index (the GPU build's
+floating-point atomics make two builds of an index differ in the last bits of the mean, the
+covariance and the centroids). Runs: the FP32,
 BF16 and FP8 forms over an (alpha, beta) grid up to alpha 0.1 / beta 0.01 (the 1M x 128
 workload on 2,000 queries, FP8 shortlists 2k-8k), the cluster fallback (a target larger than
 n: Alg. 5 keeps every level), the codes fallback, a multi-slab index and per-query k; saves
@@ -17,13 +21,16 @@ from paper_2603_24919_gb300 import TacoIndex  # noqa: E402
 from synth import budget_from_alpha, make_workload, target_from_beta  # noqa: E402
 
 
-def main(out_path):
+def main(out_path, index_path):
     torch.cuda.set_device(0)
     res = {}
     # the 1M x 128 workload: the FP8 grid at large alpha / beta, BF16 and FP32 beside it
     w, data, queries = make_workload("sift1m", nq=2000)
-    ix = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=10, seed=1,
-                         keep_bf16=True, keep_fp8=True)
+    if not os.path.exists(index_path):
+        built = TacoIndex.build(data, w.n_subspaces, w.sub_dim, w.sqrt_k, kmeans_iters=10, seed=1)
+        built.save(index_path)
+        built.close()
+    ix = TacoIndex.load(index_path, keep_bf16=True, keep_fp8=True)   # both runs: the same file
     q = torch.from_numpy(queries).cuda()
     n = w.n
     for a, b in [(0.01, 0.001), (0.05, 0.005), (0.1, 0.01), (0.1, 0.001)]:
@@ -55,4 +62,4 @@ def main(out_path):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    main(sys.argv[1], sys.argv[2])

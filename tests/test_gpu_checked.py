@@ -5,8 +5,9 @@ in the index's device status word instead of trapping.
 
 The same searches (tests/checked_workload.py: the FP8 grid up to alpha 0.1 / beta 0.01 on
 the 1M x 128 workload, BF16 and FP32 beside it, the cluster and codes fallbacks, a per-query
-batch) run in two processes, one per build; the checked run must leave the status word at 0
-and return exactly the results of the product build."""
+batch) run in two processes, one per build, on one index (built and saved by the first,
+loaded by the second); the checked run must leave the status word at 0 and return exactly
+the results of the product build."""
 import os
 import subprocess
 import sys
@@ -26,9 +27,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SCRIPT = os.path.join(ROOT, "tests", "checked_workload.py")
 
 
-def _run(lib, out):
+def _run(lib, out, index_file):
     env = dict(os.environ, TACO_LIB=lib)
-    r = subprocess.run([sys.executable, SCRIPT, out], capture_output=True, text=True, env=env,
+    r = subprocess.run([sys.executable, SCRIPT, out, index_file], capture_output=True, text=True, env=env,
                        timeout=1200, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-3000:]
     return dict(np.load(out))
@@ -37,8 +38,9 @@ def _run(lib, out):
 def test_checked_build_flags_nothing_and_changes_nothing(tmp_path):
     plain_lib = build_lib.build()
     checked_lib = build_lib.build(checked=True)
-    plain = _run(plain_lib, str(tmp_path / "plain.npz"))
-    checked = _run(checked_lib, str(tmp_path / "checked.npz"))
+    index_file = str(tmp_path / "sift1m.taco")   # built by the first run, loaded by the second
+    plain = _run(plain_lib, str(tmp_path / "plain.npz"), index_file)
+    checked = _run(checked_lib, str(tmp_path / "checked.npz"), index_file)
     status = {k: int(v[0]) for k, v in checked.items() if k.endswith("_status")}
     assert status and all(v == 0 for v in status.values()), status
     assert set(plain) == set(checked)
