@@ -353,7 +353,7 @@ int build_impl(const float* data, int64_t n, int32_t d, const taco_build_params*
         }
     // Alg. 1 step 4 and Alg. 2 (host, FP64)
     std::vector<double> vecs, vals;
-    jacobi_eigen(d, cov, vecs, vals);
+    symmetric_eigen(d, cov, vecs, vals);
     std::vector<std::vector<int>> buckets;
     eigensystem_allocation(vals, p->n_subspaces, p->sub_dim, buckets);
     std::vector<int> desc(d);

@@ -76,8 +76,8 @@ constexpr int kStatusCluster = 8;   // cluster kernel and the merge of its lists
 cudaError_t ensure_dynamic_smem(const void* func, size_t bytes);
 
 // Host FP64 linear algebra (build side).
-void jacobi_eigen(int d, std::vector<double>& a, std::vector<double>& vecs,
-                  std::vector<double>& vals);
+void symmetric_eigen(int d, std::vector<double>& a, std::vector<double>& vecs,
+                     std::vector<double>& vals);
 void eigensystem_allocation(const std::vector<double>& lam, int n_subspaces, int sub_dim,
                             std::vector<std::vector<int>>& buckets);
 
