@@ -211,12 +211,13 @@ struct NextBatch {
     int index;   // -1: no next range
 };
 
-// Walk one staged batch: rounds of WU windows handed to warps by a shared counter (*s_round,
-// zero on entry, or already counting the rounds that warps carried into this batch), so warps
-// that drew short work take more. Each warp keeps two rounds in flight: it issues the loads of
-// its next round before it counts the current one (the first current round is the one R
-// carries from the previous range, if any). A warp that finds no more rounds takes, if the
-// next range is staged, one round of it into R (issued, not counted). Warp-level; no barrier.
+// Walk one staged batch: first the round R carries from the previous range (if any), then
+// rounds of WU windows handed to warps by a shared counter (*s_round, zero on entry, or
+// already counting the rounds that warps carried into this batch), so warps that drew short
+// work take more. A warp claims its next round only when it has counted the current one
+// (claiming ahead fixes the last rounds' owners early and lengthens the range's tail). A warp
+// that finds no more rounds takes, if the next range is staged, one round of it into R
+// (issued, not counted). Warp-level; no barrier.
 template <int NW, int WU, int CB>
 __device__ __forceinline__ void walk_chunks(WalkRound<WU>& R, const uint4* __restrict__ ids4, uint32_t last_chunk,
                                             uint32_t lo, uint32_t rlen, uint32_t total, uint32_t nr,
@@ -232,17 +233,12 @@ __device__ __forceinline__ void walk_chunks(WalkRound<WU>& R, const uint4* __res
         if (lane == 0) g = atomicAdd(counter, 1u);
         return __shfl_sync(kFull, g, 0);   // warp-uniform
     };
-    if (!R.has) {
+    if (R.has) count_round<WU, CB>(R, lo, rlen, cnt, out, cap, ge, s_app, lane, status, counter_words);
+    for (;;) {
         const uint32_t g = claim(s_round);
-        if (g < nrounds) issue_round<WU>(R, ids4, last_chunk, g, total, nr, cpre, rbase, pol, lane, status);
-    }
-    while (R.has) {
-        WalkRound<WU> N;
-        N.has = false;
-        const uint32_t g = claim(s_round);
-        if (g < nrounds) issue_round<WU>(N, ids4, last_chunk, g, total, nr, cpre, rbase, pol, lane, status);
+        if (g >= nrounds) break;
+        issue_round<WU>(R, ids4, last_chunk, g, total, nr, cpre, rbase, pol, lane, status);
         count_round<WU, CB>(R, lo, rlen, cnt, out, cap, ge, s_app, lane, status, counter_words);
-        R = N;
     }
     if (nx.index < 0) return;
     // the next range's first rounds, where it is staged: issued now, counted after the barriers

@@ -229,9 +229,15 @@ __device__ __forceinline__ uint32_t shr_clamped(uint32_t a, uint32_t b) {
     return r;
 }
 
+// FP8 query pairs: float4 slot of dimensions 2j', 2j' + 1 (j' = 0..7) of 16-dimension chunk
+// f. The 8 slots of a chunk are permuted by f mod 8, so that lanes reading the same j' of
+// different chunks (the G lanes of a row) hit different shared-memory banks.
+__device__ __forceinline__ int fp8_query_slot(int f, int jp) { return (f << 3) | (jp ^ (f & 7)); }
+
 // Squared distance contribution of one 16-byte row chunk f. FP32 / BF16: qv is the query
-// (d_pad floats). FP8: qv holds (q'_c / scale_c, scale_c^2) pairs of the transformed query,
-// so the chunk adds sum_c scale_c^2 (q'_c / scale_c - x8_c)^2 = sum_c (q'_c - scale_c x8_c)^2.
+// (d_pad floats). FP8: qv holds (q'_c / scale_c, scale_c^2) pairs of the transformed query
+// (slots permuted by fp8_query_slot), so the chunk adds
+// sum_c scale_c^2 (q'_c / scale_c - x8_c)^2 = sum_c (q'_c - scale_c x8_c)^2.
 template <int RK>
 __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, float acc) {
     if constexpr (RK == kRowF32) {
@@ -250,7 +256,7 @@ __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, f
         acc = sq4(make_float4(a0.x, a0.y, a1.x, a1.y), q0, acc);
         return sq4(make_float4(a2.x, a2.y, a3.x, a3.y), q1, acc);
     } else {
-        const float4* qw = reinterpret_cast<const float4*>(qv) + 8 * f;   // 2 dims per float4
+        const float4* qw = reinterpret_cast<const float4*>(qv);   // 2 dims per float4
         const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -259,7 +265,7 @@ __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, f
                 const __half2 x2(__nv_cvt_fp8x2_to_halfraw2(
                     __nv_fp8x2_storage_t((w4[u] >> (16 * h)) & 0xffffu), __NV_E4M3));
                 const float2 x = __half22float2(x2);
-                const float4 p = qw[2 * u + h];   // (qs_a, w_a, qs_b, w_b)
+                const float4 p = qw[fp8_query_slot(f, 2 * u + h)];   // (qs_a, w_a, qs_b, w_b)
                 const float da = p.x - x.x, db = p.z - x.y;
                 acc = fmaf(p.y * da, da, acc);
                 acc = fmaf(p.w * db, db, acc);

@@ -996,8 +996,9 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
         const int R = L.kk_max <= 32 ? 1 : (L.kk_max <= 128 ? 4 : 16);
         const int G = pick_g(ix->d_pad / (bf16 ? 8 : 4));
         const int rk = fp8 ? 2 : (bf16 ? 1 : 0);
-        const int Gs = ix->tp_lanes[rk] ? ix->tp_lanes[rk]                    // lanes per row of
-                                        : (fp8 ? pick_g(ix->dp8 / 16) : G);   // the select pass
+        // lanes per row of the select pass (tuned, else from the chunks a row holds)
+        const int Gs = ix->tp_lanes[rk] ? ix->tp_lanes[rk]
+                                        : (fp8 ? pick_g(((ix->fp8_space ? ix->d : ix->Dp) + 15) / 16) : G);
         const bool two_pass = L.unit_ge != nullptr;
         if (two_pass) {
             // the two-pass range layout (tuned): tp_spc slabs of counters per range

@@ -232,7 +232,8 @@ select_rerank_kernel(const RerankParams P) {
     const int Ns = P.Ns, nr = P.n_ranges, kk = P.kk;
     const int gid = lane / G, gl = lane % G;
     constexpr bool kFP8 = RK == kRowFP8;
-    const int nch = (kFP8 ? P.dp8 : P.d_pad) / RowChunk<RK>::kElems;
+    // 16-byte chunks of a row that hold coordinates (FP8 rows are padded to whole lines)
+    const int nch = kFP8 ? ((P.fp8_space ? P.d : P.Dp) + 15) / 16 : P.d_pad / RowChunk<RK>::kElems;
     const size_t row_bytes = kFP8 ? size_t(P.dp8) : size_t(P.d_pad) * (RK == kRowBF16 ? 2 : 4);
     const unsigned char* rows = RK == kRowBF16 ? reinterpret_cast<const unsigned char*>(P.data_bf16)
                                 : kFP8         ? P.data_fp8
@@ -249,13 +250,16 @@ select_rerank_kernel(const RerankParams P) {
         if constexpr (kFP8) {
             // (x_c / scale_c, scale_c^2) of the query in the FP8 rows' space: the transformed
             // query q' (zero past N_s * s) or the centred query q - o_bar (zero past d)
+            // (the float4 slots of 16-dimension chunk f are permuted by f mod 8, so that the
+            // lanes of a row reading different chunks hit different banks: fp8_query_slot)
             const int cols = P.fp8_space ? P.d : P.Dp;
             for (int j = tid; j < P.dp8; j += kSrThreads) {
                 const float sc = P.fp8_scale[j];
                 float x = 0.f;
                 if (j < cols) x = P.fp8_space ? P.queries[q * P.d + j] - P.obar[j] : P.qt[q * P.Dp + j];
-                qf[2 * j] = j < cols ? x * P.fp8_scale[P.dp8 + j] : 0.f;
-                qf[2 * j + 1] = j < cols ? sc * sc : 0.f;
+                float* slot = qf + 4 * fp8_query_slot(j >> 4, (j >> 1) & 7) + 2 * (j & 1);
+                slot[0] = j < cols ? x * P.fp8_scale[P.dp8 + j] : 0.f;
+                slot[1] = j < cols ? sc * sc : 0.f;
             }
         }
         if (tid <= TACO_MAX_SUBSPACES + 1) s_gs[tid] = 0u;
