@@ -37,19 +37,6 @@ __device__ __forceinline__ uint4 ldg_keep_u4(const uint4* p, uint64_t pol) {
     return r;
 }
 
-// Publication of a staged batch between warps of a CTA: release store / acquire load of a
-// shared-memory flag.
-__device__ __forceinline__ void st_release_cta(int* p, int v) {
-    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_acquire_cta(const int* p) {
-    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-    int v;
-    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-
 // Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address into L2;
 // no completion to wait for.
 __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
@@ -97,14 +84,11 @@ __host__ __device__ __forceinline__ int counter_words_for(int64_t ids, int cb) {
     return int((ids + per - 1) / per);
 }
 
-// One walk round's loads, held in registers from the issue to the count (possibly across the
-// barriers between two ranges: a warp that finds no more rounds of range r takes the first
-// round it can of range r + 1, staged already, and issues its loads before it waits).
+// One walk round's loads, held in registers from the issue to the count.
 template <int WU>
 struct WalkRound {
     uint4 v[WU];
     uint32_t live;   // bit u: this lane's chunk of window u is inside the batch
-    bool has;        // warp-uniform
 };
 
 // Issue the loads of round g (WU windows of 32 chunks) of a staged batch of chunk runs
@@ -137,7 +121,6 @@ __device__ __forceinline__ void issue_round(WalkRound<WU>& R, const uint4* __res
         R.v[u] = ldg_keep_u4(ids4 + x, pol);
         R.live |= (in ? 1u : 0u) << u;
     }
-    R.has = true;
 }
 
 // Count a round whose loads are in R against the unit's range [lo, lo + rlen): every id of a
@@ -196,58 +179,32 @@ __device__ __forceinline__ void count_round(WalkRound<WU>& R, uint32_t lo, uint3
                     ++pos;
                 }
     }
-    R.has = false;
 }
 
-// The next range of a work item, for the walk's carried round: its staged batch (valid once
-// *ready == index, which the stager publishes) and its round counter.
-struct NextBatch {
-    const uint32_t* cpre;
-    const uint32_t* rbase;
-    const uint32_t* total;
-    const uint32_t* nr;
-    uint32_t* s_round;
-    const int* ready;
-    int index;   // -1: no next range
-};
-
-// Walk one staged batch: first the round R carries from the previous range (if any), then
-// rounds of WU windows handed to warps by a shared counter (*s_round, zero on entry, or
-// already counting the rounds that warps carried into this batch), so warps that drew short
-// work take more. A warp claims its next round only when it has counted the current one
-// (claiming ahead fixes the last rounds' owners early and lengthens the range's tail). A warp
-// that finds no more rounds takes, if the next range is staged, one round of it into R
-// (issued, not counted). Warp-level; no barrier.
+// Walk one staged batch: rounds of WU windows handed to warps by a shared counter (*s_round,
+// zero on entry), so warps that drew short work take more; a warp claims its next round only
+// when it has counted the current one. (Measured alternatives that were slower on the
+// 10M x 96 workload: claiming the next round before counting the current one, which fixes
+// the owners of a range's last rounds early and lengthens its tail, and issuing the next
+// range's first round before the range barriers.) Warp-level; no barrier.
 template <int NW, int WU, int CB>
-__device__ __forceinline__ void walk_chunks(WalkRound<WU>& R, const uint4* __restrict__ ids4, uint32_t last_chunk,
-                                            uint32_t lo, uint32_t rlen, uint32_t total, uint32_t nr,
-                                            uint32_t* cnt, uint32_t* out, uint32_t cap, uint32_t* ge,
-                                            uint32_t* s_app, uint32_t* s_round, const uint32_t* cpre,
-                                            const uint32_t* rbase, const NextBatch& nx, uint64_t pol, int lane,
-                                            int* status, uint32_t counter_words) {
+__device__ __forceinline__ void walk_chunks(const uint4* __restrict__ ids4, uint32_t last_chunk, uint32_t lo,
+                                            uint32_t rlen, uint32_t total, uint32_t nr, uint32_t* cnt,
+                                            uint32_t* out, uint32_t cap, uint32_t* ge, uint32_t* s_app,
+                                            uint32_t* s_round, const uint32_t* cpre, const uint32_t* rbase,
+                                            uint64_t pol, int lane, int* status, uint32_t counter_words) {
     static_assert(WU >= 1 && WU <= 8, "one lane finds the run of each window; 4 WU append bits a lane");
     constexpr uint32_t kRound = 32u * WU;
     const uint32_t nrounds = (total + kRound - 1) / kRound;
-    auto claim = [&](uint32_t* counter) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(counter, 1u);
-        return __shfl_sync(kFull, g, 0);   // warp-uniform
-    };
-    if (R.has) count_round<WU, CB>(R, lo, rlen, cnt, out, cap, ge, s_app, lane, status, counter_words);
+    WalkRound<WU> R;
     for (;;) {
-        const uint32_t g = claim(s_round);
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(s_round, 1u);
+        g = __shfl_sync(kFull, g, 0);   // warp-uniform
         if (g >= nrounds) break;
         issue_round<WU>(R, ids4, last_chunk, g, total, nr, cpre, rbase, pol, lane, status);
         count_round<WU, CB>(R, lo, rlen, cnt, out, cap, ge, s_app, lane, status, counter_words);
     }
-    if (nx.index < 0) return;
-    // the next range's first rounds, where it is staged: issued now, counted after the barriers
-    const bool ready = ld_acquire_cta(nx.ready) == nx.index;
-    if (!__all_sync(kFull, ready)) return;
-    const uint32_t ntot = *nx.total;
-    const uint32_t g = claim(nx.s_round);
-    if (g < (ntot + kRound - 1) / kRound)
-        issue_round<WU>(R, ids4, last_chunk, g, ntot, *nx.nr, nx.cpre, nx.rbase, pol, lane, status);
 }
 
 // One warp stages the chunk runs of the ncell staged cells of one range (their id-position
@@ -323,8 +280,7 @@ count_lists_kernel(const RerankParams P) {
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * NW];
     __shared__ uint32_t s_app, s_ev;
-    __shared__ uint32_t s_rnd[2];   // walk round counters of the two staged ranges
-    __shared__ int s_ready;         // the range whose staging the stager has published
+    __shared__ uint32_t s_round;    // walk round counter of the current range
     __shared__ uint32_t s_tot2[2], s_nr2[2], s_ev2[2];   // staged batch of each buffer
     __shared__ int64_t s_next;
     const int Ns = P.Ns, K = P.K;
@@ -338,7 +294,7 @@ count_lists_kernel(const RerankParams P) {
     if (tid < 16) ge[tid] = 0u;
     if (tid == 0) {
         s_app = 0u;
-        s_rnd[0] = s_rnd[1] = 0u;
+        s_round = 0u;
         s_ev = 0u;
     }
     // stager: the split bounds of every staged cell for range r into pairs[slot] (asynchronous)
@@ -369,11 +325,7 @@ count_lists_kernel(const RerankParams P) {
             s_nr2[buf] = st.y;
             s_ev2[buf] = ev;
         }
-        __threadfence_block();
-        __syncwarp();
     };
-    WalkRound<WU> R;   // a round carried into the next range (see walk_chunks)
-    R.has = false;
     // work item: ranges [rb, re) of query q (all its ranges unless a small batch splits them
     // into range_parts runs so that more CTAs work on it)
     const int parts = P.range_parts;
@@ -385,7 +337,6 @@ count_lists_kernel(const RerankParams P) {
         const int re = min(P.n_ranges, rb + per_part);
         __syncthreads();   // the previous item is finished with the shared state
         if (warp == 0) load_cell_prefix(P, q, s_pre, lane);
-        if (tid == 0) s_ready = -1;
         __syncthreads();
         const int total_cells = s_pre[Ns];
         const bool staged = total_cells <= kCellBatch;   // one batch: cells kept for every range
@@ -421,23 +372,19 @@ count_lists_kernel(const RerankParams P) {
             const uint32_t rlen = uint32_t(hi - lo);
             uint32_t* out = P.arena + size_t(u) * P.arena_per_unit;
             (void)TACO_CHECK(P.status, (size_t(u) + 1) * P.arena_per_unit <= P.arena_words, kStatusCount);
-            // (the counters are clear, ge / s_app zero, range r staged, its round counter zero
-            // or counting the rounds that warps carried from range r - 1)
+            // (the counters are clear, ge / s_app / s_round zero, range r staged)
             if (staged) {
                 const int buf = (r - rb) & 1;   // staging buffer and bounds slot of range r
                 if (warp == kStager && r + 1 < re) {
                     cp_async_wait_all();   // the bounds of range r + 1 (slot buf ^ 1)
                     __syncwarp();
                     stage_range(total_cells, buf ^ 1, buf ^ 1, true);
-                    if (lane == 0) st_release_cta(&s_ready, r + 1);   // walkers may take its rounds
                     if (r + 2 < re) load_bounds(total_cells, r + 2, buf);   // slot of range r: staged
                 }
-                const NextBatch nx{cpre + (buf ^ 1) * kPre, rbase + (buf ^ 1) * kCellBatch, &s_tot2[buf ^ 1],
-                                   &s_nr2[buf ^ 1], &s_rnd[buf ^ 1], &s_ready, r + 1 < re ? r + 1 : -1};
                 const uint32_t tot = s_tot2[buf];
-                if (tot) walk_chunks<NW, WU, CB>(R, ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, out, cap,
-                                                 ge, &s_app, &s_rnd[buf], cpre + buf * kPre, rbase + buf * kCellBatch,
-                                                 nx, pol_keep, lane, P.status, uint32_t(P.counter_words));
+                if (tot) walk_chunks<NW, WU, CB>(ids4, last_chunk, uint32_t(lo), rlen, tot, s_nr2[buf], cnt, out, cap, ge,
+                                                 &s_app, &s_round, cpre + buf * kPre, rbase + buf * kCellBatch, pol_keep,
+                                                 lane, P.status, uint32_t(P.counter_words));
             } else {
                 // batches of one cell per thread, at most kCellBatch (the staging arrays)
                 constexpr int kBatch = NW * 32 < kCellBatch ? NW * 32 : kCellBatch;
@@ -457,12 +404,11 @@ count_lists_kernel(const RerankParams P) {
                     chunk_run(b, e, start, len);
                     const uint32_t ev = __reduce_add_sync(kFull, e - b);
                     if (lane == 0 && ev) atomicAdd(&s_ev, ev);
-                    if (tid == 0) s_rnd[0] = 0u;   // read after the staging's barriers
+                    if (tid == 0) s_round = 0u;   // read after the staging's barriers
                     const uint2 st = stage_runs<NW>(start, len, rbase, cpre, s_tmp, tid, lane, warp);
-                    const NextBatch none{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1};
-                    if (st.x) walk_chunks<NW, WU, CB>(R, ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, out, cap,
-                                                      ge, &s_app, &s_rnd[0], cpre, rbase, none, pol_keep, lane,
-                                                      P.status, uint32_t(P.counter_words));
+                    if (st.x) walk_chunks<NW, WU, CB>(ids4, last_chunk, uint32_t(lo), rlen, st.x, st.y, cnt, out, cap, ge,
+                                                      &s_app, &s_round, cpre, rbase, pol_keep, lane, P.status,
+                                                      uint32_t(P.counter_words));
                 }
             }
             __syncthreads();   // the range's counters, entries and level counts are final
@@ -488,7 +434,7 @@ count_lists_kernel(const RerankParams P) {
                 }
                 if (lane == 0) {
                     s_app = 0u;
-                    s_rnd[staged ? (r - rb) & 1 : 0] = 0u;   // range r's counter (the next one's may be in use)
+                    s_round = 0u;
                     s_ev = 0u;
                 }
             }

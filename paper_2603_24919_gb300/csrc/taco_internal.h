@@ -106,6 +106,7 @@ struct taco_index {
     int cluster = 1, slabs_per_cta = 1;   // layout of the single-pass cluster kernel
     // Tuned launch choices (taco_autotune; defaults from configure_search):
     int tp_spc = 1, tp_ranges = 1;        // slabs per id range of the two-pass counting, ranges
+    int tp_spc0 = 1, tp_ranges0 = 1;      // the index's default two-pass layout (configure_search)
     int tp_lanes[3] = {0, 0, 0};          // lanes per row of the re-rank per row kind (0: auto)
     int tp_walk = -1;                     // probe by row-merge walk: -1 auto, 0 never, 1 when it fits
     int tp_count_warps = 16;              // warps per CTA of the counting pass (8, 16 or 32)

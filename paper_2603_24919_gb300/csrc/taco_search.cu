@@ -787,16 +787,16 @@ int configure_search(taco_index* ix) {
         // fallback
         ix->cluster = 0;
         ix->slabs_per_cta = 0;
-        ix->tp_spc = std::min(ix->Ns <= 7 ? 15 : 12, ix->n_slabs);
-        ix->tp_ranges = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
+        ix->tp_spc = ix->tp_spc0 = std::min(ix->Ns <= 7 ? 15 : 12, ix->n_slabs);
+        ix->tp_ranges = ix->tp_ranges0 = (ix->n_slabs + ix->tp_spc - 1) / ix->tp_spc;
         return TACO_OK;
     }
     if (cluster < 1) cluster = 1;
     if (spc > ix->n_slabs) spc = ix->n_slabs;
     ix->cluster = cluster;
     ix->slabs_per_cta = spc;
-    ix->tp_spc = spc;   // the two-pass counting starts from the cluster layout
-    ix->tp_ranges = cluster;
+    ix->tp_spc = ix->tp_spc0 = spc;   // the two-pass counting starts from the cluster layout
+    ix->tp_ranges = ix->tp_ranges0 = cluster;
     return TACO_OK;
 }
 

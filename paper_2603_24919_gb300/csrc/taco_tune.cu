@@ -55,7 +55,7 @@ extern "C" int taco_autotune(taco_index* ix, const float* queries, int64_t nq, c
                              int32_t reps, void* stream, taco_tune_result* out) {
     if (!ix || !params || !out) return fail(TACO_EINVAL, "null argument");
     const int rk = params->precision == TACO_PREC_FP8 ? 2 : (params->precision == TACO_PREC_BF16 ? 1 : 0);
-    const Choice defaults{ix->slabs_per_cta, ix->cluster, 0, -1, 16, 4};
+    const Choice defaults{ix->tp_spc0, ix->tp_ranges0, 0, -1, 16, 4};
     if (reps <= 0) {   // back to the defaults
         apply(ix, defaults, rk);
         for (int& l : ix->tp_lanes) l = 0;

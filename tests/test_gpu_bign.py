@@ -84,6 +84,10 @@ def test_big_index_parity(big):
     assert info["n_slabs"] > 16 * 12 and info["cluster_size"] == 0
     b, t = budget_from_alpha(0.001, oix.n), target_from_beta(0.0005, oix.n)
     _check(ix, oix, data, queries, 10, b, t)
+    # the autotuner's reset restores the index's own two-pass layout (no cluster layout here)
+    dflt = ix.autotune(None, 10, b, t, reps=0)
+    assert dflt["slabs_per_range"] == 15 and dflt["slabs_per_range"] * dflt["n_ranges"] >= info["n_slabs"]
+    _check(ix, oix, data, queries, 10, b, t)
 
 
 def test_big_index_refuses_cluster_paths(big):

@@ -189,7 +189,7 @@ def test_chunk_walk_counts_exactly_the_probed_ids_of_the_range(wu, n_cells, n):
         assert ge1 == len(got) - len(entries)
 
 
-# ------------------------------------------------------- counter packing and carried rounds
+# ------------------------------------------------------------------------ counter packing
 def test_three_bit_counter_word_and_shift():
     """3-bit counters (10 a word): word(x) = high 32 bits of x * ceil(2^32 / 10) equals
     x // 10 for every id offset of a 15-slab range (and far beyond), shift = 3 (x mod 10) stays
@@ -212,43 +212,3 @@ def test_three_bit_counter_word_and_shift():
                 assert (old >> (3 * j)) & 7 == ((w >> (3 * j)) & 7) - 1
         assert [(w >> (3 * j)) & 7 for j in range(10)] == list(counts)
         assert w < 2**30
-
-
-@pytest.mark.parametrize("seed", range(6))
-def test_carried_rounds_visit_every_round_once(seed):
-    """Rounds handed out by a counter per staged range; a warp that finds no more rounds of
-    range r takes one round of range r + 1 (if the stager has published it) and counts it
-    after the barriers. Under any interleaving, every round of every range is counted once,
-    and each in its own range."""
-    rng = np.random.default_rng(seed)
-    n_ranges, warps = int(rng.integers(1, 9)), int(rng.integers(1, 17))
-    nrounds = [int(v) for v in rng.integers(0, 40, n_ranges)]
-    counter = [0] * n_ranges
-    counted = []
-    carry = [None] * warps
-    for r in range(n_ranges):
-        published = False
-        active = list(range(warps))
-        pending = {w: carry[w] for w in range(warps)}
-        carry = [None] * warps
-        for w, c in pending.items():   # carried rounds are counted first, in range r
-            if c is not None:
-                assert c[0] == r
-                counted.append(c)
-        while active:
-            w = int(rng.choice(active))
-            if not published and rng.random() < 0.3:
-                published = True   # the stager publishes range r + 1 at some point
-            g = counter[r]
-            counter[r] += 1
-            if g < nrounds[r]:
-                counted.append((r, g))
-                continue
-            active.remove(w)
-            if r + 1 < n_ranges and published:
-                g2 = counter[r + 1]
-                counter[r + 1] += 1
-                if g2 < nrounds[r + 1]:
-                    carry[w] = (r + 1, g2)
-    assert all(c is None for c in carry)
-    assert sorted(counted) == [(r, g) for r in range(n_ranges) for g in range(nrounds[r])]
