@@ -53,7 +53,7 @@ def test_autotune_keeps_parity(multislab, precision):
     before_ids, _ = ix.search(q, 10, b, t, precision=precision, shortlist_mult=2)
     r = ix.autotune(q, 10, b, t, precision=precision, shortlist_mult=2, reps=2)
     assert r["trials"] >= 5 and 0 < r["ms_after"] <= r["ms_before"]
-    assert r["slabs_per_range"] in (1, 2, 4, 5, 8) and r["n_ranges"] * r["slabs_per_range"] >= 10
+    assert r["slabs_per_range"] in (1, 2, 4, 5, 8, 10) and r["n_ranges"] * r["slabs_per_range"] >= 10
     assert r["lanes_per_row"] in (0, 4, 8, 16, 32) and r["probe_walk"] in (-1, 0)
     assert r["count_warps"] in (8, 16, 32) and r["walk_unroll"] in (2, 4, 8)
     _parity(ix, oix, data, queries, 10, b, t)
