@@ -246,7 +246,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_limiter(kernel, workload="sift1m"):
+def ncu_limiter(kernel, workload=WORKLOAD):
     """The ncu reading of what bounds `kernel` from the committed summary, if it was taken on
     the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
@@ -259,7 +259,7 @@ def ncu_limiter(kernel, workload="sift1m"):
     return {k: v for k, v in lim.items() if k != "source_hash"}
 
 
-def ncu_traffic(kernel, precision, workload="sift1m"):
+def ncu_traffic(kernel, precision, workload=WORKLOAD):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
     the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")

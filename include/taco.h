@@ -239,6 +239,43 @@ int taco_search_batch_noalloc(const taco_index* index, const float* queries, int
                               int64_t* out_ids, float* out_dists, void* stream);
 
 /*
+ * Id-range shards (Alg. 6 split over the points; Def. 6 and Alg. 5 need one exchange).
+ * Shard s of S holds id ranges [s R / S, (s + 1) R / S) of the index's R two-pass ranges
+ * (taco_index_info's layout; 1 <= S <= R). Every shard probes the same cells (the global cell
+ * sizes), counts the collisions of its own ids, and reports its level counts; Alg. 5 then
+ * runs on the counts summed over all shards, so every shard takes the candidates the
+ * one-index search would take among its ids, and the k nearest of the shards' results by
+ * (distance, id) are the one-index result (FP32 rows exactly; BF16 / FP8 rows re-rank each
+ * shard's own shortlist, so the merged shortlist holds S times the candidates). Queries the
+ * threshold takes below level 2, or whose entries overflow a shard's arena slot, are answered
+ * by the codes fallback over the shard's ids. In this library the shards run in one process
+ * on the index's device; the caller sums the counts and merges the results (on a multi-GPU
+ * node: an all-reduce of [nq][N_s + 1] int64 and an all-gather of [nq][k] results).
+ *
+ * taco_shard_count -- the transform, probe and counting of `shard` for a batch (queries
+ *   [nq][d] host or device, 1 <= nq <= 16384; per_query or defaults as in taco_search_batch;
+ *   k_stride: the row length of the results the select will write). Writes the shard's level
+ *   counts hist [nq][N_s + 1] int64 (host or device): hist[q][0] = the shard's points,
+ *   hist[q][j] = its ids with SC >= j. Returns a handle that owns the batch's device state
+ *   (queries, probed cells, counts, entries) until taco_shard_free. Synchronises `stream`
+ *   when hist or per_query is on the host. TACO_EINVAL on bad arguments (shard, n_shards,
+ *   nq, parameters), TACO_ENOMEM / CUDA errors on allocation. The index's layout must not
+ *   change (taco_autotune, taco_index_set_option) between the count and the select.
+ * taco_shard_select -- Alg. 5 on global_hist [nq][N_s + 1] int64 (host or device: the sum of
+ *   every shard's hist), then the shard's candidates, re-rank and k nearest: out_ids [nq]
+ *   [k_stride] int64 and out_dists float (host or device; -1 / +inf past the shard's
+ *   candidates). Synchronises `stream`.
+ * taco_shard_free -- releases a handle (NULL is a no-op).
+ */
+typedef struct taco_shard_search taco_shard_search;
+int taco_shard_count(const taco_index* index, int32_t shard, int32_t n_shards, const float* queries, int64_t nq,
+                     const taco_query_params* per_query, const taco_query_params* defaults, int32_t k_stride,
+                     int64_t* hist, void* stream, taco_shard_search** out);
+int taco_shard_select(taco_shard_search* shard, const int64_t* global_hist, int64_t* out_ids, float* out_dists,
+                      void* stream);
+int taco_shard_free(taco_shard_search* shard);
+
+/*
  * taco_centroid_distances -- the query x centroid distance block of Alg. 6 steps 4-5 alone:
  *   qt     device, [nq][N_s*s] float32 transformed queries B^T (q - o_bar).
  *   out    device, [nq][N_s][2][sqrt_k] float32: out[q][i][h][c] = |q'_{i,h} - C_{i,h}[c]|^2,

@@ -46,6 +46,7 @@ def _units():
         ("taco_server.o", "taco_server.cu", []),
         ("taco_tc.o", "taco_tc.cu", []),
         ("taco_tune.o", "taco_tune.cu", []),
+        ("taco_shard.o", "taco_shard.cu", []),
     ]
     for bf16 in (0, 1, 2):
         for r in (1, 4, 16):

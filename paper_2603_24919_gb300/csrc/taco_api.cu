@@ -16,6 +16,20 @@
 
 using namespace taco;
 
+int taco::ensure_device_codes(taco_index* ix) {
+    if (ix->d_codes) return TACO_OK;
+    uint16_t* d = nullptr;
+    TACO_CUDA(cudaMalloc(&d, ix->codes.size() * sizeof(uint16_t)));
+    const cudaError_t e = cudaMemcpy(d, ix->codes.data(), ix->codes.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cell codes upload", __FILE__, __LINE__);
+    }
+    ix->d_codes = d;
+    ix->device_bytes += int64_t(ix->codes.size() * sizeof(uint16_t));
+    return TACO_OK;
+}
+
 namespace {
 
 template <typename T>
@@ -104,14 +118,9 @@ void set_geometry(taco_index* ix, int64_t n, int d, int Ns, int s, int sk) {
     ix->h1 = s / 2;
 }
 
-// Everything downstream of the parts: cell lists (ids ascending per cell), slab split
-// table, device copies of transform and centroids, optional BF16 rows.
 // Device copy of the cell codes, for the codes fallback of flagged queries.
 int enable_codes_fallback(taco_index* ix) {
-    if (!ix->d_codes) {
-        TRY(dev_alloc(&ix->d_codes, ix->codes.size(), &ix->device_bytes));
-        TACO_CUDA(cudaMemcpy(ix->d_codes, ix->codes.data(), ix->codes.size() * 2, cudaMemcpyHostToDevice));
-    }
+    TRY(taco::ensure_device_codes(ix));
     ix->codes_fallback = true;
     return TACO_OK;
 }

@@ -229,8 +229,18 @@ struct SearchLaunch {
     int centroid_tc;           // centroid distances from a tcgen05 block into hd: 0 none,
                                // 1 BF16 operands, 2 E4M3 operands
     float* hd;                 // device [nq][Ns][2][sk] (centroid_tc != 0)
+    // id-range shards (taco_shard_*): phase 0 runs the whole search; phase 1 the transform,
+    // probe and counting of the ranges [shard_r0, shard_r1) and their level counts into
+    // shard_hist [nq][Ns + 1]; phase 2 Alg. 5 on the all-shard counts ghist [nq][Ns + 1], the
+    // select / re-rank of the shard's ranges and the codes fallback over the shard's ids
+    int phase;
+    int shard_r0, shard_r1;    // shard_r1 <= 0: all ranges
+    int64_t* shard_hist;
+    const int64_t* ghist;
 };
 int run_search_chunk(const SearchLaunch& L, cudaStream_t st);
+cudaError_t launch_shard_hist(const uint32_t* unit_ge, int64_t nq, int nr, int r0, int r1, int Ns, int64_t points,
+                              int64_t* hist, cudaStream_t st);
 
 // Byte offsets of one launch group's device workspace (each 256-byte aligned).
 struct SearchLayout {
@@ -252,5 +262,7 @@ QueryParamsDev query_params_dev(const taco_query_params& q);
 int prof_begin(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t* b, cudaEvent_t* e);
 int prof_end(taco_index* ix, int slot, cudaStream_t st, cudaEvent_t b, cudaEvent_t e);
 int configure_search(taco_index* ix);
+// Device copy of the cell codes (the codes fallback), made once.
+int ensure_device_codes(taco_index* ix);
 
 }  // namespace taco

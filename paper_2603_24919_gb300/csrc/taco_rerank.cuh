@@ -78,6 +78,8 @@ struct RerankParams {
     // two-pass form: per (query, id range) unit
     int n_ranges;           // id ranges per query
     int range_parts;        // count_lists_kernel: work items per query, each a run of its ranges
+    int shard_r0, shard_r1; // the ranges this launch counts and selects from (all: 0, n_ranges)
+    const int64_t* ghist;   // [nq][N_s + 1] level counts summed over all shards, or null
     uint32_t arena_per_unit;  // arena entries reserved per unit
     uint32_t* unit_ge;      // [nq][n_ranges][16] ids with SC >= j, j = 1..N_s
     uint32_t* unit_off;     // [nq][n_ranges] start of the unit's entries in the arena

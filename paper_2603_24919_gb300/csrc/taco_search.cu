@@ -748,6 +748,30 @@ final_merge_kernel(const float* __restrict__ lists_d, const uint32_t* __restrict
     }
 }
 
+// Level counts of one id-range shard: hist[q][0] = the shard's points, hist[q][j] = its ids
+// with SC >= j (the sum of its units' counts), j = 1..N_s. One thread per (query, level).
+__global__ void shard_hist_kernel(const uint32_t* __restrict__ unit_ge, int64_t nq, int nr, int r0, int r1,
+                                  int Ns, int64_t points, int64_t* __restrict__ hist) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= nq * (Ns + 1)) return;
+    const int64_t q = t / (Ns + 1);
+    const int j = int(t - q * (Ns + 1));
+    int64_t v = points;
+    if (j > 0) {
+        v = 0;
+        for (int r = r0; r < r1; ++r) v += unit_ge[(q * nr + r) * 16 + j];
+    }
+    hist[t] = v;
+}
+
+cudaError_t launch_shard_hist(const uint32_t* unit_ge, int64_t nq, int nr, int r0, int r1, int Ns, int64_t points,
+                              int64_t* hist, cudaStream_t st) {
+    const int64_t n = nq * (Ns + 1);
+    if (n == 0) return cudaSuccess;
+    shard_hist_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(unit_ge, nq, nr, r0, r1, Ns, points, hist);
+    return cudaGetLastError();
+}
+
 static int next_pow2(int x) {
     int p = 1;
     while (p < x) p <<= 1;
@@ -864,6 +888,8 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
     taco_index* pix = L.skip_profile ? nullptr : ix;   // profiling target (none: no events)
     cudaEvent_t pb, pe;
     const int K = ix->K;
+    // (phase 2 of a shard: the transform, probe and counts of phase 1 are in the workspace)
+    if (L.phase != 2) {
     // 1. transform (Alg. 6 step 1)
     if (int rc = prof_begin(pix, 0, st, &pb, &pe)) return rc;
     TACO_CUDA(launch_project(L.queries, L.nq, ix->d, ix->d, ix->d_obar, ix->d_B, ix->Dp, L.qt, st));
@@ -942,6 +968,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                                       size_t(L.nq) * ix->Ns * sizeof(int64_t),
                                       cudaMemcpyDeviceToDevice, st));
     }
+    }   // phase != 2
     // 3. count, select, re-rank (Alg. 6 steps 7-9, Alg. 5)
     {
         // FP8 rows serve the select / re-rank pass; queries on the fallback cluster path
@@ -1016,10 +1043,13 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.qflag = L.qflag;
             P.qlast = L.qlast;
             P.work = L.qflag + L.nq;   // the two query counters follow the flags
-            TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq + 2) * sizeof(uint32_t), st));
+            P.shard_r0 = L.shard_r1 > 0 ? L.shard_r0 : 0;
+            P.shard_r1 = L.shard_r1 > 0 ? L.shard_r1 : ix->tp_ranges;
+            P.ghist = L.phase == 2 ? L.ghist : nullptr;
+            if (L.phase != 2)
+                TACO_CUDA(cudaMemsetAsync(L.qflag, 0, size_t(L.nq + 2) * sizeof(uint32_t), st));
             // pass 1: counting per (query, id range) unit; 256, 512 or 1024 threads per CTA and
             // 2, 4 or 8 chunk windows per walk round (tuned)
-            const size_t smem1 = P.region_a + count_lists_extra();
             struct CountVariant {
                 int nw, wu, cb;
                 void (*fn)(const RerankParams);
@@ -1040,6 +1070,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                     c1 = v;
             const int nw1 = kVariants[c1].nw;
             auto k1 = kVariants[c1].fn;
+            const size_t smem1 = P.region_a + count_lists_extra(nw1);   // (a level-count row per warp)
             static thread_local size_t c1_smem[kNumVariants] = {};
             static thread_local int c1_blocks[kNumVariants] = {};
             if (c1_smem[c1] != smem1) {
@@ -1053,16 +1084,28 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             }
             // a batch smaller than the resident CTAs splits each query's ranges into runs
             // (work items) so that more CTAs count it
+            const int own = P.shard_r1 - P.shard_r0;   // ranges this launch counts
             P.range_parts = 1;
             if (L.nq < c1_blocks[c1]) {
-                const int want = int(std::min<int64_t>(P.n_ranges, (c1_blocks[c1] + L.nq - 1) / L.nq));
-                const int per_part = (P.n_ranges + want - 1) / want;
-                P.range_parts = (P.n_ranges + per_part - 1) / per_part;
+                const int want = int(std::min<int64_t>(own, (c1_blocks[c1] + L.nq - 1) / L.nq));
+                const int per_part = (own + want - 1) / want;
+                P.range_parts = (own + per_part - 1) / per_part;
             }
-            if (int rc = prof_begin(pix, 2, st, &pb, &pe)) return rc;
-            k1<<<unsigned(std::min<int64_t>(L.nq * P.range_parts, c1_blocks[c1])), nw1 * 32, smem1, st>>>(P);
-            TACO_CUDA(cudaGetLastError());
-            if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
+            if (L.phase != 2) {
+                if (int rc = prof_begin(pix, 2, st, &pb, &pe)) return rc;
+                k1<<<unsigned(std::min<int64_t>(L.nq * P.range_parts, c1_blocks[c1])), nw1 * 32, smem1, st>>>(P);
+                TACO_CUDA(cudaGetLastError());
+                if (int rc = prof_end(pix, 2, st, pb, pe)) return rc;
+            }
+            if (L.phase == 1) {
+                // the shard's level counts for the all-shard sum (Alg. 5 needs the whole
+                // histogram): [q][0] = the shard's points, [q][j] = its ids with SC >= j
+                const int64_t lo = int64_t(P.shard_r0) * ix->tp_spc * kSlabIds;
+                const int64_t hi = std::min<int64_t>(int64_t(P.shard_r1) * ix->tp_spc * kSlabIds, ix->n);
+                TACO_CUDA(launch_shard_hist(L.unit_ge, L.nq, ix->tp_ranges, P.shard_r0, P.shard_r1, ix->Ns,
+                                            hi - lo, L.shard_hist, st));
+                return TACO_OK;
+            }
             // pass 2: Alg. 5, candidates, re-rank, results
             const size_t smem2 = select_smem_bytes(P.kkc, ix->d_pad, fp8 ? ix->dp8 : 0, P.n_ranges, ix->Ns, K, false);
             if (int rc = prof_begin(pix, 3, st, &pb, &pe)) return rc;
@@ -1075,8 +1118,9 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
             P.region_a = (size_t(P.counter_words) * 4 + 15) & ~size_t(15);
             P.n_ranges = ix->cluster;
         }
-        if (two_pass && ix->codes_fallback) {
+        if (two_pass && (ix->codes_fallback || L.phase == 2)) {
             // codes fallback for the flagged queries: the select pass again, in fallback mode
+            // (a shard always takes it: the cluster kernel counts every id of the index)
             P.fb_mode = 1;
             P.codes = ix->d_codes;
             P.slabs_per_cta = ix->tp_spc;

@@ -271,17 +271,22 @@ select_rerank_kernel(const RerankParams P) {
         __syncthreads();
         if (P.fb_mode && !s_flag) continue;   // the fallback answers flagged queries only
         if (!P.fb_mode) {
-        // Alg. 5 over the summed level counts of the query's ranges
+        // Alg. 5 over the summed level counts of the query's ranges (with shards: over the
+        // counts summed across all shards, so every shard finds the same threshold)
         if (tid < Ns) {
-            uint32_t v = 0;
-            for (int r = 0; r < nr; ++r) v += P.unit_ge[(q * nr + r) * 16 + tid + 1];
-            s_gs[tid + 1] = v;
+            uint64_t v = 0;
+            if (P.ghist) {
+                v = uint64_t(P.ghist[q * (Ns + 1) + tid + 1]);
+            } else {
+                for (int r = 0; r < nr; ++r) v += P.unit_ge[(q * nr + r) * 16 + tid + 1];
+            }
+            s_gs[tid + 1] = uint32_t(v);   // <= n < 2^32
         }
         __syncthreads();
         if (tid == 0) {
             long long gs[TACO_MAX_SUBSPACES + 2];
-            gs[0] = P.n;
-            for (int j = 1; j <= Ns; ++j) gs[j] = s_gs[j];
+            gs[0] = P.ghist ? P.ghist[q * (Ns + 1)] : P.n;
+            for (int j = 1; j <= Ns; ++j) gs[j] = (long long)s_gs[j];
             gs[Ns + 1] = 0;
             int last = Ns;
             long long cand = 0;
@@ -355,11 +360,15 @@ select_rerank_kernel(const RerankParams P) {
             // cell codes and per-subspace bitmaps of the probed cells; every probed id is
             // taken once (in the first subspace that probed it) if SC >= last; last <= 0
             // takes every point (Alg. 5 reaching level 0)
+            // (a shard: the ids of its ranges only, slabs [fb_slab0, fb_slab1))
+            const int fb_slab0 = P.shard_r0 * P.slabs_per_cta;
+            const int fb_slab1 = min(P.shard_r1 * P.slabs_per_cta, P.n_slabs);
+            const int64_t fb_id1 = min(int64_t(fb_slab1) << kSlabLog2, P.n);
             if (last <= 0) {
-                for (int64_t t0 = 0; t0 < P.n; t0 += kSrThreads) {
+                for (int64_t t0 = int64_t(fb_slab0) << kSlabLog2; t0 < fb_id1; t0 += kSrThreads) {
                     make_room();
                     const int64_t id = t0 + tid;
-                    const bool take = id < P.n;
+                    const bool take = id < fb_id1;
                     const uint32_t at = warp_append_slot(take, &s_bufn, lane);
                     if (take && TACO_CHECK(P.status, at < uint32_t(kSrBuf), kStatusSelect)) ci[at] = uint32_t(id);
                     __syncthreads();
@@ -387,9 +396,9 @@ select_rerank_kernel(const RerankParams P) {
                         while (g >= s_fpre[i + 1]) ++i;
                         const int c = P.cells[(q * Ns + i) * P.K + (g - s_fpre[i])];
                         const uint32_t* sp = P.split + (size_t(i) * P.K + c) * sstride;
-                        fst[tid] = sp[0];
+                        fst[tid] = sp[fb_slab0];
                         fsub[tid] = uint32_t(i);
-                        len = sp[P.n_slabs] - sp[0];
+                        len = sp[fb_slab1] - sp[fb_slab0];
                     }
                     uint2 tot;
                     const uint2 ex = block_excl_scan2<kSrWarps>(len, 0u, s_tmp2, tot, lane, warp);
@@ -435,22 +444,24 @@ select_rerank_kernel(const RerankParams P) {
         // level 2 .. s, so exactly the ids with SC >= last have one tagged last), in tiles of
         // kEntryLoads x kSrThreads entries (each thread's loads of a tile are independent); the
         // buffer is re-ranked and emptied before a tile that would not fit
-        uint32_t* upre = fbm;            // [nr + 1] (the fallback's bitmaps are not in use)
-        uint32_t* uoff = upre + nr + 1;  // [nr]
+        // (a shard takes the units of its ranges [shard_r0, shard_r1) only; local index r)
+        const int nsr = P.shard_r1 - P.shard_r0;
+        uint32_t* upre = fbm;             // [nsr + 1] (the fallback's bitmaps are not in use)
+        uint32_t* uoff = upre + nsr + 1;  // [nsr]
         uint32_t nent = 0;
-        for (int r0 = 0; r0 < nr; r0 += kSrThreads) {
+        for (int r0 = 0; r0 < nsr; r0 += kSrThreads) {
             const int r = r0 + tid;
             uint32_t len = 0;
-            if (r < nr) {
-                len = P.unit_len[q * nr + r];
-                uoff[r] = P.unit_off[q * nr + r];
+            if (r < nsr) {
+                len = P.unit_len[q * nr + P.shard_r0 + r];
+                uoff[r] = P.unit_off[q * nr + P.shard_r0 + r];
             }
             uint2 tot;
             const uint2 ex = block_excl_scan2<kSrWarps>(len, 0u, s_tmp2, tot, lane, warp);
-            if (r < nr) upre[r] = nent + ex.x;
+            if (r < nsr) upre[r] = nent + ex.x;
             nent += tot.x;
         }
-        if (tid == 0) upre[nr] = nent;
+        if (tid == 0) upre[nsr] = nent;
         __syncthreads();
         constexpr uint32_t kTile = uint32_t(kEntryLoads) * kSrThreads;
         for (uint32_t t0 = 0; t0 < nent; t0 += kTile) {
@@ -462,7 +473,7 @@ select_rerank_kernel(const RerankParams P) {
                 x[j] = 0u;
                 rlo[j] = 0xffffffffu;   // no entry
                 if (t < nent) {
-                    int lo_r = 0, hi_r = nr - 1;   // the range holding entry t
+                    int lo_r = 0, hi_r = nsr - 1;   // the range holding entry t
                     while (lo_r < hi_r) {
                         const int mid = (lo_r + hi_r + 1) >> 1;
                         if (upre[mid] <= t) lo_r = mid;
@@ -470,7 +481,7 @@ select_rerank_kernel(const RerankParams P) {
                     }
                     const size_t ap = size_t(uoff[lo_r]) + (t - upre[lo_r]);
                     x[j] = TACO_CHECK(P.status, ap < P.arena_words, kStatusSelect) ? P.arena[ap] : 0u;
-                    rlo[j] = uint32_t(int64_t(lo_r) * P.slabs_per_cta << kSlabLog2);
+                    rlo[j] = uint32_t(int64_t(P.shard_r0 + lo_r) * P.slabs_per_cta << kSlabLog2);
                 }
             }
 #pragma unroll

@@ -116,6 +116,11 @@ SIGNATURES = {
     "taco_search_batch_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
                                             C.POINTER(QueryParams), C.c_int32, C.c_void_p,
                                             C.c_void_p, C.c_void_p]),
+    "taco_shard_count": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                   C.c_void_p, C.POINTER(QueryParams), C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
+    "taco_shard_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "taco_shard_free": (C.c_int, [C.c_void_p]),
     "taco_search_debug": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                     C.POINTER(QueryParams), C.c_int32, C.c_void_p, C.c_void_p,
                                     C.POINTER(DebugOut), C.c_void_p]),
@@ -421,6 +426,50 @@ class TacoIndex:
             C.byref(defaults), k_stride, _ptr(out_ids), _ptr(out_dists), _stream_handle(stream)))
         return out_ids, out_dists
 
+    def shard_count(self, shard, n_shards, queries, k, budget, rerank_target, precision="fp32",
+                    select_rule="literal", shortlist_mult=4, per_query=None, k_stride=None,
+                    stream=None, probe_precision="fp32"):
+        """taco_shard_count: the transform, probe and counting of id-range shard `shard` of
+        `n_shards`; returns (ShardSearch, its level counts [nq, N_s + 1] int64)."""
+        q, nq, defaults, pq, k_stride = self._prepare(queries, k, budget, rerank_target, precision,
+                                                      select_rule, shortlist_mult, per_query, k_stride,
+                                                      probe_precision)
+        hist = np.empty((nq, self.info()["n_subspaces"] + 1), dtype=np.int64)
+        h = C.c_void_p()
+        _check(load_library().taco_shard_count(
+            self._h, int(shard), int(n_shards), _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
+            C.byref(defaults), k_stride, hist.ctypes.data, _stream_handle(stream), C.byref(h)))
+        return ShardSearch(h, nq, k_stride), hist
+
+    def search_sharded(self, queries, k, budget, rerank_target, n_shards, precision="fp32",
+                       select_rule="literal", shortlist_mult=4, per_query=None, k_stride=None,
+                       stream=None, probe_precision="fp32"):
+        """Alg. 6 split over `n_shards` id-range shards of this index, run one after another
+        on its device: every shard counted, the level counts summed, every shard selected,
+        the shards' k nearest merged (paper_2603_24919_gb300.sharding). Returns host
+        (ids int64 [nq, k_stride], dists float32 [nq, k_stride])."""
+        from . import sharding
+        shards, hists = [], []
+        try:
+            for s in range(n_shards):
+                sh, hist = self.shard_count(s, n_shards, queries, k, budget, rerank_target, precision,
+                                            select_rule, shortlist_mult, per_query, k_stride, stream,
+                                            probe_precision)
+                shards.append(sh)
+                hists.append(hist)
+            g = sharding.reduce_counts(hists)
+            parts = [sh.select(g, stream) for sh in shards]
+        finally:
+            for sh in shards:
+                sh.close()
+        ks = None
+        if per_query is not None:
+            arr = per_query if isinstance(per_query, C.Array) else query_param_array(per_query)
+            ks = [arr[j].k for j in range(len(arr))]
+        elif k < parts[0][0].shape[1]:
+            ks = [k] * parts[0][0].shape[0]
+        return sharding.merge_topk(parts, parts[0][0].shape[1], ks)
+
     def prepare(self, per_query, stream=None):
         """taco_params_create: the per-query parameters (QueryParams or dicts for query_params)
         copied to the device once; pass the result to search_prepared."""
@@ -528,6 +577,34 @@ class TacoIndex:
             _stream_handle(stream)))
         dbg["ids"], dbg["dists"] = out_ids, out_dists
         return dbg
+
+
+class ShardSearch:
+    """A shard's device state between taco_shard_count and taco_shard_select."""
+
+    def __init__(self, handle, nq, k_stride):
+        self.handle, self.nq, self.k_stride = handle, nq, k_stride
+
+    def select(self, global_hist, stream=None):
+        """taco_shard_select with the level counts summed over all shards; returns the
+        shard's (ids int64 [nq, k_stride], dists float32 [nq, k_stride]) on the host."""
+        g = np.ascontiguousarray(global_hist, dtype=np.int64)
+        ids = np.empty((self.nq, self.k_stride), dtype=np.int64)
+        dists = np.empty((self.nq, self.k_stride), dtype=np.float32)
+        _check(load_library().taco_shard_select(self.handle, g.ctypes.data, ids.ctypes.data,
+                                                dists.ctypes.data, _stream_handle(stream)))
+        return ids, dists
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().taco_shard_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class PreparedParams:

@@ -98,12 +98,13 @@ def test_ncu_figures_follow_the_kernel_source(monkeypatch):
     the current one."""
     import json
     import os
-    j = json.load(open(os.path.join(bench.ROOT, "profiles", "count_lists_sift1m.json")))
+    j = json.load(open(os.path.join(bench.ROOT, "profiles", "count_lists_deep10m.json")))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: j["bf16"]["source_hash"])
-    assert bench.ncu_traffic("count_lists", "bf16") == j["bf16"]["dram_bytes_per_launch_full_batch"]
+    assert bench.ncu_traffic("count_lists", "bf16", "deep10m") == j["bf16"]["dram_bytes_per_launch_full_batch"]
     if j.get("limiter", {}).get("source_hash") == j["bf16"]["source_hash"]:
-        assert bench.ncu_limiter("count_lists")["issue_active_pct"] > 0
+        assert bench.ncu_limiter("count_lists", "deep10m")["issue_active_pct"] > 0
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
-    assert bench.ncu_traffic("count_lists", "bf16") is None
-    assert bench.ncu_limiter("count_lists") is None
-    assert bench.ncu_traffic("no_such_kernel", "bf16") is None
+    assert bench.ncu_traffic("count_lists", "bf16", "deep10m") is None
+    assert bench.ncu_limiter("count_lists", "deep10m") is None
+    assert bench.ncu_traffic("no_such_kernel", "bf16", "deep10m") is None
+    assert bench.ncu_traffic("count_lists", "bf16", "no_such_workload") is None
