@@ -43,12 +43,12 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Shared memory of count_lists_kernel (nw warps) past the counters and their 32 spare words
-// (bytes): split bounds of the staged cells for two ranges, two staging buffers of chunk runs,
-// one row of level counts per warp, and the staged cells.
-__host__ __device__ __forceinline__ size_t count_lists_extra(int nw) {
+// Shared memory of count_lists_kernel past the counters and their 32 spare words (bytes):
+// split bounds of the staged cells for two ranges, two staging buffers of chunk runs, the
+// level counts and the staged cells.
+__host__ __device__ __forceinline__ size_t count_lists_extra() {
     return size_t(2) * kCellBatch * 8 + size_t(2) * kCellBatch * 4 + size_t(2) * (kCellBatch + kRunPad) * 4 +
-           size_t(nw) * 16 * 4 + size_t(kCellBatch) * 4;
+           16 * 4 + size_t(kCellBatch) * 4;
 }
 
 // The chunk run of id positions [b, e) of one cell list: chunks [b / 4, ceil(e / 4)), none
@@ -126,8 +126,9 @@ __device__ __forceinline__ void issue_round(WalkRound<WU>& R, const uint4* __res
 // Count a round whose loads are in R against the unit's range [lo, lo + rlen): every id of a
 // live chunk in the range adds 1 to its CB-bit counter; when the atomic's old value v is >= 1
 // the id has just reached level v + 1 >= 2 and is appended to the unit's arena slot `out` as
-// (id - lo) | (v + 1) << kLevelShift, and ge[v + 1] (the warp's own row of level counts, so
-// that the warps' counting atomics do not contend) counts it. Ids outside the range (the
+// (id - lo) | (v + 1) << kLevelShift, and ge[v + 1] counts it. (One row of level counts per
+// warp, summed at the end of the unit, was measured slower: the sum lengthens the unit's
+// barrier-to-barrier tail.) Ids outside the range (the
 // chunk's neighbours in the same cell list, padding) and idle lanes add 0 to the lane's own
 // spare word cnt[counter_words + lane] (which stays 0), so no branch depends on the data and
 // every atomic is a shared-memory one on cnt. Entries beyond `cap` are counted in *s_app but
@@ -276,9 +277,8 @@ count_lists_kernel(const RerankParams P) {
     uint2* pairs = reinterpret_cast<uint2*>(smem + P.region_a);               // [2][kCellBatch]
     uint32_t* rbase = reinterpret_cast<uint32_t*>(pairs + 2 * kCellBatch);    // [2][kCellBatch]
     uint32_t* cpre = rbase + 2 * kCellBatch;                                  // [2][kPre]
-    uint32_t* ge_rows = cpre + 2 * kPre;                                      // [NW][16]
-    uint32_t* ge = ge_rows + warp * 16;                                       // this warp's row
-    uint32_t* qcell = ge_rows + NW * 16;                                      // kCellBatch
+    uint32_t* ge = cpre + 2 * kPre;                                           // [16]
+    uint32_t* qcell = ge + 16;                                                // kCellBatch
     __shared__ int s_pre[TACO_MAX_SUBSPACES + 1];
     __shared__ uint32_t s_tmp[2 * NW];
     __shared__ uint32_t s_app, s_ev;
@@ -293,7 +293,7 @@ count_lists_kernel(const RerankParams P) {
     const uint32_t cap = P.arena_per_unit;
     // the counters and, past them, one spare word per lane for the walk's idle atomics
     for (int w = tid; w < P.counter_words + 32; w += NW * 32) cnt[w] = 0u;
-    for (int t = tid; t < NW * 16; t += NW * 32) ge_rows[t] = 0u;
+    if (tid < 16) ge[tid] = 0u;
     if (tid == 0) {
         s_app = 0u;
         s_round = 0u;
@@ -421,24 +421,19 @@ count_lists_kernel(const RerankParams P) {
             }
             if (warp == 0) {
                 // the unit's outputs: ge[1] = events - entries (an id with SC = s has s - 1
-                // entries), ge[j >= 2] = entries tagged j (summed over the warps' rows); then the
-                // shared state for the next range
+                // entries), ge[j >= 2] = entries tagged j; then the shared state for the next range
                 const uint32_t apps = s_app;
                 const bool fits = apps <= cap;
                 if (lane == 0) {
+                    ge[1] = (staged ? s_ev2[(r - rb) & 1] : s_ev) - apps;
                     P.unit_off[u] = fits ? uint32_t(u) * P.arena_per_unit : 0xffffffffu;
                     P.unit_len[u] = fits ? apps : 0u;
                     if (!fits) P.qflag[q] = 1u;   // entries lost: the query takes the fallback
                 }
+                __syncwarp();
                 if (lane < 16) {
-                    uint32_t v = 0;
-#pragma unroll 4
-                    for (int w = 0; w < NW; ++w) {
-                        v += ge_rows[w * 16 + lane];
-                        ge_rows[w * 16 + lane] = 0u;
-                    }
-                    if (lane == 1) v = (staged ? s_ev2[(r - rb) & 1] : s_ev) - apps;
-                    P.unit_ge[u * 16 + lane] = v;
+                    P.unit_ge[u * 16 + lane] = ge[lane];
+                    ge[lane] = 0u;
                 }
                 if (lane == 0) {
                     s_app = 0u;

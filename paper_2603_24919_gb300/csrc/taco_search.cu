@@ -1070,7 +1070,7 @@ int run_search_chunk(const SearchLaunch& L, cudaStream_t st) {
                     c1 = v;
             const int nw1 = kVariants[c1].nw;
             auto k1 = kVariants[c1].fn;
-            const size_t smem1 = P.region_a + count_lists_extra(nw1);   // (a level-count row per warp)
+            const size_t smem1 = P.region_a + count_lists_extra();
             static thread_local size_t c1_smem[kNumVariants] = {};
             static thread_local int c1_blocks[kNumVariants] = {};
             if (c1_smem[c1] != smem1) {
