@@ -175,3 +175,11 @@ def test_noalloc_method_checks_before_calling(monkeypatch):
     with pytest.raises(ValueError):
         ix.search_noalloc(q, ids.int(), dists, 5, 10, 1)
     ix._h = None
+
+
+def test_max_k_reads_the_records():
+    import numpy as np
+    from paper_2603_24919_gb300 import taco as T
+    ks = np.random.default_rng(1).integers(1, 300, 1000)
+    arr = T.query_param_array([dict(k=int(k), budget=7, rerank_target=3) for k in ks])
+    assert T._max_k(arr) == int(ks.max())
