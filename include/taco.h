@@ -47,10 +47,12 @@ extern "C" {
 #define TACO_PREC_FP32 0    /* re-rank candidates with FP32 distances */
 #define TACO_PREC_BF16 1    /* re-rank with a BF16 copy of D, then exact FP32 on a shortlist */
 #define TACO_PREC_FP8 2     /* re-rank with an FP8-e4m3 copy of the points, then exact FP32 on a
-                               shortlist: of the transformed points B^T (o - o_bar) with one
-                               scale per subspace when N_s*s = d (distances preserved, Lemma 1),
-                               else of the centred points o - o_bar with one scale per block of
-                               16 dimensions */
+                               shortlist: of the transformed points B^T (o - o_bar) when
+                               N_s*s = d (distances preserved, Lemma 1), else of the centred
+                               points o - o_bar; one scale per block of 16 dimensions. The
+                               candidate distances form each block's differences and squares in
+                               half precision (query coordinates clamped to 4x the block's
+                               largest point coordinate) and sum the blocks in FP32 */
 
 /* Row copies an index keeps besides the FP32 rows (bit mask, the keep_rows arguments). */
 #define TACO_ROWS_BF16 1    /* BF16 copy of D, [n][d_pad] */
@@ -116,7 +118,8 @@ typedef struct {
                                   0 when n is too large for a cluster (codes fallback) */
     int32_t has_fp8;           /* FP8 rows kept (TACO_ROWS_FP8) */
     int32_t fp8_pitch;         /* row pitch of the FP8 rows in bytes (N_s*s, or d when N_s*s < d,
-                                  rounded up to 16) */
+                                  rounded up to a power of two up to 64, else to whole
+                                  128-byte lines) */
     int32_t has_centroid_tc;   /* the tcgen05 centroid blocks (BF16 and E4M3) are available
                                   (sqrt_k <= 128 and the operands of 128 queries fit shared memory) */
     int32_t reserved;
@@ -155,9 +158,9 @@ int taco_build_index(const float* data, int64_t n, int32_t d, const taco_build_p
  *   data host or device [n][d] float32; parts host pointers as in taco_index_parts.
  *   keep_rows TACO_ROWS_* mask of the reduced-precision row copies to build.
  * Cell lists are rebuilt from codes with ids ascending in every cell. Synchronises `stream`.
- * FP8 rows: every point is transformed (Alg. 1) or centred (see TACO_PREC_FP8), each group's
- * scale is its largest |coordinate| / 448 (the e4m3 maximum), and coordinates are rounded to
- * nearest e4m3.
+ * FP8 rows: every point is transformed (Alg. 1) or centred (see TACO_PREC_FP8), each block
+ * of 16 dimensions' scale is its largest |coordinate| / 448 (the e4m3 maximum), and
+ * coordinates are rounded to nearest e4m3.
  */
 int taco_index_create(const float* data, int64_t n, int32_t d, const taco_index_parts* parts,
                       int32_t keep_rows, void* stream, taco_index** out);

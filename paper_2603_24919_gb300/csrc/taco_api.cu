@@ -125,11 +125,12 @@ int enable_codes_fallback(taco_index* ix) {
     return TACO_OK;
 }
 
-// FP8-e4m3 rows with one scale per group of dimensions (the group's largest |coordinate|
-// over all points / 448). When N_s * s = d the rows are the transformed points B^T (o - o_bar)
-// and a group is a subspace (distances are preserved, Lemma 1); otherwise the transform
-// drops dimensions, so the rows are the centred points o - o_bar and a group is a block of
-// 16 dimensions. Two passes over chunks of points: scales, then quantisation.
+// FP8-e4m3 rows with one scale per block of 16 dimensions (the block's largest |coordinate|
+// over all points / 448; a block is one 16-byte chunk of a row, so the select pass applies
+// one scale per chunk). When N_s * s = d the rows are the transformed points B^T (o - o_bar)
+// (distances are preserved, Lemma 1); otherwise the transform drops dimensions, so the rows
+// are the centred points o - o_bar. Two passes over chunks of points: scales, then
+// quantisation.
 int build_fp8_rows(taco_index* ix, cudaStream_t st) {
     const int64_t n = ix->n;
     const bool transformed = ix->Dp == ix->d;
@@ -172,7 +173,7 @@ int build_fp8_rows(taco_index* ix, cudaStream_t st) {
     TACO_CUDA(cudaMemcpyAsync(mb.data(), maxbits, size_t(cols) * 4, cudaMemcpyDeviceToHost, st));
     TACO_CUDA(cudaStreamSynchronize(st));
     std::vector<float> sc(size_t(2) * ix->dp8, 0.f);   // [scale | 1/scale]
-    const int group = transformed ? ix->s : 16;
+    const int group = 16;
     for (int g0 = 0; g0 < cols; g0 += group) {
         const int g1 = std::min(cols, g0 + group);
         float m = 0.f;

@@ -231,15 +231,17 @@ __device__ __forceinline__ uint32_t shr_clamped(uint32_t a, uint32_t b) {
     return r;
 }
 
-// FP8 query pairs: float4 slot of dimensions 2j', 2j' + 1 (j' = 0..7) of 16-dimension chunk
-// f. The 8 slots of a chunk are permuted by f mod 8, so that lanes reading the same j' of
-// different chunks (the G lanes of a row) hit different shared-memory banks.
-__device__ __forceinline__ int fp8_query_slot(int f, int jp) { return (f << 3) | (jp ^ (f & 7)); }
+// FP8 rows: the query's coordinates are divided by kFp8Pre (and clamped to kFp8Clamp / kFp8Pre)
+// in half precision, so that a difference is at most (kFp8Clamp + 448) / kFp8Pre = 70, its
+// square at most 4,900 and a half2 lane's sum over 8 dimensions at most 39,200 < 65,504.
+constexpr float kFp8Pre = 32.f;
+constexpr float kFp8Clamp = 4.f * 448.f;
 
 // Squared distance contribution of one 16-byte row chunk f. FP32 / BF16: qv is the query
-// (d_pad floats). FP8: qv holds (q'_c / scale_c, scale_c^2) pairs of the transformed query
-// (slots permuted by fp8_query_slot), so the chunk adds
-// sum_c scale_c^2 (q'_c / scale_c - x8_c)^2 = sum_c (q'_c - scale_c x8_c)^2.
+// (d_pad floats). FP8: qv holds 48 bytes per chunk, the query's 16 coordinates in half
+// precision (q'_c / scale_f / kFp8Pre) and the chunk's weight scale_f^2 kFp8Pre^2 as a float;
+// the chunk adds scale_f^2 sum_c (q'_c / scale_f - x8_c)^2 = sum_c (q'_c - scale_f x8_c)^2,
+// the 16 squares formed and summed in half2 (two 8-term sums) and weighted in FP32.
 template <int RK>
 __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, float acc) {
     if constexpr (RK == kRowF32) {
@@ -258,22 +260,30 @@ __device__ __forceinline__ float chunk_dist(uint4 raw, const float* qv, int f, f
         acc = sq4(make_float4(a0.x, a0.y, a1.x, a1.y), q0, acc);
         return sq4(make_float4(a2.x, a2.y, a3.x, a3.y), q1, acc);
     } else {
-        const float4* qw = reinterpret_cast<const float4*>(qv);   // 2 dims per float4
+        // chunk f's 48 bytes of the query: 16 halves, then its float weight (the 48-byte
+        // stride puts the G lanes of a row, reading consecutive chunks, on different banks)
+        const unsigned char* qc = reinterpret_cast<const unsigned char*>(qv) + 48 * f;
+        const uint4 qa = *reinterpret_cast<const uint4*>(qc);
+        const uint4 qb = *reinterpret_cast<const uint4*>(qc + 16);
+        const float w = *reinterpret_cast<const float*>(qc + 32);
+        const uint32_t qp[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
         const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+        const __half2 neg_pre = __float2half2_rn(-1.f / kFp8Pre);
+        __half2 s2 = __float2half2_rn(0.f);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const __half2 x2(__nv_cvt_fp8x2_to_halfraw2(
                     __nv_fp8x2_storage_t((w4[u] >> (16 * h)) & 0xffffu), __NV_E4M3));
-                const float2 x = __half22float2(x2);
-                const float4 p = qw[fp8_query_slot(f, 2 * u + h)];   // (qs_a, w_a, qs_b, w_b)
-                const float da = p.x - x.x, db = p.z - x.y;
-                acc = fmaf(p.y * da, da, acc);
-                acc = fmaf(p.w * db, db, acc);
+                __half2 q2;
+                memcpy(&q2, &qp[2 * u + h], 4);
+                const __half2 dd = __hfma2(x2, neg_pre, q2);   // (q_c - x_c) / kFp8Pre
+                s2 = __hfma2(dd, dd, s2);
             }
         }
-        return acc;
+        const float2 sf = __half22float2(s2);
+        return fmaf(w, sf.x + sf.y, acc);
     }
 }
 

@@ -216,7 +216,7 @@ select_rerank_kernel(const RerankParams P) {
     float* cd = qv + P.d_pad;                                           // [kSrBuf + TACO_MAX_K]
     uint32_t* ci = reinterpret_cast<uint32_t*>(cd + kSrBuf + TACO_MAX_K);   // candidate ids, same
     uint32_t* hist = ci + kSrBuf + TACO_MAX_K;                          // [kSelHist]
-    float* qf = reinterpret_cast<float*>(hist + kSelHist);              // FP8: [dp8][2]
+    float* qf = reinterpret_cast<float*>(hist + kSelHist);              // FP8: 48 B a chunk (of 8 dp8)
     // codes fallback: probed-cell bitmaps [Ns][K / 32] and one batch of cells' runs
     uint32_t* fbm = reinterpret_cast<uint32_t*>(qf + (RK == kRowFP8 ? 2 * P.dp8 : 0));
     uint32_t* fpre = fbm + P.Ns * ((P.K + 31) / 32);                    // [kSrThreads + 1]
@@ -248,18 +248,24 @@ select_rerank_kernel(const RerankParams P) {
         __syncthreads();
         for (int j = tid; j < P.d_pad; j += kSrThreads) qv[j] = j < P.d ? P.queries[q * P.d + j] : 0.f;
         if constexpr (kFP8) {
-            // (x_c / scale_c, scale_c^2) of the query in the FP8 rows' space: the transformed
-            // query q' (zero past N_s * s) or the centred query q - o_bar (zero past d)
-            // (the float4 slots of 16-dimension chunk f are permuted by f mod 8, so that the
-            // lanes of a row reading different chunks hit different banks: fp8_query_slot)
+            // the query in the FP8 rows' space (the transformed query q', zero past N_s * s,
+            // or the centred query q - o_bar, zero past d), per dimension c as
+            // x_c / scale_c / kFp8Pre in half precision, clamped to kFp8Clamp / kFp8Pre (a
+            // query coordinate beyond 4x the points' largest keeps the half-precision sums of
+            // a chunk finite), and per 16-dimension chunk its scale^2 * kFp8Pre^2
+            // (48 bytes per 16-dimension chunk: 16 halves, the weight, 12 bytes unused)
             const int cols = P.fp8_space ? P.d : P.Dp;
+            unsigned char* qc = reinterpret_cast<unsigned char*>(qf);
             for (int j = tid; j < P.dp8; j += kSrThreads) {
-                const float sc = P.fp8_scale[j];
                 float x = 0.f;
                 if (j < cols) x = P.fp8_space ? P.queries[q * P.d + j] - P.obar[j] : P.qt[q * P.Dp + j];
-                float* slot = qf + 4 * fp8_query_slot(j >> 4, (j >> 1) & 7) + 2 * (j & 1);
-                slot[0] = j < cols ? x * P.fp8_scale[P.dp8 + j] : 0.f;
-                slot[1] = j < cols ? sc * sc : 0.f;
+                const float xs = fminf(fmaxf(x * P.fp8_scale[P.dp8 + j], -kFp8Clamp), kFp8Clamp);
+                reinterpret_cast<__half*>(qc + 48 * (j >> 4))[j & 15] =
+                    __float2half_rn(j < cols ? xs * (1.f / kFp8Pre) : 0.f);
+                if ((j & 15) == 0) {
+                    const float sc = P.fp8_scale[j];
+                    *reinterpret_cast<float*>(qc + 48 * (j >> 4) + 32) = sc * sc * (kFp8Pre * kFp8Pre);
+                }
             }
         }
         if (tid <= TACO_MAX_SUBSPACES + 1) s_gs[tid] = 0u;

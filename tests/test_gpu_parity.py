@@ -321,7 +321,7 @@ def test_fp8_shortlist_covering_the_candidates_matches_oracle(tiny, tiny_fp8):
 
 
 def test_fp8_recall_close_to_fp32(tiny, tiny_fp8):
-    """FP8-e4m3 rows with per-subspace scales and an exact FP32 re-rank of a 4k shortlist
+    """FP8-e4m3 rows with per-16-dimension scales and an exact FP32 re-rank of a 4k shortlist
     lose at most 0.02 of recall@10 against the FP32 form; distances are exact FP32 ones."""
     w, data, queries, oix, ix32 = tiny
     q = torch.from_numpy(queries).cuda()
@@ -336,6 +336,27 @@ def test_fp8_recall_close_to_fp32(tiny, tiny_fp8):
     ok = ei >= 0
     exact = np.sqrt(((data[np.where(ok, ei, 0)].astype(np.float64) - queries[:, None, :]) ** 2).sum(-1))
     assert np.allclose(e_d.cpu().numpy()[ok], exact[ok], rtol=1e-5)
+
+
+def test_fp8_outlier_queries_stay_finite(tiny, tiny_fp8):
+    """Queries far outside the points' range (coordinates up to 10x theirs): the FP8 pass
+    clamps their half-precision coordinates at 4x the block's largest point coordinate, so
+    every candidate distance stays finite; the FP32 shortlist re-rank returns exact distances
+    and the same results as the FP32 form when the shortlist covers the candidates."""
+    w, data, queries, oix, ix32 = tiny
+    centre = data.mean(0)
+    far = (centre + 10.0 * (queries - centre)).astype(np.float32)
+    q = torch.from_numpy(far).cuda()
+    f_ids, f_d = ix32.search(q, 10, w.budget, w.rerank_target)
+    e_ids, e_d = tiny_fp8.search(q, 10, w.budget, w.rerank_target, precision="fp8", shortlist_mult=50)
+    ei, ed = e_ids.cpu().numpy(), e_d.cpu().numpy()
+    assert (ei >= 0).all() and np.isfinite(ed).all()
+    exact = np.sqrt(((data[ei].astype(np.float64) - far[:, None, :]) ** 2).sum(-1))
+    np.testing.assert_allclose(ed, exact, rtol=1e-5)
+    cand = tiny_fp8.search_debug(q, 10, w.budget, w.rerank_target, want_sc=False)["candidate_num"].cpu().numpy()
+    cover = cand <= 500   # (the two forms sum a row's FP32 distance over different lanes:
+    assert cover.any()    # compare the distances, which are equal up to that order)
+    np.testing.assert_allclose(ed[cover], f_d.cpu().numpy()[cover], rtol=1e-6)
 
 
 def test_fp8_needs_fp8_rows(tiny):
