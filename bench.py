@@ -49,8 +49,9 @@ EXTRA_WORKLOAD = "sift1m"     # extra keys of the same line
 KS_BATCHED = (1, 10, 50, 100)   # per-query k of the batched form
 # calibration grid: below the paper's ranges (alpha 0.01-0.1, beta 0.001-0.05) too, since
 # recall@10 reaches 0.95 below them on these stand-ins
-GRID_ALPHA = (0.0005, 0.001, 0.0015, 0.002, 0.003, 0.004, 0.005, 0.0075, 0.01, 0.02, 0.05)
-GRID_BETA = (0.0001, 0.0002, 0.0003, 0.0005, 0.00075, 0.001, 0.002, 0.005)
+GRID_ALPHA = (0.0005, 0.001, 0.0015, 0.002, 0.0025, 0.003, 0.0035, 0.004, 0.0045, 0.005, 0.0075, 0.01,
+              0.02, 0.05)
+GRID_BETA = (0.0001, 0.0002, 0.00025, 0.0003, 0.0004, 0.0005, 0.00075, 0.001, 0.002, 0.005)
 RECALL_TARGET = 0.95
 # (alpha, beta) of the reference arm per workload, near the GPU operating points
 REFERENCE_OP = {"deep10m": (0.005, 0.0005), "sift1m": (0.01, 0.001)}
