@@ -20,7 +20,10 @@ constexpr int kSrThreads = 256;
 constexpr int kSrWarps = kSrThreads / 32;
 constexpr int kSrBuf = 4096;   // candidate ids per re-rank round
 constexpr int kSelHist = 2048;   // bins of one radix pass of the selection (8 a thread)
-constexpr int kGatherRows = 4;   // rows a lane group gathers at once in the streaming pass
+// rows a lane group gathers at once in the streaming pass, and the CTAs per SM the kernel is
+// compiled for (its register budget), per row kind
+template <int RK> constexpr int kGatherRows = RK == kRowBF16 ? 2 : 4;
+template <int RK> constexpr int kSelectBlocksPerSm = RK == kRowF32 ? 4 : 3;
 constexpr int kEntryLoads = 4;   // arena entries a thread loads per tile of the candidate pass
 
 // Squared distances of U queued candidates per lane group (G lanes a row, rows buf[b0 + u *
@@ -201,7 +204,7 @@ inline size_t select_smem_bytes(int kkc, int d_pad, int dp8_or_0, int n_ranges, 
 
 
 template <int G, int RK>
-__global__ void __launch_bounds__(kSrThreads, 3)
+__global__ void __launch_bounds__(kSrThreads, kSelectBlocksPerSm<RK>)
 select_rerank_kernel(const RerankParams P) {
     constexpr int CPW = 32 / G;
     constexpr int U = 2;
@@ -333,7 +336,7 @@ select_rerank_kernel(const RerankParams P) {
                 if (!TACO_CHECK(P.status, ci[i] < uint32_t(P.n), kStatusSelect)) ci[i] = 0u;
             __syncthreads();
 #endif
-            constexpr int UG = kGatherRows;
+            constexpr int UG = kGatherRows<RK>;
             for (int b0 = warp * CPW * UG; b0 < m; b0 += kSrWarps * CPW * UG) {
                 float acc[UG];
                 uint32_t cid[UG];
