@@ -268,7 +268,8 @@ int taco_search_batch_noalloc(const taco_index* index, const float* queries, int
  *   every shard's hist), then the shard's candidates, re-rank and k nearest: out_ids [nq]
  *   [k_stride] int64 and out_dists float (host or device; -1 / +inf past the shard's
  *   candidates). Synchronises `stream`.
- * taco_shard_free -- releases a handle (NULL is a no-op).
+ * taco_shard_free -- releases a handle (NULL is a no-op). A handle refers to its index: free
+ *   every handle of an index before taco_index_free.
  */
 typedef struct taco_shard_search taco_shard_search;
 int taco_shard_count(const taco_index* index, int32_t shard, int32_t n_shards, const float* queries, int64_t nq,

@@ -447,7 +447,7 @@ class TacoIndex:
         _check(load_library().taco_shard_count(
             self._h, int(shard), int(n_shards), _ptr(q), nq, C.cast(pq, C.c_void_p) if pq is not None else None,
             C.byref(defaults), k_stride, hist.ctypes.data, _stream_handle(stream), C.byref(h)))
-        return ShardSearch(h, nq, k_stride), hist
+        return ShardSearch(h, nq, k_stride, self), hist
 
     def search_sharded(self, queries, k, budget, rerank_target, n_shards, precision="fp32",
                        select_rule="literal", shortlist_mult=4, per_query=None, k_stride=None,
@@ -590,13 +590,22 @@ class TacoIndex:
 class ShardSearch:
     """A shard's device state between taco_shard_count and taco_shard_select."""
 
-    def __init__(self, handle, nq, k_stride):
+    def __init__(self, handle, nq, k_stride, index=None):
         self.handle, self.nq, self.k_stride = handle, nq, k_stride
+        self.index = index   # the handle refers to the index: keep it alive
 
     def select(self, global_hist, stream=None):
         """taco_shard_select with the level counts summed over all shards; returns the
         shard's (ids int64 [nq, k_stride], dists float32 [nq, k_stride]) on the host."""
+        if self.handle is None or not self.handle.value:
+            raise ValueError("the shard handle is closed")
+        ih = getattr(self.index, "_h", None)
+        if self.index is not None and (ih is None or not ih.value):
+            raise ValueError("the shard's index is closed")
         g = np.ascontiguousarray(global_hist, dtype=np.int64)
+        n_sub = self.index.info()["n_subspaces"] if self.index is not None else g.shape[-1] - 1
+        if g.shape != (self.nq, n_sub + 1):
+            raise ValueError(f"global_hist must be [{self.nq}, {n_sub + 1}] (got {list(g.shape)})")
         ids = np.empty((self.nq, self.k_stride), dtype=np.int64)
         dists = np.empty((self.nq, self.k_stride), dtype=np.float32)
         _check(load_library().taco_shard_select(self.handle, g.ctypes.data, ids.ctypes.data,

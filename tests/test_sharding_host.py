@@ -106,3 +106,34 @@ def test_two_gloo_ranks_id_range_shards_equal_one_index(tmp_path):
         np.testing.assert_array_equal(ids[qi], t.ids)
         np.testing.assert_allclose(dists[qi], t.dists, rtol=1e-6)
     assert (last[[2, 5]] <= 1).all()   # the cases below level 2 (the codes fallback's) are covered
+
+
+def test_shard_select_checks_its_arguments_before_the_library():
+    import ctypes as C
+
+    from paper_2603_24919_gb300.taco import ShardSearch
+
+    class _Index:   # stands in for TacoIndex: only what the checks read
+        def __init__(self, h):
+            self._h = h
+
+        def info(self):
+            return {"n_subspaces": 6}
+
+    # stand-in handles are never freed: each object's handle is cleared before it goes away
+    g = np.zeros((4, 7), dtype=np.int64)
+    with pytest.raises(ValueError, match="handle is closed"):
+        ShardSearch(C.c_void_p(0), 4, 10, _Index(C.c_void_p(1))).select(g)
+    sh = ShardSearch(C.c_void_p(1), 4, 10, _Index(None))
+    try:
+        with pytest.raises(ValueError, match="index is closed"):
+            sh.select(g)
+    finally:
+        sh.handle = None
+    sh = ShardSearch(C.c_void_p(1), 4, 10, _Index(C.c_void_p(1)))
+    try:
+        for bad in (np.zeros((4, 6), np.int64), np.zeros((3, 7), np.int64), np.zeros(28, np.int64)):
+            with pytest.raises(ValueError, match="global_hist must be"):
+                sh.select(bad)
+    finally:
+        sh.handle = None
